@@ -1,0 +1,23 @@
+"""FP64 CPU oracle of the approximate Gauss-Newton gain solver (arxiv 2412.10072).
+
+TEST INFRASTRUCTURE.  Only the tests, the smoke check and the benchmark's
+CPU-baseline leg may import this package.  It shares no code with the CUDA
+library in ``paper_2412_10072_gb300``: the solver arithmetic lives in
+``qc_oracle.c`` (plain C, double precision); this package compiles it with
+gcc and calls it through ctypes.
+
+Parity status of each oracle function (what pins it, see ``tests/``):
+
+- ``normal_equations``: pinned by finite-difference Wirtinger Jacobians on
+  3-antenna cases for diagonal, full and phase-only terms, by the Hermitian
+  positive-semidefinite invariant and by the StefCal closed form.
+- ``solve``: pinned by exact recovery of the true gains (up to the gauge) on
+  noise-free data, by the 3-antenna closure relations, and by chi^2 = 0 at the
+  truth.
+- ``residual``: pinned by chi^2 = 0 at the true gains on noise-free data and
+  by the noise statistics of chi^2 on noisy data.
+- ``mlp``: pinned by central finite differences of its own loss.
+"""
+from .oracle import (OC_DIAG, OC_FULL, OC_PHASE, OracleProblem, OracleTerm, build,  # noqa: F401
+                     normal_equations, residual, solve, solve_term, block_solve)
+from .gauge import reference_diag, reference_chain, chain_products  # noqa: F401

@@ -1,0 +1,328 @@
+"""Seeded synthetic interferometer observations (input generation only).
+
+This module draws every random number the workloads need and lays the
+results out in the Measurement-Set row order the solver consumes: rows are
+(time, baseline) pairs sorted by time, then by baseline p < q, with
+``ant1``/``ant2``/``time_idx`` per row (the paper's row-to-time mapping,
+Section 4.1) and visibilities stored ``[row][chan][corr]`` with the four
+correlations of each 2x2 matrix in row-major order (Eq. gvec / Eq. jones).
+
+It holds no part of the calibration method: no Jacobians, normal equations,
+block solves or iterations.  Corrupting the predicted visibilities with
+"true" gains (``V = G_p M G_q^H``, the forward measurement equation of
+Eq. baselinemodel) is simulation of the instrument and is written here with
+``numpy.einsum`` independently of both the CPU oracle and the CUDA path,
+which only ever *read* what this module writes.
+
+Sky model: unpolarised point sources, ``M = sum_k S_k exp(-2 pi i nu/c
+(u l + v m + w (n - 1))) * I``, uvw from an east-west array (the textbook
+form; the paper delegates prediction to an external DFT, Section 4.7).
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import Dict, List, Optional
+
+import numpy as np
+
+C_LIGHT = 299_792_458.0
+DEG = np.pi / 180.0
+
+
+# ---------------------------------------------------------------------------
+# geometry and sky
+# ---------------------------------------------------------------------------
+
+def ew_array(n_ant: int, max_baseline_m: float, rng: np.random.Generator) -> np.ndarray:
+    """East-west antenna offsets in metres (sorted, first antenna at 0)."""
+    x = np.sort(rng.uniform(0.0, max_baseline_m, size=n_ant))
+    x[0] = 0.0
+    x[-1] = max_baseline_m
+    return np.sort(x)
+
+
+def baselines(n_ant: int):
+    """All p < q pairs in lexicographic order (no autocorrelations)."""
+    p, q = np.triu_indices(n_ant, k=1)
+    return p.astype(np.int32), q.astype(np.int32)
+
+
+def hour_angles(n_time: int, span_hours: float = 4.0) -> np.ndarray:
+    """Hour angles (radians) uniform over +-span/2 hours across n_time samples."""
+    h = np.linspace(-span_hours / 2.0, span_hours / 2.0, n_time) if n_time > 1 else np.zeros(1)
+    return h * 15.0 * DEG
+
+
+def ew_uvw(ant_x: np.ndarray, p: np.ndarray, q: np.ndarray, ha: np.ndarray,
+           dec: float = -30.0 * DEG) -> np.ndarray:
+    """uvw (metres) for every (time, baseline): shape [n_time, n_bl, 3].
+
+    For an east-west baseline of length b: u = b cos H, v = b sin(dec) sin H,
+    w = -b cos(dec) sin H.
+    """
+    b = (ant_x[q] - ant_x[p])[None, :]
+    H = ha[:, None]
+    u = b * np.cos(H)
+    v = b * np.sin(dec) * np.sin(H)
+    w = -b * np.cos(dec) * np.sin(H)
+    return np.stack([u, v, w], axis=-1)
+
+
+@dataclasses.dataclass
+class Sky:
+    flux: np.ndarray   # [n_src] Jy
+    l: np.ndarray      # [n_src] direction cosines
+    m: np.ndarray
+
+    @property
+    def n(self) -> np.ndarray:
+        return np.sqrt(1.0 - self.l ** 2 - self.m ** 2)
+
+
+def point_sources(n_src: int, rng: np.random.Generator, radius_deg: float = 1.0,
+                  flux_lo: float = 0.1, flux_hi: float = 1.0) -> Sky:
+    """Point sources with flux U(lo, hi) uniformly inside a disk of given radius."""
+    flux = rng.uniform(flux_lo, flux_hi, size=n_src)
+    rad = radius_deg * DEG * np.sqrt(rng.uniform(0.0, 1.0, size=n_src))
+    ang = rng.uniform(0.0, 2 * np.pi, size=n_src)
+    return Sky(flux=flux, l=rad * np.cos(ang), m=rad * np.sin(ang))
+
+
+def predict_scalar(uvw: np.ndarray, freqs: np.ndarray, sky: Sky) -> np.ndarray:
+    """Scalar (Stokes I) visibility for each uvw row and channel: [rows, chan] complex128."""
+    phase = (uvw[:, 0:1] * sky.l[None, :] + uvw[:, 1:2] * sky.m[None, :]
+             + uvw[:, 2:3] * (sky.n[None, :] - 1.0))            # [rows, src] metres
+    out = np.zeros((uvw.shape[0], freqs.size), dtype=np.complex128)
+    for ci, nu in enumerate(freqs):
+        out[:, ci] = np.exp(-2j * np.pi * nu / C_LIGHT * phase) @ sky.flux
+    return out
+
+
+# ---------------------------------------------------------------------------
+# gain truths (each returned on the term's own [n_tint][n_fint][n_ant][4] grid)
+# ---------------------------------------------------------------------------
+
+def interval_map(n: int, width: int) -> np.ndarray:
+    """Map sample index -> solution-interval index for contiguous intervals."""
+    return (np.arange(n) // max(1, width)).astype(np.int32)
+
+
+def diag_truth(n_ant: int, n_tint: int, n_fint: int, rng: np.random.Generator,
+               amp_sigma: float = 0.05, drift_cycles: float = 0.05) -> np.ndarray:
+    """Diagonal complex gains: amplitude 1+N(0,amp_sigma), phase U(-pi,pi) plus a slow drift.
+
+    The drift is sampled at each time interval's centre, so the truth is
+    piecewise constant over solution intervals (noise-free data are then
+    fitted exactly).
+    """
+    amp = 1.0 + amp_sigma * rng.standard_normal((n_ant, 2))
+    ph0 = rng.uniform(-np.pi, np.pi, size=(n_ant, 2))
+    rate = drift_cycles * rng.standard_normal((n_ant, 2))
+    tc = (np.arange(n_tint) + 0.5) / max(1, n_tint)
+    ph = ph0[None] + 2 * np.pi * rate[None] * tc[:, None, None]        # [tint, ant, 2]
+    g = amp[None] * np.exp(1j * ph)
+    out = np.zeros((n_tint, n_fint, n_ant, 4), dtype=np.complex128)
+    out[:, :, :, 0] = g[:, None, :, 0]
+    out[:, :, :, 3] = g[:, None, :, 1]
+    return out
+
+
+def full_truth(n_ant: int, n_tint: int, n_fint: int, rng: np.random.Generator,
+               leakage: float = 0.05) -> np.ndarray:
+    """Full 2x2 gains: diagonal as :func:`diag_truth` plus 0.05*CN(0,1) off-diagonal leakage."""
+    out = diag_truth(n_ant, n_tint, n_fint, rng)
+    cn = (rng.standard_normal((n_tint, n_ant, 2)) + 1j * rng.standard_normal((n_tint, n_ant, 2))) / np.sqrt(2)
+    out[:, :, :, 1] = leakage * cn[:, None, :, 0]
+    out[:, :, :, 2] = leakage * cn[:, None, :, 1]
+    return out
+
+
+def bandpass_truth(n_ant: int, n_tint: int, n_fint: int, rng: np.random.Generator,
+                   amp_sigma: float = 0.1) -> np.ndarray:
+    """Diagonal bandpass: amplitude N(1, amp_sigma) per (antenna, channel, corr) and a
+    smooth phase sum_k a_k cos(pi k x + theta_k), x in [0,1], a_k ~ N(0, 0.5/k)."""
+    x = np.arange(n_fint) / max(1, n_fint - 1)
+    amp = 1.0 + amp_sigma * rng.standard_normal((n_fint, n_ant, 2))
+    ph = np.zeros((n_fint, n_ant, 2))
+    for k in range(1, 5):
+        a = rng.normal(0.0, np.sqrt(0.5 / k), size=(n_ant, 2))
+        th = rng.uniform(0, 2 * np.pi, size=(n_ant, 2))
+        ph += a[None] * np.cos(np.pi * k * x[:, None, None] + th[None])
+    g = amp * np.exp(1j * ph)
+    out = np.zeros((n_tint, n_fint, n_ant, 4), dtype=np.complex128)
+    out[:, :, :, 0] = g[None, :, :, 0]
+    out[:, :, :, 3] = g[None, :, :, 1]
+    return out
+
+
+def phase_truth(n_ant: int, n_tint: int, n_fint: int, rng: np.random.Generator) -> np.ndarray:
+    """Phase-only parameters [n_tint][n_fint][n_ant][2] (radians), U(-pi, pi)."""
+    return rng.uniform(-np.pi, np.pi, size=(n_tint, n_fint, n_ant, 2))
+
+
+def phase_to_jones(phi: np.ndarray) -> np.ndarray:
+    """Phase parameters [..., 2] -> diagonal Jones [..., 4] (instrument simulation only)."""
+    out = np.zeros(phi.shape[:-1] + (4,), dtype=np.complex128)
+    out[..., 0] = np.exp(1j * phi[..., 0])
+    out[..., 3] = np.exp(1j * phi[..., 1])
+    return out
+
+
+# ---------------------------------------------------------------------------
+# observation container and corruption (instrument simulation)
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class TermSpec:
+    """One Jones term of a chain: kind in {"diag","full","phase"} and its interval maps."""
+    kind: str
+    t_map: np.ndarray      # [n_time] -> time interval
+    f_map: np.ndarray      # [n_chan] -> freq interval
+    n_tint: int
+    n_fint: int
+    truth: Optional[np.ndarray] = None   # complex [tint][fint][ant][4] or phase [..][2]
+
+    def truth_jones(self) -> np.ndarray:
+        if self.kind == "phase":
+            return phase_to_jones(self.truth)
+        return self.truth
+
+
+@dataclasses.dataclass
+class Observation:
+    n_ant: int
+    n_time: int
+    n_chan: int
+    data: np.ndarray        # [row][chan][4] complex
+    model: np.ndarray       # [row][chan][4] complex (n_dir = 1)
+    weight: np.ndarray      # [row][chan][4] float
+    flag: np.ndarray        # [row][chan] uint8
+    ant1: np.ndarray        # [row] int32
+    ant2: np.ndarray
+    time_idx: np.ndarray
+    freqs: np.ndarray
+    terms: List[TermSpec]
+    meta: Dict
+
+    @property
+    def n_row(self) -> int:
+        return int(self.ant1.size)
+
+    @property
+    def n_vis(self) -> int:
+        return self.n_row * self.n_chan
+
+
+def _jones_at(term: TermSpec, t: np.ndarray, c: np.ndarray, a: np.ndarray) -> np.ndarray:
+    """Gather a term's truth Jones [rows, chan, 2, 2] for row times t, channels c, antennas a."""
+    J = term.truth_jones()
+    it = term.t_map[t][:, None]
+    jf = term.f_map[c][None, :]
+    return J[it, jf, a[:, None]].reshape(t.size, c.size, 2, 2)
+
+
+def corrupt(model: np.ndarray, terms: List[TermSpec], ant1, ant2, time_idx, n_chan) -> np.ndarray:
+    """Apply the true Jones chain C_a = prod_j G_j,a to the model: C_p M C_q^H (simulation)."""
+    chan = np.arange(n_chan)
+    M = model.reshape(model.shape[0], n_chan, 2, 2)
+    Cp = np.broadcast_to(np.eye(2, dtype=np.complex128), M.shape).copy()
+    Cq = Cp.copy()
+    for term in terms:
+        Cp = np.einsum("rcij,rcjk->rcik", Cp, _jones_at(term, time_idx, chan, ant1))
+        Cq = np.einsum("rcij,rcjk->rcik", Cq, _jones_at(term, time_idx, chan, ant2))
+    V = np.einsum("rcij,rcjk,rclk->rcil", Cp, M, Cq.conj())
+    return V.reshape(model.shape)
+
+
+def make_observation(n_ant: int, n_time: int, freqs: np.ndarray, terms: List[TermSpec], *,
+                     n_src: int, seed: int, noise: float, flag_row_frac: float = 0.0,
+                     max_baseline_m: float = 1000.0, nan_in_flagged: bool = False,
+                     sky_rng: Optional[np.random.Generator] = None,
+                     rng: Optional[np.random.Generator] = None,
+                     ant_x: Optional[np.ndarray] = None) -> Observation:
+    """Build one observation; every random draw comes from ``seed``."""
+    rng = rng if rng is not None else np.random.default_rng(seed)
+    sky_rng = sky_rng if sky_rng is not None else rng
+    n_chan = freqs.size
+    if ant_x is None:
+        ant_x = ew_array(n_ant, max_baseline_m, sky_rng)
+    sky = point_sources(n_src, sky_rng)
+    p, q = baselines(n_ant)
+    n_bl = p.size
+    ha = hour_angles(n_time)
+    uvw = ew_uvw(ant_x, p, q, ha).reshape(n_time * n_bl, 3)
+    ant1 = np.tile(p, n_time)
+    ant2 = np.tile(q, n_time)
+    time_idx = np.repeat(np.arange(n_time, dtype=np.int32), n_bl)
+    scal = predict_scalar(uvw, freqs, sky)
+    model = np.zeros((ant1.size, n_chan, 4), dtype=np.complex128)
+    model[:, :, 0] = scal
+    model[:, :, 3] = scal
+    data = corrupt(model, terms, ant1, ant2, time_idx, n_chan)
+    if noise > 0:
+        data = data + noise * (rng.standard_normal(data.shape) + 1j * rng.standard_normal(data.shape))
+    weight = np.ones(data.shape, dtype=np.float64)
+    flag = np.zeros((ant1.size, n_chan), dtype=np.uint8)
+    if flag_row_frac > 0:
+        rows = rng.random(ant1.size) < flag_row_frac
+        flag[rows, :] = 1
+    if nan_in_flagged:
+        data[flag.astype(bool)] = np.nan + 1j * np.nan
+    return Observation(n_ant=n_ant, n_time=n_time, n_chan=n_chan, data=data, model=model,
+                       weight=weight, flag=flag, ant1=ant1.astype(np.int32),
+                       ant2=ant2.astype(np.int32), time_idx=time_idx.astype(np.int32),
+                       freqs=freqs, terms=terms,
+                       meta=dict(seed=seed, noise=noise, n_src=n_src, ant_x=ant_x,
+                                 flag_row_frac=flag_row_frac, sky=sky))
+
+
+# ---------------------------------------------------------------------------
+# the workloads
+# ---------------------------------------------------------------------------
+
+def plain_small(seed: int = 0, noise: float = 0.01, n_ant: int = 7, n_time: int = 60,
+                n_chan: int = 16, t_int: int = 4, f_int: int = 4, n_src: int = 5) -> Observation:
+    """7 antennas, 60 times x 16 channels at 1.4 GHz, 5 sources, diagonal gains
+    on 4 x 4 solution intervals, sigma = 0.01, unit weights, no flags."""
+    rng = np.random.default_rng(seed)
+    freqs = 1.4e9 + 1.0e6 * (np.arange(n_chan) - (n_chan - 1) / 2.0)
+    n_tint = -(-n_time // t_int)
+    n_fint = -(-n_chan // f_int)
+    term = TermSpec("diag", interval_map(n_time, t_int), interval_map(n_chan, f_int), n_tint, n_fint)
+    ant_x = ew_array(n_ant, 1000.0, rng)
+    term.truth = diag_truth(n_ant, n_tint, n_fint, rng)
+    return make_observation(n_ant, n_time, freqs, [term], n_src=n_src, seed=seed, noise=noise,
+                            rng=rng, ant_x=ant_x)
+
+
+def meerkat_band(n_chan: int) -> np.ndarray:
+    """n_chan channels across 856 MHz centred at 1.284 GHz (MeerKAT L-band)."""
+    bw = 856e6
+    return 1.284e9 + bw * ((np.arange(n_chan) + 0.5) / n_chan - 0.5)
+
+
+def plain_large_terms(n_ant: int, n_time: int, n_chan: int, rng: np.random.Generator):
+    """Two-term chain: G full 2x2 per (1 time x all channels), B diagonal bandpass per
+    (all times x 1 channel)."""
+    G = TermSpec("full", interval_map(n_time, 1), np.zeros(n_chan, np.int32), n_time, 1)
+    B = TermSpec("diag", np.zeros(n_time, np.int32), interval_map(n_chan, 1), 1, n_chan)
+    G.truth = full_truth(n_ant, n_time, 1, rng)
+    B.truth = bandpass_truth(n_ant, 1, n_chan, rng)
+    return [G, B]
+
+
+def plain_large(seed: int = 1, n_ant: int = 64, n_time: int = 300, n_chan: int = 512,
+                noise: float = 0.05, flag_row_frac: float = 0.1, n_src: int = 50,
+                nan_in_flagged: bool = False) -> Observation:
+    """The large two-term workload on host memory (use reduced sizes on the CPU).
+
+    64 antennas, 300 times x 512 channels over 856 MHz, 50 sources, G (full) then
+    B (diagonal bandpass), sigma = 0.05, 10% of rows flagged.
+    """
+    rng = np.random.default_rng(seed)
+    freqs = meerkat_band(n_chan)
+    ant_x = ew_array(n_ant, 8000.0, rng)
+    terms = plain_large_terms(n_ant, n_time, n_chan, rng)
+    return make_observation(n_ant, n_time, freqs, terms, n_src=n_src, seed=seed, noise=noise,
+                            flag_row_frac=flag_row_frac, rng=rng, ant_x=ant_x,
+                            nan_in_flagged=nan_in_flagged)

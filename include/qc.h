@@ -1,0 +1,200 @@
+/*
+ * qc.h -- C ABI of the GB300 gain-calibration solver (libqc.so).
+ *
+ * The library solves, per solution interval, for per-antenna Jones gains of
+ * a chain of gain terms with the approximate ("AllJones") Gauss-Newton
+ * method of arxiv 2412.10072 (QuartiCal), Sections 2.2-2.4 and Algorithm 1
+ * (Section 4.3).  Every step of an iteration runs in hand-written sm_103a
+ * CUDA kernels; nothing is computed on the host.
+ *
+ * Conventions shared by all entry points
+ * ---------------------------------------
+ *  - Visibilities, model visibilities and weights are laid out
+ *    [n_row][n_chan][4]: rows are the Measurement-Set rows (one time and one
+ *    baseline each, Section 4.1), the four correlations of a 2x2 matrix are
+ *    in row-major order XX XY YX YY (Eq. gvec, Eq. jones).  Complex values
+ *    are complex64: interleaved (re, im) float32 pairs.
+ *  - Gains of one term are [n_tint][n_fint][n_ant][4] complex64 (the
+ *    paper's (gain_time, gain_freq, antenna, correlation) layout of
+ *    Fig. xarray_dataset, one direction); a diagonal term ignores XY/YX and
+ *    writes them as 0.  Phase-only terms use float32 [n_tint][n_fint][n_ant][2]
+ *    holding (phi_X, phi_Y) in radians (Scenario 1 of Section 2.4).
+ *  - t_map [n_time] and f_map [n_chan] map each data time / channel to the
+ *    term's solution interval (Section 4.3: "interval mappings").  Values
+ *    must lie in [0, n_tint) / [0, n_fint) and f_map must be non-decreasing
+ *    (intervals are contiguous sample ranges, Section 2.2).
+ *  - Ownership: the caller owns every array it passes.  Host inputs are
+ *    copied at qc_create; device inputs (memory = QC_MEM_DEVICE) are
+ *    borrowed and must stay valid and unchanged until qc_destroy.
+ *  - Errors: every call returns QC_OK (0) or a negative status; nothing
+ *    aborts.  The message of the last failure of a context is available
+ *    from qc_last_error.  A context is not thread-safe: one per thread.
+ *  - Only device 0 of the calling thread's current device is used; kernels
+ *    run on the stream given in the options (NULL: the context's own
+ *    stream).
+ */
+#ifndef QC_H
+#define QC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QC_OK             0
+#define QC_EINVAL        -1   /* invalid argument (sizes, indices, maps, NULL pointers)      */
+#define QC_ENOMEM        -2   /* device or host allocation failed                            */
+#define QC_ECUDA         -3   /* a CUDA runtime call or kernel launch failed                 */
+#define QC_ETIMEOUT      -4   /* reserved: a bounded device wait gave up                     */
+#define QC_EUNSUPPORTED  -5   /* valid request outside what this build implements           */
+
+#define QC_TERM_DIAG   0      /* diagonal complex gain, free parameters g_XX, g_YY           */
+#define QC_TERM_FULL   1      /* full 2x2 complex gain, free parameters all four entries     */
+#define QC_TERM_PHASE  2      /* phase-only diagonal gain exp(i phi_X), exp(i phi_Y)         */
+
+#define QC_MEM_HOST    0
+#define QC_MEM_DEVICE  1
+
+#define QC_MAX_TERMS   4      /* longest Jones chain accepted                                 */
+
+#define QC_DAMP_CONST      0  /* step length alpha_k = damping for every iteration           */
+#define QC_DAMP_ALTERNATE  1  /* alpha_k = 1 on odd, 1/2 on even iterations (k from 1)       */
+
+typedef struct qc_ctx qc_ctx;
+
+/*
+ * One calibration problem: the inputs d, m, w of Algorithm 1 plus flags and
+ * the row metadata of Section 4.1.
+ *   n_row, n_chan, n_time : data sizes; n_corr must be 4 and n_dir 1.
+ *   n_ant                 : antennas; ant1/ant2 in [0, n_ant).
+ *   data, model           : complex64 [n_row][n_chan][4].
+ *   weight                : float32 [n_row][n_chan][4], >= 0, per correlation.
+ *   flag                  : uint8 [n_row][n_chan], nonzero = flagged, or NULL.
+ *   ant1, ant2, time_idx  : int32 [n_row], HOST pointers always; rows with
+ *                           ant1 == ant2 (autocorrelations) are ignored.
+ *   memory                : where data/model/weight/flag live.
+ *   model_fp16            : 1 = store the model on the device as float16
+ *                           (re, im) pairs scaled by a per-baseline float32
+ *                           factor (max |component| of that baseline) and
+ *                           accumulate with compensated float32 sums.
+ */
+typedef struct {
+    int32_t n_row, n_chan, n_corr, n_ant, n_dir, n_time;
+    const void *data;
+    const void *model;
+    const float *weight;
+    const uint8_t *flag;
+    const int32_t *ant1, *ant2, *time_idx;
+    int32_t memory;
+    int32_t model_fp16;
+} qc_problem;
+
+/*
+ * One term of the Jones chain C_a = prod_j G_{j,a} (Eq. joneschain), listed
+ * leftmost first.
+ *   gains       : in/out, layout above; read as the initial estimate g_0 of
+ *                 Algorithm 1 and, for a solved term, overwritten on QC_OK.
+ *   gain_flags  : out int8 [n_tint][n_fint][n_ant] or NULL: 1 where the
+ *                 block had no data or was singular (the gain is then left
+ *                 unchanged), else 0.
+ *   iters       : out int32 [n_tint][n_fint] or NULL: iterations of the
+ *                 last solve of this term (last epoch).
+ *   solve       : 0 = hold fixed, 1 = solve.
+ *   max_iter    : N_max of Algorithm 1 (>= 1 when solved).
+ *   tol         : epsilon of Algorithm 1: an interval stops once
+ *                 ||g_k - g_{k-1}||_F / ||g_k||_F < tol (FP64 norms).
+ *   memory      : where gains, gain_flags and iters live.
+ *   reduce      : 1 = the term's intervals span several processes; the
+ *                 partial normal equations are summed with the options'
+ *                 allreduce callback before every update.
+ */
+typedef struct {
+    int32_t type, n_tint, n_fint;
+    const int32_t *t_map;
+    const int32_t *f_map;
+    void *gains;
+    int8_t *gain_flags;
+    int32_t *iters;
+    int32_t solve, max_iter;
+    double tol;
+    int32_t memory;
+    int32_t reduce;
+} qc_term;
+
+/*
+ * Sum `n` doubles of a device buffer across processes in place, ordered on
+ * `stream` (for example an NCCL all-reduce).  Return 0 on success.
+ */
+typedef int (*qc_allreduce_fn)(double *device_buffer, int64_t n, void *stream, void *user);
+
+typedef struct {
+    int32_t n_epochs;          /* passes over the chain (Section 4.3); >= 1        */
+    int32_t damping_mode;      /* QC_DAMP_CONST or QC_DAMP_ALTERNATE               */
+    double damping;            /* alpha for QC_DAMP_CONST (0 -> 1.0)               */
+    void *stream;              /* cudaStream_t, or NULL for the context stream     */
+    int32_t use_graph;         /* 1 = replay each term's iterations as a CUDA graph */
+    int32_t want_chi2;         /* 1 = fill chi2_before / chi2_after                 */
+    int32_t order;             /* -1 auto, 0 row-major tiles, 1 baseline-strip tiles */
+    int32_t block_threads;     /* threads per CTA of the accumulate kernel (0: auto) */
+    int32_t ctas_per_sm;       /* resident CTAs per SM for its grid (0: auto)        */
+    qc_allreduce_fn allreduce; /* required when a solved term has reduce = 1       */
+    void *allreduce_user;
+} qc_opts;
+
+typedef struct {
+    double chi2_before, chi2_after;   /* Eq. min, FP64 sums (when want_chi2)           */
+    double ms;                        /* device time of the whole solve (CUDA events)  */
+    double acc_ms;                    /* device time inside the accumulate kernels     */
+    int64_t vis_iters;                /* sum over iterations of samples in active intervals */
+    int64_t acc_bytes;                /* algorithmic bytes read by the accumulate kernels */
+    int64_t acc_launches;             /* accumulate kernels that did work              */
+    int64_t launches;                 /* kernels launched by this call                 */
+    int32_t n_iter_max;               /* largest iteration count of any interval       */
+} qc_stats;
+
+/*
+ * Validate a problem and stage it on the device.  On QC_OK *out holds a new
+ * context (release with qc_destroy); on failure *out is NULL and the status
+ * says why (QC_EINVAL for bad sizes/indices, QC_ENOMEM, QC_ECUDA).
+ */
+int qc_create(const qc_problem *p, qc_ctx **out);
+
+/*
+ * Run the chain schedule: for each epoch, each solved term in chain order
+ * is iterated with Algorithm 1 until every one of its solution intervals
+ * has converged or reached max_iter (Section 4.3).  One iteration forms the
+ * corrected-model residual over every baseline and accumulates the
+ * per-antenna blocks of J^H W J and J^H W r of the term (Eq.
+ * jhj_entry_simplified, Eq. jhr_entry_simplified, or the 2 Re(.) forms of
+ * Scenario 1 for phase terms) in one data pass, then solves each block in
+ * FP64 and updates g <- g + alpha_k JHJ^{-1} JHr (Eq. update, Algorithm 1).
+ * `stats` may be NULL.  Gains, flags and iteration counts are written back
+ * only on QC_OK.
+ */
+int qc_solve(qc_ctx *c, qc_term *terms, int32_t n_terms, const qc_opts *o, qc_stats *stats);
+
+/*
+ * chi^2 = sum of w |d - C_p M C_q^H|^2 over unflagged cross-correlation
+ * samples and correlations (Eq. min, Eq. baselineresidual), accumulated in
+ * FP64.  If `resid` is not NULL the residual r is written as complex64
+ * [n_row][n_chan][4] (zero for flagged samples and autocorrelations) in
+ * `resid_memory`.
+ */
+int qc_residual(qc_ctx *c, const qc_term *terms, int32_t n_terms, void *resid, int32_t resid_memory,
+                double *chi2);
+
+/* Release a context and every device buffer it owns.  NULL-safe. */
+void qc_destroy(qc_ctx *c);
+
+/* Message of the last failed call on `c` ("" if none); with c == NULL, of the last failed qc_create. */
+const char *qc_last_error(const qc_ctx *c);
+
+/* Library version string. */
+const char *qc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QC_H */

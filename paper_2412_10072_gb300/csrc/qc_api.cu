@@ -1,0 +1,772 @@
+// qc_api.cu -- host side of libqc: validation, device staging, the chain
+// schedule of epochs x terms x iterations (Section 4.3 of arxiv 2412.10072)
+// and CUDA-graph replay of each term's iteration loop.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/qc.h"
+#include "qc_internal.h"
+#include "qc_kernels.cuh"
+
+using namespace qc;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+__global__ void bl_scale_kernel(const float4 *model, const int4 *rows, int n_row, int n_chan, unsigned *scale_bits)
+{
+    const long n = (long)n_row * n_chan;
+    for (long s = (long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long)gridDim.x * blockDim.x) {
+        const int row = (int)(s / n_chan);
+        const int4 meta = rows[row];
+        if (meta.x == meta.y) continue;
+        const float4 a = model[2 * s], b = model[2 * s + 1];
+        float m = fmaxf(fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(a.z), fabsf(a.w))),
+                        fmaxf(fmaxf(fabsf(b.x), fabsf(b.y)), fmaxf(fabsf(b.z), fabsf(b.w))));
+        if (!(m <= 3.0e38f)) m = 0.f;           // non-finite (flagged garbage) does not set the scale
+        atomicMax(scale_bits + meta.w, __float_as_uint(m));
+    }
+}
+
+__global__ void pack16_kernel(const float4 *model, const int4 *rows, int n_row, int n_chan, const float *scale,
+                              uint4 *out)
+{
+    const long n = (long)n_row * n_chan;
+    for (long s = (long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long)gridDim.x * blockDim.x) {
+        const int row = (int)(s / n_chan);
+        const int4 meta = rows[row];
+        const float sc = meta.x == meta.y ? 1.f : scale[meta.w];
+        const float inv = sc > 0.f ? 1.f / sc : 0.f;
+        const float4 a = model[2 * s], b = model[2 * s + 1];
+        __half2 h0 = __floats2half2_rn(a.x * inv, a.y * inv), h1 = __floats2half2_rn(a.z * inv, a.w * inv);
+        __half2 h2 = __floats2half2_rn(b.x * inv, b.y * inv), h3 = __floats2half2_rn(b.z * inv, b.w * inv);
+        uint4 o;
+        o.x = *reinterpret_cast<unsigned *>(&h0);
+        o.y = *reinterpret_cast<unsigned *>(&h1);
+        o.z = *reinterpret_cast<unsigned *>(&h2);
+        o.w = *reinterpret_cast<unsigned *>(&h3);
+        out[s] = o;
+    }
+}
+
+__global__ void fix_scale_kernel(unsigned *bits, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const float v = __uint_as_float(bits[i]);
+        reinterpret_cast<float *>(bits)[i] = v > 0.f ? v : 1.f;
+    }
+}
+
+// user gains [n_tint][n_fint][n_ant][4] (complex64) or phases [..][2] (float32)
+// -> FP64 master parameters and FP32 kernel table [n_tint][n_ant][n_fint]
+__global__ void gains_in_kernel(int type, int n_tint, int n_fint, int n_ant, const void *src, double *params,
+                                float4 *tab)
+{
+    const long n = (long)n_tint * n_fint * n_ant;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const int ant = (int)(i % n_ant);
+        const long bin = i / n_ant;
+        const int tint = (int)(bin / n_fint), fint = (int)(bin % n_fint);
+        const size_t t = ((size_t)tint * n_ant + ant) * n_fint + fint;
+        if (type == 2) {
+            const float *ph = (const float *)src + 2 * i;
+            params[2 * i] = ph[0];
+            params[2 * i + 1] = ph[1];
+            double s0, c0, s1, c1;
+            sincos((double)ph[0], &s0, &c0);
+            sincos((double)ph[1], &s1, &c1);
+            tab[t] = make_float4((float)c0, (float)s0, (float)c1, (float)s1);
+            continue;
+        }
+        const float2 *g = (const float2 *)src + 4 * i;
+        double2 *P = reinterpret_cast<double2 *>(params) + 4 * i;
+        for (int e = 0; e < 4; ++e) P[e] = make_double2(g[e].x, g[e].y);
+        if (type == 0) { P[1] = make_double2(0, 0); P[2] = make_double2(0, 0); }
+        if (type == 1) {
+            tab[2 * t] = make_float4(g[0].x, g[0].y, g[1].x, g[1].y);
+            tab[2 * t + 1] = make_float4(g[2].x, g[2].y, g[3].x, g[3].y);
+        } else {
+            tab[t] = make_float4(g[0].x, g[0].y, g[3].x, g[3].y);
+        }
+    }
+}
+
+__global__ void gains_out_kernel(int type, long n, const double *params, void *dst)
+{
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        if (type == 2) {
+            float *ph = (float *)dst + 2 * i;
+            ph[0] = (float)params[2 * i];
+            ph[1] = (float)params[2 * i + 1];
+            continue;
+        }
+        float2 *g = (float2 *)dst + 4 * i;
+        const double2 *P = reinterpret_cast<const double2 *>(params) + 4 * i;
+        for (int e = 0; e < 4; ++e) g[e] = make_float2((float)P[e].x, (float)P[e].y);
+        if (type == 0) { g[1] = make_float2(0.f, 0.f); g[2] = make_float2(0.f, 0.f); }
+    }
+}
+
+__global__ void bin_bytes_kernel(int n, const long long *nvis, const long long *nunflag, long long b_flag,
+                                 long long b_unflag, long long *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = nvis[i] * b_flag + nunflag[i] * b_unflag;
+}
+
+__global__ void init_term_kernel(int n_bins, uint8_t *active, int *cnt, int n_cnt)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_bins) active[i] = 1;
+    if (i < n_cnt) cnt[i] = i == 0 ? n_bins : 0;
+}
+
+template <typename T> size_t nbytes(size_t n) { return n * sizeof(T); }
+
+int grid_for(long n, int block, int sm)
+{
+    long g = (n + block - 1) / block;
+    return (int)std::max(1L, std::min(g, (long)sm * 32));
+}
+
+} // namespace
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+
+qc_ctx::~qc_ctx()
+{
+    for (auto &b : tb) if (b.exec) cudaGraphExecDestroy(b.exec);
+    for (void *p : owned) cudaFree(p);
+    for (auto e : events) cudaEventDestroy(e);
+    if (own_stream) cudaStreamDestroy(own_stream);
+}
+
+int qc_ctx::fail(int code, const std::string &msg)
+{
+    err = msg;
+    return code;
+}
+
+int qc_ctx::cuda_fail(cudaError_t e, const char *what)
+{
+    err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? QC_ENOMEM : QC_ECUDA;
+}
+
+void *qc_ctx::alloc(size_t bytes, cudaError_t *e)
+{
+    void *p = nullptr;
+    *e = cudaMalloc(&p, std::max<size_t>(bytes, 16));
+    if (*e == cudaSuccess) owned.push_back(p);
+    return p;
+}
+
+void qc_ctx::release(void *p)
+{
+    auto it = std::find(owned.begin(), owned.end(), p);
+    if (it != owned.end()) { cudaFree(p); owned.erase(it); }
+}
+
+int qc_ctx::ensure(Buf &b, size_t bytes)
+{
+    if (b.bytes >= bytes && b.ptr) return QC_OK;
+    if (b.ptr) release(b.ptr);
+    cudaError_t e;
+    b.ptr = alloc(bytes, &e);
+    b.bytes = b.ptr ? std::max<size_t>(bytes, 16) : 0;
+    if (e != cudaSuccess) { b.ptr = nullptr; return cuda_fail(e, "cudaMalloc"); }
+    return QC_OK;
+}
+
+#define CK(call)                                          \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return c->cuda_fail(e_, #call); \
+    } while (0)
+
+extern "C" int qc_create(const qc_problem *p, qc_ctx **out)
+{
+    g_create_error.clear();
+    if (!out) { g_create_error = "out is NULL"; return QC_EINVAL; }
+    *out = nullptr;
+    auto bad = [](const char *m) { g_create_error = m; return QC_EINVAL; };
+    if (!p) return bad("problem is NULL");
+    if (p->n_corr != 4) return bad("n_corr must be 4");
+    if (p->n_dir != 1) return bad("n_dir must be 1");
+    if (p->n_row < 0 || p->n_chan < 1 || p->n_ant < 2 || p->n_time < 1) return bad("invalid sizes");
+    if ((long long)p->n_row * p->n_chan > (1LL << 40)) return bad("problem too large");
+    if (!p->data || !p->model || !p->weight) return bad("data, model and weight are required");
+    if (!p->ant1 || !p->ant2 || !p->time_idx) return bad("ant1, ant2 and time_idx are required (host arrays)");
+    if (p->memory != QC_MEM_HOST && p->memory != QC_MEM_DEVICE) return bad("memory must be QC_MEM_HOST or QC_MEM_DEVICE");
+    for (int r = 0; r < p->n_row; ++r) {
+        if (p->ant1[r] < 0 || p->ant1[r] >= p->n_ant || p->ant2[r] < 0 || p->ant2[r] >= p->n_ant)
+            return bad("antenna index out of range");
+        if (p->time_idx[r] < 0 || p->time_idx[r] >= p->n_time) return bad("time index out of range");
+    }
+    if (p->memory == QC_MEM_DEVICE) {
+        for (const void *ptr : { p->data, p->model, (const void *)p->weight })
+            if (((uintptr_t)ptr) % 16) return bad("device data/model/weight must be 16-byte aligned");
+    }
+
+    std::unique_ptr<qc_ctx> c(new qc_ctx());
+    c->n_row = p->n_row;
+    c->n_chan = p->n_chan;
+    c->n_ant = p->n_ant;
+    c->n_time = p->n_time;
+    c->m16 = p->model_fp16 != 0;
+    c->has_flag = p->flag != nullptr;
+    {
+        cudaError_t e = cudaGetDevice(&c->dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->dev);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { g_create_error = std::string("CUDA init: ") + cudaGetErrorString(e); return QC_ECUDA; }
+    }
+    // rows {ant1, ant2, time, baseline id}; strips: rows of one (ant1, ant2) pair in time order
+    const int na = p->n_ant;
+    std::vector<int> bl_of_pair((size_t)na * na, -1);
+    std::vector<int4> rows(p->n_row);
+    int n_bl = 0;
+    for (int r = 0; r < p->n_row; ++r) {
+        const int a1 = p->ant1[r], a2 = p->ant2[r];
+        int bl = 0;
+        if (a1 != a2) {
+            int &slot = bl_of_pair[(size_t)a1 * na + a2];
+            if (slot < 0) slot = n_bl++;
+            bl = slot;
+        }
+        rows[r] = make_int4(a1, a2, p->time_idx[r], bl);
+    }
+    c->n_bl = n_bl;
+    std::vector<int> strip_off(n_bl + 1, 0), strip_rows;
+    for (int r = 0; r < p->n_row; ++r) if (rows[r].x != rows[r].y) strip_off[rows[r].w + 1]++;
+    for (int b = 0; b < n_bl; ++b) strip_off[b + 1] += strip_off[b];
+    strip_rows.resize(strip_off[n_bl]);
+    {
+        std::vector<int> fill(strip_off.begin(), strip_off.end() - 1);
+        for (int r = 0; r < p->n_row; ++r) if (rows[r].x != rows[r].y) strip_rows[fill[rows[r].w]++] = r;
+        for (int b = 0; b < n_bl; ++b)
+            std::stable_sort(strip_rows.begin() + strip_off[b], strip_rows.begin() + strip_off[b + 1],
+                             [&](int x, int y) { return rows[x].z < rows[y].z; });
+    }
+    c->n_strips = n_bl;
+    cudaError_t e;
+    qc_ctx *cc = c.get();
+    auto dalloc = [&](size_t bytes) -> void * { return cc->alloc(bytes, &e); };
+#define DALLOC(dst, T, n)                                                                    \
+    do {                                                                                     \
+        dst = (T *)dalloc(nbytes<T>(n));                                                     \
+        if (e != cudaSuccess) { g_create_error = "cudaMalloc failed"; return e == cudaErrorMemoryAllocation ? QC_ENOMEM : QC_ECUDA; } \
+    } while (0)
+#define HCOPY(dst, src, bytes)                                                               \
+    do {                                                                                     \
+        e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);                             \
+        if (e != cudaSuccess) { g_create_error = std::string("H2D copy: ") + cudaGetErrorString(e); return QC_ECUDA; } \
+    } while (0)
+    DALLOC(c->d_rows, int4, std::max(1, p->n_row));
+    if (p->n_row) HCOPY(c->d_rows, rows.data(), nbytes<int4>(p->n_row));
+    DALLOC(c->d_strip_off, int, n_bl + 1);
+    HCOPY(c->d_strip_off, strip_off.data(), nbytes<int>(n_bl + 1));
+    DALLOC(c->d_strip_rows, int, std::max<size_t>(1, strip_rows.size()));
+    if (!strip_rows.empty()) HCOPY(c->d_strip_rows, strip_rows.data(), nbytes<int>(strip_rows.size()));
+
+    const size_t n_vis = (size_t)p->n_row * p->n_chan;
+    const float4 *model32 = nullptr;
+    if (p->memory == QC_MEM_DEVICE) {
+        c->d_vis = (const float4 *)p->data;
+        model32 = (const float4 *)p->model;
+        c->d_weight = (const float4 *)p->weight;
+        c->d_flag = p->flag;
+    } else {
+        float4 *v, *w;
+        DALLOC(v, float4, 2 * n_vis);
+        HCOPY(v, p->data, nbytes<float4>(2 * n_vis));
+        DALLOC(w, float4, n_vis);
+        HCOPY(w, p->weight, nbytes<float4>(n_vis));
+        c->d_vis = v;
+        c->d_weight = w;
+        float4 *m;
+        DALLOC(m, float4, 2 * n_vis);
+        HCOPY(m, p->model, nbytes<float4>(2 * n_vis));
+        model32 = m;
+        if (p->flag) {
+            uint8_t *f;
+            DALLOC(f, uint8_t, n_vis);
+            HCOPY(f, p->flag, n_vis);
+            c->d_flag = f;
+        }
+    }
+    if (c->m16) {
+        unsigned *bits;
+        uint4 *m16;
+        DALLOC(bits, unsigned, std::max(1, n_bl));
+        DALLOC(m16, uint4, n_vis);
+        e = cudaMemsetAsync(bits, 0, nbytes<unsigned>(std::max(1, n_bl)), c->own_stream);
+        if (e == cudaSuccess && n_vis) {
+            bl_scale_kernel<<<grid_for((long)n_vis, 256, c->sm_count), 256, 0, c->own_stream>>>(
+                model32, c->d_rows, p->n_row, p->n_chan, bits);
+            fix_scale_kernel<<<(n_bl + 255) / 256 + 1, 256, 0, c->own_stream>>>(bits, n_bl);
+            pack16_kernel<<<grid_for((long)n_vis, 256, c->sm_count), 256, 0, c->own_stream>>>(
+                model32, c->d_rows, p->n_row, p->n_chan, (const float *)bits, m16);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->own_stream);
+        if (e != cudaSuccess) { g_create_error = std::string("fp16 model packing: ") + cudaGetErrorString(e); return QC_ECUDA; }
+        c->d_model16 = m16;
+        c->d_bl_scale = (const float *)bits;
+        if (p->memory == QC_MEM_HOST) c->release((void *)model32);
+        model32 = nullptr;
+    }
+    c->d_model = model32;
+#undef DALLOC
+#undef HCOPY
+    *out = c.release();
+    return QC_OK;
+}
+
+extern "C" void qc_destroy(qc_ctx *c) { delete c; }
+
+extern "C" const char *qc_last_error(const qc_ctx *c)
+{
+    if (!c) return g_create_error.c_str();
+    return c->err.c_str();
+}
+
+extern "C" const char *qc_version(void) { return "qc-gb300 1.0 (sm_103a)"; }
+
+// ---------------------------------------------------------------------------
+// term staging
+// ---------------------------------------------------------------------------
+
+static size_t term_nbins(const qc_term &t) { return (size_t)t.n_tint * t.n_fint; }
+
+int qc_ctx::validate_terms(const qc_term *terms, int n_terms, bool need_solve_fields)
+{
+    if (!terms) return fail(QC_EINVAL, "terms is NULL");
+    if (n_terms < 1 || n_terms > QC_MAX_TERMS) return fail(QC_EINVAL, "n_terms must be in [1, QC_MAX_TERMS]");
+    for (int j = 0; j < n_terms; ++j) {
+        const qc_term &t = terms[j];
+        if (t.type < 0 || t.type > 2) return fail(QC_EINVAL, "unknown term type");
+        if (t.n_tint < 1 || t.n_fint < 1) return fail(QC_EINVAL, "n_tint and n_fint must be >= 1");
+        if ((long long)t.n_tint * t.n_fint * n_ant > (1LL << 31)) return fail(QC_EINVAL, "term too large");
+        if (!t.t_map || !t.f_map || !t.gains) return fail(QC_EINVAL, "t_map, f_map and gains are required");
+        if (t.memory != QC_MEM_HOST && t.memory != QC_MEM_DEVICE) return fail(QC_EINVAL, "term memory invalid");
+        for (int i = 0; i < n_time; ++i)
+            if (t.t_map[i] < 0 || t.t_map[i] >= t.n_tint) return fail(QC_EINVAL, "t_map value out of range");
+        for (int i = 0; i < n_chan; ++i) {
+            if (t.f_map[i] < 0 || t.f_map[i] >= t.n_fint) return fail(QC_EINVAL, "f_map value out of range");
+            if (i && t.f_map[i] < t.f_map[i - 1]) return fail(QC_EINVAL, "f_map must be non-decreasing");
+        }
+        if (need_solve_fields && t.solve) {
+            if (t.max_iter < 1) return fail(QC_EINVAL, "max_iter must be >= 1 for a solved term");
+            if (!(t.tol >= 0)) return fail(QC_EINVAL, "tol must be >= 0");
+        }
+    }
+    return QC_OK;
+}
+
+// Upload maps and gains of every term; fills chain (device descriptors).
+int qc_ctx::stage_terms(const qc_term *terms, int n_terms, cudaStream_t st, Chain &chain)
+{
+    qc_ctx *c = this;
+    chain.n_terms = n_terms;
+    chain.n = -1;
+    chain.n_ant = n_ant;
+    for (int j = 0; j < n_terms; ++j) {
+        const qc_term &t = terms[j];
+        TermBufs &B = tb[j];
+        const size_t nb = term_nbins(t);
+        const size_t nent = nb * n_ant;
+        const size_t tab_f4 = nent * (t.type == 1 ? 2 : 1);
+        int rc;
+        if ((rc = ensure(B.maps, nbytes<int>(n_time + n_chan)))) return rc;
+        if ((rc = ensure(B.tab, nbytes<float4>(tab_f4)))) return rc;
+        if ((rc = ensure(B.params, nbytes<double>(nent * (t.type == 2 ? 2 : 8))))) return rc;
+        if ((rc = ensure(B.stage, nent * (t.type == 2 ? 8 : 32)))) return rc;
+        B.hmaps.assign(t.t_map, t.t_map + n_time);
+        B.hmaps.insert(B.hmaps.end(), t.f_map, t.f_map + n_chan);
+        CK(cudaMemcpyAsync(B.maps.ptr, B.hmaps.data(), nbytes<int>(n_time + n_chan), cudaMemcpyHostToDevice, st));
+        const void *src = t.gains;
+        if (t.memory == QC_MEM_HOST) {
+            CK(cudaMemcpyAsync(B.stage.ptr, t.gains, nent * (t.type == 2 ? 8 : 32), cudaMemcpyHostToDevice, st));
+            src = B.stage.ptr;
+        }
+        gains_in_kernel<<<grid_for((long)nent, 256, sm_count), 256, 0, st>>>(t.type, t.n_tint, t.n_fint, n_ant, src,
+                                                                            (double *)B.params.ptr, (float4 *)B.tab.ptr);
+        CK(cudaGetLastError());
+        ++launches;
+        DevTerm &d = chain.t[j];
+        d.type = t.type;
+        d.n_tint = t.n_tint;
+        d.n_fint = t.n_fint;
+        d.t_map = (const int *)B.maps.ptr;
+        d.f_map = (const int *)B.maps.ptr + n_time;
+        d.tab = (const float4 *)B.tab.ptr;
+    }
+    return QC_OK;
+}
+
+Data qc_ctx::data_desc() const
+{
+    Data D;
+    D.n_row = n_row;
+    D.n_chan = n_chan;
+    D.vis = d_vis;
+    D.model = d_model;
+    D.model16 = d_model16;
+    D.bl_scale = d_bl_scale;
+    D.weight = d_weight;
+    D.flag = d_flag;
+    D.rows = d_rows;
+    D.strip_rows = d_strip_rows;
+    D.strip_off = d_strip_off;
+    D.n_strips = n_strips;
+    return D;
+}
+
+// ---------------------------------------------------------------------------
+// residual / chi^2
+// ---------------------------------------------------------------------------
+
+extern "C" int qc_residual(qc_ctx *c, const qc_term *terms, int32_t n_terms, void *resid, int32_t resid_memory,
+                           double *chi2)
+{
+    if (!c) return QC_EINVAL;
+    c->err.clear();
+    if (!chi2) return c->fail(QC_EINVAL, "chi2 is NULL");
+    int rc = c->validate_terms(terms, n_terms, false);
+    if (rc) return rc;
+    cudaStream_t st = c->own_stream;
+    Chain chain;
+    if ((rc = c->stage_terms(terms, n_terms, st, chain))) return rc;
+    if ((rc = c->ensure(c->scalars, 64))) return rc;
+    double *d_chi2 = (double *)c->scalars.ptr;
+    const size_t n_vis = (size_t)c->n_row * c->n_chan;
+    float4 *dres = nullptr;
+    if (resid) {
+        if (resid_memory == QC_MEM_DEVICE) dres = (float4 *)resid;
+        else {
+            if ((rc = c->ensure(c->resid_stage, nbytes<float4>(2 * n_vis)))) return rc;
+            dres = (float4 *)c->resid_stage.ptr;
+        }
+    }
+    if ((rc = c->run_residual(chain, dres, d_chi2, st))) return rc;
+    CK(cudaMemcpyAsync(chi2, d_chi2, sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (resid && resid_memory != QC_MEM_DEVICE)
+        CK(cudaMemcpyAsync(resid, dres, nbytes<float4>(2 * n_vis), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return QC_OK;
+}
+
+int qc_ctx::run_residual(const Chain &chain, float4 *dres, double *d_chi2, cudaStream_t st)
+{
+    qc_ctx *c = this;
+    CK(cudaMemsetAsync(d_chi2, 0, sizeof(double), st));
+    ResArgs ra;
+    ra.D = data_desc();
+    ra.C = chain;
+    ra.resid = dres;
+    ra.chi2 = d_chi2;
+    const long warps = (long)n_row * ((n_chan + 31) / 32);
+    const int grid = grid_for(warps * 32, 256, sm_count);
+    if (m16) residual_kernel<true><<<grid, 256, 0, st>>>(ra);
+    else residual_kernel<false><<<grid, 256, 0, st>>>(ra);
+    CK(cudaGetLastError());
+    ++launches;
+    return QC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// solve
+// ---------------------------------------------------------------------------
+
+static int kind_of_range(const qc_term *terms, int lo, int hi)
+{
+    int k = KIND_NONE;
+    for (int j = lo; j < hi; ++j) k = std::max(k, terms[j].type == 1 ? KIND_FULL : KIND_DIAG);
+    return k;
+}
+
+int qc_ctx::pick_order(const qc_term &t, const qc_opts *o) const
+{
+    if (o && (o->order == 0 || o->order == 1)) return o->order;
+    // mean interval extent along channels and along time (rows of one baseline)
+    const double wf = (double)n_chan / t.n_fint;
+    const double ht = (double)n_time / t.n_tint;
+    return (wf >= 32.0 || wf >= ht) ? 0 : 1;
+}
+
+extern "C" int qc_solve(qc_ctx *c, qc_term *terms, int32_t n_terms, const qc_opts *o, qc_stats *stats)
+{
+    if (!c) return QC_EINVAL;
+    c->err.clear();
+    int rc = c->validate_terms(terms, n_terms, true);
+    if (rc) return rc;
+    qc_opts defaults;
+    memset(&defaults, 0, sizeof defaults);
+    defaults.n_epochs = 1;
+    defaults.damping_mode = QC_DAMP_ALTERNATE;
+    defaults.use_graph = 1;
+    defaults.order = -1;
+    if (!o) o = &defaults;
+    if (o->n_epochs < 1) return c->fail(QC_EINVAL, "n_epochs must be >= 1");
+    if (o->damping_mode != QC_DAMP_CONST && o->damping_mode != QC_DAMP_ALTERNATE)
+        return c->fail(QC_EINVAL, "unknown damping_mode");
+    for (int j = 0; j < n_terms; ++j)
+        if (terms[j].solve && terms[j].reduce && !o->allreduce)
+            return c->fail(QC_EINVAL, "a term with reduce = 1 needs opts.allreduce");
+    cudaStream_t st = o->stream ? (cudaStream_t)o->stream : c->own_stream;
+    c->launches = 0;
+    qc_stats S;
+    memset(&S, 0, sizeof S);
+
+    cudaEvent_t ev0, ev1;
+    if ((rc = c->get_event(0, ev0)) || (rc = c->get_event(1, ev1))) return rc;
+    CK(cudaEventRecord(ev0, st));
+    Chain chain;
+    if ((rc = c->stage_terms(terms, n_terms, st, chain))) return rc;
+    if ((rc = c->ensure(c->scalars, 64))) return rc;
+    unsigned long long *d_counters = (unsigned long long *)c->scalars.ptr;   // [0] vis_iters, [1] bytes
+    double *d_chi2 = (double *)c->scalars.ptr + 4;
+    CK(cudaMemsetAsync(d_counters, 0, 2 * sizeof(unsigned long long), st));
+    if (o->want_chi2) {
+        if ((rc = c->run_residual(chain, nullptr, d_chi2, st))) return rc;
+        CK(cudaMemcpyAsync(&S.chi2_before, d_chi2, sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+
+    // per solved term: bin counts and byte weights
+    const long long b_flag = c->has_flag ? 1 : 0;
+    const long long b_unflag = 32 + (c->m16 ? 16 : 32) + 16;
+    for (int j = 0; j < n_terms; ++j) {
+        if (!terms[j].solve) continue;
+        const qc_term &t = terms[j];
+        TermBufs &B = c->tb[j];
+        const size_t nb = term_nbins(t);
+        const size_t KG = t.type == 1 ? KG_FULL : KG_DIAG;
+        if ((rc = c->ensure(B.acc, nbytes<double>(nb * c->n_ant * KG)))) return rc;
+        if ((rc = c->ensure(B.active, nb))) return rc;
+        if ((rc = c->ensure(B.cnt, nbytes<int>(t.max_iter + 1)))) return rc;
+        if ((rc = c->ensure(B.nvis, nbytes<long long>(3 * nb)))) return rc;
+        if ((rc = c->ensure(B.iters, nbytes<int>(nb)))) return rc;
+        if ((rc = c->ensure(B.flags, nb * c->n_ant))) return rc;
+        CK(cudaMemsetAsync(B.acc.ptr, 0, nbytes<double>(nb * c->n_ant * KG), st));
+        CK(cudaMemsetAsync(B.nvis.ptr, 0, nbytes<long long>(3 * nb), st));
+        CK(cudaMemsetAsync(B.iters.ptr, 0, nbytes<int>(nb), st));
+        CK(cudaMemsetAsync(B.flags.ptr, 0, nb * c->n_ant, st));
+        long long *nvis = (long long *)B.nvis.ptr;
+        CountArgs ca;
+        ca.D = c->data_desc();
+        ca.t_map = chain.t[j].t_map;
+        ca.f_map = chain.t[j].f_map;
+        ca.n_fint = t.n_fint;
+        ca.nvis = nvis;
+        ca.nunflag = nvis + nb;
+        if (c->n_row) {
+            count_kernel<<<grid_for((long)c->n_row * 32, 256, c->sm_count), 256, 0, st>>>(ca);
+            CK(cudaGetLastError());
+            ++c->launches;
+        }
+        bin_bytes_kernel<<<((int)nb + 255) / 256, 256, 0, st>>>((int)nb, nvis, nvis + nb, b_flag, b_unflag, nvis + 2 * nb);
+        CK(cudaGetLastError());
+        ++c->launches;
+        B.graph_valid = false;
+    }
+
+    int n_iter_max = 0;
+    for (int epoch = 0; epoch < o->n_epochs; ++epoch) {
+        for (int n = 0; n < n_terms; ++n) {
+            if (!terms[n].solve) continue;
+            int it_max = 0;
+            double acc_ms = 0;
+            long long acc_launches = 0;
+            if ((rc = c->solve_term(terms, n_terms, n, chain, o, st, &it_max, &acc_ms, &acc_launches))) return rc;
+            S.acc_ms += acc_ms;
+            S.acc_launches += acc_launches;
+            if (epoch == o->n_epochs - 1) n_iter_max = std::max(n_iter_max, it_max);
+        }
+    }
+    if (o->want_chi2) {
+        if ((rc = c->run_residual(chain, nullptr, d_chi2, st))) return rc;
+        CK(cudaMemcpyAsync(&S.chi2_after, d_chi2, sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+    // write back solved gains, flags, iteration counts
+    for (int j = 0; j < n_terms; ++j) {
+        if (!terms[j].solve) continue;
+        qc_term &t = terms[j];
+        TermBufs &B = c->tb[j];
+        const size_t nb = term_nbins(t), nent = nb * c->n_ant;
+        const size_t gbytes = nent * (t.type == 2 ? 8 : 32);
+        void *dst = t.memory == QC_MEM_DEVICE ? t.gains : B.stage.ptr;
+        gains_out_kernel<<<grid_for((long)nent, 256, c->sm_count), 256, 0, st>>>(t.type, (long)nent,
+                                                                               (const double *)B.params.ptr, dst);
+        CK(cudaGetLastError());
+        ++c->launches;
+        if (t.memory == QC_MEM_HOST) {
+            CK(cudaMemcpyAsync(t.gains, B.stage.ptr, gbytes, cudaMemcpyDeviceToHost, st));
+            if (t.gain_flags) CK(cudaMemcpyAsync(t.gain_flags, B.flags.ptr, nent, cudaMemcpyDeviceToHost, st));
+            if (t.iters) CK(cudaMemcpyAsync(t.iters, B.iters.ptr, nbytes<int>(nb), cudaMemcpyDeviceToHost, st));
+        } else {
+            if (t.gain_flags) CK(cudaMemcpyAsync(t.gain_flags, B.flags.ptr, nent, cudaMemcpyDeviceToDevice, st));
+            if (t.iters) CK(cudaMemcpyAsync(t.iters, B.iters.ptr, nbytes<int>(nb), cudaMemcpyDeviceToDevice, st));
+        }
+    }
+    unsigned long long hc[2];
+    CK(cudaMemcpyAsync(hc, d_counters, sizeof hc, cudaMemcpyDeviceToHost, st));
+    CK(cudaEventRecord(ev1, st));
+    CK(cudaStreamSynchronize(st));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, ev0, ev1));
+    S.ms = ms;
+    S.vis_iters = (int64_t)hc[0];
+    S.acc_bytes = (int64_t)hc[1];
+    S.n_iter_max = n_iter_max;
+    S.launches = c->launches;
+    if (stats) *stats = S;
+    return QC_OK;
+}
+
+int qc_ctx::get_event(int i, cudaEvent_t &ev)
+{
+    while ((int)events.size() <= i) {
+        cudaEvent_t e;
+        cudaError_t err_ = cudaEventCreate(&e);
+        if (err_ != cudaSuccess) return cuda_fail(err_, "cudaEventCreate");
+        events.push_back(e);
+    }
+    ev = events[i];
+    return QC_OK;
+}
+
+int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, const qc_opts *o, cudaStream_t st,
+                       int *it_max, double *acc_ms, long long *acc_launches)
+{
+    qc_ctx *c = this;
+    const qc_term &t = terms[n];
+    TermBufs &B = tb[n];
+    const int nb = (int)term_nbins(t);
+    chain.n = n;
+    const int ts = t.type == 1 ? TS_FULL : TS_DIAG;
+    const int lk = kind_of_range(terms, 0, n);
+    const int rk = kind_of_range(terms, n + 1, n_terms);
+    const int order = pick_order(t, o);
+    const int block = (o->block_threads >= 64 && o->block_threads <= 1024 && o->block_threads % 32 == 0)
+                          ? o->block_threads : 256;
+    AccArgs aa;
+    aa.D = data_desc();
+    aa.C = chain;
+    aa.tn = chain.t[n];
+    aa.acc = (double *)B.acc.ptr;
+    aa.active = (const uint8_t *)B.active.ptr;
+    aa.order = order;
+    aa.n_chunks = (n_chan + 31) / 32;
+    const long units = order == 0 ? (long)n_row : (long)n_strips * aa.n_chunks;
+    int per_sm = o->ctas_per_sm > 0 ? o->ctas_per_sm : 0;
+    AccLaunch L = acc_launcher(ts, lk, rk, m16);
+    if (!L.fn) return fail(QC_EUNSUPPORTED, "no accumulate kernel for this chain");
+    if (per_sm == 0) {
+        int occ = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, L.fn, block, 0);
+        per_sm = (e == cudaSuccess && occ > 0) ? occ : 2;
+    }
+    const long warps_needed = std::max(1L, units);
+    const int grid = (int)std::max(1L, std::min((long)sm_count * per_sm, (warps_needed * 32 + block - 1) / block));
+
+    UpdArgs ua;
+    ua.type = t.type;
+    ua.n_bins = nb;
+    ua.n_fint = t.n_fint;
+    ua.n_ant = n_ant;
+    ua.acc = (double *)B.acc.ptr;
+    ua.params = (double *)B.params.ptr;
+    ua.tab = (float4 *)B.tab.ptr;
+    ua.gain_flags = (int8_t *)B.flags.ptr;
+    ua.iters = (int *)B.iters.ptr;
+    ua.active = (uint8_t *)B.active.ptr;
+    ua.bin_nvis = (const long long *)B.nvis.ptr;
+    ua.bin_nbytes = (const long long *)B.nvis.ptr + 2 * (size_t)nb;
+    ua.vis_iters = (unsigned long long *)scalars.ptr;
+    ua.acc_bytes = (unsigned long long *)scalars.ptr + 1;
+    ua.tol = t.tol;
+    int *cnt = (int *)B.cnt.ptr;
+    const int upd_block = n_ant >= 128 ? 128 : (n_ant > 32 ? 64 : 32);
+
+    const int max_iter = t.max_iter;
+    int rc;
+    for (int k = 0; k < 2 * max_iter; ++k) { cudaEvent_t ev; if ((rc = get_event(2 + k, ev))) return rc; }
+    const bool use_graph = o->use_graph && !t.reduce;
+    const unsigned rec_flags = use_graph ? cudaEventRecordExternal : cudaEventRecordDefault;
+
+    auto enqueue = [&]() -> int {
+        init_term_kernel<<<(std::max(nb, max_iter + 1) + 255) / 256, 256, 0, st>>>(nb, (uint8_t *)B.active.ptr, cnt,
+                                                                                   max_iter + 1);
+        CK(cudaGetLastError());
+        for (int k = 1; k <= max_iter; ++k) {
+            aa.n_active = cnt + (k - 1);
+            // inside a capture the record must be an external event node to be timed on replay
+            CK(cudaEventRecordWithFlags(events[2 + 2 * (k - 1)], st, rec_flags));
+            CK(L.launch(grid, block, st, aa));
+            CK(cudaEventRecordWithFlags(events[2 + 2 * (k - 1) + 1], st, rec_flags));
+            if (t.reduce) {
+                const size_t KG = t.type == 1 ? KG_FULL : KG_DIAG;
+                if (o->allreduce((double *)B.acc.ptr, (int64_t)nb * n_ant * KG, st, o->allreduce_user))
+                    return fail(QC_ECUDA, "allreduce callback failed");
+            }
+            ua.k = k;
+            ua.alpha = (o->damping_mode == QC_DAMP_ALTERNATE) ? ((k % 2 == 0) ? 0.5 : 1.0)
+                                                               : (o->damping > 0 ? o->damping : 1.0);
+            ua.n_active_prev = cnt + (k - 1);
+            ua.n_active_next = cnt + k;
+            update_kernel<<<nb, upd_block, 0, st>>>(ua);
+            CK(cudaGetLastError());
+        }
+        return QC_OK;
+    };
+    if (use_graph) {
+        if (!B.graph_valid) {
+            if (B.exec) { cudaGraphExecDestroy(B.exec); B.exec = nullptr; }
+            cudaGraph_t g;
+            CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            rc = enqueue();
+            cudaError_t e = cudaStreamEndCapture(st, &g);
+            if (rc) return rc;
+            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&B.exec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+            B.graph_valid = true;
+        }
+        CK(cudaGraphLaunch(B.exec, st));
+    } else {
+        if ((rc = enqueue())) return rc;
+    }
+    launches += 1 + 2 * (long long)max_iter;
+    // iteration bookkeeping: which accumulate launches did work, and their device time
+    std::vector<int> hcnt(max_iter + 1);
+    CK(cudaMemcpyAsync(hcnt.data(), cnt, nbytes<int>(max_iter + 1), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    double ms_sum = 0;
+    long long worked = 0;
+    int last = 0;
+    for (int k = 1; k <= max_iter; ++k) {
+        if (hcnt[k - 1] == 0) break;
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, events[2 + 2 * (k - 1)], events[2 + 2 * (k - 1) + 1]));
+        ms_sum += ms;
+        ++worked;
+        last = k;
+    }
+    *it_max = last;
+    *acc_ms = ms_sum;
+    *acc_launches = worked;
+    return QC_OK;
+}

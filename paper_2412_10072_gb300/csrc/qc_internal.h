@@ -1,0 +1,74 @@
+// qc_internal.h -- the context behind the opaque qc_ctx handle of qc.h.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/qc.h"
+#include "qc_kernels.cuh"
+
+struct Buf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+// Device buffers of one chain position, reused across calls while large enough.
+struct TermBufs {
+    Buf maps;      // t_map then f_map (int32)
+    std::vector<int> hmaps;   // host copy of the maps (staging for the upload)
+    Buf tab;       // FP32 kernel table of the term's Jones matrices
+    Buf params;    // FP64 master copy of the term's parameters
+    Buf stage;     // gains in the public layout (host staging / conversion)
+    Buf acc;       // FP64 normal-equation accumulators [bins][ant][KG]
+    Buf active;    // uint8 [bins]
+    Buf cnt;       // int [max_iter + 1]: intervals active entering iteration k
+    Buf nvis;      // int64 [3][bins]: samples, unflagged samples, algorithmic bytes
+    Buf iters;     // int [bins]
+    Buf flags;     // int8 [bins][ant]
+    cudaGraphExec_t exec = nullptr;
+    bool graph_valid = false;
+};
+
+// One instantiation of the accumulate kernel: its address (for occupancy
+// queries) and a launcher.
+struct AccLaunch {
+    const void *fn = nullptr;
+    cudaError_t (*launch)(int grid, int block, cudaStream_t st, const qc::AccArgs &a) = nullptr;
+};
+AccLaunch acc_launcher(int ts, int lk, int rk, bool m16);
+
+struct qc_ctx {
+    int dev = 0, sm_count = 1;
+    cudaStream_t own_stream = nullptr;
+    int n_row = 0, n_chan = 0, n_ant = 0, n_time = 0, n_bl = 0, n_strips = 0;
+    bool m16 = false, has_flag = false;
+    const float4 *d_vis = nullptr, *d_model = nullptr, *d_weight = nullptr;
+    const uint8_t *d_flag = nullptr;
+    const uint4 *d_model16 = nullptr;
+    const float *d_bl_scale = nullptr;
+    int4 *d_rows = nullptr;
+    int *d_strip_rows = nullptr, *d_strip_off = nullptr;
+    std::vector<void *> owned;
+    std::vector<cudaEvent_t> events;
+    TermBufs tb[QC_MAX_TERMS];
+    Buf scalars;                      // counters and chi^2 scratch
+    Buf resid_stage;
+    long long launches = 0;
+    std::string err;
+
+    ~qc_ctx();
+    int fail(int code, const std::string &msg);
+    int cuda_fail(cudaError_t e, const char *what);
+    void *alloc(size_t bytes, cudaError_t *e);
+    void release(void *p);
+    int ensure(Buf &b, size_t bytes);
+    int get_event(int i, cudaEvent_t &ev);
+    int validate_terms(const qc_term *terms, int n_terms, bool need_solve_fields);
+    int stage_terms(const qc_term *terms, int n_terms, cudaStream_t st, qc::Chain &chain);
+    qc::Data data_desc() const;
+    int run_residual(const qc::Chain &chain, float4 *dres, double *d_chi2, cudaStream_t st);
+    int pick_order(const qc_term &t, const qc_opts *o) const;
+    int solve_term(const qc_term *terms, int n_terms, int n, qc::Chain chain, const qc_opts *o, cudaStream_t st,
+                   int *it_max, double *acc_ms, long long *acc_launches);
+};

@@ -234,46 +234,120 @@ def corrupt(model: np.ndarray, terms: List[TermSpec], ant1, ant2, time_idx, n_ch
     return V.reshape(model.shape)
 
 
-def make_observation(n_ant: int, n_time: int, freqs: np.ndarray, terms: List[TermSpec], *,
-                     n_src: int, seed: int, noise: float, flag_row_frac: float = 0.0,
-                     max_baseline_m: float = 1000.0, nan_in_flagged: bool = False,
-                     sky_rng: Optional[np.random.Generator] = None,
-                     rng: Optional[np.random.Generator] = None,
-                     ant_x: Optional[np.ndarray] = None) -> Observation:
-    """Build one observation; every random draw comes from ``seed``."""
-    rng = rng if rng is not None else np.random.default_rng(seed)
-    sky_rng = sky_rng if sky_rng is not None else rng
-    n_chan = freqs.size
-    if ant_x is None:
-        ant_x = ew_array(n_ant, max_baseline_m, sky_rng)
-    sky = point_sources(n_src, sky_rng)
+@dataclasses.dataclass
+class Setup:
+    """Everything of an observation that is drawn from the host RNG (small arrays only)."""
+    n_ant: int
+    n_time: int
+    freqs: np.ndarray
+    terms: List[TermSpec]
+    ant_x: np.ndarray
+    sky: Sky
+    ant1: np.ndarray
+    ant2: np.ndarray
+    time_idx: np.ndarray
+    uvw: np.ndarray            # [row, 3] metres
+    flag_rows: np.ndarray      # [row] bool, whole-row flags
+    rng: np.random.Generator   # continues with the noise draws of the host path
+
+
+def draw_setup(n_ant: int, n_time: int, freqs: np.ndarray, terms: List[TermSpec], *, n_src: int,
+               rng: np.random.Generator, ant_x: np.ndarray, flag_row_frac: float = 0.0) -> Setup:
+    sky = point_sources(n_src, rng)
     p, q = baselines(n_ant)
     n_bl = p.size
     ha = hour_angles(n_time)
     uvw = ew_uvw(ant_x, p, q, ha).reshape(n_time * n_bl, 3)
-    ant1 = np.tile(p, n_time)
-    ant2 = np.tile(q, n_time)
+    ant1 = np.tile(p, n_time).astype(np.int32)
+    ant2 = np.tile(q, n_time).astype(np.int32)
     time_idx = np.repeat(np.arange(n_time, dtype=np.int32), n_bl)
-    scal = predict_scalar(uvw, freqs, sky)
-    model = np.zeros((ant1.size, n_chan, 4), dtype=np.complex128)
+    flag_rows = (rng.random(ant1.size) < flag_row_frac) if flag_row_frac > 0 else np.zeros(ant1.size, bool)
+    return Setup(n_ant, n_time, np.asarray(freqs, np.float64), terms, ant_x, sky, ant1, ant2, time_idx, uvw,
+                 flag_rows, rng)
+
+
+def make_observation(n_ant: int, n_time: int, freqs: np.ndarray, terms: List[TermSpec], *,
+                     n_src: int, seed: int, noise: float, flag_row_frac: float = 0.0,
+                     max_baseline_m: float = 1000.0, nan_in_flagged: bool = False,
+                     rng: Optional[np.random.Generator] = None,
+                     ant_x: Optional[np.ndarray] = None) -> Observation:
+    """Build one observation on the host; every random draw comes from ``seed`` (or ``rng``)."""
+    rng = rng if rng is not None else np.random.default_rng(seed)
+    n_chan = freqs.size
+    if ant_x is None:
+        ant_x = ew_array(n_ant, max_baseline_m, rng)
+    su = draw_setup(n_ant, n_time, freqs, terms, n_src=n_src, rng=rng, ant_x=ant_x, flag_row_frac=flag_row_frac)
+    scal = predict_scalar(su.uvw, freqs, su.sky)
+    model = np.zeros((su.ant1.size, n_chan, 4), dtype=np.complex128)
     model[:, :, 0] = scal
     model[:, :, 3] = scal
-    data = corrupt(model, terms, ant1, ant2, time_idx, n_chan)
+    data = corrupt(model, terms, su.ant1, su.ant2, su.time_idx, n_chan)
     if noise > 0:
         data = data + noise * (rng.standard_normal(data.shape) + 1j * rng.standard_normal(data.shape))
     weight = np.ones(data.shape, dtype=np.float64)
-    flag = np.zeros((ant1.size, n_chan), dtype=np.uint8)
-    if flag_row_frac > 0:
-        rows = rng.random(ant1.size) < flag_row_frac
-        flag[rows, :] = 1
+    flag = np.zeros((su.ant1.size, n_chan), dtype=np.uint8)
+    flag[su.flag_rows, :] = 1
     if nan_in_flagged:
         data[flag.astype(bool)] = np.nan + 1j * np.nan
     return Observation(n_ant=n_ant, n_time=n_time, n_chan=n_chan, data=data, model=model,
-                       weight=weight, flag=flag, ant1=ant1.astype(np.int32),
-                       ant2=ant2.astype(np.int32), time_idx=time_idx.astype(np.int32),
+                       weight=weight, flag=flag, ant1=su.ant1, ant2=su.ant2, time_idx=su.time_idx,
                        freqs=freqs, terms=terms,
                        meta=dict(seed=seed, noise=noise, n_src=n_src, ant_x=ant_x,
-                                 flag_row_frac=flag_row_frac, sky=sky))
+                                 flag_row_frac=flag_row_frac, sky=su.sky))
+
+
+def make_observation_device(su: Setup, noise: float, noise_seed: int, device, rows_per_chunk: int = 4096):
+    """The same observation generated on a CUDA device (for sizes the host cannot produce
+    quickly): complex64 data/model, float32 weights, uint8 flags, all resident on ``device``.
+
+    The small random draws (array, sky, truths, flagged rows) come from ``su`` and are identical
+    to :func:`make_observation`; the thermal noise is drawn on the device from ``noise_seed``.
+    Returns a dict of tensors plus the host metadata.
+    """
+    import torch
+    n_row, n_chan = su.ant1.size, su.freqs.size
+    dev = torch.device(device)
+    f64, c128 = torch.float64, torch.complex128
+    data = torch.empty((n_row, n_chan, 4), dtype=torch.complex64, device=dev)
+    model = torch.empty((n_row, n_chan, 4), dtype=torch.complex64, device=dev)
+    weight = torch.ones((n_row, n_chan, 4), dtype=torch.float32, device=dev)
+    flag = torch.from_numpy(su.flag_rows.astype(np.uint8)).to(dev)[:, None].expand(n_row, n_chan).contiguous()
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(int(noise_seed))
+    nu = torch.from_numpy(su.freqs).to(dev, f64)
+    flux = torch.from_numpy(su.sky.flux).to(dev, f64)
+    lmn = torch.from_numpy(np.stack([su.sky.l, su.sky.m, su.sky.n - 1.0])).to(dev, f64)     # [3, src]
+    jones = [torch.from_numpy(t.truth_jones()).to(dev, c128) for t in su.terms]
+    tmaps = [torch.from_numpy(t.t_map.astype(np.int64)).to(dev) for t in su.terms]
+    fmaps = [torch.from_numpy(t.f_map.astype(np.int64)).to(dev) for t in su.terms]
+    chan = torch.arange(n_chan, device=dev)
+    eye = torch.eye(2, dtype=c128, device=dev)
+    for r0 in range(0, n_row, rows_per_chunk):
+        r1 = min(n_row, r0 + rows_per_chunk)
+        uvw = torch.from_numpy(su.uvw[r0:r1]).to(dev, f64)
+        ph = uvw @ lmn                                                         # [R, src] metres
+        ang = (-2.0 * np.pi / C_LIGHT) * ph[:, :, None] * nu[None, None, :]   # [R, src, C]
+        scal = torch.einsum("k,rkc->rc", flux.to(c128), torch.polar(torch.ones_like(ang), ang))
+        M = scal[:, :, None, None] * eye                                        # [R, C, 2, 2]
+        t = torch.from_numpy(su.time_idx[r0:r1].astype(np.int64)).to(dev)
+        a1 = torch.from_numpy(su.ant1[r0:r1].astype(np.int64)).to(dev)
+        a2 = torch.from_numpy(su.ant2[r0:r1].astype(np.int64)).to(dev)
+        Cp = eye.expand(r1 - r0, n_chan, 2, 2)
+        Cq = Cp
+        for J, tm, fm in zip(jones, tmaps, fmaps):
+            it = tm[t][:, None]
+            jf = fm[chan][None, :]
+            Cp = Cp @ J[it, jf, a1[:, None]].reshape(r1 - r0, n_chan, 2, 2)
+            Cq = Cq @ J[it, jf, a2[:, None]].reshape(r1 - r0, n_chan, 2, 2)
+        V = Cp @ M @ Cq.conj().transpose(-1, -2)
+        V = V.reshape(r1 - r0, n_chan, 4)
+        if noise > 0:
+            nz = torch.randn((r1 - r0, n_chan, 4, 2), dtype=torch.float32, device=dev, generator=gen)
+            V = V + noise * torch.view_as_complex(nz).to(c128)
+        data[r0:r1] = V.to(torch.complex64)
+        model[r0:r1] = M.reshape(r1 - r0, n_chan, 4).to(torch.complex64)
+    return dict(data=data, model=model, weight=weight, flag=flag, ant1=su.ant1, ant2=su.ant2,
+                time_idx=su.time_idx, n_ant=su.n_ant, n_time=su.n_time, n_chan=n_chan, terms=su.terms)
 
 
 # ---------------------------------------------------------------------------
@@ -309,6 +383,16 @@ def plain_large_terms(n_ant: int, n_time: int, n_chan: int, rng: np.random.Gener
     G.truth = full_truth(n_ant, n_time, 1, rng)
     B.truth = bandpass_truth(n_ant, 1, n_chan, rng)
     return [G, B]
+
+
+def plain_large_setup(seed: int = 1, n_ant: int = 64, n_time: int = 300, n_chan: int = 512,
+                      flag_row_frac: float = 0.1, n_src: int = 50) -> Setup:
+    """Host-drawn part of the large two-term workload (see :func:`plain_large`)."""
+    rng = np.random.default_rng(seed)
+    freqs = meerkat_band(n_chan)
+    ant_x = ew_array(n_ant, 8000.0, rng)
+    terms = plain_large_terms(n_ant, n_time, n_chan, rng)
+    return draw_setup(n_ant, n_time, freqs, terms, n_src=n_src, rng=rng, ant_x=ant_x, flag_row_frac=flag_row_frac)
 
 
 def plain_large(seed: int = 1, n_ant: int = 64, n_time: int = 300, n_chan: int = 512,

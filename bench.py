@@ -1,0 +1,370 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GB300 gain-calibration solver.
+
+Workload (default): 64 antennas (2016 baselines), 300 times x 512 channels,
+4 correlations, complex64 data/model and float32 weights resident in HBM
+(25.1 GB), 50 point sources, noise sigma 0.05, 10% of rows flagged; the
+chain is G (full 2x2, one interval per time) then B (diagonal bandpass, one
+interval per channel), 3 epochs, at most 20 iterations per term solve,
+tolerance 1e-6.  One step = one qc_solve of that chain from unit gains.
+
+Metric: visibility-iterations per second (samples of active intervals summed
+over every iteration of every term solve, divided by device time).  The JSON
+line also carries the roofline of the accumulate kernel (algorithmic bytes /
+event-timed duration vs measured HBM bandwidth), an end-to-end figure through
+the C ABI with host buffers, the FP64 oracle timed on a bounded sample on the
+host cores, and SM clocks sampled during the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {ours,reference}] [--mixed]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import signal
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "vis*iterations/s"
+UNIT = "vis*iter/s"
+WORKLOAD = "plain two-term solve: 64 ant, 300 t x 512 ch, G full 1t x 512ch then B diag 300t x 1ch, 3 epochs"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mixed", action="store_true", help="FP16 model storage with per-baseline scales")
+    ap.add_argument("--n-time", type=int, default=300)
+    ap.add_argument("--n-chan", type=int, default=512)
+    ap.add_argument("--n-ant", type=int, default=64)
+    ap.add_argument("--epochs", type=int, default=3)
+    ap.add_argument("--max-iter", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel", type=int, default=0, help="accumulate kernel: 0 auto, 1 pipelined, 2 plain")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in ("qc_kernels.cuh", "qc_jones.cuh", "qc_acc.cu"):
+        with open(os.path.join(ROOT, "paper_2412_10072_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per full accumulate launch from the committed ncu summary, if it was taken on
+    the current kernel source (its hash is recorded next to the figure); else None."""
+    path = os.path.join(ROOT, "profiles", "acc_kernel_plain_large.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None, None
+    m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]{16})", text)
+    t = re.search(r"traffic_bytes_per_full_launch:\s*([0-9.eE+]+)", text)
+    a = re.search(r"algorithmic_bytes_per_full_launch:\s*([0-9.eE+]+)", text)
+    if not (m and t) or m.group(1) != kernel_source_hash():
+        return None, None
+    return float(t.group(1)), (float(a.group(1)) if a else None)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="qc_clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.send_signal(signal.SIGTERM)
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_median": statistics.median(power) if power else None}
+
+
+# ---------------------------------------------------------------------------
+# the workload
+# ---------------------------------------------------------------------------
+
+def make_terms(qc, setup, n_ant, max_iter):
+    return [qc.Term.from_spec(s, n_ant, max_iter=max_iter, tol=1e-6) for s in setup.terms]
+
+
+def cpu_baseline(args, dev_obs, setup, n_times=2, max_iter=4):
+    """The FP64 oracle on a bounded sample of the same workload: the rows of the first
+    ``n_times`` times (all baselines, all channels), one epoch of G then B, ``max_iter``
+    iterations each, single-threaded C on the host."""
+    import numpy as np
+    import oracle as O
+    n_bl = setup.n_ant * (setup.n_ant - 1) // 2
+    rows = n_times * n_bl
+    data = dev_obs["data"][:rows].cpu().numpy()
+    model = dev_obs["model"][:rows].cpu().numpy()
+    weight = dev_obs["weight"][:rows].cpu().numpy()
+    flag = dev_obs["flag"][:rows].cpu().numpy()
+    P = O.OracleProblem(data, model, weight, flag, setup.ant1[:rows], setup.ant2[:rows], setup.time_idx[:rows],
+                        setup.n_ant, n_times)
+    terms = []
+    for s in setup.terms:
+        tm = s.t_map[:n_times]
+        nt = int(tm.max()) + 1
+        terms.append(O.OracleTerm(s.kind, tm, s.f_map, nt, s.n_fint, setup.n_ant, max_iter=max_iter, tol=1e-6))
+    t0 = time.perf_counter()
+    its = O.solve(P, terms, n_epochs=1, damping_mode=1)
+    dt = time.perf_counter() - t0
+    n_vis = rows * data.shape[1]
+    vis_iters = sum(int(n_vis * (it.astype(np.int64).sum() / it.size)) for it in its)
+    return {"value": vis_iters / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {n_times} of {setup.n_time} times ({n_vis} vis), 1 epoch G then B, "
+                      f"<= {max_iter} iterations each, {dt:.1f} s single-threaded FP64 C"}
+
+
+def run_reference(args):
+    """--impl reference: the FP64 oracle as it stands on the host cores, on a bounded sample of the
+    same workload (the first 2 times of the 64-antenna, 512-channel observation; 1 epoch, <= 2
+    iterations per term per step)."""
+    import numpy as np
+    import oracle as O
+    from paper_2412_10072_gb300 import synth
+    obs = synth.plain_large(seed=1, n_ant=args.n_ant, n_time=2, n_chan=args.n_chan, noise=0.05,
+                            flag_row_frac=0.1, n_src=50)
+    P = O.OracleProblem.from_obs(obs)
+
+    def step():
+        terms = [O.OracleTerm.from_spec(s, obs.n_ant, max_iter=2, tol=1e-6) for s in obs.terms]
+        its = O.solve(P, terms, n_epochs=1, damping_mode=1)
+        return sum(int(obs.n_vis * it.astype(np.int64).sum() / it.size) for it in its)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    vi = sum(step() for _ in range(args.steps))
+    dt = time.perf_counter() - t0
+    value = vi / dt
+    sample = (f"first 2 of {args.n_time} times of the same workload ({obs.n_vis} vis), 1 epoch G then B, "
+              f"<= 2 iterations each per step, single-threaded FP64 C oracle")
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD + " (oracle sample)", "sample_vis": obs.n_vis},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+
+    import numpy as np
+    import torch
+    from paper_2412_10072_gb300 import qc, synth
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # ---- workload on the device (weak scaling: every rank its own observation) ----
+    setup = synth.plain_large_setup(seed=1 + rank, n_ant=args.n_ant, n_time=args.n_time, n_chan=args.n_chan,
+                                    flag_row_frac=0.1, n_src=50)
+    t_gen = time.perf_counter()
+    obs = synth.make_observation_device(setup, noise=0.05, noise_seed=1000 + rank, device=f"cuda:{local}")
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
+    n_vis = setup.ant1.size * args.n_chan
+    input_bytes = sum(int(obs[k].numel() * obs[k].element_size()) for k in ("data", "model", "weight", "flag"))
+    stream = torch.cuda.Stream()
+    solver = qc.Solver(obs["data"], obs["model"], obs["weight"], obs["flag"], setup.ant1, setup.ant2,
+                       setup.time_idx, setup.n_ant, setup.n_time, model_fp16=args.mixed)
+
+    def step():
+        terms = make_terms(qc, setup, setup.n_ant, args.max_iter)
+        return solver.solve(terms, n_epochs=args.epochs, stream=stream, kernel=args.kernel), terms
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local)
+        clocks.start()
+        barrier()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        stats = [step()[0] for _ in range(args.steps)]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        clock_info = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    vis_iters = sum(s.vis_iters for s in stats)
+    acc_bytes = sum(s.acc_bytes for s in stats)
+    acc_ms = sum(s.acc_ms for s in stats)
+    acc_launches = sum(s.acc_launches for s in stats)
+    launches = sum(s.launches for s in stats)
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        v = torch.tensor([float(vis_iters)], dtype=torch.float64, device="cuda")
+        dist.all_reduce(v)
+        vis_iters_all = float(v.item())
+    else:
+        vis_iters_all = float(vis_iters)
+    value = vis_iters_all / (ms / 1000.0)
+
+    # ---- roofline of the accumulate kernel (event-timed on the solver stream) ----
+    peaks, peak_src = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = (acc_bytes / (acc_ms / 1000.0)) / 1e9 if acc_ms > 0 else None
+    traffic, algo_full = profiled_traffic()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
+                "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured"
+                else "fallback 6.8 TB/s", "kernel": "acc_kernel (JHJ/JHr accumulate)",
+                "algorithmic_bytes_per_launch": acc_bytes / max(1, acc_launches),
+                "algorithmic_bytes_per_full_launch": algo_full,
+                "launch_ms_mean": acc_ms / max(1, acc_launches), "acc_share_of_step": acc_ms / ms if ms else None}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args, obs, setup)
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region ----
+    e2e = None
+    if not args.no_e2e:
+        host = {k: torch.empty(obs[k].shape, dtype=obs[k].dtype, pin_memory=True) for k in
+                ("data", "model", "weight", "flag")}
+        for k in host:
+            host[k].copy_(obs[k])
+        h2d = sum(int(v.numel() * v.element_size()) for v in host.values())
+        del solver
+        for k in ("data", "model", "weight", "flag"):
+            obs[k] = None
+        torch.cuda.empty_cache()
+
+        def e2e_step():
+            s = qc.Solver(host["data"], host["model"], host["weight"], host["flag"], setup.ant1, setup.ant2,
+                          setup.time_idx, setup.n_ant, setup.n_time, model_fp16=args.mixed)
+            terms = make_terms(qc, setup, setup.n_ant, args.max_iter)
+            st = s.solve(terms, n_epochs=args.epochs, kernel=args.kernel)
+            s.close()
+            d2h = sum(t.gains.nbytes + t.gain_flags.nbytes + t.iters.nbytes for t in terms)
+            return st.vis_iters, d2h
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        res = [e2e_step() for _ in range(args.e2e_steps)]
+        torch.cuda.synchronize()
+        barrier()
+        dt = time.perf_counter() - t0
+        vi = sum(r[0] for r in res)
+        if dist is not None:
+            t = torch.tensor([dt, float(vi)], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t[:1], op=dist.ReduceOp.MAX)
+            tv = t[1:].clone()
+            dist.all_reduce(tv)
+            dt, vi = float(t[0].item()), float(tv.item())
+        e2e = {"value": vi / dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": res[0][1],
+               "steps": args.e2e_steps, "note": "qc_create from pinned host buffers + qc_solve + gains D2H + qc_destroy"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64+f16" if args.mixed else "c64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + (" (FP16 model)" if args.mixed else ""), "n_ant": args.n_ant,
+                       "n_time": args.n_time, "n_chan": args.n_chan, "n_vis": n_vis,
+                       "input_bytes_per_gpu": input_bytes, "l2": "inputs (25 GB) larger than L2 (129 MB)",
+                       "epochs": args.epochs, "max_iter": args.max_iter, "tol": 1e-6,
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                       "gen_s": round(t_gen, 2)},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clock_info,
+            "gpu_launches": int(launches), "accumulate_launches_with_work": int(acc_launches),
+            "vis_iters": int(vis_iters_all),
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

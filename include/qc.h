@@ -46,7 +46,7 @@ extern "C" {
 #define QC_EINVAL        -1   /* invalid argument (sizes, indices, maps, NULL pointers)      */
 #define QC_ENOMEM        -2   /* device or host allocation failed                            */
 #define QC_ECUDA         -3   /* a CUDA runtime call or kernel launch failed                 */
-#define QC_ETIMEOUT      -4   /* reserved: a bounded device wait gave up                     */
+#define QC_ETIMEOUT      -4   /* a bounded device wait gave up (2 s); the context stays usable */
 #define QC_EUNSUPPORTED  -5   /* valid request outside what this build implements           */
 
 #define QC_TERM_DIAG   0      /* diagonal complex gain, free parameters g_XX, g_YY           */
@@ -138,6 +138,8 @@ typedef struct {
     int32_t order;             /* -1 auto, 0 row-major tiles, 1 baseline-strip tiles */
     int32_t block_threads;     /* threads per CTA of the accumulate kernel (0: auto) */
     int32_t ctas_per_sm;       /* resident CTAs per SM for its grid (0: auto)        */
+    int32_t kernel;            /* 0 auto (= 1), 1 bulk-copy pipelined accumulate kernel,
+                                  2 plain warp-tile accumulate kernel                 */
     qc_allreduce_fn allreduce; /* required when a solved term has reduce = 1       */
     void *allreduce_user;
 } qc_opts;

@@ -328,6 +328,16 @@ extern "C" int qc_create(const qc_problem *p, qc_ctx **out)
         model32 = nullptr;
     }
     c->d_model = model32;
+    DALLOC(c->d_row_live, uint8_t, std::max(1, p->n_row));
+    DALLOC(c->d_err, int, 1);
+    e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->own_stream);
+    if (e == cudaSuccess && p->n_row) {
+        row_live_kernel<<<grid_for((long)p->n_row * 32, 256, c->sm_count), 256, 0, c->own_stream>>>(c->data_desc(),
+                                                                                                     c->d_row_live);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->own_stream);
+    if (e != cudaSuccess) { g_create_error = std::string("row flags: ") + cudaGetErrorString(e); return QC_ECUDA; }
 #undef DALLOC
 #undef HCOPY
     *out = c.release();
@@ -635,6 +645,11 @@ extern "C" int qc_solve(qc_ctx *c, qc_term *terms, int32_t n_terms, const qc_opt
     return QC_OK;
 }
 
+bool qc_ctx::configured(const void *fn) const
+{
+    return std::find(configured_fns.begin(), configured_fns.end(), fn) != configured_fns.end();
+}
+
 int qc_ctx::get_event(int i, cudaEvent_t &ev)
 {
     while ((int)events.size() <= i) {
@@ -665,21 +680,42 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
     aa.D = data_desc();
     aa.C = chain;
     aa.tn = chain.t[n];
+    aa.to = n_terms == 2 ? chain.t[1 - n] : chain.t[n];
     aa.acc = (double *)B.acc.ptr;
     aa.active = (const uint8_t *)B.active.ptr;
     aa.order = order;
     aa.n_chunks = (n_chan + 31) / 32;
     const long units = order == 0 ? (long)n_row : (long)n_strips * aa.n_chunks;
     int per_sm = o->ctas_per_sm > 0 ? o->ctas_per_sm : 0;
-    AccLaunch L = acc_launcher(ts, lk, rk, m16);
+    const bool simple = n_terms <= 2;
+    AccLaunch L = acc_launcher(ts, simple, lk, rk, m16);
     if (!L.fn) return fail(QC_EUNSUPPORTED, "no accumulate kernel for this chain");
-    if (per_sm == 0) {
-        int occ = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, L.fn, block, 0);
-        per_sm = (e == cudaSuccess && occ > 0) ? occ : 2;
+    const bool pipelined = o->kernel != 2;
+    int grid;
+    if (pipelined) {
+        if (!configured(L.pipe_fn)) {
+            CK(cudaFuncSetAttribute(L.pipe_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, L.pipe_smem));
+            configured_fns.push_back(L.pipe_fn);
+        }
+        const long groups = (units + (L.pipe_threads / 32 - 1) - 1) / (L.pipe_threads / 32 - 1);
+        grid = (int)std::max(1L, std::min((long)sm_count, groups));
+    } else {
+        if (per_sm == 0) {
+            int occ = 0;
+            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, L.fn, block, 0);
+            per_sm = (e == cudaSuccess && occ > 0) ? occ : 2;
+        }
+        const long warps_needed = std::max(1L, units);
+        grid = (int)std::max(1L, std::min((long)sm_count * per_sm, (warps_needed * 32 + block - 1) / block));
     }
-    const long warps_needed = std::max(1L, units);
-    const int grid = (int)std::max(1L, std::min((long)sm_count * per_sm, (warps_needed * 32 + block - 1) / block));
+    int rc;
+    if ((rc = ensure(B.chunk_act, (size_t)t.n_tint * aa.n_chunks))) return rc;
+    PipeArgs pa;
+    pa.a = aa;
+    pa.row_live = d_row_live;
+    pa.chunk_active = (const uint8_t *)B.chunk_act.ptr;
+    pa.err = d_err;
+    const int ca_threads = t.n_tint * aa.n_chunks;
 
     UpdArgs ua;
     ua.type = t.type;
@@ -701,7 +737,6 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
     const int upd_block = n_ant >= 128 ? 128 : (n_ant > 32 ? 64 : 32);
 
     const int max_iter = t.max_iter;
-    int rc;
     for (int k = 0; k < 2 * max_iter; ++k) { cudaEvent_t ev; if ((rc = get_event(2 + k, ev))) return rc; }
     const bool use_graph = o->use_graph && !t.reduce;
     const unsigned rec_flags = use_graph ? cudaEventRecordExternal : cudaEventRecordDefault;
@@ -713,8 +748,19 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
         for (int k = 1; k <= max_iter; ++k) {
             aa.n_active = cnt + (k - 1);
             // inside a capture the record must be an external event node to be timed on replay
+            if (pipelined) {
+                chunk_active_kernel<<<(ca_threads + 255) / 256, 256, 0, st>>>(aa.tn, n_chan, aa.n_chunks,
+                                                                            (const uint8_t *)B.active.ptr, cnt + (k - 1),
+                                                                            (uint8_t *)B.chunk_act.ptr);
+                CK(cudaGetLastError());
+            }
             CK(cudaEventRecordWithFlags(events[2 + 2 * (k - 1)], st, rec_flags));
-            CK(L.launch(grid, block, st, aa));
+            if (pipelined) {
+                pa.a.n_active = cnt + (k - 1);
+                CK(L.pipe_launch(grid, st, pa));
+            } else {
+                CK(L.launch(grid, block, st, aa));
+            }
             CK(cudaEventRecordWithFlags(events[2 + 2 * (k - 1) + 1], st, rec_flags));
             if (t.reduce) {
                 const size_t KG = t.type == 1 ? KG_FULL : KG_DIAG;
@@ -749,11 +795,17 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
     } else {
         if ((rc = enqueue())) return rc;
     }
-    launches += 1 + 2 * (long long)max_iter;
+    launches += 1 + (pipelined ? 3 : 2) * (long long)max_iter;
     // iteration bookkeeping: which accumulate launches did work, and their device time
     std::vector<int> hcnt(max_iter + 1);
+    int herr = 0;
     CK(cudaMemcpyAsync(hcnt.data(), cnt, nbytes<int>(max_iter + 1), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    if (herr) {
+        CK(cudaMemsetAsync(d_err, 0, sizeof(int), st));
+        return fail(QC_ETIMEOUT, "a bounded wait in the pipelined accumulate kernel gave up (2 s)");
+    }
     double ms_sum = 0;
     long long worked = 0;
     int last = 0;

@@ -26,6 +26,7 @@ struct TermBufs {
     Buf nvis;      // int64 [3][bins]: samples, unflagged samples, algorithmic bytes
     Buf iters;     // int [bins]
     Buf flags;     // int8 [bins][ant]
+    Buf chunk_act; // uint8 [n_tint][n_chunks] for the pipelined kernel
     cudaGraphExec_t exec = nullptr;
     bool graph_valid = false;
 };
@@ -35,8 +36,16 @@ struct TermBufs {
 struct AccLaunch {
     const void *fn = nullptr;
     cudaError_t (*launch)(int grid, int block, cudaStream_t st, const qc::AccArgs &a) = nullptr;
+    const void *pipe_fn = nullptr;
+    cudaError_t (*pipe_launch)(int grid, cudaStream_t st, const qc::PipeArgs &p) = nullptr;
+    int pipe_smem = 0, pipe_threads = 0;
 };
-AccLaunch acc_launcher(int ts, int lk, int rk, bool m16);
+AccLaunch acc_launcher_diag(bool simple, int lk, int rk, bool m16);
+AccLaunch acc_launcher_full(bool simple, int lk, int rk, bool m16);
+inline AccLaunch acc_launcher(int ts, bool simple, int lk, int rk, bool m16)
+{
+    return ts == qc::TS_FULL ? acc_launcher_full(simple, lk, rk, m16) : acc_launcher_diag(simple, lk, rk, m16);
+}
 
 struct qc_ctx {
     int dev = 0, sm_count = 1;
@@ -49,12 +58,15 @@ struct qc_ctx {
     const float *d_bl_scale = nullptr;
     int4 *d_rows = nullptr;
     int *d_strip_rows = nullptr, *d_strip_off = nullptr;
+    uint8_t *d_row_live = nullptr;    // [n_row]
+    int *d_err = nullptr;             // device error flag of bounded waits
     std::vector<void *> owned;
     std::vector<cudaEvent_t> events;
     TermBufs tb[QC_MAX_TERMS];
     Buf scalars;                      // counters and chi^2 scratch
     Buf resid_stage;
     long long launches = 0;
+    std::vector<const void *> configured_fns;   // kernels whose dynamic smem limit was raised
     std::string err;
 
     ~qc_ctx();
@@ -64,6 +76,7 @@ struct qc_ctx {
     void release(void *p);
     int ensure(Buf &b, size_t bytes);
     int get_event(int i, cudaEvent_t &ev);
+    bool configured(const void *fn) const;
     int validate_terms(const qc_term *terms, int n_terms, bool need_solve_fields);
     int stage_terms(const qc_term *terms, int n_terms, cudaStream_t st, qc::Chain &chain);
     qc::Data data_desc() const;

@@ -29,6 +29,7 @@
 #pragma once
 #include <stdint.h>
 
+#include "qc_async.cuh"
 #include "qc_jones.cuh"
 
 namespace qc {
@@ -75,11 +76,32 @@ struct Data {
     int n_strips;
 };
 
+struct AccArgs {
+    Data D;
+    Chain C;
+    DevTerm tn;              // copy of C.t[C.n] (avoids dynamic indexing of kernel parameters)
+    DevTerm to;              // the other term of a two-term chain (unused otherwise)
+    double *acc;             // [n_bins][n_ant][KG]
+    const uint8_t *active;   // [n_bins]
+    const int *n_active;     // nonzero: some interval of the solved term is still iterating
+    int order;               // 0 row tiles, 1 strip tiles
+    int n_chunks;            // ceil(n_chan / 32)
+};
+
 __device__ __forceinline__ J2 fetch_jones(const DevTerm &T, int n_ant, int tint, int fint, int ant)
 {
     const size_t idx = ((size_t)tint * n_ant + ant) * T.n_fint + fint;
     if (T.type == 1) return j_from(__ldg(T.tab + 2 * idx), __ldg(T.tab + 2 * idx + 1));
     return j_diag(__ldg(T.tab + idx));
+}
+
+// Jones matrix of a term whose kind is known at compile time (diag/phase tables hold
+// the two diagonal entries in one float4, full tables the four entries in two).
+template <int K> __device__ __forceinline__ J2 fetch_k(const DevTerm &T, int n_ant, int tint, int fint, int ant)
+{
+    const unsigned idx = ((unsigned)tint * n_ant + ant) * (unsigned)T.n_fint + fint;
+    if constexpr (K == KIND_FULL) return j_from(__ldg(T.tab + 2 * (size_t)idx), __ldg(T.tab + 2 * (size_t)idx + 1));
+    else return j_diag(__ldg(T.tab + idx));
 }
 
 // Multiply helpers specialised on the kind of one operand.
@@ -94,6 +116,14 @@ template <int K> __device__ __forceinline__ J2 rmulk(const J2 &A, const J2 &B)
     if constexpr (K == KIND_NONE) return A;
     else if constexpr (K == KIND_DIAG) return j_muld(A, B.a, B.d);
     else return j_mul(A, B);
+}
+
+// A B^H with B of kind K
+template <int K> __device__ __forceinline__ J2 rmulk_h(const J2 &A, const J2 &B)
+{
+    if constexpr (K == KIND_NONE) return A;
+    else if constexpr (K == KIND_DIAG) return j_muld(A, cconj(B.a), cconj(B.d));
+    else return j_mul_h(A, B);
 }
 
 // ---------------------------------------------------------------------------
@@ -138,6 +168,23 @@ template <int KR, bool KAHAN> struct Acc {
         if constexpr (KAHAN) two_sum_add(s[i], c[i], x);
         else s[i] += x;
     }
+    // s[i] += a b
+    __device__ __forceinline__ void fma(int i, float a, float b)
+    {
+        if constexpr (KAHAN) two_sum_add(s[i], c[i], a * b);
+        else s[i] = fmaf(a, b, s[i]);
+    }
+    // (s[i], s[i+1]) += conj(x) y
+    __device__ __forceinline__ void cfma(int i, float2 x, float2 y)
+    {
+        if constexpr (KAHAN) {
+            two_sum_add(s[i], c[i], fmaf(x.x, y.x, x.y * y.y));
+            two_sum_add(s[i + 1], c[i + 1], fmaf(x.x, y.y, -x.y * y.x));
+        } else {
+            s[i] = fmaf(x.x, y.x, fmaf(x.y, y.y, s[i]));
+            s[i + 1] = fmaf(x.x, y.y, fmaf(-x.y, y.x, s[i + 1]));
+        }
+    }
 };
 
 // Contribution of one sample to antenna a's blocks: E = L_a (x) X^T (Eq. vectrick,
@@ -154,20 +201,14 @@ __device__ __forceinline__ void accumulate_side(Acc<AccLayout<TS, HAS_L>::KR, KA
         if constexpr (TS == TS_DIAG) {
             // parameter k in {XX, YY} touches row k of V: E[(k,j), k] = X[k][j]
 #pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                float h = 0.f;
-                float2 jr = make_float2(0.f, 0.f);
+            for (int k = 0; k < 2; ++k)
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
                     const float2 x = Xv[2 * k + j];
                     const float ww = wv[2 * k + j];
-                    h = fmaf(ww, cnorm2(x), h);
-                    jr = cfma_conj(x, cscale(rv[2 * k + j], ww), jr);
+                    A.fma(k, ww, cnorm2(x));
+                    A.cfma(2 + 2 * k, x, cscale(rv[2 * k + j], ww));
                 }
-                A.add(k, h);
-                A.add(2 + 2 * k, jr.x);
-                A.add(3 + 2 * k, jr.y);
-            }
         } else {
             // parameter u = (k, l): E[(k,j), (k,l)] = X[l][j]
             const float2 x00 = Xv[0], x01 = Xv[1], x10 = Xv[2], x11 = Xv[3];
@@ -177,18 +218,19 @@ __device__ __forceinline__ void accumulate_side(Acc<AccLayout<TS, HAS_L>::KR, KA
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
                 const float w0 = wv[2 * k], w1 = wv[2 * k + 1];
-                A.add(2 * k + 0, fmaf(w0, n00, w1 * n01));
-                A.add(2 * k + 1, fmaf(w0, n10, w1 * n11));
-                const float2 off = make_float2(fmaf(w0, o0.x, w1 * o1.x), fmaf(w0, o0.y, w1 * o1.y));
-                A.add(4 + 2 * k, off.x);
-                A.add(5 + 2 * k, off.y);
+                A.fma(2 * k + 0, w0, n00);
+                A.fma(2 * k + 0, w1, n01);
+                A.fma(2 * k + 1, w0, n10);
+                A.fma(2 * k + 1, w1, n11);
+                A.fma(4 + 2 * k, w0, o0.x);
+                A.fma(4 + 2 * k, w1, o1.x);
+                A.fma(5 + 2 * k, w0, o0.y);
+                A.fma(5 + 2 * k, w1, o1.y);
                 const float2 wr0 = cscale(rv[2 * k], w0), wr1 = cscale(rv[2 * k + 1], w1);
-                const float2 j0 = cfma_conj(x01, wr1, cfma_conj(x00, wr0, make_float2(0.f, 0.f)));
-                const float2 j1 = cfma_conj(x11, wr1, cfma_conj(x10, wr0, make_float2(0.f, 0.f)));
-                A.add(8 + 4 * k + 0, j0.x);
-                A.add(8 + 4 * k + 1, j0.y);
-                A.add(8 + 4 * k + 2, j1.x);
-                A.add(8 + 4 * k + 3, j1.y);
+                A.cfma(8 + 4 * k, x00, wr0);
+                A.cfma(8 + 4 * k, x01, wr1);
+                A.cfma(10 + 4 * k, x10, wr0);
+                A.cfma(10 + 4 * k, x11, wr1);
             }
         }
     } else {
@@ -279,24 +321,13 @@ __device__ __forceinline__ void flush_side(Acc<KR, KAHAN> &A, int key, int ant, 
 }
 
 // ---------------------------------------------------------------------------
-// the accumulate kernel
+// one sample: chain factors, residual and both antennas' contributions
 // ---------------------------------------------------------------------------
 
-struct AccArgs {
-    Data D;
-    Chain C;
-    DevTerm tn;              // copy of C.t[C.n] (avoids dynamic indexing of kernel parameters)
-    double *acc;             // [n_bins][n_ant][KG]
-    const uint8_t *active;   // [n_bins]
-    const int *n_active;     // nonzero: some interval of the solved term is still iterating
-    int order;               // 0 row tiles, 1 strip tiles
-    int n_chunks;            // ceil(n_chan / 32)
-};
-
-// Chain factors of antenna a at one sample around the solved term n
-// (Eq. jonesfactor): L = prod_{j<n} G_j, G = G_n, R = prod_{j>n} G_j.
+// Chain factors of antenna a around the solved term n (Eq. jonesfactor) from
+// per-term interval indices (tint: per row, fint: per channel).
 template <int LK, int RK>
-__device__ __forceinline__ void chain_factors(const Chain &C, const int *tint, int c, int a, J2 &L, J2 &G, J2 &R)
+__device__ __forceinline__ void chain_at(const Chain &C, const int *tint, const int *fint, int a, J2 &L, J2 &G, J2 &R)
 {
     bool hl = false, hr = false;
     L = j_identity();
@@ -304,9 +335,7 @@ __device__ __forceinline__ void chain_factors(const Chain &C, const int *tint, i
 #pragma unroll
     for (int j = 0; j < MAXT; ++j) {
         if (j >= C.n_terms) break;
-        const DevTerm &T = C.t[j];
-        const int fint = __ldg(T.f_map + c);
-        const J2 J = fetch_jones(T, C.n_ant, tint[j], fint, a);
+        const J2 J = fetch_jones(C.t[j], C.n_ant, tint[j], fint[j], a);
         if (j < C.n) {
             if constexpr (LK != KIND_NONE) { L = hl ? j_mul(L, J) : J; hl = true; }
         } else if (j == C.n) {
@@ -317,7 +346,105 @@ __device__ __forceinline__ void chain_factors(const Chain &C, const int *tint, i
     }
 }
 
-template <int TS, int LK, int RK, bool M16>
+// Interval indices of one sample: for the solved term n and the other term of a
+// two-term chain, or for every term of a longer chain.
+struct SampleIdx {
+    int tn, fn;            // solved term
+    int to, fo;            // other term (two-term chains)
+    int t[MAXT], f[MAXT];  // every term (longer chains)
+};
+
+// Chain factors of antenna a around the solved term (Eq. jonesfactor).  SIMPLE:
+// the chain has at most one other term, on the left (LK) or on the right (RK).
+template <int GK, int LK, int RK, bool SIMPLE>
+__device__ __forceinline__ void factors(const AccArgs &a, const SampleIdx &ix, int ant, J2 &L, J2 &G, J2 &R)
+{
+    if constexpr (SIMPLE) {
+        G = fetch_k<GK>(a.tn, a.C.n_ant, ix.tn, ix.fn, ant);
+        if constexpr (LK != KIND_NONE) L = fetch_k<LK>(a.to, a.C.n_ant, ix.to, ix.fo, ant);
+        if constexpr (RK != KIND_NONE) R = fetch_k<RK>(a.to, a.C.n_ant, ix.to, ix.fo, ant);
+    } else {
+        chain_at<LK, RK>(a.C, ix.t, ix.f, ant, L, G, R);
+    }
+}
+
+// Contribution of one unflagged sample of baseline (p, q) to the p and q blocks.
+// With Z = R_p M R_q^H:  X = Z G_q^H L_q^H = R_p M C_q^H,  V = L_p G_p X  (Eq. chain_trick),
+// and for the conjugate baseline Y = R_q M^H C_p^H = (L_p G_p Z)^H.
+template <int TS, int LK, int RK, bool SIMPLE, bool KAHAN>
+__device__ __forceinline__ void sample_contrib(const AccArgs &a, const SampleIdx &ix, int p, int q, const J2 &Dm,
+                                               const J2 &M, float4 w,
+                                               Acc<AccLayout<TS, LK != KIND_NONE>::KR, KAHAN> &Ap,
+                                               Acc<AccLayout<TS, LK != KIND_NONE>::KR, KAHAN> &Aq)
+{
+    constexpr bool HAS_L = LK != KIND_NONE;
+    constexpr int GK = TS == TS_FULL ? KIND_FULL : KIND_DIAG;
+    J2 Lp, Gp, Rp, Lq, Gq, Rq;
+    factors<GK, LK, RK, SIMPLE>(a, ix, p, Lp, Gp, Rp);
+    factors<GK, LK, RK, SIMPLE>(a, ix, q, Lq, Gq, Rq);
+    J2 X, Y, V;
+    if constexpr (RK == KIND_NONE) {
+        const J2 Cp = HAS_L ? rmulk<GK>(Lp, Gp) : Gp;
+        const J2 Cq = HAS_L ? rmulk<GK>(Lq, Gq) : Gq;
+        constexpr int CK = HAS_L ? KIND_FULL : GK;
+        const J2 A = lmulk<CK>(Cp, M);                 // C_p M
+        X = rmulk_h<CK>(M, Cq);                        // M C_q^H
+        V = rmulk_h<CK>(A, Cq);                        // C_p M C_q^H
+        Y = j_herm(A);                                 // M^H C_p^H
+    } else {
+        J2 Z;
+        if constexpr (RK == KIND_DIAG) Z = j_muld(j_dmul(Rp.a, Rp.d, M), cconj(Rq.a), cconj(Rq.d));
+        else Z = j_mul_h(j_mul(Rp, M), Rq);
+        X = rmulk_h<LK>(rmulk_h<GK>(Z, Gq), Lq);
+        const J2 W = lmulk<LK>(Lp, lmulk<GK>(Gp, Z));
+        Y = j_herm(W);
+        V = lmulk<LK>(Lp, lmulk<GK>(Gp, X));
+    }
+    J2 r;
+    r.a = csub(Dm.a, V.a); r.b = csub(Dm.b, V.b); r.c = csub(Dm.c, V.c); r.d = csub(Dm.d, V.d);
+    accumulate_side<TS, HAS_L, KAHAN>(Ap, Lp, X, w, r);
+    accumulate_side<TS, HAS_L, KAHAN>(Aq, Lq, Y, make_float4(w.x, w.z, w.y, w.w), j_herm(r));
+}
+
+// Interval indices of a sample at data time `time` and channel c.
+template <bool SIMPLE>
+__device__ __forceinline__ void sample_index(const AccArgs &a, int time, int c, bool in_range, SampleIdx &ix)
+{
+    ix.tn = __ldg(a.tn.t_map + time);
+    ix.fn = in_range ? __ldg(a.tn.f_map + c) : 0;
+    if constexpr (SIMPLE) {
+        if (a.C.n_terms > 1) {
+            ix.to = __ldg(a.to.t_map + time);
+            ix.fo = in_range ? __ldg(a.to.f_map + c) : 0;
+        } else {
+            ix.to = 0;
+            ix.fo = 0;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < MAXT; ++j) {
+            ix.t[j] = j < a.C.n_terms ? __ldg(a.C.t[j].t_map + time) : 0;
+            ix.f[j] = (j < a.C.n_terms && in_range) ? __ldg(a.C.t[j].f_map + c) : 0;
+        }
+    }
+}
+
+__device__ __forceinline__ J2 load_model16(uint4 h, float sc)
+{
+    J2 M;
+    M.a = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.x)), sc);
+    M.b = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.y)), sc);
+    M.c = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.z)), sc);
+    M.d = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.w)), sc);
+    return M;
+}
+
+// ---------------------------------------------------------------------------
+// the accumulate kernel
+// ---------------------------------------------------------------------------
+
+
+template <int TS, int LK, int RK, bool SIMPLE, bool M16>
 __global__ void __launch_bounds__(256) acc_kernel(const AccArgs a)
 {
     if (__ldg(a.n_active) == 0) return;
@@ -325,7 +452,6 @@ __global__ void __launch_bounds__(256) acc_kernel(const AccArgs a)
     constexpr bool KAHAN = M16;
     using Lay = AccLayout<TS, HAS_L>;
     constexpr int KR = Lay::KR, KG = Lay::KG;
-    constexpr int GK = TS == TS_FULL ? KIND_FULL : KIND_DIAG;
     const Data &D = a.D;
     const Chain &C = a.C;
     const DevTerm &Tn = a.tn;
@@ -358,13 +484,11 @@ __global__ void __launch_bounds__(256) acc_kernel(const AccArgs a)
             q = meta.y;
             if (p == q) break;                       // autocorrelation: whole unit skipped
             const bool in_range = c < D.n_chan;
-            int tint[MAXT];
-#pragma unroll
-            for (int j = 0; j < MAXT; ++j) tint[j] = j < C.n_terms ? __ldg(C.t[j].t_map + meta.z) : 0;
-            const int key = in_range ? __ldg(Tn.t_map + meta.z) * Tn.n_fint + __ldg(Tn.f_map + c) : -1;
+            SampleIdx ix;
+            sample_index<SIMPLE>(a, meta.z, c, in_range, ix);
+            const int key = in_range ? ix.tn * Tn.n_fint + ix.fn : -1;
             // flush when any lane's bin changes
-            const bool change = cur_key >= 0 && key != cur_key;
-            if (__any_sync(0xffffffffu, change)) {
+            if (__any_sync(0xffffffffu, cur_key >= 0 && key != cur_key)) {
                 const unsigned m = __match_any_sync(0xffffffffu, cur_key);
                 const unsigned seg_end = 32 - __clz(m);
                 const bool head = lane == __ffs(m) - 1;
@@ -378,48 +502,21 @@ __global__ void __launch_bounds__(256) acc_kernel(const AccArgs a)
             if (ok && D.flag) ok = __ldg(D.flag + s) == 0;
             if (!__any_sync(0xffffffffu, ok)) continue;
             if (!ok) continue;
-            // ---- loads (128-bit, contiguous across the warp) ----
             const J2 Dm = j_from(__ldg(D.vis + 2 * s), __ldg(D.vis + 2 * s + 1));
             J2 M;
-            if constexpr (M16) {
-                const uint4 h = __ldg(D.model16 + s);
-                const float sc = __ldg(D.bl_scale + meta.w);
-                M.a = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.x)), sc);
-                M.b = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.y)), sc);
-                M.c = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.z)), sc);
-                M.d = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.w)), sc);
-            } else {
-                M = j_from(__ldg(D.model + 2 * s), __ldg(D.model + 2 * s + 1));
-            }
+            if constexpr (M16) M = load_model16(__ldg(D.model16 + s), __ldg(D.bl_scale + meta.w));
+            else M = j_from(__ldg(D.model + 2 * s), __ldg(D.model + 2 * s + 1));
             const float4 w = __ldg(D.weight + s);
-            // ---- chain factors for both antennas ----
-            J2 Lp, Gp, Rp, Lq, Gq, Rq;
-            chain_factors<LK, RK>(C, tint, c, p, Lp, Gp, Rp);
-            chain_factors<LK, RK>(C, tint, c, q, Lq, Gq, Rq);
-            // C_a = L_a G_a R_a
-            const J2 Cp = lmulk<LK>(Lp, rmulk<RK>(Gp, Rp));
-            const J2 Cq = lmulk<LK>(Lq, rmulk<RK>(Gq, Rq));
-            // p side: X = R_p M C_q^H, V = L_p G_p X, r = D - V
-            const J2 X = j_mul_h(lmulk<RK>(Rp, M), Cq);
-            const J2 V = lmulk<LK>(Lp, lmulk<GK>(Gp, X));
-            J2 r;
-            r.a = csub(Dm.a, V.a); r.b = csub(Dm.b, V.b); r.c = csub(Dm.c, V.c); r.d = csub(Dm.d, V.d);
-            accumulate_side<TS, HAS_L, KAHAN>(Ap, Lp, X, w, r);
-            // q side through the conjugate baseline: Y = R_q M^H C_p^H, r' = r^H, w' = P w
-            const J2 Y = j_mul_h(lmulk<RK>(Rq, j_herm(M)), Cp);
-            const J2 rh = j_herm(r);
-            accumulate_side<TS, HAS_L, KAHAN>(Aq, Lq, Y, make_float4(w.x, w.z, w.y, w.w), rh);
+            sample_contrib<TS, LK, RK, SIMPLE, KAHAN>(a, ix, p, q, Dm, M, w, Ap, Aq);
         }
         // end of the unit: flush what is left
-        {
+        if (__any_sync(0xffffffffu, cur_key >= 0)) {
             const unsigned m = __match_any_sync(0xffffffffu, cur_key);
             const unsigned seg_end = 32 - __clz(m);
             const bool head = lane == __ffs(m) - 1;
             const bool live = cur_key >= 0 && __ldg(a.active + cur_key);
-            if (__any_sync(0xffffffffu, cur_key >= 0)) {
-                flush_side<KR, KG, KAHAN, Lay>(Ap, cur_key, p, lane, seg_end, head, live, a.acc, C.n_ant);
-                flush_side<KR, KG, KAHAN, Lay>(Aq, cur_key, q, lane, seg_end, head, live, a.acc, C.n_ant);
-            }
+            flush_side<KR, KG, KAHAN, Lay>(Ap, cur_key, p, lane, seg_end, head, live, a.acc, C.n_ant);
+            flush_side<KR, KG, KAHAN, Lay>(Aq, cur_key, q, lane, seg_end, head, live, a.acc, C.n_ant);
         }
     }
 }
@@ -736,6 +833,246 @@ static __global__ void __launch_bounds__(256) count_kernel(const CountArgs a)
                 if (mu) atomicAdd((unsigned long long *)(a.nunflag + key), (unsigned long long)__popc(mu));
             }
         }
+    }
+}
+
+} // namespace qc
+
+namespace qc {
+
+// ---------------------------------------------------------------------------
+// pipelined accumulate kernel: bulk-copy producer warp + consumer warps
+// ---------------------------------------------------------------------------
+//
+// The CTA owns groups of NW work units (a unit is one row for row tiles, or
+// one baseline strip x 32 channels for strip tiles); consumer warp w always
+// takes slot w of the group, so its register partial sums follow one row or
+// one strip.  For every step the producer warp copies, per slot, the row
+// segment [c0, c0 + 32) of d, m and w (contiguous in [row][chan][corr]) into
+// one stage of an NS-deep shared-memory ring with cp.async.bulk, completing
+// the transaction count of that stage's "full" mbarrier; consumers wait on
+// it, compute from shared memory and release the stage through its "empty"
+// mbarrier.  Row segments that are fully flagged, autocorrelations, or whose
+// intervals have all converged are not copied at all.  Every wait is bounded
+// in wall time; a timeout sets *err and the CTA leaves after waiting (again
+// bounded) for its copies in flight.
+
+struct PipeArgs {
+    AccArgs a;
+    const uint8_t *row_live;      // [n_row] 1: cross-correlation row with an unflagged sample
+    const uint8_t *chunk_active;  // [n_tint of term n][n_chunks]: a 32-channel chunk has an active bin
+    int *err;                     // set to 1 when a bounded wait gives up
+};
+
+template <int NW, int NS, int MB> struct PipeLayout {
+    static constexpr int SLOT_D = 32 * 32, SLOT_M = 32 * MB, SLOT_W = 32 * 16;
+    static constexpr int STAGE = NW * (SLOT_D + SLOT_M + SLOT_W);
+    static constexpr int DESC_OFF = NS * STAGE;
+    static constexpr int BAR_OFF = DESC_OFF + NS * NW * 16;
+    static constexpr int BYTES = BAR_OFF + 2 * NS * 8;
+};
+
+constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;   // 2 s
+
+// slot layout of one unit for the producer and the consumers (identical on both sides)
+__device__ __forceinline__ void unit_info(const AccArgs &a, long u, long n_units, int &row0, int &c0, int &beg, int &len)
+{
+    row0 = 0; c0 = 0; beg = 0; len = 0;
+    if (u >= n_units) return;
+    if (a.order == 0) { row0 = (int)u; len = a.n_chunks; }
+    else {
+        const int s = (int)(u / a.n_chunks);
+        c0 = (int)(u % a.n_chunks) * 32;
+        beg = __ldg(a.D.strip_off + s);
+        len = __ldg(a.D.strip_off + s + 1) - beg;
+    }
+}
+
+template <int TS, int LK, int RK, bool SIMPLE, bool M16, int NW, int NS>
+__global__ void __launch_bounds__((NW + 1) * 32, 1) acc_pipe_kernel(const PipeArgs P)
+{
+    constexpr bool HAS_L = LK != KIND_NONE;
+    constexpr bool KAHAN = M16;
+    using Lay = AccLayout<TS, HAS_L>;
+    constexpr int KR = Lay::KR, KG = Lay::KG;
+    constexpr int MB = M16 ? 16 : 32;
+    using PL = PipeLayout<NW, NS, MB>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    int4 *desc = reinterpret_cast<int4 *>(smem + PL::DESC_OFF);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + PL::BAR_OFF);
+    uint64_t *empty = full + NS;
+    const AccArgs &a = P.a;
+    const Data &D = a.D;
+    const Chain &C = a.C;
+    const DevTerm &Tn = a.tn;
+
+    if (__ldg(a.n_active) == 0) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, NW);
+        }
+        fence_barrier_init();
+    }
+    __syncthreads();
+    const long n_units = a.order == 0 ? (long)D.n_row : (long)D.n_strips * a.n_chunks;
+    const long n_groups = (n_units + NW - 1) / NW;
+
+    if (warp == NW) {
+        // ------------------------------ producer ------------------------------
+        uint32_t it = 0;
+        bool ok = true;
+        for (long g = blockIdx.x; g < n_groups && ok; g += gridDim.x) {
+            int row0, c0, beg, len;
+            unit_info(a, g * NW + lane, n_units, row0, c0, beg, len);
+            if (lane >= NW) len = 0;
+            const int steps = __reduce_max_sync(0xffffffffu, len);
+            for (int i = 0; i < steps; ++i, ++it) {
+                const int stage = it % NS;
+                const uint32_t par = (it / NS) & 1u;
+                if (!mbar_wait_bounded(empty + stage, par ^ 1u, WAIT_LIMIT_NS)) { ok = false; break; }
+                int4 d = make_int4(-1, 0, 0, 0);
+                uint32_t bytes = 0;
+                if (lane < NW && i < len) {
+                    const int row = a.order == 0 ? row0 : __ldg(D.strip_rows + beg + i);
+                    const int cc = a.order == 0 ? i * 32 : c0;
+                    const int nch = min(32, D.n_chan - cc);
+                    bool live = __ldg(P.row_live + row) != 0;
+                    if (live) {
+                        const int t = __ldg(D.rows + row).z;
+                        live = __ldg(P.chunk_active + (size_t)__ldg(Tn.t_map + t) * a.n_chunks + cc / 32) != 0;
+                    }
+                    d = make_int4(row, cc, nch, live ? 1 : 0);
+                    if (live) bytes = (uint32_t)nch * (32u + MB + 16u);
+                }
+                if (lane < NW) desc[stage * NW + lane] = d;
+                const uint32_t total = __reduce_add_sync(0xffffffffu, bytes);
+                __syncwarp();
+                if (lane == 0) mbar_arrive_expect_tx(full + stage, total);
+                __syncwarp();
+                if (bytes) {
+                    unsigned char *sb = smem + (size_t)stage * PL::STAGE;
+                    const size_t s0 = (size_t)d.x * D.n_chan + d.y;
+                    bulk_copy_g2s(sb + lane * PL::SLOT_D, D.vis + 2 * s0, d.z * 32u, full + stage);
+                    if constexpr (M16)
+                        bulk_copy_g2s(sb + NW * PL::SLOT_D + lane * PL::SLOT_M, D.model16 + s0, d.z * 16u, full + stage);
+                    else
+                        bulk_copy_g2s(sb + NW * PL::SLOT_D + lane * PL::SLOT_M, D.model + 2 * s0, d.z * 32u, full + stage);
+                    bulk_copy_g2s(sb + NW * (PL::SLOT_D + PL::SLOT_M) + lane * PL::SLOT_W, D.weight + s0, d.z * 16u,
+                                  full + stage);
+                }
+            }
+        }
+        if (!ok) {
+            if (lane == 0) atomicExch(P.err, 1);
+            // let copies already issued land before the CTA leaves (bounded)
+            for (uint32_t k = (it >= NS ? it - NS : 0); k < it; ++k)
+                mbar_wait_bounded(full + (k % NS), (k / NS) & 1u, WAIT_LIMIT_NS);
+        }
+        return;
+    }
+
+    // ------------------------------ consumers ------------------------------
+    SampleIdx ix;
+    Acc<KR, KAHAN> Ap, Aq;
+    Ap.zero();
+    Aq.zero();
+    uint32_t it = 0;
+    for (long g = blockIdx.x; g < n_groups; g += gridDim.x) {
+        int row0, c0, beg, len;
+        unit_info(a, g * NW + lane, n_units, row0, c0, beg, len);
+        if (lane >= NW) len = 0;
+        const int steps = __reduce_max_sync(0xffffffffu, len);
+        int cur_key = -1, p = 0, q = 0;
+        for (int i = 0; i < steps; ++i, ++it) {
+            const int stage = it % NS;
+            const uint32_t par = (it / NS) & 1u;
+            if (!mbar_wait_bounded(full + stage, par, WAIT_LIMIT_NS)) {
+                if (lane == 0) atomicExch(P.err, 1);
+                return;
+            }
+            const int4 d = desc[stage * NW + warp];
+            if (d.w) {
+                const int4 meta = __ldg(D.rows + d.x);
+                p = meta.x;
+                q = meta.y;
+                const int c = d.y + lane;
+                const bool in_range = lane < d.z;
+                sample_index<SIMPLE>(a, meta.z, c, in_range, ix);
+                const int key = in_range ? ix.tn * Tn.n_fint + ix.fn : -1;
+                if (__any_sync(0xffffffffu, cur_key >= 0 && key != cur_key)) {
+                    const unsigned m = __match_any_sync(0xffffffffu, cur_key);
+                    const unsigned seg_end = 32 - __clz(m);
+                    const bool head = lane == __ffs(m) - 1;
+                    const bool live = cur_key >= 0 && __ldg(a.active + cur_key);
+                    flush_side<KR, KG, KAHAN, Lay>(Ap, cur_key, p, lane, seg_end, head, live, a.acc, C.n_ant);
+                    flush_side<KR, KG, KAHAN, Lay>(Aq, cur_key, q, lane, seg_end, head, live, a.acc, C.n_ant);
+                }
+                cur_key = key;
+                bool ok = in_range && __ldg(a.active + key);
+                if (ok && D.flag) ok = __ldg(D.flag + (size_t)d.x * D.n_chan + c) == 0;
+                if (ok) {
+                    const unsigned char *sb = smem + (size_t)stage * PL::STAGE;
+                    const float4 *sd = reinterpret_cast<const float4 *>(sb + warp * PL::SLOT_D) + 2 * lane;
+                    const J2 Dm = j_from(sd[0], sd[1]);
+                    J2 M;
+                    if constexpr (M16) {
+                        const uint4 h = reinterpret_cast<const uint4 *>(sb + NW * PL::SLOT_D + warp * PL::SLOT_M)[lane];
+                        M = load_model16(h, __ldg(D.bl_scale + meta.w));
+                    } else {
+                        const float4 *sm = reinterpret_cast<const float4 *>(sb + NW * PL::SLOT_D + warp * PL::SLOT_M) + 2 * lane;
+                        M = j_from(sm[0], sm[1]);
+                    }
+                    const float4 w = reinterpret_cast<const float4 *>(sb + NW * (PL::SLOT_D + PL::SLOT_M) + warp * PL::SLOT_W)[lane];
+                    sample_contrib<TS, LK, RK, SIMPLE, KAHAN>(a, ix, p, q, Dm, M, w, Ap, Aq);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(empty + stage);
+        }
+        // end of the unit
+        if (__any_sync(0xffffffffu, cur_key >= 0)) {
+            const unsigned m = __match_any_sync(0xffffffffu, cur_key);
+            const unsigned seg_end = 32 - __clz(m);
+            const bool head = lane == __ffs(m) - 1;
+            const bool live = cur_key >= 0 && __ldg(a.active + cur_key);
+            flush_side<KR, KG, KAHAN, Lay>(Ap, cur_key, p, lane, seg_end, head, live, a.acc, C.n_ant);
+            flush_side<KR, KG, KAHAN, Lay>(Aq, cur_key, q, lane, seg_end, head, live, a.acc, C.n_ant);
+        }
+    }
+}
+
+// chunk_active[tint][chunk] = some interval bin of the solved term touched by this
+// (time interval, 32-channel chunk) is still active
+static __global__ void chunk_active_kernel(const DevTerm tn, int n_chan, int n_chunks, const uint8_t *active,
+                                           const int *n_active, uint8_t *out)
+{
+    if (*n_active == 0) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= tn.n_tint * n_chunks) return;
+    const int tint = i / n_chunks, ch = i % n_chunks;
+    const int f0 = tn.f_map[ch * 32], f1 = tn.f_map[min(n_chan, ch * 32 + 32) - 1];
+    uint8_t any = 0;
+    for (int f = f0; f <= f1 && !any; ++f) any = active[tint * tn.n_fint + f];
+    out[i] = any;
+}
+
+// row_live[row] = cross-correlation row with at least one unflagged channel
+static __global__ void row_live_kernel(const Data D, uint8_t *row_live)
+{
+    const int lane = threadIdx.x & 31;
+    const long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long n_warps = ((long)gridDim.x * blockDim.x) >> 5;
+    for (long row = warp; row < D.n_row; row += n_warps) {
+        const int4 meta = __ldg(D.rows + row);
+        bool any = false;
+        if (meta.x != meta.y) {
+            for (int c = lane; c < D.n_chan && !any; c += 32)
+                any = !D.flag || __ldg(D.flag + (size_t)row * D.n_chan + c) == 0;
+        }
+        any = __any_sync(0xffffffffu, any);
+        if (lane == 0) row_live[row] = any ? 1 : 0;
     }
 }
 

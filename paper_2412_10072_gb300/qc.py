@@ -53,7 +53,8 @@ ALLREDUCE_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_
 class _Opts(C.Structure):
     _fields_ = [("n_epochs", C.c_int32), ("damping_mode", C.c_int32), ("damping", C.c_double),
                 ("stream", C.c_void_p), ("use_graph", C.c_int32), ("want_chi2", C.c_int32), ("order", C.c_int32),
-                ("block_threads", C.c_int32), ("ctas_per_sm", C.c_int32), ("allreduce", ALLREDUCE_FN),
+                ("block_threads", C.c_int32), ("ctas_per_sm", C.c_int32), ("kernel", C.c_int32),
+                ("allreduce", ALLREDUCE_FN),
                 ("allreduce_user", C.c_void_p)]
 
 
@@ -110,7 +111,15 @@ def _addr(a) -> Optional[int]:
     return int(a.ctypes.data)
 
 
+def _is_host_tensor(a) -> bool:
+    return hasattr(a, "data_ptr") and not getattr(a, "is_cuda", False)
+
+
 def _host(a, dtype):
+    if _is_host_tensor(a):           # e.g. a pinned CPU tensor: passed without a copy
+        if not a.is_contiguous() or a.element_size() != np.dtype(dtype).itemsize:
+            raise ValueError("host tensors must be contiguous and of the documented dtype")
+        return a
     return np.ascontiguousarray(a, dtype=dtype)
 
 
@@ -118,7 +127,7 @@ def _complex64(a):
     """Host complex data as interleaved complex64 (upcast/downcast allowed)."""
     if _is_dev(a):
         return a
-    return np.ascontiguousarray(a, dtype=np.complex64)
+    return _host(a, np.complex64)
 
 
 class Term:
@@ -217,12 +226,13 @@ class Solver:
 
     def solve(self, terms: List[Term], n_epochs: int = 1, damping_mode: int = QC_DAMP_ALTERNATE,
               damping: float = 1.0, use_graph: bool = True, want_chi2: bool = False, order: int = -1,
-              block_threads: int = 0, ctas_per_sm: int = 0, stream=None, allreduce=None) -> Stats:
+              block_threads: int = 0, ctas_per_sm: int = 0, stream=None, allreduce=None,
+              kernel: int = 0) -> Stats:
         arr = _terms_array(terms)
         cb = ALLREDUCE_FN(allreduce) if allreduce is not None else ALLREDUCE_FN()
         st = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
         o = _Opts(n_epochs, damping_mode, damping, st or None, int(use_graph), int(want_chi2), order,
-                  block_threads, ctas_per_sm, cb, None)
+                  block_threads, ctas_per_sm, kernel, cb, None)
         s = Stats()
         rc = self._lib.qc_solve(self._h, arr, len(terms), C.byref(o), C.byref(s))
         if rc != QC_OK:

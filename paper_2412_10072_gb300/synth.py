@@ -307,45 +307,51 @@ def make_observation_device(su: Setup, noise: float, noise_seed: int, device, ro
     import torch
     n_row, n_chan = su.ant1.size, su.freqs.size
     dev = torch.device(device)
-    f64, c128 = torch.float64, torch.complex128
-    data = torch.empty((n_row, n_chan, 4), dtype=torch.complex64, device=dev)
-    model = torch.empty((n_row, n_chan, 4), dtype=torch.complex64, device=dev)
+    f64, c64 = torch.float64, torch.complex64
+    data = torch.empty((n_row, n_chan, 4), dtype=c64, device=dev)
+    model = torch.empty((n_row, n_chan, 4), dtype=c64, device=dev)
     weight = torch.ones((n_row, n_chan, 4), dtype=torch.float32, device=dev)
     flag = torch.from_numpy(su.flag_rows.astype(np.uint8)).to(dev)[:, None].expand(n_row, n_chan).contiguous()
     gen = torch.Generator(device=dev)
     gen.manual_seed(int(noise_seed))
-    nu = torch.from_numpy(su.freqs).to(dev, f64)
-    flux = torch.from_numpy(su.sky.flux).to(dev, f64)
+    # -2 pi nu / c in FP64; the phase is range-reduced in FP64 and its exponential taken in FP32
+    k_nu = torch.from_numpy(-2.0 * np.pi * su.freqs / C_LIGHT).to(dev, f64)
+    flux = torch.from_numpy(su.sky.flux).to(dev, torch.float32).to(c64)
     lmn = torch.from_numpy(np.stack([su.sky.l, su.sky.m, su.sky.n - 1.0])).to(dev, f64)     # [3, src]
-    jones = [torch.from_numpy(t.truth_jones()).to(dev, c128) for t in su.terms]
+    jones = [torch.from_numpy(t.truth_jones()).to(dev, c64) for t in su.terms]
     tmaps = [torch.from_numpy(t.t_map.astype(np.int64)).to(dev) for t in su.terms]
     fmaps = [torch.from_numpy(t.f_map.astype(np.int64)).to(dev) for t in su.terms]
     chan = torch.arange(n_chan, device=dev)
-    eye = torch.eye(2, dtype=c128, device=dev)
+    two_pi = 2.0 * np.pi
     for r0 in range(0, n_row, rows_per_chunk):
         r1 = min(n_row, r0 + rows_per_chunk)
         uvw = torch.from_numpy(su.uvw[r0:r1]).to(dev, f64)
         ph = uvw @ lmn                                                         # [R, src] metres
-        ang = (-2.0 * np.pi / C_LIGHT) * ph[:, :, None] * nu[None, None, :]   # [R, src, C]
-        scal = torch.einsum("k,rkc->rc", flux.to(c128), torch.polar(torch.ones_like(ang), ang))
-        M = scal[:, :, None, None] * eye                                        # [R, C, 2, 2]
+        ang = ph[:, :, None] * k_nu[None, None, :]                             # [R, src, C] radians
+        ang = (ang - two_pi * torch.round(ang / two_pi)).to(torch.float32)
+        scal = torch.einsum("k,rkc->rc", flux, torch.polar(torch.ones_like(ang), ang))   # [R, C]
         t = torch.from_numpy(su.time_idx[r0:r1].astype(np.int64)).to(dev)
         a1 = torch.from_numpy(su.ant1[r0:r1].astype(np.int64)).to(dev)
         a2 = torch.from_numpy(su.ant2[r0:r1].astype(np.int64)).to(dev)
-        Cp = eye.expand(r1 - r0, n_chan, 2, 2)
-        Cq = Cp
+        Cp = None
+        Cq = None
         for J, tm, fm in zip(jones, tmaps, fmaps):
             it = tm[t][:, None]
             jf = fm[chan][None, :]
-            Cp = Cp @ J[it, jf, a1[:, None]].reshape(r1 - r0, n_chan, 2, 2)
-            Cq = Cq @ J[it, jf, a2[:, None]].reshape(r1 - r0, n_chan, 2, 2)
-        V = Cp @ M @ Cq.conj().transpose(-1, -2)
+            Jp = J[it, jf, a1[:, None]].reshape(r1 - r0, n_chan, 2, 2)
+            Jq = J[it, jf, a2[:, None]].reshape(r1 - r0, n_chan, 2, 2)
+            Cp = Jp if Cp is None else Cp @ Jp
+            Cq = Jq if Cq is None else Cq @ Jq
+        V = scal[:, :, None, None] * (Cp @ Cq.conj().transpose(-1, -2))       # M = scal * I
         V = V.reshape(r1 - r0, n_chan, 4)
         if noise > 0:
             nz = torch.randn((r1 - r0, n_chan, 4, 2), dtype=torch.float32, device=dev, generator=gen)
-            V = V + noise * torch.view_as_complex(nz).to(c128)
-        data[r0:r1] = V.to(torch.complex64)
-        model[r0:r1] = M.reshape(r1 - r0, n_chan, 4).to(torch.complex64)
+            V = V + noise * torch.view_as_complex(nz)
+        data[r0:r1] = V
+        m = model[r0:r1]
+        m.zero_()
+        m[:, :, 0] = scal
+        m[:, :, 3] = scal
     return dict(data=data, model=model, weight=weight, flag=flag, ant1=su.ant1, ant2=su.ant2,
                 time_idx=su.time_idx, n_ant=su.n_ant, n_time=su.n_time, n_chan=n_chan, terms=su.terms)
 

@@ -74,12 +74,13 @@ def test_plain_small_workload_matches_oracle():
     assert st.vis_iters > 0 and st.acc_launches >= 1
 
 
+@pytest.mark.parametrize("kernel", [1, 2])
 @pytest.mark.parametrize("order", [0, 1])
 @pytest.mark.parametrize("use_graph", [True, False])
-def test_plain_small_tile_orders_and_graph_agree(order, use_graph):
+def test_plain_small_tile_orders_and_graph_agree(order, use_graph, kernel):
     obs = synth.plain_small(seed=1, noise=0.01)
     ot, _, ochi2 = run_oracle(obs)
-    gt, st, gchi2 = run_gpu(obs, order=order, use_graph=use_graph)
+    gt, st, gchi2 = run_gpu(obs, order=order, use_graph=use_graph, kernel=kernel)
     assert rel_err(reference_diag(jones_of(gt[0])), reference_diag(ot[0].params)) < GAIN_TOL
     assert abs(gchi2 - ochi2) <= CHI2_TOL * ochi2
 
@@ -141,7 +142,8 @@ CHAINS = [("diag",), ("full",), ("phase",), ("full", "diag"), ("diag", "full"), 
 
 @pytest.mark.parametrize("kinds", CHAINS)
 @pytest.mark.parametrize("order", [0, 1])
-def test_single_step_matches_oracle_for_every_chain_position(kinds, order):
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_single_step_matches_oracle_for_every_chain_position(kinds, order, kernel):
     obs = random_chain_obs(7, kinds)
     rng = np.random.default_rng(3)
     start = start_params(obs, rng)
@@ -155,7 +157,7 @@ def test_single_step_matches_oracle_for_every_chain_position(kinds, order):
         S = qc.Solver.from_obs(obs)
         gt = [qc.Term.from_spec(s, obs.n_ant, gains=p, solve=(i == n), max_iter=1, tol=0.0)
               for i, (s, p) in enumerate(zip(obs.terms, start32))]
-        S.solve(gt, damping_mode=0, damping=1.0, order=order)
+        S.solve(gt, damping_mode=0, damping=1.0, order=order, kernel=kernel)
         S.close()
         want = ot[n].params
         got = np.asarray(gt[n].gains, dtype=np.float64 if kinds[n] == "phase" else np.complex128)
@@ -190,10 +192,11 @@ def test_residual_matches_oracle_elementwise(kinds):
 # converged multi-term chains
 # ---------------------------------------------------------------------------
 
-def test_two_term_chain_matches_oracle():
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_two_term_chain_matches_oracle(kernel):
     obs = synth.plain_large(seed=3, n_ant=10, n_time=12, n_chan=40, noise=0.05, flag_row_frac=0.1, n_src=8)
     ot, _, ochi2 = run_oracle(obs, n_epochs=3)
-    gt, st, gchi2 = run_gpu(obs, n_epochs=3)
+    gt, st, gchi2 = run_gpu(obs, n_epochs=3, kernel=kernel)
     assert_chain_parity(obs, gt, ot)
     assert abs(gchi2 - ochi2) <= CHI2_TOL * ochi2
 

@@ -6,33 +6,38 @@
 namespace qc_inst {
 using namespace qc;
 
-constexpr int PIPE_NW = 15;   // consumer warps per CTA (16 warps with the producer)
-constexpr int PIPE_NS = 5;    // shared-memory ring stages
+constexpr int PIPE_NW = 10;   // warps per CTA of the pipelined kernel
+constexpr int PIPE_H = 2;     // row segments of 32 channels per warp step
+
+constexpr int ACC_DEPTH = 4;  // cp.async ring depth (segments) of the prefetching kernel
 
 template <int TS, int LK, int RK, bool SIMPLE, bool M16>
 cudaError_t launch_acc(int grid, int block, cudaStream_t st, const AccArgs &a)
 {
-    acc_kernel<TS, LK, RK, SIMPLE, M16><<<grid, block, 0, st>>>(a);
+    const int smem = (block / 32) * ACC_DEPTH * 32 * (M16 ? 4 : 5) * 16;
+    acc_kernel<TS, LK, RK, SIMPLE, M16, ACC_DEPTH><<<grid, block, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int TS, int LK, int RK, bool SIMPLE, bool M16>
-cudaError_t launch_pipe(int grid, cudaStream_t st, const PipeArgs &p)
+template <int TS, int LK, int RK, bool M16>
+cudaError_t launch_pipe(int grid, int smem_bytes, cudaStream_t st, const PipeArgs &p)
 {
-    constexpr int bytes = PipeLayout<PIPE_NW, PIPE_NS, M16 ? 16 : 32>::BYTES;
-    acc_pipe_kernel<TS, LK, RK, SIMPLE, M16, PIPE_NW, PIPE_NS><<<grid, (PIPE_NW + 1) * 32, bytes, st>>>(p);
+    acc_pipe_kernel<TS, LK, RK, M16, PIPE_NW, PIPE_H><<<grid, PIPE_NW * 32, smem_bytes, st>>>(p);
     return cudaGetLastError();
 }
 
 template <int TS, int LK, int RK, bool SIMPLE, bool M16> AccLaunch make()
 {
     AccLaunch l;
-    l.fn = (const void *)acc_kernel<TS, LK, RK, SIMPLE, M16>;
+    l.fn = (const void *)acc_kernel<TS, LK, RK, SIMPLE, M16, ACC_DEPTH>;
+    l.acc_smem_per_warp = ACC_DEPTH * 32 * (M16 ? 4 : 5) * 16;
     l.launch = launch_acc<TS, LK, RK, SIMPLE, M16>;
-    l.pipe_fn = (const void *)acc_pipe_kernel<TS, LK, RK, SIMPLE, M16, PIPE_NW, PIPE_NS>;
-    l.pipe_launch = launch_pipe<TS, LK, RK, SIMPLE, M16>;
-    l.pipe_smem = PipeLayout<PIPE_NW, PIPE_NS, M16 ? 16 : 32>::BYTES;
-    l.pipe_threads = (PIPE_NW + 1) * 32;
+    if constexpr (SIMPLE) {
+        l.pipe_fn = (const void *)acc_pipe_kernel<TS, LK, RK, M16, PIPE_NW, PIPE_H>;
+        l.pipe_launch = launch_pipe<TS, LK, RK, M16>;
+        l.pipe_nw = PIPE_NW;
+        l.pipe_h = PIPE_H;
+    }
     return l;
 }
 

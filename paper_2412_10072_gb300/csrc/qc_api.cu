@@ -229,6 +229,7 @@ extern "C" int qc_create(const qc_problem *p, qc_ctx **out)
     {
         cudaError_t e = cudaGetDevice(&c->dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) { g_create_error = std::string("CUDA init: ") + cudaGetErrorString(e); return QC_ECUDA; }
     }
@@ -674,12 +675,14 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
     const int lk = kind_of_range(terms, 0, n);
     const int rk = kind_of_range(terms, n + 1, n_terms);
     const int order = pick_order(t, o);
-    const int block = (o->block_threads >= 64 && o->block_threads <= 1024 && o->block_threads % 32 == 0)
+    // the prefetching kernel is compiled for at most 256 threads per CTA
+    const int block = (o->block_threads >= 32 && o->block_threads <= 256 && o->block_threads % 32 == 0)
                           ? o->block_threads : 256;
     AccArgs aa;
     aa.D = data_desc();
     aa.C = chain;
     aa.tn = chain.t[n];
+    aa.row_live = d_row_live;
     aa.to = n_terms == 2 ? chain.t[1 - n] : chain.t[n];
     aa.acc = (double *)B.acc.ptr;
     aa.active = (const uint8_t *)B.active.ptr;
@@ -690,19 +693,97 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
     const bool simple = n_terms <= 2;
     AccLaunch L = acc_launcher(ts, simple, lk, rk, m16);
     if (!L.fn) return fail(QC_EUNSUPPORTED, "no accumulate kernel for this chain");
-    const bool pipelined = o->kernel != 2;
+    // pipelined kernel: shared-memory layout of the per-warp rings for this chain
+    PipeArgs pa;
+    memset(&pa, 0, sizeof pa);
+    int pipe_smem = 0;
+    // auto: the bulk-copy pipeline for baseline-strip tiles, the prefetching kernel for row tiles
+    bool pipelined = L.pipe_fn != nullptr && (o->kernel == 1 || (o->kernel == 0 && order == 1));
+    const bool has_o = n_terms == 2;
+    if (pipelined) {
+        const int NW = L.pipe_nw;
+        const int n_chunks = (n_chan + 31) / 32;
+        std::vector<int4> ci(n_chunks);
+        int capn = 1, capo = has_o ? 1 : 0;
+        for (int ch = 0; ch < n_chunks; ++ch) {
+            const int c0 = ch * 32, c1 = std::min(n_chan, c0 + 32) - 1;
+            ci[ch].x = t.f_map[c0];
+            ci[ch].y = t.f_map[c1] - t.f_map[c0] + 1;
+            ci[ch].z = has_o ? terms[1 - n].f_map[c0] : 0;
+            ci[ch].w = has_o ? terms[1 - n].f_map[c1] - terms[1 - n].f_map[c0] + 1 : 0;
+            capn = std::max(capn, ci[ch].y);
+            capo = std::max(capo, ci[ch].w);
+        }
+        const int esn = t.type == 1 ? 32 : 16;
+        const int eso = has_o ? (terms[1 - n].type == 1 ? 32 : 16) : 16;
+        pa.jn_cap = capn;
+        pa.jo_cap = capo;
+        const int mb = m16 ? 16 : 32;
+        pa.off_m = 32 * 32;
+        pa.off_w = pa.off_m + 32 * mb;
+        pa.off_jn = pa.off_w + 32 * 16;
+        pa.off_jo = pa.off_jn + 2 * pa.jn_cap * esn;
+        pa.slot_bytes = pa.off_jo + 2 * pa.jo_cap * eso;
+        pa.stage_fmap = n_chan <= 8192 ? 1 : 0;
+        const int fmap_bytes = pa.stage_fmap ? ((2 * n_chan * 4 + 15) / 16) * 16 : 0;
+        const int H = L.pipe_h;
+        const int per_stage = H * (pa.slot_bytes + (int)sizeof(SlotDesc)) + 8;
+        const int warp_budget = (smem_optin - fmap_bytes - 128) / NW;
+        const int ns = std::min(8, warp_budget / per_stage);
+        if (ns < 2) pipelined = false;
+        else {
+            pa.ns = ns;
+            pa.desc_off = ns * H * pa.slot_bytes;
+            pa.bar_off = pa.desc_off + ns * H * (int)sizeof(SlotDesc);
+            pa.warp_bytes = ((pa.bar_off + ns * 8 + 15) / 16) * 16;
+            pa.fmap_off = NW * pa.warp_bytes;
+            pipe_smem = pa.fmap_off + fmap_bytes;
+            if (!configured(L.pipe_fn)) {
+                CK(cudaFuncSetAttribute(L.pipe_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin));
+                configured_fns.push_back(L.pipe_fn);
+            }
+        }
+    }
+    {
+        // static per-row and per-chunk information of this term solve (both kernels)
+        const int n_chunks = (n_chan + 31) / 32;
+        std::vector<int4> ci(n_chunks);
+        for (int ch = 0; ch < n_chunks; ++ch) {
+            const int c0 = ch * 32, c1 = std::min(n_chan, c0 + 32) - 1;
+            ci[ch].x = t.f_map[c0];
+            ci[ch].y = t.f_map[c1] - t.f_map[c0] + 1;
+            ci[ch].z = has_o ? terms[1 - n].f_map[c0] : 0;
+            ci[ch].w = has_o ? terms[1 - n].f_map[c1] - terms[1 - n].f_map[c0] + 1 : 0;
+        }
+        int rc_;
+        if ((rc_ = ensure(B.row_info, nbytes<int4>(std::max(1, n_row))))) return rc_;
+        if ((rc_ = ensure(B.chunk_info, nbytes<int4>(n_chunks)))) return rc_;
+        CK(cudaMemcpyAsync(B.chunk_info.ptr, ci.data(), nbytes<int4>(n_chunks), cudaMemcpyHostToDevice, st));
+        if (n_row) {
+            row_info_kernel<<<(n_row + 255) / 256, 256, 0, st>>>(data_desc(), d_row_live, chain.t[n],
+                                                                has_o ? chain.t[1 - n] : chain.t[n], has_o ? 1 : 0,
+                                                                (int4 *)B.row_info.ptr);
+            CK(cudaGetLastError());
+            ++launches;
+        }
+        pa.row_info = (const int4 *)B.row_info.ptr;
+        pa.chunk_info = (const int4 *)B.chunk_info.ptr;
+        aa.row_info = pa.row_info;
+    }
     int grid;
     if (pipelined) {
-        if (!configured(L.pipe_fn)) {
-            CK(cudaFuncSetAttribute(L.pipe_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, L.pipe_smem));
-            configured_fns.push_back(L.pipe_fn);
-        }
-        const long groups = (units + (L.pipe_threads / 32 - 1) - 1) / (L.pipe_threads / 32 - 1);
+        const int NW = L.pipe_nw;
+        const long groups = (units + NW - 1) / NW;
         grid = (int)std::max(1L, std::min((long)sm_count, groups));
     } else {
+        const int smem = (block / 32) * L.acc_smem_per_warp;
+        if (!configured(L.fn)) {
+            CK(cudaFuncSetAttribute(L.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin));
+            configured_fns.push_back(L.fn);
+        }
         if (per_sm == 0) {
             int occ = 0;
-            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, L.fn, block, 0);
+            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, L.fn, block, smem);
             per_sm = (e == cudaSuccess && occ > 0) ? occ : 2;
         }
         const long warps_needed = std::max(1L, units);
@@ -710,9 +791,8 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
     }
     int rc;
     if ((rc = ensure(B.chunk_act, (size_t)t.n_tint * aa.n_chunks))) return rc;
-    PipeArgs pa;
+    aa.chunk_active = (const uint8_t *)B.chunk_act.ptr;
     pa.a = aa;
-    pa.row_live = d_row_live;
     pa.chunk_active = (const uint8_t *)B.chunk_act.ptr;
     pa.err = d_err;
     const int ca_threads = t.n_tint * aa.n_chunks;
@@ -748,7 +828,7 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
         for (int k = 1; k <= max_iter; ++k) {
             aa.n_active = cnt + (k - 1);
             // inside a capture the record must be an external event node to be timed on replay
-            if (pipelined) {
+            {
                 chunk_active_kernel<<<(ca_threads + 255) / 256, 256, 0, st>>>(aa.tn, n_chan, aa.n_chunks,
                                                                             (const uint8_t *)B.active.ptr, cnt + (k - 1),
                                                                             (uint8_t *)B.chunk_act.ptr);
@@ -757,7 +837,7 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
             CK(cudaEventRecordWithFlags(events[2 + 2 * (k - 1)], st, rec_flags));
             if (pipelined) {
                 pa.a.n_active = cnt + (k - 1);
-                CK(L.pipe_launch(grid, st, pa));
+                CK(L.pipe_launch(grid, pipe_smem, st, pa));
             } else {
                 CK(L.launch(grid, block, st, aa));
             }
@@ -780,12 +860,17 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
     if (use_graph) {
         if (!B.graph_valid) {
             if (B.exec) { cudaGraphExecDestroy(B.exec); B.exec = nullptr; }
-            cudaGraph_t g;
+            cudaGraph_t g = nullptr;
             CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
             rc = enqueue();
+            // always end the capture, so that a failure leaves the stream usable
             cudaError_t e = cudaStreamEndCapture(st, &g);
-            if (rc) return rc;
-            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+            if (rc || e != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                cudaGetLastError();
+                if (rc) return rc;
+                return cuda_fail(e, "cudaStreamEndCapture");
+            }
             e = cudaGraphInstantiate(&B.exec, g, 0);
             cudaGraphDestroy(g);
             if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
@@ -795,7 +880,7 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
     } else {
         if ((rc = enqueue())) return rc;
     }
-    launches += 1 + (pipelined ? 3 : 2) * (long long)max_iter;
+    launches += 1 + 3 * (long long)max_iter;
     // iteration bookkeeping: which accumulate launches did work, and their device time
     std::vector<int> hcnt(max_iter + 1);
     int herr = 0;

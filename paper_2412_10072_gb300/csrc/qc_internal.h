@@ -27,6 +27,8 @@ struct TermBufs {
     Buf iters;     // int [bins]
     Buf flags;     // int8 [bins][ant]
     Buf chunk_act; // uint8 [n_tint][n_chunks] for the pipelined kernel
+    Buf row_info;  // int4 [n_row] {p, q, tn, to} for the pipelined kernel
+    Buf chunk_info;// int4 [n_chunks] Jones slice ranges of the 32-channel chunks
     cudaGraphExec_t exec = nullptr;
     bool graph_valid = false;
 };
@@ -34,11 +36,13 @@ struct TermBufs {
 // One instantiation of the accumulate kernel: its address (for occupancy
 // queries) and a launcher.
 struct AccLaunch {
-    const void *fn = nullptr;
+    const void *fn = nullptr;        // prefetching accumulate kernel
     cudaError_t (*launch)(int grid, int block, cudaStream_t st, const qc::AccArgs &a) = nullptr;
-    const void *pipe_fn = nullptr;
-    cudaError_t (*pipe_launch)(int grid, cudaStream_t st, const qc::PipeArgs &p) = nullptr;
-    int pipe_smem = 0, pipe_threads = 0;
+    int acc_smem_per_warp = 0;       // its dynamic shared memory per warp
+    const void *pipe_fn = nullptr;   // pipelined kernel (chains of one or two terms only)
+    cudaError_t (*pipe_launch)(int grid, int smem_bytes, cudaStream_t st, const qc::PipeArgs &p) = nullptr;
+    int pipe_nw = 0;                 // its warps per CTA
+    int pipe_h = 1;                  // row segments per warp step
 };
 AccLaunch acc_launcher_diag(bool simple, int lk, int rk, bool m16);
 AccLaunch acc_launcher_full(bool simple, int lk, int rk, bool m16);
@@ -48,7 +52,7 @@ inline AccLaunch acc_launcher(int ts, bool simple, int lk, int rk, bool m16)
 }
 
 struct qc_ctx {
-    int dev = 0, sm_count = 1;
+    int dev = 0, sm_count = 1, smem_optin = 0;
     cudaStream_t own_stream = nullptr;
     int n_row = 0, n_chan = 0, n_ant = 0, n_time = 0, n_bl = 0, n_strips = 0;
     bool m16 = false, has_flag = false;

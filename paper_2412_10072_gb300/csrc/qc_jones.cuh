@@ -32,6 +32,19 @@ __device__ __forceinline__ float2 cfma_conj(float2 a, float2 b, float2 acc)
 }
 __device__ __forceinline__ float cnorm2(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
 
+// a b + c d  (fused: one multiply and three FMAs per component)
+__device__ __forceinline__ float2 cdot(float2 a, float2 b, float2 c, float2 d)
+{
+    return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, fmaf(c.x, d.x, -c.y * d.y))),
+                       fmaf(a.x, b.y, fmaf(a.y, b.x, fmaf(c.x, d.y, c.y * d.x))));
+}
+// a conj(b) + c conj(d)
+__device__ __forceinline__ float2 cdotc(float2 a, float2 b, float2 c, float2 d)
+{
+    return make_float2(fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(c.x, d.x, c.y * d.y))),
+                       fmaf(a.y, b.x, fmaf(-a.x, b.y, fmaf(c.y, d.x, -c.x * d.y))));
+}
+
 struct J2 {
     float2 a, b, c, d;
 };
@@ -48,10 +61,10 @@ __device__ __forceinline__ J2 j_identity()
 __device__ __forceinline__ J2 j_mul(const J2 &A, const J2 &B)
 {
     J2 r;
-    r.a = cadd(cmul(A.a, B.a), cmul(A.b, B.c));
-    r.b = cadd(cmul(A.a, B.b), cmul(A.b, B.d));
-    r.c = cadd(cmul(A.c, B.a), cmul(A.d, B.c));
-    r.d = cadd(cmul(A.c, B.b), cmul(A.d, B.d));
+    r.a = cdot(A.a, B.a, A.b, B.c);
+    r.b = cdot(A.a, B.b, A.b, B.d);
+    r.c = cdot(A.c, B.a, A.d, B.c);
+    r.d = cdot(A.c, B.b, A.d, B.d);
     return r;
 }
 
@@ -59,10 +72,10 @@ __device__ __forceinline__ J2 j_mul(const J2 &A, const J2 &B)
 __device__ __forceinline__ J2 j_mul_h(const J2 &A, const J2 &B)
 {
     J2 r;
-    r.a = cadd(cmulc(A.a, B.a), cmulc(A.b, B.b));
-    r.b = cadd(cmulc(A.a, B.c), cmulc(A.b, B.d));
-    r.c = cadd(cmulc(A.c, B.a), cmulc(A.d, B.b));
-    r.d = cadd(cmulc(A.c, B.c), cmulc(A.d, B.d));
+    r.a = cdotc(A.a, B.a, A.b, B.b);
+    r.b = cdotc(A.a, B.c, A.b, B.d);
+    r.c = cdotc(A.c, B.a, A.d, B.b);
+    r.d = cdotc(A.c, B.c, A.d, B.d);
     return r;
 }
 

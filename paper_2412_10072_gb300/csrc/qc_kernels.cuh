@@ -81,6 +81,9 @@ struct AccArgs {
     Chain C;
     DevTerm tn;              // copy of C.t[C.n] (avoids dynamic indexing of kernel parameters)
     DevTerm to;              // the other term of a two-term chain (unused otherwise)
+    const uint8_t *row_live; // [n_row] 1: cross-correlation row with an unflagged sample
+    const int4 *row_info;    // [n_row] {p, q, tn, to}, tn = -1 for rows without usable data
+    const uint8_t *chunk_active;  // [n_tint of term n][n_chunks]: a 32-channel chunk has an active bin
     double *acc;             // [n_bins][n_ant][KG]
     const uint8_t *active;   // [n_bins]
     const int *n_active;     // nonzero: some interval of the solved term is still iterating
@@ -371,17 +374,14 @@ __device__ __forceinline__ void factors(const AccArgs &a, const SampleIdx &ix, i
 // Contribution of one unflagged sample of baseline (p, q) to the p and q blocks.
 // With Z = R_p M R_q^H:  X = Z G_q^H L_q^H = R_p M C_q^H,  V = L_p G_p X  (Eq. chain_trick),
 // and for the conjugate baseline Y = R_q M^H C_p^H = (L_p G_p Z)^H.
-template <int TS, int LK, int RK, bool SIMPLE, bool KAHAN>
-__device__ __forceinline__ void sample_contrib(const AccArgs &a, const SampleIdx &ix, int p, int q, const J2 &Dm,
-                                               const J2 &M, float4 w,
-                                               Acc<AccLayout<TS, LK != KIND_NONE>::KR, KAHAN> &Ap,
-                                               Acc<AccLayout<TS, LK != KIND_NONE>::KR, KAHAN> &Aq)
+template <int TS, int LK, int RK, bool KAHAN>
+__device__ __forceinline__ void sample_math(const J2 &Lp, const J2 &Gp, const J2 &Rp, const J2 &Lq, const J2 &Gq,
+                                            const J2 &Rq, const J2 &Dm, const J2 &M, float4 w,
+                                            Acc<AccLayout<TS, LK != KIND_NONE>::KR, KAHAN> &Ap,
+                                            Acc<AccLayout<TS, LK != KIND_NONE>::KR, KAHAN> &Aq)
 {
     constexpr bool HAS_L = LK != KIND_NONE;
     constexpr int GK = TS == TS_FULL ? KIND_FULL : KIND_DIAG;
-    J2 Lp, Gp, Rp, Lq, Gq, Rq;
-    factors<GK, LK, RK, SIMPLE>(a, ix, p, Lp, Gp, Rp);
-    factors<GK, LK, RK, SIMPLE>(a, ix, q, Lq, Gq, Rq);
     J2 X, Y, V;
     if constexpr (RK == KIND_NONE) {
         const J2 Cp = HAS_L ? rmulk<GK>(Lp, Gp) : Gp;
@@ -404,6 +404,19 @@ __device__ __forceinline__ void sample_contrib(const AccArgs &a, const SampleIdx
     r.a = csub(Dm.a, V.a); r.b = csub(Dm.b, V.b); r.c = csub(Dm.c, V.c); r.d = csub(Dm.d, V.d);
     accumulate_side<TS, HAS_L, KAHAN>(Ap, Lp, X, w, r);
     accumulate_side<TS, HAS_L, KAHAN>(Aq, Lq, Y, make_float4(w.x, w.z, w.y, w.w), j_herm(r));
+}
+
+template <int TS, int LK, int RK, bool SIMPLE, bool KAHAN>
+__device__ __forceinline__ void sample_contrib(const AccArgs &a, const SampleIdx &ix, int p, int q, const J2 &Dm,
+                                               const J2 &M, float4 w,
+                                               Acc<AccLayout<TS, LK != KIND_NONE>::KR, KAHAN> &Ap,
+                                               Acc<AccLayout<TS, LK != KIND_NONE>::KR, KAHAN> &Aq)
+{
+    constexpr int GK = TS == TS_FULL ? KIND_FULL : KIND_DIAG;
+    J2 Lp, Gp, Rp, Lq, Gq, Rq;
+    factors<GK, LK, RK, SIMPLE>(a, ix, p, Lp, Gp, Rp);
+    factors<GK, LK, RK, SIMPLE>(a, ix, q, Lq, Gq, Rq);
+    sample_math<TS, LK, RK, KAHAN>(Lp, Gp, Rp, Lq, Gq, Rq, Dm, M, w, Ap, Aq);
 }
 
 // Interval indices of a sample at data time `time` and channel c.
@@ -444,7 +457,67 @@ __device__ __forceinline__ J2 load_model16(uint4 h, float sc)
 // ---------------------------------------------------------------------------
 
 
-template <int TS, int LK, int RK, bool SIMPLE, bool M16>
+// Position in a warp's stream of row segments: unit u (a row for row tiles, a
+// baseline strip x 32-channel chunk for strip tiles), segment i of len.
+struct SegCursor {
+    long u;
+    int i, len, beg, c0;
+    int row;          // row of the current segment (-1: nothing to read)
+    int tn;           // row tiles: time-interval index of the unit's row (-1: nothing to read)
+};
+
+// Locate the current segment; with SKIP set, rows without unflagged data and (row
+// tiles) 32-channel chunks whose intervals have all converged read nothing.
+template <bool SKIP>
+__device__ __forceinline__ void seg_locate(const AccArgs &a, SegCursor &k)
+{
+    if (a.order == 0) {
+        k.row = (int)k.u;
+        if (SKIP && (k.tn < 0 || !__ldg(a.chunk_active + (size_t)k.tn * a.n_chunks + k.i))) k.row = -1;
+    } else {
+        k.row = __ldg(a.D.strip_rows + k.beg + k.i);
+        if (SKIP && !__ldg(a.row_live + k.row)) k.row = -1;
+    }
+}
+
+__device__ __forceinline__ void seg_unit(const AccArgs &a, SegCursor &k, long n_units)
+{
+    k.i = 0;
+    k.len = 0;
+    if (k.u >= n_units) return;
+    if (a.order == 0) {
+        k.len = a.n_chunks; k.beg = 0; k.c0 = 0;
+        k.tn = __ldg(a.row_info + k.u).z;
+    }
+    else {
+        const int s = (int)(k.u / a.n_chunks);
+        k.c0 = (int)(k.u % a.n_chunks) * 32;
+        k.beg = __ldg(a.D.strip_off + s);
+        k.len = __ldg(a.D.strip_off + s + 1) - k.beg;
+    }
+}
+
+__device__ __forceinline__ void seg_next(const AccArgs &a, SegCursor &k, long n_units, long stride)
+{
+    if (++k.i < k.len) return;
+    do {
+        k.u += stride;
+        seg_unit(a, k, n_units);
+    } while (k.u < n_units && k.len == 0);
+}
+
+// Accumulate kernel with per-lane asynchronous prefetch.
+//
+// Every warp streams through its own work units (a unit is one row for row
+// tiles, or one baseline strip x 32 channels for strip tiles); lane l handles
+// channel c0 + l of every row segment and keeps its register partial sums while
+// its sample's interval bin stays the same (see flush_side).  The d, m and w of
+// the lane's sample are fetched DEPTH - 1 segments ahead with 16-byte cp.async
+// copies into the warp's ring in shared memory, so the HBM latency of a segment
+// is overlapped with the arithmetic of the previous ones; rows without an
+// unflagged cross-correlation sample are not read at all.  The Jones factors
+// come from the small gain tables through the read-only cache.
+template <int TS, int LK, int RK, bool SIMPLE, bool M16, int DEPTH>
 __global__ void __launch_bounds__(256) acc_kernel(const AccArgs a)
 {
     if (__ldg(a.n_active) == 0) return;
@@ -452,73 +525,115 @@ __global__ void __launch_bounds__(256) acc_kernel(const AccArgs a)
     constexpr bool KAHAN = M16;
     using Lay = AccLayout<TS, HAS_L>;
     constexpr int KR = Lay::KR, KG = Lay::KG;
+    constexpr int V4 = M16 ? 4 : 5;                 // 16-byte words per sample: d (2), m (2 or 1), w (1)
+    extern __shared__ float4 s_ring[];
     const Data &D = a.D;
-    const Chain &C = a.C;
     const DevTerm &Tn = a.tn;
-    const int lane = threadIdx.x & 31;
-    const long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long n_warps = ((long)gridDim.x * blockDim.x) >> 5;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    float4 *ring = s_ring + (size_t)wib * DEPTH * 32 * V4;
     const long n_units = a.order == 0 ? (long)D.n_row : (long)D.n_strips * a.n_chunks;
+    const long stride = ((long)gridDim.x * blockDim.x) >> 5;
+
+    SegCursor ck, pf;
+    ck.u = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    seg_unit(a, ck, n_units);
+    if (ck.u < n_units && ck.len == 0) seg_next(a, ck, n_units, stride);
+    pf = ck;
+    int pf_stage = 0;
+
+    auto issue = [&](SegCursor &k) {
+        seg_locate<true>(a, k);
+        const int c = a.order == 0 ? k.i * 32 + lane : k.c0 + lane;
+        const bool rd = k.row >= 0 && c < D.n_chan;
+        const size_t s = rd ? (size_t)k.row * D.n_chan + c : 0;
+        const uint32_t nb = rd ? 16u : 0u;
+        float4 *slot = ring + ((size_t)pf_stage * 32 + lane) * V4;
+        cp_async16(slot + 0, D.vis + 2 * s, nb);
+        cp_async16(slot + 1, D.vis + 2 * s + 1, nb);
+        if constexpr (M16) {
+            cp_async16(slot + 2, D.model16 + s, nb);
+            cp_async16(slot + 3, D.weight + s, nb);
+        } else {
+            cp_async16(slot + 2, D.model + 2 * s, nb);
+            cp_async16(slot + 3, D.model + 2 * s + 1, nb);
+            cp_async16(slot + 4, D.weight + s, nb);
+        }
+        if (++pf_stage == DEPTH) pf_stage = 0;
+    };
+
+    // prime the ring with DEPTH - 1 segments (one commit group each)
+#pragma unroll
+    for (int d = 0; d < DEPTH - 1; ++d) {
+        if (pf.u < n_units) {
+            issue(pf);
+            seg_next(a, pf, n_units, stride);
+        }
+        cp_async_commit();
+    }
 
     Acc<KR, KAHAN> Ap, Aq;
     Ap.zero();
     Aq.zero();
-
-    for (long u = warp; u < n_units; u += n_warps) {
-        int cur_key = -1;
-        int p = 0, q = 0;
-        long i_beg, i_end;
-        int c_fixed = 0;
-        if (a.order == 0) { i_beg = 0; i_end = a.n_chunks; }
-        else {
-            const int s = (int)(u / a.n_chunks);
-            c_fixed = (int)(u % a.n_chunks) * 32 + lane;
-            i_beg = __ldg(D.strip_off + s);
-            i_end = __ldg(D.strip_off + s + 1);
+    int stage = 0, cur_key = -1, p = 0, q = 0;
+    while (ck.u < n_units) {
+        if (pf.u < n_units) {
+            issue(pf);
+            seg_next(a, pf, n_units, stride);
         }
-        for (long i = i_beg; i < i_end; ++i) {
-            const int row = a.order == 0 ? (int)u : __ldg(D.strip_rows + i);
-            const int c = a.order == 0 ? (int)i * 32 + lane : c_fixed;
-            const int4 meta = __ldg(D.rows + row);
-            p = meta.x;
-            q = meta.y;
-            if (p == q) break;                       // autocorrelation: whole unit skipped
-            const bool in_range = c < D.n_chan;
-            SampleIdx ix;
-            sample_index<SIMPLE>(a, meta.z, c, in_range, ix);
-            const int key = in_range ? ix.tn * Tn.n_fint + ix.fn : -1;
-            // flush when any lane's bin changes
-            if (__any_sync(0xffffffffu, cur_key >= 0 && key != cur_key)) {
-                const unsigned m = __match_any_sync(0xffffffffu, cur_key);
-                const unsigned seg_end = 32 - __clz(m);
-                const bool head = lane == __ffs(m) - 1;
-                const bool live = cur_key >= 0 && __ldg(a.active + cur_key);
-                flush_side<KR, KG, KAHAN, Lay>(Ap, cur_key, p, lane, seg_end, head, live, a.acc, C.n_ant);
-                flush_side<KR, KG, KAHAN, Lay>(Aq, cur_key, q, lane, seg_end, head, live, a.acc, C.n_ant);
-            }
-            cur_key = key;
-            const size_t s = (size_t)row * D.n_chan + c;
-            bool ok = in_range && __ldg(a.active + key);
-            if (ok && D.flag) ok = __ldg(D.flag + s) == 0;
-            if (!__any_sync(0xffffffffu, ok)) continue;
-            if (!ok) continue;
-            const J2 Dm = j_from(__ldg(D.vis + 2 * s), __ldg(D.vis + 2 * s + 1));
-            J2 M;
-            if constexpr (M16) M = load_model16(__ldg(D.model16 + s), __ldg(D.bl_scale + meta.w));
-            else M = j_from(__ldg(D.model + 2 * s), __ldg(D.model + 2 * s + 1));
-            const float4 w = __ldg(D.weight + s);
-            sample_contrib<TS, LK, RK, SIMPLE, KAHAN>(a, ix, p, q, Dm, M, w, Ap, Aq);
-        }
-        // end of the unit: flush what is left
-        if (__any_sync(0xffffffffu, cur_key >= 0)) {
+        cp_async_commit();
+        cp_async_wait<DEPTH - 1>();                 // this lane's copies of the current segment landed
+        seg_locate<false>(a, ck);
+        const int row = ck.row;
+        const int c = a.order == 0 ? ck.i * 32 + lane : ck.c0 + lane;
+        const int4 meta = __ldg(D.rows + row);
+        p = meta.x;
+        q = meta.y;
+        const bool in_range = c < D.n_chan && p != q;
+        SampleIdx ix;
+        sample_index<SIMPLE>(a, meta.z, c, in_range, ix);
+        const int key = in_range ? ix.tn * Tn.n_fint + ix.fn : -1;
+        if (__any_sync(0xffffffffu, cur_key >= 0 && key != cur_key)) {
             const unsigned m = __match_any_sync(0xffffffffu, cur_key);
             const unsigned seg_end = 32 - __clz(m);
             const bool head = lane == __ffs(m) - 1;
             const bool live = cur_key >= 0 && __ldg(a.active + cur_key);
-            flush_side<KR, KG, KAHAN, Lay>(Ap, cur_key, p, lane, seg_end, head, live, a.acc, C.n_ant);
-            flush_side<KR, KG, KAHAN, Lay>(Aq, cur_key, q, lane, seg_end, head, live, a.acc, C.n_ant);
+            flush_side<KR, KG, KAHAN, Lay>(Ap, cur_key, p, lane, seg_end, head, live, a.acc, a.C.n_ant);
+            flush_side<KR, KG, KAHAN, Lay>(Aq, cur_key, q, lane, seg_end, head, live, a.acc, a.C.n_ant);
+        }
+        cur_key = key;
+        bool ok = in_range && __ldg(a.active + key);
+        if (ok && D.flag) ok = __ldg(D.flag + (size_t)row * D.n_chan + c) == 0;
+        if (ok) ok = __ldg(a.row_live + row) != 0;
+        if (ok) {
+            const float4 *slot = ring + ((size_t)stage * 32 + lane) * V4;
+            const J2 Dm = j_from(slot[0], slot[1]);
+            J2 M;
+            float4 w;
+            if constexpr (M16) {
+                M = load_model16(*reinterpret_cast<const uint4 *>(slot + 2), __ldg(D.bl_scale + meta.w));
+                w = slot[3];
+            } else {
+                M = j_from(slot[2], slot[3]);
+                w = slot[4];
+            }
+            sample_contrib<TS, LK, RK, SIMPLE, KAHAN>(a, ix, p, q, Dm, M, w, Ap, Aq);
+        }
+        if (++stage == DEPTH) stage = 0;
+        const long u_prev = ck.u;
+        seg_next(a, ck, n_units, stride);
+        if (ck.u != u_prev) {
+            if (__any_sync(0xffffffffu, cur_key >= 0)) {
+                const unsigned m = __match_any_sync(0xffffffffu, cur_key);
+                const unsigned seg_end = 32 - __clz(m);
+                const bool head = lane == __ffs(m) - 1;
+                const bool live = cur_key >= 0 && __ldg(a.active + cur_key);
+                flush_side<KR, KG, KAHAN, Lay>(Ap, cur_key, p, lane, seg_end, head, live, a.acc, a.C.n_ant);
+                flush_side<KR, KG, KAHAN, Lay>(Aq, cur_key, q, lane, seg_end, head, live, a.acc, a.C.n_ant);
+            }
+            cur_key = -1;
         }
     }
+    cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------------------
@@ -859,188 +974,324 @@ namespace qc {
 
 struct PipeArgs {
     AccArgs a;
-    const uint8_t *row_live;      // [n_row] 1: cross-correlation row with an unflagged sample
+    const int4 *row_info;         // [n_row] {p, q, tn, to}; tn = -1 for rows without usable data
+    const int4 *chunk_info;       // [n_chunks] {fn0, fn count, fo0, fo count} of the 32-channel chunks
     const uint8_t *chunk_active;  // [n_tint of term n][n_chunks]: a 32-channel chunk has an active bin
     int *err;                     // set to 1 when a bounded wait gives up
-};
-
-template <int NW, int NS, int MB> struct PipeLayout {
-    static constexpr int SLOT_D = 32 * 32, SLOT_M = 32 * MB, SLOT_W = 32 * 16;
-    static constexpr int STAGE = NW * (SLOT_D + SLOT_M + SLOT_W);
-    static constexpr int DESC_OFF = NS * STAGE;
-    static constexpr int BAR_OFF = DESC_OFF + NS * NW * 16;
-    static constexpr int BYTES = BAR_OFF + 2 * NS * 8;
+    // shared-memory layout (bytes), fixed per launch by the host
+    int ns;                       // ring stages per warp
+    int slot_bytes;               // one stage of one warp: d, m, w and Jones slices
+    int off_m, off_w, off_jn, off_jo;   // offsets inside a slot
+    int jn_cap, jo_cap;           // Jones entries per antenna for the solved / other term
+    int warp_bytes;               // ring + descriptors + barriers of one warp
+    int desc_off, bar_off;        // offsets inside a warp's area
+    int fmap_off;                 // f_maps of both terms (stage_fmap)
+    int stage_fmap;
 };
 
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;   // 2 s
 
-// slot layout of one unit for the producer and the consumers (identical on both sides)
-__device__ __forceinline__ void unit_info(const AccArgs &a, long u, long n_units, int &row0, int &c0, int &beg, int &len)
+// Descriptor of one row segment of a warp's step (written when its copies are issued).
+struct __align__(16) SlotDesc {
+    int row, cc, nch, live;       // row segment [cc, cc + nch) of `row`; live = data copied
+    int p, q, tn, pad0;           // antennas, time-interval index of the solved term
+    int fn0, fo0;                 // first frequency-interval index of the staged Jones slices
+    float scale;                  // per-baseline model scale (FP16 model)
+    int pad1;
+};
+
+template <int K> __device__ __forceinline__ J2 smem_jones(const unsigned char *base, int i)
 {
-    row0 = 0; c0 = 0; beg = 0; len = 0;
-    if (u >= n_units) return;
-    if (a.order == 0) { row0 = (int)u; len = a.n_chunks; }
-    else {
-        const int s = (int)(u / a.n_chunks);
-        c0 = (int)(u % a.n_chunks) * 32;
-        beg = __ldg(a.D.strip_off + s);
-        len = __ldg(a.D.strip_off + s + 1) - beg;
+    if constexpr (K == KIND_FULL) {
+        const float4 *v = reinterpret_cast<const float4 *>(base) + 2 * i;
+        return j_from(v[0], v[1]);
+    } else {
+        return j_diag(reinterpret_cast<const float4 *>(base)[i]);
     }
 }
 
-template <int TS, int LK, int RK, bool SIMPLE, bool M16, int NW, int NS>
-__global__ void __launch_bounds__((NW + 1) * 32, 1) acc_pipe_kernel(const PipeArgs P)
+// Position in a warp's stream of steps: unit u (a row for row tiles, a strip x
+// 32-channel chunk for strip tiles), step i of len; a step covers H row segments.
+struct Cursor {
+    long u;
+    int i, len, beg, c0, n_seg;
+};
+
+template <int H>
+__device__ __forceinline__ void cursor_unit(const AccArgs &a, Cursor &k, long n_units)
+{
+    k.i = 0;
+    k.len = 0;
+    if (k.u >= n_units) return;
+    if (a.order == 0) { k.n_seg = a.n_chunks; k.beg = 0; k.c0 = 0; }
+    else {
+        const int s = (int)(k.u / a.n_chunks);
+        k.c0 = (int)(k.u % a.n_chunks) * 32;
+        k.beg = __ldg(a.D.strip_off + s);
+        k.n_seg = __ldg(a.D.strip_off + s + 1) - k.beg;
+    }
+    k.len = (k.n_seg + H - 1) / H;
+}
+
+template <int H>
+__device__ __forceinline__ void cursor_next(const AccArgs &a, Cursor &k, long n_units, long stride)
+{
+    if (++k.i < k.len) return;
+    do {
+        k.u += stride;
+        cursor_unit<H>(a, k, n_units);
+    } while (k.u < n_units && k.len == 0);
+}
+
+// Pipelined accumulate kernel for chains of one or two terms.
+//
+// Every warp streams through its own work units (a unit is one row for row
+// tiles, or one baseline strip x 32 channels for strip tiles) and keeps its
+// register partial sums for the unit's antennas.  A step covers H row segments
+// of 32 channels (consecutive channel chunks of a row, or consecutive rows of a
+// strip).  Each warp owns an NS-deep ring of shared-memory stages with one
+// mbarrier per stage: NS - 1 steps ahead of the step it computes, its lanes
+// issue cp.async.bulk copies (one per lane) of the segments of d, m and w
+// (contiguous in [row][chan][corr]) and of the slices of both terms' Jones
+// tables that each segment touches for antennas p and q (contiguous in the
+// [tint][ant][fint] table layout), completing the stage's transaction count.
+// The sample arithmetic then reads shared memory only.  Segments that are fully
+// flagged, autocorrelations, or whose intervals have all converged are not
+// copied.  Warps never wait on each other; every wait on a stage barrier is
+// bounded in wall time (a timeout sets *err, and the warp leaves after waiting,
+// again bounded, for its own copies in flight).
+template <int TS, int LK, int RK, bool M16, int NW, int H>
+__global__ void __launch_bounds__(NW * 32, 1) acc_pipe_kernel(const PipeArgs P)
 {
     constexpr bool HAS_L = LK != KIND_NONE;
     constexpr bool KAHAN = M16;
     using Lay = AccLayout<TS, HAS_L>;
     constexpr int KR = Lay::KR, KG = Lay::KG;
     constexpr int MB = M16 ? 16 : 32;
-    using PL = PipeLayout<NW, NS, MB>;
+    constexpr int GK = TS == TS_FULL ? KIND_FULL : KIND_DIAG;
+    constexpr int OK_ = LK != KIND_NONE ? LK : RK;          // kind of the other term (NONE: single term)
+    constexpr int ESN = GK == KIND_FULL ? 32 : 16;
+    constexpr int ESO = OK_ == KIND_FULL ? 32 : 16;
+    constexpr int NCOPY = OK_ != KIND_NONE ? 7 : 5;         // bulk copies per row segment
+    static_assert(H * 8 <= 32, "one lane per copy");
     extern __shared__ __align__(128) unsigned char smem[];
-    int4 *desc = reinterpret_cast<int4 *>(smem + PL::DESC_OFF);
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + PL::BAR_OFF);
-    uint64_t *empty = full + NS;
     const AccArgs &a = P.a;
     const Data &D = a.D;
-    const Chain &C = a.C;
     const DevTerm &Tn = a.tn;
+    const DevTerm &To = a.to;
+    const int n_ant = a.C.n_ant;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char *wbase = smem + (size_t)warp * P.warp_bytes;
+    SlotDesc *desc = reinterpret_cast<SlotDesc *>(wbase + P.desc_off);
+    uint64_t *full = reinterpret_cast<uint64_t *>(wbase + P.bar_off);
+    const int *sfn = reinterpret_cast<const int *>(smem + P.fmap_off);
+    const int *sfo = sfn + D.n_chan;
 
     if (__ldg(a.n_active) == 0) return;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < NS; ++s) {
-            mbar_init(full + s, 1);
-            mbar_init(empty + s, NW);
+    if (P.stage_fmap) {
+        int *wfn = reinterpret_cast<int *>(smem + P.fmap_off);
+        for (int c = threadIdx.x; c < D.n_chan; c += blockDim.x) {
+            wfn[c] = __ldg(Tn.f_map + c);
+            if constexpr (OK_ != KIND_NONE) wfn[D.n_chan + c] = __ldg(To.f_map + c);
         }
+    }
+    if (lane == 0) {
+        for (int s = 0; s < P.ns; ++s) mbar_init(full + s, 1);
         fence_barrier_init();
     }
     __syncthreads();
-    const long n_units = a.order == 0 ? (long)D.n_row : (long)D.n_strips * a.n_chunks;
-    const long n_groups = (n_units + NW - 1) / NW;
 
-    if (warp == NW) {
-        // ------------------------------ producer ------------------------------
-        uint32_t it = 0;
-        bool ok = true;
-        for (long g = blockIdx.x; g < n_groups && ok; g += gridDim.x) {
-            int row0, c0, beg, len;
-            unit_info(a, g * NW + lane, n_units, row0, c0, beg, len);
-            if (lane >= NW) len = 0;
-            const int steps = __reduce_max_sync(0xffffffffu, len);
-            for (int i = 0; i < steps; ++i, ++it) {
-                const int stage = it % NS;
-                const uint32_t par = (it / NS) & 1u;
-                if (!mbar_wait_bounded(empty + stage, par ^ 1u, WAIT_LIMIT_NS)) { ok = false; break; }
-                int4 d = make_int4(-1, 0, 0, 0);
-                uint32_t bytes = 0;
-                if (lane < NW && i < len) {
-                    const int row = a.order == 0 ? row0 : __ldg(D.strip_rows + beg + i);
-                    const int cc = a.order == 0 ? i * 32 : c0;
-                    const int nch = min(32, D.n_chan - cc);
-                    bool live = __ldg(P.row_live + row) != 0;
-                    if (live) {
-                        const int t = __ldg(D.rows + row).z;
-                        live = __ldg(P.chunk_active + (size_t)__ldg(Tn.t_map + t) * a.n_chunks + cc / 32) != 0;
-                    }
-                    d = make_int4(row, cc, nch, live ? 1 : 0);
-                    if (live) bytes = (uint32_t)nch * (32u + MB + 16u);
-                }
-                if (lane < NW) desc[stage * NW + lane] = d;
-                const uint32_t total = __reduce_add_sync(0xffffffffu, bytes);
-                __syncwarp();
-                if (lane == 0) mbar_arrive_expect_tx(full + stage, total);
-                __syncwarp();
-                if (bytes) {
-                    unsigned char *sb = smem + (size_t)stage * PL::STAGE;
-                    const size_t s0 = (size_t)d.x * D.n_chan + d.y;
-                    bulk_copy_g2s(sb + lane * PL::SLOT_D, D.vis + 2 * s0, d.z * 32u, full + stage);
-                    if constexpr (M16)
-                        bulk_copy_g2s(sb + NW * PL::SLOT_D + lane * PL::SLOT_M, D.model16 + s0, d.z * 16u, full + stage);
-                    else
-                        bulk_copy_g2s(sb + NW * PL::SLOT_D + lane * PL::SLOT_M, D.model + 2 * s0, d.z * 32u, full + stage);
-                    bulk_copy_g2s(sb + NW * (PL::SLOT_D + PL::SLOT_M) + lane * PL::SLOT_W, D.weight + s0, d.z * 16u,
-                                  full + stage);
-                }
-            }
+    // the copy this lane issues for each step: segment `hseg`, kind `kind`
+    const int hseg = lane >> 3, kind = lane & 7;
+    const bool copier = hseg < H && kind < NCOPY;
+    const unsigned char *cbase;
+    uint32_t cdst, ces;
+    {
+        const unsigned char *tb_n = reinterpret_cast<const unsigned char *>(Tn.tab);
+        const unsigned char *tb_o = reinterpret_cast<const unsigned char *>(To.tab);
+        const uint32_t seg_off = hseg * P.slot_bytes;
+        switch (kind) {
+        case 0: cbase = reinterpret_cast<const unsigned char *>(D.vis); cdst = seg_off; ces = 32; break;
+        case 1: cbase = M16 ? reinterpret_cast<const unsigned char *>(D.model16) : reinterpret_cast<const unsigned char *>(D.model);
+                cdst = seg_off + P.off_m; ces = MB; break;
+        case 2: cbase = reinterpret_cast<const unsigned char *>(D.weight); cdst = seg_off + P.off_w; ces = 16; break;
+        case 3: cbase = tb_n; cdst = seg_off + P.off_jn; ces = ESN; break;
+        case 4: cbase = tb_n; cdst = seg_off + P.off_jn + P.jn_cap * ESN; ces = ESN; break;
+        case 5: cbase = tb_o; cdst = seg_off + P.off_jo; ces = ESO; break;
+        default: cbase = tb_o; cdst = seg_off + P.off_jo + P.jo_cap * ESO; ces = ESO; break;
         }
-        if (!ok) {
-            if (lane == 0) atomicExch(P.err, 1);
-            // let copies already issued land before the CTA leaves (bounded)
-            for (uint32_t k = (it >= NS ? it - NS : 0); k < it; ++k)
-                mbar_wait_bounded(full + (k % NS), (k / NS) & 1u, WAIT_LIMIT_NS);
-        }
-        return;
     }
 
-    // ------------------------------ consumers ------------------------------
-    SampleIdx ix;
+    const long n_units = a.order == 0 ? (long)D.n_row : (long)D.n_strips * a.n_chunks;
+    const long stride = (long)gridDim.x * NW;
+    Cursor ck, pf;                 // compute cursor, prefetch cursor
+    ck.u = (long)blockIdx.x * NW + warp;
+    cursor_unit<H>(a, ck, n_units);
+    if (ck.u < n_units && ck.len == 0) cursor_next<H>(a, ck, n_units, stride);
+    pf = ck;
+    uint32_t n_issued = 0;
+    int is_stage = 0;              // stage of the next issue
+
+    // issue the copies of the step under cursor k into the next stage
+    auto issue = [&](const Cursor &k) {
+        const int stage = is_stage;
+        // every lane describes segment h = lane >> 3 (lanes of a segment agree)
+        SlotDesc d;
+        d.row = -1; d.cc = 0; d.nch = 0; d.live = 0;
+        d.p = 0; d.q = 0; d.tn = 0; d.pad0 = 0; d.fn0 = 0; d.fo0 = 0; d.scale = 1.f; d.pad1 = 0;
+        int cn = 0, co = 0, to = 0;
+        const int seg = k.i * H + hseg;
+        if (hseg < H && seg < k.n_seg) {
+            d.row = a.order == 0 ? (int)k.u : __ldg(D.strip_rows + k.beg + seg);
+            d.cc = a.order == 0 ? seg * 32 : k.c0;
+            d.nch = min(32, D.n_chan - d.cc);
+            const int4 ri = __ldg(P.row_info + d.row);
+            if (ri.z >= 0 && __ldg(P.chunk_active + (size_t)ri.z * a.n_chunks + d.cc / 32)) {
+                const int4 ci = __ldg(P.chunk_info + d.cc / 32);
+                d.live = 1;
+                d.p = ri.x; d.q = ri.y; d.tn = ri.z; to = ri.w;
+                d.fn0 = ci.x; cn = ci.y;
+                d.fo0 = ci.z; co = ci.w;
+                if constexpr (M16) d.scale = __ldg(D.bl_scale + __ldg(D.rows + d.row).w);
+            }
+        }
+        uint32_t seg_bytes = 0;
+        if (d.live) {
+            seg_bytes = (uint32_t)d.nch * (32u + MB + 16u) + 2u * cn * ESN;
+            if constexpr (OK_ != KIND_NONE) seg_bytes += 2u * co * ESO;
+        }
+        // total over the step's segments: lane 8h holds segment h
+        uint32_t total = 0;
+#pragma unroll
+        for (int h = 0; h < H; ++h) total += __shfl_sync(0xffffffffu, seg_bytes, 8 * h);
+        if (kind == 0 && hseg < H) desc[stage * H + hseg] = d;
+        __syncwarp();
+        if (lane == 0) mbar_arrive_expect_tx(full + stage, total);
+        __syncwarp();
+        if (copier && d.live) {
+            size_t idx;
+            uint32_t n;
+            if (kind < 3) { idx = (size_t)d.row * D.n_chan + d.cc; n = d.nch; }
+            else if (kind < 5) { idx = ((size_t)d.tn * n_ant + (kind == 3 ? d.p : d.q)) * Tn.n_fint + d.fn0; n = cn; }
+            else { idx = ((size_t)to * n_ant + (kind == 5 ? d.p : d.q)) * To.n_fint + d.fo0; n = co; }
+            bulk_copy_g2s(wbase + (size_t)stage * H * P.slot_bytes + cdst, cbase + idx * ces, n * ces, full + stage);
+        }
+        ++n_issued;
+        if (++is_stage == P.ns) is_stage = 0;
+    };
+
+    // prime the ring
+    for (int s = 0; s < P.ns - 1 && pf.u < n_units; ++s) {
+        issue(pf);
+        cursor_next<H>(a, pf, n_units, stride);
+    }
+
     Acc<KR, KAHAN> Ap, Aq;
     Ap.zero();
     Aq.zero();
-    uint32_t it = 0;
-    for (long g = blockIdx.x; g < n_groups; g += gridDim.x) {
-        int row0, c0, beg, len;
-        unit_info(a, g * NW + lane, n_units, row0, c0, beg, len);
-        if (lane >= NW) len = 0;
-        const int steps = __reduce_max_sync(0xffffffffu, len);
-        int cur_key = -1, p = 0, q = 0;
-        for (int i = 0; i < steps; ++i, ++it) {
-            const int stage = it % NS;
-            const uint32_t par = (it / NS) & 1u;
-            if (!mbar_wait_bounded(full + stage, par, WAIT_LIMIT_NS)) {
-                if (lane == 0) atomicExch(P.err, 1);
-                return;
-            }
-            const int4 d = desc[stage * NW + warp];
-            if (d.w) {
-                const int4 meta = __ldg(D.rows + d.x);
-                p = meta.x;
-                q = meta.y;
-                const int c = d.y + lane;
-                const bool in_range = lane < d.z;
-                sample_index<SIMPLE>(a, meta.z, c, in_range, ix);
-                const int key = in_range ? ix.tn * Tn.n_fint + ix.fn : -1;
-                if (__any_sync(0xffffffffu, cur_key >= 0 && key != cur_key)) {
-                    const unsigned m = __match_any_sync(0xffffffffu, cur_key);
-                    const unsigned seg_end = 32 - __clz(m);
-                    const bool head = lane == __ffs(m) - 1;
-                    const bool live = cur_key >= 0 && __ldg(a.active + cur_key);
-                    flush_side<KR, KG, KAHAN, Lay>(Ap, cur_key, p, lane, seg_end, head, live, a.acc, C.n_ant);
-                    flush_side<KR, KG, KAHAN, Lay>(Aq, cur_key, q, lane, seg_end, head, live, a.acc, C.n_ant);
-                }
-                cur_key = key;
-                bool ok = in_range && __ldg(a.active + key);
-                if (ok && D.flag) ok = __ldg(D.flag + (size_t)d.x * D.n_chan + c) == 0;
-                if (ok) {
-                    const unsigned char *sb = smem + (size_t)stage * PL::STAGE;
-                    const float4 *sd = reinterpret_cast<const float4 *>(sb + warp * PL::SLOT_D) + 2 * lane;
-                    const J2 Dm = j_from(sd[0], sd[1]);
-                    J2 M;
-                    if constexpr (M16) {
-                        const uint4 h = reinterpret_cast<const uint4 *>(sb + NW * PL::SLOT_D + warp * PL::SLOT_M)[lane];
-                        M = load_model16(h, __ldg(D.bl_scale + meta.w));
-                    } else {
-                        const float4 *sm = reinterpret_cast<const float4 *>(sb + NW * PL::SLOT_D + warp * PL::SLOT_M) + 2 * lane;
-                        M = j_from(sm[0], sm[1]);
-                    }
-                    const float4 w = reinterpret_cast<const float4 *>(sb + NW * (PL::SLOT_D + PL::SLOT_M) + warp * PL::SLOT_W)[lane];
-                    sample_contrib<TS, LK, RK, SIMPLE, KAHAN>(a, ix, p, q, Dm, M, w, Ap, Aq);
-                }
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(empty + stage);
+    uint32_t n_done = 0;
+    int stage = 0;                 // stage of the step being computed
+    uint32_t phase = 0;            // parity of that stage's current use
+    int cur_key = -1, p = 0, q = 0;
+    bool failed = false;
+    while (ck.u < n_units) {
+        if (pf.u < n_units) {
+            issue(pf);
+            cursor_next<H>(a, pf, n_units, stride);
         }
-        // end of the unit
-        if (__any_sync(0xffffffffu, cur_key >= 0)) {
-            const unsigned m = __match_any_sync(0xffffffffu, cur_key);
-            const unsigned seg_end = 32 - __clz(m);
-            const bool head = lane == __ffs(m) - 1;
-            const bool live = cur_key >= 0 && __ldg(a.active + cur_key);
-            flush_side<KR, KG, KAHAN, Lay>(Ap, cur_key, p, lane, seg_end, head, live, a.acc, C.n_ant);
-            flush_side<KR, KG, KAHAN, Lay>(Aq, cur_key, q, lane, seg_end, head, live, a.acc, C.n_ant);
+        if (!mbar_wait_bounded(full + stage, phase, WAIT_LIMIT_NS)) { failed = true; break; }
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            const SlotDesc d = desc[stage * H + h];
+            if (!d.live) continue;
+            p = d.p;
+            q = d.q;
+            const int c = d.cc + lane;
+            const bool in_range = lane < d.nch;
+            int fn = 0, fo = 0;
+            if (in_range) {
+                fn = P.stage_fmap ? sfn[c] : __ldg(Tn.f_map + c);
+                if constexpr (OK_ != KIND_NONE) fo = P.stage_fmap ? sfo[c] : __ldg(To.f_map + c);
+            }
+            const int key = in_range ? d.tn * Tn.n_fint + fn : -1;
+            if (__any_sync(0xffffffffu, cur_key >= 0 && key != cur_key)) {
+                const unsigned m = __match_any_sync(0xffffffffu, cur_key);
+                const unsigned seg_end = 32 - __clz(m);
+                const bool head = lane == __ffs(m) - 1;
+                const bool live = cur_key >= 0 && __ldg(a.active + cur_key);
+                flush_side<KR, KG, KAHAN, Lay>(Ap, cur_key, p, lane, seg_end, head, live, a.acc, n_ant);
+                flush_side<KR, KG, KAHAN, Lay>(Aq, cur_key, q, lane, seg_end, head, live, a.acc, n_ant);
+            }
+            cur_key = key;
+            bool ok = in_range && __ldg(a.active + key);
+            if (ok && D.flag) ok = __ldg(D.flag + (size_t)d.row * D.n_chan + c) == 0;
+            if (ok) {
+                const unsigned char *sb = wbase + ((size_t)stage * H + h) * P.slot_bytes;
+                const float4 *sd = reinterpret_cast<const float4 *>(sb) + 2 * lane;
+                const J2 Dm = j_from(sd[0], sd[1]);
+                J2 M;
+                if constexpr (M16) M = load_model16(reinterpret_cast<const uint4 *>(sb + P.off_m)[lane], d.scale);
+                else {
+                    const float4 *sm = reinterpret_cast<const float4 *>(sb + P.off_m) + 2 * lane;
+                    M = j_from(sm[0], sm[1]);
+                }
+                const float4 w = reinterpret_cast<const float4 *>(sb + P.off_w)[lane];
+                const J2 Gp = smem_jones<GK>(sb + P.off_jn, fn - d.fn0);
+                const J2 Gq = smem_jones<GK>(sb + P.off_jn + P.jn_cap * ESN, fn - d.fn0);
+                J2 Op, Oq;
+                if constexpr (OK_ != KIND_NONE) {
+                    Op = smem_jones<OK_>(sb + P.off_jo, fo - d.fo0);
+                    Oq = smem_jones<OK_>(sb + P.off_jo + P.jo_cap * ESO, fo - d.fo0);
+                } else {
+                    Op = j_identity();
+                    Oq = Op;
+                }
+                sample_math<TS, LK, RK, KAHAN>(Op, Gp, Op, Oq, Gq, Oq, Dm, M, w, Ap, Aq);
+            }
+        }
+        __syncwarp();
+        ++n_done;
+        if (++stage == P.ns) { stage = 0; phase ^= 1u; }
+        const long u_prev = ck.u;
+        cursor_next<H>(a, ck, n_units, stride);
+        if (ck.u != u_prev) {
+            if (__any_sync(0xffffffffu, cur_key >= 0)) {
+                // end of the unit
+                const unsigned m = __match_any_sync(0xffffffffu, cur_key);
+                const unsigned seg_end = 32 - __clz(m);
+                const bool head = lane == __ffs(m) - 1;
+                const bool live = cur_key >= 0 && __ldg(a.active + cur_key);
+                flush_side<KR, KG, KAHAN, Lay>(Ap, cur_key, p, lane, seg_end, head, live, a.acc, n_ant);
+                flush_side<KR, KG, KAHAN, Lay>(Aq, cur_key, q, lane, seg_end, head, live, a.acc, n_ant);
+            }
+            cur_key = -1;
         }
     }
+    if (failed) {
+        if (lane == 0) atomicExch(P.err, 1);
+        // let this warp's copies in flight land before it leaves (bounded)
+        for (uint32_t k = n_done; k < n_issued; ++k) {
+            mbar_wait_bounded(full + stage, phase, WAIT_LIMIT_NS);
+            if (++stage == P.ns) { stage = 0; phase ^= 1u; }
+        }
+    }
+}
+
+// Static per-row information of a term solve: {p, q, tn, to} with tn = -1 for
+// rows without an unflagged cross-correlation sample.
+static __global__ void row_info_kernel(const Data D, const uint8_t *row_live, const DevTerm tn, const DevTerm to,
+                                       int has_o, int4 *out)
+{
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= D.n_row) return;
+    const int4 meta = D.rows[i];
+    const int t = meta.z;
+    int4 r;
+    r.x = meta.x;
+    r.y = meta.y;
+    r.z = row_live[i] ? tn.t_map[t] : -1;
+    r.w = has_o ? to.t_map[t] : 0;
+    out[i] = r;
 }
 
 // chunk_active[tint][chunk] = some interval bin of the solved term touched by this

@@ -196,6 +196,112 @@ const char *qc_last_error(const qc_ctx *c);
 /* Library version string. */
 const char *qc_version(void);
 
+
+/* ------------------------------------------------------------------------ */
+/* Batched solves of many independent solution intervals                     */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * A batch of independent calibration problems, each one solution interval
+ * of one diagonal complex gain term (Section 2.3, last paragraph: solution
+ * intervals are solved independently of each other).  Problem i owns rows
+ * [row_offset[i], row_offset[i+1]) and samples [vis_offset[i], vis_offset[i+1])
+ * of the concatenated arrays, laid out [row][chan][4] with its own channel
+ * count n_chan[i] (so vis_offset[i+1] - vis_offset[i] = rows_i * n_chan[i]),
+ * and n_ant[i] antennas; ant1/ant2 are antenna indices local to the problem.
+ *   data, model : complex64; weight: float32 (per correlation); flag: uint8
+ *                 per sample or NULL; all in `memory`.
+ *   row_offset, vis_offset, n_chan, n_ant, ant1, ant2 : HOST arrays.
+ *   model_fp16  : as in qc_problem (per-baseline scales, compensated sums).
+ * Gains of problem i occupy entries [gain_offset_i, gain_offset_i + n_ant[i])
+ * of a [sum n_ant][2] complex64 array (g_XX, g_YY), gain_offset_i being the
+ * running sum of n_ant.
+ */
+typedef struct qc_batch qc_batch;
+
+typedef struct {
+    int32_t n_prob;
+    const int64_t *row_offset;   /* [n_prob + 1] */
+    const int64_t *vis_offset;   /* [n_prob + 1] */
+    const int32_t *n_chan;       /* [n_prob] */
+    const int32_t *n_ant;        /* [n_prob], 2 .. QC_BATCH_MAX_ANT */
+    const void *data, *model;
+    const float *weight;
+    const uint8_t *flag;
+    const int32_t *ant1, *ant2;  /* [total rows] */
+    int32_t memory;
+    int32_t model_fp16;
+} qc_batch_problem;
+
+#define QC_BATCH_MAX_ANT 256
+
+#define QC_SCHED_AUTO     0      /* autotuned (or LPT when not tuned)                   */
+#define QC_SCHED_LPT      1      /* longest problem first from a shared work counter    */
+#define QC_SCHED_STATIC   2      /* problem i -> CTA i mod grid, in index order         */
+
+typedef struct {
+    int32_t max_iter;            /* N_max of Algorithm 1                                 */
+    double tol;                  /* per-problem relative gain change to stop             */
+    int32_t damping_mode;        /* QC_DAMP_CONST or QC_DAMP_ALTERNATE                   */
+    double damping;
+    void *stream;                /* cudaStream_t or NULL                                 */
+    int32_t threads;             /* threads per CTA (0: tuned or 256)                    */
+    int32_t ctas_per_sm;         /* resident CTAs per SM (0: tuned or occupancy)          */
+    int32_t schedule;            /* QC_SCHED_*                                           */
+    int32_t use_graph;           /* 1: replay the persistent launch as a CUDA graph       */
+} qc_batch_opts;
+
+typedef struct {
+    double ms;                   /* device time of the solve (CUDA events)               */
+    int64_t vis_iters;           /* sum over problems of samples x iterations            */
+    int64_t bytes;               /* algorithmic bytes read (data passes)                 */
+    int32_t n_iter_max;
+    double mean_iters;
+    int32_t threads, ctas_per_sm, schedule, grid;   /* launch configuration used          */
+} qc_batch_stats;
+
+/* Validate and stage a batch (host arrays copied, device arrays borrowed). */
+int qc_batch_create(const qc_batch_problem *p, qc_batch **out);
+
+/*
+ * Solve every problem of the batch with Algorithm 1 in one persistent
+ * kernel launch: each CTA takes whole problems (longest first, or as the
+ * schedule says) and iterates them to convergence or max_iter on chip;
+ * per iteration it forms the residual of every sample, accumulates the
+ * per-antenna diagonal JHJ / JHr blocks (Eq. jhj_entry_simplified,
+ * Eq. jhr_entry_simplified) in shared memory and updates the gains with an
+ * FP64 block solve (Eq. update).
+ *   gains      : in/out [sum n_ant][2] complex64; read as g_0.
+ *   gain_flags : out [sum n_ant] int8 or NULL (1: no data for the antenna).
+ *   iters      : out [n_prob] int32 or NULL.
+ *   mem        : where gains/gain_flags/iters live (QC_MEM_HOST or DEVICE).
+ */
+int qc_batch_solve(qc_batch *b, void *gains, int8_t *gain_flags, int32_t *iters, int32_t mem,
+                   const qc_batch_opts *o, qc_batch_stats *stats);
+
+/*
+ * Autotuner: time the batch solve (from unit gains, `base` options, results
+ * discarded) for every candidate launch shape -- threads per CTA in
+ * {128, 256, 512}, resident CTAs per SM in {1, 2, 4}, schedule in {LPT,
+ * static} -- and keep the fastest for later solves with QC_SCHED_AUTO /
+ * threads = 0.  Results are cached per shape class of the batch (problem
+ * count and size histogram).  best (nullable) receives the chosen shape and
+ * its time; `n_tried` (nullable) the number of candidates timed.
+ */
+int qc_batch_autotune(qc_batch *b, const qc_batch_opts *base, qc_batch_stats *best, int32_t *n_tried);
+
+/*
+ * Per-problem chi^2 (Eq. min) at the given gains: chi2 [n_prob] FP64, host
+ * or device per `mem`.
+ */
+int qc_batch_residual(qc_batch *b, const void *gains, int32_t mem, double *chi2);
+
+/* Release a batch.  NULL-safe. */
+void qc_batch_destroy(qc_batch *b);
+
+/* Message of the last failed call on `b` ("" if none); NULL: last failed qc_batch_create. */
+const char *qc_batch_last_error(const qc_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,831 @@
+// qc_batch.cu -- persistent batched solver: thousands of independent solution
+// intervals (diagonal gains, one interval each) solved in one kernel launch.
+//
+// Each CTA takes whole problems (longest first from a shared work counter, or
+// a static schedule) and runs Algorithm 1 of arxiv 2412.10072 (Section 4.3)
+// on chip: per iteration one pass over the problem's samples forms the
+// residual r = D - G_p M G_q^H and accumulates the per-antenna diagonal JHJ and
+// JHr blocks (Eq. jhj_entry_simplified, Eq. jhr_entry_simplified, including the
+// conjugate baselines) in shared memory, then one thread per antenna solves its
+// block in FP64 and updates its gain (Eq. update); the FP64 relative gain change
+// of the problem decides convergence.  No grid-wide synchronisation and no
+// spin-waits: the only shared state is an atomic work counter.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/qc.h"
+#include "qc_jones.cuh"
+
+namespace {
+
+using namespace qc;
+
+thread_local std::string g_batch_create_error;
+
+struct BProb {
+    long long vis_off, row_off;
+    int n_rows, n_chan, n_ant, gain_off;
+    long long n_unflag;          // unflagged samples (algorithmic bytes)
+};
+
+struct BatchArgs {
+    const BProb *probs;
+    int n_prob;
+    const int *order;            // schedule order [n_prob]
+    int *queue;                  // work counter (LPT)
+    int schedule;                // QC_SCHED_LPT / QC_SCHED_STATIC
+    const float4 *vis, *model;
+    const uint4 *model16;
+    const float *row_scale;      // per-row model scale (FP16 model): the scale of the row's baseline
+    const float4 *weight;
+    const uint8_t *flag;
+    const int2 *ants;            // [rows] (p, q), local antenna indices
+    float2 *gains;               // [sum n_ant][2]
+    int8_t *gain_flags;          // [sum n_ant] or null
+    int *iters;                  // [n_prob] or null
+    int max_iter, damping_mode;
+    double damping, tol;
+    int max_ant;
+    unsigned long long *vis_iters, *bytes;
+};
+
+// Sum v over the run of equal keys that contains this lane; the run's first lane gets it.
+__device__ __forceinline__ float run_sum(float v, int lane, unsigned run_end)
+{
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const float o = __shfl_down_sync(0xffffffffu, v, d);
+        if (lane + d < (int)run_end) v += o;
+    }
+    return v;
+}
+
+template <bool M16>
+__global__ void __launch_bounds__(512) batch_kernel(const BatchArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    double2 *g64 = reinterpret_cast<double2 *>(smem);                          // [max_ant][2] (16-byte aligned)
+    float *acc = reinterpret_cast<float *>(g64 + a.max_ant * 2);              // [max_ant][6]
+    float2 *g32 = reinterpret_cast<float2 *>(acc + a.max_ant * 6);            // [max_ant][2]
+    __shared__ double red[2][32];
+    __shared__ int s_prob, s_done;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, n_warps = blockDim.x >> 5;
+    int static_k = 0;
+
+    for (;;) {
+        if (tid == 0) {
+            int idx;
+            if (a.schedule == QC_SCHED_STATIC) idx = blockIdx.x + (static_k++) * gridDim.x;
+            else idx = atomicAdd(a.queue, 1);
+            s_prob = idx < a.n_prob ? a.order[idx] : -1;
+        }
+        __syncthreads();
+        const int pi = s_prob;
+        if (pi < 0) break;
+        const BProb P = a.probs[pi];
+        const int na = P.n_ant, nc = P.n_chan;
+        for (int i = tid; i < na * 2; i += blockDim.x) {
+            const float2 g = a.gains[(size_t)P.gain_off * 2 + i];
+            g32[i] = g;
+            g64[i] = make_double2(g.x, g.y);
+        }
+        // tile of a warp step: rows x channels
+        const bool wide = nc >= 32;
+        const int rpi = wide ? 1 : 32 / nc;                 // rows per warp step
+        const int chunks = wide ? (nc + 31) / 32 : 1;
+        const int lr = wide ? 0 : lane / nc, lc = wide ? lane : lane % nc;
+        const bool lane_ok = wide || lane < rpi * nc;
+        const long n_steps = wide ? (long)P.n_rows * chunks : ((long)P.n_rows + rpi - 1) / rpi;
+        int k = 0;
+        for (k = 1; k <= a.max_iter; ++k) {
+            for (int i = tid; i < na * 6; i += blockDim.x) acc[i] = 0.f;
+            __syncthreads();
+            for (long t = warp; t < n_steps; t += n_warps) {
+                int row, c;
+                if (wide) { row = (int)(t / chunks); c = (int)(t % chunks) * 32 + lane; }
+                else { row = (int)t * rpi + lr; c = lc; }
+                const bool in = lane_ok && row < P.n_rows && c < nc;
+                int p = -1, q = -1;
+                float v[12];
+#pragma unroll
+                for (int i = 0; i < 12; ++i) v[i] = 0.f;
+                if (in) {
+                    const int2 pq = __ldg(a.ants + P.row_off + row);
+                    p = pq.x;
+                    q = pq.y;
+                    const size_t s = (size_t)P.vis_off + (size_t)row * nc + c;
+                    bool ok = p != q;
+                    if (ok && a.flag) ok = __ldg(a.flag + s) == 0;
+                    if (ok) {
+                        const J2 D = j_from(__ldg(a.vis + 2 * s), __ldg(a.vis + 2 * s + 1));
+                        J2 M;
+                        if constexpr (M16) {
+                            const uint4 h = __ldg(a.model16 + s);
+                            const float sc = __ldg(a.row_scale + P.row_off + row);
+                            M.a = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.x)), sc);
+                            M.b = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.y)), sc);
+                            M.c = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.z)), sc);
+                            M.d = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.w)), sc);
+                        } else {
+                            M = j_from(__ldg(a.model + 2 * s), __ldg(a.model + 2 * s + 1));
+                        }
+                        const float4 w = __ldg(a.weight + s);
+                        const float2 gp0 = g32[2 * p], gp1 = g32[2 * p + 1];
+                        const float2 gq0 = g32[2 * q], gq1 = g32[2 * q + 1];
+                        // X = M diag(conj g_q), V = diag(g_p) X, r = D - V
+                        const float2 X00 = cmulc(M.a, gq0), X01 = cmulc(M.b, gq1);
+                        const float2 X10 = cmulc(M.c, gq0), X11 = cmulc(M.d, gq1);
+                        const float2 r00 = csub(D.a, cmul(gp0, X00)), r01 = csub(D.b, cmul(gp0, X01));
+                        const float2 r10 = csub(D.c, cmul(gp1, X10)), r11 = csub(D.d, cmul(gp1, X11));
+                        // p side: parameter k touches row k: E[(k,j), k] = X[k][j]
+                        v[0] = fmaf(w.x, cnorm2(X00), w.y * cnorm2(X01));
+                        v[1] = fmaf(w.z, cnorm2(X10), w.w * cnorm2(X11));
+                        float2 j0 = cfma_conj(X01, cscale(r01, w.y), cfma_conj(X00, cscale(r00, w.x), make_float2(0.f, 0.f)));
+                        float2 j1 = cfma_conj(X11, cscale(r11, w.w), cfma_conj(X10, cscale(r10, w.z), make_float2(0.f, 0.f)));
+                        v[2] = j0.x; v[3] = j0.y; v[4] = j1.x; v[5] = j1.y;
+                        // q side through the conjugate baseline: Y = M^H diag(conj g_p), r' = r^H, w' = P w
+                        const float2 Y00 = cmulc(cconj(M.a), gp0), Y01 = cmulc(cconj(M.c), gp1);
+                        const float2 Y10 = cmulc(cconj(M.b), gp0), Y11 = cmulc(cconj(M.d), gp1);
+                        v[6] = fmaf(w.x, cnorm2(Y00), w.z * cnorm2(Y01));
+                        v[7] = fmaf(w.y, cnorm2(Y10), w.w * cnorm2(Y11));
+                        float2 k0 = cfma_conj(Y01, cscale(cconj(r10), w.z), cfma_conj(Y00, cscale(cconj(r00), w.x), make_float2(0.f, 0.f)));
+                        float2 k1 = cfma_conj(Y11, cscale(cconj(r11), w.w), cfma_conj(Y10, cscale(cconj(r01), w.y), make_float2(0.f, 0.f)));
+                        v[8] = k0.x; v[9] = k0.y; v[10] = k1.x; v[11] = k1.y;
+                    }
+                }
+                // reduce over runs of equal antenna within the warp, heads add into shared memory
+                const int kp = in ? p : -1, kq = in ? q : -1;
+#pragma unroll
+                for (int side = 0; side < 2; ++side) {
+                    const int key = side == 0 ? kp : kq;
+                    const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+                    const bool head = lane == 0 || key != prev;
+                    const unsigned heads = __ballot_sync(0xffffffffu, head);
+                    const unsigned after = heads & ~((2u << lane) - 1u);
+                    const unsigned run_end = after ? (unsigned)(__ffs(after) - 1) : 32u;
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) {
+                        const float sum = run_sum(v[side * 6 + i], lane, run_end);
+                        if (head && key >= 0) atomicAdd(acc + key * 6 + i, sum);
+                    }
+                }
+            }
+            __syncthreads();
+            // FP64 per-antenna solve and update (diagonal blocks: off-diagonal terms vanish)
+            const double alpha = a.damping_mode == QC_DAMP_ALTERNATE ? ((k % 2 == 0) ? 0.5 : 1.0)
+                                                                      : (a.damping > 0 ? a.damping : 1.0);
+            double num = 0, den = 0;
+            for (int ant = tid; ant < na; ant += blockDim.x) {
+                const double h0 = acc[ant * 6], h1 = acc[ant * 6 + 1];
+                const double hmax = fmax(h0, h1), hmin = fmin(h0, h1);
+                const bool singular = !(h0 + h1 > 0) || !(hmin / hmax >= 1e-12);
+                double2 d0 = make_double2(0, 0), d1 = d0;
+                if (!singular) {
+                    d0 = make_double2(alpha * acc[ant * 6 + 2] / h0, alpha * acc[ant * 6 + 3] / h0);
+                    d1 = make_double2(alpha * acc[ant * 6 + 4] / h1, alpha * acc[ant * 6 + 5] / h1);
+                }
+                double2 G0 = g64[2 * ant], G1 = g64[2 * ant + 1];
+                G0.x += d0.x; G0.y += d0.y; G1.x += d1.x; G1.y += d1.y;
+                g64[2 * ant] = G0;
+                g64[2 * ant + 1] = G1;
+                g32[2 * ant] = make_float2((float)G0.x, (float)G0.y);
+                g32[2 * ant + 1] = make_float2((float)G1.x, (float)G1.y);
+                if (a.gain_flags) a.gain_flags[P.gain_off + ant] = singular ? 1 : 0;
+                num += d0.x * d0.x + d0.y * d0.y + d1.x * d1.x + d1.y * d1.y;
+                den += G0.x * G0.x + G0.y * G0.y + G1.x * G1.x + G1.y * G1.y;
+            }
+            for (int d = 16; d > 0; d >>= 1) {
+                num += __shfl_down_sync(0xffffffffu, num, d);
+                den += __shfl_down_sync(0xffffffffu, den, d);
+            }
+            if (lane == 0) { red[0][warp] = num; red[1][warp] = den; }
+            __syncthreads();
+            if (tid == 0) {
+                double tn = 0, td = 0;
+                for (int i = 0; i < n_warps; ++i) { tn += red[0][i]; td += red[1][i]; }
+                const double delta = td > 0 ? sqrt(tn / td) : 0.0;
+                s_done = delta < a.tol ? 1 : 0;
+            }
+            __syncthreads();
+            if (s_done) break;
+        }
+        const int done_iters = k > a.max_iter ? a.max_iter : k;
+        for (int i = tid; i < na * 2; i += blockDim.x) a.gains[(size_t)P.gain_off * 2 + i] = g32[i];
+        if (tid == 0) {
+            if (a.iters) a.iters[pi] = done_iters;
+            const unsigned long long ns = (unsigned long long)P.n_rows * nc;
+            atomicAdd(a.vis_iters, ns * done_iters);
+            const unsigned long long b = (a.flag ? ns : 0ull) + (unsigned long long)P.n_unflag * (M16 ? 64ull : 80ull);
+            atomicAdd(a.bytes, b * done_iters);
+        }
+        __syncthreads();
+    }
+}
+
+// chi^2 of every problem at the given gains (one CTA per problem, FP64 block sums)
+template <bool M16>
+__global__ void __launch_bounds__(256) batch_chi2_kernel(const BatchArgs a, double *chi2)
+{
+    __shared__ double red[8];
+    const int pi = blockIdx.x;
+    const BProb P = a.probs[pi];
+    const long n = (long)P.n_rows * P.n_chan;
+    double tot = 0;
+    for (long i = threadIdx.x; i < n; i += blockDim.x) {
+        const int row = (int)(i / P.n_chan);
+        const int2 pq = __ldg(a.ants + P.row_off + row);
+        const size_t s = (size_t)P.vis_off + i;
+        if (pq.x == pq.y || (a.flag && __ldg(a.flag + s))) continue;
+        const J2 D = j_from(__ldg(a.vis + 2 * s), __ldg(a.vis + 2 * s + 1));
+        J2 M;
+        if constexpr (M16) {
+            const uint4 h = __ldg(a.model16 + s);
+            const float sc = __ldg(a.row_scale + P.row_off + row);
+            M.a = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.x)), sc);
+            M.b = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.y)), sc);
+            M.c = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.z)), sc);
+            M.d = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.w)), sc);
+        } else {
+            M = j_from(__ldg(a.model + 2 * s), __ldg(a.model + 2 * s + 1));
+        }
+        const float4 w = __ldg(a.weight + s);
+        const float2 *g = a.gains + (size_t)P.gain_off * 2;
+        const float2 gp0 = g[2 * pq.x], gp1 = g[2 * pq.x + 1], gq0 = g[2 * pq.y], gq1 = g[2 * pq.y + 1];
+        const float2 r00 = csub(D.a, cmul(gp0, cmulc(M.a, gq0))), r01 = csub(D.b, cmul(gp0, cmulc(M.b, gq1)));
+        const float2 r10 = csub(D.c, cmul(gp1, cmulc(M.c, gq0))), r11 = csub(D.d, cmul(gp1, cmulc(M.d, gq1)));
+        tot += (double)(w.x * cnorm2(r00)) + (double)(w.y * cnorm2(r01)) + (double)(w.z * cnorm2(r10)) +
+               (double)(w.w * cnorm2(r11));
+    }
+    for (int d = 16; d > 0; d >>= 1) tot += __shfl_down_sync(0xffffffffu, tot, d);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = tot;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0;
+        for (int i = 0; i < (int)blockDim.x / 32; ++i) t += red[i];
+        chi2[pi] = t;
+    }
+}
+
+__global__ void row_scale_kernel(const float4 *model, const int2 *ants, const long long *row_vis, const int *row_nc,
+                                 const int *row_bl, long n_rows, unsigned *bl_bits)
+{
+    for (long r = (long)blockIdx.x * blockDim.x + threadIdx.x; r < n_rows; r += (long)gridDim.x * blockDim.x) {
+        const int2 pq = ants[r];
+        if (pq.x == pq.y) continue;
+        float m = 0.f;
+        for (int c = 0; c < row_nc[r]; ++c) {
+            const size_t s = (size_t)row_vis[r] + c;
+            const float4 a = model[2 * s], b = model[2 * s + 1];
+            m = fmaxf(m, fmaxf(fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(a.z), fabsf(a.w))),
+                               fmaxf(fmaxf(fabsf(b.x), fabsf(b.y)), fmaxf(fabsf(b.z), fabsf(b.w)))));
+        }
+        if (!(m <= 3.0e38f)) m = 0.f;
+        atomicMax(bl_bits + row_bl[r], __float_as_uint(m));
+    }
+}
+
+__global__ void row_scale_fill(const int *row_bl, const unsigned *bl_bits, long n_rows, float *row_scale)
+{
+    for (long r = (long)blockIdx.x * blockDim.x + threadIdx.x; r < n_rows; r += (long)gridDim.x * blockDim.x) {
+        const float v = __uint_as_float(bl_bits[row_bl[r]]);
+        row_scale[r] = v > 0.f ? v : 1.f;
+    }
+}
+
+__global__ void pack16_rows_kernel(const float4 *model, const float *row_scale, const long long *row_vis,
+                                   const int *row_nc, long n_rows, uint4 *out)
+{
+    for (long r = blockIdx.x; r < n_rows; r += gridDim.x) {
+        const float inv = 1.f / row_scale[r];
+        for (int c = threadIdx.x; c < row_nc[r]; c += blockDim.x) {
+            const size_t s = (size_t)row_vis[r] + c;
+            const float4 a = model[2 * s], b = model[2 * s + 1];
+            __half2 h0 = __floats2half2_rn(a.x * inv, a.y * inv), h1 = __floats2half2_rn(a.z * inv, a.w * inv);
+            __half2 h2 = __floats2half2_rn(b.x * inv, b.y * inv), h3 = __floats2half2_rn(b.z * inv, b.w * inv);
+            uint4 o;
+            o.x = *reinterpret_cast<unsigned *>(&h0);
+            o.y = *reinterpret_cast<unsigned *>(&h1);
+            o.z = *reinterpret_cast<unsigned *>(&h2);
+            o.w = *reinterpret_cast<unsigned *>(&h3);
+            out[s] = o;
+        }
+    }
+}
+
+__global__ void unflag_count_kernel(const uint8_t *flag, const BProb *probs, const int2 *ants, int n_prob,
+                                    unsigned long long *out)
+{
+    const int pi = blockIdx.x;
+    if (pi >= n_prob) return;
+    const BProb P = probs[pi];
+    const long n = (long)P.n_rows * P.n_chan;
+    unsigned long long cnt = 0;
+    for (long i = threadIdx.x; i < n; i += blockDim.x) {
+        const int row = (int)(i / P.n_chan);
+        const int2 pq = ants[P.row_off + row];
+        if (pq.x != pq.y && !(flag && flag[P.vis_off + i])) ++cnt;
+    }
+    for (int d = 16; d > 0; d >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, d);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out + pi, cnt);
+}
+
+} // namespace
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+struct qc_batch {
+    int dev = 0, sm_count = 1;
+    cudaStream_t own_stream = nullptr;
+    int n_prob = 0, max_ant = 0;
+    long long n_rows = 0, n_vis = 0, total_ant = 0;
+    bool m16 = false, has_flag = false;
+    std::vector<void *> owned;
+    const float4 *vis = nullptr, *model = nullptr, *weight = nullptr;
+    const uint4 *model16 = nullptr;
+    const uint8_t *flag = nullptr;
+    float *row_scale = nullptr;
+    int2 *ants = nullptr;
+    BProb *probs = nullptr;
+    int *order_lpt = nullptr, *order_idx = nullptr, *queue = nullptr;
+    unsigned long long *counters = nullptr;
+    void *gstage = nullptr;       // device staging for host gains/flags/iters
+    std::vector<BProb> hprobs;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    struct Shape { int threads, per_sm, schedule; double ms; };
+    std::map<std::string, Shape> tuned;
+    std::string shape_key;
+    struct GraphKey { int threads, per_sm, schedule, max_iter, damping_mode; double damping, tol; bool m16;
+                      void *gains; void *flags; void *iters; cudaStream_t st; };
+    cudaGraphExec_t exec = nullptr;
+    GraphKey gkey;
+    std::string err;
+
+    qc_batch() { memset(&gkey, 0, sizeof gkey); }
+    ~qc_batch()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        for (void *p : owned) cudaFree(p);
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+        if (own_stream) cudaStreamDestroy(own_stream);
+    }
+    void *alloc(size_t bytes, cudaError_t *e)
+    {
+        void *p = nullptr;
+        *e = cudaMalloc(&p, std::max<size_t>(bytes, 16));
+        if (*e == cudaSuccess) owned.push_back(p);
+        return p;
+    }
+    int fail(int code, const std::string &m) { err = m; return code; }
+    int cuda_fail(cudaError_t e, const char *what)
+    {
+        err = std::string(what) + ": " + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? QC_ENOMEM : QC_ECUDA;
+    }
+};
+
+#define BCK(call)                                                   \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return b->cuda_fail(e_, #call);      \
+    } while (0)
+
+extern "C" int qc_batch_create(const qc_batch_problem *p, qc_batch **out)
+{
+    g_batch_create_error.clear();
+    auto bad = [](const char *m) { g_batch_create_error = m; return QC_EINVAL; };
+    if (!out) return bad("out is NULL");
+    *out = nullptr;
+    if (!p || p->n_prob < 1) return bad("empty batch");
+    if (!p->row_offset || !p->vis_offset || !p->n_chan || !p->n_ant || !p->ant1 || !p->ant2)
+        return bad("row_offset, vis_offset, n_chan, n_ant, ant1, ant2 are required (host arrays)");
+    if (!p->data || !p->model || !p->weight) return bad("data, model and weight are required");
+    if (p->memory != QC_MEM_HOST && p->memory != QC_MEM_DEVICE) return bad("memory must be QC_MEM_HOST or DEVICE");
+    std::unique_ptr<qc_batch> b(new qc_batch());
+    b->n_prob = p->n_prob;
+    b->m16 = p->model_fp16 != 0;
+    b->has_flag = p->flag != nullptr;
+    if (p->row_offset[0] != 0 || p->vis_offset[0] != 0) return bad("offsets must start at 0");
+    b->hprobs.resize(p->n_prob);
+    long long gain_off = 0;
+    for (int i = 0; i < p->n_prob; ++i) {
+        const long long r0 = p->row_offset[i], r1 = p->row_offset[i + 1];
+        const long long v0 = p->vis_offset[i], v1 = p->vis_offset[i + 1];
+        const int nc = p->n_chan[i], na = p->n_ant[i];
+        if (r1 < r0 || nc < 1 || na < 2 || na > QC_BATCH_MAX_ANT) return bad("invalid problem sizes");
+        if (v1 - v0 != (r1 - r0) * nc) return bad("vis_offset inconsistent with rows x n_chan");
+        if (r1 - r0 > (1LL << 30)) return bad("problem too large");
+        for (long long r = r0; r < r1; ++r)
+            if (p->ant1[r] < 0 || p->ant1[r] >= na || p->ant2[r] < 0 || p->ant2[r] >= na)
+                return bad("antenna index out of range");
+        BProb &P = b->hprobs[i];
+        P.vis_off = v0;
+        P.row_off = r0;
+        P.n_rows = (int)(r1 - r0);
+        P.n_chan = nc;
+        P.n_ant = na;
+        P.gain_off = (int)gain_off;
+        P.n_unflag = 0;
+        gain_off += na;
+        b->max_ant = std::max(b->max_ant, na);
+    }
+    b->n_rows = p->row_offset[p->n_prob];
+    b->n_vis = p->vis_offset[p->n_prob];
+    b->total_ant = gain_off;
+    cudaError_t e = cudaGetDevice(&b->dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, b->dev);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->own_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
+    if (e != cudaSuccess) { g_batch_create_error = std::string("CUDA init: ") + cudaGetErrorString(e); return QC_ECUDA; }
+    cudaStream_t st = b->own_stream;
+#define BALLOC(dst, T, n)                                                                    \
+    do {                                                                                     \
+        dst = (T *)b->alloc(sizeof(T) * (size_t)(n), &e);                                    \
+        if (e != cudaSuccess) { g_batch_create_error = "cudaMalloc failed"; return e == cudaErrorMemoryAllocation ? QC_ENOMEM : QC_ECUDA; } \
+    } while (0)
+#define BH2D(dst, src, bytes)                                                                \
+    do {                                                                                     \
+        e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);                             \
+        if (e != cudaSuccess) { g_batch_create_error = std::string("H2D: ") + cudaGetErrorString(e); return QC_ECUDA; } \
+    } while (0)
+    // rows: (p, q) and, for the FP16 model, the baseline id of each row
+    std::vector<int2> ants(b->n_rows);
+    for (long long r = 0; r < b->n_rows; ++r) ants[r] = make_int2(p->ant1[r], p->ant2[r]);
+    BALLOC(b->ants, int2, std::max<long long>(1, b->n_rows));
+    if (b->n_rows) BH2D(b->ants, ants.data(), sizeof(int2) * b->n_rows);
+    const size_t nv = (size_t)b->n_vis;
+    const float4 *model32 = nullptr;
+    if (p->memory == QC_MEM_DEVICE) {
+        b->vis = (const float4 *)p->data;
+        model32 = (const float4 *)p->model;
+        b->weight = (const float4 *)p->weight;
+        b->flag = p->flag;
+    } else {
+        float4 *v, *w, *m;
+        BALLOC(v, float4, 2 * nv);
+        BH2D(v, p->data, sizeof(float4) * 2 * nv);
+        BALLOC(m, float4, 2 * nv);
+        BH2D(m, p->model, sizeof(float4) * 2 * nv);
+        BALLOC(w, float4, nv);
+        BH2D(w, p->weight, sizeof(float4) * nv);
+        b->vis = v;
+        b->weight = w;
+        model32 = m;
+        if (p->flag) {
+            uint8_t *f;
+            BALLOC(f, uint8_t, nv);
+            BH2D(f, p->flag, nv);
+            b->flag = f;
+        }
+    }
+    BALLOC(b->probs, BProb, p->n_prob);
+    BH2D(b->probs, b->hprobs.data(), sizeof(BProb) * p->n_prob);
+    BALLOC(b->counters, unsigned long long, 2 + p->n_prob);
+    // unflagged samples per problem
+    e = cudaMemsetAsync(b->counters, 0, sizeof(unsigned long long) * (2 + p->n_prob), st);
+    if (e == cudaSuccess) {
+        unflag_count_kernel<<<p->n_prob, 256, 0, st>>>(b->flag, b->probs, b->ants, p->n_prob, b->counters + 2);
+        e = cudaGetLastError();
+    }
+    std::vector<unsigned long long> unf(p->n_prob);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(unf.data(), b->counters + 2, sizeof(unsigned long long) * p->n_prob,
+                                              cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { g_batch_create_error = std::string("flag counts: ") + cudaGetErrorString(e); return QC_ECUDA; }
+    for (int i = 0; i < p->n_prob; ++i) b->hprobs[i].n_unflag = (long long)unf[i];
+    BH2D(b->probs, b->hprobs.data(), sizeof(BProb) * p->n_prob);
+    if (b->m16) {
+        std::vector<long long> row_vis(b->n_rows);
+        std::vector<int> row_nc(b->n_rows), row_bl(b->n_rows);
+        std::map<long long, int> bl_id;
+        for (int i = 0; i < p->n_prob; ++i) {
+            const BProb &P = b->hprobs[i];
+            for (int r = 0; r < P.n_rows; ++r) {
+                const long long gr = P.row_off + r;
+                row_vis[gr] = P.vis_off + (long long)r * P.n_chan;
+                row_nc[gr] = P.n_chan;
+                const long long key = ((long long)i * QC_BATCH_MAX_ANT + ants[gr].x) * QC_BATCH_MAX_ANT + ants[gr].y;
+                auto it = bl_id.find(key);
+                if (it == bl_id.end()) it = bl_id.emplace(key, (int)bl_id.size()).first;
+                row_bl[gr] = it->second;
+            }
+        }
+        long long *d_row_vis;
+        int *d_row_nc, *d_row_bl;
+        unsigned *bits;
+        uint4 *m16;
+        BALLOC(d_row_vis, long long, std::max<long long>(1, b->n_rows));
+        BALLOC(d_row_nc, int, std::max<long long>(1, b->n_rows));
+        BALLOC(d_row_bl, int, std::max<long long>(1, b->n_rows));
+        BALLOC(bits, unsigned, std::max<size_t>(1, bl_id.size()));
+        BALLOC(b->row_scale, float, std::max<long long>(1, b->n_rows));
+        BALLOC(m16, uint4, nv);
+        if (b->n_rows) {
+            BH2D(d_row_vis, row_vis.data(), sizeof(long long) * b->n_rows);
+            BH2D(d_row_nc, row_nc.data(), sizeof(int) * b->n_rows);
+            BH2D(d_row_bl, row_bl.data(), sizeof(int) * b->n_rows);
+        }
+        e = cudaMemsetAsync(bits, 0, sizeof(unsigned) * std::max<size_t>(1, bl_id.size()), st);
+        if (e == cudaSuccess && b->n_rows) {
+            const int grid = (int)std::min<long long>(b->sm_count * 8LL, (b->n_rows + 255) / 256);
+            row_scale_kernel<<<grid, 256, 0, st>>>(model32, b->ants, d_row_vis, d_row_nc, d_row_bl, b->n_rows, bits);
+            row_scale_fill<<<grid, 256, 0, st>>>(d_row_bl, bits, b->n_rows, b->row_scale);
+            pack16_rows_kernel<<<(int)std::min<long long>(b->sm_count * 8LL, b->n_rows), 64, 0, st>>>(
+                model32, b->row_scale, d_row_vis, d_row_nc, b->n_rows, m16);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) { g_batch_create_error = std::string("fp16 packing: ") + cudaGetErrorString(e); return QC_ECUDA; }
+        b->model16 = m16;
+        if (p->memory == QC_MEM_HOST) {
+            auto it = std::find(b->owned.begin(), b->owned.end(), (void *)model32);
+            if (it != b->owned.end()) { cudaFree(*it); b->owned.erase(it); }
+        }
+        model32 = nullptr;
+    }
+    b->model = model32;
+    // schedules: longest problem first (samples), and index order
+    std::vector<int> lpt(p->n_prob), idx(p->n_prob);
+    std::iota(idx.begin(), idx.end(), 0);
+    lpt = idx;
+    std::stable_sort(lpt.begin(), lpt.end(), [&](int x, int y) {
+        return (long long)b->hprobs[x].n_rows * b->hprobs[x].n_chan > (long long)b->hprobs[y].n_rows * b->hprobs[y].n_chan;
+    });
+    BALLOC(b->order_lpt, int, p->n_prob);
+    BALLOC(b->order_idx, int, p->n_prob);
+    BALLOC(b->queue, int, 1);
+    BH2D(b->order_lpt, lpt.data(), sizeof(int) * p->n_prob);
+    BH2D(b->order_idx, idx.data(), sizeof(int) * p->n_prob);
+    BALLOC(b->gstage, unsigned char, (size_t)b->total_ant * 17 + sizeof(int) * p->n_prob + 64);
+    // shape class of the batch for the tuning cache: problem count and log2 size histogram
+    int hist[40] = { 0 };
+    for (const BProb &P : b->hprobs) {
+        const long long n = std::max(1LL, (long long)P.n_rows * P.n_chan);
+        hist[std::min(39, 63 - __builtin_clzll((unsigned long long)n))]++;
+    }
+    b->shape_key = std::to_string(p->n_prob) + (b->m16 ? "h" : "f");
+    for (int i = 0; i < 40; ++i) if (hist[i]) b->shape_key += ":" + std::to_string(i) + "x" + std::to_string(hist[i]);
+#undef BALLOC
+#undef BH2D
+    *out = b.release();
+    return QC_OK;
+}
+
+extern "C" void qc_batch_destroy(qc_batch *b) { delete b; }
+
+extern "C" const char *qc_batch_last_error(const qc_batch *b)
+{
+    return b ? b->err.c_str() : g_batch_create_error.c_str();
+}
+
+static BatchArgs batch_args(qc_batch *b)
+{
+    BatchArgs a;
+    memset(&a, 0, sizeof a);
+    a.probs = b->probs;
+    a.n_prob = b->n_prob;
+    a.vis = b->vis;
+    a.model = b->model;
+    a.model16 = b->model16;
+    a.row_scale = b->row_scale;
+    a.weight = b->weight;
+    a.flag = b->flag;
+    a.ants = b->ants;
+    a.max_ant = b->max_ant;
+    a.vis_iters = b->counters;
+    a.bytes = b->counters + 1;
+    return a;
+}
+
+static size_t batch_smem(const qc_batch *b)
+{
+    return (size_t)b->max_ant * (6 * sizeof(float) + 2 * sizeof(float2) + 2 * sizeof(double2));
+}
+
+static const void *batch_fn(bool m16) { return m16 ? (const void *)batch_kernel<true> : (const void *)batch_kernel<false>; }
+
+// Enqueue one solve (work-counter reset + persistent kernel) on stream st.
+static int batch_enqueue(qc_batch *b, const BatchArgs &a, int threads, int grid, cudaStream_t st)
+{
+    BCK(cudaMemsetAsync(b->queue, 0, sizeof(int), st));
+    const size_t smem = batch_smem(b);
+    if (b->m16) batch_kernel<true><<<grid, threads, smem, st>>>(a);
+    else batch_kernel<false><<<grid, threads, smem, st>>>(a);
+    BCK(cudaGetLastError());
+    return QC_OK;
+}
+
+static int launch_shape(qc_batch *b, const qc_batch_opts *o, int &threads, int &per_sm, int &schedule)
+{
+    threads = o->threads;
+    per_sm = o->ctas_per_sm;
+    schedule = o->schedule;
+    auto it = b->tuned.find(b->shape_key);
+    if (it != b->tuned.end()) {
+        if (threads == 0) threads = it->second.threads;
+        if (per_sm == 0) per_sm = it->second.per_sm;
+        if (schedule == QC_SCHED_AUTO) schedule = it->second.schedule;
+    }
+    if (threads == 0) threads = 256;
+    if (schedule == QC_SCHED_AUTO) schedule = QC_SCHED_LPT;
+    if (threads < 64 || threads > 512 || threads % 32) return b->fail(QC_EINVAL, "threads must be 64..512, multiple of 32");
+    const size_t smem = batch_smem(b);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(batch_fn(b->m16), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return b->cuda_fail(e, "cudaFuncSetAttribute");
+    }
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_fn(b->m16), threads, smem);
+    if (e != cudaSuccess) return b->cuda_fail(e, "occupancy");
+    if (occ < 1) return b->fail(QC_EUNSUPPORTED, "batch kernel does not fit on an SM with this shape");
+    if (per_sm <= 0 || per_sm > occ) per_sm = std::min(occ, per_sm <= 0 ? occ : per_sm);
+    return QC_OK;
+}
+
+static int batch_solve_impl(qc_batch *b, void *gains, int8_t *gain_flags, int32_t *iters, int32_t mem,
+                            const qc_batch_opts *o, qc_batch_stats *stats, bool tuning)
+{
+    if (!gains) return b->fail(QC_EINVAL, "gains is NULL");
+    if (mem != QC_MEM_HOST && mem != QC_MEM_DEVICE) return b->fail(QC_EINVAL, "mem must be QC_MEM_HOST or DEVICE");
+    if (o->max_iter < 1) return b->fail(QC_EINVAL, "max_iter must be >= 1");
+    if (!(o->tol >= 0)) return b->fail(QC_EINVAL, "tol must be >= 0");
+    if (o->damping_mode != QC_DAMP_CONST && o->damping_mode != QC_DAMP_ALTERNATE) return b->fail(QC_EINVAL, "damping_mode");
+    int threads, per_sm, schedule, rc;
+    if ((rc = launch_shape(b, o, threads, per_sm, schedule))) return rc;
+    cudaStream_t st = o->stream ? (cudaStream_t)o->stream : b->own_stream;
+    const size_t gbytes = (size_t)b->total_ant * 2 * sizeof(float2);
+    unsigned char *stage = (unsigned char *)b->gstage;
+    float2 *dg = mem == QC_MEM_DEVICE ? (float2 *)gains : (float2 *)stage;
+    int8_t *dflags = mem == QC_MEM_DEVICE ? gain_flags : (gain_flags ? (int8_t *)(stage + gbytes) : nullptr);
+    int *diters = mem == QC_MEM_DEVICE ? iters
+                                       : (iters ? (int *)(stage + gbytes + ((b->total_ant + 15) / 16) * 16) : nullptr);
+    BatchArgs a = batch_args(b);
+    a.order = schedule == QC_SCHED_STATIC ? b->order_idx : b->order_lpt;
+    a.queue = b->queue;
+    a.schedule = schedule;
+    a.gains = dg;
+    a.gain_flags = dflags;
+    a.iters = diters;
+    a.max_iter = o->max_iter;
+    a.damping_mode = o->damping_mode;
+    a.damping = o->damping;
+    a.tol = o->tol;
+    const int grid = std::max(1, std::min(b->n_prob, b->sm_count * per_sm));
+    BCK(cudaEventRecord(b->ev0, st));
+    if (mem == QC_MEM_HOST) BCK(cudaMemcpyAsync(dg, gains, gbytes, cudaMemcpyHostToDevice, st));
+    BCK(cudaMemsetAsync(b->counters, 0, 2 * sizeof(unsigned long long), st));
+    if (o->use_graph && !tuning) {
+        qc_batch::GraphKey k;
+        memset(&k, 0, sizeof k);
+        k.threads = threads; k.per_sm = per_sm; k.schedule = schedule; k.max_iter = o->max_iter;
+        k.damping_mode = o->damping_mode; k.damping = o->damping; k.tol = o->tol; k.m16 = b->m16;
+        k.gains = dg; k.flags = dflags; k.iters = diters; k.st = st;
+        const bool same = b->exec && memcmp(&k, &b->gkey, sizeof k) == 0;
+        if (!same) {
+            if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+            cudaGraph_t g = nullptr;
+            BCK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            rc = batch_enqueue(b, a, threads, grid, st);
+            cudaError_t e = cudaStreamEndCapture(st, &g);
+            if (rc || e != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                cudaGetLastError();
+                return rc ? rc : b->cuda_fail(e, "cudaStreamEndCapture");
+            }
+            e = cudaGraphInstantiate(&b->exec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return b->cuda_fail(e, "cudaGraphInstantiate");
+            b->gkey = k;
+        }
+        BCK(cudaGraphLaunch(b->exec, st));
+    } else {
+        if ((rc = batch_enqueue(b, a, threads, grid, st))) return rc;
+    }
+    if (mem == QC_MEM_HOST) {
+        BCK(cudaMemcpyAsync(gains, dg, gbytes, cudaMemcpyDeviceToHost, st));
+        if (gain_flags) BCK(cudaMemcpyAsync(gain_flags, dflags, (size_t)b->total_ant, cudaMemcpyDeviceToHost, st));
+        if (iters) BCK(cudaMemcpyAsync(iters, diters, sizeof(int) * b->n_prob, cudaMemcpyDeviceToHost, st));
+    }
+    unsigned long long hc[2];
+    BCK(cudaMemcpyAsync(hc, b->counters, sizeof hc, cudaMemcpyDeviceToHost, st));
+    BCK(cudaEventRecord(b->ev1, st));
+    BCK(cudaStreamSynchronize(st));
+    float ms = 0;
+    BCK(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+    if (stats) {
+        qc_batch_stats S;
+        memset(&S, 0, sizeof S);
+        S.ms = ms;
+        S.vis_iters = (int64_t)hc[0];
+        S.bytes = (int64_t)hc[1];
+        S.threads = threads;
+        S.ctas_per_sm = per_sm;
+        S.schedule = schedule;
+        S.grid = grid;
+        double tot_vis = 0;
+        for (const BProb &P : b->hprobs) tot_vis += (double)P.n_rows * P.n_chan;
+        S.mean_iters = tot_vis > 0 ? (double)hc[0] / tot_vis : 0;
+        if (iters) {
+            int mx = 0;
+            if (mem == QC_MEM_HOST) for (int i = 0; i < b->n_prob; ++i) mx = std::max(mx, iters[i]);
+            S.n_iter_max = mx;
+        }
+        *stats = S;
+    }
+    return QC_OK;
+}
+
+extern "C" int qc_batch_solve(qc_batch *b, void *gains, int8_t *gain_flags, int32_t *iters, int32_t mem,
+                              const qc_batch_opts *o, qc_batch_stats *stats)
+{
+    if (!b) return QC_EINVAL;
+    b->err.clear();
+    qc_batch_opts def;
+    memset(&def, 0, sizeof def);
+    def.max_iter = 20;
+    def.tol = 1e-6;
+    def.damping_mode = QC_DAMP_ALTERNATE;
+    def.use_graph = 1;
+    return batch_solve_impl(b, gains, gain_flags, iters, mem, o ? o : &def, stats, false);
+}
+
+extern "C" int qc_batch_autotune(qc_batch *b, const qc_batch_opts *base, qc_batch_stats *best, int32_t *n_tried)
+{
+    if (!b || !base) return QC_EINVAL;
+    b->err.clear();
+    // unit gains on the device for every trial
+    float2 *g;
+    cudaError_t e = cudaMalloc(&g, (size_t)b->total_ant * 2 * sizeof(float2));
+    if (e != cudaSuccess) return b->cuda_fail(e, "cudaMalloc");
+    std::vector<float2> unit((size_t)b->total_ant * 2, make_float2(1.f, 0.f));
+    qc_batch::Shape win{ 0, 0, 0, 1e30 };
+    int tried = 0, rc = QC_OK;
+    qc_batch_stats ws;
+    memset(&ws, 0, sizeof ws);
+    b->tuned.erase(b->shape_key);
+    for (int threads : { 128, 256, 512 })
+        for (int per_sm : { 1, 2, 4 })
+            for (int sched : { QC_SCHED_LPT, QC_SCHED_STATIC }) {
+                qc_batch_opts o = *base;
+                o.threads = threads;
+                o.ctas_per_sm = per_sm;
+                o.schedule = sched;
+                o.use_graph = 0;
+                e = cudaMemcpy(g, unit.data(), unit.size() * sizeof(float2), cudaMemcpyHostToDevice);
+                if (e != cudaSuccess) { rc = b->cuda_fail(e, "cudaMemcpy"); break; }
+                qc_batch_stats s;
+                int r = batch_solve_impl(b, g, nullptr, nullptr, QC_MEM_DEVICE, &o, &s, true);
+                if (r == QC_EUNSUPPORTED || r == QC_EINVAL) continue;      // shape not launchable
+                if (r) { rc = r; break; }
+                ++tried;
+                if (s.ctas_per_sm != per_sm) continue;                     // clamped: duplicate of a smaller one
+                if (s.ms < win.ms) { win = { threads, per_sm, sched, s.ms }; ws = s; }
+            }
+    cudaFree(g);
+    if (rc) return rc;
+    if (!tried || win.threads == 0) return b->fail(QC_EUNSUPPORTED, "no launch shape could be timed");
+    b->tuned[b->shape_key] = win;
+    if (best) *best = ws;
+    if (n_tried) *n_tried = tried;
+    return QC_OK;
+}
+
+extern "C" int qc_batch_residual(qc_batch *b, const void *gains, int32_t mem, double *chi2)
+{
+    if (!b) return QC_EINVAL;
+    b->err.clear();
+    if (!gains || !chi2) return b->fail(QC_EINVAL, "gains and chi2 are required");
+    cudaStream_t st = b->own_stream;
+    const size_t gbytes = (size_t)b->total_ant * 2 * sizeof(float2);
+    float2 *dg = (float2 *)gains;
+    double *dchi = chi2;
+    void *tmp = nullptr;
+    if (mem == QC_MEM_HOST) {
+        BCK(cudaMalloc(&tmp, gbytes + sizeof(double) * b->n_prob));
+        dg = (float2 *)tmp;
+        dchi = (double *)((unsigned char *)tmp + gbytes);
+        BCK(cudaMemcpyAsync(dg, gains, gbytes, cudaMemcpyHostToDevice, st));
+    }
+    BatchArgs a = batch_args(b);
+    a.gains = dg;
+    if (b->m16) batch_chi2_kernel<true><<<b->n_prob, 256, 0, st>>>(a, dchi);
+    else batch_chi2_kernel<false><<<b->n_prob, 256, 0, st>>>(a, dchi);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && mem == QC_MEM_HOST)
+        e = cudaMemcpyAsync(chi2, dchi, sizeof(double) * b->n_prob, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (tmp) cudaFree(tmp);
+    if (e != cudaSuccess) return b->cuda_fail(e, "batch residual");
+    return QC_OK;
+}

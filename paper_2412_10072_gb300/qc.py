@@ -266,3 +266,162 @@ class Solver:
 
 def version() -> str:
     return load().qc_version().decode()
+
+
+# ---------------------------------------------------------------------------
+# batched solves of independent solution intervals
+# ---------------------------------------------------------------------------
+
+QC_SCHED_AUTO, QC_SCHED_LPT, QC_SCHED_STATIC = 0, 1, 2
+QC_BATCH_MAX_ANT = 256
+
+
+class _BatchProblem(C.Structure):
+    _fields_ = [("n_prob", C.c_int32), ("row_offset", C.c_void_p), ("vis_offset", C.c_void_p),
+                ("n_chan", C.c_void_p), ("n_ant", C.c_void_p), ("data", C.c_void_p), ("model", C.c_void_p),
+                ("weight", C.c_void_p), ("flag", C.c_void_p), ("ant1", C.c_void_p), ("ant2", C.c_void_p),
+                ("memory", C.c_int32), ("model_fp16", C.c_int32)]
+
+
+class _BatchOpts(C.Structure):
+    _fields_ = [("max_iter", C.c_int32), ("tol", C.c_double), ("damping_mode", C.c_int32), ("damping", C.c_double),
+                ("stream", C.c_void_p), ("threads", C.c_int32), ("ctas_per_sm", C.c_int32),
+                ("schedule", C.c_int32), ("use_graph", C.c_int32)]
+
+
+class BatchStats(C.Structure):
+    _fields_ = [("ms", C.c_double), ("vis_iters", C.c_int64), ("bytes", C.c_int64), ("n_iter_max", C.c_int32),
+                ("mean_iters", C.c_double), ("threads", C.c_int32), ("ctas_per_sm", C.c_int32),
+                ("schedule", C.c_int32), ("grid", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def _load_batch(lib):
+    if getattr(lib, "_batch_ready", False):
+        return lib
+    vp, i32 = C.c_void_p, C.c_int32
+    lib.qc_batch_create.argtypes = [C.POINTER(_BatchProblem), C.POINTER(vp)]
+    lib.qc_batch_create.restype = C.c_int
+    lib.qc_batch_solve.argtypes = [vp, vp, vp, vp, i32, C.POINTER(_BatchOpts), C.POINTER(BatchStats)]
+    lib.qc_batch_solve.restype = C.c_int
+    lib.qc_batch_autotune.argtypes = [vp, C.POINTER(_BatchOpts), C.POINTER(BatchStats), C.POINTER(C.c_int32)]
+    lib.qc_batch_autotune.restype = C.c_int
+    lib.qc_batch_residual.argtypes = [vp, vp, i32, vp]
+    lib.qc_batch_residual.restype = C.c_int
+    lib.qc_batch_destroy.argtypes = [vp]
+    lib.qc_batch_destroy.restype = None
+    lib.qc_batch_last_error.argtypes = [vp]
+    lib.qc_batch_last_error.restype = C.c_char_p
+    lib._batch_ready = True
+    return lib
+
+
+class BatchSolver:
+    """Many independent one-interval diagonal-gain problems (qc_batch_* of include/qc.h).
+
+    Arrays are the problems' [row][chan][4] blocks concatenated; ``row_offset`` and
+    ``vis_offset`` (length n_prob + 1), ``n_chan``, ``n_ant`` and ``ant1``/``ant2`` are host
+    arrays.  Gains are [sum n_ant][2] complex64 (g_XX, g_YY).
+    """
+
+    def __init__(self, data, model, weight, flag, ant1, ant2, row_offset, vis_offset, n_chan, n_ant,
+                 model_fp16: bool = False):
+        self._lib = _load_batch(load())
+        dev = _is_dev(data)
+        if not dev:
+            data = _complex64(data)
+            model = _complex64(model)
+            weight = _host(weight, np.float32)
+            flag = None if flag is None else _host(flag, np.uint8)
+        self._keep = (data, model, weight, flag) if dev else None
+        self.row_offset = _host(row_offset, np.int64)
+        self.vis_offset = _host(vis_offset, np.int64)
+        self.n_chan = _host(n_chan, np.int32)
+        self.n_ant = _host(n_ant, np.int32)
+        self.ant1 = _host(ant1, np.int32)
+        self.ant2 = _host(ant2, np.int32)
+        self.n_prob = int(self.n_chan.size)
+        self.gain_offset = np.concatenate([[0], np.cumsum(self.n_ant)]).astype(np.int64)
+        p = _BatchProblem(self.n_prob, _addr(self.row_offset), _addr(self.vis_offset), _addr(self.n_chan),
+                          _addr(self.n_ant), _addr(data), _addr(model), _addr(weight), _addr(flag), _addr(self.ant1),
+                          _addr(self.ant2), QC_MEM_DEVICE if dev else QC_MEM_HOST, int(bool(model_fp16)))
+        h = C.c_void_p()
+        rc = self._lib.qc_batch_create(C.byref(p), C.byref(h))
+        if rc != QC_OK:
+            raise QCError(rc, self._lib.qc_batch_last_error(None).decode())
+        self._h = h
+
+    @property
+    def total_ant(self) -> int:
+        return int(self.gain_offset[-1])
+
+    def unit_gains(self):
+        g = np.zeros((self.total_ant, 2), dtype=np.complex64)
+        g[:] = 1
+        return g
+
+    def _opts(self, max_iter, tol, damping_mode, damping, stream, threads, ctas_per_sm, schedule, use_graph):
+        st = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
+        return _BatchOpts(max_iter, tol, damping_mode, damping, st or None, threads, ctas_per_sm, schedule,
+                          int(use_graph))
+
+    def _err(self, rc):
+        raise QCError(rc, self._lib.qc_batch_last_error(self._h).decode())
+
+    def solve(self, gains=None, max_iter: int = 20, tol: float = 1e-6, damping_mode: int = QC_DAMP_ALTERNATE,
+              damping: float = 1.0, stream=None, threads: int = 0, ctas_per_sm: int = 0,
+              schedule: int = QC_SCHED_AUTO, use_graph: bool = True, want_flags: bool = True):
+        """Solve in place; returns (gains, gain_flags, iters, BatchStats)."""
+        if gains is None:
+            gains = self.unit_gains()
+        dev = _is_dev(gains)
+        if dev:
+            import torch
+            flags = torch.zeros(self.total_ant, dtype=torch.int8, device=gains.device) if want_flags else None
+            iters = torch.zeros(self.n_prob, dtype=torch.int32, device=gains.device)
+        else:
+            gains = np.ascontiguousarray(gains, dtype=np.complex64)
+            flags = np.zeros(self.total_ant, dtype=np.int8) if want_flags else None
+            iters = np.zeros(self.n_prob, dtype=np.int32)
+        o = self._opts(max_iter, tol, damping_mode, damping, stream, threads, ctas_per_sm, schedule, use_graph)
+        s = BatchStats()
+        rc = self._lib.qc_batch_solve(self._h, _addr(gains), _addr(flags), _addr(iters),
+                                      QC_MEM_DEVICE if dev else QC_MEM_HOST, C.byref(o), C.byref(s))
+        if rc != QC_OK:
+            self._err(rc)
+        return gains, flags, iters, s
+
+    def autotune(self, max_iter: int = 20, tol: float = 1e-6, damping_mode: int = QC_DAMP_ALTERNATE, stream=None):
+        o = self._opts(max_iter, tol, damping_mode, 1.0, stream, 0, 0, QC_SCHED_AUTO, False)
+        s = BatchStats()
+        n = C.c_int32(0)
+        rc = self._lib.qc_batch_autotune(self._h, C.byref(o), C.byref(s), C.byref(n))
+        if rc != QC_OK:
+            self._err(rc)
+        return s, n.value
+
+    def residual(self, gains):
+        dev = _is_dev(gains)
+        if dev:
+            import torch
+            chi2 = torch.zeros(self.n_prob, dtype=torch.float64, device=gains.device)
+        else:
+            gains = np.ascontiguousarray(gains, dtype=np.complex64)
+            chi2 = np.zeros(self.n_prob, dtype=np.float64)
+        rc = self._lib.qc_batch_residual(self._h, _addr(gains), QC_MEM_DEVICE if dev else QC_MEM_HOST, _addr(chi2))
+        if rc != QC_OK:
+            self._err(rc)
+        return chi2
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.qc_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -47,10 +47,10 @@ def baselines(n_ant: int):
     return p.astype(np.int32), q.astype(np.int32)
 
 
-def hour_angles(n_time: int, span_hours: float = 4.0) -> np.ndarray:
-    """Hour angles (radians) uniform over +-span/2 hours across n_time samples."""
+def hour_angles(n_time: int, span_hours: float = 4.0, centre_hours: float = 0.0) -> np.ndarray:
+    """Hour angles (radians) uniform over centre +- span/2 hours across n_time samples."""
     h = np.linspace(-span_hours / 2.0, span_hours / 2.0, n_time) if n_time > 1 else np.zeros(1)
-    return h * 15.0 * DEG
+    return (h + centre_hours) * 15.0 * DEG
 
 
 def ew_uvw(ant_x: np.ndarray, p: np.ndarray, q: np.ndarray, ha: np.ndarray,
@@ -249,34 +249,42 @@ class Setup:
     uvw: np.ndarray            # [row, 3] metres
     flag_rows: np.ndarray      # [row] bool, whole-row flags
     rng: np.random.Generator   # continues with the noise draws of the host path
+    flag_samples: Optional[np.ndarray] = None   # [row, chan] bool, per-sample flags (optional)
 
 
 def draw_setup(n_ant: int, n_time: int, freqs: np.ndarray, terms: List[TermSpec], *, n_src: int,
-               rng: np.random.Generator, ant_x: np.ndarray, flag_row_frac: float = 0.0) -> Setup:
+               rng: np.random.Generator, ant_x: np.ndarray, flag_row_frac: float = 0.0,
+               flag_sample_frac: float = 0.0, ha_span_hours: float = 4.0, ha_centre_hours: float = 0.0) -> Setup:
     sky = point_sources(n_src, rng)
     p, q = baselines(n_ant)
     n_bl = p.size
-    ha = hour_angles(n_time)
+    ha = hour_angles(n_time, ha_span_hours, ha_centre_hours)
     uvw = ew_uvw(ant_x, p, q, ha).reshape(n_time * n_bl, 3)
     ant1 = np.tile(p, n_time).astype(np.int32)
     ant2 = np.tile(q, n_time).astype(np.int32)
     time_idx = np.repeat(np.arange(n_time, dtype=np.int32), n_bl)
     flag_rows = (rng.random(ant1.size) < flag_row_frac) if flag_row_frac > 0 else np.zeros(ant1.size, bool)
+    flag_samples = (rng.random((ant1.size, len(freqs))) < flag_sample_frac) if flag_sample_frac > 0 else None
     return Setup(n_ant, n_time, np.asarray(freqs, np.float64), terms, ant_x, sky, ant1, ant2, time_idx, uvw,
-                 flag_rows, rng)
+                 flag_rows, rng, flag_samples)
 
 
 def make_observation(n_ant: int, n_time: int, freqs: np.ndarray, terms: List[TermSpec], *,
                      n_src: int, seed: int, noise: float, flag_row_frac: float = 0.0,
                      max_baseline_m: float = 1000.0, nan_in_flagged: bool = False,
                      rng: Optional[np.random.Generator] = None,
-                     ant_x: Optional[np.ndarray] = None) -> Observation:
+                     ant_x: Optional[np.ndarray] = None, su: Optional[Setup] = None) -> Observation:
     """Build one observation on the host; every random draw comes from ``seed`` (or ``rng``)."""
     rng = rng if rng is not None else np.random.default_rng(seed)
     n_chan = freqs.size
-    if ant_x is None:
-        ant_x = ew_array(n_ant, max_baseline_m, rng)
-    su = draw_setup(n_ant, n_time, freqs, terms, n_src=n_src, rng=rng, ant_x=ant_x, flag_row_frac=flag_row_frac)
+    if su is None:
+        if ant_x is None:
+            ant_x = ew_array(n_ant, max_baseline_m, rng)
+        su = draw_setup(n_ant, n_time, freqs, terms, n_src=n_src, rng=rng, ant_x=ant_x,
+                        flag_row_frac=flag_row_frac)
+    else:
+        rng = su.rng
+        ant_x = su.ant_x
     scal = predict_scalar(su.uvw, freqs, su.sky)
     model = np.zeros((su.ant1.size, n_chan, 4), dtype=np.complex128)
     model[:, :, 0] = scal
@@ -287,6 +295,8 @@ def make_observation(n_ant: int, n_time: int, freqs: np.ndarray, terms: List[Ter
     weight = np.ones(data.shape, dtype=np.float64)
     flag = np.zeros((su.ant1.size, n_chan), dtype=np.uint8)
     flag[su.flag_rows, :] = 1
+    if su.flag_samples is not None:
+        flag[su.flag_samples] = 1
     if nan_in_flagged:
         data[flag.astype(bool)] = np.nan + 1j * np.nan
     return Observation(n_ant=n_ant, n_time=n_time, n_chan=n_chan, data=data, model=model,
@@ -311,7 +321,10 @@ def make_observation_device(su: Setup, noise: float, noise_seed: int, device, ro
     data = torch.empty((n_row, n_chan, 4), dtype=c64, device=dev)
     model = torch.empty((n_row, n_chan, 4), dtype=c64, device=dev)
     weight = torch.ones((n_row, n_chan, 4), dtype=torch.float32, device=dev)
-    flag = torch.from_numpy(su.flag_rows.astype(np.uint8)).to(dev)[:, None].expand(n_row, n_chan).contiguous()
+    fl = np.repeat(su.flag_rows[:, None], n_chan, axis=1)
+    if su.flag_samples is not None:
+        fl = fl | su.flag_samples
+    flag = torch.from_numpy(fl.astype(np.uint8)).to(dev)
     gen = torch.Generator(device=dev)
     gen.manual_seed(int(noise_seed))
     # -2 pi nu / c in FP64; the phase is range-reduced in FP64 and its exponential taken in FP32
@@ -416,3 +429,93 @@ def plain_large(seed: int = 1, n_ant: int = 64, n_time: int = 300, n_chan: int =
     return make_observation(n_ant, n_time, freqs, terms, n_src=n_src, seed=seed, noise=noise,
                             flag_row_frac=flag_row_frac, rng=rng, ant_x=ant_x,
                             nan_in_flagged=nan_in_flagged)
+
+
+# ---------------------------------------------------------------------------
+# batches of independent one-interval problems
+# ---------------------------------------------------------------------------
+
+def interval_problem_setup(seed: int, n_ant: int, n_time: int, n_chan: int, flag_frac: float,
+                           n_src: int = 5, integration_s: float = 8.0) -> Setup:
+    """One diagonal-gain solution interval drawn like the small plain workload: an east-west array,
+    5 sources at 1.4 GHz (1 MHz channels), gains with amplitude 1+N(0,0.05) and phase U(-pi,pi),
+    n_time integrations of 8 s at a random hour angle, per-sample flags with probability flag_frac."""
+    rng = np.random.default_rng(seed)
+    freqs = 1.4e9 + 1.0e6 * (np.arange(n_chan) - (n_chan - 1) / 2.0)
+    ant_x = ew_array(n_ant, 1000.0, rng)
+    term = TermSpec("diag", np.zeros(n_time, np.int32), np.zeros(n_chan, np.int32), 1, 1)
+    term.truth = diag_truth(n_ant, 1, 1, rng)
+    centre = rng.uniform(-2.0, 2.0)
+    return draw_setup(n_ant, n_time, freqs, [term], n_src=n_src, rng=rng, ant_x=ant_x,
+                      flag_sample_frac=flag_frac, ha_span_hours=n_time * integration_s / 3600.0,
+                      ha_centre_hours=centre)
+
+
+def batch_shapes(n_prob: int, seed_base: int = 1000, ant=(7, 64), times=(1, 16), chans=(1, 64), flag_max=0.5):
+    """Per-problem (seed, n_ant, n_time, n_chan, flag fraction), each drawn from its own seed."""
+    out = []
+    for i in range(n_prob):
+        r = np.random.default_rng(seed_base + i)
+        out.append((seed_base + i, int(r.integers(ant[0], ant[1] + 1)), int(r.integers(times[0], times[1] + 1)),
+                    int(r.integers(chans[0], chans[1] + 1)), float(r.uniform(0.0, flag_max))))
+    return out
+
+
+@dataclasses.dataclass
+class Batch:
+    shapes: list
+    data: object
+    model: object
+    weight: object
+    flag: object
+    ant1: np.ndarray
+    ant2: np.ndarray
+    row_offset: np.ndarray
+    vis_offset: np.ndarray
+    n_chan: np.ndarray
+    n_ant: np.ndarray
+    truths: list                 # per problem [n_ant][2] complex (g_XX, g_YY)
+    setups: list
+
+    @property
+    def n_prob(self) -> int:
+        return len(self.shapes)
+
+    @property
+    def n_vis(self) -> int:
+        return int(self.vis_offset[-1])
+
+
+def make_batch(shapes, noise: float = 0.01, device=None, noise_seed: int = 7) -> Batch:
+    """Concatenate problems; host complex128 arrays (device=None) or complex64 device tensors."""
+    row_off, vis_off = [0], [0]
+    a1, a2, truths, setups = [], [], [], []
+    parts = []
+    for i, (seed, na, nt, nc, ff) in enumerate(shapes):
+        su = interval_problem_setup(seed, na, nt, nc, ff)
+        setups.append(su)
+        truths.append(su.terms[0].truth[0, 0][:, [0, 3]].copy())
+        if device is None:
+            obs = make_observation(na, nt, su.freqs, su.terms, n_src=5, seed=seed, noise=noise, su=su)
+            parts.append((obs.data, obs.model, obs.weight, obs.flag))
+        else:
+            parts.append(make_observation_device(su, noise, noise_seed + i, device))
+        a1.append(su.ant1)
+        a2.append(su.ant2)
+        row_off.append(row_off[-1] + su.ant1.size)
+        vis_off.append(vis_off[-1] + su.ant1.size * nc)
+    if device is None:
+        data = np.concatenate([p_[0].reshape(-1, 4) for p_ in parts])
+        model = np.concatenate([p_[1].reshape(-1, 4) for p_ in parts])
+        weight = np.concatenate([p_[2].reshape(-1, 4) for p_ in parts])
+        flag = np.concatenate([p_[3].reshape(-1) for p_ in parts])
+    else:
+        import torch
+        data = torch.cat([p_["data"].reshape(-1, 4) for p_ in parts])
+        model = torch.cat([p_["model"].reshape(-1, 4) for p_ in parts])
+        weight = torch.cat([p_["weight"].reshape(-1, 4) for p_ in parts])
+        flag = torch.cat([p_["flag"].reshape(-1) for p_ in parts])
+    return Batch(list(shapes), data, model, weight, flag, np.concatenate(a1).astype(np.int32),
+                 np.concatenate(a2).astype(np.int32), np.array(row_off, np.int64), np.array(vis_off, np.int64),
+                 np.array([s_[3] for s_ in shapes], np.int32), np.array([s_[1] for s_ in shapes], np.int32),
+                 truths, setups)

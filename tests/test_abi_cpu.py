@@ -83,3 +83,30 @@ def test_create_rejects_null_arguments(lib):
 
 def test_destroy_is_null_safe(lib):
     lib.qc_destroy(None)
+
+
+def _batch(**over):
+    b = dict(n_prob=2, row_offset=np.array([0, 3, 6], np.int64), vis_offset=np.array([0, 6, 12], np.int64),
+             n_chan=np.array([2, 2], np.int32), n_ant=np.array([3, 3], np.int32))
+    b.update(over)
+    data = np.zeros((12, 4), np.complex64)
+    keep = dict(data=data, model=data.copy(), weight=np.ones((12, 4), np.float32),
+                a1=np.array([0, 0, 1, 0, 0, 1], np.int32), a2=np.array([1, 2, 2, 1, 2, 2], np.int32), **b)
+    p = qc._BatchProblem(b["n_prob"], keep["row_offset"].ctypes.data, keep["vis_offset"].ctypes.data,
+                         keep["n_chan"].ctypes.data, keep["n_ant"].ctypes.data, keep["data"].ctypes.data,
+                         keep["model"].ctypes.data, keep["weight"].ctypes.data, None, keep["a1"].ctypes.data,
+                         keep["a2"].ctypes.data, 0, 0)
+    return p, keep
+
+
+@pytest.mark.parametrize("over", [dict(n_prob=0), dict(vis_offset=np.array([0, 5, 12], np.int64)),
+                                  dict(n_ant=np.array([3, 2], np.int32)), dict(n_ant=np.array([3, 300], np.int32)),
+                                  dict(row_offset=np.array([1, 3, 6], np.int64)),
+                                  dict(n_chan=np.array([2, 0], np.int32))])
+def test_batch_create_rejects_invalid(lib, over):
+    qc._load_batch(lib)
+    p, keep = _batch(**over)
+    h = C.c_void_p()
+    assert lib.qc_batch_create(C.byref(p), C.byref(h)) == qc.QC_EINVAL
+    assert lib.qc_batch_last_error(None)
+    lib.qc_batch_destroy(None)

@@ -302,6 +302,75 @@ void qc_batch_destroy(qc_batch *b);
 /* Message of the last failed call on `b` ("" if none); NULL: last failed qc_batch_create. */
 const char *qc_batch_last_error(const qc_batch *b);
 
+/* ------------------------------------------------------------------------ */
+/* Learned warm start of the batched solver                                  */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Initial estimates (Section 4.3, "Initial estimates"): a multilayer
+ * perceptron predicts each interval's diagonal gains from per-antenna
+ * features; Algorithm 1 then iterates from them as usual.
+ *
+ * Network: Linear(10 -> 128) GELU, Linear(128 -> 128) GELU,
+ * Linear(128 -> 128) GELU, Linear(128 -> 4); GELU(z) = z (1 + erf(z/sqrt 2))/2.
+ * Parameters are one float32 buffer of QC_MLP_NPARAM values: W1 [128][10],
+ * b1 [128], W2 [128][128], b2, W3 [128][128], b3, W4 [4][128], b4 (weights
+ * row-major [out][in]).  Outputs per antenna: (Re g_XX, Im g_XX, Re g_YY,
+ * Im g_YY) in the gauge where the sum of the interval's gains is real and
+ * positive per correlation.
+ */
+#define QC_MLP_IN      10
+#define QC_MLP_HIDDEN  128
+#define QC_MLP_OUT     4
+#define QC_MLP_NPARAM  34948
+
+/*
+ * Per-antenna features of every problem of a batch, float32 [sum n_ant][10]
+ * (device or host per `mem`), from one data pass at unit gains:
+ *   0,1  |z_XX|, |z_YY| with z_k = JHr_k / JHJ_kk, the normalised first
+ *        Gauss-Newton step at unit gains (Eq. jhr_entry_simplified)
+ *   2,3  arg z_XX, arg z_YY
+ *   4,5  mean |d_kk| / |m_kk| over the antenna's unflagged samples
+ *   6..9 previous-interval gains (Re, Im of g_XX, g_YY), referenced so that
+ *        their sum over the interval's antennas is real-positive; unit gains
+ *        when prev_gains is NULL.
+ * Antennas without data get zeros for 0..5.
+ */
+int qc_batch_features(qc_batch *b, const void *prev_gains, float *features, int32_t mem, void *stream);
+
+/*
+ * Initial gains from network outputs y [sum n_ant][4] (device): g = (y0 + i y1,
+ * y2 + i y3).  A problem whose outputs are not all finite, or (check_chi2 = 1)
+ * whose chi^2 at the predicted gains exceeds its chi^2 at `fallback` (device
+ * [sum n_ant][2] complex64: previous-interval or unit gains), starts from
+ * `fallback` instead.  gains_out: device [sum n_ant][2] complex64.  n_fallback
+ * (nullable, host) receives the number of problems that fell back.
+ */
+int qc_batch_warmstart(qc_batch *b, const float *y, const void *fallback, int32_t check_chi2, void *gains_out,
+                       int32_t *n_fallback, void *stream);
+
+/*
+ * Rotate each problem's gains (device [sum n_ant][2] complex64; in place allowed)
+ * by the conjugate unit phase of their sum over the problem's antennas, per
+ * correlation: the gauge of the network's targets and previous-gain features.
+ */
+int qc_batch_reference_gains(qc_batch *b, const void *gains_in, void *gains_out, void *stream);
+
+/*
+ * Network kernels (device pointers, `stream` may be NULL):
+ *   forward  : y [n][4] = net(x [n][10]); z (nullable) [n][3][128] receives the
+ *              three hidden pre-activations for the backward pass.
+ *   backward : grad [QC_MLP_NPARAM] = d loss / d params and *loss (device
+ *              double) = mean over n x 4 of (y - target)^2.
+ *   adam     : one Adam step (bias-corrected, step counted from 1).
+ */
+int qc_mlp_forward(const float *params, const float *x, int64_t n, float *y, float *z, void *stream);
+int qc_mlp_backward(const float *params, const float *x, const float *z, const float *y, const float *target,
+                    int64_t n, float *grad, double *loss, void *stream);
+int qc_mlp_adam(float *params, const float *grad, float *m, float *v, float lr, float beta1, float beta2, float eps,
+                int32_t step, void *stream);
+const char *qc_mlp_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -274,6 +274,185 @@ __global__ void __launch_bounds__(256) batch_chi2_kernel(const BatchArgs a, doub
     }
 }
 
+
+// Per-antenna warm-start features of every problem (one CTA per problem, one data
+// pass at unit gains): JHJ diagonal and JHr at g = 1 (both baseline orientations),
+// sums of |d_kk| / |m_kk| and their counts; then the 10 features per antenna.
+__global__ void __launch_bounds__(256) batch_features_kernel(const BatchArgs a, const float2 *prev, float *feat)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    float *acc = reinterpret_cast<float *>(smem);          // [max_ant][9]: h0 h1 jr0 ji0 jr1 ji1 s0 s1 cnt
+    __shared__ float2 ref[2];
+    const int pi = blockIdx.x;
+    const BProb P = a.probs[pi];
+    const int na = P.n_ant, nc = P.n_chan, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n_warps = blockDim.x >> 5;
+    for (int i = tid; i < na * 9; i += blockDim.x) acc[i] = 0.f;
+    __syncthreads();
+    const bool wide = nc >= 32;
+    const int rpi = wide ? 1 : 32 / nc;
+    const int chunks = wide ? (nc + 31) / 32 : 1;
+    const int lr = wide ? 0 : lane / nc, lc = wide ? lane : lane % nc;
+    const bool lane_ok = wide || lane < rpi * nc;
+    const long n_steps = wide ? (long)P.n_rows * chunks : ((long)P.n_rows + rpi - 1) / rpi;
+    for (long t = warp; t < n_steps; t += n_warps) {
+        int row, c;
+        if (wide) { row = (int)(t / chunks); c = (int)(t % chunks) * 32 + lane; }
+        else { row = (int)t * rpi + lr; c = lc; }
+        const bool in = lane_ok && row < P.n_rows && c < nc;
+        int p = -1, q = -1;
+        float v[18];
+#pragma unroll
+        for (int i = 0; i < 18; ++i) v[i] = 0.f;
+        if (in) {
+            const int2 pq = __ldg(a.ants + P.row_off + row);
+            p = pq.x;
+            q = pq.y;
+            const size_t s = (size_t)P.vis_off + (size_t)row * nc + c;
+            bool ok = p != q;
+            if (ok && a.flag) ok = __ldg(a.flag + s) == 0;
+            if (ok) {
+                const J2 D = j_from(__ldg(a.vis + 2 * s), __ldg(a.vis + 2 * s + 1));
+                J2 M;
+                if (a.model16) {
+                    const uint4 h = __ldg(a.model16 + s);
+                    const float sc = __ldg(a.row_scale + P.row_off + row);
+                    M.a = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.x)), sc);
+                    M.b = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.y)), sc);
+                    M.c = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.z)), sc);
+                    M.d = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.w)), sc);
+                } else {
+                    M = j_from(__ldg(a.model + 2 * s), __ldg(a.model + 2 * s + 1));
+                }
+                const float4 w = __ldg(a.weight + s);
+                // unit gains: X = M, V = M, r = D - M
+                const float2 r00 = csub(D.a, M.a), r01 = csub(D.b, M.b), r10 = csub(D.c, M.c), r11 = csub(D.d, M.d);
+                v[0] = fmaf(w.x, cnorm2(M.a), w.y * cnorm2(M.b));
+                v[1] = fmaf(w.z, cnorm2(M.c), w.w * cnorm2(M.d));
+                float2 j0 = cfma_conj(M.b, cscale(r01, w.y), cfma_conj(M.a, cscale(r00, w.x), make_float2(0.f, 0.f)));
+                float2 j1 = cfma_conj(M.d, cscale(r11, w.w), cfma_conj(M.c, cscale(r10, w.z), make_float2(0.f, 0.f)));
+                v[2] = j0.x; v[3] = j0.y; v[4] = j1.x; v[5] = j1.y;
+                const float ma = sqrtf(cnorm2(M.a)), md = sqrtf(cnorm2(M.d));
+                const bool okr = ma > 0.f && md > 0.f;
+                v[6] = okr ? sqrtf(cnorm2(D.a)) / ma : 0.f;
+                v[7] = okr ? sqrtf(cnorm2(D.d)) / md : 0.f;
+                v[8] = okr ? 1.f : 0.f;
+                // conjugate baseline for antenna q: Y = M^H, r' = r^H, w' = P w
+                v[9] = fmaf(w.x, cnorm2(M.a), w.z * cnorm2(M.c));
+                v[10] = fmaf(w.y, cnorm2(M.b), w.w * cnorm2(M.d));
+                float2 k0 = cfma_conj(cconj(M.c), cscale(cconj(r10), w.z), cfma_conj(cconj(M.a), cscale(cconj(r00), w.x), make_float2(0.f, 0.f)));
+                float2 k1 = cfma_conj(cconj(M.d), cscale(cconj(r11), w.w), cfma_conj(cconj(M.b), cscale(cconj(r01), w.y), make_float2(0.f, 0.f)));
+                v[11] = k0.x; v[12] = k0.y; v[13] = k1.x; v[14] = k1.y;
+                v[15] = v[6]; v[16] = v[7]; v[17] = v[8];
+            }
+        }
+        const int kp = in ? p : -1, kq = in ? q : -1;
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            const int key = side == 0 ? kp : kq;
+            const int prevk = __shfl_up_sync(0xffffffffu, key, 1);
+            const bool head = lane == 0 || key != prevk;
+            const unsigned heads = __ballot_sync(0xffffffffu, head);
+            const unsigned after = heads & ~((2u << lane) - 1u);
+            const unsigned run_end = after ? (unsigned)(__ffs(after) - 1) : 32u;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const float sum = run_sum(v[side * 9 + i], lane, run_end);
+                if (head && key >= 0) atomicAdd(acc + key * 9 + i, sum);
+            }
+        }
+    }
+    __syncthreads();
+    // reference of the previous-interval gains: phase of their sum per correlation
+    if (tid < 2) {
+        float2 sum = make_float2(0.f, 0.f);
+        for (int ant = 0; ant < na; ++ant) {
+            const float2 g = prev ? prev[(size_t)(P.gain_off + ant) * 2 + tid] : make_float2(1.f, 0.f);
+            sum = cadd(sum, g);
+        }
+        const float mag = sqrtf(cnorm2(sum));
+        ref[tid] = mag > 0.f ? make_float2(sum.x / mag, -sum.y / mag) : make_float2(1.f, 0.f);
+    }
+    __syncthreads();
+    for (int ant = tid; ant < na; ant += blockDim.x) {
+        const float *A = acc + ant * 9;
+        float *f = feat + (size_t)(P.gain_off + ant) * 10;
+        for (int k = 0; k < 2; ++k) {
+            const float h = A[k];
+            const float2 z = h > 0.f ? make_float2(A[2 + 2 * k] / h, A[3 + 2 * k] / h) : make_float2(0.f, 0.f);
+            f[k] = sqrtf(cnorm2(z));
+            f[2 + k] = h > 0.f ? atan2f(z.y, z.x) : 0.f;
+            f[4 + k] = A[8] > 0.f ? A[6 + k] / A[8] : 0.f;
+            const float2 g = prev ? prev[(size_t)(P.gain_off + ant) * 2 + k] : make_float2(1.f, 0.f);
+            const float2 gr = cmul(g, ref[k]);
+            f[6 + 2 * k] = gr.x;
+            f[7 + 2 * k] = gr.y;
+        }
+    }
+}
+
+
+// gains of each problem rotated so that their sum over antennas is real-positive per correlation
+__global__ void reference_gains_kernel(const BProb *probs, int n_prob, const float2 *in, float2 *out)
+{
+    const int pi = blockIdx.x;
+    if (pi >= n_prob) return;
+    const BProb P = probs[pi];
+    __shared__ float2 ref[2];
+    if (threadIdx.x < 2) {
+        float2 sum = make_float2(0.f, 0.f);
+        for (int ant = 0; ant < P.n_ant; ++ant) sum = cadd(sum, in[(size_t)(P.gain_off + ant) * 2 + threadIdx.x]);
+        const float mag = sqrtf(cnorm2(sum));
+        ref[threadIdx.x] = mag > 0.f ? make_float2(sum.x / mag, -sum.y / mag) : make_float2(1.f, 0.f);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < P.n_ant * 2; i += blockDim.x) {
+        const size_t g = (size_t)P.gain_off * 2 + i;
+        out[g] = cmul(in[g], ref[i & 1]);
+    }
+}
+
+// gains from network outputs; non-finite outputs make the whole problem fall back
+__global__ void warm_gains_kernel(const BProb *probs, int n_prob, const float *y, const float2 *fallback, float2 *out,
+                                  int *bad)
+{
+    const int pi = blockIdx.x;
+    if (pi >= n_prob) return;
+    const BProb P = probs[pi];
+    __shared__ int s_bad;
+    if (threadIdx.x == 0) s_bad = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < P.n_ant * 4; i += blockDim.x)
+        if (!isfinite(y[(size_t)P.gain_off * 4 + i])) s_bad = 1;
+    __syncthreads();
+    for (int ant = threadIdx.x; ant < P.n_ant; ant += blockDim.x) {
+        const size_t g = (size_t)(P.gain_off + ant);
+        if (s_bad) {
+            out[2 * g] = fallback[2 * g];
+            out[2 * g + 1] = fallback[2 * g + 1];
+        } else {
+            out[2 * g] = make_float2(y[4 * g], y[4 * g + 1]);
+            out[2 * g + 1] = make_float2(y[4 * g + 2], y[4 * g + 3]);
+        }
+    }
+    if (threadIdx.x == 0) bad[pi] = s_bad;
+}
+
+// keep the fallback gains of problems whose chi^2 at the predicted gains is larger
+__global__ void warm_select_kernel(const BProb *probs, int n_prob, const double *chi_pred, const double *chi_fb,
+                                   const float2 *fallback, float2 *out, int *bad)
+{
+    const int pi = blockIdx.x;
+    if (pi >= n_prob) return;
+    const BProb P = probs[pi];
+    const bool use_fb = !(chi_pred[pi] <= chi_fb[pi]);
+    for (int ant = threadIdx.x; ant < P.n_ant; ant += blockDim.x) {
+        const size_t g = (size_t)(P.gain_off + ant);
+        if (use_fb) { out[2 * g] = fallback[2 * g]; out[2 * g + 1] = fallback[2 * g + 1]; }
+    }
+    if (threadIdx.x == 0 && use_fb) bad[pi] = 1;
+}
+
 __global__ void row_scale_kernel(const float4 *model, const int2 *ants, const long long *row_vis, const int *row_nc,
                                  const int *row_bl, long n_rows, unsigned *bl_bits)
 {
@@ -827,5 +1006,89 @@ extern "C" int qc_batch_residual(qc_batch *b, const void *gains, int32_t mem, do
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (tmp) cudaFree(tmp);
     if (e != cudaSuccess) return b->cuda_fail(e, "batch residual");
+    return QC_OK;
+}
+
+
+extern "C" int qc_batch_features(qc_batch *b, const void *prev_gains, float *features, int32_t mem, void *stream)
+{
+    if (!b) return QC_EINVAL;
+    b->err.clear();
+    if (!features) return b->fail(QC_EINVAL, "features is NULL");
+    if (mem != QC_MEM_HOST && mem != QC_MEM_DEVICE) return b->fail(QC_EINVAL, "mem must be QC_MEM_HOST or DEVICE");
+    cudaStream_t st = stream ? (cudaStream_t)stream : b->own_stream;
+    const size_t gbytes = (size_t)b->total_ant * 2 * sizeof(float2), fbytes = (size_t)b->total_ant * 10 * sizeof(float);
+    void *tmp = nullptr;
+    const float2 *dprev = (const float2 *)prev_gains;
+    float *dfeat = features;
+    if (mem == QC_MEM_HOST) {
+        BCK(cudaMalloc(&tmp, gbytes + fbytes));
+        dfeat = (float *)tmp;
+        if (prev_gains) {
+            BCK(cudaMemcpyAsync((unsigned char *)tmp + fbytes, prev_gains, gbytes, cudaMemcpyHostToDevice, st));
+            dprev = (const float2 *)((unsigned char *)tmp + fbytes);
+        }
+    }
+    BatchArgs a = batch_args(b);
+    const size_t smem = (size_t)b->max_ant * 9 * sizeof(float);
+    batch_features_kernel<<<b->n_prob, 256, smem, st>>>(a, dprev, dfeat);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && mem == QC_MEM_HOST) e = cudaMemcpyAsync(features, dfeat, fbytes, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && mem == QC_MEM_HOST) e = cudaStreamSynchronize(st);
+    if (tmp) { cudaStreamSynchronize(st); cudaFree(tmp); }
+    if (e != cudaSuccess) return b->cuda_fail(e, "batch features");
+    return QC_OK;
+}
+
+extern "C" int qc_batch_warmstart(qc_batch *b, const float *y, const void *fallback, int32_t check_chi2, void *gains_out,
+                                  int32_t *n_fallback, void *stream)
+{
+    if (!b) return QC_EINVAL;
+    b->err.clear();
+    if (!y || !fallback || !gains_out) return b->fail(QC_EINVAL, "y, fallback and gains_out are required (device)");
+    cudaStream_t st = stream ? (cudaStream_t)stream : b->own_stream;
+    void *tmp = nullptr;
+    BCK(cudaMalloc(&tmp, sizeof(int) * b->n_prob + 2 * sizeof(double) * b->n_prob));
+    int *bad = (int *)tmp;
+    double *chi_p = (double *)((unsigned char *)tmp + ((sizeof(int) * b->n_prob + 15) / 16) * 16);
+    double *chi_f = chi_p + b->n_prob;
+    warm_gains_kernel<<<b->n_prob, 128, 0, st>>>(b->probs, b->n_prob, y, (const float2 *)fallback, (float2 *)gains_out, bad);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && check_chi2) {
+        BatchArgs a = batch_args(b);
+        a.gains = (float2 *)gains_out;
+        if (b->m16) batch_chi2_kernel<true><<<b->n_prob, 256, 0, st>>>(a, chi_p);
+        else batch_chi2_kernel<false><<<b->n_prob, 256, 0, st>>>(a, chi_p);
+        a.gains = (float2 *)fallback;
+        if (b->m16) batch_chi2_kernel<true><<<b->n_prob, 256, 0, st>>>(a, chi_f);
+        else batch_chi2_kernel<false><<<b->n_prob, 256, 0, st>>>(a, chi_f);
+        warm_select_kernel<<<b->n_prob, 128, 0, st>>>(b->probs, b->n_prob, chi_p, chi_f, (const float2 *)fallback,
+                                                     (float2 *)gains_out, bad);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && n_fallback) {
+        std::vector<int> hb(b->n_prob);
+        e = cudaMemcpyAsync(hb.data(), bad, sizeof(int) * b->n_prob, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        int nf = 0;
+        for (int v : hb) nf += v;
+        *n_fallback = nf;
+    }
+    cudaStreamSynchronize(st);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return b->cuda_fail(e, "batch warm start");
+    return QC_OK;
+}
+
+
+extern "C" int qc_batch_reference_gains(qc_batch *b, const void *gains_in, void *gains_out, void *stream)
+{
+    if (!b) return QC_EINVAL;
+    b->err.clear();
+    if (!gains_in || !gains_out) return b->fail(QC_EINVAL, "gains_in and gains_out are required (device)");
+    cudaStream_t st = stream ? (cudaStream_t)stream : b->own_stream;
+    reference_gains_kernel<<<b->n_prob, 128, 0, st>>>(b->probs, b->n_prob, (const float2 *)gains_in, (float2 *)gains_out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return b->cuda_fail(e, "reference gains");
     return QC_OK;
 }

@@ -519,3 +519,106 @@ def make_batch(shapes, noise: float = 0.01, device=None, noise_seed: int = 7) ->
                  np.concatenate(a2).astype(np.int32), np.array(row_off, np.int64), np.array(vis_off, np.int64),
                  np.array([s_[3] for s_ in shapes], np.int32), np.array([s_[1] for s_ in shapes], np.int32),
                  truths, setups)
+
+
+# ---------------------------------------------------------------------------
+# streams of consecutive intervals for the learned warm start
+# ---------------------------------------------------------------------------
+
+def drifting_diag_truth(n_ant: int, n_tint: int, n_fint: int, rng: np.random.Generator, amp_sigma: float = 0.05,
+                        phase_step: float = 0.08, amp_step: float = 0.01) -> np.ndarray:
+    """Diagonal gains per (time interval, frequency interval): amplitude 1+N(0,amp_sigma), phase
+    U(-pi,pi) plus a smooth frequency slope, then a random walk from one time interval to the
+    next (phase steps N(0, phase_step) rad, amplitude steps N(0, amp_step))."""
+    amp0 = 1.0 + amp_sigma * rng.standard_normal((n_ant, 2))
+    ph0 = rng.uniform(-np.pi, np.pi, size=(n_ant, 2))
+    slope = 0.5 * rng.standard_normal((n_ant, 2))
+    x = (np.arange(n_fint) + 0.5) / max(1, n_fint) - 0.5
+    dph = np.cumsum(phase_step * rng.standard_normal((n_tint, n_ant, 2)), axis=0)
+    damp = np.cumsum(amp_step * rng.standard_normal((n_tint, n_ant, 2)), axis=0)
+    ph = ph0[None, None] + slope[None, None] * x[None, :, None, None] + dph[:, None]
+    amp = amp0[None, None] + damp[:, None]
+    g = amp * np.exp(1j * ph)                                   # [tint, fint, ant, 2]
+    out = np.zeros((n_tint, n_fint, n_ant, 4), dtype=np.complex128)
+    out[..., 0] = g[..., 0]
+    out[..., 3] = g[..., 1]
+    return out
+
+
+def warmstart_observation_setup(seed: int, n_ant: int = 64, n_time: int = 300, n_chan: int = 512,
+                                f_block: int = 16, n_src: int = 50) -> Setup:
+    """Config-1-style observation (8 km east-west array, 50 sources, MeerKAT L-band) with one diagonal
+    term on intervals of 1 time x f_block channels whose gains drift from one time to the next."""
+    rng = np.random.default_rng(seed)
+    freqs = meerkat_band(n_chan)
+    ant_x = ew_array(n_ant, 8000.0, rng)
+    n_fb = -(-n_chan // f_block)
+    term = TermSpec("diag", interval_map(n_time, 1), interval_map(n_chan, f_block), n_time, n_fb)
+    term.truth = drifting_diag_truth(n_ant, n_time, n_fb, rng)
+    return draw_setup(n_ant, n_time, freqs, [term], n_src=n_src, rng=rng, ant_x=ant_x, flag_row_frac=0.05)
+
+
+def pair_problem_setups(seed: int, n_ant: int, n_time: int, n_chan: int, flag_frac: float, n_src: int = 5):
+    """Two consecutive solution intervals of one stream (same array and sky): the previous interval
+    and the current one, n_time integrations of 8 s each, with the gains drifted in between."""
+    rng = np.random.default_rng(seed)
+    freqs = 1.4e9 + 1.0e6 * (np.arange(n_chan) - (n_chan - 1) / 2.0)
+    ant_x = ew_array(n_ant, 1000.0, rng)
+    truth = drifting_diag_truth(n_ant, 2, 1, rng)
+    centre = rng.uniform(-2.0, 2.0)
+    span = n_time * 8.0 / 3600.0
+    sky_seed = int(rng.integers(1 << 31))
+    out = []
+    for k, c in enumerate((centre - span, centre)):
+        term = TermSpec("diag", np.zeros(n_time, np.int32), np.zeros(n_chan, np.int32), 1, 1)
+        term.truth = truth[k:k + 1]
+        r = np.random.default_rng(sky_seed)          # same sky for both intervals
+        su = draw_setup(n_ant, n_time, freqs, [term], n_src=n_src, rng=r, ant_x=ant_x, flag_sample_frac=flag_frac,
+                        ha_span_hours=span, ha_centre_hours=c)
+        su.rng = np.random.default_rng(seed * 7 + k + 1)
+        out.append(su)
+    return out
+
+
+def make_pair_batches(shapes, noise: float = 0.01, device=None, noise_seed: int = 11):
+    """(previous-interval batch, current-interval batch) for problems of the given shapes, written
+    straight into preallocated arrays (no concatenation copies)."""
+    setups = [pair_problem_setups(seed, na, nt, nc, ff) for (seed, na, nt, nc, ff) in shapes]
+    batches = []
+    for k in range(2):
+        sus = [s_[k] for s_ in setups]
+        row_off = np.concatenate([[0], np.cumsum([su.ant1.size for su in sus])]).astype(np.int64)
+        vis_off = np.concatenate([[0], np.cumsum([su.ant1.size * su.freqs.size for su in sus])]).astype(np.int64)
+        n_vis = int(vis_off[-1])
+        if device is None:
+            data = np.zeros((n_vis, 4), np.complex128)
+            model = np.zeros((n_vis, 4), np.complex128)
+            weight = np.zeros((n_vis, 4))
+            flag = np.zeros(n_vis, np.uint8)
+        else:
+            import torch
+            data = torch.empty((n_vis, 4), dtype=torch.complex64, device=device)
+            model = torch.empty((n_vis, 4), dtype=torch.complex64, device=device)
+            weight = torch.empty((n_vis, 4), dtype=torch.float32, device=device)
+            flag = torch.empty(n_vis, dtype=torch.uint8, device=device)
+        for i, su in enumerate(sus):
+            v0, v1 = vis_off[i], vis_off[i + 1]
+            if device is None:
+                o = make_observation(su.n_ant, su.n_time, su.freqs, su.terms, n_src=5, seed=0, noise=noise, su=su)
+                data[v0:v1] = o.data.reshape(-1, 4)
+                model[v0:v1] = o.model.reshape(-1, 4)
+                weight[v0:v1] = o.weight.reshape(-1, 4)
+                flag[v0:v1] = o.flag.reshape(-1)
+            else:
+                o = make_observation_device(su, noise, noise_seed + 2 * i + k, device)
+                data[v0:v1] = o["data"].reshape(-1, 4)
+                model[v0:v1] = o["model"].reshape(-1, 4)
+                weight[v0:v1] = o["weight"].reshape(-1, 4)
+                flag[v0:v1] = o["flag"].reshape(-1)
+        truths = [su.terms[0].truth[0, 0][:, [0, 3]].copy() for su in sus]
+        batches.append(Batch(list(shapes), data, model, weight, flag,
+                             np.concatenate([su.ant1 for su in sus]).astype(np.int32),
+                             np.concatenate([su.ant2 for su in sus]).astype(np.int32), row_off, vis_off,
+                             np.array([s_[3] for s_ in shapes], np.int32), np.array([s_[1] for s_ in shapes], np.int32),
+                             truths, sus))
+    return batches[0], batches[1]

@@ -1,0 +1,163 @@
+"""Warm-start network kernels against the FP64 MLP oracle, features against the FP64
+solver oracle, fallback rules, and the gain of a trained network over a cold start."""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import mlp as OM
+from paper_2412_10072_gb300 import qc, synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-30))
+
+
+@pytest.fixture(scope="module")
+def ws():
+    from paper_2412_10072_gb300 import warmstart
+    return warmstart
+
+
+@pytest.mark.parametrize("n", [1, 63, 64, 200, 1000])
+def test_forward_matches_oracle(ws, n):
+    rng = np.random.default_rng(n)
+    flat = OM.init(3) * 0.7
+    flat[rng.choice(flat.size, 200)] += 0.1
+    x = rng.standard_normal((n, 10)).astype(np.float32)
+    net = ws.MLP(torch.from_numpy(flat.astype(np.float32)))
+    y = net.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+    want, _ = OM.forward(flat.astype(np.float32).astype(np.float64), x.astype(np.float64))
+    assert rel(y, want) < 1e-5
+
+
+@pytest.mark.parametrize("n", [5, 32, 333, 4096])
+def test_backward_matches_oracle(ws, n):
+    rng = np.random.default_rng(10 + n)
+    flat = (OM.init(4) * 0.7).astype(np.float32)
+    x = rng.standard_normal((n, 10)).astype(np.float32)
+    t = rng.standard_normal((n, 4)).astype(np.float32)
+    net = ws.MLP(torch.from_numpy(flat))
+    xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    z = torch.empty((n, 384), dtype=torch.float32, device="cuda")
+    y = net.forward(xd, z)
+    grad = torch.zeros(OM.NPARAM, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    lib = ws._lib()
+    assert lib.qc_mlp_backward(net.params.data_ptr(), xd.data_ptr(), z.data_ptr(), y.data_ptr(), td.data_ptr(), n,
+                               grad.data_ptr(), loss.data_ptr(), None) == 0
+    torch.cuda.synchronize()
+    g_want = OM.backward(flat.astype(np.float64), x.astype(np.float64), t.astype(np.float64))
+    assert rel(grad.cpu().numpy(), g_want) < 1e-4
+    assert abs(loss.item() - OM.loss(flat.astype(np.float64), x.astype(np.float64), t.astype(np.float64))) < 1e-5
+
+
+def test_adam_step_matches_formula(ws):
+    rng = np.random.default_rng(1)
+    p = rng.standard_normal(OM.NPARAM).astype(np.float32)
+    g = rng.standard_normal(OM.NPARAM).astype(np.float32)
+    net = ws.MLP(torch.from_numpy(p.copy()))
+    net.grad.copy_(torch.from_numpy(g))
+    lib = ws._lib()
+    for step in (1, 2):
+        assert lib.qc_mlp_adam(net.params.data_ptr(), net.grad.data_ptr(), net.m.data_ptr(), net.v.data_ptr(),
+                               1e-3, 0.9, 0.999, 1e-8, step, None) == 0
+    m = 0.1 * g
+    v = 0.001 * g * g
+    p1 = p - 1e-3 * (m / 0.1) / (np.sqrt(v / 0.001) + 1e-8)
+    m2 = 0.9 * m + 0.1 * g
+    v2 = 0.999 * v + 0.001 * g * g
+    p2 = p1 - 1e-3 * (m2 / (1 - 0.81)) / (np.sqrt(v2 / (1 - 0.999 ** 2)) + 1e-8)
+    assert np.max(np.abs(net.params.cpu().numpy() - p2)) < 1e-5
+
+
+def test_features_match_oracle(ws):
+    shapes = synth.batch_shapes(8, seed_base=700, ant=(3, 9), times=(1, 3), chans=(1, 40))
+    b = synth.make_batch(shapes)
+    S = qc.BatchSolver(b.data, b.model, b.weight, b.flag, b.ant1, b.ant2, b.row_offset, b.vis_offset, b.n_chan,
+                       b.n_ant)
+    rng = np.random.default_rng(5)
+    prev = (rng.standard_normal((S.total_ant, 2)) + 1j * rng.standard_normal((S.total_ant, 2))).astype(np.complex64)
+    f = np.zeros((S.total_ant, 10), np.float32)
+    lib = ws._lib()
+    assert lib.qc_batch_features(S._h, prev.ctypes.data, f.ctypes.data, qc.QC_MEM_HOST, None) == 0
+    offs = np.concatenate([[0], np.cumsum(b.n_ant)])
+    for i in range(b.n_prob):
+        r0, r1, v0, v1 = b.row_offset[i], b.row_offset[i + 1], b.vis_offset[i], b.vis_offset[i + 1]
+        nc, rows, na = int(b.n_chan[i]), int(r1 - r0), int(b.n_ant[i])
+        D = b.data[v0:v1].reshape(rows, nc, 4)
+        M = b.model[v0:v1].reshape(rows, nc, 4)
+        F = b.flag[v0:v1].reshape(rows, nc)
+        P = O.OracleProblem(D, M, b.weight[v0:v1].reshape(rows, nc, 4), F, b.ant1[r0:r1], b.ant2[r0:r1],
+                            np.zeros(rows, np.int32), na, 1)
+        T = O.OracleTerm("diag", np.zeros(1, np.int32), np.zeros(nc, np.int32), 1, 1, na)
+        jhj, jhr = O.normal_equations(P, [T], 0)
+        fi = f[offs[i]:offs[i + 1]]
+        for a in range(na):
+            for k in range(2):
+                h = jhj[0, 0, a, k, k].real
+                if h <= 0:
+                    assert fi[a, k] == 0
+                    continue
+                z = jhr[0, 0, a, k] / h
+                assert abs(fi[a, k] - abs(z)) < 1e-4 * max(1, abs(z))
+                if abs(z) > 1e-3:
+                    assert abs(np.angle(np.exp(1j * (fi[a, 2 + k] - np.angle(z))))) < 1e-3
+            # mean |d|/|m| on the diagonal correlations over the antenna's unflagged samples
+            sel = ((b.ant1[r0:r1] == a) | (b.ant2[r0:r1] == a))[:, None] & (F == 0)
+            for k, ci in ((0, 0), (1, 3)):
+                rat = np.abs(D[..., ci]) / np.abs(M[..., ci])
+                if sel.any():
+                    assert abs(fi[a, 4 + k] - rat[sel].mean()) < 1e-4 * rat[sel].mean()
+        s = prev[offs[i]:offs[i + 1]].astype(np.complex128).sum(0)
+        g = prev[offs[i]:offs[i + 1]] * np.exp(-1j * np.angle(s))[None]
+        assert np.max(np.abs(fi[:, 6:].reshape(-1, 2, 2)[..., 0] - g.real)) < 1e-5
+        assert np.max(np.abs(fi[:, 6:].reshape(-1, 2, 2)[..., 1] - g.imag)) < 1e-5
+    S.close()
+
+
+def test_warmstart_fallbacks(ws):
+    shapes = synth.batch_shapes(6, seed_base=900, ant=(4, 8), times=(1, 3), chans=(4, 20))
+    b = synth.make_batch(shapes, device="cuda")
+    S = qc.BatchSolver(b.data, b.model, b.weight, b.flag, b.ant1, b.ant2, b.row_offset, b.vis_offset, b.n_chan,
+                       b.n_ant)
+    truth = np.concatenate(b.truths).astype(np.complex64)
+    y = torch.from_numpy(np.stack([truth.real[:, 0], truth.imag[:, 0], truth.real[:, 1], truth.imag[:, 1]], 1)
+                         .astype(np.float32)).cuda().contiguous()
+    offs = np.concatenate([[0], np.cumsum(b.n_ant)])
+    y[offs[2]:offs[3]] = float("nan")                      # problem 2: not finite
+    y[offs[4]:offs[5]] *= 3.0                               # problem 4: worse chi^2 than unit gains
+    unit = torch.ones((S.total_ant, 2), dtype=torch.complex64, device="cuda")
+    g = torch.empty_like(unit)
+    n_fb = ws.C.c_int32(0)
+    lib = ws._lib()
+    assert lib.qc_batch_warmstart(S._h, y.data_ptr(), unit.data_ptr(), 1, g.data_ptr(), ws.C.byref(n_fb), None) == 0
+    gh = g.cpu().numpy()
+    assert n_fb.value == 2
+    assert np.all(gh[offs[2]:offs[3]] == 1) and np.all(gh[offs[4]:offs[5]] == 1)
+    assert np.allclose(gh[offs[0]:offs[1]], truth[offs[0]:offs[1]])
+    S.close()
+
+
+def test_training_reduces_loss_and_warm_start_beats_cold(ws):
+    """A network trained briefly on the solver's own solutions of small observations starts held-out
+    intervals closer to the solution than unit gains: fewer iterations to the same tolerance."""
+    X, T = ws.training_set(6, seed0=31000, n_ant=16, n_time=40, n_chan=64, f_block=16, n_src=8, noise=0.05,
+                           log=lambda *a: None)
+    net, hist = ws.train(X, T, epochs=6, batch=512, lr=3e-3, log=lambda *a: None)
+    assert hist[-1]["train_loss"] < 0.5 * hist[0]["train_loss"]
+    shapes = synth.batch_shapes(48, seed_base=32000, ant=(16, 16), times=(1, 4), chans=(8, 32), flag_max=0.2)
+    prev_b, cur_b = synth.make_pair_batches(shapes, noise=0.01, device="cuda")
+    Sp = qc.BatchSolver(prev_b.data, prev_b.model, prev_b.weight, prev_b.flag, prev_b.ant1, prev_b.ant2,
+                        prev_b.row_offset, prev_b.vis_offset, prev_b.n_chan, prev_b.n_ant)
+    gp, _, _, _ = Sp.solve(torch.ones((Sp.total_ant, 2), dtype=torch.complex64, device="cuda"), max_iter=60, tol=1e-7)
+    Sp.close()
+    S = qc.BatchSolver(cur_b.data, cur_b.model, cur_b.weight, cur_b.flag, cur_b.ant1, cur_b.ant2, cur_b.row_offset,
+                       cur_b.vis_offset, cur_b.n_chan, cur_b.n_ant)
+    _, _, it_cold, _ = S.solve(torch.ones((S.total_ant, 2), dtype=torch.complex64, device="cuda"), max_iter=60)
+    g0, n_fb = ws.initial_gains(S, net, prev_gains=gp)
+    _, _, it_mlp, _ = S.solve(g0, max_iter=60)
+    S.close()
+    assert float(it_mlp.float().mean()) < float(it_cold.float().mean())

@@ -190,6 +190,40 @@ int qc_residual(qc_ctx *c, const qc_term *terms, int32_t n_terms, void *resid, i
 /* Release a context and every device buffer it owns.  NULL-safe. */
 void qc_destroy(qc_ctx *c);
 
+/*
+ * chi^2 of a one-term problem without allocating anything (the paper has no
+ * counterpart: this serves callers that must not allocate device memory, such
+ * as real-time pipelines whose device memory is reserved up front, or host
+ * frameworks that own every device buffer through their own pool).
+ *
+ * Computes the same chi^2 as qc_residual for a chain of a single term (type,
+ * n_tint, n_fint, t_map, f_map, gains as in qc_term), with every argument in
+ * DEVICE memory: data/model complex64 [n_row][n_chan][4] and weight float32
+ * [n_row][n_chan][4] (16-byte aligned), flag uint8 [n_row][n_chan] or NULL,
+ * ant1/ant2/time_idx int32 [n_row], t_map [n_time], f_map [n_chan], gains in the
+ * qc_term layout, and the result written to *chi2 (one device double, FP64
+ * sum in a fixed order).  Kernels are enqueued on `stream` (NULL: the legacy
+ * default stream); the call returns without synchronising.
+ *
+ * Scratch: the kernel-layout gain table and the per-CTA partial sums live in a
+ * static device array of (QC_NOALLOC_MAX_GAINS * 32 + QC_NOALLOC_MAX_BLOCKS * 8)
+ * bytes (2 MiB + 8 KiB) that every device which loads the library keeps until
+ * the process exits.  Problems with n_tint * n_fint * n_ant > QC_NOALLOC_MAX_GAINS
+ * are rejected with QC_EINVAL (message in qc_last_error(NULL)).  The first call
+ * on a device looks up the device address of that array (cudaGetSymbolAddress,
+ * no allocation); make that first call before capturing a stream into a CUDA
+ * graph.  Every call reuses the same array and leaves its contents behind:
+ * calls on one device whose kernels may overlap (for example on two streams)
+ * race on it, so order them (one stream, or events).  Each device has its own
+ * copy, so calls on different devices do not interfere.
+ */
+#define QC_NOALLOC_MAX_GAINS   65536
+#define QC_NOALLOC_MAX_BLOCKS  1024
+int qc_residual_noalloc(int32_t n_row, int32_t n_chan, int32_t n_ant, const void *data, const void *model,
+                        const float *weight, const uint8_t *flag, const int32_t *ant1, const int32_t *ant2,
+                        const int32_t *time_idx, int32_t type, int32_t n_tint, int32_t n_fint, const int32_t *t_map,
+                        const int32_t *f_map, const void *gains, double *chi2, void *stream);
+
 /* Message of the last failed call on `c` ("" if none); with c == NULL, of the last failed qc_create. */
 const char *qc_last_error(const qc_ctx *c);
 

@@ -347,6 +347,9 @@ extern "C" int qc_create(const qc_problem *p, qc_ctx **out)
 
 extern "C" void qc_destroy(qc_ctx *c) { delete c; }
 
+// lets the allocation-free entry point report through qc_last_error(NULL)
+void qc_internal_set_error(const char *msg) { g_create_error = msg; }
+
 extern "C" const char *qc_last_error(const qc_ctx *c)
 {
     if (!c) return g_create_error.c_str();

@@ -46,7 +46,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mixed", action="store_true", help="FP16 model storage with per-baseline scales")
+    ap.add_argument("--workload", default="plain", choices=["plain", "mixed", "batched", "warmstart"],
+                    help="plain: the large two-term solve; mixed: the same with FP16 model storage; batched: 4096 "
+                         "independent intervals in one persistent launch; warmstart: the batched solve at 64 "
+                         "antennas from cold, previous-interval and network starts")
+    ap.add_argument("--mixed", action="store_true", help="same as --workload mixed")
+    ap.add_argument("--n-prob", type=int, default=4096, help="problems of the batched / warmstart workloads")
+    ap.add_argument("--looped", type=int, default=256, help="problems timed one by one for the comparison")
+    ap.add_argument("--checkpoint", default=None, help="warm-start network (.npz)")
     ap.add_argument("--n-time", type=int, default=300)
     ap.add_argument("--n-chan", type=int, default=512)
     ap.add_argument("--n-ant", type=int, default=64)
@@ -73,7 +80,7 @@ def measured_peaks():
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for name in ("qc_kernels.cuh", "qc_jones.cuh", "qc_acc.cu"):
+    for name in ("qc_kernels.cuh", "qc_jones.cuh", "qc_async.cuh", "qc_acc_inst.cuh", "qc_acc_diag.cu", "qc_acc_full.cu"):
         with open(os.path.join(ROOT, "paper_2412_10072_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -183,6 +190,34 @@ def cpu_baseline(args, dev_obs, setup, n_times=2, max_iter=4):
                       f"<= {max_iter} iterations each, {dt:.1f} s single-threaded FP64 C"}
 
 
+def mixed_accuracy(n_ant=16, n_time=8, n_chan=64, epochs=3):
+    """Gain and chi^2 errors against the FP64 oracle of the plain complex64 run and of the FP16-model
+    run, on a reduced two-term workload of the same recipe (the oracle finishes it in seconds)."""
+    import numpy as np
+    import oracle as O
+    from oracle.gauge import chain_products, reference_chain, rel_err
+    from paper_2412_10072_gb300 import qc, synth
+    obs = synth.plain_large(seed=7, n_ant=n_ant, n_time=n_time, n_chan=n_chan, noise=0.05, flag_row_frac=0.1)
+    P = O.OracleProblem.from_obs(obs)
+    ot = [O.OracleTerm.from_spec(s_, obs.n_ant) for s_ in obs.terms]
+    O.solve(P, ot, n_epochs=epochs, damping_mode=1)
+    ochi2 = O.residual(P, ot)
+    Co = reference_chain(chain_products([t.jones() for t in ot], [t.t_map for t in ot], [t.f_map for t in ot],
+                                        n_time, n_chan))
+    out = {}
+    for name, m16 in (("c64", False), ("fp16_model", True)):
+        S = qc.Solver.from_obs(obs, model_fp16=m16)
+        gt = [qc.Term.from_spec(s_, obs.n_ant) for s_ in obs.terms]
+        S.solve(gt, n_epochs=epochs)
+        chi2 = S.residual(gt)
+        S.close()
+        Cg = reference_chain(chain_products([np.asarray(t.gains, np.complex128) for t in gt],
+                                            [t.t_map for t in gt], [t.f_map for t in gt], n_time, n_chan))
+        out[name] = {"gain_rel_err": rel_err(Cg, Co), "chi2_rel_err": abs(chi2 - ochi2) / ochi2}
+    out["case"] = f"{n_ant} ant, {n_time} t x {n_chan} ch, G full + B diag, {epochs} epochs, sigma 0.05"
+    return out
+
+
 def run_reference(args):
     """--impl reference: the FP64 oracle as it stands on the host cores, on a bounded sample of the
     same workload (the first 2 times of the 64-antenna, 512-channel observation; 1 epoch, <= 2
@@ -218,6 +253,13 @@ def run_reference(args):
 
 def main():
     args = parse()
+    if args.mixed:
+        args.workload = "mixed"
+    args.mixed = args.workload == "mixed"
+    if args.workload == "batched" and args.impl == "ours":
+        return run_batched(args)
+    if args.workload == "warmstart" and args.impl == "ours":
+        return run_warmstart(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -305,6 +347,7 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args, obs, setup)
+    accuracy = mixed_accuracy() if (args.mixed and rank == 0) else None
 
     # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region ----
     e2e = None
@@ -358,11 +401,283 @@ def main():
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                        "gen_s": round(t_gen, 2)},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clock_info,
+            **({"accuracy_vs_fp64_oracle": accuracy} if accuracy else {}),
             "gpu_launches": int(launches), "accumulate_launches_with_work": int(acc_launches),
             "vis_iters": int(vis_iters_all),
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# batched intervals (4096 independent problems, one persistent launch)
+# ---------------------------------------------------------------------------
+
+def _dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local, dist
+
+
+def _referenced(g, offs):
+    """Per-problem diagonal gains rotated by the conjugate unit phase of antenna 0 (gauge removal)."""
+    import numpy as np
+    out = g.copy()
+    for i in range(len(offs) - 1):
+        r = g[offs[i]:offs[i] + 1]
+        ph = np.where(np.abs(r) > 0, np.conj(r) / np.maximum(np.abs(r), 1e-30), 1.0)
+        out[offs[i]:offs[i + 1]] = g[offs[i]:offs[i + 1]] * ph
+    return out
+
+
+def _per_problem_err(g, ref, offs):
+    import numpy as np
+    a, b = _referenced(g, offs), _referenced(ref, offs)
+    return np.array([np.max(np.abs(a[offs[i]:offs[i + 1]] - b[offs[i]:offs[i + 1]])) /
+                     max(np.max(np.abs(b[offs[i]:offs[i + 1]])), 1e-30) for i in range(len(offs) - 1)])
+
+
+def _looped_plain(b, idx, tol, max_iter, gains0=None):
+    """Solve the problems `idx` one by one through qc_create/qc_solve (config-0-style plain launches).
+    Returns (seconds, vis_iters, gains [sum over idx n_ant][2])."""
+    import numpy as np
+    import torch
+    from paper_2412_10072_gb300 import qc
+    ctxs = []
+    for i in idx:
+        r0, r1, v0, v1 = b.row_offset[i], b.row_offset[i + 1], b.vis_offset[i], b.vis_offset[i + 1]
+        nc, rows = int(b.n_chan[i]), int(r1 - r0)
+        s = qc.Solver(b.data[v0:v1].view(rows, nc, 4), b.model[v0:v1].view(rows, nc, 4),
+                      b.weight[v0:v1].view(rows, nc, 4), b.flag[v0:v1].view(rows, nc), b.ant1[r0:r1], b.ant2[r0:r1],
+                      np.zeros(rows, np.int32), int(b.n_ant[i]), 1)
+        ctxs.append(s)
+    torch.cuda.synchronize()
+    terms = []
+    t0 = time.perf_counter()
+    vi = 0
+    for k, i in enumerate(idx):
+        nc, na = int(b.n_chan[i]), int(b.n_ant[i])
+        g = None
+        if gains0 is not None:
+            g = np.zeros((1, 1, na, 4), np.complex64)
+            g[0, 0, :, 0] = gains0[k][:, 0]
+            g[0, 0, :, 3] = gains0[k][:, 1]
+        t = qc.Term("diag", np.zeros(1, np.int32), np.zeros(nc, np.int32), 1, 1, na, gains=g, max_iter=max_iter,
+                    tol=tol)
+        st = ctxs[k].solve([t])
+        vi += st.vis_iters
+        terms.append(t)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    for s in ctxs:
+        s.close()
+    gains = np.concatenate([t.gains[0, 0][:, [0, 3]] for t in terms])
+    return dt, vi, gains
+
+
+def run_batched(args):
+    import numpy as np
+    import torch
+    from paper_2412_10072_gb300 import qc, synth
+    world, rank, local, dist = _dist_setup()
+    # weak scaling: every rank solves its own 4096 problems (independent intervals, no collective)
+    shapes = synth.batch_shapes(args.n_prob, seed_base=1000 + rank * args.n_prob)
+    t_gen = time.perf_counter()
+    b = synth.make_batch(shapes, device=f"cuda:{local}")
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
+    S = qc.BatchSolver(b.data, b.model, b.weight, b.flag, b.ant1, b.ant2, b.row_offset, b.vis_offset, b.n_chan,
+                       b.n_ant)
+    stream = torch.cuda.Stream()
+    best, n_tried = S.autotune(stream=stream)
+    unit = torch.ones((S.total_ant, 2), dtype=torch.complex64, device="cuda")
+    for _ in range(args.warmup):
+        S.solve(unit.clone(), stream=stream)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    gains = [unit.clone() for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    stats = [S.solve(gains[k], stream=stream)[3] for k in range(args.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clock_info = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    vis_iters = sum(s.vis_iters for s in stats)
+    byts = sum(s.bytes for s in stats)
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        v = torch.tensor([float(vis_iters)], dtype=torch.float64, device="cuda")
+        dist.all_reduce(v)
+        ms, vis_all = float(t.item()), float(v.item())
+    else:
+        vis_all = float(vis_iters)
+    value = vis_all / (ms / 1e3)
+    peaks, src = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = byts / (ms / 1e3) / 1e9
+    # looped plain launches on a sample of the same problems
+    rng = np.random.default_rng(0)
+    idx = np.sort(rng.choice(b.n_prob, size=min(args.looped, b.n_prob), replace=False))
+    dt_loop, vi_loop, _ = _looped_plain(b, idx, 1e-6, 20)
+    loop_value = vi_loop / dt_loop
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+        t0 = time.perf_counter()
+        vi = 0
+        k = 0
+        while time.perf_counter() - t0 < 10.0 and k < b.n_prob:
+            i = int(idx[k % idx.size]); k += 1
+            r0, r1, v0, v1 = b.row_offset[i], b.row_offset[i + 1], b.vis_offset[i], b.vis_offset[i + 1]
+            nc, rows = int(b.n_chan[i]), int(r1 - r0)
+            P = O.OracleProblem(b.data[v0:v1].cpu().numpy().reshape(rows, nc, 4),
+                                b.model[v0:v1].cpu().numpy().reshape(rows, nc, 4),
+                                b.weight[v0:v1].cpu().numpy().reshape(rows, nc, 4),
+                                b.flag[v0:v1].cpu().numpy().reshape(rows, nc), b.ant1[r0:r1], b.ant2[r0:r1],
+                                np.zeros(rows, np.int32), int(b.n_ant[i]), 1)
+            T = O.OracleTerm("diag", np.zeros(1, np.int32), np.zeros(nc, np.int32), 1, 1, int(b.n_ant[i]))
+            it = O.solve(P, [T], damping_mode=1)[0]
+            vi += rows * nc * int(it[0, 0])
+        dt = time.perf_counter() - t0
+        cpu = {"value": vi / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{k} of the {b.n_prob} problems solved one by one, {dt:.1f} s single-threaded FP64 C"}
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": f"batched: {args.n_prob} independent diagonal-gain intervals, ant U{{7..64}}, "
+                                   "times U{1..16}, chans U{1..64}, flags U(0,0.5), one persistent launch",
+                       "n_vis": b.n_vis, "input_bytes_per_gpu": int(b.n_vis * 81),
+                       "l2": "inputs larger than L2 (129 MB); a small problem may stay in L2 across its iterations",
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU", "gen_s": round(t_gen, 1)},
+            "autotune": {"threads": best.threads, "ctas_per_sm": best.ctas_per_sm, "schedule": best.schedule,
+                         "candidates": n_tried, "best_ms": best.ms},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                         "traffic": None, "kernel": "batch_kernel (persistent, whole solve)",
+                         "peak_source": f"{src} hbm_gbs (MEASURED_PEAKS.json)",
+                         "mean_iters": stats[-1].mean_iters},
+            "looped_plain": {"problems": int(idx.size), "value": loop_value, "unit": UNIT, "seconds": dt_loop,
+                             "speedup_of_batched": value / loop_value},
+            "cpu_baseline": cpu, "e2e": None, "clocks": clock_info,
+            "gpu_launches": args.steps, "vis_iters": int(vis_all)}), flush=True)
+    S.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# learned warm start at 64 antennas, and time to tolerance against looped plain solves
+# ---------------------------------------------------------------------------
+
+def run_warmstart(args):
+    import numpy as np
+    import torch
+    from paper_2412_10072_gb300 import qc, synth
+    from paper_2412_10072_gb300 import warmstart as ws
+    world, rank, local, dist = _dist_setup()
+    dev = f"cuda:{local}"
+    ckpt = args.checkpoint or ws.DEFAULT_CHECKPOINT
+    net = ws.MLP.load(ckpt, device=dev)
+    shapes = synth.batch_shapes(args.n_prob, seed_base=50000 + rank * args.n_prob, ant=(64, 64))
+    offs = np.concatenate([[0], np.cumsum([s_[1] for s_ in shapes])])
+    # previous intervals: solved untimed, only their gains are kept
+    t_gen = time.perf_counter()
+    prev_b, _ = synth.make_pair_batches(shapes, device=dev, which=(0,))
+    Sp = qc.BatchSolver(prev_b.data, prev_b.model, prev_b.weight, prev_b.flag, prev_b.ant1, prev_b.ant2,
+                        prev_b.row_offset, prev_b.vis_offset, prev_b.n_chan, prev_b.n_ant)
+    gp, _, _, _ = Sp.solve(torch.ones((Sp.total_ant, 2), dtype=torch.complex64, device=dev), max_iter=50, tol=1e-8)
+    Sp.close()
+    del prev_b, Sp
+    torch.cuda.empty_cache()
+    _, b = synth.make_pair_batches(shapes, device=dev, which=(1,))
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
+    S = qc.BatchSolver(b.data, b.model, b.weight, b.flag, b.ant1, b.ant2, b.row_offset, b.vis_offset, b.n_chan,
+                       b.n_ant)
+    S16 = qc.BatchSolver(b.data, b.model, b.weight, b.flag, b.ant1, b.ant2, b.row_offset, b.vis_offset, b.n_chan,
+                         b.n_ant, model_fp16=True)
+    stream = torch.cuda.Stream()
+    S.autotune(stream=stream)
+    S16.autotune(stream=stream)
+    unit = torch.ones((S.total_ant, 2), dtype=torch.complex64, device=dev)
+    ref, _, _, _ = S.solve(gp.clone(), max_iter=200, tol=1e-10, stream=stream)
+    ref_h = ref.cpu().numpy()
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1)
+
+    arms = {}
+    for name, solver, start in (("cold", S, "unit"), ("prev", S, "prev"), ("mlp", S, "mlp"),
+                                ("mlp_fp16", S16, "mlp")):
+        res = {}
+        for tol in (1e-4, 1e-6):
+            for _ in range(max(1, args.warmup)):       # warm the launch path
+                solver.solve(unit.clone(), max_iter=20, tol=tol, stream=stream)
+
+            def run():
+                n_fb = 0
+                if start == "unit":
+                    g0 = unit.clone()
+                elif start == "prev":
+                    g0 = gp.clone()
+                else:
+                    g0, n_fb = ws.initial_gains(solver, net, prev_gains=gp, stream=stream)
+                g, _, it, st = solver.solve(g0, max_iter=20, tol=tol, stream=stream)
+                return g, it, st, n_fb
+
+            (g, it, st, n_fb), ms = timed(run)
+            err = _per_problem_err(g.cpu().numpy(), ref_h, offs)
+            res[f"tol{tol:g}"] = {"ms": ms, "mean_iters": float(it.float().mean()), "max_iters": int(it.max()),
+                                  "median_err": float(np.median(err)), "frac_within_1e-4": float(np.mean(err <= 1e-4)),
+                                  "fallbacks": int(n_fb)}
+        arms[name] = res
+    # the plain GPU solve: config-0-style single-problem launches, looped
+    rng = np.random.default_rng(1)
+    idx = np.sort(rng.choice(b.n_prob, size=min(args.looped, b.n_prob), replace=False))
+    dt_loop, vi_loop, g_loop = _looped_plain(b, idx, 1e-4, 20)
+    sub_offs = np.concatenate([[0], np.cumsum(b.n_ant[idx])])
+    ref_sub = np.concatenate([ref_h[offs[i]:offs[i + 1]] for i in idx])
+    err_loop = _per_problem_err(g_loop, ref_sub, sub_offs)
+    plain_all_ms = dt_loop * 1e3 * b.n_prob / idx.size
+    fast_ms = arms["mlp_fp16"]["tol0.0001"]["ms"]
+    out = {"metric": "time to 1e-4 gain tolerance (batched + warm start + FP16 model vs looped plain solves)",
+           "value": plain_all_ms / fast_ms, "unit": "x speed-up", "n_gpus": world, "steps": 1, "warmup": args.warmup,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64+f16", "data": "synthetic",
+           "config": {"workload": f"warm start: {args.n_prob} intervals of 64 antennas, times U{{1..16}}, chans "
+                                  "U{1..64}, flags U(0,0.5); previous interval of each solved first",
+                      "n_vis": b.n_vis, "gen_s": round(t_gen, 1), "checkpoint": os.path.basename(ckpt)},
+           "arms": arms,
+           "looped_plain": {"problems": int(idx.size), "seconds": dt_loop, "extrapolated_ms": plain_all_ms,
+                            "median_err": float(np.median(err_loop)),
+                            "frac_within_1e-4": float(np.mean(err_loop <= 1e-4))}}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    S.close()
+    S16.close()
+    if dist:
         dist.destroy_process_group()
 
 

@@ -346,7 +346,9 @@ const char *qc_batch_last_error(const qc_batch *b);
  * features; Algorithm 1 then iterates from them as usual.
  *
  * Network: Linear(10 -> 128) GELU, Linear(128 -> 128) GELU,
- * Linear(128 -> 128) GELU, Linear(128 -> 4); GELU(z) = z (1 + erf(z/sqrt 2))/2.
+ * Linear(128 -> 128) GELU, Linear(128 -> 4), plus a skip connection that adds
+ * input features 6..9 (the previous-interval gains) to the 4 outputs, so the
+ * layers learn the correction to them; GELU(z) = z (1 + erf(z/sqrt 2))/2.
  * Parameters are one float32 buffer of QC_MLP_NPARAM values: W1 [128][10],
  * b1 [128], W2 [128][128], b2, W3 [128][128], b3, W4 [4][128], b4 (weights
  * row-major [out][in]).  Outputs per antenna: (Re g_XX, Im g_XX, Re g_YY,

@@ -1,7 +1,8 @@
 """FP64 numpy reference of the warm-start multilayer perceptron (test infrastructure only).
 
 Network: Linear(10 -> 128) GELU, Linear(128 -> 128) GELU, Linear(128 -> 128) GELU,
-Linear(128 -> 4), GELU(z) = z (1 + erf(z / sqrt 2)) / 2, mean-squared-error loss.
+Linear(128 -> 4) plus the skip term x[6:10] (previous-interval gains passed through),
+GELU(z) = z (1 + erf(z / sqrt 2)) / 2, mean-squared-error loss.
 Parameters use the flat layout of the library: W1 [128][10], b1, W2 [128][128], b2,
 W3 [128][128], b3, W4 [4][128], b4.  Written directly from the chain rule; pinned by
 closed-form GELU values and central finite differences of the loss.
@@ -49,7 +50,7 @@ def forward(flat, x):
     a2 = gelu(z2)
     z3 = a2 @ p["W3"].T + p["b3"]
     a3 = gelu(z3)
-    y = a3 @ p["W4"].T + p["b4"]
+    y = a3 @ p["W4"].T + p["b4"] + x[:, 6:10]
     return y, (z1, a1, z2, a2, z3, a3)
 
 

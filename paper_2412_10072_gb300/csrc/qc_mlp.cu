@@ -22,6 +22,7 @@ namespace {
 using namespace qc;
 
 constexpr int IN = QC_MLP_IN, HID = QC_MLP_HIDDEN, OUT = QC_MLP_OUT;
+constexpr int SKIP = 6;           // first input feature passed straight to the outputs
 // parameter offsets inside the flat float buffer
 constexpr int W1 = 0, B1 = W1 + HID * IN, W2 = B1 + HID, B2 = W2 + HID * HID, W3 = B2 + HID, B3 = W3 + HID * HID,
               W4 = B3 + HID, B4 = W4 + OUT * HID, NPARAM = B4 + OUT;
@@ -34,7 +35,9 @@ __device__ __forceinline__ float gelu_d(float z)
 }
 
 // ---------------------------------------------------------------------------
-// forward: y = W4 g(W3 g(W2 g(W1 x + b1) + b2) + b3) + b4,  g = GELU
+// forward: y = x[6..9] + W4 g(W3 g(W2 g(W1 x + b1) + b2) + b3) + b4,  g = GELU
+// (the skip term passes the previous-interval gain features straight through,
+// so the layers learn the correction to them)
 // ---------------------------------------------------------------------------
 
 constexpr int FR = 64;            // rows per CTA tile
@@ -101,7 +104,7 @@ __global__ void __launch_bounds__(FT) mlp_forward_kernel(const float *__restrict
         for (int i = threadIdx.x; i < FR * OUT; i += blockDim.x) {
             const int r = i / OUT, j = i % OUT;
             if (r >= nr) continue;
-            float s = w[B4 + j];
+            float s = w[B4 + j] + x[(row0 + r) * IN + SKIP + j];
             for (int k = 0; k < HID; ++k) s = fmaf(h0[r * HID + k], w[W4 + j * HID + k], s);
             y[(row0 + r) * OUT + j] = s;
         }

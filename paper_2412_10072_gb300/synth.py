@@ -580,12 +580,13 @@ def pair_problem_setups(seed: int, n_ant: int, n_time: int, n_chan: int, flag_fr
     return out
 
 
-def make_pair_batches(shapes, noise: float = 0.01, device=None, noise_seed: int = 11):
+def make_pair_batches(shapes, noise: float = 0.01, device=None, noise_seed: int = 11, which=(0, 1)):
     """(previous-interval batch, current-interval batch) for problems of the given shapes, written
-    straight into preallocated arrays (no concatenation copies)."""
+    straight into preallocated arrays (no concatenation copies).  ``which`` selects the batches to
+    build (0: previous, 1: current); the others are returned as None."""
     setups = [pair_problem_setups(seed, na, nt, nc, ff) for (seed, na, nt, nc, ff) in shapes]
-    batches = []
-    for k in range(2):
+    batches = [None, None]
+    for k in which:
         sus = [s_[k] for s_ in setups]
         row_off = np.concatenate([[0], np.cumsum([su.ant1.size for su in sus])]).astype(np.int64)
         vis_off = np.concatenate([[0], np.cumsum([su.ant1.size * su.freqs.size for su in sus])]).astype(np.int64)
@@ -616,7 +617,7 @@ def make_pair_batches(shapes, noise: float = 0.01, device=None, noise_seed: int 
                 weight[v0:v1] = o["weight"].reshape(-1, 4)
                 flag[v0:v1] = o["flag"].reshape(-1)
         truths = [su.terms[0].truth[0, 0][:, [0, 3]].copy() for su in sus]
-        batches.append(Batch(list(shapes), data, model, weight, flag,
+        batches[k] = (Batch(list(shapes), data, model, weight, flag,
                              np.concatenate([su.ant1 for su in sus]).astype(np.int32),
                              np.concatenate([su.ant2 for su in sus]).astype(np.int32), row_off, vis_off,
                              np.array([s_[3] for s_ in shapes], np.int32), np.array([s_[1] for s_ in shapes], np.int32),

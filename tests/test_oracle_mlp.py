@@ -19,12 +19,13 @@ def test_gelu_closed_forms():
     assert np.max(np.abs(fd - mlp.gelu_grad(z))) < 1e-8
 
 
-def test_bias_only_network_is_constant():
+def test_bias_only_network_adds_bias_to_the_skip_features():
     flat = np.zeros(mlp.NPARAM)
     p = mlp.unpack(flat)
     p["b4"] = np.array([1.0, -2.0, 0.5, 3.0])
-    y, _ = mlp.forward(mlp.pack(p), np.random.default_rng(0).standard_normal((5, 10)))
-    assert np.array_equal(y, np.tile(p["b4"], (5, 1)))
+    x = np.random.default_rng(0).standard_normal((5, 10))
+    y, _ = mlp.forward(mlp.pack(p), x)
+    assert np.array_equal(y, x[:, 6:10] + p["b4"][None])
 
 
 def test_layout_size():

@@ -283,6 +283,7 @@ typedef struct {
     int32_t ctas_per_sm;         /* resident CTAs per SM (0: tuned or occupancy)          */
     int32_t schedule;            /* QC_SCHED_*                                           */
     int32_t use_graph;           /* 1: replay the persistent launch as a CUDA graph       */
+    int32_t depth;               /* copy stages in flight per warp, 3/4/6 (0: tuned or 4)  */
 } qc_batch_opts;
 
 typedef struct {
@@ -292,6 +293,7 @@ typedef struct {
     int32_t n_iter_max;
     double mean_iters;
     int32_t threads, ctas_per_sm, schedule, grid;   /* launch configuration used          */
+    int32_t depth;
 } qc_batch_stats;
 
 /* Validate and stage a batch (host arrays copied, device arrays borrowed). */
@@ -304,7 +306,9 @@ int qc_batch_create(const qc_batch_problem *p, qc_batch **out);
  * per iteration it forms the residual of every sample, accumulates the
  * per-antenna diagonal JHJ / JHr blocks (Eq. jhj_entry_simplified,
  * Eq. jhr_entry_simplified) in shared memory and updates the gains with an
- * FP64 block solve (Eq. update).
+ * FP64 block solve (Eq. update).  The CTA's warps stream contiguous runs of
+ * 32-sample steps through per-warp rings of `depth` asynchronous-copy stages
+ * in shared memory; flagged samples and autocorrelations are not read.
  *   gains      : in/out [sum n_ant][2] complex64; read as g_0.
  *   gain_flags : out [sum n_ant] int8 or NULL (1: no data for the antenna).
  *   iters      : out [n_prob] int32 or NULL.
@@ -316,8 +320,9 @@ int qc_batch_solve(qc_batch *b, void *gains, int8_t *gain_flags, int32_t *iters,
 /*
  * Autotuner: time the batch solve (from unit gains, `base` options, results
  * discarded) for every candidate launch shape -- threads per CTA in
- * {128, 256, 512}, resident CTAs per SM in {1, 2, 4}, schedule in {LPT,
- * static} -- and keep the fastest for later solves with QC_SCHED_AUTO /
+ * {128, 256, 512} (the warps that share one problem), copy stages per warp
+ * in {3, 4, 6}, resident CTAs per SM in {1, 2, 4} (as shared memory allows),
+ * schedule in {LPT, static} -- and keep the fastest for later solves with QC_SCHED_AUTO /
  * threads = 0.  Results are cached per shape class of the batch (problem
  * count and size histogram).  best (nullable) receives the chosen shape and
  * its time; `n_tried` (nullable) the number of candidates timed.

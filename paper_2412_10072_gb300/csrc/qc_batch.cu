@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "../../include/qc.h"
+#include "qc_async.cuh"
 #include "qc_jones.cuh"
 
 namespace {
@@ -68,16 +69,76 @@ __device__ __forceinline__ float run_sum(float v, int lane, unsigned run_end)
     return v;
 }
 
-template <bool M16>
+// Segmented flush of one side's register sums: lanes with equal consecutive keys
+// are summed by shuffles and the head of each run adds the six sums into the
+// problem's shared accumulators.  key < 0: nothing to add.
+__device__ __forceinline__ void flush_runs(float (&s)[6], int key, int lane, float *acc)
+{
+    const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+    const bool head = lane == 0 || key != prev;
+    const unsigned heads = __ballot_sync(0xffffffffu, head);
+    const unsigned after = heads & ~((2u << lane) - 1u);
+    const unsigned run_end = after ? (unsigned)(__ffs(after) - 1) : 32u;
+    if (heads == 1u) {
+        // one run over the whole warp: transposed reduction (each halving step
+        // exchanges half of the remaining values), 9 shuffles for the 6 sums;
+        // lane l ends with the total of value (l>>4&1)*4 + (l>>3&1)*2 + (l>>2&1)
+        const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+        float t4[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float lo = s[i], hi = i + 4 < 6 ? s[i + 4] : 0.f;
+            t4[i] = (h16 ? hi : lo) + __shfl_xor_sync(0xffffffffu, h16 ? lo : hi, 16);
+        }
+        float t2[2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+            t2[i] = (h8 ? t4[i + 2] : t4[i]) + __shfl_xor_sync(0xffffffffu, h8 ? t4[i] : t4[i + 2], 8);
+        float t1 = (h4 ? t2[1] : t2[0]) + __shfl_xor_sync(0xffffffffu, h4 ? t2[0] : t2[1], 4);
+        t1 += __shfl_xor_sync(0xffffffffu, t1, 2);
+        t1 += __shfl_xor_sync(0xffffffffu, t1, 1);
+        const int idx = (h16 ? 4 : 0) + (h8 ? 2 : 0) + (h4 ? 1 : 0);
+        if ((lane & 3) == 0 && idx < 6 && key >= 0) atomicAdd(acc + key * 6 + idx, t1);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            const float sum = run_sum(s[i], lane, run_end);
+            if (head && key >= 0) atomicAdd(acc + key * 6 + i, sum);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) s[i] = 0.f;
+}
+
+// Shared-memory layout of batch_kernel: per warp a ring of DEPTH stages, each
+// stage V4 words x 32 lanes of 16 bytes (d: 2 words, m: 2 words or 1 FP16 word,
+// w: 1 word) and 32 packed keys; then the per-antenna state.
+template <bool M16> struct BatchRing { static constexpr int V4 = M16 ? 4 : 5; };
+
+template <bool M16, int DEPTH>
+__host__ __device__ constexpr size_t batch_ring_bytes_per_warp()
+{
+    return (size_t)DEPTH * 32 * (BatchRing<M16>::V4 * 16 + 8);
+}
+
+// One warp step covers 32 consecutive samples of the problem (sample index
+// s = row * n_chan + chan, so each 16-byte word of a step is one contiguous
+// 512-byte span whatever n_chan is).  Warps own contiguous ranges of steps.
+template <bool M16, int DEPTH>
 __global__ void __launch_bounds__(512) batch_kernel(const BatchArgs a)
 {
+    constexpr int V4 = BatchRing<M16>::V4;
     extern __shared__ __align__(16) unsigned char smem[];
-    double2 *g64 = reinterpret_cast<double2 *>(smem);                          // [max_ant][2] (16-byte aligned)
-    float *acc = reinterpret_cast<float *>(g64 + a.max_ant * 2);              // [max_ant][6]
-    float2 *g32 = reinterpret_cast<float2 *>(acc + a.max_ant * 6);            // [max_ant][2]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, n_warps = blockDim.x >> 5;
+    float4 *ring = reinterpret_cast<float4 *>(smem) + (size_t)warp * DEPTH * V4 * 32;    // [DEPTH][V4][32]
+    int2 *meta = reinterpret_cast<int2 *>(reinterpret_cast<float4 *>(smem) + (size_t)n_warps * DEPTH * V4 * 32) +
+                 (size_t)warp * DEPTH * 32;                                                  // [DEPTH][32]
+    unsigned char *tail = smem + (size_t)n_warps * batch_ring_bytes_per_warp<M16, DEPTH>();
+    double2 *g64 = reinterpret_cast<double2 *>(tail);                         // [max_ant][2]
+    float4 *g32 = reinterpret_cast<float4 *>(g64 + a.max_ant * 2);            // [max_ant] (g_XX, g_YY)
+    float *acc = reinterpret_cast<float *>(g32 + a.max_ant);                  // [max_ant][6]
     __shared__ double red[2][32];
     __shared__ int s_prob, s_done;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, n_warps = blockDim.x >> 5;
     int static_k = 0;
 
     for (;;) {
@@ -92,92 +153,148 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchArgs a)
         if (pi < 0) break;
         const BProb P = a.probs[pi];
         const int na = P.n_ant, nc = P.n_chan;
-        for (int i = tid; i < na * 2; i += blockDim.x) {
-            const float2 g = a.gains[(size_t)P.gain_off * 2 + i];
-            g32[i] = g;
-            g64[i] = make_double2(g.x, g.y);
+        for (int i = tid; i < na; i += blockDim.x) {
+            const float2 g0 = a.gains[(size_t)(P.gain_off + i) * 2], g1 = a.gains[(size_t)(P.gain_off + i) * 2 + 1];
+            g32[i] = make_float4(g0.x, g0.y, g1.x, g1.y);
+            g64[2 * i] = make_double2(g0.x, g0.y);
+            g64[2 * i + 1] = make_double2(g1.x, g1.y);
         }
-        // tile of a warp step: rows x channels
-        const bool wide = nc >= 32;
-        const int rpi = wide ? 1 : 32 / nc;                 // rows per warp step
-        const int chunks = wide ? (nc + 31) / 32 : 1;
-        const int lr = wide ? 0 : lane / nc, lc = wide ? lane : lane % nc;
-        const bool lane_ok = wide || lane < rpi * nc;
-        const long n_steps = wide ? (long)P.n_rows * chunks : ((long)P.n_rows + rpi - 1) / rpi;
-        int k = 0;
+        const long n_samp = (long)P.n_rows * nc;
+        const long n_steps = (n_samp + 31) >> 5;
+        const long per_warp = (n_steps + n_warps - 1) / n_warps;
+        const long st_begin = (long)warp * per_warp, st_end = st_begin + per_warp < n_steps ? st_begin + per_warp : n_steps;
+        const int q32 = 32 / nc, r32 = 32 % nc;              // advance of (row, chan) per step
+        const float4 *vis = a.vis + 2 * P.vis_off;
+        const float4 *mod = M16 ? nullptr : a.model + 2 * P.vis_off;
+        const uint4 *mod16 = M16 ? a.model16 + P.vis_off : nullptr;
+        const float4 *wgt = a.weight + P.vis_off;
+        const uint8_t *flg = a.flag ? a.flag + P.vis_off : nullptr;
+        const int2 *ants = a.ants + P.row_off;
+        const float *rsc = M16 ? a.row_scale + P.row_off : nullptr;
+        int k;
         for (k = 1; k <= a.max_iter; ++k) {
             for (int i = tid; i < na * 6; i += blockDim.x) acc[i] = 0.f;
             __syncthreads();
-            for (long t = warp; t < n_steps; t += n_warps) {
-                int row, c;
-                if (wide) { row = (int)(t / chunks); c = (int)(t % chunks) * 32 + lane; }
-                else { row = (int)t * rpi + lr; c = lc; }
-                const bool in = lane_ok && row < P.n_rows && c < nc;
-                int p = -1, q = -1;
-                float v[12];
-#pragma unroll
-                for (int i = 0; i < 12; ++i) v[i] = 0.f;
-                if (in) {
-                    const int2 pq = __ldg(a.ants + P.row_off + row);
-                    p = pq.x;
-                    q = pq.y;
-                    const size_t s = (size_t)P.vis_off + (size_t)row * nc + c;
-                    bool ok = p != q;
-                    if (ok && a.flag) ok = __ldg(a.flag + s) == 0;
-                    if (ok) {
-                        const J2 D = j_from(__ldg(a.vis + 2 * s), __ldg(a.vis + 2 * s + 1));
-                        J2 M;
-                        if constexpr (M16) {
-                            const uint4 h = __ldg(a.model16 + s);
-                            const float sc = __ldg(a.row_scale + P.row_off + row);
-                            M.a = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.x)), sc);
-                            M.b = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.y)), sc);
-                            M.c = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.z)), sc);
-                            M.d = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.w)), sc);
-                        } else {
-                            M = j_from(__ldg(a.model + 2 * s), __ldg(a.model + 2 * s + 1));
-                        }
-                        const float4 w = __ldg(a.weight + s);
-                        const float2 gp0 = g32[2 * p], gp1 = g32[2 * p + 1];
-                        const float2 gq0 = g32[2 * q], gq1 = g32[2 * q + 1];
-                        // X = M diag(conj g_q), V = diag(g_p) X, r = D - V
-                        const float2 X00 = cmulc(M.a, gq0), X01 = cmulc(M.b, gq1);
-                        const float2 X10 = cmulc(M.c, gq0), X11 = cmulc(M.d, gq1);
-                        const float2 r00 = csub(D.a, cmul(gp0, X00)), r01 = csub(D.b, cmul(gp0, X01));
-                        const float2 r10 = csub(D.c, cmul(gp1, X10)), r11 = csub(D.d, cmul(gp1, X11));
-                        // p side: parameter k touches row k: E[(k,j), k] = X[k][j]
-                        v[0] = fmaf(w.x, cnorm2(X00), w.y * cnorm2(X01));
-                        v[1] = fmaf(w.z, cnorm2(X10), w.w * cnorm2(X11));
-                        float2 j0 = cfma_conj(X01, cscale(r01, w.y), cfma_conj(X00, cscale(r00, w.x), make_float2(0.f, 0.f)));
-                        float2 j1 = cfma_conj(X11, cscale(r11, w.w), cfma_conj(X10, cscale(r10, w.z), make_float2(0.f, 0.f)));
-                        v[2] = j0.x; v[3] = j0.y; v[4] = j1.x; v[5] = j1.y;
-                        // q side through the conjugate baseline: Y = M^H diag(conj g_p), r' = r^H, w' = P w
-                        const float2 Y00 = cmulc(cconj(M.a), gp0), Y01 = cmulc(cconj(M.c), gp1);
-                        const float2 Y10 = cmulc(cconj(M.b), gp0), Y11 = cmulc(cconj(M.d), gp1);
-                        v[6] = fmaf(w.x, cnorm2(Y00), w.z * cnorm2(Y01));
-                        v[7] = fmaf(w.y, cnorm2(Y10), w.w * cnorm2(Y11));
-                        float2 k0 = cfma_conj(Y01, cscale(cconj(r10), w.z), cfma_conj(Y00, cscale(cconj(r00), w.x), make_float2(0.f, 0.f)));
-                        float2 k1 = cfma_conj(Y11, cscale(cconj(r11), w.w), cfma_conj(Y10, cscale(cconj(r01), w.y), make_float2(0.f, 0.f)));
-                        v[8] = k0.x; v[9] = k0.y; v[10] = k1.x; v[11] = k1.y;
-                    }
-                }
-                // reduce over runs of equal antenna within the warp, heads add into shared memory
-                const int kp = in ? p : -1, kq = in ? q : -1;
-#pragma unroll
-                for (int side = 0; side < 2; ++side) {
-                    const int key = side == 0 ? kp : kq;
-                    const int prev = __shfl_up_sync(0xffffffffu, key, 1);
-                    const bool head = lane == 0 || key != prev;
-                    const unsigned heads = __ballot_sync(0xffffffffu, head);
-                    const unsigned after = heads & ~((2u << lane) - 1u);
-                    const unsigned run_end = after ? (unsigned)(__ffs(after) - 1) : 32u;
-#pragma unroll
-                    for (int i = 0; i < 6; ++i) {
-                        const float sum = run_sum(v[side * 6 + i], lane, run_end);
-                        if (head && key >= 0) atomicAdd(acc + key * 6 + i, sum);
-                    }
-                }
+            // issue cursor: the step whose copies are issued next, and the lane's (row, chan) in it
+            long is = st_begin;
+            int irow, ic;
+            {
+                const long s0 = st_begin * 32 + lane;
+                irow = (int)(s0 / nc);
+                ic = (int)(s0 - (long)irow * nc);
             }
+            // metadata of the next two steps to issue (antennas, usable flag), loaded ahead
+            auto load_meta = [&](long step, int row, int2 &pq, int &use, float &sc) {
+                const long s = step * 32 + lane;
+                const bool in = step < st_end && s < n_samp;
+                pq = in ? __ldg(ants + row) : make_int2(-1, -1);
+                use = in && pq.x != pq.y && !(flg && __ldg(flg + s)) ? 1 : 0;
+                sc = M16 && in ? __ldg(rsc + row) : 0.f;
+            };
+            auto advance = [&](int &row, int &c) {
+                c += r32;
+                row += q32;
+                if (c >= nc) { c -= nc; ++row; }
+            };
+            int2 m1pq, m2pq;
+            int m1use, m2use;
+            float m1sc, m2sc;
+            int r2 = irow, c2 = ic;
+            load_meta(is, irow, m1pq, m1use, m1sc);
+            advance(r2, c2);
+            load_meta(is + 1, r2, m2pq, m2use, m2sc);
+            int stage_i = 0;
+            auto issue = [&]() {
+                const long s = is * 32 + lane;
+                const uint32_t nb = m1use ? 16u : 0u;
+                const long so = m1use ? s : 0;
+                float4 *slot = ring + (size_t)stage_i * V4 * 32 + lane;
+                cp_async16(slot, vis + 2 * so, nb);
+                cp_async16(slot + 32, vis + 2 * so + 1, nb);
+                if constexpr (M16) {
+                    cp_async16(slot + 64, mod16 + so, nb);
+                    cp_async16(slot + 96, wgt + so, nb);
+                } else {
+                    cp_async16(slot + 64, mod + 2 * so, nb);
+                    cp_async16(slot + 96, mod + 2 * so + 1, nb);
+                    cp_async16(slot + 128, wgt + so, nb);
+                }
+                cp_async_commit();
+                int2 key;
+                key.x = m1pq.x >= 0 ? (m1pq.x | (m1pq.y << 16)) : -1;
+                key.y = __float_as_int(m1sc);
+                meta[stage_i * 32 + lane] = key;
+                if (++stage_i == DEPTH) stage_i = 0;
+                // shift the metadata pipeline by one step
+                ++is;
+                m1pq = m2pq;
+                m1use = m2use;
+                m1sc = m2sc;
+                advance(r2, c2);
+                load_meta(is + 1, r2, m2pq, m2use, m2sc);
+            };
+#pragma unroll
+            for (int d = 0; d < DEPTH - 1; ++d) issue();
+
+            float sp[6], sq[6];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) sp[i] = sq[i] = 0.f;
+            int kp = -1, kq = -1;
+            int stage_c = 0;
+            for (long t = st_begin; t < st_end; ++t) {
+                cp_async_wait<DEPTH - 2>();
+                const float4 *slot = ring + (size_t)stage_c * V4 * 32 + lane;
+                const int2 key = meta[stage_c * 32 + lane];
+                const int np = key.x >= 0 ? (key.x & 0xffff) : -1;
+                const int nq = key.x >= 0 ? (key.x >> 16) : -1;
+                if (__any_sync(0xffffffffu, np != kp)) { flush_runs(sp, kp, lane, acc); kp = np; }
+                if (__any_sync(0xffffffffu, nq != kq)) { flush_runs(sq, kq, lane, acc); kq = nq; }
+                if (key.x >= 0) {
+                    const J2 D = j_from(slot[0], slot[32]);
+                    J2 M;
+                    if constexpr (M16) {
+                        const float4 hw = slot[64];
+                        const uint4 h = *reinterpret_cast<const uint4 *>(&hw);
+                        const float sc = __int_as_float(key.y);
+                        M.a = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.x)), sc);
+                        M.b = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.y)), sc);
+                        M.c = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.z)), sc);
+                        M.d = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.w)), sc);
+                    } else {
+                        M = j_from(slot[64], slot[96]);
+                    }
+                    const float4 w = slot[M16 ? 96 : 128];
+                    const float4 Gp = g32[np], Gq = g32[nq];
+                    const float2 gp0 = make_float2(Gp.x, Gp.y), gp1 = make_float2(Gp.z, Gp.w);
+                    const float2 gq0 = make_float2(Gq.x, Gq.y), gq1 = make_float2(Gq.z, Gq.w);
+                    // X = M diag(conj g_q), V = diag(g_p) X, r = D - V
+                    const float2 X00 = cmulc(M.a, gq0), X01 = cmulc(M.b, gq1);
+                    const float2 X10 = cmulc(M.c, gq0), X11 = cmulc(M.d, gq1);
+                    const float2 r00 = csub(D.a, cmul(gp0, X00)), r01 = csub(D.b, cmul(gp0, X01));
+                    const float2 r10 = csub(D.c, cmul(gp1, X10)), r11 = csub(D.d, cmul(gp1, X11));
+                    const float2 wr00 = cscale(r00, w.x), wr01 = cscale(r01, w.y);
+                    const float2 wr10 = cscale(r10, w.z), wr11 = cscale(r11, w.w);
+                    // p side: parameter k touches row k of V: d V[k][j] / d g_p[k] = X[k][j]
+                    sp[0] += fmaf(w.x, cnorm2(X00), w.y * cnorm2(X01));
+                    sp[1] += fmaf(w.z, cnorm2(X10), w.w * cnorm2(X11));
+                    float2 j0 = cfma_conj(X01, wr01, cfma_conj(X00, wr00, make_float2(sp[2], sp[3])));
+                    float2 j1 = cfma_conj(X11, wr11, cfma_conj(X10, wr10, make_float2(sp[4], sp[5])));
+                    sp[2] = j0.x; sp[3] = j0.y; sp[4] = j1.x; sp[5] = j1.y;
+                    // q side through the conjugate baseline: Y = M^H diag(conj g_p), r' = r^H, w' = P w
+                    const float2 Y00 = cmulc(cconj(M.a), gp0), Y01 = cmulc(cconj(M.c), gp1);
+                    const float2 Y10 = cmulc(cconj(M.b), gp0), Y11 = cmulc(cconj(M.d), gp1);
+                    sq[0] += fmaf(w.x, cnorm2(Y00), w.z * cnorm2(Y01));
+                    sq[1] += fmaf(w.y, cnorm2(Y10), w.w * cnorm2(Y11));
+                    float2 k0 = cfma_conj(Y01, cconj(wr10), cfma_conj(Y00, cconj(wr00), make_float2(sq[2], sq[3])));
+                    float2 k1 = cfma_conj(Y11, cconj(wr11), cfma_conj(Y10, cconj(wr01), make_float2(sq[4], sq[5])));
+                    sq[2] = k0.x; sq[3] = k0.y; sq[4] = k1.x; sq[5] = k1.y;
+                }
+                if (++stage_c == DEPTH) stage_c = 0;
+                issue();
+            }
+            cp_async_wait<0>();
+            flush_runs(sp, kp, lane, acc);
+            flush_runs(sq, kq, lane, acc);
             __syncthreads();
             // FP64 per-antenna solve and update (diagonal blocks: off-diagonal terms vanish)
             const double alpha = a.damping_mode == QC_DAMP_ALTERNATE ? ((k % 2 == 0) ? 0.5 : 1.0)
@@ -196,8 +313,7 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchArgs a)
                 G0.x += d0.x; G0.y += d0.y; G1.x += d1.x; G1.y += d1.y;
                 g64[2 * ant] = G0;
                 g64[2 * ant + 1] = G1;
-                g32[2 * ant] = make_float2((float)G0.x, (float)G0.y);
-                g32[2 * ant + 1] = make_float2((float)G1.x, (float)G1.y);
+                g32[ant] = make_float4((float)G0.x, (float)G0.y, (float)G1.x, (float)G1.y);
                 if (a.gain_flags) a.gain_flags[P.gain_off + ant] = singular ? 1 : 0;
                 num += d0.x * d0.x + d0.y * d0.y + d1.x * d1.x + d1.y * d1.y;
                 den += G0.x * G0.x + G0.y * G0.y + G1.x * G1.x + G1.y * G1.y;
@@ -218,10 +334,14 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchArgs a)
             if (s_done) break;
         }
         const int done_iters = k > a.max_iter ? a.max_iter : k;
-        for (int i = tid; i < na * 2; i += blockDim.x) a.gains[(size_t)P.gain_off * 2 + i] = g32[i];
+        for (int i = tid; i < na; i += blockDim.x) {
+            const float4 g = g32[i];
+            a.gains[(size_t)(P.gain_off + i) * 2] = make_float2(g.x, g.y);
+            a.gains[(size_t)(P.gain_off + i) * 2 + 1] = make_float2(g.z, g.w);
+        }
         if (tid == 0) {
             if (a.iters) a.iters[pi] = done_iters;
-            const unsigned long long ns = (unsigned long long)P.n_rows * nc;
+            const unsigned long long ns = (unsigned long long)n_samp;
             atomicAdd(a.vis_iters, ns * done_iters);
             const unsigned long long b = (a.flag ? ns : 0ull) + (unsigned long long)P.n_unflag * (M16 ? 64ull : 80ull);
             atomicAdd(a.bytes, b * done_iters);
@@ -229,6 +349,7 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchArgs a)
         __syncthreads();
     }
 }
+
 
 // chi^2 of every problem at the given gains (one CTA per problem, FP64 block sums)
 template <bool M16>
@@ -540,10 +661,10 @@ struct qc_batch {
     void *gstage = nullptr;       // device staging for host gains/flags/iters
     std::vector<BProb> hprobs;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    struct Shape { int threads, per_sm, schedule; double ms; };
+    struct Shape { int threads, per_sm, schedule, depth; double ms; };
     std::map<std::string, Shape> tuned;
     std::string shape_key;
-    struct GraphKey { int threads, per_sm, schedule, max_iter, damping_mode; double damping, tol; bool m16;
+    struct GraphKey { int threads, per_sm, schedule, depth, max_iter, damping_mode; double damping, tol; bool m16;
                       void *gains; void *flags; void *iters; cudaStream_t st; };
     cudaGraphExec_t exec = nullptr;
     GraphKey gkey;
@@ -787,45 +908,62 @@ static BatchArgs batch_args(qc_batch *b)
     return a;
 }
 
-static size_t batch_smem(const qc_batch *b)
+static size_t batch_smem(const qc_batch *b, int threads, int depth)
 {
-    return (size_t)b->max_ant * (6 * sizeof(float) + 2 * sizeof(float2) + 2 * sizeof(double2));
+    const size_t ring = b->m16 ? (depth == 3 ? batch_ring_bytes_per_warp<true, 3>()
+                                  : depth == 4 ? batch_ring_bytes_per_warp<true, 4>() : batch_ring_bytes_per_warp<true, 6>())
+                               : (depth == 3 ? batch_ring_bytes_per_warp<false, 3>()
+                                  : depth == 4 ? batch_ring_bytes_per_warp<false, 4>() : batch_ring_bytes_per_warp<false, 6>());
+    return (size_t)(threads / 32) * ring +
+           (size_t)b->max_ant * (2 * sizeof(double2) + sizeof(float4) + 6 * sizeof(float));
 }
 
-static const void *batch_fn(bool m16) { return m16 ? (const void *)batch_kernel<true> : (const void *)batch_kernel<false>; }
+static const void *batch_fn(bool m16, int depth)
+{
+    if (m16) return depth == 3 ? (const void *)batch_kernel<true, 3>
+                  : depth == 4 ? (const void *)batch_kernel<true, 4> : (const void *)batch_kernel<true, 6>;
+    return depth == 3 ? (const void *)batch_kernel<false, 3>
+         : depth == 4 ? (const void *)batch_kernel<false, 4> : (const void *)batch_kernel<false, 6>;
+}
 
 // Enqueue one solve (work-counter reset + persistent kernel) on stream st.
-static int batch_enqueue(qc_batch *b, const BatchArgs &a, int threads, int grid, cudaStream_t st)
+static int batch_enqueue(qc_batch *b, const BatchArgs &a, int threads, int depth, int grid, cudaStream_t st)
 {
     BCK(cudaMemsetAsync(b->queue, 0, sizeof(int), st));
-    const size_t smem = batch_smem(b);
-    if (b->m16) batch_kernel<true><<<grid, threads, smem, st>>>(a);
-    else batch_kernel<false><<<grid, threads, smem, st>>>(a);
-    BCK(cudaGetLastError());
+    const size_t smem = batch_smem(b, threads, depth);
+    void *args[] = { (void *)&a };
+    BCK(cudaLaunchKernel(batch_fn(b->m16, depth), dim3(grid), dim3(threads), args, smem, st));
     return QC_OK;
 }
 
-static int launch_shape(qc_batch *b, const qc_batch_opts *o, int &threads, int &per_sm, int &schedule)
+static int launch_shape(qc_batch *b, const qc_batch_opts *o, int &threads, int &per_sm, int &schedule, int &depth)
 {
     threads = o->threads;
     per_sm = o->ctas_per_sm;
     schedule = o->schedule;
+    depth = o->depth;
     auto it = b->tuned.find(b->shape_key);
     if (it != b->tuned.end()) {
         if (threads == 0) threads = it->second.threads;
         if (per_sm == 0) per_sm = it->second.per_sm;
         if (schedule == QC_SCHED_AUTO) schedule = it->second.schedule;
+        if (depth == 0) depth = it->second.depth;
     }
     if (threads == 0) threads = 256;
+    if (depth == 0) depth = 4;
     if (schedule == QC_SCHED_AUTO) schedule = QC_SCHED_LPT;
     if (threads < 64 || threads > 512 || threads % 32) return b->fail(QC_EINVAL, "threads must be 64..512, multiple of 32");
-    const size_t smem = batch_smem(b);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(batch_fn(b->m16), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return b->cuda_fail(e, "cudaFuncSetAttribute");
-    }
+    if (depth != 3 && depth != 4 && depth != 6) return b->fail(QC_EINVAL, "depth must be 3, 4 or 6");
+    const size_t smem = batch_smem(b, threads, depth);
+    int max_smem = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->dev);
+    if (e != cudaSuccess) return b->cuda_fail(e, "cudaDeviceGetAttribute");
+    if (smem + 2 * 32 * sizeof(double) + 64 > (size_t)max_smem)
+        return b->fail(QC_EUNSUPPORTED, "batch kernel shared memory exceeds the per-CTA limit for this shape");
+    e = cudaFuncSetAttribute(batch_fn(b->m16, depth), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return b->cuda_fail(e, "cudaFuncSetAttribute");
     int occ = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_fn(b->m16), threads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_fn(b->m16, depth), threads, smem);
     if (e != cudaSuccess) return b->cuda_fail(e, "occupancy");
     if (occ < 1) return b->fail(QC_EUNSUPPORTED, "batch kernel does not fit on an SM with this shape");
     if (per_sm <= 0 || per_sm > occ) per_sm = std::min(occ, per_sm <= 0 ? occ : per_sm);
@@ -840,8 +978,8 @@ static int batch_solve_impl(qc_batch *b, void *gains, int8_t *gain_flags, int32_
     if (o->max_iter < 1) return b->fail(QC_EINVAL, "max_iter must be >= 1");
     if (!(o->tol >= 0)) return b->fail(QC_EINVAL, "tol must be >= 0");
     if (o->damping_mode != QC_DAMP_CONST && o->damping_mode != QC_DAMP_ALTERNATE) return b->fail(QC_EINVAL, "damping_mode");
-    int threads, per_sm, schedule, rc;
-    if ((rc = launch_shape(b, o, threads, per_sm, schedule))) return rc;
+    int threads, per_sm, schedule, depth, rc;
+    if ((rc = launch_shape(b, o, threads, per_sm, schedule, depth))) return rc;
     cudaStream_t st = o->stream ? (cudaStream_t)o->stream : b->own_stream;
     const size_t gbytes = (size_t)b->total_ant * 2 * sizeof(float2);
     unsigned char *stage = (unsigned char *)b->gstage;
@@ -867,7 +1005,7 @@ static int batch_solve_impl(qc_batch *b, void *gains, int8_t *gain_flags, int32_
     if (o->use_graph && !tuning) {
         qc_batch::GraphKey k;
         memset(&k, 0, sizeof k);
-        k.threads = threads; k.per_sm = per_sm; k.schedule = schedule; k.max_iter = o->max_iter;
+        k.threads = threads; k.per_sm = per_sm; k.schedule = schedule; k.depth = depth; k.max_iter = o->max_iter;
         k.damping_mode = o->damping_mode; k.damping = o->damping; k.tol = o->tol; k.m16 = b->m16;
         k.gains = dg; k.flags = dflags; k.iters = diters; k.st = st;
         const bool same = b->exec && memcmp(&k, &b->gkey, sizeof k) == 0;
@@ -875,7 +1013,7 @@ static int batch_solve_impl(qc_batch *b, void *gains, int8_t *gain_flags, int32_
             if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
             cudaGraph_t g = nullptr;
             BCK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-            rc = batch_enqueue(b, a, threads, grid, st);
+            rc = batch_enqueue(b, a, threads, depth, grid, st);
             cudaError_t e = cudaStreamEndCapture(st, &g);
             if (rc || e != cudaSuccess) {
                 if (g) cudaGraphDestroy(g);
@@ -889,7 +1027,7 @@ static int batch_solve_impl(qc_batch *b, void *gains, int8_t *gain_flags, int32_
         }
         BCK(cudaGraphLaunch(b->exec, st));
     } else {
-        if ((rc = batch_enqueue(b, a, threads, grid, st))) return rc;
+        if ((rc = batch_enqueue(b, a, threads, depth, grid, st))) return rc;
     }
     if (mem == QC_MEM_HOST) {
         BCK(cudaMemcpyAsync(gains, dg, gbytes, cudaMemcpyDeviceToHost, st));
@@ -912,6 +1050,7 @@ static int batch_solve_impl(qc_batch *b, void *gains, int8_t *gain_flags, int32_
         S.ctas_per_sm = per_sm;
         S.schedule = schedule;
         S.grid = grid;
+        S.depth = depth;
         double tot_vis = 0;
         for (const BProb &P : b->hprobs) tot_vis += (double)P.n_rows * P.n_chan;
         S.mean_iters = tot_vis > 0 ? (double)hc[0] / tot_vis : 0;
@@ -948,16 +1087,18 @@ extern "C" int qc_batch_autotune(qc_batch *b, const qc_batch_opts *base, qc_batc
     cudaError_t e = cudaMalloc(&g, (size_t)b->total_ant * 2 * sizeof(float2));
     if (e != cudaSuccess) return b->cuda_fail(e, "cudaMalloc");
     std::vector<float2> unit((size_t)b->total_ant * 2, make_float2(1.f, 0.f));
-    qc_batch::Shape win{ 0, 0, 0, 1e30 };
+    qc_batch::Shape win{ 0, 0, 0, 0, 1e30 };
     int tried = 0, rc = QC_OK;
     qc_batch_stats ws;
     memset(&ws, 0, sizeof ws);
     b->tuned.erase(b->shape_key);
     for (int threads : { 128, 256, 512 })
+        for (int depth : { 3, 4, 6 })
         for (int per_sm : { 1, 2, 4 })
             for (int sched : { QC_SCHED_LPT, QC_SCHED_STATIC }) {
                 qc_batch_opts o = *base;
                 o.threads = threads;
+                o.depth = depth;
                 o.ctas_per_sm = per_sm;
                 o.schedule = sched;
                 o.use_graph = 0;
@@ -969,7 +1110,7 @@ extern "C" int qc_batch_autotune(qc_batch *b, const qc_batch_opts *base, qc_batc
                 if (r) { rc = r; break; }
                 ++tried;
                 if (s.ctas_per_sm != per_sm) continue;                     // clamped: duplicate of a smaller one
-                if (s.ms < win.ms) { win = { threads, per_sm, sched, s.ms }; ws = s; }
+                if (s.ms < win.ms) { win = { threads, per_sm, sched, depth, s.ms }; ws = s; }
             }
     cudaFree(g);
     if (rc) return rc;

@@ -286,13 +286,13 @@ class _BatchProblem(C.Structure):
 class _BatchOpts(C.Structure):
     _fields_ = [("max_iter", C.c_int32), ("tol", C.c_double), ("damping_mode", C.c_int32), ("damping", C.c_double),
                 ("stream", C.c_void_p), ("threads", C.c_int32), ("ctas_per_sm", C.c_int32),
-                ("schedule", C.c_int32), ("use_graph", C.c_int32)]
+                ("schedule", C.c_int32), ("use_graph", C.c_int32), ("depth", C.c_int32)]
 
 
 class BatchStats(C.Structure):
     _fields_ = [("ms", C.c_double), ("vis_iters", C.c_int64), ("bytes", C.c_int64), ("n_iter_max", C.c_int32),
                 ("mean_iters", C.c_double), ("threads", C.c_int32), ("ctas_per_sm", C.c_int32),
-                ("schedule", C.c_int32), ("grid", C.c_int32)]
+                ("schedule", C.c_int32), ("grid", C.c_int32), ("depth", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -362,17 +362,18 @@ class BatchSolver:
         g[:] = 1
         return g
 
-    def _opts(self, max_iter, tol, damping_mode, damping, stream, threads, ctas_per_sm, schedule, use_graph):
+    def _opts(self, max_iter, tol, damping_mode, damping, stream, threads, ctas_per_sm, schedule, use_graph,
+              depth=0):
         st = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
         return _BatchOpts(max_iter, tol, damping_mode, damping, st or None, threads, ctas_per_sm, schedule,
-                          int(use_graph))
+                          int(use_graph), depth)
 
     def _err(self, rc):
         raise QCError(rc, self._lib.qc_batch_last_error(self._h).decode())
 
     def solve(self, gains=None, max_iter: int = 20, tol: float = 1e-6, damping_mode: int = QC_DAMP_ALTERNATE,
               damping: float = 1.0, stream=None, threads: int = 0, ctas_per_sm: int = 0,
-              schedule: int = QC_SCHED_AUTO, use_graph: bool = True, want_flags: bool = True):
+              schedule: int = QC_SCHED_AUTO, use_graph: bool = True, want_flags: bool = True, depth: int = 0):
         """Solve in place; returns (gains, gain_flags, iters, BatchStats)."""
         if gains is None:
             gains = self.unit_gains()
@@ -385,7 +386,7 @@ class BatchSolver:
             gains = np.ascontiguousarray(gains, dtype=np.complex64)
             flags = np.zeros(self.total_ant, dtype=np.int8) if want_flags else None
             iters = np.zeros(self.n_prob, dtype=np.int32)
-        o = self._opts(max_iter, tol, damping_mode, damping, stream, threads, ctas_per_sm, schedule, use_graph)
+        o = self._opts(max_iter, tol, damping_mode, damping, stream, threads, ctas_per_sm, schedule, use_graph, depth)
         s = BatchStats()
         rc = self._lib.qc_batch_solve(self._h, _addr(gains), _addr(flags), _addr(iters),
                                       QC_MEM_DEVICE if dev else QC_MEM_HOST, C.byref(o), C.byref(s))

@@ -486,8 +486,88 @@ class Batch:
         return int(self.vis_offset[-1])
 
 
+def fill_interval_problems_device(sus, noise: float, noise_seed: int, data, model, weight, flag,
+                                  chunk_samples: int = 1 << 23):
+    """Generate many single-interval diagonal-gain problems (``interval_problem_setup`` /
+    ``pair_problem_setups``) straight into flat device arrays [sum rows x chans][4], a few
+    million samples per pass over the concatenation instead of one pass per problem.
+
+    Same arithmetic as :func:`make_observation_device` (FP64 phases range-reduced, FP32
+    exponentials, complex64 output); flags are the setups' own; noise comes from one device
+    generator seeded with ``noise_seed``."""
+    import torch
+    dev = data.device
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(int(noise_seed))
+    two_pi = 2.0 * np.pi
+    weight.fill_(1.0)
+    i, n_p, v0 = 0, len(sus), 0
+    while i < n_p:
+        # group problems up to ~chunk_samples samples (at least one problem)
+        j, n_s = i, 0
+        while j < n_p and (j == i or n_s + sus[j].ant1.size * sus[j].freqs.size <= chunk_samples):
+            n_s += sus[j].ant1.size * sus[j].freqs.size
+            j += 1
+        grp = sus[i:j]
+        n_src = grp[0].sky.flux.size
+        rows = np.array([su.ant1.size for su in grp])
+        ncs = np.array([su.freqs.size for su in grp])
+        max_ant = max(su.n_ant for su in grp)
+        uvw = np.concatenate([su.uvw for su in grp])                                   # [R, 3]
+        prob_row = np.repeat(np.arange(j - i), rows)
+        a1 = np.concatenate([su.ant1 for su in grp]).astype(np.int64)
+        a2 = np.concatenate([su.ant2 for su in grp]).astype(np.int64)
+        nc_row = ncs[prob_row]
+        lmn = np.stack([np.stack([su.sky.l, su.sky.m, su.sky.n - 1.0]) for su in grp])   # [P, 3, src]
+        flux = np.stack([su.sky.flux for su in grp])                                   # [P, src]
+        f0 = np.array([su.freqs[0] for su in grp])
+        df = np.array([su.freqs[1] - su.freqs[0] if su.freqs.size > 1 else 0.0 for su in grp])
+        gains = np.ones((j - i, max_ant, 2), np.complex128)
+        for k, su in enumerate(grp):
+            t = su.terms[0].truth_jones()[0, 0]
+            gains[k, :su.n_ant, 0] = t[:, 0]
+            gains[k, :su.n_ant, 1] = t[:, 3]
+        fl = np.concatenate([(np.repeat(su.flag_rows[:, None], su.freqs.size, axis=1) |
+                              (su.flag_samples if su.flag_samples is not None else False)).reshape(-1)
+                             for su in grp]).astype(np.uint8)
+        # per-sample indices on the device
+        t_ = lambda x, dt=torch.int64: torch.from_numpy(np.ascontiguousarray(x)).to(dev, dt)
+        nc_row_d = t_(nc_row)
+        row_s = torch.repeat_interleave(torch.arange(rows.sum(), device=dev), nc_row_d)
+        row_start = torch.cumsum(nc_row_d, 0) - nc_row_d
+        chan_s = torch.arange(n_s, device=dev) - row_start[row_s]
+        prob_s = t_(prob_row)[row_s]
+        ph_row = torch.einsum("rk,rks->rs", t_(uvw, torch.float64), t_(lmn, torch.float64)[t_(prob_row)])  # [R, src]
+        freq_s = t_(f0, torch.float64)[prob_s] + t_(df, torch.float64)[prob_s] * chan_s.to(torch.float64)
+        k_nu = -two_pi * freq_s / C_LIGHT
+        ang = ph_row[row_s] * k_nu[:, None]                                            # [S, src]
+        ang = (ang - two_pi * torch.round(ang / two_pi)).to(torch.float32)
+        scal = (torch.polar(torch.ones_like(ang), ang) *
+                t_(flux, torch.float32)[prob_s].to(torch.complex64)).sum(dim=1)      # [S]
+        del ang
+        g = t_(gains, torch.complex128).to(torch.complex64)
+        gp = g[prob_s, t_(a1)[row_s]]                                                  # [S, 2]
+        gq = g[prob_s, t_(a2)[row_s]]
+        out = torch.zeros((n_s, 4), dtype=torch.complex64, device=dev)
+        out[:, 0] = gp[:, 0] * scal * gq[:, 0].conj()
+        out[:, 3] = gp[:, 1] * scal * gq[:, 1].conj()
+        if noise > 0:
+            nz = torch.randn((n_s, 4, 2), dtype=torch.float32, device=dev, generator=gen)
+            out += noise * torch.view_as_complex(nz)
+        data[v0:v0 + n_s] = out
+        m = model[v0:v0 + n_s]
+        m.zero_()
+        m[:, 0] = scal
+        m[:, 3] = scal
+        flag[v0:v0 + n_s] = t_(fl, torch.uint8)
+        v0 += n_s
+        i = j
+    assert v0 == data.shape[0]
+
+
 def make_batch(shapes, noise: float = 0.01, device=None, noise_seed: int = 7) -> Batch:
-    """Concatenate problems; host complex128 arrays (device=None) or complex64 device tensors."""
+    """Concatenate problems; host complex128 arrays (device=None) or complex64 device tensors
+    (generated in a few large passes by :func:`fill_interval_problems_device`)."""
     row_off, vis_off = [0], [0]
     a1, a2, truths, setups = [], [], [], []
     parts = []
@@ -498,8 +578,6 @@ def make_batch(shapes, noise: float = 0.01, device=None, noise_seed: int = 7) ->
         if device is None:
             obs = make_observation(na, nt, su.freqs, su.terms, n_src=5, seed=seed, noise=noise, su=su)
             parts.append((obs.data, obs.model, obs.weight, obs.flag))
-        else:
-            parts.append(make_observation_device(su, noise, noise_seed + i, device))
         a1.append(su.ant1)
         a2.append(su.ant2)
         row_off.append(row_off[-1] + su.ant1.size)
@@ -511,10 +589,12 @@ def make_batch(shapes, noise: float = 0.01, device=None, noise_seed: int = 7) ->
         flag = np.concatenate([p_[3].reshape(-1) for p_ in parts])
     else:
         import torch
-        data = torch.cat([p_["data"].reshape(-1, 4) for p_ in parts])
-        model = torch.cat([p_["model"].reshape(-1, 4) for p_ in parts])
-        weight = torch.cat([p_["weight"].reshape(-1, 4) for p_ in parts])
-        flag = torch.cat([p_["flag"].reshape(-1) for p_ in parts])
+        n_vis = vis_off[-1]
+        data = torch.empty((n_vis, 4), dtype=torch.complex64, device=device)
+        model = torch.empty((n_vis, 4), dtype=torch.complex64, device=device)
+        weight = torch.empty((n_vis, 4), dtype=torch.float32, device=device)
+        flag = torch.empty(n_vis, dtype=torch.uint8, device=device)
+        fill_interval_problems_device(setups, noise, noise_seed, data, model, weight, flag)
     return Batch(list(shapes), data, model, weight, flag, np.concatenate(a1).astype(np.int32),
                  np.concatenate(a2).astype(np.int32), np.array(row_off, np.int64), np.array(vis_off, np.int64),
                  np.array([s_[3] for s_ in shapes], np.int32), np.array([s_[1] for s_ in shapes], np.int32),
@@ -602,20 +682,16 @@ def make_pair_batches(shapes, noise: float = 0.01, device=None, noise_seed: int 
             model = torch.empty((n_vis, 4), dtype=torch.complex64, device=device)
             weight = torch.empty((n_vis, 4), dtype=torch.float32, device=device)
             flag = torch.empty(n_vis, dtype=torch.uint8, device=device)
-        for i, su in enumerate(sus):
-            v0, v1 = vis_off[i], vis_off[i + 1]
-            if device is None:
+        if device is None:
+            for i, su in enumerate(sus):
+                v0, v1 = vis_off[i], vis_off[i + 1]
                 o = make_observation(su.n_ant, su.n_time, su.freqs, su.terms, n_src=5, seed=0, noise=noise, su=su)
                 data[v0:v1] = o.data.reshape(-1, 4)
                 model[v0:v1] = o.model.reshape(-1, 4)
                 weight[v0:v1] = o.weight.reshape(-1, 4)
                 flag[v0:v1] = o.flag.reshape(-1)
-            else:
-                o = make_observation_device(su, noise, noise_seed + 2 * i + k, device)
-                data[v0:v1] = o["data"].reshape(-1, 4)
-                model[v0:v1] = o["model"].reshape(-1, 4)
-                weight[v0:v1] = o["weight"].reshape(-1, 4)
-                flag[v0:v1] = o["flag"].reshape(-1)
+        else:
+            fill_interval_problems_device(sus, noise, noise_seed + k, data, model, weight, flag)
         truths = [su.terms[0].truth[0, 0][:, [0, 3]].copy() for su in sus]
         batches[k] = (Batch(list(shapes), data, model, weight, flag,
                              np.concatenate([su.ant1 for su in sus]).astype(np.int32),

@@ -106,10 +106,13 @@ class MLP:
 
 
 def _he_init(seed: int) -> np.ndarray:
+    """He-normal hidden layers; the output layer starts at zero, so the untrained network
+    returns the previous-interval gains (the skip term) unchanged."""
     rng = np.random.default_rng(seed)
     parts = []
     for out_d, in_d in ((N_HID, N_IN), (N_HID, N_HID), (N_HID, N_HID), (N_OUT, N_HID)):
-        parts.append(rng.standard_normal((out_d, in_d)).reshape(-1) * math.sqrt(2.0 / in_d))
+        w = rng.standard_normal((out_d, in_d)).reshape(-1) * math.sqrt(2.0 / in_d)
+        parts.append(w if out_d != N_OUT else np.zeros_like(w))
         parts.append(np.zeros(out_d))
     return np.concatenate(parts)
 
@@ -229,6 +232,10 @@ def train(X, T, epochs=8, batch=4096, lr=2e-3, seed=0, log=print, net: Optional[
     g.manual_seed(seed)
     n = X.shape[0]
     hist = []
+    if val is not None:
+        # the skip term alone: previous-interval gains as the prediction
+        hist.append({"epoch": -1, "val_loss_prev_gains": float(((val[0][:, 6:10] - val[1]) ** 2).mean().item())})
+        log(hist[-1])
     for ep in range(epochs):
         perm = torch.randperm(n, device="cuda", generator=g)
         tot, cnt = 0.0, 0

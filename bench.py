@@ -629,50 +629,66 @@ def run_warmstart(args):
         torch.cuda.synchronize()
         return out, e0.elapsed_time(e1)
 
+    # time to tolerance: each arm is run with a ladder of stopping tolerances (relative gain
+    # change); its time to tolerance is its fastest run that leaves >= 99% of the intervals
+    # within 1e-4 (relative, referenced) of the converged solution
+    ladder = (1e-4, 3e-5, 1e-5, 3e-6, 1e-6)
+    goal, quorum = 1e-4, 0.99
+
+    def pick(res):
+        ok = [(v["ms"], k) for k, v in res.items() if v["frac_within_1e-4"] >= quorum]
+        return min(ok) if ok else (None, None)
+
     arms = {}
     for name, solver, start in (("cold", S, "unit"), ("prev", S, "prev"), ("mlp", S, "mlp"),
                                 ("mlp_fp16", S16, "mlp")):
         res = {}
-        for tol in (1e-4, 1e-6):
+        for tol in ladder:
             for _ in range(max(1, args.warmup)):       # warm the launch path
                 solver.solve(unit.clone(), max_iter=20, tol=tol, stream=stream)
 
             def run():
-                n_fb = 0
-                if start == "unit":
-                    g0 = unit.clone()
-                elif start == "prev":
-                    g0 = gp.clone()
-                else:
-                    g0, n_fb = ws.initial_gains(solver, net, prev_gains=gp, stream=stream)
-                g, _, it, st = solver.solve(g0, max_iter=20, tol=tol, stream=stream)
-                return g, it, st, n_fb
+                if start == "mlp":
+                    return ws.warm_solve(solver, net, gp, max_iter=40, tol=tol, stream=stream)
+                g0 = unit.clone() if start == "unit" else gp.clone()
+                g, _, it, st = solver.solve(g0, max_iter=40, tol=tol, stream=stream)
+                return g, it, st, 0
 
             (g, it, st, n_fb), ms = timed(run)
             err = _per_problem_err(g.cpu().numpy(), ref_h, offs)
             res[f"tol{tol:g}"] = {"ms": ms, "mean_iters": float(it.float().mean()), "max_iters": int(it.max()),
-                                  "median_err": float(np.median(err)), "frac_within_1e-4": float(np.mean(err <= 1e-4)),
+                                  "median_err": float(np.median(err)), "frac_within_1e-4": float(np.mean(err <= goal)),
                                   "fallbacks": int(n_fb)}
-        arms[name] = res
-    # the plain GPU solve: config-0-style single-problem launches, looped
+        ms_best, tol_best = pick(res)
+        arms[name] = {"time_to_tol_ms": ms_best, "stop_tol": tol_best, "runs": res}
+    # the plain GPU solve: config-0-style single-problem launches, looped, on a sample of the problems
     rng = np.random.default_rng(1)
     idx = np.sort(rng.choice(b.n_prob, size=min(args.looped, b.n_prob), replace=False))
-    dt_loop, vi_loop, g_loop = _looped_plain(b, idx, 1e-4, 20)
     sub_offs = np.concatenate([[0], np.cumsum(b.n_ant[idx])])
     ref_sub = np.concatenate([ref_h[offs[i]:offs[i + 1]] for i in idx])
-    err_loop = _per_problem_err(g_loop, ref_sub, sub_offs)
-    plain_all_ms = dt_loop * 1e3 * b.n_prob / idx.size
-    fast_ms = arms["mlp_fp16"]["tol0.0001"]["ms"]
+    loop_res = {}
+    for tol in ladder:
+        dt_loop, vi_loop, g_loop = _looped_plain(b, idx, tol, 40)
+        err_loop = _per_problem_err(g_loop, ref_sub, sub_offs)
+        loop_res[f"tol{tol:g}"] = {"ms": dt_loop * 1e3 * b.n_prob / idx.size, "sample_seconds": dt_loop,
+                                   "median_err": float(np.median(err_loop)),
+                                   "frac_within_1e-4": float(np.mean(err_loop <= goal))}
+    plain_ms, plain_tol = pick(loop_res)
+    fast_ms = arms["mlp_fp16"]["time_to_tol_ms"]
+    value = plain_ms / fast_ms if (plain_ms and fast_ms) else None
     out = {"metric": "time to 1e-4 gain tolerance (batched + warm start + FP16 model vs looped plain solves)",
-           "value": plain_all_ms / fast_ms, "unit": "x speed-up", "n_gpus": world, "steps": 1, "warmup": args.warmup,
+           "value": value, "unit": "x speed-up", "n_gpus": world, "steps": 1, "warmup": args.warmup,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64+f16", "data": "synthetic",
            "config": {"workload": f"warm start: {args.n_prob} intervals of 64 antennas, times U{{1..16}}, chans "
                                   "U{1..64}, flags U(0,0.5); previous interval of each solved first",
-                      "n_vis": b.n_vis, "gen_s": round(t_gen, 1), "checkpoint": os.path.basename(ckpt)},
+                      "n_vis": b.n_vis, "gen_s": round(t_gen, 1), "checkpoint": os.path.basename(ckpt),
+                      "time_to_tolerance": f">= {quorum:.0%} of intervals within {goal:g} of the converged gains "
+                                           "(relative, referenced); fastest stopping tolerance of " + str(ladder)},
            "arms": arms,
-           "looped_plain": {"problems": int(idx.size), "seconds": dt_loop, "extrapolated_ms": plain_all_ms,
-                            "median_err": float(np.median(err_loop)),
-                            "frac_within_1e-4": float(np.mean(err_loop <= 1e-4))}}
+           "speedup_vs_looped_plain": {k: (plain_ms / v["time_to_tol_ms"] if plain_ms and v["time_to_tol_ms"]
+                                           else None) for k, v in arms.items()},
+           "looped_plain": {"problems": int(idx.size), "time_to_tol_ms_extrapolated": plain_ms, "stop_tol": plain_tol,
+                            "runs": loop_res}}
     if rank == 0:
         print(json.dumps(out), flush=True)
     S.close()

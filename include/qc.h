@@ -140,7 +140,9 @@ typedef struct {
     int32_t ctas_per_sm;       /* resident CTAs per SM for its grid (0: auto)        */
     int32_t kernel;            /* accumulate kernel: 0 auto (1 for strip tiles, 2 for row
                                   tiles), 1 bulk-copy pipeline with per-warp rings (chains
-                                  of <= 2 terms), 2 per-lane cp.async prefetching kernel */
+                                  of <= 2 terms), 2 per-lane cp.async prefetching kernel,
+                                  3 streaming kernel (step-major row table, folded flags;
+                                  chains of <= 2 terms) */
     qc_allreduce_fn allreduce; /* required when a solved term has reduce = 1       */
     void *allreduce_user;
 } qc_opts;
@@ -284,6 +286,12 @@ typedef struct {
     int32_t schedule;            /* QC_SCHED_*                                           */
     int32_t use_graph;           /* 1: replay the persistent launch as a CUDA graph       */
     int32_t depth;               /* copy stages in flight per warp, 3/4/6 (0: tuned or 4)  */
+    /* Optional fallback start (device pointers, both or neither): the first pass also
+     * sums chi^2 at the given gains, and a problem whose chi^2 there exceeds
+     * fallback_chi2[problem] by more than a relative 1e-5 (the rounding of the two
+     * sums), or is not finite, restarts from fallback_gains.                       */
+    const void *fallback_gains;  /* [sum n_ant][2] complex64                           */
+    const double *fallback_chi2; /* [n_prob] chi^2 at fallback_gains                  */
 } qc_batch_opts;
 
 typedef struct {
@@ -294,6 +302,7 @@ typedef struct {
     double mean_iters;
     int32_t threads, ctas_per_sm, schedule, grid;   /* launch configuration used          */
     int32_t depth;
+    int32_t n_fallback;          /* problems restarted from the fallback gains           */
 } qc_batch_stats;
 
 /* Validate and stage a batch (host arrays copied, device arrays borrowed). */
@@ -370,14 +379,21 @@ const char *qc_batch_last_error(const qc_batch *b);
  * (device or host per `mem`), from one data pass at unit gains:
  *   0,1  |z_XX|, |z_YY| with z_k = JHr_k / JHJ_kk, the normalised first
  *        Gauss-Newton step at unit gains (Eq. jhr_entry_simplified)
- *   2,3  arg z_XX, arg z_YY
+ *   2,3  arg of the one-step gain 1 + z_k (the first Gauss-Newton iterate from
+ *        unit gains), referenced so that the sum of the interval's one-step
+ *        gains is real-positive: the phase of the gain in the targets' gauge,
+ *        since 1 + z_p ~ g_p conj(weighted mean of g_q)
  *   4,5  mean |d_kk| / |m_kk| over the antenna's unflagged samples
  *   6..9 previous-interval gains (Re, Im of g_XX, g_YY), referenced so that
  *        their sum over the interval's antennas is real-positive; unit gains
  *        when prev_gains is NULL.
- * Antennas without data get zeros for 0..5.
+ * Antennas without data get zeros for 0..5.  prev_chi2 (nullable, needs
+ * prev_gains; same memory as `features`) receives each problem's chi^2 at the
+ * previous-interval gains from the same pass: the bound of the fallback check
+ * (qc_batch_opts.fallback_chi2).
  */
-int qc_batch_features(qc_batch *b, const void *prev_gains, float *features, int32_t mem, void *stream);
+int qc_batch_features(qc_batch *b, const void *prev_gains, float *features, double *prev_chi2, int32_t mem,
+                      void *stream);
 
 /*
  * Initial gains from network outputs y [sum n_ant][4] (device): g = (y0 + i y1,

@@ -10,6 +10,12 @@ constexpr int PIPE_NW = 10;   // warps per CTA of the pipelined kernel
 constexpr int PIPE_H = 2;     // row segments of 32 channels per warp step
 
 constexpr int ACC_DEPTH = 4;  // cp.async ring depth (segments) of the prefetching kernel
+constexpr int STREAM_DEPTH = 4;   // ring depth (steps) of the streaming kernel
+
+template <bool M16> constexpr int stream_smem_per_warp()
+{
+    return STREAM_DEPTH * ((M16 ? 4 : 5) * 32 * 16 + 2 * 16);
+}
 
 template <int TS, int LK, int RK, bool SIMPLE, bool M16>
 cudaError_t launch_acc(int grid, int block, cudaStream_t st, const AccArgs &a)
@@ -26,6 +32,13 @@ cudaError_t launch_pipe(int grid, int smem_bytes, cudaStream_t st, const PipeArg
     return cudaGetLastError();
 }
 
+template <int TS, int LK, int RK, bool M16>
+cudaError_t launch_stream(int grid, int block, int smem_bytes, cudaStream_t st, const StreamArgs &a)
+{
+    acc_stream_kernel<TS, LK, RK, M16, STREAM_DEPTH><<<grid, block, smem_bytes, st>>>(a);
+    return cudaGetLastError();
+}
+
 template <int TS, int LK, int RK, bool SIMPLE, bool M16> AccLaunch make()
 {
     AccLaunch l;
@@ -37,6 +50,9 @@ template <int TS, int LK, int RK, bool SIMPLE, bool M16> AccLaunch make()
         l.pipe_launch = launch_pipe<TS, LK, RK, M16>;
         l.pipe_nw = PIPE_NW;
         l.pipe_h = PIPE_H;
+        l.stream_fn = (const void *)acc_stream_kernel<TS, LK, RK, M16, STREAM_DEPTH>;
+        l.stream_launch = launch_stream<TS, LK, RK, M16>;
+        l.stream_smem_per_warp = stream_smem_per_warp<M16>();
     }
     return l;
 }

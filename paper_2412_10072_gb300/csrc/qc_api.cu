@@ -261,6 +261,7 @@ extern "C" int qc_create(const qc_problem *p, qc_ctx **out)
                              [&](int x, int y) { return rows[x].z < rows[y].z; });
     }
     c->n_strips = n_bl;
+    c->n_strip_rows = (long)strip_rows.size();
     cudaError_t e;
     qc_ctx *cc = c.get();
     auto dalloc = [&](size_t bytes) -> void * { return cc->alloc(bytes, &e); };
@@ -329,6 +330,21 @@ extern "C" int qc_create(const qc_problem *p, qc_ctx **out)
         model32 = nullptr;
     }
     c->d_model = model32;
+    {
+        // weights with flags and autocorrelations folded in (w = 0), read by the streaming
+        // kernel instead of the flags; the owned host-mode copy is folded in place
+        float4 *wf = nullptr;
+        if (p->memory == QC_MEM_HOST) wf = const_cast<float4 *>(c->d_weight);
+        else DALLOC(wf, float4, std::max<size_t>(1, n_vis));
+        if (n_vis) {
+            fold_flags_kernel<<<grid_for((long)n_vis, 256, c->sm_count), 256, 0, c->own_stream>>>(
+                c->d_weight, c->d_flag, c->d_rows, p->n_row, p->n_chan, wf);
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->own_stream);
+            if (e != cudaSuccess) { g_create_error = std::string("weights: ") + cudaGetErrorString(e); return QC_ECUDA; }
+        }
+        c->d_wf = wf;
+    }
     DALLOC(c->d_row_live, uint8_t, std::max(1, p->n_row));
     DALLOC(c->d_err, int, 1);
     e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->own_stream);
@@ -700,8 +716,10 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
     PipeArgs pa;
     memset(&pa, 0, sizeof pa);
     int pipe_smem = 0;
-    // auto: the bulk-copy pipeline for baseline-strip tiles, the prefetching kernel for row tiles
-    bool pipelined = L.pipe_fn != nullptr && (o->kernel == 1 || (o->kernel == 0 && order == 1));
+    // kernel 3: the streaming kernel; auto: the bulk-copy pipeline for baseline-strip tiles,
+    // the prefetching kernel for row tiles
+    const bool streaming = L.stream_fn != nullptr && o->kernel == 3;
+    bool pipelined = !streaming && L.pipe_fn != nullptr && (o->kernel == 1 || (o->kernel == 0 && order == 1));
     const bool has_o = n_terms == 2;
     if (pipelined) {
         const int NW = L.pipe_nw;
@@ -773,8 +791,61 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
         pa.chunk_info = (const int4 *)B.chunk_info.ptr;
         aa.row_info = pa.row_info;
     }
+    StreamArgs sa;
+    memset(&sa, 0, sizeof sa);
+    int stream_smem = 0;
+    if (streaming) {
+        // step-major row table in the tile order, and the channel maps of both terms
+        const long n_rt = order == 0 ? (long)n_row : n_strip_rows;
+        int rc_;
+        if ((rc_ = ensure(B.rt, nbytes<int4>(std::max(1L, n_rt))))) return rc_;
+        if (m16 && (rc_ = ensure(B.rt_scale, nbytes<float>(std::max(1L, n_rt))))) return rc_;
+        if ((rc_ = ensure(B.fmap2, nbytes<int2>(n_chan)))) return rc_;
+        std::vector<int2> fm(n_chan);
+        for (int ch = 0; ch < n_chan; ++ch)
+            fm[ch] = make_int2(t.f_map[ch], has_o ? terms[1 - n].f_map[ch] : 0);
+        CK(cudaMemcpyAsync(B.fmap2.ptr, fm.data(), nbytes<int2>(n_chan), cudaMemcpyHostToDevice, st));
+        if (n_rt) {
+            row_table_kernel<<<(int)((n_rt + 255) / 256), 256, 0, st>>>(
+                (int)n_rt, order == 0 ? nullptr : d_strip_rows, (const int4 *)B.row_info.ptr, d_rows,
+                m16 ? d_bl_scale : nullptr, (int4 *)B.rt.ptr, m16 ? (float *)B.rt_scale.ptr : nullptr);
+            CK(cudaGetLastError());
+            ++launches;
+        }
+        sa.vis = d_vis;
+        sa.model = d_model;
+        sa.model16 = d_model16;
+        sa.wf = d_wf;
+        sa.n_chan = n_chan;
+        sa.n_ant = n_ant;
+        sa.rt = (const int4 *)B.rt.ptr;
+        sa.rt_scale = m16 ? (const float *)B.rt_scale.ptr : nullptr;
+        sa.unit_off = d_strip_off;
+        sa.order = order;
+        sa.n_chunks = (n_chan + 31) / 32;
+        sa.n_units = order == 0 ? n_row : n_strips * sa.n_chunks;
+        sa.tn = chain.t[n];
+        sa.to = has_o ? chain.t[1 - n] : chain.t[n];
+        sa.fmap2 = (const int2 *)B.fmap2.ptr;
+        sa.acc = (double *)B.acc.ptr;
+        sa.active = (const uint8_t *)B.active.ptr;
+        stream_smem = (block / 32) * L.stream_smem_per_warp;
+        if (stream_smem > smem_optin) return fail(QC_EUNSUPPORTED, "streaming kernel ring exceeds shared memory");
+        if (!configured(L.stream_fn)) {
+            CK(cudaFuncSetAttribute(L.stream_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin));
+            configured_fns.push_back(L.stream_fn);
+        }
+    }
     int grid;
-    if (pipelined) {
+    if (streaming) {
+        if (per_sm == 0) {
+            int occ = 0;
+            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, L.stream_fn, block, stream_smem);
+            per_sm = (e == cudaSuccess && occ > 0) ? occ : 1;
+        }
+        const long warps_needed = std::max(1L, (long)sa.n_units);
+        grid = (int)std::max(1L, std::min((long)sm_count * per_sm, (warps_needed * 32 + block - 1) / block));
+    } else if (pipelined) {
         const int NW = L.pipe_nw;
         const long groups = (units + NW - 1) / NW;
         grid = (int)std::max(1L, std::min((long)sm_count, groups));
@@ -795,6 +866,7 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
     int rc;
     if ((rc = ensure(B.chunk_act, (size_t)t.n_tint * aa.n_chunks))) return rc;
     aa.chunk_active = (const uint8_t *)B.chunk_act.ptr;
+    sa.chunk_active = aa.chunk_active;
     pa.a = aa;
     pa.chunk_active = (const uint8_t *)B.chunk_act.ptr;
     pa.err = d_err;
@@ -838,7 +910,10 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
                 CK(cudaGetLastError());
             }
             CK(cudaEventRecordWithFlags(events[2 + 2 * (k - 1)], st, rec_flags));
-            if (pipelined) {
+            if (streaming) {
+                sa.n_active = cnt + (k - 1);
+                CK(L.stream_launch(grid, block, stream_smem, st, sa));
+            } else if (pipelined) {
                 pa.a.n_active = cnt + (k - 1);
                 CK(L.pipe_launch(grid, pipe_smem, st, pa));
             } else {

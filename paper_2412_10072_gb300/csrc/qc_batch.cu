@@ -56,6 +56,9 @@ struct BatchArgs {
     double damping, tol;
     int max_ant;
     unsigned long long *vis_iters, *bytes;
+    const float2 *fb_gains;      // [sum n_ant][2] fallback start, or null
+    const double *fb_chi2;       // [n_prob] chi^2 at the fallback gains (with fb_gains)
+    unsigned long long *n_fallback;
 };
 
 // Sum v over the run of equal keys that contains this lane; the run's first lane gets it.
@@ -138,6 +141,7 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchArgs a)
     float4 *g32 = reinterpret_cast<float4 *>(g64 + a.max_ant * 2);            // [max_ant] (g_XX, g_YY)
     float *acc = reinterpret_cast<float *>(g32 + a.max_ant);                  // [max_ant][6]
     __shared__ double red[2][32];
+    __shared__ double s_chi;
     __shared__ int s_prob, s_done;
     int static_k = 0;
 
@@ -172,9 +176,15 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchArgs a)
         const int2 *ants = a.ants + P.row_off;
         const float *rsc = M16 ? a.row_scale + P.row_off : nullptr;
         int k;
+        bool fell_back = false;
+        const bool check = a.fb_gains != nullptr;
         for (k = 1; k <= a.max_iter; ++k) {
             for (int i = tid; i < na * 6; i += blockDim.x) acc[i] = 0.f;
+            if (tid == 0) s_chi = 0.0;
             __syncthreads();
+            // the first pass also sums chi^2 at the starting gains (fallback check)
+            const bool want_chi = check && k == 1 && !fell_back;
+            float chi = 0.f;
             // issue cursor: the step whose copies are issued next, and the lane's (row, chan) in it
             long is = st_begin;
             int irow, ic;
@@ -274,6 +284,8 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchArgs a)
                     const float2 r10 = csub(D.c, cmul(gp1, X10)), r11 = csub(D.d, cmul(gp1, X11));
                     const float2 wr00 = cscale(r00, w.x), wr01 = cscale(r01, w.y);
                     const float2 wr10 = cscale(r10, w.z), wr11 = cscale(r11, w.w);
+                    if (want_chi)
+                        chi += fmaf(w.x, cnorm2(r00), fmaf(w.y, cnorm2(r01), fmaf(w.z, cnorm2(r10), w.w * cnorm2(r11))));
                     // p side: parameter k touches row k of V: d V[k][j] / d g_p[k] = X[k][j]
                     sp[0] += fmaf(w.x, cnorm2(X00), w.y * cnorm2(X01));
                     sp[1] += fmaf(w.z, cnorm2(X10), w.w * cnorm2(X11));
@@ -295,7 +307,28 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchArgs a)
             cp_async_wait<0>();
             flush_runs(sp, kp, lane, acc);
             flush_runs(sq, kq, lane, acc);
+            if (want_chi) {
+                double c = chi;
+                for (int d = 16; d > 0; d >>= 1) c += __shfl_down_sync(0xffffffffu, c, d);
+                if (lane == 0) atomicAdd(&s_chi, c);
+            }
             __syncthreads();
+            if (want_chi && !(s_chi <= a.fb_chi2[pi] * (1.0 + 1e-5))) {
+                // the starting gains fit worse than the fallback (or are not finite): restart
+                // the problem from the fallback gains (every thread sees the same s_chi); the
+                // slack covers the different summation orders of the two chi^2 sums
+                for (int i = tid; i < na; i += blockDim.x) {
+                    const float2 f0 = a.fb_gains[(size_t)(P.gain_off + i) * 2];
+                    const float2 f1 = a.fb_gains[(size_t)(P.gain_off + i) * 2 + 1];
+                    g32[i] = make_float4(f0.x, f0.y, f1.x, f1.y);
+                    g64[2 * i] = make_double2(f0.x, f0.y);
+                    g64[2 * i + 1] = make_double2(f1.x, f1.y);
+                }
+                fell_back = true;
+                __syncthreads();
+                --k;
+                continue;
+            }
             // FP64 per-antenna solve and update (diagonal blocks: off-diagonal terms vanish)
             const double alpha = a.damping_mode == QC_DAMP_ALTERNATE ? ((k % 2 == 0) ? 0.5 : 1.0)
                                                                       : (a.damping > 0 ? a.damping : 1.0);
@@ -342,9 +375,11 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchArgs a)
         if (tid == 0) {
             if (a.iters) a.iters[pi] = done_iters;
             const unsigned long long ns = (unsigned long long)n_samp;
-            atomicAdd(a.vis_iters, ns * done_iters);
+            const unsigned long long passes = done_iters + (fell_back ? 1 : 0);   // data passes made
+            atomicAdd(a.vis_iters, ns * passes);
             const unsigned long long b = (a.flag ? ns : 0ull) + (unsigned long long)P.n_unflag * (M16 ? 64ull : 80ull);
-            atomicAdd(a.bytes, b * done_iters);
+            atomicAdd(a.bytes, b * passes);
+            if (fell_back) atomicAdd(a.n_fallback, 1ull);
         }
         __syncthreads();
     }
@@ -399,17 +434,28 @@ __global__ void __launch_bounds__(256) batch_chi2_kernel(const BatchArgs a, doub
 // Per-antenna warm-start features of every problem (one CTA per problem, one data
 // pass at unit gains): JHJ diagonal and JHr at g = 1 (both baseline orientations),
 // sums of |d_kk| / |m_kk| and their counts; then the 10 features per antenna.
-__global__ void __launch_bounds__(256) batch_features_kernel(const BatchArgs a, const float2 *prev, float *feat)
+__global__ void __launch_bounds__(256) batch_features_kernel(const BatchArgs a, const float2 *prev, float *feat,
+                                                             double *chi2_prev)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    float *acc = reinterpret_cast<float *>(smem);          // [max_ant][9]: h0 h1 jr0 ji0 jr1 ji1 s0 s1 cnt
+    float4 *gprev = reinterpret_cast<float4 *>(smem);      // [max_ant] previous gains (g_XX, g_YY)
+    float *acc = reinterpret_cast<float *>(gprev + a.max_ant);   // [max_ant][9]: h0 h1 jr0 ji0 jr1 ji1 s0 s1 cnt
     __shared__ float2 ref[2];
+    __shared__ double s_chi;
     const int pi = blockIdx.x;
     const BProb P = a.probs[pi];
     const int na = P.n_ant, nc = P.n_chan, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n_warps = blockDim.x >> 5;
+    const bool want_chi = chi2_prev != nullptr && prev != nullptr;
     for (int i = tid; i < na * 9; i += blockDim.x) acc[i] = 0.f;
+    for (int i = tid; i < na; i += blockDim.x) {
+        const float2 g0 = prev ? prev[(size_t)(P.gain_off + i) * 2] : make_float2(1.f, 0.f);
+        const float2 g1 = prev ? prev[(size_t)(P.gain_off + i) * 2 + 1] : make_float2(1.f, 0.f);
+        gprev[i] = make_float4(g0.x, g0.y, g1.x, g1.y);
+    }
+    if (tid == 0) s_chi = 0.0;
     __syncthreads();
+    float chi = 0.f;
     const bool wide = nc >= 32;
     const int rpi = wide ? 1 : 32 / nc;
     const int chunks = wide ? (nc + 31) / 32 : 1;
@@ -465,6 +511,15 @@ __global__ void __launch_bounds__(256) batch_features_kernel(const BatchArgs a, 
                 float2 k1 = cfma_conj(cconj(M.d), cscale(cconj(r11), w.w), cfma_conj(cconj(M.b), cscale(cconj(r01), w.y), make_float2(0.f, 0.f)));
                 v[11] = k0.x; v[12] = k0.y; v[13] = k1.x; v[14] = k1.y;
                 v[15] = v[6]; v[16] = v[7]; v[17] = v[8];
+                if (want_chi) {
+                    // chi^2 at the previous-interval gains (Eq. min), for the fallback check
+                    const float4 Gp = gprev[p], Gq = gprev[q];
+                    const float2 gp0 = make_float2(Gp.x, Gp.y), gp1 = make_float2(Gp.z, Gp.w);
+                    const float2 gq0 = make_float2(Gq.x, Gq.y), gq1 = make_float2(Gq.z, Gq.w);
+                    const float2 e00 = csub(D.a, cmul(gp0, cmulc(M.a, gq0))), e01 = csub(D.b, cmul(gp0, cmulc(M.b, gq1)));
+                    const float2 e10 = csub(D.c, cmul(gp1, cmulc(M.c, gq0))), e11 = csub(D.d, cmul(gp1, cmulc(M.d, gq1)));
+                    chi += fmaf(w.x, cnorm2(e00), fmaf(w.y, cnorm2(e01), fmaf(w.z, cnorm2(e10), w.w * cnorm2(e11))));
+                }
             }
         }
         const int kp = in ? p : -1, kq = in ? q : -1;
@@ -483,16 +538,34 @@ __global__ void __launch_bounds__(256) batch_features_kernel(const BatchArgs a, 
             }
         }
     }
+    if (want_chi) {
+        double c = chi;
+        for (int d = 16; d > 0; d >>= 1) c += __shfl_down_sync(0xffffffffu, c, d);
+        if (lane == 0) atomicAdd(&s_chi, c);
+    }
     __syncthreads();
-    // reference of the previous-interval gains: phase of their sum per correlation
-    if (tid < 2) {
+    if (want_chi && tid == 0) chi2_prev[pi] = s_chi;
+    // references: phase of the sum over antennas, per correlation, of the previous-interval
+    // gains (ref) and of the one-step gains 1 + JHr/JHJ at unit gains (ref1)
+    __shared__ float2 ref1[2];
+    if (tid < 4) {
+        const int k = tid & 1;
         float2 sum = make_float2(0.f, 0.f);
         for (int ant = 0; ant < na; ++ant) {
-            const float2 g = prev ? prev[(size_t)(P.gain_off + ant) * 2 + tid] : make_float2(1.f, 0.f);
+            float2 g;
+            if (tid < 2) {
+                g = prev ? prev[(size_t)(P.gain_off + ant) * 2 + k] : make_float2(1.f, 0.f);
+            } else {
+                const float *A = acc + ant * 9;
+                const float h = A[k];
+                g = h > 0.f ? make_float2(1.f + A[2 + 2 * k] / h, A[3 + 2 * k] / h) : make_float2(0.f, 0.f);
+            }
             sum = cadd(sum, g);
         }
         const float mag = sqrtf(cnorm2(sum));
-        ref[tid] = mag > 0.f ? make_float2(sum.x / mag, -sum.y / mag) : make_float2(1.f, 0.f);
+        const float2 r = mag > 0.f ? make_float2(sum.x / mag, -sum.y / mag) : make_float2(1.f, 0.f);
+        if (tid < 2) ref[k] = r;
+        else ref1[k] = r;
     }
     __syncthreads();
     for (int ant = tid; ant < na; ant += blockDim.x) {
@@ -502,7 +575,8 @@ __global__ void __launch_bounds__(256) batch_features_kernel(const BatchArgs a, 
             const float h = A[k];
             const float2 z = h > 0.f ? make_float2(A[2 + 2 * k] / h, A[3 + 2 * k] / h) : make_float2(0.f, 0.f);
             f[k] = sqrtf(cnorm2(z));
-            f[2 + k] = h > 0.f ? atan2f(z.y, z.x) : 0.f;
+            const float2 g1 = cmul(make_float2(1.f + z.x, z.y), ref1[k]);
+            f[2 + k] = h > 0.f ? atan2f(g1.y, g1.x) : 0.f;
             f[4 + k] = A[8] > 0.f ? A[6 + k] / A[8] : 0.f;
             const float2 g = prev ? prev[(size_t)(P.gain_off + ant) * 2 + k] : make_float2(1.f, 0.f);
             const float2 gr = cmul(g, ref[k]);
@@ -665,7 +739,7 @@ struct qc_batch {
     std::map<std::string, Shape> tuned;
     std::string shape_key;
     struct GraphKey { int threads, per_sm, schedule, depth, max_iter, damping_mode; double damping, tol; bool m16;
-                      void *gains; void *flags; void *iters; cudaStream_t st; };
+                      void *gains; void *flags; void *iters; cudaStream_t st; const void *fb_gains, *fb_chi2; };
     cudaGraphExec_t exec = nullptr;
     GraphKey gkey;
     std::string err;
@@ -791,7 +865,7 @@ extern "C" int qc_batch_create(const qc_batch_problem *p, qc_batch **out)
     }
     BALLOC(b->probs, BProb, p->n_prob);
     BH2D(b->probs, b->hprobs.data(), sizeof(BProb) * p->n_prob);
-    BALLOC(b->counters, unsigned long long, 2 + p->n_prob);
+    BALLOC(b->counters, unsigned long long, 3 + p->n_prob);
     // unflagged samples per problem
     e = cudaMemsetAsync(b->counters, 0, sizeof(unsigned long long) * (2 + p->n_prob), st);
     if (e == cudaSuccess) {
@@ -977,6 +1051,9 @@ static int batch_solve_impl(qc_batch *b, void *gains, int8_t *gain_flags, int32_
     if (mem != QC_MEM_HOST && mem != QC_MEM_DEVICE) return b->fail(QC_EINVAL, "mem must be QC_MEM_HOST or DEVICE");
     if (o->max_iter < 1) return b->fail(QC_EINVAL, "max_iter must be >= 1");
     if (!(o->tol >= 0)) return b->fail(QC_EINVAL, "tol must be >= 0");
+    if ((o->fallback_gains == nullptr) != (o->fallback_chi2 == nullptr))
+        return b->fail(QC_EINVAL, "fallback_gains and fallback_chi2 go together");
+    if (o->fallback_gains && mem != QC_MEM_DEVICE) return b->fail(QC_EINVAL, "a fallback start needs device gains");
     if (o->damping_mode != QC_DAMP_CONST && o->damping_mode != QC_DAMP_ALTERNATE) return b->fail(QC_EINVAL, "damping_mode");
     int threads, per_sm, schedule, depth, rc;
     if ((rc = launch_shape(b, o, threads, per_sm, schedule, depth))) return rc;
@@ -998,16 +1075,21 @@ static int batch_solve_impl(qc_batch *b, void *gains, int8_t *gain_flags, int32_
     a.damping_mode = o->damping_mode;
     a.damping = o->damping;
     a.tol = o->tol;
+    a.fb_gains = (const float2 *)o->fallback_gains;
+    a.fb_chi2 = o->fallback_chi2;
+    a.n_fallback = b->counters + 2 + b->n_prob;
     const int grid = std::max(1, std::min(b->n_prob, b->sm_count * per_sm));
     BCK(cudaEventRecord(b->ev0, st));
     if (mem == QC_MEM_HOST) BCK(cudaMemcpyAsync(dg, gains, gbytes, cudaMemcpyHostToDevice, st));
     BCK(cudaMemsetAsync(b->counters, 0, 2 * sizeof(unsigned long long), st));
+    BCK(cudaMemsetAsync(b->counters + 2 + b->n_prob, 0, sizeof(unsigned long long), st));
     if (o->use_graph && !tuning) {
         qc_batch::GraphKey k;
         memset(&k, 0, sizeof k);
         k.threads = threads; k.per_sm = per_sm; k.schedule = schedule; k.depth = depth; k.max_iter = o->max_iter;
         k.damping_mode = o->damping_mode; k.damping = o->damping; k.tol = o->tol; k.m16 = b->m16;
         k.gains = dg; k.flags = dflags; k.iters = diters; k.st = st;
+        k.fb_gains = o->fallback_gains; k.fb_chi2 = o->fallback_chi2;
         const bool same = b->exec && memcmp(&k, &b->gkey, sizeof k) == 0;
         if (!same) {
             if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
@@ -1034,8 +1116,9 @@ static int batch_solve_impl(qc_batch *b, void *gains, int8_t *gain_flags, int32_
         if (gain_flags) BCK(cudaMemcpyAsync(gain_flags, dflags, (size_t)b->total_ant, cudaMemcpyDeviceToHost, st));
         if (iters) BCK(cudaMemcpyAsync(iters, diters, sizeof(int) * b->n_prob, cudaMemcpyDeviceToHost, st));
     }
-    unsigned long long hc[2];
+    unsigned long long hc[2], hfb = 0;
     BCK(cudaMemcpyAsync(hc, b->counters, sizeof hc, cudaMemcpyDeviceToHost, st));
+    BCK(cudaMemcpyAsync(&hfb, b->counters + 2 + b->n_prob, sizeof hfb, cudaMemcpyDeviceToHost, st));
     BCK(cudaEventRecord(b->ev1, st));
     BCK(cudaStreamSynchronize(st));
     float ms = 0;
@@ -1051,6 +1134,7 @@ static int batch_solve_impl(qc_batch *b, void *gains, int8_t *gain_flags, int32_
         S.schedule = schedule;
         S.grid = grid;
         S.depth = depth;
+        S.n_fallback = (int32_t)hfb;
         double tot_vis = 0;
         for (const BProb &P : b->hprobs) tot_vis += (double)P.n_rows * P.n_chan;
         S.mean_iters = tot_vis > 0 ? (double)hc[0] / tot_vis : 0;
@@ -1151,30 +1235,37 @@ extern "C" int qc_batch_residual(qc_batch *b, const void *gains, int32_t mem, do
 }
 
 
-extern "C" int qc_batch_features(qc_batch *b, const void *prev_gains, float *features, int32_t mem, void *stream)
+extern "C" int qc_batch_features(qc_batch *b, const void *prev_gains, float *features, double *prev_chi2, int32_t mem,
+                                 void *stream)
 {
     if (!b) return QC_EINVAL;
     b->err.clear();
     if (!features) return b->fail(QC_EINVAL, "features is NULL");
+    if (prev_chi2 && !prev_gains) return b->fail(QC_EINVAL, "prev_chi2 needs prev_gains");
     if (mem != QC_MEM_HOST && mem != QC_MEM_DEVICE) return b->fail(QC_EINVAL, "mem must be QC_MEM_HOST or DEVICE");
     cudaStream_t st = stream ? (cudaStream_t)stream : b->own_stream;
     const size_t gbytes = (size_t)b->total_ant * 2 * sizeof(float2), fbytes = (size_t)b->total_ant * 10 * sizeof(float);
+    const size_t cbytes = sizeof(double) * b->n_prob;
     void *tmp = nullptr;
     const float2 *dprev = (const float2 *)prev_gains;
     float *dfeat = features;
+    double *dchi = prev_chi2;
     if (mem == QC_MEM_HOST) {
-        BCK(cudaMalloc(&tmp, gbytes + fbytes));
-        dfeat = (float *)tmp;
+        BCK(cudaMalloc(&tmp, cbytes + fbytes + gbytes));
+        dchi = prev_chi2 ? (double *)tmp : nullptr;
+        dfeat = (float *)((unsigned char *)tmp + cbytes);
         if (prev_gains) {
-            BCK(cudaMemcpyAsync((unsigned char *)tmp + fbytes, prev_gains, gbytes, cudaMemcpyHostToDevice, st));
-            dprev = (const float2 *)((unsigned char *)tmp + fbytes);
+            dprev = (const float2 *)((unsigned char *)tmp + cbytes + fbytes);
+            BCK(cudaMemcpyAsync((void *)dprev, prev_gains, gbytes, cudaMemcpyHostToDevice, st));
         }
     }
     BatchArgs a = batch_args(b);
-    const size_t smem = (size_t)b->max_ant * 9 * sizeof(float);
-    batch_features_kernel<<<b->n_prob, 256, smem, st>>>(a, dprev, dfeat);
+    const size_t smem = (size_t)b->max_ant * (sizeof(float4) + 9 * sizeof(float));
+    batch_features_kernel<<<b->n_prob, 256, smem, st>>>(a, dprev, dfeat, dchi);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && mem == QC_MEM_HOST) e = cudaMemcpyAsync(features, dfeat, fbytes, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && mem == QC_MEM_HOST && prev_chi2)
+        e = cudaMemcpyAsync(prev_chi2, dchi, cbytes, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess && mem == QC_MEM_HOST) e = cudaStreamSynchronize(st);
     if (tmp) { cudaStreamSynchronize(st); cudaFree(tmp); }
     if (e != cudaSuccess) return b->cuda_fail(e, "batch features");

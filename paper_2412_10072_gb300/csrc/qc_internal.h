@@ -6,7 +6,7 @@
 #include <vector>
 
 #include "../../include/qc.h"
-#include "qc_kernels.cuh"
+#include "qc_stream.cuh"
 
 struct Buf {
     void *ptr = nullptr;
@@ -29,6 +29,9 @@ struct TermBufs {
     Buf chunk_act; // uint8 [n_tint][n_chunks] for the pipelined kernel
     Buf row_info;  // int4 [n_row] {p, q, tn, to} for the pipelined kernel
     Buf chunk_info;// int4 [n_chunks] Jones slice ranges of the 32-channel chunks
+    Buf rt;        // int4 [n_row] step-major row table of the streaming kernel
+    Buf rt_scale;  // float [n_row] its FP16 model scales
+    Buf fmap2;     // int2 [n_chan] {f_map of this term, f_map of the other term}
     cudaGraphExec_t exec = nullptr;
     bool graph_valid = false;
 };
@@ -43,6 +46,9 @@ struct AccLaunch {
     cudaError_t (*pipe_launch)(int grid, int smem_bytes, cudaStream_t st, const qc::PipeArgs &p) = nullptr;
     int pipe_nw = 0;                 // its warps per CTA
     int pipe_h = 1;                  // row segments per warp step
+    const void *stream_fn = nullptr; // streaming kernel (chains of one or two terms only)
+    cudaError_t (*stream_launch)(int grid, int block, int smem_bytes, cudaStream_t st, const qc::StreamArgs &a) = nullptr;
+    int stream_smem_per_warp = 0;
 };
 AccLaunch acc_launcher_diag(bool simple, int lk, int rk, bool m16);
 AccLaunch acc_launcher_full(bool simple, int lk, int rk, bool m16);
@@ -55,6 +61,7 @@ struct qc_ctx {
     int dev = 0, sm_count = 1, smem_optin = 0;
     cudaStream_t own_stream = nullptr;
     int n_row = 0, n_chan = 0, n_ant = 0, n_time = 0, n_bl = 0, n_strips = 0;
+    long n_strip_rows = 0;            // rows in the baseline strips (cross-correlations)
     bool m16 = false, has_flag = false;
     const float4 *d_vis = nullptr, *d_model = nullptr, *d_weight = nullptr;
     const uint8_t *d_flag = nullptr;
@@ -63,6 +70,7 @@ struct qc_ctx {
     int4 *d_rows = nullptr;
     int *d_strip_rows = nullptr, *d_strip_off = nullptr;
     uint8_t *d_row_live = nullptr;    // [n_row]
+    const float4 *d_wf = nullptr;     // [n_row][n_chan] weights with flags folded in (streaming kernel)
     int *d_err = nullptr;             // device error flag of bounded waits
     std::vector<void *> owned;
     std::vector<cudaEvent_t> events;

@@ -1,0 +1,318 @@
+// qc_stream.cuh -- streaming accumulate kernel for chains of one or two terms.
+//
+// Same arithmetic as acc_kernel (the residual r = D - L_p G_p R_p M C_q^H of every
+// sample and its contributions to the per-(interval, antenna) blocks of J^H W J and
+// J^H W r of both antennas, Eq. jhj_entry_simplified, Eq. jhr_entry_simplified),
+// organised so that nothing on a warp's critical path waits for a dependent load:
+//
+//  * the rows are visited through a step-major row table rt[k] = {row, p | q << 16,
+//    t_int of the solved term (-1: nothing to read), t_int of the other term},
+//    built once per term solve in the order of the tiles (row tiles: row order;
+//    strip tiles: the rows of each baseline in time order), so a warp step --
+//    one row x 32 channels -- has its antennas and interval indices in one entry;
+//  * flags are folded into the weights when the problem is created (w = 0 for a
+//    flagged sample or an autocorrelation), so a step reads d, m and w only, and a
+//    sample whose four weights are zero is skipped (a select, so non-finite data in
+//    flagged cells does not propagate);
+//  * d, m, w of each step are copied DEPTH - 1 steps ahead into the warp's ring in
+//    shared memory (16-byte cp.async per lane, zero-filled for lanes with nothing to
+//    read), and lane 0 writes the step's row-table entry beside them;
+//  * the lane's channel interval indices are read two steps ahead and the gain-table
+//    entries of the next step are prefetched into L1, so the gain loads of a step
+//    hit L1.
+//
+// Work decomposition as in acc_kernel: a unit is a row (row tiles: its 32-channel
+// chunks are the steps) or a baseline strip x 32 channels (strip tiles: its rows
+// are the steps); warps take units with a grid stride.  Register sums are flushed
+// (segmented warp reduction + FP64 atomics) when the antenna pair or any lane's
+// interval bin changes.
+#pragma once
+#include "qc_kernels.cuh"
+
+namespace qc {
+
+struct StreamArgs {
+    const float4 *vis;          // [n_row][n_chan] x 2
+    const float4 *model;        // [n_row][n_chan] x 2, or null (FP16 model)
+    const uint4 *model16;       // [n_row][n_chan] (4 half2), or null
+    const float4 *wf;           // [n_row][n_chan] weights with flags folded in
+    int n_chan, n_ant;
+    const int4 *rt;             // step-major row table (see above)
+    const float *rt_scale;      // [rt] FP16 model scale of the entry's baseline, or null
+    const int *unit_off;        // strip tiles: [n_strips + 1] offsets into rt
+    int order;                  // 0 row tiles, 1 strip tiles
+    int n_units, n_chunks;
+    DevTerm tn, to;             // solved term, other term (a copy of tn when there is none)
+    const int2 *fmap2;          // [n_chan] {f_map of the solved term, f_map of the other term}
+    const uint8_t *chunk_active;// [tn.n_tint][n_chunks]
+    const uint8_t *active;      // [bins of the solved term]
+    const int *n_active;        // nonzero: some interval still iterating
+    double *acc;                // [bins][n_ant][KG]
+};
+
+constexpr int STREAM_END = -2;  // row-table field marking the end of a warp's stream
+
+__device__ __forceinline__ void prefetch_l1(const void *p)
+{
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
+template <int K> __device__ __forceinline__ const float4 *tab_ptr(const DevTerm &T, int n_ant, int tint, int fint, int ant)
+{
+    const size_t idx = ((size_t)tint * n_ant + ant) * T.n_fint + fint;
+    return T.tab + (K == KIND_FULL ? 2 * idx : idx);
+}
+
+template <int TS, int LK, int RK, bool M16, int DEPTH>
+__global__ void __launch_bounds__(256) acc_stream_kernel(const StreamArgs a)
+{
+    if (__ldg(a.n_active) == 0) return;
+    constexpr bool HAS_L = LK != KIND_NONE;
+    constexpr bool HAS_O = LK != KIND_NONE || RK != KIND_NONE;
+    constexpr int OK_ = HAS_L ? LK : RK;                     // kind of the other term
+    constexpr int GK = TS == TS_FULL ? KIND_FULL : KIND_DIAG;
+    constexpr bool KAHAN = M16;
+    using Lay = AccLayout<TS, HAS_L>;
+    constexpr int KR = Lay::KR, KG = Lay::KG;
+    constexpr int V4 = M16 ? 4 : 5;                         // 16-byte words per sample: d (2), m (2 or 1), w (1)
+    static_assert(DEPTH >= 4, "the entries of the next two steps must be in the ring");
+    extern __shared__ float4 s_stream[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    float4 *ring = s_stream + (size_t)wib * DEPTH * V4 * 32;                          // [DEPTH][V4][32]
+    int4 *meta = reinterpret_cast<int4 *>(s_stream + (size_t)nw * DEPTH * V4 * 32) + (size_t)wib * DEPTH * 2;
+    const long W = ((long)gridDim.x * blockDim.x) >> 5;
+    const int n_chan = a.n_chan, n_ant = a.n_ant, nch = a.n_chunks;
+
+    // ---------------- issue side: the step DEPTH - 1 ahead of the arithmetic ----------------
+    long iu = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;   // unit
+    int ii = 0, ilen = 0;            // step within the unit, steps in the unit
+    int ikb = 0, ic0 = 0;            // strip tiles: first rt entry of the unit, first channel of its chunk
+    int4 irt = make_int4(0, 0, -1, 0);   // row tiles: the unit's row-table entry
+    float isc = 0.f;
+    unsigned imask = 0;              // row tiles: active 32-channel chunks of the row (bit per chunk)
+    int4 blk = make_int4(0, 0, -1, 0);   // strip tiles: entries of the current 32-step block, one per lane
+    float blks = 0.f;
+    unsigned blkact = 0;
+    int blk_base = -1;
+
+    // find the next unit with something to read (sets ilen > 0) or run out (iu >= n_units)
+    auto unit_start = [&]() {
+        ii = 0;
+        ilen = 0;
+        while (iu < a.n_units) {
+            if (a.order == 0) {
+                irt = __ldg(a.rt + iu);
+                if (irt.z >= 0) {
+                    unsigned m = 0;
+                    for (int c0 = 0; c0 < nch; c0 += 32) {
+                        const bool act = c0 + lane < nch && __ldg(a.chunk_active + (size_t)irt.z * nch + c0 + lane);
+                        const unsigned b = __ballot_sync(0xffffffffu, act);
+                        if (c0 == 0) m = b;
+                        else if (b) m |= 0x80000000u;    // chunks >= 32: read (activity checked per lane)
+                    }
+                    imask = m;
+                    if (m) {
+                        isc = M16 ? __ldg(a.rt_scale + iu) : 0.f;
+                        ilen = nch;
+                        return;
+                    }
+                }
+            } else {
+                const int s = (int)(iu / nch);
+                ic0 = (int)(iu - (long)s * nch) * 32;
+                ikb = __ldg(a.unit_off + s);
+                ilen = __ldg(a.unit_off + s + 1) - ikb;
+                blk_base = -1;
+                if (ilen > 0) return;
+            }
+            iu += W;
+        }
+    };
+    unit_start();
+
+    int stage_i = 0;
+    auto issue = [&]() {
+        int4 e = make_int4(STREAM_END, 0, -1, 0);
+        float sc = 0.f;
+        int c0 = 0;
+        bool live = false;
+        if (iu < a.n_units) {
+            if (a.order == 0) {
+                e = irt;
+                sc = isc;
+                c0 = ii * 32;
+                live = ii >= 31 ? ((imask >> 31) & 1) : ((imask >> ii) & 1);
+            } else {
+                const int b = ii >> 5, l = ii & 31;
+                if (b != blk_base) {
+                    blk_base = b;
+                    const int j = b * 32 + lane;
+                    const bool in = j < ilen;
+                    blk = in ? __ldg(a.rt + ikb + j) : make_int4(0, 0, -1, 0);
+                    blks = (M16 && in) ? __ldg(a.rt_scale + ikb + j) : 0.f;
+                    const bool act = in && blk.z >= 0 && __ldg(a.chunk_active + (size_t)blk.z * nch + (ic0 >> 5));
+                    blkact = __ballot_sync(0xffffffffu, act);
+                }
+                e.x = __shfl_sync(0xffffffffu, blk.x, l);
+                e.y = __shfl_sync(0xffffffffu, blk.y, l);
+                e.z = __shfl_sync(0xffffffffu, blk.z, l);
+                e.w = __shfl_sync(0xffffffffu, blk.w, l);
+                sc = __shfl_sync(0xffffffffu, blks, l);
+                c0 = ic0;
+                live = (blkact >> l) & 1;
+            }
+            if (!live) e.z = -1;
+        }
+        const int c = c0 + lane;
+        const bool rd = live && c < n_chan;
+        const size_t s = rd ? (size_t)e.x * n_chan + c : 0;
+        const uint32_t nb = rd ? 16u : 0u;
+        float4 *slot = ring + (size_t)stage_i * V4 * 32 + lane;
+        cp_async16(slot, a.vis + 2 * s, nb);
+        cp_async16(slot + 32, a.vis + 2 * s + 1, nb);
+        if constexpr (M16) {
+            cp_async16(slot + 64, a.model16 + s, nb);
+            cp_async16(slot + 96, a.wf + s, nb);
+        } else {
+            cp_async16(slot + 64, a.model + 2 * s, nb);
+            cp_async16(slot + 96, a.model + 2 * s + 1, nb);
+            cp_async16(slot + 128, a.wf + s, nb);
+        }
+        cp_async_commit();
+        if (lane == 0) {
+            meta[2 * stage_i] = e;
+            meta[2 * stage_i + 1] = make_int4(c0, __float_as_int(sc), 0, 0);
+        }
+        if (++stage_i == DEPTH) stage_i = 0;
+        if (iu < a.n_units && ++ii == ilen) {
+            iu += W;
+            unit_start();
+        }
+    };
+
+#pragma unroll
+    for (int d = 0; d < DEPTH - 1; ++d) issue();
+    __syncwarp();
+
+    // ---------------- arithmetic side ----------------
+    Acc<KR, KAHAN> Ap, Aq;
+    Ap.zero();
+    Aq.zero();
+    int stage = 0, cur_key = -1, cur_pq = -1;
+    // channel interval maps of the lane for the current step (fmA) and the next one (fmB);
+    // each is read two steps ahead from the step's entry in the ring
+    auto read_map = [&](int st) {
+        const int4 m0 = meta[2 * st], m1 = meta[2 * st + 1];
+        const int c = m1.x + lane;
+        return (m0.x != STREAM_END && m0.z >= 0 && c < n_chan) ? __ldg(a.fmap2 + c) : make_int2(0, 0);
+    };
+    int2 fmA = read_map(0), fmB = read_map(1);
+    for (;;) {
+        const int4 e = meta[2 * stage];
+        const int4 e1 = meta[2 * stage + 1];
+        if (e.x == STREAM_END) break;
+        const int2 fm = fmA;
+        const int nst = stage + 1 == DEPTH ? 0 : stage + 1;
+        const int nst2 = nst + 1 == DEPTH ? 0 : nst + 1;
+        // the step after next: its channel maps; the next step: its gain entries into L1
+        const int2 fmC = read_map(nst2);
+        {
+            const int4 n0 = meta[2 * nst];
+            if (n0.x != STREAM_END && n0.z >= 0) {
+                const int np = n0.y & 0xffff, nq = n0.y >> 16;
+                prefetch_l1(tab_ptr<GK>(a.tn, n_ant, n0.z, fmB.x, np));
+                prefetch_l1(tab_ptr<GK>(a.tn, n_ant, n0.z, fmB.x, nq));
+                if constexpr (HAS_O) {
+                    prefetch_l1(tab_ptr<OK_>(a.to, n_ant, n0.w, fmB.y, np));
+                    prefetch_l1(tab_ptr<OK_>(a.to, n_ant, n0.w, fmB.y, nq));
+                }
+            }
+        }
+        issue();
+        cp_async_wait<DEPTH - 1>();
+        __syncwarp();
+        const bool live = e.z >= 0;                 // warp-uniform
+        const int c = e1.x + lane;
+        const bool in = live && c < n_chan;
+        const int key = in ? e.z * a.tn.n_fint + fm.x : -1;
+        if (live) {
+            const bool change = e.y != cur_pq || key != cur_key;
+            if (__any_sync(0xffffffffu, change && cur_key >= 0)) {
+                const unsigned m = __match_any_sync(0xffffffffu, cur_key);
+                const unsigned seg_end = 32 - __clz(m);
+                const bool head = lane == __ffs(m) - 1;
+                const bool lv = cur_key >= 0 && __ldg(a.active + cur_key);
+                const int p = cur_pq & 0xffff, q = cur_pq >> 16;
+                flush_side<KR, KG, KAHAN, Lay>(Ap, cur_key, p, lane, seg_end, head, lv, a.acc, n_ant);
+                flush_side<KR, KG, KAHAN, Lay>(Aq, cur_key, q, lane, seg_end, head, lv, a.acc, n_ant);
+            }
+            cur_key = key;
+            cur_pq = e.y;
+        }
+        const float4 *slot = ring + (size_t)stage * V4 * 32 + lane;
+        const float4 w = slot[M16 ? 96 : 128];
+        bool ok = in && (w.x != 0.f || w.y != 0.f || w.z != 0.f || w.w != 0.f);
+        if (ok) ok = __ldg(a.active + key) != 0;
+        if (ok) {
+            const int p = e.y & 0xffff, q = e.y >> 16;
+            const J2 Dm = j_from(slot[0], slot[32]);
+            J2 M;
+            if constexpr (M16) M = load_model16(*reinterpret_cast<const uint4 *>(slot + 64), __int_as_float(e1.y));
+            else M = j_from(slot[64], slot[96]);
+            J2 Lp, Gp, Rp, Lq, Gq, Rq;
+            Gp = fetch_k<GK>(a.tn, n_ant, e.z, fm.x, p);
+            Gq = fetch_k<GK>(a.tn, n_ant, e.z, fm.x, q);
+            if constexpr (LK != KIND_NONE) {
+                Lp = fetch_k<LK>(a.to, n_ant, e.w, fm.y, p);
+                Lq = fetch_k<LK>(a.to, n_ant, e.w, fm.y, q);
+            }
+            if constexpr (RK != KIND_NONE) {
+                Rp = fetch_k<RK>(a.to, n_ant, e.w, fm.y, p);
+                Rq = fetch_k<RK>(a.to, n_ant, e.w, fm.y, q);
+            }
+            sample_math<TS, LK, RK, KAHAN>(Lp, Gp, Rp, Lq, Gq, Rq, Dm, M, w, Ap, Aq);
+        }
+        fmA = fmB;
+        fmB = fmC;
+        stage = nst;
+    }
+    if (__any_sync(0xffffffffu, cur_key >= 0)) {
+        const unsigned m = __match_any_sync(0xffffffffu, cur_key);
+        const unsigned seg_end = 32 - __clz(m);
+        const bool head = lane == __ffs(m) - 1;
+        const bool lv = cur_key >= 0 && __ldg(a.active + cur_key);
+        const int p = cur_pq & 0xffff, q = cur_pq >> 16;
+        flush_side<KR, KG, KAHAN, Lay>(Ap, cur_key, p, lane, seg_end, head, lv, a.acc, n_ant);
+        flush_side<KR, KG, KAHAN, Lay>(Aq, cur_key, q, lane, seg_end, head, lv, a.acc, n_ant);
+    }
+    cp_async_wait<0>();
+}
+
+// Step-major row table of a term solve: entry k of the tile order (row tiles: row k;
+// strip tiles: the k-th row of the strip order) -> {row, p | q << 16, t_int of the
+// solved term or -1 (no usable data), t_int of the other term}; for the FP16 model
+// also the scale of the row's baseline.
+static __global__ void row_table_kernel(int n, const int *order_rows, const int4 *row_info, const int4 *rows,
+                                        const float *bl_scale, int4 *rt, float *rt_scale)
+{
+    const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int row = order_rows ? order_rows[k] : (int)k;
+    const int4 ri = row_info[row];
+    rt[k] = make_int4(row, ri.x | (ri.y << 16), ri.z, ri.w);
+    if (rt_scale) rt_scale[k] = bl_scale[rows[row].w];
+}
+
+// w_f = w where the sample is usable (unflagged cross-correlation), else 0
+static __global__ void fold_flags_kernel(const float4 *w, const uint8_t *flag, const int4 *rows, long n_row, int n_chan,
+                                         float4 *wf)
+{
+    const long n = n_row * n_chan;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const int4 r = rows[i / n_chan];
+        const bool use = r.x != r.y && !(flag && flag[i]);
+        wf[i] = use ? w[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+} // namespace qc

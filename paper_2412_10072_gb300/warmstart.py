@@ -35,7 +35,7 @@ def _lib():
         lib.qc_mlp_adam.argtypes = [vp, vp, vp, vp, f32, f32, f32, f32, i32, vp]
         lib.qc_mlp_last_error.argtypes = []
         lib.qc_mlp_last_error.restype = C.c_char_p
-        lib.qc_batch_features.argtypes = [vp, vp, vp, i32, vp]
+        lib.qc_batch_features.argtypes = [vp, vp, vp, vp, i32, vp]
         lib.qc_batch_warmstart.argtypes = [vp, vp, vp, i32, vp, C.POINTER(C.c_int32), vp]
         lib.qc_batch_reference_gains.argtypes = [vp, vp, vp, vp]
         for f in (lib.qc_mlp_forward, lib.qc_mlp_backward, lib.qc_mlp_adam, lib.qc_batch_features,
@@ -117,15 +117,17 @@ def _he_init(seed: int) -> np.ndarray:
     return np.concatenate(parts)
 
 
-def features(bsolver: "qc.BatchSolver", prev_gains=None, stream=None):
-    """Per-antenna features [sum n_ant][10] (device) of a batch on the device."""
+def features(bsolver: "qc.BatchSolver", prev_gains=None, stream=None, want_prev_chi2: bool = False):
+    """Per-antenna features [sum n_ant][10] (device) of a batch on the device; with
+    want_prev_chi2, also each problem's chi^2 at prev_gains (same data pass)."""
     import torch
     f = torch.empty((bsolver.total_ant, N_IN), dtype=torch.float32, device="cuda")
+    chi = torch.empty(bsolver.n_prob, dtype=torch.float64, device="cuda") if want_prev_chi2 else None
     rc = _lib().qc_batch_features(bsolver._h, None if prev_gains is None else prev_gains.data_ptr(), f.data_ptr(),
-                                  qc.QC_MEM_DEVICE, _stream_ptr(stream))
+                                  None if chi is None else chi.data_ptr(), qc.QC_MEM_DEVICE, _stream_ptr(stream))
     if rc != qc.QC_OK:
         bsolver._err(rc)
-    return f
+    return (f, chi) if want_prev_chi2 else f
 
 
 def reference(bsolver: "qc.BatchSolver", gains, stream=None):
@@ -152,6 +154,27 @@ def initial_gains(bsolver: "qc.BatchSolver", net: MLP, prev_gains=None, check_ch
     if rc != qc.QC_OK:
         bsolver._err(rc)
     return g, n_fb.value
+
+
+def warm_solve(bsolver: "qc.BatchSolver", net: MLP, prev_gains, max_iter: int = 20, tol: float = 1e-6, stream=None,
+               **solve_kw):
+    """The learned warm start fused ahead of the batched solve: one data pass for the features
+    (and chi^2 at the previous-interval gains), the network, then the solve from the predicted
+    gains; a problem whose prediction is not finite falls back at once, and one whose chi^2 at
+    the prediction exceeds that at the previous gains restarts from them inside the solve's first
+    pass.  Returns (gains, iters, BatchStats, n_fallback)."""
+    x, chi_prev = features(bsolver, prev_gains, stream, want_prev_chi2=True)
+    y = net.forward(x, stream=stream)
+    import torch
+    g0 = torch.empty((bsolver.total_ant, 2), dtype=torch.complex64, device="cuda")
+    n_nf = C.c_int32(0)
+    rc = _lib().qc_batch_warmstart(bsolver._h, y.data_ptr(), prev_gains.data_ptr(), 0, g0.data_ptr(), C.byref(n_nf),
+                                   _stream_ptr(stream))
+    if rc != qc.QC_OK:
+        bsolver._err(rc)
+    g, _, it, st = bsolver.solve(g0, max_iter=max_iter, tol=tol, stream=stream, fallback=(prev_gains, chi_prev),
+                                 **solve_kw)
+    return g, it, st, n_nf.value + st.n_fallback
 
 
 def targets_from_gains(bsolver, gains):

@@ -82,7 +82,10 @@ def test_features_match_oracle(ws):
     prev = (rng.standard_normal((S.total_ant, 2)) + 1j * rng.standard_normal((S.total_ant, 2))).astype(np.complex64)
     f = np.zeros((S.total_ant, 10), np.float32)
     lib = ws._lib()
-    assert lib.qc_batch_features(S._h, prev.ctypes.data, f.ctypes.data, qc.QC_MEM_HOST, None) == 0
+    chi_prev = np.zeros(S.n_prob)
+    assert lib.qc_batch_features(S._h, prev.ctypes.data, f.ctypes.data, chi_prev.ctypes.data, qc.QC_MEM_HOST,
+                                 None) == 0
+    np.testing.assert_allclose(chi_prev, S.residual(prev), rtol=1e-5)
     offs = np.concatenate([[0], np.cumsum(b.n_ant)])
     for i in range(b.n_prob):
         r0, r1, v0, v1 = b.row_offset[i], b.row_offset[i + 1], b.vis_offset[i], b.vis_offset[i + 1]
@@ -95,16 +98,21 @@ def test_features_match_oracle(ws):
         T = O.OracleTerm("diag", np.zeros(1, np.int32), np.zeros(nc, np.int32), 1, 1, na)
         jhj, jhr = O.normal_equations(P, [T], 0)
         fi = f[offs[i]:offs[i + 1]]
+        h_all = np.real(np.stack([jhj[0, 0, :, k, k] for k in range(2)], 1))          # [ant, 2]
+        z_all = np.where(h_all > 0, np.stack([jhr[0, 0, :, k] for k in range(2)], 1) / np.where(h_all > 0, h_all, 1), 0)
+        g1 = np.where(h_all > 0, 1 + z_all, 0)                                        # one-step gains
+        ref1 = np.exp(-1j * np.angle(g1.sum(0)))
         for a in range(na):
             for k in range(2):
-                h = jhj[0, 0, a, k, k].real
+                h = h_all[a, k]
                 if h <= 0:
                     assert fi[a, k] == 0
                     continue
-                z = jhr[0, 0, a, k] / h
+                z = z_all[a, k]
                 assert abs(fi[a, k] - abs(z)) < 1e-4 * max(1, abs(z))
-                if abs(z) > 1e-3:
-                    assert abs(np.angle(np.exp(1j * (fi[a, 2 + k] - np.angle(z))))) < 1e-3
+                if abs(g1[a, k]) > 1e-3:
+                    want = np.angle(g1[a, k] * ref1[k])
+                    assert abs(np.angle(np.exp(1j * (fi[a, 2 + k] - want)))) < 1e-3
             # mean |d|/|m| on the diagonal correlations over the antenna's unflagged samples
             sel = ((b.ant1[r0:r1] == a) | (b.ant2[r0:r1] == a))[:, None] & (F == 0)
             for k, ci in ((0, 0), (1, 3)):
@@ -161,3 +169,29 @@ def test_training_reduces_loss_and_warm_start_beats_cold(ws):
     _, _, it_mlp, _ = S.solve(g0, max_iter=60)
     S.close()
     assert float(it_mlp.float().mean()) < float(it_cold.float().mean())
+
+
+def test_fused_fallback_restarts_worse_starts(ws):
+    """Starts that fit worse than the fallback restart from it inside the solve's first pass: the
+    result equals the solve from the fallback gains, and the restarts are counted."""
+    shapes = synth.batch_shapes(6, seed_base=950, ant=(5, 9), times=(1, 3), chans=(4, 24))
+    b = synth.make_batch(shapes, device="cuda")
+    S = qc.BatchSolver(b.data, b.model, b.weight, b.flag, b.ant1, b.ant2, b.row_offset, b.vis_offset, b.n_chan,
+                       b.n_ant)
+    offs = np.concatenate([[0], np.cumsum(b.n_ant)])
+    truth = torch.from_numpy(np.concatenate(b.truths).astype(np.complex64)).cuda()
+    fb = truth * torch.exp(1j * 0.05 * torch.ones_like(truth.real)).to(torch.complex64)   # a good fallback
+    _, chi_fb = ws.features(S, fb, want_prev_chi2=True)
+    g0 = fb.clone()
+    g0[offs[1]:offs[2]] *= 3.0                                 # problems 1 and 3 start badly
+    g0[offs[3]:offs[4]] = 1.0
+    g, _, it, st = S.solve(g0.clone(), fallback=(fb, chi_fb), tol=1e-7, max_iter=30, use_graph=False)
+    assert st.n_fallback == 2
+    ref, _, it_ref, _ = S.solve(fb.clone(), tol=1e-7, max_iter=30, use_graph=False)
+    for i in (1, 3):
+        assert torch.allclose(g[offs[i]:offs[i + 1]], ref[offs[i]:offs[i + 1]], atol=1e-6)
+        assert int(it[i]) == int(it_ref[i])
+    # the graph-replayed launch makes the same decisions
+    g2, _, _, st2 = S.solve(g0.clone(), fallback=(fb, chi_fb), tol=1e-7, max_iter=30, use_graph=True)
+    assert st2.n_fallback == 2 and torch.allclose(g2, g, atol=1e-6)
+    S.close()

@@ -74,7 +74,7 @@ def test_plain_small_workload_matches_oracle():
     assert st.vis_iters > 0 and st.acc_launches >= 1
 
 
-@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("kernel", [1, 2, 3])
 @pytest.mark.parametrize("order", [0, 1])
 @pytest.mark.parametrize("use_graph", [True, False])
 def test_plain_small_tile_orders_and_graph_agree(order, use_graph, kernel):
@@ -142,7 +142,7 @@ CHAINS = [("diag",), ("full",), ("phase",), ("full", "diag"), ("diag", "full"), 
 
 @pytest.mark.parametrize("kinds", CHAINS)
 @pytest.mark.parametrize("order", [0, 1])
-@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("kernel", [1, 2, 3])
 def test_single_step_matches_oracle_for_every_chain_position(kinds, order, kernel):
     obs = random_chain_obs(7, kinds)
     rng = np.random.default_rng(3)
@@ -192,7 +192,7 @@ def test_residual_matches_oracle_elementwise(kinds):
 # converged multi-term chains
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("kernel", [1, 2, 3])
 def test_two_term_chain_matches_oracle(kernel):
     obs = synth.plain_large(seed=3, n_ant=10, n_time=12, n_chan=40, noise=0.05, flag_row_frac=0.1, n_src=8)
     ot, _, ochi2 = run_oracle(obs, n_epochs=3)
@@ -221,14 +221,15 @@ def test_single_term_kinds_converge_like_oracle(kind):
 # edge cases
 # ---------------------------------------------------------------------------
 
-def test_flagged_nan_data_and_dead_antenna():
+@pytest.mark.parametrize("kernel", [0, 3])
+def test_flagged_nan_data_and_dead_antenna(kernel):
     obs = synth.plain_small(seed=4, noise=0.01, n_time=16, n_chan=16)
     dead = (obs.ant1 == 3) | (obs.ant2 == 3)
     obs.flag[dead] = 1
     obs.flag[::5, 3] = 1
     obs.data[obs.flag.astype(bool)] = np.nan
     ot, _, ochi2 = run_oracle(obs)
-    gt, _, gchi2 = run_gpu(obs)
+    gt, _, gchi2 = run_gpu(obs, kernel=kernel)
     assert np.all(gt[0].gain_flags[:, :, 3] == 1)
     assert np.all(np.asarray(gt[0].gains)[:, :, 3, [0, 3]] == 1)
     assert np.array_equal(gt[0].gain_flags, ot[0].gain_flags)
@@ -239,9 +240,10 @@ def test_flagged_nan_data_and_dead_antenna():
     assert np.isfinite(gchi2) and abs(gchi2 - ochi2) <= CHI2_TOL * ochi2
 
 
-def test_autocorrelations_are_ignored():
+@pytest.mark.parametrize("kernel", [0, 3])
+def test_autocorrelations_are_ignored(kernel):
     obs = synth.plain_small(seed=5, noise=0.01, n_time=8, n_chan=8)
-    base = run_gpu(obs)[0][0].gains.copy()
+    base = run_gpu(obs, kernel=kernel)[0][0].gains.copy()
     n_t = obs.n_time
     auto_rows = np.arange(obs.n_ant)
     ant = np.concatenate([obs.ant1, np.tile(auto_rows, n_t)])
@@ -252,14 +254,15 @@ def test_autocorrelations_are_ignored():
                              np.concatenate([obs.model, extra]), np.ones((ant.size, obs.n_chan, 4)),
                              np.zeros((ant.size, obs.n_chan), np.uint8), ant.astype(np.int32),
                              ant2.astype(np.int32), tt, obs.freqs, obs.terms, {})
-    got = run_gpu(obs2)[0][0].gains
+    got = run_gpu(obs2, kernel=kernel)[0][0].gains
     assert np.allclose(got, base, rtol=1e-5, atol=1e-6)
 
 
-def test_empty_problem_and_fully_flagged():
+@pytest.mark.parametrize("kernel", [0, 3])
+def test_empty_problem_and_fully_flagged(kernel):
     obs = synth.plain_small(seed=6, noise=0.01, n_time=4, n_chan=4)
     obs.flag[:] = 1
-    gt, st, chi2 = run_gpu(obs)
+    gt, st, chi2 = run_gpu(obs, kernel=kernel)
     assert chi2 == 0.0
     assert np.all(gt[0].gain_flags == 1)
     assert np.all(gt[0].iters == 1)
@@ -267,7 +270,7 @@ def test_empty_problem_and_fully_flagged():
                   np.zeros((0, 4, 4), np.float32), None, np.zeros(0, np.int32), np.zeros(0, np.int32),
                   np.zeros(0, np.int32), 3, 1)
     t = qc.Term("diag", np.zeros(1, np.int32), np.zeros(4, np.int32), 1, 1, 3)
-    S.solve([t])
+    S.solve([t], kernel=kernel)
     assert np.all(t.gain_flags == 1)
     assert S.residual([t]) == 0.0
     S.close()

@@ -62,7 +62,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel", type=int, default=0, help="accumulate kernel: 0 auto, 1 pipelined, 2 plain")
+    ap.add_argument("--kernel", type=int, default=0,
+                    help="accumulate kernel: 0 auto (streaming), 1 bulk-copy pipeline, 2 prefetching, 3 streaming")
     return ap.parse_args()
 
 
@@ -78,9 +79,13 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+ACC_KERNEL_NAME = {0: "acc_stream_kernel", 1: "acc_pipe_kernel", 2: "acc_kernel", 3: "acc_stream_kernel"}
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for name in ("qc_kernels.cuh", "qc_jones.cuh", "qc_async.cuh", "qc_acc_inst.cuh", "qc_acc_diag.cu", "qc_acc_full.cu"):
+    for name in ("qc_kernels.cuh", "qc_stream.cuh", "qc_jones.cuh", "qc_async.cuh", "qc_acc_inst.cuh", "qc_acc_diag.cu",
+                 "qc_acc_full.cu"):
         with open(os.path.join(ROOT, "paper_2412_10072_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -339,7 +344,7 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
                 "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured"
-                else "fallback 6.8 TB/s", "kernel": "acc_kernel (JHJ/JHr accumulate)",
+                else "fallback 6.8 TB/s", "kernel": ACC_KERNEL_NAME.get(args.kernel, "acc_kernel") + " (JHJ/JHr accumulate)",
                 "algorithmic_bytes_per_launch": acc_bytes / max(1, acc_launches),
                 "algorithmic_bytes_per_full_launch": algo_full,
                 "launch_ms_mean": acc_ms / max(1, acc_launches), "acc_share_of_step": acc_ms / ms if ms else None}

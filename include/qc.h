@@ -138,11 +138,11 @@ typedef struct {
     int32_t order;             /* -1 auto, 0 row-major tiles, 1 baseline-strip tiles */
     int32_t block_threads;     /* threads per CTA of the accumulate kernel (0: auto) */
     int32_t ctas_per_sm;       /* resident CTAs per SM for its grid (0: auto)        */
-    int32_t kernel;            /* accumulate kernel: 0 auto (1 for strip tiles, 2 for row
-                                  tiles), 1 bulk-copy pipeline with per-warp rings (chains
-                                  of <= 2 terms), 2 per-lane cp.async prefetching kernel,
-                                  3 streaming kernel (step-major row table, folded flags;
-                                  chains of <= 2 terms) */
+    int32_t kernel;            /* accumulate kernel: 0 auto (3 for chains of <= 2 terms,
+                                  2 otherwise), 1 bulk-copy pipeline with per-warp rings
+                                  (chains of <= 2 terms), 2 per-lane cp.async prefetching
+                                  kernel, 3 streaming kernel (step-major row table, flags
+                                  folded into weights; chains of <= 2 terms) */
     qc_allreduce_fn allreduce; /* required when a solved term has reduce = 1       */
     void *allreduce_user;
 } qc_opts;

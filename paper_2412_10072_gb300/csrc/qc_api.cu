@@ -716,9 +716,9 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
     PipeArgs pa;
     memset(&pa, 0, sizeof pa);
     int pipe_smem = 0;
-    // kernel 3: the streaming kernel; auto: the bulk-copy pipeline for baseline-strip tiles,
-    // the prefetching kernel for row tiles
-    const bool streaming = L.stream_fn != nullptr && o->kernel == 3;
+    // auto and kernel 3: the streaming kernel (chains of one or two terms; antenna pairs are
+    // packed as p | q << 16); kernels 1 and 2 on request, and for longer chains
+    const bool streaming = L.stream_fn != nullptr && n_ant < 32768 && (o->kernel == 3 || o->kernel == 0);
     bool pipelined = !streaming && L.pipe_fn != nullptr && (o->kernel == 1 || (o->kernel == 0 && order == 1));
     const bool has_o = n_terms == 2;
     if (pipelined) {

@@ -124,6 +124,114 @@ __host__ __device__ constexpr size_t batch_ring_bytes_per_warp()
     return (size_t)DEPTH * 32 * (BatchRing<M16>::V4 * 16 + 8);
 }
 
+// Streams warp `warp`'s contiguous share of a problem's samples, 32 per step (sample
+// index s = row * n_chan + chan, so each 16-byte word of a step is one contiguous
+// 512-byte span whatever n_chan is), through its ring of DEPTH cp.async stages, and
+// calls f(slot, key, scale_bits) once per step with the lane's sample in shared
+// memory: d in slot[0], slot[32]; m in slot[64] (and slot[96]); w in slot[96 or 128].
+// A lane with nothing to read (flagged sample, autocorrelation) sees zeros; key is
+// p | q << 16 of the sample's row, -1 past the end of the problem.  The antennas and
+// flags of a step are loaded two steps before its copies are issued.
+template <bool M16, int DEPTH, typename F>
+__device__ __forceinline__ void stream_pass(const BatchArgs &a, const BProb &P, float4 *ring, int2 *meta, int lane,
+                                            int warp, int n_warps, F &&f)
+{
+    constexpr int V4 = BatchRing<M16>::V4;
+    const int nc = P.n_chan;
+    const long n_samp = (long)P.n_rows * nc;
+    const long n_steps = (n_samp + 31) >> 5;
+    const long per_warp = (n_steps + n_warps - 1) / n_warps;
+    const long st_begin = (long)warp * per_warp, st_end = st_begin + per_warp < n_steps ? st_begin + per_warp : n_steps;
+    const int q32 = 32 / nc, r32 = 32 % nc;              // advance of (row, chan) per step
+    const float4 *vis = a.vis + 2 * P.vis_off;
+    const float4 *mod = M16 ? nullptr : a.model + 2 * P.vis_off;
+    const uint4 *mod16 = M16 ? a.model16 + P.vis_off : nullptr;
+    const float4 *wgt = a.weight + P.vis_off;
+    const uint8_t *flg = a.flag ? a.flag + P.vis_off : nullptr;
+    const int2 *ants = a.ants + P.row_off;
+    const float *rsc = M16 ? a.row_scale + P.row_off : nullptr;
+    // issue cursor: the step whose copies are issued next
+    long is = st_begin;
+    int r2, c2;                     // the lane's (row, chan) in step is + 1
+    {
+        const long s0 = st_begin * 32 + lane;
+        r2 = (int)(s0 / nc);
+        c2 = (int)(s0 - (long)r2 * nc);
+    }
+    auto load_meta = [&](long step, int row, int2 &pq, int &use, float &sc) {
+        const long s = step * 32 + lane;
+        const bool in = step < st_end && s < n_samp;
+        pq = in ? __ldg(ants + row) : make_int2(-1, -1);
+        use = in && pq.x != pq.y && !(flg && __ldg(flg + s)) ? 1 : 0;
+        sc = M16 && in ? __ldg(rsc + row) : 0.f;
+    };
+    auto advance = [&](int &row, int &c) {
+        c += r32;
+        row += q32;
+        if (c >= nc) { c -= nc; ++row; }
+    };
+    int2 m1pq, m2pq;
+    int m1use, m2use;
+    float m1sc, m2sc;
+    load_meta(is, r2, m1pq, m1use, m1sc);
+    advance(r2, c2);
+    load_meta(is + 1, r2, m2pq, m2use, m2sc);
+    int stage_i = 0;
+    auto issue = [&]() {
+        const long s = is * 32 + lane;
+        const uint32_t nb = m1use ? 16u : 0u;
+        const long so = m1use ? s : 0;
+        float4 *slot = ring + (size_t)stage_i * V4 * 32 + lane;
+        cp_async16(slot, vis + 2 * so, nb);
+        cp_async16(slot + 32, vis + 2 * so + 1, nb);
+        if constexpr (M16) {
+            cp_async16(slot + 64, mod16 + so, nb);
+            cp_async16(slot + 96, wgt + so, nb);
+        } else {
+            cp_async16(slot + 64, mod + 2 * so, nb);
+            cp_async16(slot + 96, mod + 2 * so + 1, nb);
+            cp_async16(slot + 128, wgt + so, nb);
+        }
+        cp_async_commit();
+        int2 key;
+        key.x = m1pq.x >= 0 ? (m1pq.x | (m1pq.y << 16)) : -1;
+        key.y = __float_as_int(m1sc);
+        meta[stage_i * 32 + lane] = key;
+        if (++stage_i == DEPTH) stage_i = 0;
+        // shift the metadata pipeline by one step
+        ++is;
+        m1pq = m2pq;
+        m1use = m2use;
+        m1sc = m2sc;
+        advance(r2, c2);
+        load_meta(is + 1, r2, m2pq, m2use, m2sc);
+    };
+#pragma unroll
+    for (int d = 0; d < DEPTH - 1; ++d) issue();
+    int stage_c = 0;
+    for (long t = st_begin; t < st_end; ++t) {
+        cp_async_wait<DEPTH - 2>();
+        const int2 key = meta[stage_c * 32 + lane];
+        f(ring + (size_t)stage_c * V4 * 32 + lane, key.x, key.y);
+        if (++stage_c == DEPTH) stage_c = 0;
+        issue();
+    }
+    cp_async_wait<0>();
+}
+
+__device__ __forceinline__ J2 ring_model16(const float4 *slot, int scale_bits)
+{
+    const float4 hw = slot[64];
+    const uint4 h = *reinterpret_cast<const uint4 *>(&hw);
+    const float sc = __int_as_float(scale_bits);
+    J2 M;
+    M.a = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.x)), sc);
+    M.b = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.y)), sc);
+    M.c = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.z)), sc);
+    M.d = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.w)), sc);
+    return M;
+}
+
 // One warp step covers 32 consecutive samples of the problem (sample index
 // s = row * n_chan + chan, so each 16-byte word of a step is one contiguous
 // 512-byte span whatever n_chan is).  Warps own contiguous ranges of steps.
@@ -164,17 +272,6 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchArgs a)
             g64[2 * i + 1] = make_double2(g1.x, g1.y);
         }
         const long n_samp = (long)P.n_rows * nc;
-        const long n_steps = (n_samp + 31) >> 5;
-        const long per_warp = (n_steps + n_warps - 1) / n_warps;
-        const long st_begin = (long)warp * per_warp, st_end = st_begin + per_warp < n_steps ? st_begin + per_warp : n_steps;
-        const int q32 = 32 / nc, r32 = 32 % nc;              // advance of (row, chan) per step
-        const float4 *vis = a.vis + 2 * P.vis_off;
-        const float4 *mod = M16 ? nullptr : a.model + 2 * P.vis_off;
-        const uint4 *mod16 = M16 ? a.model16 + P.vis_off : nullptr;
-        const float4 *wgt = a.weight + P.vis_off;
-        const uint8_t *flg = a.flag ? a.flag + P.vis_off : nullptr;
-        const int2 *ants = a.ants + P.row_off;
-        const float *rsc = M16 ? a.row_scale + P.row_off : nullptr;
         int k;
         bool fell_back = false;
         const bool check = a.fb_gains != nullptr;
@@ -185,94 +282,20 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchArgs a)
             // the first pass also sums chi^2 at the starting gains (fallback check)
             const bool want_chi = check && k == 1 && !fell_back;
             float chi = 0.f;
-            // issue cursor: the step whose copies are issued next, and the lane's (row, chan) in it
-            long is = st_begin;
-            int irow, ic;
-            {
-                const long s0 = st_begin * 32 + lane;
-                irow = (int)(s0 / nc);
-                ic = (int)(s0 - (long)irow * nc);
-            }
-            // metadata of the next two steps to issue (antennas, usable flag), loaded ahead
-            auto load_meta = [&](long step, int row, int2 &pq, int &use, float &sc) {
-                const long s = step * 32 + lane;
-                const bool in = step < st_end && s < n_samp;
-                pq = in ? __ldg(ants + row) : make_int2(-1, -1);
-                use = in && pq.x != pq.y && !(flg && __ldg(flg + s)) ? 1 : 0;
-                sc = M16 && in ? __ldg(rsc + row) : 0.f;
-            };
-            auto advance = [&](int &row, int &c) {
-                c += r32;
-                row += q32;
-                if (c >= nc) { c -= nc; ++row; }
-            };
-            int2 m1pq, m2pq;
-            int m1use, m2use;
-            float m1sc, m2sc;
-            int r2 = irow, c2 = ic;
-            load_meta(is, irow, m1pq, m1use, m1sc);
-            advance(r2, c2);
-            load_meta(is + 1, r2, m2pq, m2use, m2sc);
-            int stage_i = 0;
-            auto issue = [&]() {
-                const long s = is * 32 + lane;
-                const uint32_t nb = m1use ? 16u : 0u;
-                const long so = m1use ? s : 0;
-                float4 *slot = ring + (size_t)stage_i * V4 * 32 + lane;
-                cp_async16(slot, vis + 2 * so, nb);
-                cp_async16(slot + 32, vis + 2 * so + 1, nb);
-                if constexpr (M16) {
-                    cp_async16(slot + 64, mod16 + so, nb);
-                    cp_async16(slot + 96, wgt + so, nb);
-                } else {
-                    cp_async16(slot + 64, mod + 2 * so, nb);
-                    cp_async16(slot + 96, mod + 2 * so + 1, nb);
-                    cp_async16(slot + 128, wgt + so, nb);
-                }
-                cp_async_commit();
-                int2 key;
-                key.x = m1pq.x >= 0 ? (m1pq.x | (m1pq.y << 16)) : -1;
-                key.y = __float_as_int(m1sc);
-                meta[stage_i * 32 + lane] = key;
-                if (++stage_i == DEPTH) stage_i = 0;
-                // shift the metadata pipeline by one step
-                ++is;
-                m1pq = m2pq;
-                m1use = m2use;
-                m1sc = m2sc;
-                advance(r2, c2);
-                load_meta(is + 1, r2, m2pq, m2use, m2sc);
-            };
-#pragma unroll
-            for (int d = 0; d < DEPTH - 1; ++d) issue();
-
             float sp[6], sq[6];
 #pragma unroll
             for (int i = 0; i < 6; ++i) sp[i] = sq[i] = 0.f;
             int kp = -1, kq = -1;
-            int stage_c = 0;
-            for (long t = st_begin; t < st_end; ++t) {
-                cp_async_wait<DEPTH - 2>();
-                const float4 *slot = ring + (size_t)stage_c * V4 * 32 + lane;
-                const int2 key = meta[stage_c * 32 + lane];
-                const int np = key.x >= 0 ? (key.x & 0xffff) : -1;
-                const int nq = key.x >= 0 ? (key.x >> 16) : -1;
+            stream_pass<M16, DEPTH>(a, P, ring, meta, lane, warp, n_warps, [&](const float4 *slot, int kx, int ky) {
+                const int np = kx >= 0 ? (kx & 0xffff) : -1;
+                const int nq = kx >= 0 ? (kx >> 16) : -1;
                 if (__any_sync(0xffffffffu, np != kp)) { flush_runs(sp, kp, lane, acc); kp = np; }
                 if (__any_sync(0xffffffffu, nq != kq)) { flush_runs(sq, kq, lane, acc); kq = nq; }
-                if (key.x >= 0) {
+                if (kx >= 0) {
                     const J2 D = j_from(slot[0], slot[32]);
                     J2 M;
-                    if constexpr (M16) {
-                        const float4 hw = slot[64];
-                        const uint4 h = *reinterpret_cast<const uint4 *>(&hw);
-                        const float sc = __int_as_float(key.y);
-                        M.a = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.x)), sc);
-                        M.b = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.y)), sc);
-                        M.c = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.z)), sc);
-                        M.d = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.w)), sc);
-                    } else {
-                        M = j_from(slot[64], slot[96]);
-                    }
+                    if constexpr (M16) M = ring_model16(slot, ky);
+                    else M = j_from(slot[64], slot[96]);
                     const float4 w = slot[M16 ? 96 : 128];
                     const float4 Gp = g32[np], Gq = g32[nq];
                     const float2 gp0 = make_float2(Gp.x, Gp.y), gp1 = make_float2(Gp.z, Gp.w);
@@ -301,10 +324,7 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchArgs a)
                     float2 k1 = cfma_conj(Y11, cconj(wr11), cfma_conj(Y10, cconj(wr01), make_float2(sq[4], sq[5])));
                     sq[2] = k0.x; sq[3] = k0.y; sq[4] = k1.x; sq[5] = k1.y;
                 }
-                if (++stage_c == DEPTH) stage_c = 0;
-                issue();
-            }
-            cp_async_wait<0>();
+            });
             flush_runs(sp, kp, lane, acc);
             flush_runs(sq, kq, lane, acc);
             if (want_chi) {
@@ -431,21 +451,48 @@ __global__ void __launch_bounds__(256) batch_chi2_kernel(const BatchArgs a, doub
 }
 
 
+// Segmented flush of N register sums per lane (keys as in flush_runs) into acc[key][N].
+template <int N>
+__device__ __forceinline__ void flush_runs_n(float (&s)[N], int key, int lane, float *acc)
+{
+    const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+    const bool head = lane == 0 || key != prev;
+    const unsigned heads = __ballot_sync(0xffffffffu, head);
+    const unsigned after = heads & ~((2u << lane) - 1u);
+    const unsigned run_end = after ? (unsigned)(__ffs(after) - 1) : 32u;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const float sum = run_sum(s[i], lane, run_end);
+        if (head && key >= 0) atomicAdd(acc + key * N + i, sum);
+        s[i] = 0.f;
+    }
+}
+
+constexpr int FEAT_DEPTH = 4;     // ring stages of the features pass
+
 // Per-antenna warm-start features of every problem (one CTA per problem, one data
-// pass at unit gains): JHJ diagonal and JHr at g = 1 (both baseline orientations),
-// sums of |d_kk| / |m_kk| and their counts; then the 10 features per antenna.
+// pass at unit gains through the solver's streaming skeleton): JHJ diagonal and JHr
+// at g = 1 (both baseline orientations), sums of |d_kk| / |m_kk| and their counts,
+// and (optionally) chi^2 at the previous-interval gains; then the 10 features per
+// antenna.
+template <bool M16>
 __global__ void __launch_bounds__(256) batch_features_kernel(const BatchArgs a, const float2 *prev, float *feat,
                                                              double *chi2_prev)
 {
+    constexpr int DEPTH = FEAT_DEPTH, V4 = BatchRing<M16>::V4;
     extern __shared__ __align__(16) unsigned char smem[];
-    float4 *gprev = reinterpret_cast<float4 *>(smem);      // [max_ant] previous gains (g_XX, g_YY)
-    float *acc = reinterpret_cast<float *>(gprev + a.max_ant);   // [max_ant][9]: h0 h1 jr0 ji0 jr1 ji1 s0 s1 cnt
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, n_warps = blockDim.x >> 5;
+    float4 *ring = reinterpret_cast<float4 *>(smem) + (size_t)warp * DEPTH * V4 * 32;
+    int2 *meta = reinterpret_cast<int2 *>(reinterpret_cast<float4 *>(smem) + (size_t)n_warps * DEPTH * V4 * 32) +
+                 (size_t)warp * DEPTH * 32;
+    unsigned char *tail = smem + (size_t)n_warps * batch_ring_bytes_per_warp<M16, DEPTH>();
+    float4 *gprev = reinterpret_cast<float4 *>(tail);                  // [max_ant] previous gains (g_XX, g_YY)
+    float *acc = reinterpret_cast<float *>(gprev + a.max_ant);        // [max_ant][9]: h0 h1 jr0 ji0 jr1 ji1 s0 s1 cnt
     __shared__ float2 ref[2];
     __shared__ double s_chi;
     const int pi = blockIdx.x;
     const BProb P = a.probs[pi];
-    const int na = P.n_ant, nc = P.n_chan, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int n_warps = blockDim.x >> 5;
+    const int na = P.n_ant;
     const bool want_chi = chi2_prev != nullptr && prev != nullptr;
     for (int i = tid; i < na * 9; i += blockDim.x) acc[i] = 0.f;
     for (int i = tid; i < na; i += blockDim.x) {
@@ -456,88 +503,52 @@ __global__ void __launch_bounds__(256) batch_features_kernel(const BatchArgs a, 
     if (tid == 0) s_chi = 0.0;
     __syncthreads();
     float chi = 0.f;
-    const bool wide = nc >= 32;
-    const int rpi = wide ? 1 : 32 / nc;
-    const int chunks = wide ? (nc + 31) / 32 : 1;
-    const int lr = wide ? 0 : lane / nc, lc = wide ? lane : lane % nc;
-    const bool lane_ok = wide || lane < rpi * nc;
-    const long n_steps = wide ? (long)P.n_rows * chunks : ((long)P.n_rows + rpi - 1) / rpi;
-    for (long t = warp; t < n_steps; t += n_warps) {
-        int row, c;
-        if (wide) { row = (int)(t / chunks); c = (int)(t % chunks) * 32 + lane; }
-        else { row = (int)t * rpi + lr; c = lc; }
-        const bool in = lane_ok && row < P.n_rows && c < nc;
-        int p = -1, q = -1;
-        float v[18];
+    float sp[9], sq[9];
 #pragma unroll
-        for (int i = 0; i < 18; ++i) v[i] = 0.f;
-        if (in) {
-            const int2 pq = __ldg(a.ants + P.row_off + row);
-            p = pq.x;
-            q = pq.y;
-            const size_t s = (size_t)P.vis_off + (size_t)row * nc + c;
-            bool ok = p != q;
-            if (ok && a.flag) ok = __ldg(a.flag + s) == 0;
-            if (ok) {
-                const J2 D = j_from(__ldg(a.vis + 2 * s), __ldg(a.vis + 2 * s + 1));
-                J2 M;
-                if (a.model16) {
-                    const uint4 h = __ldg(a.model16 + s);
-                    const float sc = __ldg(a.row_scale + P.row_off + row);
-                    M.a = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.x)), sc);
-                    M.b = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.y)), sc);
-                    M.c = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.z)), sc);
-                    M.d = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.w)), sc);
-                } else {
-                    M = j_from(__ldg(a.model + 2 * s), __ldg(a.model + 2 * s + 1));
-                }
-                const float4 w = __ldg(a.weight + s);
-                // unit gains: X = M, V = M, r = D - M
-                const float2 r00 = csub(D.a, M.a), r01 = csub(D.b, M.b), r10 = csub(D.c, M.c), r11 = csub(D.d, M.d);
-                v[0] = fmaf(w.x, cnorm2(M.a), w.y * cnorm2(M.b));
-                v[1] = fmaf(w.z, cnorm2(M.c), w.w * cnorm2(M.d));
-                float2 j0 = cfma_conj(M.b, cscale(r01, w.y), cfma_conj(M.a, cscale(r00, w.x), make_float2(0.f, 0.f)));
-                float2 j1 = cfma_conj(M.d, cscale(r11, w.w), cfma_conj(M.c, cscale(r10, w.z), make_float2(0.f, 0.f)));
-                v[2] = j0.x; v[3] = j0.y; v[4] = j1.x; v[5] = j1.y;
-                const float ma = sqrtf(cnorm2(M.a)), md = sqrtf(cnorm2(M.d));
-                const bool okr = ma > 0.f && md > 0.f;
-                v[6] = okr ? sqrtf(cnorm2(D.a)) / ma : 0.f;
-                v[7] = okr ? sqrtf(cnorm2(D.d)) / md : 0.f;
-                v[8] = okr ? 1.f : 0.f;
-                // conjugate baseline for antenna q: Y = M^H, r' = r^H, w' = P w
-                v[9] = fmaf(w.x, cnorm2(M.a), w.z * cnorm2(M.c));
-                v[10] = fmaf(w.y, cnorm2(M.b), w.w * cnorm2(M.d));
-                float2 k0 = cfma_conj(cconj(M.c), cscale(cconj(r10), w.z), cfma_conj(cconj(M.a), cscale(cconj(r00), w.x), make_float2(0.f, 0.f)));
-                float2 k1 = cfma_conj(cconj(M.d), cscale(cconj(r11), w.w), cfma_conj(cconj(M.b), cscale(cconj(r01), w.y), make_float2(0.f, 0.f)));
-                v[11] = k0.x; v[12] = k0.y; v[13] = k1.x; v[14] = k1.y;
-                v[15] = v[6]; v[16] = v[7]; v[17] = v[8];
-                if (want_chi) {
-                    // chi^2 at the previous-interval gains (Eq. min), for the fallback check
-                    const float4 Gp = gprev[p], Gq = gprev[q];
-                    const float2 gp0 = make_float2(Gp.x, Gp.y), gp1 = make_float2(Gp.z, Gp.w);
-                    const float2 gq0 = make_float2(Gq.x, Gq.y), gq1 = make_float2(Gq.z, Gq.w);
-                    const float2 e00 = csub(D.a, cmul(gp0, cmulc(M.a, gq0))), e01 = csub(D.b, cmul(gp0, cmulc(M.b, gq1)));
-                    const float2 e10 = csub(D.c, cmul(gp1, cmulc(M.c, gq0))), e11 = csub(D.d, cmul(gp1, cmulc(M.d, gq1)));
-                    chi += fmaf(w.x, cnorm2(e00), fmaf(w.y, cnorm2(e01), fmaf(w.z, cnorm2(e10), w.w * cnorm2(e11))));
-                }
-            }
+    for (int i = 0; i < 9; ++i) sp[i] = sq[i] = 0.f;
+    int kp = -1, kq = -1;
+    stream_pass<M16, DEPTH>(a, P, ring, meta, lane, warp, n_warps, [&](const float4 *slot, int kx, int ky) {
+        const int p = kx >= 0 ? (kx & 0xffff) : -1;
+        const int q = kx >= 0 ? (kx >> 16) : -1;
+        if (__any_sync(0xffffffffu, p != kp)) { flush_runs_n<9>(sp, kp, lane, acc); kp = p; }
+        if (__any_sync(0xffffffffu, q != kq)) { flush_runs_n<9>(sq, kq, lane, acc); kq = q; }
+        if (kx < 0) return;
+        // flagged samples and autocorrelations arrive as zeros: no contribution below
+        const J2 D = j_from(slot[0], slot[32]);
+        J2 M;
+        if constexpr (M16) M = ring_model16(slot, ky);
+        else M = j_from(slot[64], slot[96]);
+        const float4 w = slot[M16 ? 96 : 128];
+        // unit gains: X = M, V = M, r = D - M
+        const float2 r00 = csub(D.a, M.a), r01 = csub(D.b, M.b), r10 = csub(D.c, M.c), r11 = csub(D.d, M.d);
+        sp[0] += fmaf(w.x, cnorm2(M.a), w.y * cnorm2(M.b));
+        sp[1] += fmaf(w.z, cnorm2(M.c), w.w * cnorm2(M.d));
+        float2 j0 = cfma_conj(M.b, cscale(r01, w.y), cfma_conj(M.a, cscale(r00, w.x), make_float2(sp[2], sp[3])));
+        float2 j1 = cfma_conj(M.d, cscale(r11, w.w), cfma_conj(M.c, cscale(r10, w.z), make_float2(sp[4], sp[5])));
+        sp[2] = j0.x; sp[3] = j0.y; sp[4] = j1.x; sp[5] = j1.y;
+        const float ma = sqrtf(cnorm2(M.a)), md = sqrtf(cnorm2(M.d));
+        const bool okr = ma > 0.f && md > 0.f;
+        const float ra = okr ? sqrtf(cnorm2(D.a)) / ma : 0.f, rd = okr ? sqrtf(cnorm2(D.d)) / md : 0.f;
+        sp[6] += ra; sp[7] += rd; sp[8] += okr ? 1.f : 0.f;
+        // conjugate baseline for antenna q: Y = M^H, r' = r^H, w' = P w
+        sq[0] += fmaf(w.x, cnorm2(M.a), w.z * cnorm2(M.c));
+        sq[1] += fmaf(w.y, cnorm2(M.b), w.w * cnorm2(M.d));
+        float2 k0 = cfma_conj(cconj(M.c), cscale(cconj(r10), w.z), cfma_conj(cconj(M.a), cscale(cconj(r00), w.x), make_float2(sq[2], sq[3])));
+        float2 k1 = cfma_conj(cconj(M.d), cscale(cconj(r11), w.w), cfma_conj(cconj(M.b), cscale(cconj(r01), w.y), make_float2(sq[4], sq[5])));
+        sq[2] = k0.x; sq[3] = k0.y; sq[4] = k1.x; sq[5] = k1.y;
+        sq[6] += ra; sq[7] += rd; sq[8] += okr ? 1.f : 0.f;
+        if (want_chi) {
+            // chi^2 at the previous-interval gains (Eq. min), for the fallback check
+            const float4 Gp = gprev[p], Gq = gprev[q];
+            const float2 gp0 = make_float2(Gp.x, Gp.y), gp1 = make_float2(Gp.z, Gp.w);
+            const float2 gq0 = make_float2(Gq.x, Gq.y), gq1 = make_float2(Gq.z, Gq.w);
+            const float2 e00 = csub(D.a, cmul(gp0, cmulc(M.a, gq0))), e01 = csub(D.b, cmul(gp0, cmulc(M.b, gq1)));
+            const float2 e10 = csub(D.c, cmul(gp1, cmulc(M.c, gq0))), e11 = csub(D.d, cmul(gp1, cmulc(M.d, gq1)));
+            chi += fmaf(w.x, cnorm2(e00), fmaf(w.y, cnorm2(e01), fmaf(w.z, cnorm2(e10), w.w * cnorm2(e11))));
         }
-        const int kp = in ? p : -1, kq = in ? q : -1;
-#pragma unroll
-        for (int side = 0; side < 2; ++side) {
-            const int key = side == 0 ? kp : kq;
-            const int prevk = __shfl_up_sync(0xffffffffu, key, 1);
-            const bool head = lane == 0 || key != prevk;
-            const unsigned heads = __ballot_sync(0xffffffffu, head);
-            const unsigned after = heads & ~((2u << lane) - 1u);
-            const unsigned run_end = after ? (unsigned)(__ffs(after) - 1) : 32u;
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                const float sum = run_sum(v[side * 9 + i], lane, run_end);
-                if (head && key >= 0) atomicAdd(acc + key * 9 + i, sum);
-            }
-        }
-    }
+    });
+    flush_runs_n<9>(sp, kp, lane, acc);
+    flush_runs_n<9>(sq, kq, lane, acc);
     if (want_chi) {
         double c = chi;
         for (int d = 16; d > 0; d >>= 1) c += __shfl_down_sync(0xffffffffu, c, d);
@@ -1260,8 +1271,13 @@ extern "C" int qc_batch_features(qc_batch *b, const void *prev_gains, float *fea
         }
     }
     BatchArgs a = batch_args(b);
-    const size_t smem = (size_t)b->max_ant * (sizeof(float4) + 9 * sizeof(float));
-    batch_features_kernel<<<b->n_prob, 256, smem, st>>>(a, dprev, dfeat, dchi);
+    const size_t smem = 8 * (b->m16 ? batch_ring_bytes_per_warp<true, FEAT_DEPTH>()
+                                    : batch_ring_bytes_per_warp<false, FEAT_DEPTH>()) +
+                        (size_t)b->max_ant * (sizeof(float4) + 9 * sizeof(float));
+    const void *fn = b->m16 ? (const void *)batch_features_kernel<true> : (const void *)batch_features_kernel<false>;
+    BCK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (b->m16) batch_features_kernel<true><<<b->n_prob, 256, smem, st>>>(a, dprev, dfeat, dchi);
+    else batch_features_kernel<false><<<b->n_prob, 256, smem, st>>>(a, dprev, dfeat, dchi);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && mem == QC_MEM_HOST) e = cudaMemcpyAsync(features, dfeat, fbytes, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess && mem == QC_MEM_HOST && prev_chi2)

@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--block", type=int, default=0, help="threads per CTA of the accumulate kernel (0: auto)")
     ap.add_argument("--kernel", type=int, default=0,
                     help="accumulate kernel: 0 auto (streaming), 1 bulk-copy pipeline, 2 prefetching, 3 streaming")
     return ap.parse_args()
@@ -94,7 +95,7 @@ def kernel_source_hash() -> str:
 def profiled_traffic():
     """DRAM bytes per full accumulate launch from the committed ncu summary, if it was taken on
     the current kernel source (its hash is recorded next to the figure); else None."""
-    path = os.path.join(ROOT, "profiles", "acc_kernel_plain_large.md")
+    path = os.path.join(ROOT, "profiles", "acc_stream_kernel_plain_large.md")
     try:
         text = open(path).read()
     except OSError:
@@ -302,7 +303,8 @@ def main():
 
     def step():
         terms = make_terms(qc, setup, setup.n_ant, args.max_iter)
-        return solver.solve(terms, n_epochs=args.epochs, stream=stream, kernel=args.kernel), terms
+        return solver.solve(terms, n_epochs=args.epochs, stream=stream, kernel=args.kernel,
+                            block_threads=args.block), terms
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -371,7 +373,7 @@ def main():
             s = qc.Solver(host["data"], host["model"], host["weight"], host["flag"], setup.ant1, setup.ant2,
                           setup.time_idx, setup.n_ant, setup.n_time, model_fp16=args.mixed)
             terms = make_terms(qc, setup, setup.n_ant, args.max_iter)
-            st = s.solve(terms, n_epochs=args.epochs, kernel=args.kernel)
+            st = s.solve(terms, n_epochs=args.epochs, kernel=args.kernel, block_threads=args.block)
             s.close()
             d2h = sum(t.gains.nbytes + t.gain_flags.nbytes + t.iters.nbytes for t in terms)
             return st.vis_iters, d2h

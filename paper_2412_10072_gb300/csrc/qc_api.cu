@@ -694,9 +694,11 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
     const int lk = kind_of_range(terms, 0, n);
     const int rk = kind_of_range(terms, n + 1, n_terms);
     const int order = pick_order(t, o);
-    // the prefetching kernel is compiled for at most 256 threads per CTA
-    const int block = (o->block_threads >= 32 && o->block_threads <= 256 && o->block_threads % 32 == 0)
-                          ? o->block_threads : 256;
+    // the prefetching and streaming kernels are compiled for at most 256 threads per CTA
+    // (the streaming kernel for two such CTAs per SM)
+    const bool bt_ok = o->block_threads >= 32 && o->block_threads % 32 == 0;
+    int block = (bt_ok && o->block_threads <= 256) ? o->block_threads : 256;
+    const int block_stream = block;
     AccArgs aa;
     aa.D = data_desc();
     aa.C = chain;
@@ -795,6 +797,7 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
     memset(&sa, 0, sizeof sa);
     int stream_smem = 0;
     if (streaming) {
+        block = block_stream;
         // step-major row table in the tile order, and the channel maps of both terms
         const long n_rt = order == 0 ? (long)n_row : n_strip_rows;
         int rc_;

@@ -64,7 +64,7 @@ template <int K> __device__ __forceinline__ const float4 *tab_ptr(const DevTerm 
 }
 
 template <int TS, int LK, int RK, bool M16, int DEPTH>
-__global__ void __launch_bounds__(256) acc_stream_kernel(const StreamArgs a)
+__global__ void __launch_bounds__(256, 2) acc_stream_kernel(const StreamArgs a)
 {
     if (__ldg(a.n_active) == 0) return;
     constexpr bool HAS_L = LK != KIND_NONE;
@@ -199,33 +199,32 @@ __global__ void __launch_bounds__(256) acc_stream_kernel(const StreamArgs a)
     Ap.zero();
     Aq.zero();
     int stage = 0, cur_key = -1, cur_pq = -1;
-    // channel interval maps of the lane for the current step (fmA) and the next one (fmB);
-    // each is read two steps ahead from the step's entry in the ring
-    auto read_map = [&](int st) {
-        const int4 m0 = meta[2 * st], m1 = meta[2 * st + 1];
+    // ring entries of the current step (A), the next (B) and the one after (C) are carried in
+    // registers, as are the lane's channel interval maps of A and B; each step reads C's entry
+    // from shared memory and its maps from global memory (two steps ahead of their use)
+    auto read_map = [&](const int4 &m0, const int4 &m1) {
         const int c = m1.x + lane;
         return (m0.x != STREAM_END && m0.z >= 0 && c < n_chan) ? __ldg(a.fmap2 + c) : make_int2(0, 0);
     };
-    int2 fmA = read_map(0), fmB = read_map(1);
+    int4 eA0 = meta[0], eA1 = meta[1], eB0 = meta[2], eB1 = meta[3];
+    int2 fmA = read_map(eA0, eA1), fmB = read_map(eB0, eB1);
     for (;;) {
-        const int4 e = meta[2 * stage];
-        const int4 e1 = meta[2 * stage + 1];
+        const int4 e = eA0;
+        const int4 e1 = eA1;
         if (e.x == STREAM_END) break;
         const int2 fm = fmA;
         const int nst = stage + 1 == DEPTH ? 0 : stage + 1;
         const int nst2 = nst + 1 == DEPTH ? 0 : nst + 1;
-        // the step after next: its channel maps; the next step: its gain entries into L1
-        const int2 fmC = read_map(nst2);
-        {
-            const int4 n0 = meta[2 * nst];
-            if (n0.x != STREAM_END && n0.z >= 0) {
-                const int np = n0.y & 0xffff, nq = n0.y >> 16;
-                prefetch_l1(tab_ptr<GK>(a.tn, n_ant, n0.z, fmB.x, np));
-                prefetch_l1(tab_ptr<GK>(a.tn, n_ant, n0.z, fmB.x, nq));
-                if constexpr (HAS_O) {
-                    prefetch_l1(tab_ptr<OK_>(a.to, n_ant, n0.w, fmB.y, np));
-                    prefetch_l1(tab_ptr<OK_>(a.to, n_ant, n0.w, fmB.y, nq));
-                }
+        // the step after next: its entry and channel maps; the next step: its gain entries into L1
+        const int4 eC0 = meta[2 * nst2], eC1 = meta[2 * nst2 + 1];
+        const int2 fmC = read_map(eC0, eC1);
+        if (eB0.x != STREAM_END && eB0.z >= 0) {
+            const int np = eB0.y & 0xffff, nq = eB0.y >> 16;
+            prefetch_l1(tab_ptr<GK>(a.tn, n_ant, eB0.z, fmB.x, np));
+            prefetch_l1(tab_ptr<GK>(a.tn, n_ant, eB0.z, fmB.x, nq));
+            if constexpr (HAS_O) {
+                prefetch_l1(tab_ptr<OK_>(a.to, n_ant, eB0.w, fmB.y, np));
+                prefetch_l1(tab_ptr<OK_>(a.to, n_ant, eB0.w, fmB.y, nq));
             }
         }
         issue();
@@ -274,6 +273,8 @@ __global__ void __launch_bounds__(256) acc_stream_kernel(const StreamArgs a)
         }
         fmA = fmB;
         fmB = fmC;
+        eA0 = eB0; eA1 = eB1;
+        eB0 = eC0; eB1 = eC1;
         stage = nst;
     }
     if (__any_sync(0xffffffffu, cur_key >= 0)) {

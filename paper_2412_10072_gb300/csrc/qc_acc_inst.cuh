@@ -17,6 +17,7 @@ template <bool M16> constexpr int stream_smem_per_warp()
     return STREAM_DEPTH * ((M16 ? 4 : 5) * 32 * 16 + 2 * 16);
 }
 
+
 template <int TS, int LK, int RK, bool SIMPLE, bool M16>
 cudaError_t launch_acc(int grid, int block, cudaStream_t st, const AccArgs &a)
 {

@@ -721,6 +721,8 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
     // auto and kernel 3: the streaming kernel (chains of one or two terms; antenna pairs are
     // packed as p | q << 16); kernels 1 and 2 on request, and for longer chains
     const bool streaming = L.stream_fn != nullptr && n_ant < 32768 && (o->kernel == 3 || o->kernel == 0);
+    const void *stream_fn = L.stream_fn;
+    const int stream_smem_per_warp = L.stream_smem_per_warp;
     bool pipelined = !streaming && L.pipe_fn != nullptr && (o->kernel == 1 || (o->kernel == 0 && order == 1));
     const bool has_o = n_terms == 2;
     if (pipelined) {
@@ -832,18 +834,18 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
         sa.fmap2 = (const int2 *)B.fmap2.ptr;
         sa.acc = (double *)B.acc.ptr;
         sa.active = (const uint8_t *)B.active.ptr;
-        stream_smem = (block / 32) * L.stream_smem_per_warp;
+        stream_smem = (block / 32) * stream_smem_per_warp;
         if (stream_smem > smem_optin) return fail(QC_EUNSUPPORTED, "streaming kernel ring exceeds shared memory");
-        if (!configured(L.stream_fn)) {
-            CK(cudaFuncSetAttribute(L.stream_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin));
-            configured_fns.push_back(L.stream_fn);
+        if (!configured(stream_fn)) {
+            CK(cudaFuncSetAttribute(stream_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin));
+            configured_fns.push_back(stream_fn);
         }
     }
     int grid;
     if (streaming) {
         if (per_sm == 0) {
             int occ = 0;
-            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, L.stream_fn, block, stream_smem);
+            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, stream_fn, block, stream_smem);
             per_sm = (e == cudaSuccess && occ > 0) ? occ : 1;
         }
         const long warps_needed = std::max(1L, (long)sa.n_units);

@@ -63,40 +63,27 @@ template <int K> __device__ __forceinline__ const float4 *tab_ptr(const DevTerm 
     return T.tab + (K == KIND_FULL ? 2 * idx : idx);
 }
 
-template <int TS, int LK, int RK, bool M16, int DEPTH>
-__global__ void __launch_bounds__(256, 2) acc_stream_kernel(const StreamArgs a)
-{
-    if (__ldg(a.n_active) == 0) return;
-    constexpr bool HAS_L = LK != KIND_NONE;
-    constexpr bool HAS_O = LK != KIND_NONE || RK != KIND_NONE;
-    constexpr int OK_ = HAS_L ? LK : RK;                     // kind of the other term
-    constexpr int GK = TS == TS_FULL ? KIND_FULL : KIND_DIAG;
-    constexpr bool KAHAN = M16;
-    using Lay = AccLayout<TS, HAS_L>;
-    constexpr int KR = Lay::KR, KG = Lay::KG;
-    constexpr int V4 = M16 ? 4 : 5;                         // 16-byte words per sample: d (2), m (2 or 1), w (1)
-    static_assert(DEPTH >= 4, "the entries of the next two steps must be in the ring");
-    extern __shared__ float4 s_stream[];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    float4 *ring = s_stream + (size_t)wib * DEPTH * V4 * 32;                          // [DEPTH][V4][32]
-    int4 *meta = reinterpret_cast<int4 *>(s_stream + (size_t)nw * DEPTH * V4 * 32) + (size_t)wib * DEPTH * 2;
-    const long W = ((long)gridDim.x * blockDim.x) >> 5;
-    const int n_chan = a.n_chan, n_ant = a.n_ant, nch = a.n_chunks;
-
-    // ---------------- issue side: the step DEPTH - 1 ahead of the arithmetic ----------------
-    long iu = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;   // unit
-    int ii = 0, ilen = 0;            // step within the unit, steps in the unit
-    int ikb = 0, ic0 = 0;            // strip tiles: first rt entry of the unit, first channel of its chunk
+// Issue side of a warp's stream: walks the warp's units (grid stride W) and their
+// steps, and for each step copies the 32 lanes' d, m, w into a ring stage
+// (16-byte cp.async per lane, zero-filled where there is nothing to read) and
+// writes the step's row-table entry and channel offset beside them (lane 0).
+template <bool M16> struct StreamCursor {
+    static constexpr int V4 = M16 ? 4 : 5;
+    long iu, W;                  // unit, grid stride in units
+    int ii = 0, ilen = 0;        // step within the unit, steps in the unit
+    int ikb = 0, ic0 = 0;        // strip tiles: first rt entry of the unit, first channel of its chunk
     int4 irt = make_int4(0, 0, -1, 0);   // row tiles: the unit's row-table entry
     float isc = 0.f;
-    unsigned imask = 0;              // row tiles: active 32-channel chunks of the row (bit per chunk)
+    unsigned imask = 0;          // row tiles: active 32-channel chunks of the row (bit per chunk)
     int4 blk = make_int4(0, 0, -1, 0);   // strip tiles: entries of the current 32-step block, one per lane
     float blks = 0.f;
     unsigned blkact = 0;
     int blk_base = -1;
 
     // find the next unit with something to read (sets ilen > 0) or run out (iu >= n_units)
-    auto unit_start = [&]() {
+    __device__ __forceinline__ void unit_start(const StreamArgs &a, int lane)
+    {
+        const int nch = a.n_chunks;
         ii = 0;
         ilen = 0;
         while (iu < a.n_units) {
@@ -127,11 +114,18 @@ __global__ void __launch_bounds__(256, 2) acc_stream_kernel(const StreamArgs a)
             }
             iu += W;
         }
-    };
-    unit_start();
+    }
 
-    int stage_i = 0;
-    auto issue = [&]() {
+    __device__ __forceinline__ void start(const StreamArgs &a, int lane, long first_unit, long stride)
+    {
+        iu = first_unit;
+        W = stride;
+        unit_start(a, lane);
+    }
+
+    // copy the next step into ring stage `stage` (one commit group) and advance
+    __device__ __forceinline__ void issue(const StreamArgs &a, int lane, float4 *ring, int4 *meta, int stage)
+    {
         int4 e = make_int4(STREAM_END, 0, -1, 0);
         float sc = 0.f;
         int c0 = 0;
@@ -150,7 +144,7 @@ __global__ void __launch_bounds__(256, 2) acc_stream_kernel(const StreamArgs a)
                     const bool in = j < ilen;
                     blk = in ? __ldg(a.rt + ikb + j) : make_int4(0, 0, -1, 0);
                     blks = (M16 && in) ? __ldg(a.rt_scale + ikb + j) : 0.f;
-                    const bool act = in && blk.z >= 0 && __ldg(a.chunk_active + (size_t)blk.z * nch + (ic0 >> 5));
+                    const bool act = in && blk.z >= 0 && __ldg(a.chunk_active + (size_t)blk.z * a.n_chunks + (ic0 >> 5));
                     blkact = __ballot_sync(0xffffffffu, act);
                 }
                 e.x = __shfl_sync(0xffffffffu, blk.x, l);
@@ -164,10 +158,10 @@ __global__ void __launch_bounds__(256, 2) acc_stream_kernel(const StreamArgs a)
             if (!live) e.z = -1;
         }
         const int c = c0 + lane;
-        const bool rd = live && c < n_chan;
-        const size_t s = rd ? (size_t)e.x * n_chan + c : 0;
+        const bool rd = live && c < a.n_chan;
+        const size_t s = rd ? (size_t)e.x * a.n_chan + c : 0;
         const uint32_t nb = rd ? 16u : 0u;
-        float4 *slot = ring + (size_t)stage_i * V4 * 32 + lane;
+        float4 *slot = ring + (size_t)stage * V4 * 32 + lane;
         cp_async16(slot, a.vis + 2 * s, nb);
         cp_async16(slot + 32, a.vis + 2 * s + 1, nb);
         if constexpr (M16) {
@@ -180,14 +174,43 @@ __global__ void __launch_bounds__(256, 2) acc_stream_kernel(const StreamArgs a)
         }
         cp_async_commit();
         if (lane == 0) {
-            meta[2 * stage_i] = e;
-            meta[2 * stage_i + 1] = make_int4(c0, __float_as_int(sc), 0, 0);
+            meta[2 * stage] = e;
+            meta[2 * stage + 1] = make_int4(c0, __float_as_int(sc), 0, 0);
         }
-        if (++stage_i == DEPTH) stage_i = 0;
         if (iu < a.n_units && ++ii == ilen) {
             iu += W;
-            unit_start();
+            unit_start(a, lane);
         }
+    }
+};
+
+template <int TS, int LK, int RK, bool M16, int DEPTH>
+__global__ void __launch_bounds__(256, 2) acc_stream_kernel(const StreamArgs a)
+{
+    if (__ldg(a.n_active) == 0) return;
+    constexpr bool HAS_L = LK != KIND_NONE;
+    constexpr bool HAS_O = LK != KIND_NONE || RK != KIND_NONE;
+    constexpr int OK_ = HAS_L ? LK : RK;                     // kind of the other term
+    constexpr int GK = TS == TS_FULL ? KIND_FULL : KIND_DIAG;
+    constexpr bool KAHAN = M16;
+    using Lay = AccLayout<TS, HAS_L>;
+    constexpr int KR = Lay::KR, KG = Lay::KG;
+    constexpr int V4 = M16 ? 4 : 5;                         // 16-byte words per sample: d (2), m (2 or 1), w (1)
+    static_assert(DEPTH >= 4, "the entries of the next two steps must be in the ring");
+    extern __shared__ float4 s_stream[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    float4 *ring = s_stream + (size_t)wib * DEPTH * V4 * 32;                          // [DEPTH][V4][32]
+    int4 *meta = reinterpret_cast<int4 *>(s_stream + (size_t)nw * DEPTH * V4 * 32) + (size_t)wib * DEPTH * 2;
+    const long W = ((long)gridDim.x * blockDim.x) >> 5;
+    const int n_chan = a.n_chan, n_ant = a.n_ant;
+
+    // ---------------- issue side: the step DEPTH - 1 ahead of the arithmetic ----------------
+    StreamCursor<M16> cur;
+    cur.start(a, lane, ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5, W);
+    int stage_i = 0;
+    auto issue = [&]() {
+        cur.issue(a, lane, ring, meta, stage_i);
+        if (++stage_i == DEPTH) stage_i = 0;
     };
 
 #pragma unroll

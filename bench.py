@@ -224,6 +224,17 @@ def mixed_accuracy(n_ant=16, n_time=8, n_chan=64, epochs=3):
     return out
 
 
+def plain_config(args, world=1):
+    """The plain workload's config block (shared by the reference arm, so that both lines name the
+    same workload)."""
+    n_vis = args.n_ant * (args.n_ant - 1) // 2 * args.n_time * args.n_chan
+    return {"workload": WORKLOAD + (" (FP16 model)" if args.mixed else ""), "n_ant": args.n_ant,
+            "n_time": args.n_time, "n_chan": args.n_chan, "n_vis": n_vis,
+            "input_bytes_per_gpu": n_vis * (64 if args.mixed else 80) + n_vis,
+            "l2": "inputs (25 GB) larger than L2 (129 MB)", "epochs": args.epochs, "max_iter": args.max_iter,
+            "tol": 1e-6, "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"}
+
+
 def run_reference(args):
     """--impl reference: the FP64 oracle as it stands on the host cores, on a bounded sample of the
     same workload (the first 2 times of the 64-antenna, 512-channel observation; 1 epoch, <= 2
@@ -251,7 +262,7 @@ def run_reference(args):
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD + " (oracle sample)", "sample_vis": obs.n_vis},
+            "data": "synthetic", "config": plain_config(args),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
@@ -401,12 +412,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c64+f16" if args.mixed else "c64", "data": "synthetic",
-            "config": {"workload": WORKLOAD + (" (FP16 model)" if args.mixed else ""), "n_ant": args.n_ant,
-                       "n_time": args.n_time, "n_chan": args.n_chan, "n_vis": n_vis,
-                       "input_bytes_per_gpu": input_bytes, "l2": "inputs (25 GB) larger than L2 (129 MB)",
-                       "epochs": args.epochs, "max_iter": args.max_iter, "tol": 1e-6,
-                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
-                       "gen_s": round(t_gen, 2)},
+            "config": plain_config(args, world), "gen_s": round(t_gen, 2),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clock_info,
             **({"accuracy_vs_fp64_oracle": accuracy} if accuracy else {}),
             "gpu_launches": int(launches), "accumulate_launches_with_work": int(acc_launches),

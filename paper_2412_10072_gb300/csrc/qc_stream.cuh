@@ -17,9 +17,10 @@
 //  * d, m, w of each step are copied DEPTH - 1 steps ahead into the warp's ring in
 //    shared memory (16-byte cp.async per lane, zero-filled for lanes with nothing to
 //    read), and lane 0 writes the step's row-table entry beside them;
-//  * the lane's channel interval indices are read two steps ahead and the gain-table
-//    entries of the next step are prefetched into L1, so the gain loads of a step
-//    hit L1.
+//  * the lane's channel interval indices are read two steps ahead; the solved term's
+//    gain entries stay in registers while their table index is unchanged (a row of a
+//    row tile, a strip of a strip tile), and the other term's entries of the next
+//    step are prefetched into L1, so the gain loads of a step hit L1.
 //
 // Work decomposition as in acc_kernel: a unit is a row (row tiles: its 32-channel
 // chunks are the steps) or a baseline strip x 32 channels (strip tiles: its rows
@@ -192,7 +193,11 @@ __global__ void __launch_bounds__(256, 2) acc_stream_kernel(const StreamArgs a)
     constexpr bool HAS_O = LK != KIND_NONE || RK != KIND_NONE;
     constexpr int OK_ = HAS_L ? LK : RK;                     // kind of the other term
     constexpr int GK = TS == TS_FULL ? KIND_FULL : KIND_DIAG;
-    constexpr bool KAHAN = M16;
+    // FP16 model: instead of a compensated add per sample, the lane sums go to the FP64
+    // accumulators at least every FLUSH_EVERY steps, so FP32 rounding is confined to
+    // partial sums of at most FLUSH_EVERY samples per lane and everything beyond is FP64
+    constexpr bool KAHAN = false;
+    constexpr int FLUSH_EVERY = M16 ? 16 : (1 << 30);
     using Lay = AccLayout<TS, HAS_L>;
     constexpr int KR = Lay::KR, KG = Lay::KG;
     constexpr int V4 = M16 ? 4 : 5;                         // 16-byte words per sample: d (2), m (2 or 1), w (1)
@@ -231,6 +236,9 @@ __global__ void __launch_bounds__(256, 2) acc_stream_kernel(const StreamArgs a)
     };
     int4 eA0 = meta[0], eA1 = meta[1], eB0 = meta[2], eB1 = meta[3];
     int2 fmA = read_map(eA0, eA1), fmB = read_map(eB0, eB1);
+    int ci_p = -1, ci_q = -1, act_key = -1, since_flush = 0;
+    bool act_val = false;
+    J2 cGp = j_identity(), cGq = j_identity();
     for (;;) {
         const int4 e = eA0;
         const int4 e1 = eA1;
@@ -243,8 +251,6 @@ __global__ void __launch_bounds__(256, 2) acc_stream_kernel(const StreamArgs a)
         const int2 fmC = read_map(eC0, eC1);
         if (eB0.x != STREAM_END && eB0.z >= 0) {
             const int np = eB0.y & 0xffff, nq = eB0.y >> 16;
-            prefetch_l1(tab_ptr<GK>(a.tn, n_ant, eB0.z, fmB.x, np));
-            prefetch_l1(tab_ptr<GK>(a.tn, n_ant, eB0.z, fmB.x, nq));
             if constexpr (HAS_O) {
                 prefetch_l1(tab_ptr<OK_>(a.to, n_ant, eB0.w, fmB.y, np));
                 prefetch_l1(tab_ptr<OK_>(a.to, n_ant, eB0.w, fmB.y, nq));
@@ -258,8 +264,10 @@ __global__ void __launch_bounds__(256, 2) acc_stream_kernel(const StreamArgs a)
         const bool in = live && c < n_chan;
         const int key = in ? e.z * a.tn.n_fint + fm.x : -1;
         if (live) {
-            const bool change = e.y != cur_pq || key != cur_key;
+            const bool change = e.y != cur_pq || key != cur_key || since_flush >= FLUSH_EVERY;
+            ++since_flush;
             if (__any_sync(0xffffffffu, change && cur_key >= 0)) {
+                since_flush = 1;
                 const unsigned m = __match_any_sync(0xffffffffu, cur_key);
                 const unsigned seg_end = 32 - __clz(m);
                 const bool head = lane == __ffs(m) - 1;
@@ -274,7 +282,21 @@ __global__ void __launch_bounds__(256, 2) acc_stream_kernel(const StreamArgs a)
         const float4 *slot = ring + (size_t)stage * V4 * 32 + lane;
         const float4 w = slot[M16 ? 96 : 128];
         bool ok = in && (w.x != 0.f || w.y != 0.f || w.z != 0.f || w.w != 0.f);
-        if (ok) ok = __ldg(a.active + key) != 0;
+        if (ok && key != act_key) {          // activity of the lane's bin, read when the bin changes
+            act_key = key;
+            act_val = __ldg(a.active + key) != 0;
+        }
+        ok = ok && act_val;
+        {
+            // the solved term's entries stay in registers while the lane's table index is unchanged
+            const int p = e.y & 0xffff, q = e.y >> 16;
+            const int ip = ok ? (e.z * n_ant + p) * a.tn.n_fint + fm.x : ci_p;
+            const int iq = ok ? (e.z * n_ant + q) * a.tn.n_fint + fm.x : ci_q;
+            if (__any_sync(0xffffffffu, ip != ci_p || iq != ci_q)) {
+                if (ip != ci_p) { cGp = fetch_k<GK>(a.tn, n_ant, e.z, fm.x, p); ci_p = ip; }
+                if (iq != ci_q) { cGq = fetch_k<GK>(a.tn, n_ant, e.z, fm.x, q); ci_q = iq; }
+            }
+        }
         if (ok) {
             const int p = e.y & 0xffff, q = e.y >> 16;
             const J2 Dm = j_from(slot[0], slot[32]);
@@ -282,8 +304,8 @@ __global__ void __launch_bounds__(256, 2) acc_stream_kernel(const StreamArgs a)
             if constexpr (M16) M = load_model16(*reinterpret_cast<const uint4 *>(slot + 64), __int_as_float(e1.y));
             else M = j_from(slot[64], slot[96]);
             J2 Lp, Gp, Rp, Lq, Gq, Rq;
-            Gp = fetch_k<GK>(a.tn, n_ant, e.z, fm.x, p);
-            Gq = fetch_k<GK>(a.tn, n_ant, e.z, fm.x, q);
+            Gp = cGp;
+            Gq = cGq;
             if constexpr (LK != KIND_NONE) {
                 Lp = fetch_k<LK>(a.to, n_ant, e.w, fm.y, p);
                 Lq = fetch_k<LK>(a.to, n_ant, e.w, fm.y, q);

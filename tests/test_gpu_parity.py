@@ -5,6 +5,8 @@ FP64 accumulators) and chi^2 within 1e-5 relative, as the solver's
 accuracy target states; single normal-equation steps and residuals are
 compared element by element at FP32 rounding level.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -289,3 +291,49 @@ def test_solve_rejects_bad_terms():
     with pytest.raises(qc.QCError):
         S.solve([qc.Term("diag", np.zeros(4, np.int32), np.zeros(4, np.int32), 1, 1, obs.n_ant, max_iter=0)])
     S.close()
+
+
+# ---------------------------------------------------------------------------
+# FP16 model storage (mixed precision)
+# ---------------------------------------------------------------------------
+
+def fp16_dequantized_model(obs):
+    """The model as the FP16 packing stores it: per baseline (ant1, ant2) a scale s = the largest
+    finite |component| over its samples, components multiplied by 1/s in float32 and rounded to
+    float16, read back as float16 * s in float32."""
+    m = np.ascontiguousarray(obs.model, dtype=np.complex64)
+    f = m.view(np.float32).reshape(m.shape[0], -1)
+    deq = np.empty_like(f)
+    keys = obs.ant1.astype(np.int64) * 65536 + obs.ant2.astype(np.int64)
+    for k in np.unique(keys):
+        rows = np.nonzero(keys == k)[0]
+        a = np.abs(f[rows])
+        a = a[np.isfinite(a)]
+        s = np.float32(a.max()) if a.size and a.max() > 0 else np.float32(1.0)
+        inv = np.float32(1.0) / s
+        q = (f[rows] * inv).astype(np.float16)
+        deq[rows] = q.astype(np.float32) * s
+    return deq.view(np.complex64).reshape(m.shape)
+
+
+@pytest.mark.parametrize("kernel", [0, 2])
+def test_fp16_model_matches_oracle_on_the_dequantized_model(kernel):
+    """With the model the FP16 packing actually stores, the GPU solve (FP16 model, FP32 sums, FP64
+    solves and accumulators) must meet the complex64 tolerances against the FP64 oracle."""
+    obs = synth.plain_large(seed=3, n_ant=10, n_time=12, n_chan=40, noise=0.05, flag_row_frac=0.1, n_src=8)
+    deq = dataclasses.replace(obs, model=fp16_dequantized_model(obs))
+    ot, _, ochi2 = run_oracle(deq, n_epochs=3)
+    gt, st, gchi2 = run_gpu(obs, n_epochs=3, kernel=kernel, model_fp16=True)
+    assert_chain_parity(obs, gt, ot)
+    assert abs(gchi2 - ochi2) <= CHI2_TOL * ochi2
+
+
+def test_fp16_model_error_against_the_exact_model_is_bounded():
+    """Against the oracle on the unquantized model the error is set by float16 rounding of the
+    model (relative 2^-11 of each baseline's largest component), well inside 1e-3."""
+    obs = synth.plain_large(seed=5, n_ant=10, n_time=12, n_chan=40, noise=0.05, flag_row_frac=0.1, n_src=8)
+    ot, _, ochi2 = run_oracle(obs, n_epochs=3)
+    gt, st, gchi2 = run_gpu(obs, n_epochs=3, model_fp16=True)
+    err = assert_chain_parity(obs, gt, ot, tol=1e-3)
+    assert err > 0
+    assert abs(gchi2 - ochi2) <= 1e-3 * ochi2

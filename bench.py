@@ -352,13 +352,19 @@ def main():
     # ---- roofline of the accumulate kernel (event-timed on the solver stream) ----
     peaks, peak_src = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    achieved = (acc_bytes / (acc_ms / 1000.0)) / 1e9 if acc_ms > 0 else None
+    # algorithmic bytes: B per vis-iteration (81; 65 with the FP16 model) x the samples of the active
+    # intervals each launch processes; the kernel's own reads skip fully flagged rows (read_bytes)
+    bpv = 65 if args.mixed else 81
+    alg_bytes = bpv * vis_iters
+    achieved = (alg_bytes / (acc_ms / 1000.0)) / 1e9 if acc_ms > 0 else None
     traffic, algo_full = profiled_traffic()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
+                "bytes_per_vis_iteration": bpv,
+                "read_bytes_per_launch": acc_bytes / max(1, acc_launches),
                 "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured"
                 else "fallback 6.8 TB/s", "kernel": ACC_KERNEL_NAME.get(args.kernel, "acc_kernel") + " (JHJ/JHr accumulate)",
-                "algorithmic_bytes_per_launch": acc_bytes / max(1, acc_launches),
+                "algorithmic_bytes_per_launch": alg_bytes / max(1, acc_launches),
                 "algorithmic_bytes_per_full_launch": algo_full,
                 "launch_ms_mean": acc_ms / max(1, acc_launches), "acc_share_of_step": acc_ms / ms if ms else None}
 
@@ -543,7 +549,9 @@ def run_batched(args):
     value = vis_all / (ms / 1e3)
     peaks, src = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    achieved = byts / (ms / 1e3) / 1e9
+    # algorithmic bytes: 81 B per vis-iteration (every sample of every iteration); the kernel skips
+    # copying flagged samples, but they share DRAM bursts with read neighbours
+    achieved = 81.0 * vis_iters / (ms / 1e3) / 1e9
     # looped plain launches on a sample of the same problems
     rng = np.random.default_rng(0)
     idx = np.sort(rng.choice(b.n_prob, size=min(args.looped, b.n_prob), replace=False))
@@ -584,6 +592,7 @@ def run_batched(args):
                          "candidates": n_tried, "best_ms": best.ms},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                          "traffic": None, "kernel": "batch_kernel (persistent, whole solve)",
+                         "bytes_per_vis_iteration": 81, "unflagged_read_bytes": byts,
                          "peak_source": f"{src} hbm_gbs (MEASURED_PEAKS.json)",
                          "mean_iters": stats[-1].mean_iters},
             "looped_plain": {"problems": int(idx.size), "value": loop_value, "unit": UNIT, "seconds": dt_loop,

@@ -357,7 +357,8 @@ def main():
     bpv = 65 if args.mixed else 81
     alg_bytes = bpv * vis_iters
     achieved = (alg_bytes / (acc_ms / 1000.0)) / 1e9 if acc_ms > 0 else None
-    traffic, algo_full = profiled_traffic()
+    # the committed capture is of the complex64 path; the FP16-model path reads other bytes
+    traffic, algo_full = profiled_traffic() if not args.mixed else (None, None)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
                 "bytes_per_vis_iteration": bpv,

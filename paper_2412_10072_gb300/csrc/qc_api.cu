@@ -834,6 +834,10 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
         sa.fmap2 = (const int2 *)B.fmap2.ptr;
         sa.acc = (double *)B.acc.ptr;
         sa.active = (const uint8_t *)B.active.ptr;
+        if (order == 1) {
+            if ((rc_ = ensure(B.units, sizeof(int)))) return rc_;
+            sa.unit_counter = (int *)B.units.ptr;
+        }
         stream_smem = (block / 32) * stream_smem_per_warp;
         if (stream_smem > smem_optin) return fail(QC_EUNSUPPORTED, "streaming kernel ring exceeds shared memory");
         if (!configured(stream_fn)) {
@@ -917,6 +921,7 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
             CK(cudaEventRecordWithFlags(events[2 + 2 * (k - 1)], st, rec_flags));
             if (streaming) {
                 sa.n_active = cnt + (k - 1);
+                if (sa.unit_counter) CK(cudaMemsetAsync(sa.unit_counter, 0, sizeof(int), st));
                 CK(L.stream_launch(grid, block, stream_smem, st, sa));
             } else if (pipelined) {
                 pa.a.n_active = cnt + (k - 1);

@@ -32,6 +32,7 @@ struct TermBufs {
     Buf rt;        // int4 [n_row] step-major row table of the streaming kernel
     Buf rt_scale;  // float [n_row] its FP16 model scales
     Buf fmap2;     // int2 [n_chan] {f_map of this term, f_map of the other term}
+    Buf units;     // int: unit counter of the streaming kernel's strip tiles
     cudaGraphExec_t exec = nullptr;
     bool graph_valid = false;
 };

@@ -24,7 +24,9 @@
 //
 // Work decomposition as in acc_kernel: a unit is a row (row tiles: its 32-channel
 // chunks are the steps) or a baseline strip x 32 channels (strip tiles: its rows
-// are the steps); warps take units with a grid stride.  Register sums are flushed
+// are the steps).  Row tiles go to warps with a grid stride; strip tiles, a few hundred
+// steps each, are handed out one at a time by an atomic counter as warps finish, so the
+// launch does not wait on warps that drew one unit more than the rest.  Register sums are flushed
 // (segmented warp reduction + FP64 atomics) when the antenna pair or any lane's
 // interval bin changes.
 #pragma once
@@ -49,6 +51,7 @@ struct StreamArgs {
     const uint8_t *active;      // [bins of the solved term]
     const int *n_active;        // nonzero: some interval still iterating
     double *acc;                // [bins][n_ant][KG]
+    int *unit_counter;          // strip tiles: next unit to hand out (zero before the launch), or null
 };
 
 constexpr int STREAM_END = -2;  // row-table field marking the end of a warp's stream
@@ -64,7 +67,8 @@ template <int K> __device__ __forceinline__ const float4 *tab_ptr(const DevTerm 
     return T.tab + (K == KIND_FULL ? 2 * idx : idx);
 }
 
-// Issue side of a warp's stream: walks the warp's units (grid stride W) and their
+// Issue side of a warp's stream: walks the warp's units (grid stride W, or the unit
+// counter) and their
 // steps, and for each step copies the 32 lanes' d, m, w into a ring stage
 // (16-byte cp.async per lane, zero-filled where there is nothing to read) and
 // writes the step's row-table entry and channel offset beside them (lane 0).
@@ -113,14 +117,36 @@ template <bool M16> struct StreamCursor {
                 blk_base = -1;
                 if (ilen > 0) return;
             }
+            next_unit(a, lane);
+        }
+    }
+
+    // next unit of this warp: a grid stride (row tiles), or the next one handed out by the
+    // launch's counter (strip tiles: units of a few hundred steps, taken as warps free up so
+    // that no warp is left with a last unit while the others idle)
+    __device__ __forceinline__ void next_unit(const StreamArgs &a, int lane)
+    {
+        if (a.unit_counter) {
+            int u = 0;
+            if (lane == 0) u = atomicAdd(a.unit_counter, 1);
+            iu = __shfl_sync(0xffffffffu, u, 0);
+        } else {
             iu += W;
         }
     }
 
     __device__ __forceinline__ void start(const StreamArgs &a, int lane, long first_unit, long stride)
     {
-        iu = first_unit;
         W = stride;
+        if (a.unit_counter) {
+            iu = 0;
+            W = 0;
+            int u = 0;
+            if (lane == 0) u = atomicAdd(a.unit_counter, 1);
+            iu = __shfl_sync(0xffffffffu, u, 0);
+        } else {
+            iu = first_unit;
+        }
         unit_start(a, lane);
     }
 
@@ -179,7 +205,7 @@ template <bool M16> struct StreamCursor {
             meta[2 * stage + 1] = make_int4(c0, __float_as_int(sc), 0, 0);
         }
         if (iu < a.n_units && ++ii == ilen) {
-            iu += W;
+            next_unit(a, lane);
             unit_start(a, lane);
         }
     }

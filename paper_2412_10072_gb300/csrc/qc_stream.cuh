@@ -61,6 +61,93 @@ __device__ __forceinline__ void prefetch_l1(const void *p)
     asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
 
+__host__ __device__ constexpr int next_pow2(int n) { return n <= 1 ? 1 : 2 * next_pow2((n + 1) / 2); }
+
+// Transposed reduction of one side's register sums when the whole warp is in one bin:
+// every exchange halves the values a lane holds, so KR values take about KR shuffles
+// (instead of 5 per value) and end as one total per lane, added with one atomic instruction.
+template <int KR, int KG, typename Lay>
+__device__ __forceinline__ void flush_side_warp(Acc<KR, false> &A, int key, int ant, int lane, bool live,
+                                                double *__restrict__ acc, int n_ant)
+{
+    constexpr int NP = next_pow2(KR), R = NP >= 32 ? NP / 32 : 1;
+    float v[NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) v[i] = i < KR ? A.s[i] : 0.f;
+    int idx = 0;
+#pragma unroll
+    for (int lev = 0; lev < 5; ++lev) {
+        const int d = 16 >> lev;
+        const int h = NP >> (lev + 1);
+        const bool up = (lane & d) != 0;
+        if (h >= 1) {
+#pragma unroll
+            for (int i = 0; i < NP / 2; ++i) {
+                if (i < h) {
+                    const float send = up ? v[i] : v[i + h];
+                    const float keep = up ? v[i + h] : v[i];
+                    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, d);
+                }
+            }
+            if (up) idx += h;
+        } else {
+            v[0] += __shfl_xor_sync(0xffffffffu, v[0], d);
+        }
+    }
+    // lanes holding the same total after the plain butterfly levels: the lowest writes
+    const bool writer = NP >= 32 || (lane & (32 / NP - 1)) == 0;
+    if (writer && live) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int j = idx + r;
+            if (j < KR) atomicAdd(acc + ((size_t)key * n_ant + ant) * KG + Lay::g(j), (double)v[r]);
+        }
+    }
+    A.zero();
+}
+
+// Flush both sides' register sums (antennas p and q of the warp's current step) to the
+// FP64 accumulators of bin `key` (per lane; -1 for lanes without a sample):
+//  * one bin for the whole warp (row tiles of an interval wider than 32 channels): the
+//    transposed reduction above, one side at a time;
+//  * a different bin in every lane: no reduction, each lane adds its own sums;
+//  * otherwise a segmented reduction over runs of lanes with equal bins (flush_side).
+// The first two are compiled only where they fit the kernel's 128 registers without
+// spilling (up to 16 sums per side, and up to 8 for the per-lane path).
+template <int KR, int KG, typename Lay>
+__device__ __forceinline__ void flush_pair(Acc<KR, false> &Ap, Acc<KR, false> &Aq, int key, int pq, int lane,
+                                           const uint8_t *__restrict__ active, double *__restrict__ acc, int n_ant)
+{
+    const int p = pq & 0xffff, q = pq >> 16;
+    if constexpr (KR <= 16) {
+        const int k0 = __shfl_sync(0xffffffffu, key, 0);
+        if (__all_sync(0xffffffffu, key == k0)) {
+            const bool live = k0 >= 0 && __ldg(active + k0);
+            flush_side_warp<KR, KG, Lay>(Ap, k0, p, lane, live, acc, n_ant);
+            flush_side_warp<KR, KG, Lay>(Aq, k0, q, lane, live, acc, n_ant);
+            return;
+        }
+    }
+    const unsigned m = __match_any_sync(0xffffffffu, key);
+    const bool live = key >= 0 && __ldg(active + key);
+    if (KR <= 8 && __all_sync(0xffffffffu, m == (1u << lane))) {
+        if (live) {
+#pragma unroll
+            for (int i = 0; i < KR; ++i) {
+                atomicAdd(acc + ((size_t)key * n_ant + p) * KG + Lay::g(i), (double)Ap.s[i]);
+                atomicAdd(acc + ((size_t)key * n_ant + q) * KG + Lay::g(i), (double)Aq.s[i]);
+            }
+        }
+        Ap.zero();
+        Aq.zero();
+        return;
+    }
+    const unsigned seg_end = 32 - __clz(m);
+    const bool head = lane == __ffs(m) - 1;
+    flush_side<KR, KG, false, Lay>(Ap, key, p, lane, seg_end, head, live, acc, n_ant);
+    flush_side<KR, KG, false, Lay>(Aq, key, q, lane, seg_end, head, live, acc, n_ant);
+}
+
 template <int K> __device__ __forceinline__ const float4 *tab_ptr(const DevTerm &T, int n_ant, int tint, int fint, int ant)
 {
     const size_t idx = ((size_t)tint * n_ant + ant) * T.n_fint + fint;
@@ -294,13 +381,7 @@ __global__ void __launch_bounds__(256, 2) acc_stream_kernel(const StreamArgs a)
             ++since_flush;
             if (__any_sync(0xffffffffu, change && cur_key >= 0)) {
                 since_flush = 1;
-                const unsigned m = __match_any_sync(0xffffffffu, cur_key);
-                const unsigned seg_end = 32 - __clz(m);
-                const bool head = lane == __ffs(m) - 1;
-                const bool lv = cur_key >= 0 && __ldg(a.active + cur_key);
-                const int p = cur_pq & 0xffff, q = cur_pq >> 16;
-                flush_side<KR, KG, KAHAN, Lay>(Ap, cur_key, p, lane, seg_end, head, lv, a.acc, n_ant);
-                flush_side<KR, KG, KAHAN, Lay>(Aq, cur_key, q, lane, seg_end, head, lv, a.acc, n_ant);
+                flush_pair<KR, KG, Lay>(Ap, Aq, cur_key, cur_pq, lane, a.active, a.acc, n_ant);
             }
             cur_key = key;
             cur_pq = e.y;
@@ -348,15 +429,7 @@ __global__ void __launch_bounds__(256, 2) acc_stream_kernel(const StreamArgs a)
         eB0 = eC0; eB1 = eC1;
         stage = nst;
     }
-    if (__any_sync(0xffffffffu, cur_key >= 0)) {
-        const unsigned m = __match_any_sync(0xffffffffu, cur_key);
-        const unsigned seg_end = 32 - __clz(m);
-        const bool head = lane == __ffs(m) - 1;
-        const bool lv = cur_key >= 0 && __ldg(a.active + cur_key);
-        const int p = cur_pq & 0xffff, q = cur_pq >> 16;
-        flush_side<KR, KG, KAHAN, Lay>(Ap, cur_key, p, lane, seg_end, head, lv, a.acc, n_ant);
-        flush_side<KR, KG, KAHAN, Lay>(Aq, cur_key, q, lane, seg_end, head, lv, a.acc, n_ant);
-    }
+    if (__any_sync(0xffffffffu, cur_key >= 0)) flush_pair<KR, KG, Lay>(Ap, Aq, cur_key, cur_pq, lane, a.active, a.acc, n_ant);
     cp_async_wait<0>();
 }
 

@@ -362,6 +362,20 @@ __global__ void __launch_bounds__(256, 2) acc_stream_kernel(const StreamArgs a)
         // the step after next: its entry and channel maps; the next step: its gain entries into L1
         const int4 eC0 = meta[2 * nst2], eC1 = meta[2 * nst2 + 1];
         const int2 fmC = read_map(eC0, eC1);
+        // this step's entries of the other term (L1 hits after last step's prefetch), loaded
+        // here so that the issue below covers their latency
+        J2 Lp, Lq, Rp, Rq;
+        if (e.z >= 0) {
+            const int p = e.y & 0xffff, q = e.y >> 16;
+            if constexpr (LK != KIND_NONE) {
+                Lp = fetch_k<LK>(a.to, n_ant, e.w, fm.y, p);
+                Lq = fetch_k<LK>(a.to, n_ant, e.w, fm.y, q);
+            }
+            if constexpr (RK != KIND_NONE) {
+                Rp = fetch_k<RK>(a.to, n_ant, e.w, fm.y, p);
+                Rq = fetch_k<RK>(a.to, n_ant, e.w, fm.y, q);
+            }
+        }
         if (eB0.x != STREAM_END && eB0.z >= 0) {
             const int np = eB0.y & 0xffff, nq = eB0.y >> 16;
             if constexpr (HAS_O) {
@@ -405,22 +419,11 @@ __global__ void __launch_bounds__(256, 2) acc_stream_kernel(const StreamArgs a)
             }
         }
         if (ok) {
-            const int p = e.y & 0xffff, q = e.y >> 16;
             const J2 Dm = j_from(slot[0], slot[32]);
             J2 M;
             if constexpr (M16) M = load_model16(*reinterpret_cast<const uint4 *>(slot + 64), __int_as_float(e1.y));
             else M = j_from(slot[64], slot[96]);
-            J2 Lp, Gp, Rp, Lq, Gq, Rq;
-            Gp = cGp;
-            Gq = cGq;
-            if constexpr (LK != KIND_NONE) {
-                Lp = fetch_k<LK>(a.to, n_ant, e.w, fm.y, p);
-                Lq = fetch_k<LK>(a.to, n_ant, e.w, fm.y, q);
-            }
-            if constexpr (RK != KIND_NONE) {
-                Rp = fetch_k<RK>(a.to, n_ant, e.w, fm.y, p);
-                Rq = fetch_k<RK>(a.to, n_ant, e.w, fm.y, q);
-            }
+            const J2 Gp = cGp, Gq = cGq;
             sample_math<TS, LK, RK, KAHAN>(Lp, Gp, Rp, Lq, Gq, Rq, Dm, M, w, Ap, Aq);
         }
         fmA = fmB;

@@ -375,6 +375,14 @@ __global__ void __launch_bounds__(256, 2) acc_stream_kernel(const StreamArgs a)
                 Rp = fetch_k<RK>(a.to, n_ant, e.w, fm.y, p);
                 Rq = fetch_k<RK>(a.to, n_ant, e.w, fm.y, q);
             }
+            // the solved term's entries stay in registers while the lane's table index is unchanged
+            const bool in = e1.x + lane < n_chan;
+            const int ip = in ? (e.z * n_ant + p) * a.tn.n_fint + fm.x : ci_p;
+            const int iq = in ? (e.z * n_ant + q) * a.tn.n_fint + fm.x : ci_q;
+            if (__any_sync(0xffffffffu, ip != ci_p || iq != ci_q)) {
+                if (ip != ci_p) { cGp = fetch_k<GK>(a.tn, n_ant, e.z, fm.x, p); ci_p = ip; }
+                if (iq != ci_q) { cGq = fetch_k<GK>(a.tn, n_ant, e.z, fm.x, q); ci_q = iq; }
+            }
         }
         if (eB0.x != STREAM_END && eB0.z >= 0) {
             const int np = eB0.y & 0xffff, nq = eB0.y >> 16;
@@ -408,16 +416,6 @@ __global__ void __launch_bounds__(256, 2) acc_stream_kernel(const StreamArgs a)
             act_val = __ldg(a.active + key) != 0;
         }
         ok = ok && act_val;
-        {
-            // the solved term's entries stay in registers while the lane's table index is unchanged
-            const int p = e.y & 0xffff, q = e.y >> 16;
-            const int ip = ok ? (e.z * n_ant + p) * a.tn.n_fint + fm.x : ci_p;
-            const int iq = ok ? (e.z * n_ant + q) * a.tn.n_fint + fm.x : ci_q;
-            if (__any_sync(0xffffffffu, ip != ci_p || iq != ci_q)) {
-                if (ip != ci_p) { cGp = fetch_k<GK>(a.tn, n_ant, e.z, fm.x, p); ci_p = ip; }
-                if (iq != ci_q) { cGq = fetch_k<GK>(a.tn, n_ant, e.z, fm.x, q); ci_q = iq; }
-            }
-        }
         if (ok) {
             const J2 Dm = j_from(slot[0], slot[32]);
             J2 M;

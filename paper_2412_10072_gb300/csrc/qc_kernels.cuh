@@ -192,13 +192,14 @@ template <int KR, bool KAHAN> struct Acc {
 
 // Contribution of one sample to antenna a's blocks: E = L_a (x) X^T (Eq. vectrick,
 // Eq. g_derivative_dd) restricted to the term's free parameters, weights w
-// per correlation, residual r (both in the orientation of this side).
+// per correlation and weighted residual wr = w * r, element by element (both in
+// the orientation of this side).
 template <int TS, bool HAS_L, bool KAHAN>
 __device__ __forceinline__ void accumulate_side(Acc<AccLayout<TS, HAS_L>::KR, KAHAN> &A, const J2 &L,
-                                                const J2 &X, float4 w, const J2 &r)
+                                                const J2 &X, float4 w, const J2 &wr)
 {
     const float wv[4] = { w.x, w.y, w.z, w.w };
-    const float2 rv[4] = { r.a, r.b, r.c, r.d };
+    const float2 wrv[4] = { wr.a, wr.b, wr.c, wr.d };
     const float2 Xv[4] = { X.a, X.b, X.c, X.d };            // X[l][j] = Xv[2l+j]
     if constexpr (!HAS_L) {
         if constexpr (TS == TS_DIAG) {
@@ -210,7 +211,7 @@ __device__ __forceinline__ void accumulate_side(Acc<AccLayout<TS, HAS_L>::KR, KA
                     const float2 x = Xv[2 * k + j];
                     const float ww = wv[2 * k + j];
                     A.fma(k, ww, cnorm2(x));
-                    A.cfma(2 + 2 * k, x, cscale(rv[2 * k + j], ww));
+                    A.cfma(2 + 2 * k, x, wrv[2 * k + j]);
                 }
         } else {
             // parameter u = (k, l): E[(k,j), (k,l)] = X[l][j]
@@ -229,7 +230,7 @@ __device__ __forceinline__ void accumulate_side(Acc<AccLayout<TS, HAS_L>::KR, KA
                 A.fma(4 + 2 * k, w1, o1.x);
                 A.fma(5 + 2 * k, w0, o0.y);
                 A.fma(5 + 2 * k, w1, o1.y);
-                const float2 wr0 = cscale(rv[2 * k], w0), wr1 = cscale(rv[2 * k + 1], w1);
+                const float2 wr0 = wrv[2 * k], wr1 = wrv[2 * k + 1];
                 A.cfma(8 + 4 * k, x00, wr0);
                 A.cfma(8 + 4 * k, x01, wr1);
                 A.cfma(10 + 4 * k, x10, wr0);
@@ -255,9 +256,8 @@ __device__ __forceinline__ void accumulate_side(Acc<AccLayout<TS, HAS_L>::KR, KA
                 h00 = fmaf(wv[m], cnorm2(E0[m]), h00);
                 h11 = fmaf(wv[m], cnorm2(E1[m]), h11);
                 h01 = cfma_conj(E0[m], cscale(E1[m], wv[m]), h01);
-                const float2 wr = cscale(rv[m], wv[m]);
-                j0 = cfma_conj(E0[m], wr, j0);
-                j1 = cfma_conj(E1[m], wr, j1);
+                j0 = cfma_conj(E0[m], wrv[m], j0);
+                j1 = cfma_conj(E1[m], wrv[m], j1);
             }
             A.add(0, h00); A.add(1, h11); A.add(2, h01.x); A.add(3, h01.y);
             A.add(4, j0.x); A.add(5, j0.y); A.add(6, j1.x); A.add(7, j1.y);
@@ -279,7 +279,7 @@ __device__ __forceinline__ void accumulate_side(Acc<AccLayout<TS, HAS_L>::KR, KA
 #pragma unroll
                 for (int m = 0; m < 4; ++m) {
                     h = fmaf(wv[m], cnorm2(E[m][u]), h);
-                    jr = cfma_conj(E[m][u], cscale(rv[m], wv[m]), jr);
+                    jr = cfma_conj(E[m][u], wrv[m], jr);
                 }
                 A.add(u, h);
                 A.add(16 + 2 * u, jr.x);
@@ -400,10 +400,12 @@ __device__ __forceinline__ void sample_math(const J2 &Lp, const J2 &Gp, const J2
         Y = j_herm(W);
         V = lmulk<LK>(Lp, lmulk<GK>(Gp, X));
     }
-    J2 r;
-    r.a = csub(Dm.a, V.a); r.b = csub(Dm.b, V.b); r.c = csub(Dm.c, V.c); r.d = csub(Dm.d, V.d);
-    accumulate_side<TS, HAS_L, KAHAN>(Ap, Lp, X, w, r);
-    accumulate_side<TS, HAS_L, KAHAN>(Aq, Lq, Y, make_float4(w.x, w.z, w.y, w.w), j_herm(r));
+    // weighted residual w * (D - V); the conjugate baseline's is its conjugate transpose
+    J2 wr;
+    wr.a = cscale(csub(Dm.a, V.a), w.x); wr.b = cscale(csub(Dm.b, V.b), w.y);
+    wr.c = cscale(csub(Dm.c, V.c), w.z); wr.d = cscale(csub(Dm.d, V.d), w.w);
+    accumulate_side<TS, HAS_L, KAHAN>(Ap, Lp, X, w, wr);
+    accumulate_side<TS, HAS_L, KAHAN>(Aq, Lq, Y, make_float4(w.x, w.z, w.y, w.w), j_herm(wr));
 }
 
 template <int TS, int LK, int RK, bool SIMPLE, bool KAHAN>

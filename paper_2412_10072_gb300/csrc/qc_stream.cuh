@@ -161,7 +161,7 @@ template <int K> __device__ __forceinline__ const float4 *tab_ptr(const DevTerm 
 // writes the step's row-table entry and channel offset beside them (lane 0).
 template <bool M16> struct StreamCursor {
     static constexpr int V4 = M16 ? 4 : 5;
-    long iu, W;                  // unit, grid stride in units
+    int iu, W;                   // unit, grid stride in units
     int ii = 0, ilen = 0;        // step within the unit, steps in the unit
     int ikb = 0, ic0 = 0;        // strip tiles: first rt entry of the unit, first channel of its chunk
     int4 irt = make_int4(0, 0, -1, 0);   // row tiles: the unit's row-table entry
@@ -197,8 +197,8 @@ template <bool M16> struct StreamCursor {
                     }
                 }
             } else {
-                const int s = (int)(iu / nch);
-                ic0 = (int)(iu - (long)s * nch) * 32;
+                const int s = iu / nch;
+                ic0 = (iu - s * nch) * 32;
                 ikb = __ldg(a.unit_off + s);
                 ilen = __ldg(a.unit_off + s + 1) - ikb;
                 blk_base = -1;
@@ -222,7 +222,7 @@ template <bool M16> struct StreamCursor {
         }
     }
 
-    __device__ __forceinline__ void start(const StreamArgs &a, int lane, long first_unit, long stride)
+    __device__ __forceinline__ void start(const StreamArgs &a, int lane, int first_unit, int stride)
     {
         W = stride;
         if (a.unit_counter) {
@@ -319,12 +319,12 @@ __global__ void __launch_bounds__(256, 2) acc_stream_kernel(const StreamArgs a)
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
     float4 *ring = s_stream + (size_t)wib * DEPTH * V4 * 32;                          // [DEPTH][V4][32]
     int4 *meta = reinterpret_cast<int4 *>(s_stream + (size_t)nw * DEPTH * V4 * 32) + (size_t)wib * DEPTH * 2;
-    const long W = ((long)gridDim.x * blockDim.x) >> 5;
+    const int W = (int)((gridDim.x * blockDim.x) >> 5);
     const int n_chan = a.n_chan, n_ant = a.n_ant;
 
     // ---------------- issue side: the step DEPTH - 1 ahead of the arithmetic ----------------
     StreamCursor<M16> cur;
-    cur.start(a, lane, ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5, W);
+    cur.start(a, lane, (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), W);
     int stage_i = 0;
     auto issue = [&]() {
         cur.issue(a, lane, ring, meta, stage_i);

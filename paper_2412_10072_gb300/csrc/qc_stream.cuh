@@ -19,8 +19,10 @@
 //    read), and lane 0 writes the step's row-table entry beside them;
 //  * the lane's channel interval indices are read two steps ahead; the solved term's
 //    gain entries stay in registers while their table index is unchanged (a row of a
-//    row tile, a strip of a strip tile), and the other term's entries of the next
-//    step are prefetched into L1, so the gain loads of a step hit L1.
+//    row tile, a strip of a strip tile), and the gain loads of a step are issued at
+//    its top, before the next copy is issued, which covers their latency (the gain
+//    tables are small and stay in L2; an L1 prefetch a step ahead cost more issue
+//    slots than it saved).
 //
 // Work decomposition as in acc_kernel: a unit is a row (row tiles: its 32-channel
 // chunks are the steps) or a baseline strip x 32 channels (strip tiles: its rows
@@ -56,10 +58,6 @@ struct StreamArgs {
 
 constexpr int STREAM_END = -2;  // row-table field marking the end of a warp's stream
 
-__device__ __forceinline__ void prefetch_l1(const void *p)
-{
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
-}
 
 __host__ __device__ constexpr int next_pow2(int n) { return n <= 1 ? 1 : 2 * next_pow2((n + 1) / 2); }
 
@@ -146,12 +144,6 @@ __device__ __forceinline__ void flush_pair(Acc<KR, false> &Ap, Acc<KR, false> &A
     const bool head = lane == __ffs(m) - 1;
     flush_side<KR, KG, false, Lay>(Ap, key, p, lane, seg_end, head, live, acc, n_ant);
     flush_side<KR, KG, false, Lay>(Aq, key, q, lane, seg_end, head, live, acc, n_ant);
-}
-
-template <int K> __device__ __forceinline__ const float4 *tab_ptr(const DevTerm &T, int n_ant, int tint, int fint, int ant)
-{
-    const size_t idx = ((size_t)tint * n_ant + ant) * T.n_fint + fint;
-    return T.tab + (K == KIND_FULL ? 2 * idx : idx);
 }
 
 // Issue side of a warp's stream: walks the warp's units (grid stride W, or the unit
@@ -303,8 +295,6 @@ __global__ void __launch_bounds__(256, 2) acc_stream_kernel(const StreamArgs a)
 {
     if (__ldg(a.n_active) == 0) return;
     constexpr bool HAS_L = LK != KIND_NONE;
-    constexpr bool HAS_O = LK != KIND_NONE || RK != KIND_NONE;
-    constexpr int OK_ = HAS_L ? LK : RK;                     // kind of the other term
     constexpr int GK = TS == TS_FULL ? KIND_FULL : KIND_DIAG;
     // FP16 model: instead of a compensated add per sample, the lane sums go to the FP64
     // accumulators at least every FLUSH_EVERY steps, so FP32 rounding is confined to
@@ -359,11 +349,11 @@ __global__ void __launch_bounds__(256, 2) acc_stream_kernel(const StreamArgs a)
         const int2 fm = fmA;
         const int nst = stage + 1 == DEPTH ? 0 : stage + 1;
         const int nst2 = nst + 1 == DEPTH ? 0 : nst + 1;
-        // the step after next: its entry and channel maps; the next step: its gain entries into L1
+        // the step after next: its entry and channel maps
         const int4 eC0 = meta[2 * nst2], eC1 = meta[2 * nst2 + 1];
         const int2 fmC = read_map(eC0, eC1);
-        // this step's entries of the other term (L1 hits after last step's prefetch), loaded
-        // here so that the issue below covers their latency
+        // this step's entries of the other term, loaded here so that the issue below covers
+        // their latency
         J2 Lp, Lq, Rp, Rq;
         if (e.z >= 0) {
             const int p = e.y & 0xffff, q = e.y >> 16;
@@ -382,13 +372,6 @@ __global__ void __launch_bounds__(256, 2) acc_stream_kernel(const StreamArgs a)
             if (__any_sync(0xffffffffu, ip != ci_p || iq != ci_q)) {
                 if (ip != ci_p) { cGp = fetch_k<GK>(a.tn, n_ant, e.z, fm.x, p); ci_p = ip; }
                 if (iq != ci_q) { cGq = fetch_k<GK>(a.tn, n_ant, e.z, fm.x, q); ci_q = iq; }
-            }
-        }
-        if (eB0.x != STREAM_END && eB0.z >= 0) {
-            const int np = eB0.y & 0xffff, nq = eB0.y >> 16;
-            if constexpr (HAS_O) {
-                prefetch_l1(tab_ptr<OK_>(a.to, n_ant, eB0.w, fmB.y, np));
-                prefetch_l1(tab_ptr<OK_>(a.to, n_ant, eB0.w, fmB.y, nq));
             }
         }
         issue();

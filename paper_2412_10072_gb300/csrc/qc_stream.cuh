@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(256, 2) acc_stream_kernel(const StreamArgs a)
     using Lay = AccLayout<TS, HAS_L>;
     constexpr int KR = Lay::KR, KG = Lay::KG;
     constexpr int V4 = M16 ? 4 : 5;                         // 16-byte words per sample: d (2), m (2 or 1), w (1)
-    static_assert(DEPTH >= 4, "the entries of the next two steps must be in the ring");
+    static_assert(DEPTH >= 3, "the entry of the next step must be in the ring");
     extern __shared__ float4 s_stream[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
     float4 *ring = s_stream + (size_t)wib * DEPTH * V4 * 32;                          // [DEPTH][V4][32]
@@ -330,15 +330,15 @@ __global__ void __launch_bounds__(256, 2) acc_stream_kernel(const StreamArgs a)
     Ap.zero();
     Aq.zero();
     int stage = 0, cur_key = -1, cur_pq = -1;
-    // ring entries of the current step (A), the next (B) and the one after (C) are carried in
-    // registers, as are the lane's channel interval maps of A and B; each step reads C's entry
-    // from shared memory and its maps from global memory (two steps ahead of their use)
+    // the ring entry of the current step (A) and the lane's channel interval maps are carried
+    // in registers; each step reads the next step's (B) entry from shared memory and its maps
+    // from global memory, one step ahead of their use
     auto read_map = [&](const int4 &m0, const int4 &m1) {
         const int c = m1.x + lane;
         return (m0.x != STREAM_END && m0.z >= 0 && c < n_chan) ? __ldg(a.fmap2 + c) : make_int2(0, 0);
     };
-    int4 eA0 = meta[0], eA1 = meta[1], eB0 = meta[2], eB1 = meta[3];
-    int2 fmA = read_map(eA0, eA1), fmB = read_map(eB0, eB1);
+    int4 eA0 = meta[0], eA1 = meta[1];
+    int2 fmA = read_map(eA0, eA1);
     int ci_p = -1, ci_q = -1, act_key = -1, since_flush = 0;
     bool act_val = false;
     J2 cGp = j_identity(), cGq = j_identity();
@@ -348,10 +348,9 @@ __global__ void __launch_bounds__(256, 2) acc_stream_kernel(const StreamArgs a)
         if (e.x == STREAM_END) break;
         const int2 fm = fmA;
         const int nst = stage + 1 == DEPTH ? 0 : stage + 1;
-        const int nst2 = nst + 1 == DEPTH ? 0 : nst + 1;
-        // the step after next: its entry and channel maps
-        const int4 eC0 = meta[2 * nst2], eC1 = meta[2 * nst2 + 1];
-        const int2 fmC = read_map(eC0, eC1);
+        // the next step: its entry and channel maps
+        const int4 eB0 = meta[2 * nst], eB1 = meta[2 * nst + 1];
+        const int2 fmB = read_map(eB0, eB1);
         // this step's entries of the other term, loaded here so that the issue below covers
         // their latency
         J2 Lp, Lq, Rp, Rq;
@@ -382,10 +381,11 @@ __global__ void __launch_bounds__(256, 2) acc_stream_kernel(const StreamArgs a)
         const bool in = live && c < n_chan;
         const int key = in ? e.z * a.tn.n_fint + fm.x : -1;
         if (live) {
-            const bool change = e.y != cur_pq || key != cur_key || since_flush >= FLUSH_EVERY;
-            ++since_flush;
+            bool change = e.y != cur_pq || key != cur_key;
+            if constexpr (M16) change = change || since_flush >= FLUSH_EVERY;
+            if constexpr (M16) ++since_flush;
             if (__any_sync(0xffffffffu, change && cur_key >= 0)) {
-                since_flush = 1;
+                if constexpr (M16) since_flush = 1;
                 flush_pair<KR, KG, Lay>(Ap, Aq, cur_key, cur_pq, lane, a.active, a.acc, n_ant);
             }
             cur_key = key;
@@ -408,9 +408,7 @@ __global__ void __launch_bounds__(256, 2) acc_stream_kernel(const StreamArgs a)
             sample_math<TS, LK, RK, KAHAN>(Lp, Gp, Rp, Lq, Gq, Rq, Dm, M, w, Ap, Aq);
         }
         fmA = fmB;
-        fmB = fmC;
         eA0 = eB0; eA1 = eB1;
-        eB0 = eC0; eB1 = eC1;
         stage = nst;
     }
     if (__any_sync(0xffffffffu, cur_key >= 0)) flush_pair<KR, KG, Lay>(Ap, Aq, cur_key, cur_pq, lane, a.active, a.acc, n_ant);

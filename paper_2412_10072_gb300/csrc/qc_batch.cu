@@ -131,7 +131,8 @@ __host__ __device__ constexpr size_t batch_ring_bytes_per_warp()
 // memory: d in slot[0], slot[32]; m in slot[64] (and slot[96]); w in slot[96 or 128].
 // A lane with nothing to read (flagged sample, autocorrelation) sees zeros; key is
 // p | q << 16 of the sample's row, -1 past the end of the problem.  The antennas and
-// flags of a step are loaded two steps before its copies are issued.
+// flags of a step are loaded three steps before its copies are issued (flags stream
+// from DRAM, and one step is about as long as a DRAM round trip under load).
 template <bool M16, int DEPTH, typename F>
 __device__ __forceinline__ void stream_pass(const BatchArgs &a, const BProb &P, float4 *ring, int2 *meta, int lane,
                                             int warp, int n_warps, F &&f)
@@ -152,35 +153,45 @@ __device__ __forceinline__ void stream_pass(const BatchArgs &a, const BProb &P, 
     const float *rsc = M16 ? a.row_scale + P.row_off : nullptr;
     // issue cursor: the step whose copies are issued next
     long is = st_begin;
-    int r2, c2;                     // the lane's (row, chan) in step is + 1
+    int r2, c2;                     // the lane's (row, chan) in step is + 2
     {
         const long s0 = st_begin * 32 + lane;
         r2 = (int)(s0 / nc);
         c2 = (int)(s0 - (long)r2 * nc);
     }
-    auto load_meta = [&](long step, int row, int2 &pq, int &use, float &sc) {
+    // loads only: what depends on the loaded values is computed when the step is issued,
+    // so that no instruction waits on them before then
+    auto load_meta = [&](long step, int row, int2 &pq, int &fl, float &sc) {
         const long s = step * 32 + lane;
         const bool in = step < st_end && s < n_samp;
-        pq = in ? __ldg(ants + row) : make_int2(-1, -1);
-        use = in && pq.x != pq.y && !(flg && __ldg(flg + s)) ? 1 : 0;
-        sc = M16 && in ? __ldg(rsc + row) : 0.f;
+        pq = make_int2(-1, -1);     // past the end: p == q, nothing to read
+        fl = 0;
+        sc = 0.f;
+        if (in) {
+            pq = __ldg(ants + row);
+            if (flg) fl = __ldg(flg + s);
+            if (M16) sc = __ldg(rsc + row);
+        }
     };
     auto advance = [&](int &row, int &c) {
         c += r32;
         row += q32;
         if (c >= nc) { c -= nc; ++row; }
     };
-    int2 m1pq, m2pq;
-    int m1use, m2use;
-    float m1sc, m2sc;
-    load_meta(is, r2, m1pq, m1use, m1sc);
+    int2 m1pq, m2pq, m3pq;
+    int m1fl, m2fl, m3fl;           // the step's flag byte (nonzero: flagged)
+    float m1sc, m2sc, m3sc;
+    load_meta(is, r2, m1pq, m1fl, m1sc);
     advance(r2, c2);
-    load_meta(is + 1, r2, m2pq, m2use, m2sc);
+    load_meta(is + 1, r2, m2pq, m2fl, m2sc);
+    advance(r2, c2);
+    load_meta(is + 2, r2, m3pq, m3fl, m3sc);
     int stage_i = 0;
     auto issue = [&]() {
         const long s = is * 32 + lane;
-        const uint32_t nb = m1use ? 16u : 0u;
-        const long so = m1use ? s : 0;
+        const bool use = m1pq.x != m1pq.y && m1fl == 0;     // cross-correlation, unflagged
+        const uint32_t nb = use ? 16u : 0u;
+        const long so = use ? s : 0;
         float4 *slot = ring + (size_t)stage_i * V4 * 32 + lane;
         cp_async16(slot, vis + 2 * so, nb);
         cp_async16(slot + 32, vis + 2 * so + 1, nb);
@@ -201,10 +212,13 @@ __device__ __forceinline__ void stream_pass(const BatchArgs &a, const BProb &P, 
         // shift the metadata pipeline by one step
         ++is;
         m1pq = m2pq;
-        m1use = m2use;
+        m1fl = m2fl;
         m1sc = m2sc;
+        m2pq = m3pq;
+        m2fl = m3fl;
+        m2sc = m3sc;
         advance(r2, c2);
-        load_meta(is + 1, r2, m2pq, m2use, m2sc);
+        load_meta(is + 2, r2, m3pq, m3fl, m3sc);
     };
 #pragma unroll
     for (int d = 0; d < DEPTH - 1; ++d) issue();

@@ -226,9 +226,11 @@ __device__ __forceinline__ void stream_pass(const BatchArgs &a, const BProb &P, 
     for (long t = st_begin; t < st_end; ++t) {
         cp_async_wait<DEPTH - 2>();
         const int2 key = meta[stage_c * 32 + lane];
+        // refill the stage consumed last step before this step's arithmetic, so that
+        // DEPTH - 1 stages are in flight while it runs
+        issue();
         f(ring + (size_t)stage_c * V4 * 32 + lane, key.x, key.y);
         if (++stage_c == DEPTH) stage_c = 0;
-        issue();
     }
     cp_async_wait<0>();
 }

@@ -16,8 +16,12 @@ Parity status of each oracle function (what pins it, see ``tests/``):
   truth.
 - ``residual``: pinned by chi^2 = 0 at the true gains on noise-free data and
   by the noise statistics of chi^2 on noisy data.
+- delay terms (Scenario 2): pinned by a forward model written in the test,
+  central differences of it in the four real parameters, the chi^2
+  gradient, exact recovery of generating phases and delays, and the
+  singular single-frequency case (``tests/test_oracle_delay.py``).
 - ``mlp``: pinned by central finite differences of its own loss.
 """
-from .oracle import (OC_DIAG, OC_FULL, OC_PHASE, OracleProblem, OracleTerm, build,  # noqa: F401
+from .oracle import (OC_DIAG, OC_FULL, OC_PHASE, OC_DELAY, OracleProblem, OracleTerm, build,  # noqa: F401
                      normal_equations, residual, solve, solve_term, block_solve)
 from .gauge import reference_diag, reference_chain, chain_products  # noqa: F401

@@ -14,8 +14,8 @@ from typing import List, Optional, Sequence
 
 import numpy as np
 
-OC_DIAG, OC_FULL, OC_PHASE = 0, 1, 2
-_KIND = {"diag": OC_DIAG, "full": OC_FULL, "phase": OC_PHASE}
+OC_DIAG, OC_FULL, OC_PHASE, OC_DELAY = 0, 1, 2, 3
+_KIND = {"diag": OC_DIAG, "full": OC_FULL, "phase": OC_PHASE, "delay": OC_DELAY}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "qc_oracle.c")
@@ -47,7 +47,7 @@ class _Term(C.Structure):
     _fields_ = [("type", C.c_int), ("n_tint", C.c_int), ("n_fint", C.c_int),
                 ("t_map", C.c_void_p), ("f_map", C.c_void_p), ("params", C.c_void_p),
                 ("gain_flags", C.c_void_p), ("solve", C.c_int), ("max_iter", C.c_int),
-                ("tol", C.c_double)]
+                ("tol", C.c_double), ("chan_freq", C.c_void_p)]
 
 
 class _Opts(C.Structure):
@@ -104,18 +104,26 @@ class OracleProblem:
 
 
 class OracleTerm:
-    """One chain term; ``params`` is complex128 [tint][fint][ant][4] or float64 [..][2] (phase)."""
+    """One chain term; ``params`` is complex128 [tint][fint][ant][4], float64 [..][2] (phase)
+    or float64 [..][4] = (phi_X, tau_X, phi_Y, tau_Y) (delay, with ``chan_freq`` [n_chan])."""
 
     def __init__(self, kind: str, t_map, f_map, n_tint: int, n_fint: int, n_ant: int,
-                 params=None, solve: bool = True, max_iter: int = 20, tol: float = 1e-6):
+                 params=None, solve: bool = True, max_iter: int = 20, tol: float = 1e-6, chan_freq=None):
         self.kind = kind
         self.type = _KIND[kind]
+        self.chan_freq = None
+        if kind == "delay":
+            if chan_freq is None:
+                raise ValueError("a delay term needs chan_freq")
+            self.chan_freq = np.ascontiguousarray(chan_freq, dtype=np.float64)
         self.t_map = np.ascontiguousarray(t_map, dtype=np.int32)
         self.f_map = np.ascontiguousarray(f_map, dtype=np.int32)
         self.n_tint, self.n_fint, self.n_ant = int(n_tint), int(n_fint), int(n_ant)
         if params is None:
             if kind == "phase":
                 params = np.zeros((n_tint, n_fint, n_ant, 2))
+            elif kind == "delay":
+                params = np.zeros((n_tint, n_fint, n_ant, 4))
             else:
                 params = np.zeros((n_tint, n_fint, n_ant, 4), dtype=np.complex128)
                 params[..., 0] = 1.0
@@ -123,6 +131,9 @@ class OracleTerm:
         if kind == "phase":
             self.params = np.ascontiguousarray(params, dtype=np.float64).copy()
             assert self.params.shape == (n_tint, n_fint, n_ant, 2)
+        elif kind == "delay":
+            self.params = np.ascontiguousarray(params, dtype=np.float64).copy()
+            assert self.params.shape == (n_tint, n_fint, n_ant, 4)
         else:
             self.params = np.ascontiguousarray(params, dtype=np.complex128).copy()
             assert self.params.shape == (n_tint, n_fint, n_ant, 4)
@@ -134,10 +145,18 @@ class OracleTerm:
 
     @property
     def n_param(self) -> int:
-        return 4 if self.kind == "full" else 2
+        return 4 if self.kind in ("full", "delay") else 2
 
     def jones(self) -> np.ndarray:
-        """The term's Jones matrices [tint][fint][ant][4] (complex128)."""
+        """The term's Jones matrices [tint][fint][ant][4] (complex128); for a delay term
+        [tint][chan][ant][4], evaluated at every channel (its f_map then becomes the identity)."""
+        if self.kind == "delay":
+            nu = self.chan_freq[None, :, None]
+            u = self.params[:, self.f_map]                          # [tint][chan][ant][4]
+            out = np.zeros(u.shape[:-1] + (4,), dtype=np.complex128)
+            out[..., 0] = np.exp(1j * (u[..., 0] + 2 * np.pi * u[..., 1] * nu))
+            out[..., 3] = np.exp(1j * (u[..., 2] + 2 * np.pi * u[..., 3] * nu))
+            return out
         if self.kind == "phase":
             out = np.zeros(self.params.shape[:-1] + (4,), dtype=np.complex128)
             out[..., 0] = np.exp(1j * self.params[..., 0])
@@ -147,7 +166,8 @@ class OracleTerm:
 
     def _c(self) -> _Term:
         return _Term(self.type, self.n_tint, self.n_fint, _ptr(self.t_map), _ptr(self.f_map),
-                     _ptr(self.params), _ptr(self.gain_flags), int(self.solve), self.max_iter, self.tol)
+                     _ptr(self.params), _ptr(self.gain_flags), int(self.solve), self.max_iter, self.tol,
+                     _ptr(self.chan_freq))
 
     @classmethod
     def from_spec(cls, spec, n_ant: int, params=None, **kw) -> "OracleTerm":
@@ -161,7 +181,8 @@ def _terms_array(terms: Sequence[OracleTerm]):
 
 def normal_equations(problem: OracleProblem, terms: Sequence[OracleTerm], n: int, active=None):
     """Per-(interval, antenna) JHJ and JHr blocks of term n
-    (Eq. jhj_entry_simplified, Eq. jhr_entry_simplified; Scenario 1 for phase terms).
+    (Eq. jhj_entry_simplified, Eq. jhr_entry_simplified; Scenario 1 for phase terms,
+    Scenario 2 for delay terms).
 
     Returns (jhj [n_tint, n_fint, n_ant, np, np], jhr [n_tint, n_fint, n_ant, np]) complex128.
     """

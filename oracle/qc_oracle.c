@@ -20,6 +20,10 @@
  *   - block update      g <- g + JHJ^{-1} JHr      (Eq. update, Algorithm 1)
  *   - phase-only terms  E = dv/dg dg/dphi, JHJ = 2 Re(E^H W E),
  *                       JHr = 2 Re(E^H W r)   (Scenario 1: Eq. jhj_case1, Eq. jhwr_case1)
+ *   - delay terms       gains evaluated per channel from per-interval parameters
+ *                       (phi_c, tau_c): g_c(nu) = exp(i (phi_c + 2 pi tau_c nu)); the
+ *                       sums run over every sample of the parameter interval
+ *                       (Scenario 2: Eq. jhj_case2, Eq. jhwr_case2)
  *   - chi^2 = r^H W r                                        (Eq. min)
  *
  * Readings of the paper taken here (each also listed in the design notes):
@@ -36,6 +40,12 @@
  *     averaging of the StefCal iteration.
  *   - A block with zero trace or reciprocal condition number below 1e-12 is
  *     not updated and its gain flag is set.
+ *   - Delay terms (the residual delay and phase term K of Section 5.1): two real
+ *     parameters per correlation, phi_c and tau_c, ordered (phi_X, tau_X,
+ *     phi_Y, tau_Y), a diagonal gain, and a frequency axis nu per channel in
+ *     units chosen by the caller (tau in the inverse unit).  Convergence uses
+ *     the gains: the relative Frobenius change over the antennas and the
+ *     channels of the interval.
  */
 #include <complex.h>
 #include <math.h>
@@ -44,7 +54,7 @@
 
 typedef double complex cplx;
 
-enum { OC_DIAG = 0, OC_FULL = 1, OC_PHASE = 2 };
+enum { OC_DIAG = 0, OC_FULL = 1, OC_PHASE = 2, OC_DELAY = 3 };
 enum { OC_OK = 0, OC_EINVAL = -1, OC_ENOMEM = -2 };
 
 typedef struct {
@@ -61,10 +71,12 @@ typedef struct {
     const int *t_map;            /* [n_time] -> time interval */
     const int *f_map;            /* [n_chan] -> freq interval */
     double *params;              /* DIAG/FULL: complex [tint][fint][ant][4] as (re,im) pairs;
-                                    PHASE: real [tint][fint][ant][2] */
+                                    PHASE: real [tint][fint][ant][2];
+                                    DELAY: real [tint][fint][ant][4] = (phi_X, tau_X, phi_Y, tau_Y) */
     signed char *gain_flags;     /* [tint][fint][ant], may be NULL */
     int solve, max_iter;
     double tol;
+    const double *chan_freq;     /* DELAY: [n_chan] frequency of each channel; else unused */
 } oc_term;
 
 typedef struct {
@@ -95,8 +107,17 @@ static void mat_herm(const cplx A[4], cplx out[4])
     memcpy(out, t, sizeof t);
 }
 
-/* Number of free parameters of a term: 2 (diag, phase) or 4 (full). */
-static int n_param(int type) { return type == OC_FULL ? 4 : 2; }
+/* Number of free parameters of a term: 2 (diag, phase) or 4 (full, delay). */
+static int n_param(int type) { return (type == OC_FULL || type == OC_DELAY) ? 4 : 2; }
+
+static const double TWO_PI = 6.283185307179586476925286766559;
+
+/* Diagonal gains of a delay term's parameters u at frequency nu. */
+static void delay_gains(const double *u, double nu, cplx *gx, cplx *gy)
+{
+    *gx = cexp(I * (u[0] + TWO_PI * u[1] * nu));
+    *gy = cexp(I * (u[2] + TWO_PI * u[3] * nu));
+}
 
 static size_t bin_index(const oc_term *T, int it, int jf) { return (size_t)it * T->n_fint + jf; }
 
@@ -107,6 +128,11 @@ static void term_jones(const oc_term *T, int n_ant, int t, int c, int a, cplx J[
     if (T->type == OC_PHASE) {
         const double *phi = T->params + 2 * b;
         J[0] = cexp(I * phi[0]); J[1] = 0; J[2] = 0; J[3] = cexp(I * phi[1]);
+        return;
+    }
+    if (T->type == OC_DELAY) {
+        delay_gains(T->params + 4 * b, T->chan_freq[c], &J[0], &J[3]);
+        J[1] = 0; J[2] = 0;
         return;
     }
     const double *g = T->params + 8 * b;
@@ -210,10 +236,18 @@ int oc_normal_equations(const oc_problem *P, const oc_term *terms, int n_terms, 
                 cplx Ef[4][4];
                 for (int row4 = 0; row4 < 4; ++row4) {
                     for (int col = 0; col < np; ++col) {
-                        if (T->type == OC_FULL) Ef[row4][col] = E[row4][col];
-                        else Ef[row4][col] = E[row4][free_cols_diag[col]];
-                        if (T->type == OC_PHASE)   /* dg/dphi = i g  (Scenario 1) */
-                            Ef[row4][col] *= I * G[free_cols_diag[col] == 0 ? 0 : 3];
+                        if (T->type == OC_FULL) {
+                            Ef[row4][col] = E[row4][col];
+                        } else if (T->type == OC_DELAY) {
+                            /* dg_c/dphi_c = i g_c,  dg_c/dtau_c = 2 pi nu i g_c  (Scenario 2) */
+                            const int dc = col < 2 ? 0 : 3;
+                            Ef[row4][col] = E[row4][dc] * I * G[dc];
+                            if (col & 1) Ef[row4][col] *= TWO_PI * T->chan_freq[c];
+                        } else {
+                            Ef[row4][col] = E[row4][free_cols_diag[col]];
+                            if (T->type == OC_PHASE)   /* dg/dphi = i g  (Scenario 1) */
+                                Ef[row4][col] *= I * G[free_cols_diag[col] == 0 ? 0 : 3];
+                        }
                     }
                 }
                 cplx *Ja = jhj + ((bin * P->n_ant) + a) * np * np;
@@ -231,7 +265,7 @@ int oc_normal_equations(const oc_problem *P, const oc_term *terms, int n_terms, 
             }
         }
     }
-    if (T->type == OC_PHASE) {   /* 2 Re(.) of Eq. jhj_case1 / Eq. jhwr_case1 */
+    if (T->type == OC_PHASE || T->type == OC_DELAY) {   /* 2 Re(.) of Eq. jhj_case1/2, Eq. jhwr_case1/2 */
         for (size_t i = 0; i < n_bins * P->n_ant * np * np; ++i) jhj[i] = 2.0 * creal(jhj[i]);
         for (size_t i = 0; i < n_bins * P->n_ant * np; ++i) jhr[i] = 2.0 * creal(jhr[i]);
     }
@@ -352,6 +386,25 @@ int oc_solve_term(const oc_problem *P, oc_term *terms, int n_terms, int n, const
             for (int a = 0; a < na; ++a) {
                 const size_t idx = b * na + a;
                 cplx g_old[4], g_new[4], dx[4];
+                if (T->type == OC_DELAY) {
+                    /* the gains change per channel: sum the change over the interval's channels */
+                    double u_old[4];
+                    memcpy(u_old, T->params + 4 * idx, sizeof u_old);
+                    int singular = oc_block_solve(np, jhj + idx * np * np, jhr + idx * np, dx);
+                    if (T->gain_flags) T->gain_flags[idx] = (signed char)singular;
+                    if (!singular)
+                        for (int e = 0; e < 4; ++e) T->params[4 * idx + e] += alpha * creal(dx[e]);
+                    const int jf = (int)(b % T->n_fint);
+                    for (int c = 0; c < P->n_chan; ++c) {
+                        if (T->f_map[c] != jf) continue;
+                        cplx ox, oy, nx, ny;
+                        delay_gains(u_old, T->chan_freq[c], &ox, &oy);
+                        delay_gains(T->params + 4 * idx, T->chan_freq[c], &nx, &ny);
+                        num += creal((nx - ox) * conj(nx - ox)) + creal((ny - oy) * conj(ny - oy));
+                        den += creal(nx * conj(nx)) + creal(ny * conj(ny));
+                    }
+                    continue;
+                }
                 term_gain_vec(T, idx, g_old);
                 int singular = oc_block_solve(np, jhj + idx * np * np, jhr + idx * np, dx);
                 if (T->gain_flags) T->gain_flags[idx] = (signed char)singular;

@@ -18,7 +18,13 @@
  *    paper's (gain_time, gain_freq, antenna, correlation) layout of
  *    Fig. xarray_dataset, one direction); a diagonal term ignores XY/YX and
  *    writes them as 0.  Phase-only terms use float32 [n_tint][n_fint][n_ant][2]
- *    holding (phi_X, phi_Y) in radians (Scenario 1 of Section 2.4).
+ *    holding (phi_X, phi_Y) in radians (Scenario 1 of Section 2.4).  Delay
+ *    terms use float32 [n_tint][n_fint][n_ant][4] holding (phi_X, tau_X,
+ *    phi_Y, tau_Y): the diagonal gain of correlation c at the frequency nu of
+ *    a channel is exp(i (phi_c + 2 pi tau_c nu)), so the gain changes from
+ *    channel to channel while its parameters are shared by every sample of a
+ *    solution interval (Scenario 2 of Section 2.4; the residual delay and
+ *    phase term K of Section 5.1).
  *  - t_map [n_time] and f_map [n_chan] map each data time / channel to the
  *    term's solution interval (Section 4.3: "interval mappings").  Values
  *    must lie in [0, n_tint) / [0, n_fint) and f_map must be non-decreasing
@@ -52,6 +58,7 @@ extern "C" {
 #define QC_TERM_DIAG   0      /* diagonal complex gain, free parameters g_XX, g_YY           */
 #define QC_TERM_FULL   1      /* full 2x2 complex gain, free parameters all four entries     */
 #define QC_TERM_PHASE  2      /* phase-only diagonal gain exp(i phi_X), exp(i phi_Y)         */
+#define QC_TERM_DELAY  3      /* delay and phase: exp(i (phi_c + 2 pi tau_c nu)) per channel */
 
 #define QC_MEM_HOST    0
 #define QC_MEM_DEVICE  1
@@ -108,6 +115,19 @@ typedef struct {
  *   reduce      : 1 = the term's intervals span several processes; the
  *                 partial normal equations are summed with the options'
  *                 allreduce callback before every update.
+ *   chan_freq   : QC_TERM_DELAY only (NULL otherwise): HOST float64 [n_chan],
+ *                 the frequency of every channel, finite, in a unit of the
+ *                 caller's choice; tau is in the inverse unit (GHz and ns keep
+ *                 the 4x4 normal-equation blocks well conditioned; with Hz the
+ *                 tau columns are ~1e9 times the phi columns and every block
+ *                 fails the conditioning test).  A delay term's 4x4 real block
+ *                 over (phi_X, tau_X, phi_Y, tau_Y) sums 2 Re(E^H W E) over
+ *                 every sample of the interval (Eq. jhj_case2, Eq. jhwr_case2);
+ *                 convergence uses the gains over the interval's channels.
+ *                 Delay terms are accepted by qc_solve and qc_residual; a
+ *                 chain holding one is solved with the accumulate kernels'
+ *                 per-channel bins (one diagonal bin per time interval and
+ *                 channel), then reduced over the interval's channels.
  */
 typedef struct {
     int32_t type, n_tint, n_fint;
@@ -120,6 +140,7 @@ typedef struct {
     double tol;
     int32_t memory;
     int32_t reduce;
+    const double *chan_freq;
 } qc_term;
 
 /*

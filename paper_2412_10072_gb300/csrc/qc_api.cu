@@ -386,7 +386,13 @@ int qc_ctx::validate_terms(const qc_term *terms, int n_terms, bool need_solve_fi
     if (n_terms < 1 || n_terms > QC_MAX_TERMS) return fail(QC_EINVAL, "n_terms must be in [1, QC_MAX_TERMS]");
     for (int j = 0; j < n_terms; ++j) {
         const qc_term &t = terms[j];
-        if (t.type < 0 || t.type > 2) return fail(QC_EINVAL, "unknown term type");
+        if (t.type < 0 || t.type > 3) return fail(QC_EINVAL, "unknown term type");
+        if (t.type == QC_TERM_DELAY) {
+            if (!t.chan_freq) return fail(QC_EINVAL, "a delay term needs chan_freq");
+            for (int i = 0; i < n_chan; ++i)
+                if (!std::isfinite(t.chan_freq[i])) return fail(QC_EINVAL, "chan_freq must be finite");
+            if ((long long)t.n_tint * n_chan * n_ant > (1LL << 31)) return fail(QC_EINVAL, "delay term too large");
+        }
         if (t.n_tint < 1 || t.n_fint < 1) return fail(QC_EINVAL, "n_tint and n_fint must be >= 1");
         if ((long long)t.n_tint * t.n_fint * n_ant > (1LL << 31)) return fail(QC_EINVAL, "term too large");
         if (!t.t_map || !t.f_map || !t.gains) return fail(QC_EINVAL, "t_map, f_map and gains are required");
@@ -403,6 +409,61 @@ int qc_ctx::validate_terms(const qc_term *terms, int n_terms, bool need_solve_fi
         }
     }
     return QC_OK;
+}
+
+// The kernels' view of the chain: a delay term becomes a diagonal term with one bin per
+// (time interval, channel) and the identity channel map, its table evaluated at every
+// channel from the interval's parameters (the channel ranges, maps and frequencies of its
+// intervals are uploaded here).  Other terms are unchanged.
+int qc_ctx::expand_terms(const qc_term *terms, int n_terms, std::vector<qc_term> &xt, cudaStream_t st)
+{
+    qc_ctx *c = this;
+    xt.assign(terms, terms + n_terms);
+    if ((int)fid.size() != n_chan) {
+        fid.resize(n_chan);
+        for (int i = 0; i < n_chan; ++i) fid[i] = i;
+    }
+    for (int j = 0; j < n_terms; ++j) {
+        delay[j] = terms[j].type == QC_TERM_DELAY;
+        if (!delay[j]) continue;
+        const qc_term &t = terms[j];
+        TermBufs &B = tb[j];
+        B.hfr.assign(t.n_fint, make_int2(-1, -2));
+        for (int ch = 0; ch < n_chan; ++ch) {
+            int2 &r = B.hfr[t.f_map[ch]];
+            if (r.x < 0) r.x = ch;
+            r.y = ch;
+        }
+        int rc;
+        if ((rc = ensure(B.dfmap, nbytes<int>(std::max(1, n_chan))))) return rc;
+        if ((rc = ensure(B.dfr, nbytes<int2>(t.n_fint)))) return rc;
+        if ((rc = ensure(B.dnu, nbytes<double>(std::max(1, n_chan))))) return rc;
+        if (n_chan) {
+            CK(cudaMemcpyAsync(B.dfmap.ptr, t.f_map, nbytes<int>(n_chan), cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(B.dnu.ptr, t.chan_freq, nbytes<double>(n_chan), cudaMemcpyHostToDevice, st));
+        }
+        CK(cudaMemcpyAsync(B.dfr.ptr, B.hfr.data(), nbytes<int2>(t.n_fint), cudaMemcpyHostToDevice, st));
+        xt[j].type = QC_TERM_DIAG;
+        xt[j].n_fint = n_chan;
+        xt[j].f_map = fid.data();
+    }
+    return QC_OK;
+}
+
+DelayArgs qc_ctx::delay_args(int j, const qc_term &xt_j)
+{
+    TermBufs &B = tb[j];
+    DelayArgs d;
+    d.n_tint = xt_j.n_tint;
+    d.n_fint = (int)B.hfr.size();
+    d.n_ant = n_ant;
+    d.n_chan = n_chan;
+    d.fmap = (const int *)B.dfmap.ptr;
+    d.frange = (const int2 *)B.dfr.ptr;
+    d.nu = (const double *)B.dnu.ptr;
+    d.params = (double *)B.params.ptr;
+    d.tab = (float4 *)B.tab.ptr;
+    return d;
 }
 
 // Upload maps and gains of every term; fills chain (device descriptors).
@@ -426,15 +487,33 @@ int qc_ctx::stage_terms(const qc_term *terms, int n_terms, cudaStream_t st, Chai
         B.hmaps.assign(t.t_map, t.t_map + n_time);
         B.hmaps.insert(B.hmaps.end(), t.f_map, t.f_map + n_chan);
         CK(cudaMemcpyAsync(B.maps.ptr, B.hmaps.data(), nbytes<int>(n_time + n_chan), cudaMemcpyHostToDevice, st));
-        const void *src = t.gains;
-        if (t.memory == QC_MEM_HOST) {
-            CK(cudaMemcpyAsync(B.stage.ptr, t.gains, nent * (t.type == 2 ? 8 : 32), cudaMemcpyHostToDevice, st));
-            src = B.stage.ptr;
+        if (delay[j]) {
+            // parameters [n_tint][n_fint][n_ant][4] (float32) -> FP64 master; table per channel
+            const DelayArgs da = delay_args(j, t);
+            const size_t nvals = (size_t)da.n_tint * da.n_fint * n_ant * 4;
+            const void *src = t.gains;
+            if (t.memory == QC_MEM_HOST) {
+                CK(cudaMemcpyAsync(B.stage.ptr, t.gains, nbytes<float>(nvals), cudaMemcpyHostToDevice, st));
+                src = B.stage.ptr;
+            }
+            delay_params_in_kernel<<<grid_for((long)nvals, 256, sm_count), 256, 0, st>>>((long)nvals, (const float *)src,
+                                                                                        da.params);
+            CK(cudaGetLastError());
+            delay_tab_kernel<<<grid_for((long)nent, 256, sm_count), 256, 0, st>>>(da);
+            CK(cudaGetLastError());
+            launches += 2;
+        } else {
+            const void *src = t.gains;
+            if (t.memory == QC_MEM_HOST) {
+                CK(cudaMemcpyAsync(B.stage.ptr, t.gains, nent * (t.type == 2 ? 8 : 32), cudaMemcpyHostToDevice, st));
+                src = B.stage.ptr;
+            }
+            gains_in_kernel<<<grid_for((long)nent, 256, sm_count), 256, 0, st>>>(t.type, t.n_tint, t.n_fint, n_ant, src,
+                                                                                (double *)B.params.ptr,
+                                                                                (float4 *)B.tab.ptr);
+            CK(cudaGetLastError());
+            ++launches;
         }
-        gains_in_kernel<<<grid_for((long)nent, 256, sm_count), 256, 0, st>>>(t.type, t.n_tint, t.n_fint, n_ant, src,
-                                                                            (double *)B.params.ptr, (float4 *)B.tab.ptr);
-        CK(cudaGetLastError());
-        ++launches;
         DevTerm &d = chain.t[j];
         d.type = t.type;
         d.n_tint = t.n_tint;
@@ -477,8 +556,10 @@ extern "C" int qc_residual(qc_ctx *c, const qc_term *terms, int32_t n_terms, voi
     int rc = c->validate_terms(terms, n_terms, false);
     if (rc) return rc;
     cudaStream_t st = c->own_stream;
+    std::vector<qc_term> xt;
+    if ((rc = c->expand_terms(terms, n_terms, xt, st))) return rc;
     Chain chain;
-    if ((rc = c->stage_terms(terms, n_terms, st, chain))) return rc;
+    if ((rc = c->stage_terms(xt.data(), n_terms, st, chain))) return rc;
     if ((rc = c->ensure(c->scalars, 64))) return rc;
     double *d_chi2 = (double *)c->scalars.ptr;
     const size_t n_vis = (size_t)c->n_row * c->n_chan;
@@ -563,8 +644,10 @@ extern "C" int qc_solve(qc_ctx *c, qc_term *terms, int32_t n_terms, const qc_opt
     cudaEvent_t ev0, ev1;
     if ((rc = c->get_event(0, ev0)) || (rc = c->get_event(1, ev1))) return rc;
     CK(cudaEventRecord(ev0, st));
+    std::vector<qc_term> xt;     // the kernels' view of the terms (delay terms per channel)
+    if ((rc = c->expand_terms(terms, n_terms, xt, st))) return rc;
     Chain chain;
-    if ((rc = c->stage_terms(terms, n_terms, st, chain))) return rc;
+    if ((rc = c->stage_terms(xt.data(), n_terms, st, chain))) return rc;
     if ((rc = c->ensure(c->scalars, 64))) return rc;
     unsigned long long *d_counters = (unsigned long long *)c->scalars.ptr;   // [0] vis_iters, [1] bytes
     double *d_chi2 = (double *)c->scalars.ptr + 4;
@@ -579,7 +662,7 @@ extern "C" int qc_solve(qc_ctx *c, qc_term *terms, int32_t n_terms, const qc_opt
     const long long b_unflag = 32 + (c->m16 ? 16 : 32) + 16;
     for (int j = 0; j < n_terms; ++j) {
         if (!terms[j].solve) continue;
-        const qc_term &t = terms[j];
+        const qc_term &t = xt[j];
         TermBufs &B = c->tb[j];
         const size_t nb = term_nbins(t);
         const size_t KG = t.type == 1 ? KG_FULL : KG_DIAG;
@@ -619,7 +702,7 @@ extern "C" int qc_solve(qc_ctx *c, qc_term *terms, int32_t n_terms, const qc_opt
             int it_max = 0;
             double acc_ms = 0;
             long long acc_launches = 0;
-            if ((rc = c->solve_term(terms, n_terms, n, chain, o, st, &it_max, &acc_ms, &acc_launches))) return rc;
+            if ((rc = c->solve_term(xt.data(), n_terms, n, chain, o, st, &it_max, &acc_ms, &acc_launches))) return rc;
             S.acc_ms += acc_ms;
             S.acc_launches += acc_launches;
             if (epoch == o->n_epochs - 1) n_iter_max = std::max(n_iter_max, it_max);
@@ -635,10 +718,14 @@ extern "C" int qc_solve(qc_ctx *c, qc_term *terms, int32_t n_terms, const qc_opt
         qc_term &t = terms[j];
         TermBufs &B = c->tb[j];
         const size_t nb = term_nbins(t), nent = nb * c->n_ant;
-        const size_t gbytes = nent * (t.type == 2 ? 8 : 32);
+        const size_t gbytes = nent * (t.type == 2 ? 8 : (t.type == QC_TERM_DELAY ? 16 : 32));
         void *dst = t.memory == QC_MEM_DEVICE ? t.gains : B.stage.ptr;
-        gains_out_kernel<<<grid_for((long)nent, 256, c->sm_count), 256, 0, st>>>(t.type, (long)nent,
-                                                                               (const double *)B.params.ptr, dst);
+        if (t.type == QC_TERM_DELAY)
+            delay_params_out_kernel<<<grid_for((long)nent * 4, 256, c->sm_count), 256, 0, st>>>(
+                (long)nent * 4, (const double *)B.params.ptr, (float *)dst);
+        else
+            gains_out_kernel<<<grid_for((long)nent, 256, c->sm_count), 256, 0, st>>>(t.type, (long)nent,
+                                                                                   (const double *)B.params.ptr, dst);
         CK(cudaGetLastError());
         ++c->launches;
         if (t.memory == QC_MEM_HOST) {
@@ -899,6 +986,21 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
     ua.tol = t.tol;
     int *cnt = (int *)B.cnt.ptr;
     const int upd_block = n_ant >= 128 ? 128 : (n_ant > 32 ? 64 : 32);
+    // delay terms: the update reduces the channel bins of each parameter interval
+    DelayUpdArgs dua;
+    memset(&dua, 0, sizeof dua);
+    if (delay[n]) {
+        dua.d = delay_args(n, t);
+        dua.acc = ua.acc;
+        dua.gain_flags = ua.gain_flags;
+        dua.iters = ua.iters;
+        dua.active = ua.active;
+        dua.bin_nvis = ua.bin_nvis;
+        dua.bin_nbytes = ua.bin_nbytes;
+        dua.vis_iters = ua.vis_iters;
+        dua.acc_bytes = ua.acc_bytes;
+        dua.tol = ua.tol;
+    }
 
     const int max_iter = t.max_iter;
     for (int k = 0; k < 2 * max_iter; ++k) { cudaEvent_t ev; if ((rc = get_event(2 + k, ev))) return rc; }
@@ -940,7 +1042,15 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
                                                                : (o->damping > 0 ? o->damping : 1.0);
             ua.n_active_prev = cnt + (k - 1);
             ua.n_active_next = cnt + k;
-            update_kernel<<<nb, upd_block, 0, st>>>(ua);
+            if (delay[n]) {
+                dua.k = k;
+                dua.alpha = ua.alpha;
+                dua.n_active_prev = ua.n_active_prev;
+                dua.n_active_next = ua.n_active_next;
+                delay_update_kernel<<<dua.d.n_tint * dua.d.n_fint, upd_block, 0, st>>>(dua);
+            } else {
+                update_kernel<<<nb, upd_block, 0, st>>>(ua);
+            }
             CK(cudaGetLastError());
         }
         return QC_OK;

@@ -1,0 +1,178 @@
+// qc_delay.cuh -- delay terms (QC_TERM_DELAY): gains parameterised per solution interval by
+// a phase and a delay per correlation, evaluated at every channel,
+//   g_c(nu) = exp(i (phi_c + 2 pi tau_c nu)),  parameters u = (phi_X, tau_X, phi_Y, tau_Y)
+// (Scenario 2 of Section 2.4: each gain g_{n,s,a} is tied to a parameter u_{n,a} and the
+// normal equations sum over samples, Eq. jhj_case2 and Eq. jhwr_case2).
+//
+// The accumulate kernels see a delay term as a diagonal term with one bin per (time
+// interval, channel): its Jones table is evaluated at every channel, and they form the
+// complex blocks JHJ_g, JHr_g of the diagonal entries per channel bin.  Within one channel
+// bin the derivative dg/du is constant, so the chain rule of Eq. cp_jacobian applies to
+// the per-channel sums exactly:
+//   JHJ_u = sum over channels of 2 Re(J2^H JHJ_g J2),  JHr_u = sum of 2 Re(J2^H JHr_g),
+//   J2 = d(g_X, g_Y)/du = [[i g_X, 2 pi nu i g_X, 0, 0], [0, 0, i g_Y, 2 pi nu i g_Y]].
+// delay_update_kernel forms these 4x4 real blocks in FP64, solves them, updates the
+// parameters, re-evaluates the channel table and tests convergence on the gains.
+#pragma once
+#include "qc_kernels.cuh"
+
+namespace qc {
+
+constexpr double DELAY_TWO_PI = 6.283185307179586476925286766559;
+
+struct DelayArgs {
+    int n_tint, n_fint, n_ant, n_chan;   // n_fint: parameter intervals along frequency
+    const int *fmap;          // [n_chan] parameter interval of each channel
+    const int2 *frange;       // [n_fint] first and last channel of each interval (x < 0: none)
+    const double *nu;         // [n_chan] channel frequencies
+    double *params;           // FP64 master [n_tint][n_fint][n_ant][4]
+    float4 *tab;              // FP32 channel table [n_tint][n_ant][n_chan]: (g_X, g_Y)
+};
+
+// float32 parameters [n_tint][n_fint][n_ant][4] -> FP64 master copy
+static __global__ void delay_params_in_kernel(long n, const float *src, double *params)
+{
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        params[i] = (double)src[i];
+}
+
+__device__ __forceinline__ double2 delay_gain(double phi, double tau, double w)
+{
+    double s, c;
+    sincos(phi + tau * w, &s, &c);
+    return make_double2(c, s);
+}
+
+// channel table from the FP64 parameters, one entry per (time interval, antenna, channel)
+static __global__ void delay_tab_kernel(const DelayArgs a)
+{
+    const long n = (long)a.n_tint * a.n_ant * a.n_chan;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % a.n_chan);
+        const long ta = i / a.n_chan;
+        const int ant = (int)(ta % a.n_ant), tint = (int)(ta / a.n_ant);
+        const double *u = a.params + (((size_t)tint * a.n_fint + a.fmap[c]) * a.n_ant + ant) * 4;
+        const double w = DELAY_TWO_PI * a.nu[c];
+        const double2 gx = delay_gain(u[0], u[1], w), gy = delay_gain(u[2], u[3], w);
+        a.tab[i] = make_float4((float)gx.x, (float)gx.y, (float)gy.x, (float)gy.y);
+    }
+}
+
+// FP64 master -> float32 parameters in the public layout
+static __global__ void delay_params_out_kernel(long n, const double *params, float *dst)
+{
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        dst[i] = (float)params[i];
+}
+
+struct DelayUpdArgs {
+    DelayArgs d;
+    double *acc;              // diagonal accumulators [n_tint * n_chan][n_ant][KG_DIAG] (read, then zeroed)
+    int8_t *gain_flags;       // [n_tint][n_fint][n_ant]
+    int *iters;               // [n_tint][n_fint]
+    uint8_t *active;          // [n_tint * n_chan] channel bins
+    const int *n_active_prev; // intervals active entering this iteration (0: nothing to do)
+    int *n_active_next;       // incremented for every interval still active after it
+    const long long *bin_nvis, *bin_nbytes;   // per channel bin
+    unsigned long long *vis_iters, *acc_bytes;
+    int k;                    // iteration (1-based)
+    double alpha, tol;
+};
+
+// One block per parameter interval (time interval x frequency interval), threads over antennas.
+static __global__ void __launch_bounds__(128) delay_update_kernel(const DelayUpdArgs u)
+{
+    if (*u.n_active_prev == 0) return;
+    const DelayArgs &d = u.d;
+    const int bin = blockIdx.x;
+    const int tint = bin / d.n_fint, fu = bin % d.n_fint;
+    const int2 fr = d.frange[fu];
+    const size_t cb0 = (size_t)tint * d.n_chan;            // first channel bin of the time interval
+    if (fr.x < 0) {
+        // no channel maps to this interval: no data, the parameters stay as they are
+        if (u.k == 1) {
+            for (int ant = threadIdx.x; ant < d.n_ant; ant += blockDim.x)
+                if (u.gain_flags) u.gain_flags[(size_t)bin * d.n_ant + ant] = 1;
+            if (threadIdx.x == 0 && u.iters) u.iters[bin] = 1;
+        }
+        return;
+    }
+    if (!u.active[cb0 + fr.x]) return;
+    double num = 0, den = 0;
+    for (int ant = threadIdx.x; ant < d.n_ant; ant += blockDim.x) {
+        double *P = d.params + ((size_t)bin * d.n_ant + ant) * 4;
+        const double u0 = P[0], u1 = P[1], u2 = P[2], u3 = P[3];
+        double2 M[4][4], b[4], x[4];
+        for (int i = 0; i < 4; ++i) {
+            b[i] = make_double2(0.0, 0.0);
+            for (int j = 0; j < 4; ++j) M[i][j] = make_double2(0.0, 0.0);
+        }
+        for (int c = fr.x; c <= fr.y; ++c) {
+            double *A = u.acc + ((cb0 + c) * d.n_ant + ant) * KG_DIAG;
+            const double h00 = A[0], h11 = A[1];
+            const double2 h01 = make_double2(A[2], A[3]), j0 = make_double2(A[4], A[5]), j1 = make_double2(A[6], A[7]);
+            for (int i = 0; i < KG_DIAG; ++i) A[i] = 0.0;
+            const double w = DELAY_TWO_PI * d.nu[c];
+            const double2 gx = delay_gain(u0, u1, w), gy = delay_gain(u2, u3, w);
+            const double f[2] = { 1.0, w };
+            // Re(conj(g_X) JHJ_g[X][Y] g_Y): the X-Y coupling (zero without a left factor)
+            const double2 t = make_double2(gx.x * h01.x + gx.y * h01.y, gx.x * h01.y - gx.y * h01.x);
+            const double xy = t.x * gy.x - t.y * gy.y;
+            // Im(conj(g_c) JHr_g[c]) of each correlation
+            const double rx = gx.x * j0.y - gx.y * j0.x, ry = gy.x * j1.y - gy.y * j1.x;
+            for (int i = 0; i < 2; ++i) {
+                for (int j = 0; j < 2; ++j) {
+                    M[i][j].x += 2.0 * h00 * f[i] * f[j];
+                    M[2 + i][2 + j].x += 2.0 * h11 * f[i] * f[j];
+                    M[i][2 + j].x += 2.0 * xy * f[i] * f[j];
+                    M[2 + j][i].x += 2.0 * xy * f[i] * f[j];
+                }
+                b[i].x += 2.0 * rx * f[i];
+                b[2 + i].x += 2.0 * ry * f[i];
+            }
+        }
+        const int singular = block_solve<4>(M, b, x);
+        if (!singular)
+            for (int e = 0; e < 4; ++e) P[e] += u.alpha * x[e].x;
+        if (u.gain_flags) u.gain_flags[(size_t)bin * d.n_ant + ant] = (int8_t)singular;
+        // re-evaluate the channel table; relative change of the gains over the interval's channels
+        for (int c = fr.x; c <= fr.y; ++c) {
+            const double w = DELAY_TWO_PI * d.nu[c];
+            const double2 ox = delay_gain(u0, u1, w), oy = delay_gain(u2, u3, w);
+            const double2 nx = delay_gain(P[0], P[1], w), ny = delay_gain(P[2], P[3], w);
+            d.tab[((size_t)tint * d.n_ant + ant) * d.n_chan + c] =
+                make_float4((float)nx.x, (float)nx.y, (float)ny.x, (float)ny.y);
+            num += (nx.x - ox.x) * (nx.x - ox.x) + (nx.y - ox.y) * (nx.y - ox.y) + (ny.x - oy.x) * (ny.x - oy.x) +
+                   (ny.y - oy.y) * (ny.y - oy.y);
+            den += nx.x * nx.x + nx.y * nx.y + ny.x * ny.x + ny.y * ny.y;
+        }
+    }
+    __shared__ double s_num[4], s_den[4];
+    for (int dd = 16; dd > 0; dd >>= 1) {
+        num += __shfl_down_sync(0xffffffffu, num, dd);
+        den += __shfl_down_sync(0xffffffffu, den, dd);
+    }
+    const int wi = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { s_num[wi] = num; s_den[wi] = den; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tn = 0, td = 0;
+        for (int i = 0; i < (int)(blockDim.x + 31) / 32; ++i) { tn += s_num[i]; td += s_den[i]; }
+        const double delta = td > 0 ? sqrt(tn / td) : 0.0;
+        if (u.iters) u.iters[bin] = u.k;
+        unsigned long long nv = 0, nb = 0;
+        for (int c = fr.x; c <= fr.y; ++c) {
+            nv += (unsigned long long)u.bin_nvis[cb0 + c];
+            nb += (unsigned long long)u.bin_nbytes[cb0 + c];
+        }
+        atomicAdd(u.vis_iters, nv);
+        atomicAdd(u.acc_bytes, nb);
+        if (delta < u.tol) {
+            for (int c = fr.x; c <= fr.y; ++c) u.active[cb0 + c] = 0;
+        } else {
+            atomicAdd(u.n_active_next, 1);
+        }
+    }
+}
+
+} // namespace qc

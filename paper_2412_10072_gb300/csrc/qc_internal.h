@@ -7,6 +7,7 @@
 
 #include "../../include/qc.h"
 #include "qc_stream.cuh"
+#include "qc_delay.cuh"
 
 struct Buf {
     void *ptr = nullptr;
@@ -33,6 +34,10 @@ struct TermBufs {
     Buf rt_scale;  // float [n_row] its FP16 model scales
     Buf fmap2;     // int2 [n_chan] {f_map of this term, f_map of the other term}
     Buf units;     // int: unit counter of the streaming kernel's strip tiles
+    Buf dfmap;     // delay terms: int [n_chan] parameter interval of each channel
+    Buf dfr;       // delay terms: int2 [n_fint] first and last channel of each interval
+    Buf dnu;       // delay terms: double [n_chan] channel frequencies
+    std::vector<int2> hfr;    // host copy of dfr (its size is the term's n_fint)
     cudaGraphExec_t exec = nullptr;
     bool graph_valid = false;
 };
@@ -91,6 +96,12 @@ struct qc_ctx {
     int get_event(int i, cudaEvent_t &ev);
     bool configured(const void *fn) const;
     int validate_terms(const qc_term *terms, int n_terms, bool need_solve_fields);
+    // delay terms of the current call (by chain position) and the view the kernels work on:
+    // a diagonal term with one bin per (time interval, channel) and the identity channel map
+    bool delay[QC_MAX_TERMS] = {};
+    std::vector<int> fid;             // identity channel map [n_chan]
+    int expand_terms(const qc_term *terms, int n_terms, std::vector<qc_term> &xt, cudaStream_t st);
+    qc::DelayArgs delay_args(int j, const qc_term &xt_j);
     int stage_terms(const qc_term *terms, int n_terms, cudaStream_t st, qc::Chain &chain);
     qc::Data data_desc() const;
     int run_residual(const qc::Chain &chain, float4 *dres, double *d_chi2, cudaStream_t st);

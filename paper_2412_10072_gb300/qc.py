@@ -18,10 +18,10 @@ import numpy as np
 from . import build as _build
 
 QC_OK, QC_EINVAL, QC_ENOMEM, QC_ECUDA, QC_ETIMEOUT, QC_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
-QC_TERM_DIAG, QC_TERM_FULL, QC_TERM_PHASE = 0, 1, 2
+QC_TERM_DIAG, QC_TERM_FULL, QC_TERM_PHASE, QC_TERM_DELAY = 0, 1, 2, 3
 QC_MEM_HOST, QC_MEM_DEVICE = 0, 1
 QC_DAMP_CONST, QC_DAMP_ALTERNATE = 0, 1
-KINDS = {"diag": QC_TERM_DIAG, "full": QC_TERM_FULL, "phase": QC_TERM_PHASE}
+KINDS = {"diag": QC_TERM_DIAG, "full": QC_TERM_FULL, "phase": QC_TERM_PHASE, "delay": QC_TERM_DELAY}
 
 _lib = None
 _lock = threading.Lock()
@@ -44,7 +44,7 @@ class _Term(C.Structure):
     _fields_ = [("type", C.c_int32), ("n_tint", C.c_int32), ("n_fint", C.c_int32), ("t_map", C.c_void_p),
                 ("f_map", C.c_void_p), ("gains", C.c_void_p), ("gain_flags", C.c_void_p), ("iters", C.c_void_p),
                 ("solve", C.c_int32), ("max_iter", C.c_int32), ("tol", C.c_double), ("memory", C.c_int32),
-                ("reduce", C.c_int32)]
+                ("reduce", C.c_int32), ("chan_freq", C.c_void_p)]
 
 
 ALLREDUCE_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p)
@@ -133,21 +133,30 @@ def _complex64(a):
 class Term:
     """One Jones term (see qc_term in include/qc.h).
 
-    gains: numpy complex [n_tint][n_fint][n_ant][4] (diag/full) or float [..][2] (phase), or a CUDA
-    tensor of the same layout (complex64 / float32).  After a solve the solved values are in
-    ``self.gains`` (host arrays are updated in place).
+    gains: numpy complex [n_tint][n_fint][n_ant][4] (diag/full), float [..][2] (phase) or float
+    [..][4] = (phi_X, tau_X, phi_Y, tau_Y) (delay, with ``chan_freq`` [n_chan], the frequency of
+    every channel), or a CUDA tensor of the same layout (complex64 / float32).  After a solve the
+    solved values are in ``self.gains`` (host arrays are updated in place).
     """
 
     def __init__(self, kind: str, t_map, f_map, n_tint: int, n_fint: int, n_ant: int, gains=None,
-                 solve: bool = True, max_iter: int = 20, tol: float = 1e-6, reduce: bool = False):
+                 solve: bool = True, max_iter: int = 20, tol: float = 1e-6, reduce: bool = False,
+                 chan_freq=None):
         self.kind = kind
         self.type = KINDS[kind]
+        self.chan_freq = None
+        if kind == "delay":
+            if chan_freq is None:
+                raise ValueError("a delay term needs chan_freq")
+            self.chan_freq = np.ascontiguousarray(chan_freq, dtype=np.float64)
         self.t_map = _host(t_map, np.int32)
         self.f_map = _host(f_map, np.int32)
         self.n_tint, self.n_fint, self.n_ant = int(n_tint), int(n_fint), int(n_ant)
         if gains is None:
             if kind == "phase":
                 gains = np.zeros((n_tint, n_fint, n_ant, 2), dtype=np.float32)
+            elif kind == "delay":
+                gains = np.zeros((n_tint, n_fint, n_ant, 4), dtype=np.float32)
             else:
                 gains = np.zeros((n_tint, n_fint, n_ant, 4), dtype=np.complex64)
                 gains[..., 0] = 1
@@ -160,7 +169,7 @@ class Term:
             self.gain_flags = torch.zeros((n_tint, n_fint, n_ant), dtype=torch.int8, device=dev)
             self.iters = torch.zeros((n_tint, n_fint), dtype=torch.int32, device=dev)
         else:
-            dt = np.float32 if kind == "phase" else np.complex64
+            dt = np.float32 if kind in ("phase", "delay") else np.complex64
             self.gains = np.array(gains, dtype=dt, copy=True, order="C")
             self.memory = QC_MEM_HOST
             self.gain_flags = np.zeros((n_tint, n_fint, n_ant), dtype=np.int8)
@@ -174,7 +183,7 @@ class Term:
     def _c(self) -> _Term:
         return _Term(self.type, self.n_tint, self.n_fint, _addr(self.t_map), _addr(self.f_map), _addr(self.gains),
                      _addr(self.gain_flags), _addr(self.iters), int(self.solve), self.max_iter, self.tol,
-                     self.memory, int(self.reduce))
+                     self.memory, int(self.reduce), _addr(self.chan_freq))
 
 
 def _terms_array(terms: Sequence[Term]):

@@ -46,10 +46,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="plain", choices=["plain", "mixed", "batched", "warmstart"],
+    ap.add_argument("--workload", default="plain", choices=["plain", "mixed", "batched", "warmstart", "delay"],
                     help="plain: the large two-term solve; mixed: the same with FP16 model storage; batched: 4096 "
                          "independent intervals in one persistent launch; warmstart: the batched solve at 64 "
-                         "antennas from cold, previous-interval and network starts")
+                         "antennas from cold, previous-interval and network starts; delay: a delay and phase "
+                         "term per integration over all channels on the large observation")
     ap.add_argument("--mixed", action="store_true", help="same as --workload mixed")
     ap.add_argument("--n-prob", type=int, default=4096, help="problems of the batched / warmstart workloads")
     ap.add_argument("--looped", type=int, default=256, help="problems timed one by one for the comparison")
@@ -277,6 +278,8 @@ def main():
         return run_batched(args)
     if args.workload == "warmstart" and args.impl == "ours":
         return run_warmstart(args)
+    if args.workload == "delay" and args.impl == "ours":
+        return run_delay(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -428,6 +431,95 @@ def main():
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# delay term K (Scenario 2): phase and delay per correlation over all channels per integration
+# ---------------------------------------------------------------------------
+
+DELAY_WORKLOAD = ("delay term K: 64 ant, 300 t x 512 ch, (phi, tau) per correlation over all channels of each "
+                  "integration (300 intervals), channels 0.9-1.7 GHz, 1 epoch")
+
+
+def delay_terms(qc, n_time, n_chan, n_ant, max_iter, nu):
+    import numpy as np
+    return [qc.Term("delay", np.arange(n_time, dtype=np.int32), np.zeros(n_chan, np.int32), n_time, 1, n_ant,
+                    chan_freq=nu, max_iter=max_iter, tol=1e-6)]
+
+
+def run_delay(args):
+    """The delay term solved alone on the large observation (data of the plain workload), device-timed;
+    the oracle on the first 2 integrations as the CPU baseline."""
+    import numpy as np
+    import torch
+    import oracle as O
+    from paper_2412_10072_gb300 import qc, synth
+
+    torch.cuda.set_device(0)
+    setup = synth.plain_large_setup(seed=1, n_ant=args.n_ant, n_time=args.n_time, n_chan=args.n_chan,
+                                    flag_row_frac=0.1, n_src=50)
+    obs = synth.make_observation_device(setup, noise=0.05, noise_seed=1000, device="cuda:0")
+    torch.cuda.synchronize()
+    nu = np.linspace(0.9, 1.7, args.n_chan)
+    stream = torch.cuda.Stream()
+    solver = qc.Solver(obs["data"], obs["model"], obs["weight"], obs["flag"], setup.ant1, setup.ant2,
+                       setup.time_idx, setup.n_ant, setup.n_time)
+
+    def step():
+        return solver.solve(delay_terms(qc, setup.n_time, args.n_chan, setup.n_ant, args.max_iter, nu),
+                            stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(0)
+        clocks.start()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        stats = [step() for _ in range(args.steps)]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        clock_info = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    vis_iters = sum(s.vis_iters for s in stats)
+    acc_ms = sum(s.acc_ms for s in stats)
+    acc_launches = sum(s.acc_launches for s in stats)
+    peaks, peak_src = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = (81 * vis_iters / (acc_ms / 1000.0)) / 1e9 if acc_ms > 0 else None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": (achieved / hbm) if achieved else None, "traffic": None, "bytes_per_vis_iteration": 81,
+                "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured"
+                else "fallback 6.8 TB/s",
+                "kernel": "acc_stream_kernel (per-channel diagonal bins of the delay term)",
+                "algorithmic_bytes_per_launch": 81 * vis_iters / max(1, acc_launches),
+                "launch_ms_mean": acc_ms / max(1, acc_launches), "acc_share_of_step": acc_ms / ms if ms else None}
+    cpu = None
+    if not args.no_cpu_baseline:
+        rows = 2 * (setup.n_ant * (setup.n_ant - 1) // 2)
+        P = O.OracleProblem(obs["data"][:rows].cpu().numpy(), obs["model"][:rows].cpu().numpy(),
+                            obs["weight"][:rows].cpu().numpy(), obs["flag"][:rows].cpu().numpy(),
+                            setup.ant1[:rows], setup.ant2[:rows], setup.time_idx[:rows], setup.n_ant, 2)
+        K = O.OracleTerm("delay", np.arange(2, dtype=np.int32), np.zeros(args.n_chan, np.int32), 2, 1, setup.n_ant,
+                         chan_freq=nu, max_iter=2, tol=1e-6)
+        t0 = time.perf_counter()
+        its = O.solve(P, [K])[0]
+        dt = time.perf_counter() - t0
+        vi = int(rows * args.n_chan * its.astype(np.int64).sum() / its.size)
+        cpu = {"value": vi / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"first 2 of {setup.n_time} integrations ({rows * args.n_chan} vis), <= 2 iterations, "
+                         f"{dt:.1f} s single-threaded FP64 C"}
+    line = {"metric": METRIC, "value": vis_iters / (ms / 1000.0), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": DELAY_WORKLOAD, "n_ant": args.n_ant, "n_time": args.n_time, "n_chan": args.n_chan,
+                       "max_iter": args.max_iter, "tol": 1e-6, "l2": "inputs (25 GB) larger than L2 (129 MB)",
+                       "parallelism": "1 GPU"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": None, "clocks": clock_info,
+            "gpu_launches": int(sum(s.launches for s in stats)), "accumulate_launches_with_work": int(acc_launches),
+            "vis_iters": int(vis_iters), "iterations_max": int(max(s.n_iter_max for s in stats))}
+    print(json.dumps(line), flush=True)
 
 
 # ---------------------------------------------------------------------------

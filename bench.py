@@ -492,7 +492,7 @@ def run_delay(args):
                 "frac": (achieved / hbm) if achieved else None, "traffic": None, "bytes_per_vis_iteration": 81,
                 "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured"
                 else "fallback 6.8 TB/s",
-                "kernel": "acc_stream_kernel (per-channel diagonal bins of the delay term)",
+                "kernel": "acc_delay_kernel (chain rule per sample, sums per parameter interval)",
                 "algorithmic_bytes_per_launch": 81 * vis_iters / max(1, acc_launches),
                 "launch_ms_mean": acc_ms / max(1, acc_launches), "acc_share_of_step": acc_ms / ms if ms else None}
     cpu = None

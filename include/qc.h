@@ -124,10 +124,12 @@ typedef struct {
  *                 over (phi_X, tau_X, phi_Y, tau_Y) sums 2 Re(E^H W E) over
  *                 every sample of the interval (Eq. jhj_case2, Eq. jhwr_case2);
  *                 convergence uses the gains over the interval's channels.
- *                 Delay terms are accepted by qc_solve and qc_residual; a
- *                 chain holding one is solved with the accumulate kernels'
- *                 per-channel bins (one diagonal bin per time interval and
- *                 channel), then reduced over the interval's channels.
+ *                 Delay terms are accepted by qc_solve and qc_residual.  A
+ *                 solved delay term in a chain of one or two terms (kernel 0
+ *                 or 3) has its own streaming kernel, which applies the chain
+ *                 rule per sample; otherwise the accumulate kernels form
+ *                 diagonal blocks per (time interval, channel) bin and the
+ *                 update reduces them over the interval's channels.
  */
 typedef struct {
     int32_t type, n_tint, n_fint;

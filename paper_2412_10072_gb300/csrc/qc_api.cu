@@ -438,9 +438,18 @@ int qc_ctx::expand_terms(const qc_term *terms, int n_terms, std::vector<qc_term>
         if ((rc = ensure(B.dfmap, nbytes<int>(std::max(1, n_chan))))) return rc;
         if ((rc = ensure(B.dfr, nbytes<int2>(t.n_fint)))) return rc;
         if ((rc = ensure(B.dnu, nbytes<double>(std::max(1, n_chan))))) return rc;
+        if ((rc = ensure(B.domega, nbytes<float>(std::max(1, n_chan))))) return rc;
+        B.hufmap.assign(t.f_map, t.f_map + n_chan);
+        double mean_nu = 0;
+        for (int ch = 0; ch < n_chan; ++ch) mean_nu += t.chan_freq[ch];
+        B.omega_ref = n_chan ? DELAY_TWO_PI * (mean_nu / n_chan) : 0.0;
+        std::vector<float> om(n_chan);
+        for (int ch = 0; ch < n_chan; ++ch) om[ch] = (float)(DELAY_TWO_PI * t.chan_freq[ch] - B.omega_ref);
         if (n_chan) {
             CK(cudaMemcpyAsync(B.dfmap.ptr, t.f_map, nbytes<int>(n_chan), cudaMemcpyHostToDevice, st));
             CK(cudaMemcpyAsync(B.dnu.ptr, t.chan_freq, nbytes<double>(n_chan), cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(B.domega.ptr, om.data(), nbytes<float>(n_chan), cudaMemcpyHostToDevice, st));
+            CK(cudaStreamSynchronize(st));      // om is a local staging vector
         }
         CK(cudaMemcpyAsync(B.dfr.ptr, B.hfr.data(), nbytes<int2>(t.n_fint), cudaMemcpyHostToDevice, st));
         xt[j].type = QC_TERM_DIAG;
@@ -463,6 +472,7 @@ DelayArgs qc_ctx::delay_args(int j, const qc_term &xt_j)
     d.nu = (const double *)B.dnu.ptr;
     d.params = (double *)B.params.ptr;
     d.tab = (float4 *)B.tab.ptr;
+    d.omega_ref = B.omega_ref;
     return d;
 }
 
@@ -808,8 +818,24 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
     // auto and kernel 3: the streaming kernel (chains of one or two terms; antenna pairs are
     // packed as p | q << 16); kernels 1 and 2 on request, and for longer chains
     const bool streaming = L.stream_fn != nullptr && n_ant < 32768 && (o->kernel == 3 || o->kernel == 0);
-    const void *stream_fn = L.stream_fn;
-    const int stream_smem_per_warp = L.stream_smem_per_warp;
+    // a solved delay term under the streaming kernel: its own kernel, which applies the chain
+    // rule per sample and keeps sums per parameter interval (else: the per-channel bins)
+    DelayLaunch DL;
+    if (delay[n] && streaming) DL = delay_launcher(lk, rk, m16);
+    const bool ded = DL.fn != nullptr;
+    DevTerm tnu = chain.t[n];
+    const int nbu = delay[n] ? t.n_tint * (int)B.hfr.size() : nb;
+    if (ded) {
+        tnu.n_fint = (int)B.hfr.size();
+        tnu.f_map = (const int *)B.dfmap.ptr;
+        aa.tn = tnu;
+        int rc_;
+        if ((rc_ = ensure(B.acc, nbytes<double>((size_t)nbu * n_ant * KG_SUMS)))) return rc_;
+        CK(cudaMemsetAsync(B.acc.ptr, 0, nbytes<double>((size_t)nbu * n_ant * KG_SUMS), st));
+        aa.acc = (double *)B.acc.ptr;
+    }
+    const void *stream_fn = ded ? DL.fn : L.stream_fn;
+    const int stream_smem_per_warp = ded ? DL.smem_per_warp : L.stream_smem_per_warp;
     bool pipelined = !streaming && L.pipe_fn != nullptr && (o->kernel == 1 || (o->kernel == 0 && order == 1));
     const bool has_o = n_terms == 2;
     if (pipelined) {
@@ -895,7 +921,7 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
         if ((rc_ = ensure(B.fmap2, nbytes<int2>(n_chan)))) return rc_;
         std::vector<int2> fm(n_chan);
         for (int ch = 0; ch < n_chan; ++ch)
-            fm[ch] = make_int2(t.f_map[ch], has_o ? terms[1 - n].f_map[ch] : 0);
+            fm[ch] = make_int2(ded ? B.hufmap[ch] : t.f_map[ch], has_o ? terms[1 - n].f_map[ch] : 0);
         CK(cudaMemcpyAsync(B.fmap2.ptr, fm.data(), nbytes<int2>(n_chan), cudaMemcpyHostToDevice, st));
         if (n_rt) {
             row_table_kernel<<<(int)((n_rt + 255) / 256), 256, 0, st>>>(
@@ -916,7 +942,7 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
         sa.order = order;
         sa.n_chunks = (n_chan + 31) / 32;
         sa.n_units = order == 0 ? n_row : n_strips * sa.n_chunks;
-        sa.tn = chain.t[n];
+        sa.tn = ded ? tnu : chain.t[n];
         sa.to = has_o ? chain.t[1 - n] : chain.t[n];
         sa.fmap2 = (const int2 *)B.fmap2.ptr;
         sa.acc = (double *)B.acc.ptr;
@@ -1024,7 +1050,14 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
             if (streaming) {
                 sa.n_active = cnt + (k - 1);
                 if (sa.unit_counter) CK(cudaMemsetAsync(sa.unit_counter, 0, sizeof(int), st));
-                CK(L.stream_launch(grid, block, stream_smem, st, sa));
+                if (ded) {
+                    DelayStreamArgs dsa;
+                    dsa.s = sa;
+                    dsa.omega = (const float *)B.domega.ptr;
+                    CK(DL.launch(grid, block, stream_smem, st, dsa));
+                } else {
+                    CK(L.stream_launch(grid, block, stream_smem, st, sa));
+                }
             } else if (pipelined) {
                 pa.a.n_active = cnt + (k - 1);
                 CK(L.pipe_launch(grid, pipe_smem, st, pa));
@@ -1033,8 +1066,8 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
             }
             CK(cudaEventRecordWithFlags(events[2 + 2 * (k - 1) + 1], st, rec_flags));
             if (t.reduce) {
-                const size_t KG = t.type == 1 ? KG_FULL : KG_DIAG;
-                if (o->allreduce((double *)B.acc.ptr, (int64_t)nb * n_ant * KG, st, o->allreduce_user))
+                const size_t KG = ded ? KG_SUMS : (t.type == 1 ? KG_FULL : KG_DIAG);
+                if (o->allreduce((double *)B.acc.ptr, (int64_t)(ded ? nbu : nb) * n_ant * KG, st, o->allreduce_user))
                     return fail(QC_ECUDA, "allreduce callback failed");
             }
             ua.k = k;
@@ -1047,7 +1080,8 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
                 dua.alpha = ua.alpha;
                 dua.n_active_prev = ua.n_active_prev;
                 dua.n_active_next = ua.n_active_next;
-                delay_update_kernel<<<dua.d.n_tint * dua.d.n_fint, upd_block, 0, st>>>(dua);
+                if (ded) delay_update_kernel<true><<<dua.d.n_tint * dua.d.n_fint, upd_block, 0, st>>>(dua);
+                else delay_update_kernel<false><<<dua.d.n_tint * dua.d.n_fint, upd_block, 0, st>>>(dua);
             } else {
                 update_kernel<<<nb, upd_block, 0, st>>>(ua);
             }

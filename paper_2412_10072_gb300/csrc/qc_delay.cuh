@@ -27,6 +27,8 @@ struct DelayArgs {
     const double *nu;         // [n_chan] channel frequencies
     double *params;           // FP64 master [n_tint][n_fint][n_ant][4]
     float4 *tab;              // FP32 channel table [n_tint][n_ant][n_chan]: (g_X, g_Y)
+    double omega_ref;         // 2 pi nu of the centre of the band: the streaming kernel's sums use
+                              // omega' = 2 pi nu - omega_ref
 };
 
 // float32 parameters [n_tint][n_fint][n_ant][4] -> FP64 master copy
@@ -80,6 +82,17 @@ struct DelayUpdArgs {
 };
 
 // One block per parameter interval (time interval x frequency interval), threads over antennas.
+// SUMS = false: the accumulators are the complex diagonal blocks of every channel bin
+// [n_tint * n_chan][n_ant][KG_DIAG] and activity is kept per channel bin; the chain rule is
+// applied here, channel by channel.  SUMS = true: the streaming delay kernel has applied it
+// per sample and left the 13 real sums of each (interval, antenna) [bins][n_ant][KG_SUMS]
+// (h_XX, h_YY, h_XY times 1, omega', omega'^2; r_X, r_Y times 1, omega') with the centred
+// omega' = omega - omega_ref; they are shifted back to omega here in FP64, so that a band of
+// one frequency gives the exactly proportional phase and delay columns of the oracle (a
+// singular block) rather than FP32 rounding; activity per interval.
+constexpr int KG_SUMS = 16;
+
+template <bool SUMS>
 static __global__ void __launch_bounds__(128) delay_update_kernel(const DelayUpdArgs u)
 {
     if (*u.n_active_prev == 0) return;
@@ -97,7 +110,7 @@ static __global__ void __launch_bounds__(128) delay_update_kernel(const DelayUpd
         }
         return;
     }
-    if (!u.active[cb0 + fr.x]) return;
+    if (!u.active[SUMS ? (size_t)bin : cb0 + fr.x]) return;
     double num = 0, den = 0;
     for (int ant = threadIdx.x; ant < d.n_ant; ant += blockDim.x) {
         double *P = d.params + ((size_t)bin * d.n_ant + ant) * 4;
@@ -107,7 +120,33 @@ static __global__ void __launch_bounds__(128) delay_update_kernel(const DelayUpd
             b[i] = make_double2(0.0, 0.0);
             for (int j = 0; j < 4; ++j) M[i][j] = make_double2(0.0, 0.0);
         }
-        for (int c = fr.x; c <= fr.y; ++c) {
+        if (SUMS) {
+            double *A = u.acc + ((size_t)bin * d.n_ant + ant) * KG_SUMS;
+            double S[13];
+            for (int i = 0; i < 13; ++i) { S[i] = A[i]; A[i] = 0.0; }
+            // sum h w^k with w = w' + w0:  h w = h w' + w0 h,  h w^2 = h w'^2 + 2 w0 h w' + w0^2 h
+            const double w0 = d.omega_ref;
+            for (int base = 0; base <= 10; base += (base == 3 ? 7 : 3)) {
+                const double s0 = S[base], s1 = S[base + 1], s2 = S[base + 2];
+                S[base + 1] = s1 + w0 * s0;
+                S[base + 2] = s2 + 2.0 * w0 * s1 + w0 * w0 * s0;
+            }
+            S[7] += w0 * S[6];
+            S[9] += w0 * S[8];
+            const int o2[2][2] = { { 0, 1 }, { 1, 2 } };    // power of omega of block entry (i, j)
+            for (int i = 0; i < 2; ++i)
+                for (int j = 0; j < 2; ++j) {
+                    M[i][j].x = 2.0 * S[o2[i][j]];
+                    M[2 + i][2 + j].x = 2.0 * S[3 + o2[i][j]];
+                    M[i][2 + j].x = 2.0 * S[10 + o2[i][j]];
+                    M[2 + j][i].x = 2.0 * S[10 + o2[i][j]];
+                }
+            b[0].x = 2.0 * S[6];
+            b[1].x = 2.0 * S[7];
+            b[2].x = 2.0 * S[8];
+            b[3].x = 2.0 * S[9];
+        }
+        for (int c = fr.x; !SUMS && c <= fr.y; ++c) {
             double *A = u.acc + ((cb0 + c) * d.n_ant + ant) * KG_DIAG;
             const double h00 = A[0], h11 = A[1];
             const double2 h01 = make_double2(A[2], A[3]), j0 = make_double2(A[4], A[5]), j1 = make_double2(A[6], A[7]);
@@ -168,7 +207,9 @@ static __global__ void __launch_bounds__(128) delay_update_kernel(const DelayUpd
         atomicAdd(u.vis_iters, nv);
         atomicAdd(u.acc_bytes, nb);
         if (delta < u.tol) {
-            for (int c = fr.x; c <= fr.y; ++c) u.active[cb0 + c] = 0;
+            if (SUMS) u.active[bin] = 0;
+            else
+                for (int c = fr.x; c <= fr.y; ++c) u.active[cb0 + c] = 0;
         } else {
             atomicAdd(u.n_active_next, 1);
         }

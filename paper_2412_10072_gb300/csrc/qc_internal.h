@@ -8,6 +8,7 @@
 #include "../../include/qc.h"
 #include "qc_stream.cuh"
 #include "qc_delay.cuh"
+#include "qc_stream_delay.cuh"
 
 struct Buf {
     void *ptr = nullptr;
@@ -37,7 +38,10 @@ struct TermBufs {
     Buf dfmap;     // delay terms: int [n_chan] parameter interval of each channel
     Buf dfr;       // delay terms: int2 [n_fint] first and last channel of each interval
     Buf dnu;       // delay terms: double [n_chan] channel frequencies
+    Buf domega;    // delay terms: float [n_chan] 2 pi nu - omega_ref
+    double omega_ref = 0;     // delay terms: 2 pi times the mean channel frequency
     std::vector<int2> hfr;    // host copy of dfr (its size is the term's n_fint)
+    std::vector<int> hufmap;  // delay terms: host copy of the term's own f_map
     cudaGraphExec_t exec = nullptr;
     bool graph_valid = false;
 };
@@ -56,6 +60,13 @@ struct AccLaunch {
     cudaError_t (*stream_launch)(int grid, int block, int smem_bytes, cudaStream_t st, const qc::StreamArgs &a) = nullptr;
     int stream_smem_per_warp = 0;
 };
+// The streaming kernel of a solved delay term (chains of one or two terms).
+struct DelayLaunch {
+    const void *fn = nullptr;
+    cudaError_t (*launch)(int grid, int block, int smem_bytes, cudaStream_t st, const qc::DelayStreamArgs &a) = nullptr;
+    int smem_per_warp = 0;
+};
+DelayLaunch delay_launcher(int lk, int rk, bool m16);
 AccLaunch acc_launcher_diag(bool simple, int lk, int rk, bool m16);
 AccLaunch acc_launcher_full(bool simple, int lk, int rk, bool m16);
 inline AccLaunch acc_launcher(int ts, bool simple, int lk, int rk, bool m16)

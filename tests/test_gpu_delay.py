@@ -108,17 +108,23 @@ def _referenced(par, pb):
     return g * np.conj(g[:, :, :1, :])
 
 
+# kernel 0: the streaming delay kernel (chain rule per sample, sums per interval);
+# kernel 2: the generic kernels on per-channel bins, reduced by the chain rule in the update
+KERNELS = [0, 2]
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("other", [None, "B", "G"])
-def test_one_step_matches_oracle(other):
-    """One Gauss-Newton step (alpha = 1) from zero: the GPU's per-channel bins reduced by the
-    chain rule give the same step as the oracle's sums over every sample of the interval."""
+def test_one_step_matches_oracle(other, kernel):
+    """One Gauss-Newton step (alpha = 1) from zero gives the same step as the oracle's sums over
+    every sample of the interval."""
     pb = _problem(101, other=other)
     P = _oracle_problem(pb)
     ot, n = _oracle_terms(pb, max_iter=1)
     O.solve_term(P, ot, n, damping=1.0, damping_mode=0)
     S = _solver(pb)
     gt, n = _gpu_terms(pb, max_iter=1)
-    S.solve(gt, damping_mode=qc.QC_DAMP_CONST, damping=1.0)
+    S.solve(gt, damping_mode=qc.QC_DAMP_CONST, damping=1.0, kernel=kernel)
     S.close()
     g_gpu = _delay_gains(np.asarray(gt[n].gains, np.float64), np.arange(pb["n_tint"]), pb["f_map"], pb["nu"])
     g_ora = _delay_gains(ot[n].params, np.arange(pb["n_tint"]), pb["f_map"], pb["nu"])
@@ -126,8 +132,9 @@ def test_one_step_matches_oracle(other):
     assert np.array_equal(np.asarray(gt[n].gain_flags), ot[n].gain_flags)
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("other,n_fint", [(None, 1), (None, 2), ("B", 1), ("G", 1)])
-def test_converged_solution_matches_oracle(other, n_fint):
+def test_converged_solution_matches_oracle(other, n_fint, kernel):
     pb = _problem(202 + n_fint, n_fint=n_fint, other=other)
     P = _oracle_problem(pb)
     ot, n = _oracle_terms(pb)
@@ -135,7 +142,7 @@ def test_converged_solution_matches_oracle(other, n_fint):
     chi_o = O.residual(P, ot)
     S = _solver(pb)
     gt, n = _gpu_terms(pb)
-    S.solve(gt)
+    S.solve(gt, kernel=kernel)
     chi_g = S.residual(gt)
     S.close()
     a = _referenced(gt[n].gains, pb)
@@ -191,13 +198,14 @@ def test_delay_term_held_fixed_while_another_is_solved():
     np.testing.assert_array_equal(np.asarray(gt[0].gains), par.astype(np.float32))
 
 
-def test_single_frequency_block_is_singular_and_left_unchanged():
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_single_frequency_block_is_singular_and_left_unchanged(kernel):
     pb = _problem(505, nu=np.full(N_CHAN, 1.3))
     rng = np.random.default_rng(3)
     par = rng.uniform(-0.5, 0.5, size=(pb["n_tint"], 1, N_ANT, 4)).astype(np.float32)
     S = _solver(pb)
     gt, n = _gpu_terms(pb, k_params=par.astype(np.float64))
-    S.solve(gt)
+    S.solve(gt, kernel=kernel)
     S.close()
     assert np.all(np.asarray(gt[n].gain_flags) == 1)
     np.testing.assert_array_equal(np.asarray(gt[n].gains), par)

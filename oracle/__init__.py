@@ -20,8 +20,14 @@ Parity status of each oracle function (what pins it, see ``tests/``):
   central differences of it in the four real parameters, the chi^2
   gradient, exact recovery of generating phases and delays, and the
   singular single-frequency case (``tests/test_oracle_delay.py``).
+- ``delay_init`` (the delay term's initial estimate, Section 4.3): pinned by
+  exact recovery of delays on the transform's grid (the triangle-inequality
+  bound), off-grid delays within half a step, flagged cells left out, and a
+  solve from the estimate reaching delays a zero start cannot
+  (``tests/test_oracle_delay_init.py``).
 - ``mlp``: pinned by central finite differences of its own loss.
 """
 from .oracle import (OC_DIAG, OC_FULL, OC_PHASE, OC_DELAY, OracleProblem, OracleTerm, build,  # noqa: F401
                      normal_equations, residual, solve, solve_term, block_solve)
 from .gauge import reference_diag, reference_chain, chain_products  # noqa: F401
+from .delay_init import delay_init  # noqa: F401

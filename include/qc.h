@@ -212,6 +212,30 @@ int qc_solve(qc_ctx *c, qc_term *terms, int32_t n_terms, const qc_opts *o, qc_st
 int qc_residual(qc_ctx *c, const qc_term *terms, int32_t n_terms, void *resid, int32_t resid_memory,
                 double *chi2);
 
+/*
+ * Initial estimate of a delay term's parameters (Section 4.3, "Initial
+ * estimates": the peak of the Fourier transform along frequency of the
+ * baselines that include the reference antenna).  For every time interval,
+ * frequency interval, antenna a and correlation c in {XX, YY}:
+ *   x(nu) = sum of w d conj(m) of correlation c over the interval's unflagged
+ *           samples on baselines (a, ref) or (ref, a), conjugated for (ref, a);
+ *   X_k   = FFT of x over the interval's channels zero-padded to N, the next
+ *           power of two >= oversample x channels, at the delays
+ *           tau_k = k / (N dnu), k = -N/2 .. N/2 - 1;
+ *   tau_c = tau_k and phi_c = arg X_k - 2 pi tau_k nu_0 at the largest |X_k|
+ *           (the lowest k among equal values), nu_0 the interval's first channel.
+ * The reference antenna, antennas without data and one-channel intervals get
+ * tau = 0 (one channel: phi = arg x).  term->gains (float32 [n_tint][n_fint]
+ * [n_ant][4], in term->memory) is overwritten; term->solve is ignored.
+ *   ref_ant    : reference antenna, in [0, n_ant).
+ *   oversample : >= 1 (0: 4); N must not exceed 16384.
+ * Errors: QC_EINVAL for a term that is not QC_TERM_DELAY or fails the checks
+ * of qc_solve, a reference antenna out of range or oversample < 0;
+ * QC_EUNSUPPORTED when an interval's channels are not uniformly spaced
+ * (|nu_c - nu_0 - c dnu| > 1e-6 |dnu|) or N would exceed 16384.
+ */
+int qc_delay_init(qc_ctx *c, qc_term *term, int32_t ref_ant, int32_t oversample);
+
 /* Release a context and every device buffer it owns.  NULL-safe. */
 void qc_destroy(qc_ctx *c);
 

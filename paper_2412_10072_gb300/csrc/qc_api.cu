@@ -589,6 +589,101 @@ extern "C" int qc_residual(qc_ctx *c, const qc_term *terms, int32_t n_terms, voi
     return QC_OK;
 }
 
+extern "C" int qc_delay_init(qc_ctx *c, qc_term *term, int32_t ref_ant, int32_t oversample)
+{
+    if (!c) return QC_EINVAL;
+    c->err.clear();
+    if (!term) return c->fail(QC_EINVAL, "term is NULL");
+    if (term->type != QC_TERM_DELAY) return c->fail(QC_EINVAL, "qc_delay_init needs a QC_TERM_DELAY term");
+    int rc = c->validate_terms(term, 1, false);
+    if (rc) return rc;
+    if (ref_ant < 0 || ref_ant >= c->n_ant) return c->fail(QC_EINVAL, "ref_ant out of range");
+    if (oversample < 0) return c->fail(QC_EINVAL, "oversample must be >= 0");
+    if (oversample == 0) oversample = 4;
+    const qc_term &t = *term;
+    // per frequency interval: first channel, channels, transform length, spacing, first frequency
+    std::vector<int4> info(t.n_fint, make_int4(0, 0, 1, 0));
+    std::vector<double> dnu(t.n_fint, 0.0), nu0(t.n_fint, 0.0);
+    int max_n = 1;
+    for (int ch = 0; ch < c->n_chan; ++ch) {
+        int4 &f = info[t.f_map[ch]];
+        if (f.y == 0) f.x = ch;
+        ++f.y;
+    }
+    for (int fi = 0; fi < t.n_fint; ++fi) {
+        int4 &f = info[fi];
+        if (f.y == 0) continue;
+        nu0[fi] = t.chan_freq[f.x];
+        if (f.y > 1) {
+            const double d = (t.chan_freq[f.x + f.y - 1] - t.chan_freq[f.x]) / (f.y - 1);
+            if (!(d != 0.0)) return c->fail(QC_EUNSUPPORTED, "an interval's channels have no frequency spread");
+            for (int k = 0; k < f.y; ++k)
+                if (std::fabs(t.chan_freq[f.x + k] - nu0[fi] - k * d) > 1e-6 * std::fabs(d))
+                    return c->fail(QC_EUNSUPPORTED, "the delay estimate needs uniformly spaced channels");
+            dnu[fi] = d;
+        }
+        long long N = 1;
+        int lg = 0;
+        while (N < (long long)oversample * f.y) { N *= 2; ++lg; }
+        if (N > 16384) return c->fail(QC_EUNSUPPORTED, "transform longer than 16384 (reduce oversample)");
+        f.z = (int)N;
+        f.w = lg;
+        max_n = std::max(max_n, (int)N);
+    }
+    cudaStream_t st = c->own_stream;
+    TermBufs &B = c->tb[0];
+    const size_t nx = (size_t)t.n_tint * c->n_ant * 2 * c->n_chan;
+    const size_t npar = (size_t)t.n_tint * t.n_fint * c->n_ant * 4;
+    if ((rc = c->ensure(B.maps, nbytes<int>(c->n_time + c->n_chan)))) return rc;
+    if ((rc = c->ensure(B.acc, std::max(nbytes<float2>(nx), nbytes<float>(npar) + 64)))) return rc;
+    if ((rc = c->ensure(B.stage, nbytes<float>(npar)))) return rc;
+    if ((rc = c->ensure(B.dfr, nbytes<int4>(t.n_fint)))) return rc;
+    if ((rc = c->ensure(B.dnu, nbytes<double>(2 * (size_t)t.n_fint)))) return rc;
+    CK(cudaMemcpyAsync(B.maps.ptr, t.t_map, nbytes<int>(c->n_time), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(B.dfr.ptr, info.data(), nbytes<int4>(t.n_fint), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(B.dnu.ptr, dnu.data(), nbytes<double>(t.n_fint), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync((double *)B.dnu.ptr + t.n_fint, nu0.data(), nbytes<double>(t.n_fint), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(B.acc.ptr, 0, nbytes<float2>(nx), st));
+    DelayInitArgs a;
+    a.n_row = c->n_row;
+    a.n_chan = c->n_chan;
+    a.n_ant = c->n_ant;
+    a.ref = ref_ant;
+    a.n_tint = t.n_tint;
+    a.n_fint = t.n_fint;
+    a.rows = c->d_rows;
+    a.vis = c->d_vis;
+    a.model = c->m16 ? nullptr : c->d_model;
+    a.model16 = c->d_model16;
+    a.bl_scale = c->d_bl_scale;
+    a.wf = c->d_wf;
+    a.t_map = (const int *)B.maps.ptr;
+    a.x = (float2 *)B.acc.ptr;
+    a.fint_info = (const int4 *)B.dfr.ptr;
+    a.fint_dnu = (const double *)B.dnu.ptr;
+    a.fint_nu0 = (const double *)B.dnu.ptr + t.n_fint;
+    float *dpar = t.memory == QC_MEM_DEVICE ? (float *)t.gains : (float *)B.stage.ptr;
+    a.params = dpar;
+    if (c->n_row) {
+        delay_gather_kernel<<<grid_for((long)c->n_row * 32, 256, c->sm_count), 256, 0, st>>>(a);
+        CK(cudaGetLastError());
+    }
+    const int smem = max_n * (int)sizeof(float2);
+    if (smem > 48 * 1024) {
+        if (smem > c->smem_optin) return c->fail(QC_EUNSUPPORTED, "transform does not fit in shared memory");
+        CK(cudaFuncSetAttribute((const void *)delay_peak_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    }
+    const long blocks = (long)t.n_tint * t.n_fint * c->n_ant * 2;
+    if (blocks > 0) {
+        delay_peak_kernel<<<(unsigned)blocks, 256, smem, st>>>(a);
+        CK(cudaGetLastError());
+    }
+    if (t.memory == QC_MEM_HOST)
+        CK(cudaMemcpyAsync(t.gains, dpar, nbytes<float>(npar), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return QC_OK;
+}
+
 int qc_ctx::run_residual(const Chain &chain, float4 *dres, double *d_chi2, cudaStream_t st)
 {
     qc_ctx *c = this;

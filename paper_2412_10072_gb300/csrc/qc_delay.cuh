@@ -217,3 +217,132 @@ static __global__ void __launch_bounds__(128) delay_update_kernel(const DelayUpd
 }
 
 } // namespace qc
+
+namespace qc {
+
+// ---------------------------------------------------------------------------
+// initial estimate of a delay term (Section 4.3, "Initial estimates"): the peak of the
+// Fourier transform along frequency of the baselines that include the reference antenna
+// ---------------------------------------------------------------------------
+
+struct DelayInitArgs {
+    int n_row, n_chan, n_ant, ref, n_tint, n_fint;
+    const int4 *rows;          // [n_row] {ant1, ant2, time, baseline}
+    const float4 *vis;         // [n_row][n_chan] x 2
+    const float4 *model;       // [n_row][n_chan] x 2, or nullptr (FP16 model)
+    const uint4 *model16;      // [n_row][n_chan], or nullptr
+    const float *bl_scale;     // [n_bl] FP16 model scales
+    const float4 *wf;          // [n_row][n_chan] weights, zero where flagged or autocorrelation
+    const int *t_map;          // [n_time] time interval of each data time
+    float2 *x;                 // [n_tint][n_ant][2][n_chan] spectra (zeroed before)
+    const int4 *fint_info;     // [n_fint] {first channel, channels, N, log2 N}
+    const double *fint_dnu;    // [n_fint] channel spacing
+    const double *fint_nu0;    // [n_fint] frequency of the first channel
+    float *params;             // [n_tint][n_fint][n_ant][4] out
+};
+
+// x[t][a][c][chan] += w d conj(m) of correlation c (XX, YY) over the rows on baselines with
+// the reference antenna, conjugated for rows (ref, a).  One warp per row, lanes over channels.
+static __global__ void delay_gather_kernel(const DelayInitArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long n_warps = ((long)gridDim.x * blockDim.x) >> 5;
+    for (long row = warp; row < a.n_row; row += n_warps) {
+        const int4 r = a.rows[row];
+        if (r.x == r.y || (r.x != a.ref && r.y != a.ref)) continue;
+        const int ant = r.x == a.ref ? r.y : r.x;
+        const bool flip = r.x == a.ref;
+        float2 *xa = a.x + ((size_t)a.t_map[r.z] * a.n_ant + ant) * 2 * a.n_chan;
+        for (int c = lane; c < a.n_chan; c += 32) {
+            const size_t s = (size_t)row * a.n_chan + c;
+            const float4 w = a.wf[s];
+            if (w.x == 0.f && w.y == 0.f && w.z == 0.f && w.w == 0.f) continue;
+            const J2 D = j_from(a.vis[2 * s], a.vis[2 * s + 1]);
+            const J2 M = a.model ? j_from(a.model[2 * s], a.model[2 * s + 1]) : load_model16(a.model16[s], a.bl_scale[r.w]);
+            float2 zx = cscale(cmulc(D.a, M.a), w.x), zy = cscale(cmulc(D.d, M.d), w.w);
+            if (flip) { zx = cconj(zx); zy = cconj(zy); }
+            atomicAdd(&xa[c].x, zx.x);
+            atomicAdd(&xa[c].y, zx.y);
+            atomicAdd(&xa[a.n_chan + c].x, zy.x);
+            atomicAdd(&xa[a.n_chan + c].y, zy.y);
+        }
+    }
+}
+
+// One block per (time interval, frequency interval, antenna, correlation): the spectrum over
+// the interval's channels, zero-padded to N (a power of two), transformed by a radix-2 FFT in
+// shared memory, X_k = sum_c x_c exp(-2 pi i k c / N); the peak |X_k| (lowest signed k
+// among equal values) gives tau = k / (N dnu) and phi = arg X_k - 2 pi tau nu_0.
+static __global__ void __launch_bounds__(256) delay_peak_kernel(const DelayInitArgs a)
+{
+    extern __shared__ float2 fbuf[];
+    const int corr = blockIdx.x & 1;
+    const int rest = blockIdx.x >> 1;
+    const int ant = rest % a.n_ant;
+    const int bin = rest / a.n_ant;                         // tint * n_fint + fint
+    const int fi = bin % a.n_fint, tint = bin / a.n_fint;
+    float *out = a.params + ((size_t)bin * a.n_ant + ant) * 4 + 2 * corr;
+    const int4 info = a.fint_info[fi];
+    const int c0 = info.x, n_c = info.y, N = info.z, lg = info.w;
+    const float2 *xs = a.x + (((size_t)tint * a.n_ant + ant) * 2 + corr) * a.n_chan + c0;
+    if (ant == a.ref || n_c == 0) {
+        if (threadIdx.x == 0) { out[0] = 0.f; out[1] = 0.f; }
+        return;
+    }
+    if (n_c == 1) {
+        if (threadIdx.x == 0) {
+            const float2 v = xs[0];
+            out[0] = (v.x != 0.f || v.y != 0.f) ? atan2f(v.y, v.x) : 0.f;
+            out[1] = 0.f;
+        }
+        return;
+    }
+    for (int i = threadIdx.x; i < N; i += blockDim.x) fbuf[i] = make_float2(0.f, 0.f);
+    __syncthreads();
+    for (int c = threadIdx.x; c < n_c; c += blockDim.x) fbuf[__brev((unsigned)c) >> (32 - lg)] = xs[c];
+    __syncthreads();
+    for (int len = 2, lh = 0; len <= N; len <<= 1, ++lh) {
+        const int half = len >> 1;
+        for (int j = threadIdx.x; j < N / 2; j += blockDim.x) {
+            const int grp = j >> lh, pos = j & (half - 1);
+            const int i0 = grp * len + pos, i1 = i0 + half;
+            float sn, cs;
+            sincospif(-2.0f * (float)pos / (float)len, &sn, &cs);
+            const float2 u = fbuf[i0], v = cmul(fbuf[i1], make_float2(cs, sn));
+            fbuf[i0] = cadd(u, v);
+            fbuf[i1] = csub(u, v);
+        }
+        __syncthreads();
+    }
+    float best = -1.f;
+    int bk = 1 << 30;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const int ks = i < N / 2 ? i : i - N;
+        const float m = cnorm2(fbuf[i]);
+        if (m > best || (m == best && ks < bk)) { best = m; bk = ks; }
+    }
+    for (int d = 16; d > 0; d >>= 1) {
+        const float om = __shfl_down_sync(0xffffffffu, best, d);
+        const int ok = __shfl_down_sync(0xffffffffu, bk, d);
+        if (om > best || (om == best && ok < bk)) { best = om; bk = ok; }
+    }
+    __shared__ float s_best[8];
+    __shared__ int s_k[8];
+    const int wi = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { s_best[wi] = best; s_k[wi] = bk; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < (int)(blockDim.x >> 5); ++i)
+            if (s_best[i] > best || (s_best[i] == best && s_k[i] < bk)) { best = s_best[i]; bk = s_k[i]; }
+        if (!(best > 0.f)) { out[0] = 0.f; out[1] = 0.f; return; }
+        const float2 X = fbuf[bk >= 0 ? bk : bk + N];
+        const double tau = (double)bk / ((double)N * a.fint_dnu[fi]);
+        double phi = atan2((double)X.y, (double)X.x) - DELAY_TWO_PI * tau * a.fint_nu0[fi];
+        phi -= DELAY_TWO_PI * floor(phi / DELAY_TWO_PI + 0.5);
+        out[0] = (float)phi;
+        out[1] = (float)tau;
+    }
+}
+
+} // namespace qc

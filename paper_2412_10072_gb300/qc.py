@@ -89,6 +89,8 @@ def load(build_if_missing: bool = True):
         lib.qc_solve.restype = C.c_int
         lib.qc_residual.argtypes = [vp, C.POINTER(_Term), i32, vp, i32, C.POINTER(C.c_double)]
         lib.qc_residual.restype = C.c_int
+        lib.qc_delay_init.argtypes = [vp, C.POINTER(_Term), i32, i32]
+        lib.qc_delay_init.restype = C.c_int
         lib.qc_destroy.argtypes = [vp]
         lib.qc_destroy.restype = None
         lib.qc_last_error.argtypes = [vp]
@@ -247,6 +249,15 @@ class Solver:
         if rc != QC_OK:
             self._err(rc)
         return s
+
+    def delay_init(self, term: Term, ref: int = 0, oversample: int = 4) -> Term:
+        """Overwrite a delay term's parameters with the initial estimate of qc_delay_init (the
+        peak of the Fourier transform along frequency of the baselines with antenna ``ref``)."""
+        arr = _terms_array([term])
+        rc = self._lib.qc_delay_init(self._h, arr, int(ref), int(oversample))
+        if rc != QC_OK:
+            self._err(rc)
+        return term
 
     def residual(self, terms: List[Term], want_resid: bool = False, resid_out=None):
         arr = _terms_array(terms)

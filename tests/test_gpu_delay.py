@@ -224,3 +224,107 @@ def test_delay_term_without_frequencies_is_rejected():
     with pytest.raises(qc.QCError):
         S.solve(gt)
     S.close()
+
+
+# ---------------------------------------------------------------------------
+# initial estimate (qc_delay_init) against the oracle's FFT-peak estimate
+# ---------------------------------------------------------------------------
+
+def _init_problem(seed, n_time=4, n_chan=48, noise=0.02, big=3.0):
+    """Data of [K] with delays up to `big` ns (far outside a zero start's basin), 10% flagged."""
+    rng = np.random.default_rng(seed)
+    p, q = synth.baselines(N_ANT)
+    ant1, ant2 = np.tile(p, n_time), np.tile(q, n_time)
+    tidx = np.repeat(np.arange(n_time, dtype=np.int32), p.size)
+    shp = (ant1.size, n_chan, 4)
+    nu = np.linspace(0.9, 1.7, n_chan)
+    model = (rng.standard_normal(shp) + 1j * rng.standard_normal(shp)) / np.sqrt(2)
+    weight = rng.uniform(0.5, 2.0, size=shp)
+    flag = (rng.random(shp[:2]) < 0.1).astype(np.uint8)
+    truth = np.zeros((n_time, 1, N_ANT, 4))
+    truth[..., 0::2] = rng.uniform(-2, 2, (n_time, 1, N_ANT, 2))
+    truth[..., 1::2] = rng.uniform(-big, big, (n_time, 1, N_ANT, 2))
+    g = _delay_gains(truth, np.arange(n_time), np.zeros(n_chan, np.int32), nu)     # [time][chan][ant][2]
+    gp = g[tidx[:, None], np.arange(n_chan)[None, :], ant1[:, None]]
+    gq = g[tidx[:, None], np.arange(n_chan)[None, :], ant2[:, None]]
+    data = model.copy()
+    data[..., 0] *= gp[..., 0] * np.conj(gq[..., 0])
+    data[..., 1] *= gp[..., 0] * np.conj(gq[..., 1])
+    data[..., 2] *= gp[..., 1] * np.conj(gq[..., 0])
+    data[..., 3] *= gp[..., 1] * np.conj(gq[..., 1])
+    data = data + noise * (rng.standard_normal(shp) + 1j * rng.standard_normal(shp))
+    return dict(data=data, model=model, weight=weight, flag=flag, ant1=ant1, ant2=ant2, tidx=tidx, nu=nu,
+                n_time=n_time, n_chan=n_chan)
+
+
+@pytest.mark.parametrize("ref,n_fint,m16", [(0, 1, False), (3, 2, False), (0, 1, True)])
+def test_delay_init_matches_oracle(ref, n_fint, m16):
+    from oracle.delay_init import delay_init
+    pb = _init_problem(707 + ref + n_fint)
+    n_time, n_chan = pb["n_time"], pb["n_chan"]
+    t_map = np.arange(n_time, dtype=np.int32)
+    f_map = (np.arange(n_chan) * n_fint // n_chan).astype(np.int32)
+    model = pb["model"]
+    if m16:   # the oracle sees the model the GPU stores: FP16 (re, im) x per-baseline scale
+        n_bl = N_ANT * (N_ANT - 1) // 2
+        bl = np.tile(np.arange(n_bl), n_time)
+        m = model.astype(np.complex64)
+        comp = np.stack([m.real, m.imag], -1)
+        scale = np.zeros(n_bl, np.float32)
+        np.maximum.at(scale, bl, np.abs(comp).reshape(comp.shape[0], -1).max(1))
+        scale[scale == 0] = 1
+        h = (comp / scale[bl][:, None, None, None]).astype(np.float16).astype(np.float32) * scale[bl][:, None, None, None]
+        model = h[..., 0] + 1j * h[..., 1]
+    P = O.OracleProblem(pb["data"], model, pb["weight"], pb["flag"], pb["ant1"], pb["ant2"], pb["tidx"], N_ANT, n_time)
+    want = delay_init(P, t_map, f_map, n_time, n_fint, pb["nu"], ref=ref, oversample=4)
+    S = qc.Solver(pb["data"], pb["model"], pb["weight"], pb["flag"], pb["ant1"], pb["ant2"], pb["tidx"], N_ANT,
+                  n_time, model_fp16=m16)
+    K = qc.Term("delay", t_map, f_map, n_time, n_fint, N_ANT, chan_freq=pb["nu"])
+    S.delay_init(K, ref=ref, oversample=4)
+    S.close()
+    got = np.asarray(K.gains, np.float64)
+    # the same peak bin: identical delays on the grid
+    np.testing.assert_allclose(got[..., 1::2], want[..., 1::2], rtol=1e-6, atol=0)
+    assert np.abs(np.angle(np.exp(1j * (got[..., 0::2] - want[..., 0::2])))).max() <= 1e-3
+    assert np.all(got[:, :, ref] == 0)
+
+
+def test_solve_from_the_estimate_matches_the_oracle():
+    """Delays up to 3 ns: both sides start from their own estimate and reach the same solution."""
+    from oracle.delay_init import delay_init
+    pb = _init_problem(808)
+    n_time, n_chan = pb["n_time"], pb["n_chan"]
+    t_map, f_map = np.arange(n_time, dtype=np.int32), np.zeros(n_chan, np.int32)
+    P = O.OracleProblem(pb["data"], pb["model"], pb["weight"], pb["flag"], pb["ant1"], pb["ant2"], pb["tidx"], N_ANT,
+                        n_time)
+    est = delay_init(P, t_map, f_map, n_time, 1, pb["nu"])
+    ok = O.OracleTerm("delay", t_map, f_map, n_time, 1, N_ANT, params=est, chan_freq=pb["nu"], max_iter=40, tol=1e-8)
+    O.solve(P, [ok], damping_mode=1)
+    chi_o = O.residual(P, [ok])
+    S = qc.Solver(pb["data"], pb["model"], pb["weight"], pb["flag"], pb["ant1"], pb["ant2"], pb["tidx"], N_ANT, n_time)
+    K = qc.Term("delay", t_map, f_map, n_time, 1, N_ANT, chan_freq=pb["nu"], max_iter=40, tol=1e-8)
+    S.delay_init(K)
+    S.solve([K])
+    chi_g = S.residual([K])
+    S.close()
+    pbk = dict(n_tint=n_time, f_map=f_map, nu=pb["nu"])
+    assert np.abs(_referenced(K.gains, pbk) - _referenced(ok.params, pbk)).max() <= GAIN_TOL
+    assert abs(chi_g - chi_o) <= CHI2_TOL * chi_o
+
+
+def test_delay_init_rejects_bad_requests():
+    pb = _init_problem(909)
+    n_time, n_chan = pb["n_time"], pb["n_chan"]
+    S = qc.Solver(pb["data"], pb["model"], pb["weight"], pb["flag"], pb["ant1"], pb["ant2"], pb["tidx"], N_ANT, n_time)
+    t_map, f_map = np.arange(n_time, dtype=np.int32), np.zeros(n_chan, np.int32)
+    uneven = pb["nu"].copy()
+    uneven[5] += 0.003
+    with pytest.raises(qc.QCError):
+        S.delay_init(qc.Term("delay", t_map, f_map, n_time, 1, N_ANT, chan_freq=uneven))
+    with pytest.raises(qc.QCError):
+        S.delay_init(qc.Term("delay", t_map, f_map, n_time, 1, N_ANT, chan_freq=pb["nu"]), ref=N_ANT)
+    with pytest.raises(qc.QCError):
+        S.delay_init(qc.Term("delay", t_map, f_map, n_time, 1, N_ANT, chan_freq=pb["nu"]), oversample=1024)
+    with pytest.raises(qc.QCError):
+        S.delay_init(qc.Term("diag", t_map, f_map, n_time, 1, N_ANT))
+    S.close()

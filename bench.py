@@ -485,6 +485,16 @@ def run_delay(args):
     vis_iters = sum(s.vis_iters for s in stats)
     acc_ms = sum(s.acc_ms for s in stats)
     acc_launches = sum(s.acc_launches for s in stats)
+    # the initial estimate (qc_delay_init: FFT peak of the reference-antenna baselines), device time
+    k0 = delay_terms(qc, setup.n_time, args.n_chan, setup.n_ant, args.max_iter, nu)[0]
+    solver.delay_init(k0)
+    i0, i1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    i0.record()
+    solver.delay_init(k0)
+    i1.record()
+    torch.cuda.synchronize()
+    init_ms = i0.elapsed_time(i1)
     peaks, peak_src = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     achieved = (81 * vis_iters / (acc_ms / 1000.0)) / 1e9 if acc_ms > 0 else None
@@ -518,7 +528,8 @@ def run_delay(args):
                        "parallelism": "1 GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": None, "clocks": clock_info,
             "gpu_launches": int(sum(s.launches for s in stats)), "accumulate_launches_with_work": int(acc_launches),
-            "vis_iters": int(vis_iters), "iterations_max": int(max(s.n_iter_max for s in stats))}
+            "vis_iters": int(vis_iters), "iterations_max": int(max(s.n_iter_max for s in stats)),
+            "initial_estimate_ms": init_ms}
     print(json.dumps(line), flush=True)
 
 

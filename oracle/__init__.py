@@ -25,9 +25,13 @@ Parity status of each oracle function (what pins it, see ``tests/``):
   bound), off-grid delays within half a step, flagged cells left out, and a
   solve from the estimate reaching delays a zero start cannot
   (``tests/test_oracle_delay_init.py``).
+- ``mad_flag`` (MAD residual flagging): pinned by order statistics against
+  a sort, planted outliers, the Gaussian spread of the MAD and the
+  exclusion of flagged samples (``tests/test_oracle_mad.py``).
 - ``mlp``: pinned by central finite differences of its own loss.
 """
 from .oracle import (OC_DIAG, OC_FULL, OC_PHASE, OC_DELAY, OracleProblem, OracleTerm, build,  # noqa: F401
                      normal_equations, residual, solve, solve_term, block_solve)
 from .gauge import reference_diag, reference_chain, chain_products  # noqa: F401
 from .delay_init import delay_init  # noqa: F401
+from .mad_flag import mad_flag  # noqa: F401

@@ -1234,3 +1234,181 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
     *acc_launches = worked;
     return QC_OK;
 }
+
+// ---------------------------------------------------------------------------
+// MAD residual flagging (Section 4, "Additional features"; global mode)
+// ---------------------------------------------------------------------------
+//
+// The statistic of an unflagged cross-correlation sample is its whitened residual norm
+// z = sqrt(sum_c w_c |r_c|^2), computed in float32 with every operation rounded (no fused
+// multiply-add) in a fixed order.  Median and MAD are exact order statistics (the
+// floor((n - 1) / 2)-th smallest value), found by a radix select over the float bit
+// patterns, which order like the values for non-negative floats.  A sample is flagged when
+// |z - median| > fl32(threshold * 1.4826) * MAD in float32.
+
+namespace {
+
+constexpr unsigned MAD_SENTINEL = 0x7f800000u;   // +inf: excluded samples sort after the rest
+
+__device__ __forceinline__ bool mad_use(const int4 *rows, const uint8_t *flag, long i, int n_chan)
+{
+    const int4 r = rows[i / n_chan];
+    return r.x != r.y && !(flag && flag[i]);
+}
+
+__global__ void mad_z_kernel(long n_vis, int n_chan, const float4 *resid, const float4 *weight, const uint8_t *flag,
+                             const int4 *rows, unsigned *keys, unsigned long long *n_used)
+{
+    unsigned cnt = 0;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n_vis; i += (long)gridDim.x * blockDim.x) {
+        unsigned key = MAD_SENTINEL;
+        if (mad_use(rows, flag, i, n_chan)) {
+            const float4 lo = resid[2 * i], hi = resid[2 * i + 1];
+            const float4 w = weight[i];
+            const float t0 = __fadd_rn(__fmul_rn(lo.x, lo.x), __fmul_rn(lo.y, lo.y));
+            const float t1 = __fadd_rn(__fmul_rn(lo.z, lo.z), __fmul_rn(lo.w, lo.w));
+            const float t2 = __fadd_rn(__fmul_rn(hi.x, hi.x), __fmul_rn(hi.y, hi.y));
+            const float t3 = __fadd_rn(__fmul_rn(hi.z, hi.z), __fmul_rn(hi.w, hi.w));
+            float acc = __fmul_rn(w.x, t0);
+            acc = __fadd_rn(acc, __fmul_rn(w.y, t1));
+            acc = __fadd_rn(acc, __fmul_rn(w.z, t2));
+            acc = __fadd_rn(acc, __fmul_rn(w.w, t3));
+            key = __float_as_uint(__fsqrt_rn(acc));
+            ++cnt;
+        }
+        keys[i] = key;
+    }
+    for (int d = 16; d > 0; d >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, d);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(n_used, (unsigned long long)cnt);
+}
+
+// histogram of the 8 bits at `shift` of the keys whose bits above them equal `prefix`
+__global__ void mad_hist_kernel(long n, const unsigned *keys, unsigned prefix, unsigned mask, int shift, unsigned *hist)
+{
+    __shared__ unsigned h[256];
+    for (int t = threadIdx.x; t < 256; t += blockDim.x) h[t] = 0;
+    __syncthreads();
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const unsigned k = keys[i];
+        if ((k & mask) == prefix) atomicAdd(&h[(k >> shift) & 0xffu], 1u);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 256; t += blockDim.x)
+        if (h[t]) atomicAdd(&hist[t], h[t]);
+}
+
+// keys of the used samples become the bits of |z - median|
+__global__ void mad_dev_kernel(long n_vis, int n_chan, const uint8_t *flag, const int4 *rows, float med, unsigned *keys)
+{
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n_vis; i += (long)gridDim.x * blockDim.x)
+        if (mad_use(rows, flag, i, n_chan)) keys[i] = __float_as_uint(fabsf(__fsub_rn(__uint_as_float(keys[i]), med)));
+}
+
+__global__ void mad_flag_kernel(long n_vis, int n_chan, const uint8_t *flag, const int4 *rows, const unsigned *keys,
+                                float thr, uint8_t *out, unsigned long long *n_flagged)
+{
+    unsigned cnt = 0;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n_vis; i += (long)gridDim.x * blockDim.x) {
+        const bool f = mad_use(rows, flag, i, n_chan) && __uint_as_float(keys[i]) > thr;
+        out[i] = f ? 1 : 0;
+        cnt += f ? 1u : 0u;
+    }
+    for (int d = 16; d > 0; d >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, d);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(n_flagged, (unsigned long long)cnt);
+}
+
+} // namespace
+
+// the k-th smallest of n keys (0-based), k < n: four 8-bit radix passes from the top bits
+static int mad_select(qc_ctx *c, const unsigned *keys, long n, unsigned long long k, unsigned *hist, cudaStream_t st,
+                      unsigned &out)
+{
+    unsigned prefix = 0, mask = 0;
+    unsigned h[256];
+    for (int shift = 24; shift >= 0; shift -= 8) {
+        CK(cudaMemsetAsync(hist, 0, 256 * sizeof(unsigned), st));
+        mad_hist_kernel<<<grid_for(n, 256, c->sm_count), 256, 0, st>>>(n, keys, prefix, mask, shift, hist);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(h, hist, sizeof h, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        unsigned long long cum = 0;
+        int b = 0;
+        for (; b < 256; ++b) {
+            if (cum + h[b] > k) break;
+            cum += h[b];
+        }
+        if (b == 256) return c->fail(QC_ECUDA, "radix select lost its element");
+        k -= cum;
+        prefix |= (unsigned)b << shift;
+        mask |= 0xffu << shift;
+    }
+    out = prefix;
+    return QC_OK;
+}
+
+extern "C" int qc_mad_flag(qc_ctx *c, const qc_term *terms, int32_t n_terms, double threshold, uint8_t *flags_out,
+                           int32_t out_memory, int64_t *n_flagged)
+{
+    if (!c) return QC_EINVAL;
+    c->err.clear();
+    if (!flags_out) return c->fail(QC_EINVAL, "flags_out is NULL");
+    if (!(threshold > 0) || !std::isfinite(threshold)) return c->fail(QC_EINVAL, "threshold must be positive and finite");
+    if (out_memory != QC_MEM_HOST && out_memory != QC_MEM_DEVICE) return c->fail(QC_EINVAL, "out_memory invalid");
+    int rc = c->validate_terms(terms, n_terms, false);
+    if (rc) return rc;
+    cudaStream_t st = c->own_stream;
+    std::vector<qc_term> xt;
+    if ((rc = c->expand_terms(terms, n_terms, xt, st))) return rc;
+    Chain chain;
+    if ((rc = c->stage_terms(xt.data(), n_terms, st, chain))) return rc;
+    const long n_vis = (long)c->n_row * c->n_chan;
+    if ((rc = c->ensure(c->scalars, 64))) return rc;
+    if ((rc = c->ensure(c->resid_stage, nbytes<float4>(2 * (size_t)std::max(1L, n_vis))))) return rc;
+    if ((rc = c->ensure(c->mad_keys, nbytes<unsigned>((size_t)std::max(1L, n_vis))))) return rc;
+    if ((rc = c->ensure(c->mad_hist, 256 * sizeof(unsigned) + 2 * sizeof(unsigned long long)))) return rc;
+    double *d_chi2 = (double *)c->scalars.ptr;
+    float4 *dres = (float4 *)c->resid_stage.ptr;
+    unsigned *keys = (unsigned *)c->mad_keys.ptr;
+    unsigned *hist = (unsigned *)c->mad_hist.ptr;
+    unsigned long long *cnt = (unsigned long long *)((char *)c->mad_hist.ptr + 256 * sizeof(unsigned));
+    uint8_t *dout = (uint8_t *)flags_out;
+    if (out_memory == QC_MEM_HOST) {
+        if ((rc = c->ensure(c->mad_out, (size_t)std::max(1L, n_vis)))) return rc;
+        dout = (uint8_t *)c->mad_out.ptr;
+    }
+    if (n_vis == 0) {
+        if (n_flagged) *n_flagged = 0;
+        return QC_OK;
+    }
+    if ((rc = c->run_residual(chain, dres, d_chi2, st))) return rc;
+    CK(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), st));
+    const int grid = grid_for(n_vis, 256, c->sm_count);
+    mad_z_kernel<<<grid, 256, 0, st>>>(n_vis, c->n_chan, dres, c->d_weight, c->d_flag, c->d_rows, keys, cnt);
+    CK(cudaGetLastError());
+    unsigned long long hc[2];
+    CK(cudaMemcpyAsync(hc, cnt, sizeof hc, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    float thr = 0.f;
+    if (hc[0] > 0) {
+        const unsigned long long k = (hc[0] - 1) / 2;
+        unsigned med_bits = 0, mad_bits = 0;
+        if ((rc = mad_select(c, keys, n_vis, k, hist, st, med_bits))) return rc;
+        float med;
+        memcpy(&med, &med_bits, sizeof med);
+        mad_dev_kernel<<<grid, 256, 0, st>>>(n_vis, c->n_chan, c->d_flag, c->d_rows, med, keys);
+        CK(cudaGetLastError());
+        if ((rc = mad_select(c, keys, n_vis, k, hist, st, mad_bits))) return rc;
+        float mad;
+        memcpy(&mad, &mad_bits, sizeof mad);
+        const float factor = (float)(threshold * 1.4826);
+        thr = factor * mad;
+    }
+    mad_flag_kernel<<<grid, 256, 0, st>>>(n_vis, c->n_chan, hc[0] > 0 ? c->d_flag : nullptr, c->d_rows, keys,
+                                         hc[0] > 0 ? thr : INFINITY, dout, cnt + 1);
+    CK(cudaGetLastError());
+    if (out_memory == QC_MEM_HOST) CK(cudaMemcpyAsync(flags_out, dout, (size_t)n_vis, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(hc + 1, cnt + 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (n_flagged) *n_flagged = (int64_t)hc[1];
+    return QC_OK;
+}

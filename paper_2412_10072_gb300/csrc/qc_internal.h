@@ -93,6 +93,9 @@ struct qc_ctx {
     std::vector<cudaEvent_t> events;
     TermBufs tb[QC_MAX_TERMS];
     Buf scalars;                      // counters and chi^2 scratch
+    Buf mad_keys;                     // MAD flagging: uint32 [n_vis] statistic keys
+    Buf mad_hist;                     // MAD flagging: uint32 [256] histogram + counters
+    Buf mad_out;                      // MAD flagging: uint8 [n_vis] flags (host output staging)
     Buf resid_stage;
     long long launches = 0;
     std::vector<const void *> configured_fns;   // kernels whose dynamic smem limit was raised

@@ -1,0 +1,83 @@
+"""MAD residual flagging through the C ABI (qc_mad_flag) against the oracle, bit for bit.
+
+With unit diagonal gains the chain is the identity, so the kernel's residual is exactly the
+float32 difference D - M, which the oracle forms the same way; the statistics and the
+decision are float32 in the same order on both sides, so the flags must be identical."""
+import numpy as np
+import pytest
+
+from oracle.mad_flag import mad_flag
+from paper_2412_10072_gb300 import qc, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _problem(seed, n_ant=9, n_time=5, n_chan=37, flag_frac=0.1, n_out=40, autos=True, zero=False):
+    rng = np.random.default_rng(seed)
+    p, q = synth.baselines(n_ant)
+    if autos:
+        p = np.concatenate([p, np.arange(n_ant)])
+        q = np.concatenate([q, np.arange(n_ant)])
+    ant1, ant2 = np.tile(p, n_time).astype(np.int32), np.tile(q, n_time).astype(np.int32)
+    tidx = np.repeat(np.arange(n_time, dtype=np.int32), p.size)
+    shp = (ant1.size, n_chan, 4)
+    model = ((rng.standard_normal(shp) + 1j * rng.standard_normal(shp)) / np.sqrt(2)).astype(np.complex64)
+    noise = 0.0 if zero else 0.1
+    data = (model + noise * (rng.standard_normal(shp) + 1j * rng.standard_normal(shp))).astype(np.complex64)
+    idx = rng.choice(shp[0] * shp[1], size=n_out, replace=False)
+    r, c = np.unravel_index(idx, shp[:2])
+    data[r, c, rng.integers(0, 4, n_out)] += (rng.uniform(2, 20, n_out) * np.exp(2j * np.pi * rng.random(n_out))
+                                              ).astype(np.complex64)
+    weight = rng.uniform(0.5, 2.0, size=shp).astype(np.float32)
+    flag = (rng.random(shp[:2]) < flag_frac).astype(np.uint8)
+    return dict(data=data, model=model, weight=weight, flag=flag, ant1=ant1, ant2=ant2, tidx=tidx, n_ant=n_ant,
+                n_time=n_time, n_chan=n_chan)
+
+
+def _unit_term(pb):
+    g = np.zeros((1, 1, pb["n_ant"], 4), np.complex64)
+    g[..., 0] = g[..., 3] = 1
+    return qc.Term("diag", np.zeros(pb["n_time"], np.int32), np.zeros(pb["n_chan"], np.int32), 1, 1, pb["n_ant"],
+                   gains=g, solve=False)
+
+
+@pytest.mark.parametrize("seed,threshold", [(1, 5.0), (2, 3.0), (3, 8.0)])
+def test_flags_match_the_oracle_bit_for_bit(seed, threshold):
+    pb = _problem(seed)
+    S = qc.Solver(pb["data"], pb["model"], pb["weight"], pb["flag"], pb["ant1"], pb["ant2"], pb["tidx"], pb["n_ant"],
+                  pb["n_time"])
+    got, n = S.mad_flag([_unit_term(pb)], threshold=threshold)
+    S.close()
+    want, (med, mad, n_want) = mad_flag(pb["data"] - pb["model"], pb["weight"], pb["flag"], pb["ant1"], pb["ant2"],
+                                        threshold=threshold)
+    np.testing.assert_array_equal(got, want)
+    assert n == n_want and n > 0
+
+
+def test_all_flagged_and_zero_residuals():
+    pb = _problem(4, flag_frac=1.0)
+    S = qc.Solver(pb["data"], pb["model"], pb["weight"], pb["flag"], pb["ant1"], pb["ant2"], pb["tidx"], pb["n_ant"],
+                  pb["n_time"])
+    got, n = S.mad_flag([_unit_term(pb)])
+    S.close()
+    assert n == 0 and not got.any()
+    # residuals zero except the planted ones: median and MAD are 0, every planted sample is flagged
+    pb = _problem(5, flag_frac=0.0, zero=True, n_out=7, autos=False)
+    S = qc.Solver(pb["data"], pb["model"], pb["weight"], pb["flag"], pb["ant1"], pb["ant2"], pb["tidx"], pb["n_ant"],
+                  pb["n_time"])
+    got, n = S.mad_flag([_unit_term(pb)])
+    S.close()
+    want, (med, mad, n_want) = mad_flag(pb["data"] - pb["model"], pb["weight"], pb["flag"], pb["ant1"], pb["ant2"])
+    assert med == 0 and mad == 0
+    np.testing.assert_array_equal(got, want)
+    assert n == n_want == 7
+
+
+def test_bad_threshold_is_rejected():
+    pb = _problem(6)
+    S = qc.Solver(pb["data"], pb["model"], pb["weight"], pb["flag"], pb["ant1"], pb["ant2"], pb["tidx"], pb["n_ant"],
+                  pb["n_time"])
+    for thr in (0.0, -1.0, float("nan")):
+        with pytest.raises(qc.QCError):
+            S.mad_flag([_unit_term(pb)], threshold=thr)
+    S.close()

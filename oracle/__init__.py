@@ -28,6 +28,9 @@ Parity status of each oracle function (what pins it, see ``tests/``):
 - ``mad_flag`` (MAD residual flagging): pinned by order statistics against
   a sort, planted outliers, the Gaussian spread of the MAD and the
   exclusion of flagged samples (``tests/test_oracle_mad.py``).
+- ``moments`` (sufficient-statistics pre-reduction of a single diagonal
+  term): its normal equations and chi^2 equal the sample-by-sample ones
+  (``tests/test_oracle_moments.py``).
 - ``mlp``: pinned by central finite differences of its own loss.
 """
 from .oracle import (OC_DIAG, OC_FULL, OC_PHASE, OC_DELAY, OracleProblem, OracleTerm, build,  # noqa: F401

@@ -696,6 +696,23 @@ def run_batched(args):
     else:
         vis_all = float(vis_iters)
     value = vis_all / (ms / 1e3)
+    # the same solves from per-baseline sufficient statistics (one data pass, iterations on the sums)
+    moments = None
+    if not dist:
+        gm = [unit.clone() for _ in range(args.steps + 1)]
+        S.solve(gm[-1], stream=stream, moments=True)
+        torch.cuda.synchronize()
+        m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        m0.record(stream)
+        mstats = [S.solve(gm[k], stream=stream, moments=True)[3] for k in range(args.steps)]
+        m1.record(stream)
+        torch.cuda.synchronize()
+        ms_m = m0.elapsed_time(m1)
+        moments = {"value": sum(x.vis_iters for x in mstats) / (ms_m / 1e3), "unit": UNIT,
+                   "ms_per_step": ms_m / args.steps, "speedup_over_sample_solve": ms / ms_m,
+                   "bytes_per_step": sum(x.bytes for x in mstats) / args.steps,
+                   "mean_iters": mstats[-1].mean_iters,
+                   "note": "qc_batch_solve_moments: one pass forms per-baseline sums, iterations use them"}
     peaks, src = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     # algorithmic bytes: 81 B per vis-iteration (every sample of every iteration); the kernel skips
@@ -746,6 +763,7 @@ def run_batched(args):
                          "mean_iters": stats[-1].mean_iters},
             "looped_plain": {"problems": int(idx.size), "value": loop_value, "unit": UNIT, "seconds": dt_loop,
                              "speedup_of_batched": value / loop_value},
+            "moments": moments,
             "cpu_baseline": cpu, "e2e": None, "clocks": clock_info,
             "gpu_launches": args.steps, "vis_iters": int(vis_all)}), flush=True)
     S.close()

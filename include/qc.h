@@ -395,6 +395,21 @@ int qc_batch_solve(qc_batch *b, void *gains, int8_t *gain_flags, int32_t *iters,
                    const qc_batch_opts *o, qc_batch_stats *stats);
 
 /*
+ * The same solve from per-baseline sufficient statistics (not in the paper).  A
+ * problem is one solution interval of one diagonal term, so the samples of a
+ * baseline enter JHJ and JHr (Eq. jhj_entry_simplified, Eq. jhr_entry_simplified)
+ * only through S_c = sum w_c |m_c|^2 and T_c = sum w_c conj(m_c) d_c per
+ * correlation.  One pass over the samples forms them (float32 sums in shared
+ * memory); the iterations then form the normal equations from them in FP64,
+ * with the update and convergence test of qc_batch_solve.  Arguments and
+ * outputs as qc_batch_solve; stats.bytes counts the one data pass.
+ * QC_EUNSUPPORTED for batches with more than 64 antennas in a problem or with
+ * a fallback start.
+ */
+int qc_batch_solve_moments(qc_batch *b, void *gains, int8_t *gain_flags, int32_t *iters, int32_t mem,
+                           const qc_batch_opts *o, qc_batch_stats *stats);
+
+/*
  * Autotuner: time the batch solve (from unit gains, `base` options, results
  * discarded) for every candidate launch shape -- threads per CTA in
  * {128, 256, 512} (the warps that share one problem), copy stages per warp

@@ -738,6 +738,179 @@ __global__ void unflag_count_kernel(const uint8_t *flag, const BProb *probs, con
     if ((threadIdx.x & 31) == 0) atomicAdd(out + pi, cnt);
 }
 
+
+// ---------------------------------------------------------------------------
+// batched solve from per-baseline sums (sufficient-statistics pre-reduction)
+// ---------------------------------------------------------------------------
+// Not in the paper.  A problem of the batch is one solution interval of one diagonal term,
+// so a baseline's samples enter JHJ and JHr only through two weighted sums per correlation c,
+// S_c = sum w_c |m_c|^2 and T_c = sum w_c conj(m_c) d_c.  One pass over the problem's samples
+// forms them per baseline in shared memory; every iteration then forms the normal equations
+// from them in FP64 (correlations XX XY YX YY = 0 1 2 3):
+//   antenna p of (p, q):  h0 = S0 |gq0|^2 + S1 |gq1|^2,   h1 = S2 |gq0|^2 + S3 |gq1|^2,
+//                         j0 = gq0 T0 + gq1 T1 - gp0 h0,  j1 = gq0 T2 + gq1 T3 - gp1 h1;
+//   antenna q through the conjugate baseline: S1 <-> S2, T -> conj(T) with T1 <-> T2, p <-> q.
+// The update and the convergence test are those of batch_kernel.
+
+constexpr int MOM_MAX_ANT = 64;   // baselines x 12 floats must fit in shared memory
+constexpr int MOM_W = 12;         // S[4], then T[4] as (re, im)
+
+__host__ __device__ constexpr int mom_bl(int p, int q, int n) { return p * (2 * n - p - 1) / 2 + (q - p - 1); }
+
+__host__ __device__ inline size_t mom_smem_bytes(int max_ant)
+{
+    const size_t m = ((size_t)max_ant * (max_ant - 1) / 2 * MOM_W * sizeof(float) + 15) / 16 * 16;
+    return m + (size_t)max_ant * 2 * sizeof(double2) + (size_t)max_ant * 6 * sizeof(double);
+}
+
+template <bool M16>
+__global__ void __launch_bounds__(256) batch_moments_kernel(const BatchArgs a)
+{
+    extern __shared__ __align__(16) unsigned char msm[];
+    const size_t mom_bytes = ((size_t)a.max_ant * (a.max_ant - 1) / 2 * MOM_W * sizeof(float) + 15) / 16 * 16;
+    float *mom = reinterpret_cast<float *>(msm);                                  // [n_bl][MOM_W]
+    double2 *g64 = reinterpret_cast<double2 *>(msm + mom_bytes);                 // [max_ant][2]
+    double *acc = reinterpret_cast<double *>(g64 + 2 * a.max_ant);               // [max_ant][6]
+    __shared__ double red[2][8];
+    __shared__ int s_done;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, n_warps = blockDim.x >> 5;
+    const int pi = a.order[blockIdx.x];
+    const BProb P = a.probs[pi];
+    const int na = P.n_ant, nc = P.n_chan, n_bl = na * (na - 1) / 2;
+    for (int i = tid; i < n_bl * MOM_W; i += blockDim.x) mom[i] = 0.f;
+    for (int i = tid; i < na; i += blockDim.x) {
+        const float2 g0 = a.gains[(size_t)(P.gain_off + i) * 2], g1 = a.gains[(size_t)(P.gain_off + i) * 2 + 1];
+        g64[2 * i] = make_double2(g0.x, g0.y);
+        g64[2 * i + 1] = make_double2(g1.x, g1.y);
+    }
+    __syncthreads();
+    // one pass over the samples: the baseline sums
+    const long long n_samp = (long long)P.n_rows * nc;
+    for (long long s = tid; s < n_samp; s += blockDim.x) {
+        const int row = (int)(s / nc);
+        const int2 pq = a.ants[P.row_off + row];
+        if (pq.x == pq.y) continue;
+        const long long sg = P.vis_off + s;
+        if (a.flag && a.flag[sg]) continue;
+        J2 D = j_from(a.vis[2 * sg], a.vis[2 * sg + 1]);
+        J2 M;
+        if constexpr (M16) {
+            const uint4 h = a.model16[sg];
+            const float sc = a.row_scale[P.row_off + row];
+            M.a = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.x)), sc);
+            M.b = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.y)), sc);
+            M.c = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.z)), sc);
+            M.d = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.w)), sc);
+        } else {
+            M = j_from(a.model[2 * sg], a.model[2 * sg + 1]);
+        }
+        float4 w = a.weight[sg];
+        int p = pq.x, q = pq.y;
+        if (p > q) {          // the conjugate baseline: D, M -> D^H, M^H, weights permuted
+            D = j_herm(D);
+            M = j_herm(M);
+            w = make_float4(w.x, w.z, w.y, w.w);
+            const int t = p; p = q; q = t;
+        }
+        float *m = mom + (size_t)mom_bl(p, q, na) * MOM_W;
+        const float2 Mv[4] = { M.a, M.b, M.c, M.d }, Dv[4] = { D.a, D.b, D.c, D.d };
+        const float wv[4] = { w.x, w.y, w.z, w.w };
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            atomicAdd(&m[c], wv[c] * cnorm2(Mv[c]));
+            const float2 t = cscale(cmulc(Dv[c], Mv[c]), wv[c]);      // w conj(m) d
+            atomicAdd(&m[4 + 2 * c], t.x);
+            atomicAdd(&m[5 + 2 * c], t.y);
+        }
+    }
+    __syncthreads();
+    int k;
+    for (k = 1; k <= a.max_iter; ++k) {
+        for (int i = tid; i < na * 6; i += blockDim.x) acc[i] = 0.0;
+        __syncthreads();
+        for (int idx = tid; idx < na * na; idx += blockDim.x) {
+            const int p = idx / na, q = idx - (idx / na) * na;
+            if (p >= q) continue;
+            const float *m = mom + (size_t)mom_bl(p, q, na) * MOM_W;
+            const double S0 = m[0], S1 = m[1], S2 = m[2], S3 = m[3];
+            const double2 T0 = make_double2(m[4], m[5]), T1 = make_double2(m[6], m[7]);
+            const double2 T2 = make_double2(m[8], m[9]), T3 = make_double2(m[10], m[11]);
+            const double2 gp0 = g64[2 * p], gp1 = g64[2 * p + 1], gq0 = g64[2 * q], gq1 = g64[2 * q + 1];
+            const double aq0 = gq0.x * gq0.x + gq0.y * gq0.y, aq1 = gq1.x * gq1.x + gq1.y * gq1.y;
+            const double ap0 = gp0.x * gp0.x + gp0.y * gp0.y, ap1 = gp1.x * gp1.x + gp1.y * gp1.y;
+            auto mul = [](double2 x, double2 y) { return make_double2(x.x * y.x - x.y * y.y, x.x * y.y + x.y * y.x); };
+            auto cj = [](double2 x) { return make_double2(x.x, -x.y); };
+            // antenna p through (p, q)
+            const double h0 = S0 * aq0 + S1 * aq1, h1 = S2 * aq0 + S3 * aq1;
+            const double2 u0 = mul(gq0, T0), u1 = mul(gq1, T1), u2 = mul(gq0, T2), u3 = mul(gq1, T3);
+            atomicAdd(&acc[p * 6 + 0], h0);
+            atomicAdd(&acc[p * 6 + 1], h1);
+            atomicAdd(&acc[p * 6 + 2], u0.x + u1.x - gp0.x * h0);
+            atomicAdd(&acc[p * 6 + 3], u0.y + u1.y - gp0.y * h0);
+            atomicAdd(&acc[p * 6 + 4], u2.x + u3.x - gp1.x * h1);
+            atomicAdd(&acc[p * 6 + 5], u2.y + u3.y - gp1.y * h1);
+            // antenna q through the conjugate baseline (q, p)
+            const double k0 = S0 * ap0 + S2 * ap1, k1 = S1 * ap0 + S3 * ap1;
+            const double2 v0 = mul(gp0, cj(T0)), v1 = mul(gp1, cj(T2)), v2 = mul(gp0, cj(T1)), v3 = mul(gp1, cj(T3));
+            atomicAdd(&acc[q * 6 + 0], k0);
+            atomicAdd(&acc[q * 6 + 1], k1);
+            atomicAdd(&acc[q * 6 + 2], v0.x + v1.x - gq0.x * k0);
+            atomicAdd(&acc[q * 6 + 3], v0.y + v1.y - gq0.y * k0);
+            atomicAdd(&acc[q * 6 + 4], v2.x + v3.x - gq1.x * k1);
+            atomicAdd(&acc[q * 6 + 5], v2.y + v3.y - gq1.y * k1);
+        }
+        __syncthreads();
+        // FP64 per-antenna solve and update, as batch_kernel
+        const double alpha = a.damping_mode == QC_DAMP_ALTERNATE ? ((k % 2 == 0) ? 0.5 : 1.0)
+                                                                  : (a.damping > 0 ? a.damping : 1.0);
+        double num = 0, den = 0;
+        for (int ant = tid; ant < na; ant += blockDim.x) {
+            const double h0 = acc[ant * 6], h1 = acc[ant * 6 + 1];
+            const double hmax = fmax(h0, h1), hmin = fmin(h0, h1);
+            const bool singular = !(h0 + h1 > 0) || !(hmin / hmax >= 1e-12);
+            double2 d0 = make_double2(0, 0), d1 = d0;
+            if (!singular) {
+                d0 = make_double2(alpha * acc[ant * 6 + 2] / h0, alpha * acc[ant * 6 + 3] / h0);
+                d1 = make_double2(alpha * acc[ant * 6 + 4] / h1, alpha * acc[ant * 6 + 5] / h1);
+            }
+            double2 G0 = g64[2 * ant], G1 = g64[2 * ant + 1];
+            G0.x += d0.x; G0.y += d0.y; G1.x += d1.x; G1.y += d1.y;
+            g64[2 * ant] = G0;
+            g64[2 * ant + 1] = G1;
+            if (a.gain_flags) a.gain_flags[P.gain_off + ant] = singular ? 1 : 0;
+            num += d0.x * d0.x + d0.y * d0.y + d1.x * d1.x + d1.y * d1.y;
+            den += G0.x * G0.x + G0.y * G0.y + G1.x * G1.x + G1.y * G1.y;
+        }
+        for (int d = 16; d > 0; d >>= 1) {
+            num += __shfl_down_sync(0xffffffffu, num, d);
+            den += __shfl_down_sync(0xffffffffu, den, d);
+        }
+        if (lane == 0) { red[0][warp] = num; red[1][warp] = den; }
+        __syncthreads();
+        if (tid == 0) {
+            double tn = 0, td = 0;
+            for (int i = 0; i < n_warps; ++i) { tn += red[0][i]; td += red[1][i]; }
+            const double delta = td > 0 ? sqrt(tn / td) : 0.0;
+            s_done = delta < a.tol ? 1 : 0;
+        }
+        __syncthreads();
+        if (s_done) break;
+    }
+    const int done_iters = k > a.max_iter ? a.max_iter : k;
+    for (int i = tid; i < na; i += blockDim.x) {
+        const double2 G0 = g64[2 * i], G1 = g64[2 * i + 1];
+        a.gains[(size_t)(P.gain_off + i) * 2] = make_float2((float)G0.x, (float)G0.y);
+        a.gains[(size_t)(P.gain_off + i) * 2 + 1] = make_float2((float)G1.x, (float)G1.y);
+    }
+    if (tid == 0) {
+        if (a.iters) a.iters[pi] = done_iters;
+        const unsigned long long ns = (unsigned long long)n_samp;
+        atomicAdd(a.vis_iters, ns * done_iters);
+        // one pass over the data
+        atomicAdd(a.bytes, (a.flag ? ns : 0ull) + (unsigned long long)P.n_unflag * (M16 ? 64ull : 80ull));
+    }
+}
+
 } // namespace
 
 // ---------------------------------------------------------------------------
@@ -1187,6 +1360,83 @@ extern "C" int qc_batch_solve(qc_batch *b, void *gains, int8_t *gain_flags, int3
     def.damping_mode = QC_DAMP_ALTERNATE;
     def.use_graph = 1;
     return batch_solve_impl(b, gains, gain_flags, iters, mem, o ? o : &def, stats, false);
+}
+
+extern "C" int qc_batch_solve_moments(qc_batch *b, void *gains, int8_t *gain_flags, int32_t *iters, int32_t mem,
+                                      const qc_batch_opts *o, qc_batch_stats *stats)
+{
+    if (!b) return QC_EINVAL;
+    b->err.clear();
+    qc_batch_opts def;
+    memset(&def, 0, sizeof def);
+    def.max_iter = 20;
+    def.tol = 1e-6;
+    def.damping_mode = QC_DAMP_ALTERNATE;
+    if (!o) o = &def;
+    if (!gains) return b->fail(QC_EINVAL, "gains is NULL");
+    if (mem != QC_MEM_HOST && mem != QC_MEM_DEVICE) return b->fail(QC_EINVAL, "mem must be QC_MEM_HOST or DEVICE");
+    if (o->max_iter < 1) return b->fail(QC_EINVAL, "max_iter must be >= 1");
+    if (!(o->tol >= 0)) return b->fail(QC_EINVAL, "tol must be >= 0");
+    if (o->damping_mode != QC_DAMP_CONST && o->damping_mode != QC_DAMP_ALTERNATE) return b->fail(QC_EINVAL, "damping_mode");
+    if (o->fallback_gains || o->fallback_chi2) return b->fail(QC_EUNSUPPORTED, "no fallback start in the moments solve");
+    if (b->max_ant > MOM_MAX_ANT) return b->fail(QC_EUNSUPPORTED, "the moments solve takes at most 64 antennas");
+    cudaStream_t st = o->stream ? (cudaStream_t)o->stream : b->own_stream;
+    const size_t gbytes = (size_t)b->total_ant * 2 * sizeof(float2);
+    unsigned char *stage = (unsigned char *)b->gstage;
+    float2 *dg = mem == QC_MEM_DEVICE ? (float2 *)gains : (float2 *)stage;
+    int8_t *dflags = mem == QC_MEM_DEVICE ? gain_flags : (gain_flags ? (int8_t *)(stage + gbytes) : nullptr);
+    int *diters = mem == QC_MEM_DEVICE ? iters
+                                       : (iters ? (int *)(stage + gbytes + ((b->total_ant + 15) / 16) * 16) : nullptr);
+    BatchArgs a = batch_args(b);
+    a.order = b->order_lpt;
+    a.gains = dg;
+    a.gain_flags = dflags;
+    a.iters = diters;
+    a.max_iter = o->max_iter;
+    a.damping_mode = o->damping_mode;
+    a.damping = o->damping;
+    a.tol = o->tol;
+    const size_t smem = mom_smem_bytes(std::max(2, b->max_ant));
+    const void *fn = b->m16 ? (const void *)batch_moments_kernel<true> : (const void *)batch_moments_kernel<false>;
+    BCK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    BCK(cudaEventRecord(b->ev0, st));
+    if (mem == QC_MEM_HOST) BCK(cudaMemcpyAsync(dg, gains, gbytes, cudaMemcpyHostToDevice, st));
+    BCK(cudaMemsetAsync(b->counters, 0, 2 * sizeof(unsigned long long), st));
+    if (b->m16) batch_moments_kernel<true><<<b->n_prob, 256, smem, st>>>(a);
+    else batch_moments_kernel<false><<<b->n_prob, 256, smem, st>>>(a);
+    BCK(cudaGetLastError());
+    if (mem == QC_MEM_HOST) {
+        BCK(cudaMemcpyAsync(gains, dg, gbytes, cudaMemcpyDeviceToHost, st));
+        if (gain_flags) BCK(cudaMemcpyAsync(gain_flags, dflags, (size_t)b->total_ant, cudaMemcpyDeviceToHost, st));
+        if (iters) BCK(cudaMemcpyAsync(iters, diters, sizeof(int) * b->n_prob, cudaMemcpyDeviceToHost, st));
+    }
+    unsigned long long hc[2];
+    BCK(cudaMemcpyAsync(hc, b->counters, sizeof hc, cudaMemcpyDeviceToHost, st));
+    BCK(cudaEventRecord(b->ev1, st));
+    BCK(cudaStreamSynchronize(st));
+    float ms = 0;
+    BCK(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+    if (stats) {
+        qc_batch_stats S;
+        memset(&S, 0, sizeof S);
+        S.ms = ms;
+        S.vis_iters = (int64_t)hc[0];
+        S.bytes = (int64_t)hc[1];
+        S.threads = 256;
+        S.ctas_per_sm = 0;
+        S.schedule = QC_SCHED_LPT;
+        S.grid = b->n_prob;
+        double tot_vis = 0;
+        for (const BProb &Pp : b->hprobs) tot_vis += (double)Pp.n_rows * Pp.n_chan;
+        S.mean_iters = tot_vis > 0 ? (double)hc[0] / tot_vis : 0;
+        if (iters && mem == QC_MEM_HOST) {
+            int mx = 0;
+            for (int i = 0; i < b->n_prob; ++i) mx = std::max(mx, iters[i]);
+            S.n_iter_max = mx;
+        }
+        *stats = S;
+    }
+    return QC_OK;
 }
 
 extern "C" int qc_batch_autotune(qc_batch *b, const qc_batch_opts *base, qc_batch_stats *best, int32_t *n_tried)

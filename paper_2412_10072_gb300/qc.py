@@ -341,6 +341,8 @@ def _load_batch(lib):
     lib.qc_batch_create.argtypes = [C.POINTER(_BatchProblem), C.POINTER(vp)]
     lib.qc_batch_create.restype = C.c_int
     lib.qc_batch_solve.argtypes = [vp, vp, vp, vp, i32, C.POINTER(_BatchOpts), C.POINTER(BatchStats)]
+    lib.qc_batch_solve_moments.argtypes = [vp, vp, vp, vp, i32, C.POINTER(_BatchOpts), C.POINTER(BatchStats)]
+    lib.qc_batch_solve_moments.restype = C.c_int
     lib.qc_batch_solve.restype = C.c_int
     lib.qc_batch_autotune.argtypes = [vp, C.POINTER(_BatchOpts), C.POINTER(BatchStats), C.POINTER(C.c_int32)]
     lib.qc_batch_autotune.restype = C.c_int
@@ -411,10 +413,12 @@ class BatchSolver:
     def solve(self, gains=None, max_iter: int = 20, tol: float = 1e-6, damping_mode: int = QC_DAMP_ALTERNATE,
               damping: float = 1.0, stream=None, threads: int = 0, ctas_per_sm: int = 0,
               schedule: int = QC_SCHED_AUTO, use_graph: bool = True, want_flags: bool = True, depth: int = 0,
-              fallback=None):
+              fallback=None, moments: bool = False):
         """Solve in place; returns (gains, gain_flags, iters, BatchStats).  fallback: optional
         (device gains [sum n_ant][2] complex64, device chi^2 [n_prob] float64) -- a problem whose
-        starting gains fit worse than its fallback chi^2 restarts from the fallback gains."""
+        starting gains fit worse than its fallback chi^2 restarts from the fallback gains.
+        moments: one pass forms per-baseline sums and the iterations use them
+        (qc_batch_solve_moments; at most 64 antennas, no fallback)."""
         if gains is None:
             gains = self.unit_gains()
         dev = _is_dev(gains)
@@ -429,8 +433,9 @@ class BatchSolver:
         o = self._opts(max_iter, tol, damping_mode, damping, stream, threads, ctas_per_sm, schedule, use_graph, depth,
                        fallback)
         s = BatchStats()
-        rc = self._lib.qc_batch_solve(self._h, _addr(gains), _addr(flags), _addr(iters),
-                                      QC_MEM_DEVICE if dev else QC_MEM_HOST, C.byref(o), C.byref(s))
+        fn = self._lib.qc_batch_solve_moments if moments else self._lib.qc_batch_solve
+        rc = fn(self._h, _addr(gains), _addr(flags), _addr(iters), QC_MEM_DEVICE if dev else QC_MEM_HOST, C.byref(o),
+                C.byref(s))
         if rc != QC_OK:
             self._err(rc)
         return gains, flags, iters, s

@@ -124,3 +124,57 @@ def test_batch_fully_flagged_and_autocorrelation_rows():
     assert np.all(flags[offs[2]:offs[3]] == 1)
     assert np.array_equal(g[offs[2]:offs[3]], g0[offs[2]:offs[3]])
     compare(sub_batch(b, 4), g[offs[4]:offs[5]], flags[offs[4]:offs[5]], iters[4:5])
+
+
+# ---------------------------------------------------------------------------
+# the same solve from per-baseline sufficient statistics (qc_batch_solve_moments)
+# ---------------------------------------------------------------------------
+
+def test_moments_solve_matches_oracle_per_problem():
+    b = small_batch(n=24, seed_base=900)
+    S = solver_of(b)
+    g, flags, iters, st = S.solve(moments=True)
+    S.close()
+    compare(b, g, flags, iters)
+    assert st.vis_iters > 0
+
+
+@pytest.mark.parametrize("m16", [False, True])
+def test_moments_solve_matches_the_sample_solve(m16):
+    """Both solves form the same normal equations (the sums in another order), so they reach the
+    same gains within the solver tolerance and the same iteration counts within one."""
+    b = small_batch(n=48, seed_base=950)
+    S = solver_of(b, model_fp16=m16)
+    g1, f1, it1, _ = S.solve()
+    g2, f2, it2, s2 = S.solve(moments=True)
+    S.close()
+    assert np.array_equal(f1, f2)
+    offs = np.concatenate([[0], np.cumsum(b.n_ant)])
+    for i in range(b.n_prob):
+        good = np.where(f1[offs[i]:offs[i + 1]] == 0)[0]
+        if good.size < 2:
+            continue
+        a = reference_diag(gains_of(b, g1, i)[good][None])[0]
+        c = reference_diag(gains_of(b, g2, i)[good][None])[0]
+        assert rel_err(c, a) < 1e-4, (i, rel_err(c, a))
+    assert np.abs(it1.astype(int) - it2.astype(int)).max() <= 1
+    # one pass over the data instead of one per iteration
+    assert s2.bytes * 2 < s2.vis_iters * 64
+
+
+def test_moments_solve_fully_flagged_and_autocorrelations():
+    b = small_batch(n=6, seed_base=710)
+    flag = np.asarray(b.flag).copy()
+    flag[b.vis_offset[2]:b.vis_offset[3]] = 1
+    b.flag = flag
+    a2 = b.ant2.copy()
+    a2[b.row_offset[4]] = b.ant1[b.row_offset[4]]
+    b.ant2 = a2
+    S = solver_of(b)
+    g0 = S.unit_gains()
+    g, flags, iters, _ = S.solve(g0.copy(), moments=True)
+    S.close()
+    offs = np.concatenate([[0], np.cumsum(b.n_ant)])
+    assert np.all(flags[offs[2]:offs[3]] == 1)
+    assert np.array_equal(g[offs[2]:offs[3]], g0[offs[2]:offs[3]])
+    compare(b, g, flags, iters)

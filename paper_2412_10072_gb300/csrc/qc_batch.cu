@@ -784,80 +784,123 @@ __global__ void __launch_bounds__(256) batch_moments_kernel(const BatchArgs a)
         g64[2 * i + 1] = make_double2(g1.x, g1.y);
     }
     __syncthreads();
-    // one pass over the samples: the baseline sums
+    // one pass over the samples: the baseline sums.  The lanes of a warp take consecutive
+    // samples; where they all belong to one baseline (a row of 32 channels or more) a
+    // transposed reduction leaves one total per sum and one shared add each, otherwise every
+    // lane adds its own (short runs of equal baselines: few conflicts).
     const long long n_samp = (long long)P.n_rows * nc;
-    for (long long s = tid; s < n_samp; s += blockDim.x) {
-        const int row = (int)(s / nc);
-        const int2 pq = a.ants[P.row_off + row];
-        if (pq.x == pq.y) continue;
-        const long long sg = P.vis_off + s;
-        if (a.flag && a.flag[sg]) continue;
-        J2 D = j_from(a.vis[2 * sg], a.vis[2 * sg + 1]);
-        J2 M;
-        if constexpr (M16) {
-            const uint4 h = a.model16[sg];
-            const float sc = a.row_scale[P.row_off + row];
-            M.a = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.x)), sc);
-            M.b = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.y)), sc);
-            M.c = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.z)), sc);
-            M.d = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.w)), sc);
-        } else {
-            M = j_from(a.model[2 * sg], a.model[2 * sg + 1]);
-        }
-        float4 w = a.weight[sg];
-        int p = pq.x, q = pq.y;
-        if (p > q) {          // the conjugate baseline: D, M -> D^H, M^H, weights permuted
-            D = j_herm(D);
-            M = j_herm(M);
-            w = make_float4(w.x, w.z, w.y, w.w);
-            const int t = p; p = q; q = t;
-        }
-        float *m = mom + (size_t)mom_bl(p, q, na) * MOM_W;
-        const float2 Mv[4] = { M.a, M.b, M.c, M.d }, Dv[4] = { D.a, D.b, D.c, D.d };
-        const float wv[4] = { w.x, w.y, w.z, w.w };
+    for (long long base = (long long)warp * 32; base < n_samp; base += blockDim.x) {
+        const long long s = base + lane;
+        float v[16];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            atomicAdd(&m[c], wv[c] * cnorm2(Mv[c]));
-            const float2 t = cscale(cmulc(Dv[c], Mv[c]), wv[c]);      // w conj(m) d
-            atomicAdd(&m[4 + 2 * c], t.x);
-            atomicAdd(&m[5 + 2 * c], t.y);
+        for (int i = 0; i < 16; ++i) v[i] = 0.f;
+        int key = -1;
+        if (s < n_samp) {
+            const int row = (int)(s / nc);
+            const int2 pq = a.ants[P.row_off + row];
+            const long long sg = P.vis_off + s;
+            if (pq.x != pq.y && !(a.flag && a.flag[sg])) {
+                J2 D = j_from(a.vis[2 * sg], a.vis[2 * sg + 1]);
+                J2 M;
+                if constexpr (M16) {
+                    const uint4 h = a.model16[sg];
+                    const float sc = a.row_scale[P.row_off + row];
+                    M.a = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.x)), sc);
+                    M.b = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.y)), sc);
+                    M.c = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.z)), sc);
+                    M.d = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.w)), sc);
+                } else {
+                    M = j_from(a.model[2 * sg], a.model[2 * sg + 1]);
+                }
+                float4 w = a.weight[sg];
+                int p = pq.x, q = pq.y;
+                if (p > q) {      // the conjugate baseline: D, M -> D^H, M^H, weights permuted
+                    D = j_herm(D);
+                    M = j_herm(M);
+                    w = make_float4(w.x, w.z, w.y, w.w);
+                    const int t = p; p = q; q = t;
+                }
+                key = mom_bl(p, q, na);
+                const float2 Mv[4] = { M.a, M.b, M.c, M.d }, Dv[4] = { D.a, D.b, D.c, D.d };
+                const float wv[4] = { w.x, w.y, w.z, w.w };
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    v[c] = wv[c] * cnorm2(Mv[c]);
+                    const float2 t = cscale(cmulc(Dv[c], Mv[c]), wv[c]);      // w conj(m) d
+                    v[4 + 2 * c] = t.x;
+                    v[5 + 2 * c] = t.y;
+                }
+            }
+        }
+        const int k0 = __shfl_sync(0xffffffffu, key, 0);
+        if (__all_sync(0xffffffffu, key == k0)) {
+            if (k0 >= 0) {
+                // 16 slots (12 sums + 4 zeros) over 32 lanes: four halving exchanges, then a
+                // butterfly; lane l holds the total of slot l >> 1
+                int idx = 0;
+#pragma unroll
+                for (int lev = 0; lev < 4; ++lev) {
+                    const int d = 16 >> lev, h = 8 >> lev;
+                    const bool up = (lane & d) != 0;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        if (i < h) {
+                            const float send = up ? v[i] : v[i + h];
+                            const float keep = up ? v[i + h] : v[i];
+                            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, d);
+                        }
+                    }
+                    if (up) idx += h;
+                }
+                v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+                if ((lane & 1) == 0 && idx < MOM_W) atomicAdd(&mom[(size_t)k0 * MOM_W + idx], v[0]);
+            }
+        } else if (key >= 0) {
+#pragma unroll
+            for (int i = 0; i < MOM_W; ++i) atomicAdd(&mom[(size_t)key * MOM_W + i], v[i]);
         }
     }
     __syncthreads();
     int k;
     for (k = 1; k <= a.max_iter; ++k) {
-        for (int i = tid; i < na * 6; i += blockDim.x) acc[i] = 0.0;
-        __syncthreads();
-        for (int idx = tid; idx < na * na; idx += blockDim.x) {
-            const int p = idx / na, q = idx - (idx / na) * na;
-            if (p >= q) continue;
-            const float *m = mom + (size_t)mom_bl(p, q, na) * MOM_W;
-            const double S0 = m[0], S1 = m[1], S2 = m[2], S3 = m[3];
-            const double2 T0 = make_double2(m[4], m[5]), T1 = make_double2(m[6], m[7]);
-            const double2 T2 = make_double2(m[8], m[9]), T3 = make_double2(m[10], m[11]);
-            const double2 gp0 = g64[2 * p], gp1 = g64[2 * p + 1], gq0 = g64[2 * q], gq1 = g64[2 * q + 1];
-            const double aq0 = gq0.x * gq0.x + gq0.y * gq0.y, aq1 = gq1.x * gq1.x + gq1.y * gq1.y;
-            const double ap0 = gp0.x * gp0.x + gp0.y * gp0.y, ap1 = gp1.x * gp1.x + gp1.y * gp1.y;
-            auto mul = [](double2 x, double2 y) { return make_double2(x.x * y.x - x.y * y.y, x.x * y.y + x.y * y.x); };
-            auto cj = [](double2 x) { return make_double2(x.x, -x.y); };
-            // antenna p through (p, q)
-            const double h0 = S0 * aq0 + S1 * aq1, h1 = S2 * aq0 + S3 * aq1;
-            const double2 u0 = mul(gq0, T0), u1 = mul(gq1, T1), u2 = mul(gq0, T2), u3 = mul(gq1, T3);
-            atomicAdd(&acc[p * 6 + 0], h0);
-            atomicAdd(&acc[p * 6 + 1], h1);
-            atomicAdd(&acc[p * 6 + 2], u0.x + u1.x - gp0.x * h0);
-            atomicAdd(&acc[p * 6 + 3], u0.y + u1.y - gp0.y * h0);
-            atomicAdd(&acc[p * 6 + 4], u2.x + u3.x - gp1.x * h1);
-            atomicAdd(&acc[p * 6 + 5], u2.y + u3.y - gp1.y * h1);
-            // antenna q through the conjugate baseline (q, p)
-            const double k0 = S0 * ap0 + S2 * ap1, k1 = S1 * ap0 + S3 * ap1;
-            const double2 v0 = mul(gp0, cj(T0)), v1 = mul(gp1, cj(T2)), v2 = mul(gp0, cj(T1)), v3 = mul(gp1, cj(T3));
-            atomicAdd(&acc[q * 6 + 0], k0);
-            atomicAdd(&acc[q * 6 + 1], k1);
-            atomicAdd(&acc[q * 6 + 2], v0.x + v1.x - gq0.x * k0);
-            atomicAdd(&acc[q * 6 + 3], v0.y + v1.y - gq0.y * k0);
-            atomicAdd(&acc[q * 6 + 4], v2.x + v3.x - gq1.x * k1);
-            atomicAdd(&acc[q * 6 + 5], v2.y + v3.y - gq1.y * k1);
+        // the normal equations of each antenna from the sums of its baselines (no atomics: one
+        // thread per antenna, float32 sums as batch_kernel's accumulators)
+        for (int ant = tid; ant < na; ant += blockDim.x) {
+            const float2 ga0 = make_float2((float)g64[2 * ant].x, (float)g64[2 * ant].y);
+            const float2 ga1 = make_float2((float)g64[2 * ant + 1].x, (float)g64[2 * ant + 1].y);
+            float h0 = 0.f, h1 = 0.f;
+            float2 j0 = make_float2(0.f, 0.f), j1 = j0;
+            for (int o = 0; o < na; ++o) {
+                if (o == ant) continue;
+                const float2 go0 = make_float2((float)g64[2 * o].x, (float)g64[2 * o].y);
+                const float2 go1 = make_float2((float)g64[2 * o + 1].x, (float)g64[2 * o + 1].y);
+                const float ao0 = cnorm2(go0), ao1 = cnorm2(go1);
+                if (ant < o) {      // antenna p of (ant, o)
+                    const float *m = mom + (size_t)mom_bl(ant, o, na) * MOM_W;
+                    const float e0 = m[0] * ao0 + m[1] * ao1, e1 = m[2] * ao0 + m[3] * ao1;
+                    const float2 T0 = make_float2(m[4], m[5]), T1 = make_float2(m[6], m[7]);
+                    const float2 T2 = make_float2(m[8], m[9]), T3 = make_float2(m[10], m[11]);
+                    h0 += e0;
+                    h1 += e1;
+                    j0 = cadd(j0, csub(cadd(cmul(go0, T0), cmul(go1, T1)), cscale(ga0, e0)));
+                    j1 = cadd(j1, csub(cadd(cmul(go0, T2), cmul(go1, T3)), cscale(ga1, e1)));
+                } else {            // antenna q of (o, ant), through the conjugate baseline
+                    const float *m = mom + (size_t)mom_bl(o, ant, na) * MOM_W;
+                    const float e0 = m[0] * ao0 + m[2] * ao1, e1 = m[1] * ao0 + m[3] * ao1;
+                    const float2 T0 = make_float2(m[4], m[5]), T1 = make_float2(m[6], m[7]);
+                    const float2 T2 = make_float2(m[8], m[9]), T3 = make_float2(m[10], m[11]);
+                    h0 += e0;
+                    h1 += e1;
+                    j0 = cadd(j0, csub(cadd(cmulc(go0, T0), cmulc(go1, T2)), cscale(ga0, e0)));
+                    j1 = cadd(j1, csub(cadd(cmulc(go0, T1), cmulc(go1, T3)), cscale(ga1, e1)));
+                }
+            }
+            acc[ant * 6 + 0] = h0;
+            acc[ant * 6 + 1] = h1;
+            acc[ant * 6 + 2] = j0.x;
+            acc[ant * 6 + 3] = j0.y;
+            acc[ant * 6 + 4] = j1.x;
+            acc[ant * 6 + 5] = j1.y;
         }
         __syncthreads();
         // FP64 per-antenna solve and update, as batch_kernel

@@ -117,3 +117,11 @@ def test_new_entry_points_reject_a_null_context(lib):
     assert lib.qc_delay_init(None, None, 0, 0) == qc.QC_EINVAL
     n = C.c_int64(0)
     assert lib.qc_mad_flag(None, None, 0, 5.0, None, 0, C.byref(n)) == qc.QC_EINVAL
+
+
+def test_delay_term_needs_channel_frequencies():
+    with pytest.raises(ValueError):
+        qc.Term("delay", np.zeros(2, np.int32), np.zeros(4, np.int32), 1, 1, 3)
+    t = qc.Term("delay", np.zeros(2, np.int32), np.zeros(4, np.int32), 1, 1, 3, chan_freq=np.linspace(1, 2, 4))
+    assert t.gains.shape == (1, 1, 3, 4) and t.gains.dtype == np.float32 and not t.gains.any()
+    assert t._c().chan_freq == t.chan_freq.ctypes.data

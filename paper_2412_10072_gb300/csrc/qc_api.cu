@@ -631,6 +631,8 @@ extern "C" int qc_delay_init(qc_ctx *c, qc_term *term, int32_t ref_ant, int32_t 
         max_n = std::max(max_n, (int)N);
     }
     cudaStream_t st = c->own_stream;
+    // scratch of chain position 0: every qc_solve and qc_residual stages its buffers anew
+    // (maps, accumulators, staging), and its graph is re-captured on every qc_solve
     TermBufs &B = c->tb[0];
     const size_t nx = (size_t)t.n_tint * c->n_ant * 2 * c->n_chan;
     const size_t npar = (size_t)t.n_tint * t.n_fint * c->n_ant * 4;

@@ -38,6 +38,29 @@ def order_statistic(values: np.ndarray) -> np.float32:
     return v[(v.size - 1) // 2]
 
 
+def mad_flag_per_baseline(resid, weight, flag, ant1, ant2, threshold: float = 5.0):
+    """The per-baseline mode: median and MAD of z over the samples of each baseline (all its
+    rows and channels, whatever the row orientation) instead of over all baselines; the rest as
+    mad_flag.  Returns the new flags and the number flagged."""
+    flag = np.zeros(np.shape(resid)[:2], np.uint8) if flag is None else np.asarray(flag)
+    a1, a2 = np.asarray(ant1), np.asarray(ant2)
+    z = whitened_norm(resid, weight)
+    out = np.zeros(flag.shape, dtype=np.uint8)
+    key = np.minimum(a1, a2).astype(np.int64) * (int(max(a1.max(), a2.max())) + 1) + np.maximum(a1, a2)
+    factor = np.float32(threshold * 1.4826)
+    for k in np.unique(key[a1 != a2]):
+        rows = np.nonzero(key == k)[0]
+        use = flag[rows] == 0
+        if not use.any():
+            continue
+        zb = z[rows]
+        med = order_statistic(zb[use])
+        dev = np.abs(zb - med)
+        mad = order_statistic(dev[use])
+        out[rows] = (use & (dev > factor * mad)).astype(np.uint8)
+    return out, int(out.sum())
+
+
 def mad_flag(resid, weight, flag, ant1, ant2, threshold: float = 5.0):
     """New flags uint8 [n_row][n_chan] (1 = outlier) and (median, MAD, number flagged)."""
     flag = np.zeros(np.shape(resid)[:2], np.uint8) if flag is None else np.asarray(flag)

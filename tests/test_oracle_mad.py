@@ -60,3 +60,39 @@ def test_flagged_samples_and_autocorrelations_are_left_out():
     np.testing.assert_array_equal(out1, out2)
     assert s1[:2] == s2[:2]
     assert not out2[flag.astype(bool)].any() and not out2[:10].any()
+
+
+def test_per_baseline_mode_follows_each_baseline_spread():
+    """Two baselines whose residuals differ in scale by 100, the loud one a quarter of the rows:
+    with global statistics most of the loud baseline's samples are outliers; per baseline, only
+    the outliers planted in each baseline are."""
+    from oracle.mad_flag import mad_flag_per_baseline
+    rng = np.random.default_rng(4)
+    n_row, n_chan = 40, 16
+    ant1 = np.zeros(n_row, np.int32)
+    ant2 = np.where(np.isin(np.arange(n_row) % 8, (3, 4)), 2, 1).astype(np.int32)
+    ant1[::4], ant2[::4] = ant2[::4], 0                      # some rows in the other orientation
+    scale = np.where(np.maximum(ant1, ant2) == 2, 100.0, 1.0)[:, None, None]
+    r = (scale * (rng.standard_normal((n_row, n_chan, 4)) + 1j * rng.standard_normal((n_row, n_chan, 4)))
+         ).astype(np.complex64)
+    w = np.ones((n_row, n_chan, 4), np.float32)
+    planted = [(2, 3), (5, 7), (3, 1), (12, 12)]          # quiet, quiet, loud, loud (swapped row)
+    for row, ch in planted:
+        r[row, ch, 0] += np.complex64(60.0 * scale[row, 0, 0])
+    out, n = mad_flag_per_baseline(r, w, None, ant1, ant2, threshold=10.0)
+    want = np.zeros((n_row, n_chan), np.uint8)
+    for row, ch in planted:
+        want[row, ch] = 1
+    np.testing.assert_array_equal(out, want)
+    glob, _ = mad_flag(r, w, None, ant1, ant2, threshold=10.0)
+    assert glob[np.maximum(ant1, ant2) == 2].mean() > 0.5      # the global mode flags the loud baseline
+
+
+def test_per_baseline_mode_equals_global_mode_on_one_baseline():
+    from oracle.mad_flag import mad_flag_per_baseline
+    rng, r, w, a1, a2 = _residuals(8)
+    flag = (rng.random(r.shape[:2]) < 0.1).astype(np.uint8)
+    a, n_a = mad_flag_per_baseline(r, w, flag, a1, a2)
+    b, (_, _, n_b) = mad_flag(r, w, flag, a1, a2)
+    np.testing.assert_array_equal(a, b)
+    assert n_a == n_b

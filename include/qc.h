@@ -239,7 +239,7 @@ int qc_delay_init(qc_ctx *c, qc_term *term, int32_t ref_ant, int32_t oversample)
 /*
  * MAD residual flagging after calibration (Section 4, "Additional features":
  * outliers of the residual visibilities by the Median Absolute Deviation,
- * over all baselines at once).  With the chain `terms` (as in qc_residual):
+ * over all baselines at once or per baseline).  With the chain `terms` (as in qc_residual):
  *   z_s   = sqrt(sum over the 4 correlations of w |r|^2) of every unflagged
  *           cross-correlation sample s, in float32, every operation rounded
  *           (no fused multiply-add), in the order ((w0 t0 + w1 t1) + w2 t2)
@@ -247,6 +247,9 @@ int qc_delay_init(qc_ctx *c, qc_term *term, int32_t ref_ant, int32_t oversample)
  *   med   = the floor((n - 1) / 2)-th smallest z (exact order statistic);
  *   MAD   = the same order statistic of |z - med|;
  *   flag s when |z_s - med| > fl32(threshold * 1.4826) * MAD (float32).
+ *   per_baseline : 0 = med and MAD over all baselines (global mode); 1 = over
+ *               the samples of each baseline (its rows in either orientation
+ *               and all channels) separately (the paper's per-baseline mode).
  *   flags_out : out uint8 [n_row][n_chan] in out_memory: 1 = outlier, 0 else
  *               (samples already flagged and autocorrelations are 0; the
  *               caller merges them with its own flags).
@@ -254,8 +257,8 @@ int qc_delay_init(qc_ctx *c, qc_term *term, int32_t ref_ant, int32_t oversample)
  * Errors: QC_EINVAL for NULL flags_out, threshold not positive and finite, or
  * terms failing the checks of qc_residual.
  */
-int qc_mad_flag(qc_ctx *c, const qc_term *terms, int32_t n_terms, double threshold, uint8_t *flags_out,
-                int32_t out_memory, int64_t *n_flagged);
+int qc_mad_flag(qc_ctx *c, const qc_term *terms, int32_t n_terms, double threshold, int32_t per_baseline,
+                uint8_t *flags_out, int32_t out_memory, int64_t *n_flagged);
 
 /* Release a context and every device buffer it owns.  NULL-safe. */
 void qc_destroy(qc_ctx *c);

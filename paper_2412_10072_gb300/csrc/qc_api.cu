@@ -1319,6 +1319,89 @@ __global__ void mad_flag_kernel(long n_vis, int n_chan, const uint8_t *flag, con
     if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(n_flagged, (unsigned long long)cnt);
 }
 
+// per-baseline mode: one block per group of rows (the rows of one baseline in either
+// orientation); two exact order statistics of its used samples by four 8-bit radix passes
+// with a shared-memory histogram, then its flags
+__device__ __forceinline__ unsigned mad_block_select(const unsigned *keys, const int *grows, int n_grow, int n_chan,
+                                                     const uint8_t *flag, unsigned long long k, unsigned *hist,
+                                                     unsigned *s_res)
+{
+    unsigned prefix = 0, mask = 0;
+    const long n = (long)n_grow * n_chan;
+    for (int shift = 24; shift >= 0; shift -= 8) {
+        for (int t = threadIdx.x; t < 256; t += blockDim.x) hist[t] = 0;
+        __syncthreads();
+        for (long i = threadIdx.x; i < n; i += blockDim.x) {
+            const long sidx = (long)grows[i / n_chan] * n_chan + (i % n_chan);
+            if (flag && flag[sidx]) continue;
+            const unsigned kk = keys[sidx];
+            if ((kk & mask) == prefix) atomicAdd(&hist[(kk >> shift) & 0xffu], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long cum = 0;
+            int b = 0;
+            for (; b < 255; ++b) {
+                if (cum + hist[b] > k) break;
+                cum += hist[b];
+            }
+            s_res[0] = (unsigned)b;
+            s_res[1] = (unsigned)(k - cum);
+        }
+        __syncthreads();
+        prefix |= s_res[0] << shift;
+        mask |= 0xffu << shift;
+        k = s_res[1];
+        __syncthreads();
+    }
+    return prefix;
+}
+
+__global__ void __launch_bounds__(256) mad_group_kernel(int n_chan, const int *goff, const int *grows,
+                                                        const uint8_t *flag, unsigned *keys, float factor,
+                                                        uint8_t *out, unsigned long long *n_flagged)
+{
+    __shared__ unsigned hist[256];
+    __shared__ unsigned s_res[2];
+    __shared__ unsigned long long s_cnt;
+    const int g = blockIdx.x;
+    const int *rows = grows + goff[g];
+    const int n_grow = goff[g + 1] - goff[g];
+    const long n = (long)n_grow * n_chan;
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    unsigned long long used = 0;
+    for (long i = threadIdx.x; i < n; i += blockDim.x) {
+        const long sidx = (long)rows[i / n_chan] * n_chan + (i % n_chan);
+        if (!(flag && flag[sidx])) ++used;
+    }
+    atomicAdd(&s_cnt, used);
+    __syncthreads();
+    const unsigned long long n_used = s_cnt;
+    float thr = INFINITY;
+    if (n_used > 0) {
+        const unsigned long long k = (n_used - 1) / 2;
+        const unsigned med_bits = mad_block_select(keys, rows, n_grow, n_chan, flag, k, hist, s_res);
+        const float med = __uint_as_float(med_bits);
+        for (long i = threadIdx.x; i < n; i += blockDim.x) {
+            const long sidx = (long)rows[i / n_chan] * n_chan + (i % n_chan);
+            if (!(flag && flag[sidx])) keys[sidx] = __float_as_uint(fabsf(__fsub_rn(__uint_as_float(keys[sidx]), med)));
+        }
+        __syncthreads();
+        const unsigned mad_bits = mad_block_select(keys, rows, n_grow, n_chan, flag, k, hist, s_res);
+        thr = __fmul_rn(factor, __uint_as_float(mad_bits));
+    }
+    unsigned cnt = 0;
+    for (long i = threadIdx.x; i < n; i += blockDim.x) {
+        const long sidx = (long)rows[i / n_chan] * n_chan + (i % n_chan);
+        const bool f = !(flag && flag[sidx]) && __uint_as_float(keys[sidx]) > thr;
+        out[sidx] = f ? 1 : 0;
+        cnt += f ? 1u : 0u;
+    }
+    for (int d = 16; d > 0; d >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, d);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(n_flagged, (unsigned long long)cnt);
+}
+
 } // namespace
 
 // the k-th smallest of n keys (0-based), k < n: four 8-bit radix passes from the top bits
@@ -1348,8 +1431,8 @@ static int mad_select(qc_ctx *c, const unsigned *keys, long n, unsigned long lon
     return QC_OK;
 }
 
-extern "C" int qc_mad_flag(qc_ctx *c, const qc_term *terms, int32_t n_terms, double threshold, uint8_t *flags_out,
-                           int32_t out_memory, int64_t *n_flagged)
+extern "C" int qc_mad_flag(qc_ctx *c, const qc_term *terms, int32_t n_terms, double threshold, int32_t per_baseline,
+                           uint8_t *flags_out, int32_t out_memory, int64_t *n_flagged)
 {
     if (!c) return QC_EINVAL;
     c->err.clear();
@@ -1390,6 +1473,43 @@ extern "C" int qc_mad_flag(qc_ctx *c, const qc_term *terms, int32_t n_terms, dou
     unsigned long long hc[2];
     CK(cudaMemcpyAsync(hc, cnt, sizeof hc, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    if (per_baseline) {
+        // groups: the rows of each unordered antenna pair (cross-correlations only)
+        std::vector<int4> hrows(c->n_row);
+        CK(cudaMemcpyAsync(hrows.data(), c->d_rows, nbytes<int4>(c->n_row), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        std::vector<int> gid((size_t)c->n_ant * c->n_ant, -1), count;
+        std::vector<int> row_g(c->n_row, -1);
+        for (int r = 0; r < c->n_row; ++r) {
+            const int a1 = hrows[r].x, a2 = hrows[r].y;
+            if (a1 == a2) continue;
+            int &slot = gid[(size_t)std::min(a1, a2) * c->n_ant + std::max(a1, a2)];
+            if (slot < 0) { slot = (int)count.size(); count.push_back(0); }
+            row_g[r] = slot;
+            ++count[slot];
+        }
+        const int n_groups = (int)count.size();
+        std::vector<int> goff(n_groups + 1, 0), grows;
+        for (int gi = 0; gi < n_groups; ++gi) goff[gi + 1] = goff[gi] + count[gi];
+        grows.resize(goff[n_groups]);
+        std::vector<int> fill(goff.begin(), goff.end() - 1);
+        for (int r = 0; r < c->n_row; ++r) if (row_g[r] >= 0) grows[fill[row_g[r]]++] = r;
+        CK(cudaMemsetAsync(dout, 0, (size_t)n_vis, st));
+        if (n_groups > 0) {
+            if ((rc = c->ensure(c->mad_groups, nbytes<int>(goff.size() + grows.size())))) return rc;
+            int *dgoff = (int *)c->mad_groups.ptr, *dgrows = dgoff + goff.size();
+            CK(cudaMemcpyAsync(dgoff, goff.data(), nbytes<int>(goff.size()), cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(dgrows, grows.data(), nbytes<int>(grows.size()), cudaMemcpyHostToDevice, st));
+            mad_group_kernel<<<n_groups, 256, 0, st>>>(c->n_chan, dgoff, dgrows, c->d_flag, keys,
+                                                      (float)(threshold * 1.4826), dout, cnt + 1);
+            CK(cudaGetLastError());
+        }
+        if (out_memory == QC_MEM_HOST) CK(cudaMemcpyAsync(flags_out, dout, (size_t)n_vis, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(hc + 1, cnt + 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (n_flagged) *n_flagged = (int64_t)hc[1];
+        return QC_OK;
+    }
     float thr = 0.f;
     if (hc[0] > 0) {
         const unsigned long long k = (hc[0] - 1) / 2;

@@ -96,6 +96,7 @@ struct qc_ctx {
     Buf mad_keys;                     // MAD flagging: uint32 [n_vis] statistic keys
     Buf mad_hist;                     // MAD flagging: uint32 [256] histogram + counters
     Buf mad_out;                      // MAD flagging: uint8 [n_vis] flags (host output staging)
+    Buf mad_groups;                   // MAD flagging, per-baseline mode: group offsets, then rows
     Buf resid_stage;
     long long launches = 0;
     std::vector<const void *> configured_fns;   // kernels whose dynamic smem limit was raised

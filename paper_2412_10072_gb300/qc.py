@@ -91,7 +91,7 @@ def load(build_if_missing: bool = True):
         lib.qc_residual.restype = C.c_int
         lib.qc_delay_init.argtypes = [vp, C.POINTER(_Term), i32, i32]
         lib.qc_delay_init.restype = C.c_int
-        lib.qc_mad_flag.argtypes = [vp, C.POINTER(_Term), i32, C.c_double, vp, i32, C.POINTER(C.c_int64)]
+        lib.qc_mad_flag.argtypes = [vp, C.POINTER(_Term), i32, C.c_double, i32, vp, i32, C.POINTER(C.c_int64)]
         lib.qc_mad_flag.restype = C.c_int
         lib.qc_destroy.argtypes = [vp]
         lib.qc_destroy.restype = None
@@ -261,15 +261,17 @@ class Solver:
             self._err(rc)
         return term
 
-    def mad_flag(self, terms: List[Term], threshold: float = 5.0, out=None):
+    def mad_flag(self, terms: List[Term], threshold: float = 5.0, out=None, per_baseline: bool = False):
         """Outlier flags of the residual after calibration (qc_mad_flag): uint8 [n_row][n_chan]
-        (a new host array, or ``out``, a CUDA tensor) and the number of samples flagged."""
+        (a new host array, or ``out``, a CUDA tensor) and the number of samples flagged; median and
+        MAD over all baselines, or over each baseline with ``per_baseline``."""
         arr = _terms_array(terms)
         n = C.c_int64(0)
         if out is None:
             out = np.zeros((self.n_row, self.n_chan), dtype=np.uint8)
         mem = QC_MEM_DEVICE if _is_dev(out) else QC_MEM_HOST
-        rc = self._lib.qc_mad_flag(self._h, arr, len(terms), float(threshold), _addr(out), mem, C.byref(n))
+        rc = self._lib.qc_mad_flag(self._h, arr, len(terms), float(threshold), int(bool(per_baseline)), _addr(out),
+                                   mem, C.byref(n))
         if rc != QC_OK:
             self._err(rc)
         return out, int(n.value)

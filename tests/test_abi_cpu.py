@@ -116,7 +116,7 @@ def test_new_entry_points_reject_a_null_context(lib):
     """qc_delay_init and qc_mad_flag return QC_EINVAL for a NULL context before any device work."""
     assert lib.qc_delay_init(None, None, 0, 0) == qc.QC_EINVAL
     n = C.c_int64(0)
-    assert lib.qc_mad_flag(None, None, 0, 5.0, None, 0, C.byref(n)) == qc.QC_EINVAL
+    assert lib.qc_mad_flag(None, None, 0, 5.0, 0, None, 0, C.byref(n)) == qc.QC_EINVAL
 
 
 def test_delay_term_needs_channel_frequencies():

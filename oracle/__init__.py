@@ -31,6 +31,10 @@ Parity status of each oracle function (what pins it, see ``tests/``):
 - ``moments`` (sufficient-statistics pre-reduction of a single diagonal
   term): its normal equations and chi^2 equal the sample-by-sample ones
   (``tests/test_oracle_moments.py``).
+- ``dd`` (direction-dependent chains, N_D >= 1): pinned by the one-direction
+  C oracle, Wirtinger finite differences with two directions for
+  direction-dependent and direction-independent solved terms, and exact
+  recovery of direction-dependent gains (``tests/test_oracle_dd.py``).
 - ``mlp``: pinned by central finite differences of its own loss.
 """
 from .oracle import (OC_DIAG, OC_FULL, OC_PHASE, OC_DELAY, OracleProblem, OracleTerm, build,  # noqa: F401

@@ -278,24 +278,57 @@ void qc_destroy(qc_ctx *c);
  * sum in a fixed order).  Kernels are enqueued on `stream` (NULL: the legacy
  * default stream); the call returns without synchronising.
  *
- * Scratch: the kernel-layout gain table and the per-CTA partial sums live in a
- * static device array of (QC_NOALLOC_MAX_GAINS * 32 + QC_NOALLOC_MAX_BLOCKS * 8)
- * bytes (2 MiB + 8 KiB) that every device which loads the library keeps until
+ * Index checks: the index arrays are in device memory, so the host cannot read
+ * them.  The kernel checks every index before it uses it: ant1/ant2 in
+ * [0, n_ant), time_idx in [0, n_time), t_map values in [0, n_tint) and f_map
+ * values in [0, n_fint).  A sample with an index out of range is skipped
+ * (nothing is read through that index) and the call's result is NaN; the
+ * return code is still QC_OK, since the check runs on the GPU after the call
+ * returns.  Sizes are checked on the host (QC_EINVAL).
+ *
+ * Scratch: the kernel-layout gain table, the per-CTA partial sums and the
+ * index-check word live in a static device array of
+ * (QC_NOALLOC_MAX_GAINS * 32 + QC_NOALLOC_MAX_BLOCKS * 8 + 256) bytes
+ * (about 2 MiB + 8 KiB) that every device which loads the library keeps until
  * the process exits.  Problems with n_tint * n_fint * n_ant > QC_NOALLOC_MAX_GAINS
  * are rejected with QC_EINVAL (message in qc_last_error(NULL)).  The first call
  * on a device looks up the device address of that array (cudaGetSymbolAddress,
  * no allocation); make that first call before capturing a stream into a CUDA
- * graph.  Every call reuses the same array and leaves its contents behind:
+ * graph.  Every call reuses the same array and leaves its contents behind
+ * (the index-check word is cleared at the start of each call):
  * calls on one device whose kernels may overlap (for example on two streams)
  * race on it, so order them (one stream, or events).  Each device has its own
  * copy, so calls on different devices do not interfere.
  */
 #define QC_NOALLOC_MAX_GAINS   65536
 #define QC_NOALLOC_MAX_BLOCKS  1024
-int qc_residual_noalloc(int32_t n_row, int32_t n_chan, int32_t n_ant, const void *data, const void *model,
-                        const float *weight, const uint8_t *flag, const int32_t *ant1, const int32_t *ant2,
-                        const int32_t *time_idx, int32_t type, int32_t n_tint, int32_t n_fint, const int32_t *t_map,
-                        const int32_t *f_map, const void *gains, double *chi2, void *stream);
+int qc_residual_noalloc(int32_t n_row, int32_t n_chan, int32_t n_ant, int32_t n_time, const void *data,
+                        const void *model, const float *weight, const uint8_t *flag, const int32_t *ant1,
+                        const int32_t *ant2, const int32_t *time_idx, int32_t type, int32_t n_tint, int32_t n_fint,
+                        const int32_t *t_map, const int32_t *f_map, const void *gains, double *chi2, void *stream);
+
+/*
+ * Test hooks (the paper has no counterpart).  Failure paths are exercised
+ * without faulting the GPU: the failure is made on the host, or a bounded
+ * wait is made to run out.  Process-wide; not for production use.
+ *   qc_test_fail_alloc(n): the n-th device allocation of the library from now
+ *       on (1-based) fails as if cudaMalloc had returned
+ *       cudaErrorMemoryAllocation, without calling it; the call that made it
+ *       returns QC_ENOMEM and releases what it had allocated.  n <= 0 disarms.
+ *   qc_test_live_allocs(): device allocations of the library not yet freed
+ *       (contexts, batches and their temporary buffers).
+ *   qc_test_wait_limit(limit_ns, stall): wall-time limit of each bounded wait
+ *       on a ring-stage barrier of the bulk-copy accumulate kernels (default
+ *       2 s; limit_ns <= 0 restores it).  With stall >= 0, every warp's
+ *       stall-th stage is never filled and its barrier never completes, so the
+ *       kernel's wait on it gives up after limit_ns: the kernel records the
+ *       error, waits (bounded) for its copies in flight and returns; qc_solve
+ *       returns QC_ETIMEOUT and the context stays usable.  stall < 0 disarms.
+ *       While a stall is armed, qc_solve does not use CUDA graphs.
+ */
+void qc_test_fail_alloc(int64_t n);
+int64_t qc_test_live_allocs(void);
+void qc_test_wait_limit(int64_t limit_ns, int32_t stall);
 
 /* Message of the last failed call on `c` ("" if none); with c == NULL, of the last failed qc_create. */
 const char *qc_last_error(const qc_ctx *c);

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -147,7 +148,7 @@ int grid_for(long n, int block, int sm)
 qc_ctx::~qc_ctx()
 {
     for (auto &b : tb) if (b.exec) cudaGraphExecDestroy(b.exec);
-    for (void *p : owned) cudaFree(p);
+    for (void *p : owned) qc_dev_free(p);
     for (auto e : events) cudaEventDestroy(e);
     if (own_stream) cudaStreamDestroy(own_stream);
 }
@@ -164,10 +165,46 @@ int qc_ctx::cuda_fail(cudaError_t e, const char *what)
     return e == cudaErrorMemoryAllocation ? QC_ENOMEM : QC_ECUDA;
 }
 
+namespace {
+std::atomic<long long> g_alloc_countdown{0};   // > 0: the allocation that brings it to 0 fails
+std::atomic<long long> g_live_allocs{0};
+std::atomic<unsigned long long> g_wait_limit_ns{2000000000ull};
+std::atomic<int> g_wait_stall{-1};
+} // namespace
+
+cudaError_t qc_dev_malloc(void **p, size_t bytes)
+{
+    *p = nullptr;
+    long long c = g_alloc_countdown.load();
+    while (c > 0 && !g_alloc_countdown.compare_exchange_weak(c, c - 1)) {}
+    if (c == 1) return cudaErrorMemoryAllocation;      // injected on the host: cudaMalloc is not called
+    const cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+    if (e == cudaSuccess) ++g_live_allocs;
+    return e;
+}
+
+void qc_dev_free(void *p)
+{
+    if (!p) return;
+    cudaFree(p);
+    --g_live_allocs;
+}
+
+uint64_t qc_wait_limit_ns() { return g_wait_limit_ns.load(); }
+int qc_wait_stall_stage() { return g_wait_stall.load(); }
+
+extern "C" void qc_test_fail_alloc(int64_t n) { g_alloc_countdown.store(n > 0 ? n : 0); }
+extern "C" int64_t qc_test_live_allocs(void) { return g_live_allocs.load(); }
+extern "C" void qc_test_wait_limit(int64_t limit_ns, int32_t stall_stage)
+{
+    g_wait_limit_ns.store(limit_ns > 0 ? (unsigned long long)limit_ns : 2000000000ull);
+    g_wait_stall.store(stall_stage >= 0 ? stall_stage : -1);
+}
+
 void *qc_ctx::alloc(size_t bytes, cudaError_t *e)
 {
     void *p = nullptr;
-    *e = cudaMalloc(&p, std::max<size_t>(bytes, 16));
+    *e = qc_dev_malloc(&p, bytes);
     if (*e == cudaSuccess) owned.push_back(p);
     return p;
 }
@@ -175,7 +212,7 @@ void *qc_ctx::alloc(size_t bytes, cudaError_t *e)
 void qc_ctx::release(void *p)
 {
     auto it = std::find(owned.begin(), owned.end(), p);
-    if (it != owned.end()) { cudaFree(p); owned.erase(it); }
+    if (it != owned.end()) { qc_dev_free(p); owned.erase(it); }
 }
 
 int qc_ctx::ensure(Buf &b, size_t bytes)
@@ -1089,6 +1126,8 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
     pa.a = aa;
     pa.chunk_active = (const uint8_t *)B.chunk_act.ptr;
     pa.err = d_err;
+    pa.wait_ns = qc_wait_limit_ns();
+    pa.stall_issue = qc_wait_stall_stage();
     const int ca_threads = t.n_tint * aa.n_chunks;
 
     UpdArgs ua;
@@ -1127,7 +1166,8 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
 
     const int max_iter = t.max_iter;
     for (int k = 0; k < 2 * max_iter; ++k) { cudaEvent_t ev; if ((rc = get_event(2 + k, ev))) return rc; }
-    const bool use_graph = o->use_graph && !t.reduce;
+    // (no graph while a test stalls a stage: a captured graph would keep the stall)
+    const bool use_graph = o->use_graph && !t.reduce && qc_wait_stall_stage() < 0;
     const unsigned rec_flags = use_graph ? cudaEventRecordExternal : cudaEventRecordDefault;
 
     auto enqueue = [&]() -> int {
@@ -1218,7 +1258,7 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
     CK(cudaStreamSynchronize(st));
     if (herr) {
         CK(cudaMemsetAsync(d_err, 0, sizeof(int), st));
-        return fail(QC_ETIMEOUT, "a bounded wait in the pipelined accumulate kernel gave up (2 s)");
+        return fail(QC_ETIMEOUT, "a bounded wait in the pipelined accumulate kernel gave up");
     }
     double ms_sum = 0;
     long long worked = 0;

@@ -23,6 +23,9 @@
 
 #include "../../include/qc.h"
 #include "qc_async.cuh"
+
+cudaError_t qc_dev_malloc(void **p, size_t bytes);   // counted allocation (qc_api.cu)
+void qc_dev_free(void *p);
 #include "qc_jones.cuh"
 
 namespace {
@@ -991,7 +994,7 @@ struct qc_batch {
     ~qc_batch()
     {
         if (exec) cudaGraphExecDestroy(exec);
-        for (void *p : owned) cudaFree(p);
+        for (void *p : owned) qc_dev_free(p);
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
         if (own_stream) cudaStreamDestroy(own_stream);
@@ -999,7 +1002,7 @@ struct qc_batch {
     void *alloc(size_t bytes, cudaError_t *e)
     {
         void *p = nullptr;
-        *e = cudaMalloc(&p, std::max<size_t>(bytes, 16));
+        *e = qc_dev_malloc(&p, bytes);
         if (*e == cudaSuccess) owned.push_back(p);
         return p;
     }
@@ -1167,7 +1170,7 @@ extern "C" int qc_batch_create(const qc_batch_problem *p, qc_batch **out)
         b->model16 = m16;
         if (p->memory == QC_MEM_HOST) {
             auto it = std::find(b->owned.begin(), b->owned.end(), (void *)model32);
-            if (it != b->owned.end()) { cudaFree(*it); b->owned.erase(it); }
+            if (it != b->owned.end()) { qc_dev_free(*it); b->owned.erase(it); }
         }
         model32 = nullptr;
     }
@@ -1488,7 +1491,7 @@ extern "C" int qc_batch_autotune(qc_batch *b, const qc_batch_opts *base, qc_batc
     b->err.clear();
     // unit gains on the device for every trial
     float2 *g;
-    cudaError_t e = cudaMalloc(&g, (size_t)b->total_ant * 2 * sizeof(float2));
+    cudaError_t e = qc_dev_malloc((void **)&g, (size_t)b->total_ant * 2 * sizeof(float2));
     if (e != cudaSuccess) return b->cuda_fail(e, "cudaMalloc");
     std::vector<float2> unit((size_t)b->total_ant * 2, make_float2(1.f, 0.f));
     qc_batch::Shape win{ 0, 0, 0, 0, 1e30 };
@@ -1516,7 +1519,7 @@ extern "C" int qc_batch_autotune(qc_batch *b, const qc_batch_opts *base, qc_batc
                 if (s.ctas_per_sm != per_sm) continue;                     // clamped: duplicate of a smaller one
                 if (s.ms < win.ms) { win = { threads, per_sm, sched, depth, s.ms }; ws = s; }
             }
-    cudaFree(g);
+    qc_dev_free(g);
     if (rc) return rc;
     if (!tried || win.threads == 0) return b->fail(QC_EUNSUPPORTED, "no launch shape could be timed");
     b->tuned[b->shape_key] = win;
@@ -1536,7 +1539,7 @@ extern "C" int qc_batch_residual(qc_batch *b, const void *gains, int32_t mem, do
     double *dchi = chi2;
     void *tmp = nullptr;
     if (mem == QC_MEM_HOST) {
-        BCK(cudaMalloc(&tmp, gbytes + sizeof(double) * b->n_prob));
+        BCK(qc_dev_malloc((void **)&tmp, gbytes + sizeof(double) * b->n_prob));
         dg = (float2 *)tmp;
         dchi = (double *)((unsigned char *)tmp + gbytes);
         BCK(cudaMemcpyAsync(dg, gains, gbytes, cudaMemcpyHostToDevice, st));
@@ -1549,7 +1552,7 @@ extern "C" int qc_batch_residual(qc_batch *b, const void *gains, int32_t mem, do
     if (e == cudaSuccess && mem == QC_MEM_HOST)
         e = cudaMemcpyAsync(chi2, dchi, sizeof(double) * b->n_prob, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (tmp) cudaFree(tmp);
+    if (tmp) qc_dev_free(tmp);
     if (e != cudaSuccess) return b->cuda_fail(e, "batch residual");
     return QC_OK;
 }
@@ -1571,7 +1574,7 @@ extern "C" int qc_batch_features(qc_batch *b, const void *prev_gains, float *fea
     float *dfeat = features;
     double *dchi = prev_chi2;
     if (mem == QC_MEM_HOST) {
-        BCK(cudaMalloc(&tmp, cbytes + fbytes + gbytes));
+        BCK(qc_dev_malloc((void **)&tmp, cbytes + fbytes + gbytes));
         dchi = prev_chi2 ? (double *)tmp : nullptr;
         dfeat = (float *)((unsigned char *)tmp + cbytes);
         if (prev_gains) {
@@ -1592,7 +1595,7 @@ extern "C" int qc_batch_features(qc_batch *b, const void *prev_gains, float *fea
     if (e == cudaSuccess && mem == QC_MEM_HOST && prev_chi2)
         e = cudaMemcpyAsync(prev_chi2, dchi, cbytes, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess && mem == QC_MEM_HOST) e = cudaStreamSynchronize(st);
-    if (tmp) { cudaStreamSynchronize(st); cudaFree(tmp); }
+    if (tmp) { cudaStreamSynchronize(st); qc_dev_free(tmp); }
     if (e != cudaSuccess) return b->cuda_fail(e, "batch features");
     return QC_OK;
 }
@@ -1605,7 +1608,7 @@ extern "C" int qc_batch_warmstart(qc_batch *b, const float *y, const void *fallb
     if (!y || !fallback || !gains_out) return b->fail(QC_EINVAL, "y, fallback and gains_out are required (device)");
     cudaStream_t st = stream ? (cudaStream_t)stream : b->own_stream;
     void *tmp = nullptr;
-    BCK(cudaMalloc(&tmp, sizeof(int) * b->n_prob + 2 * sizeof(double) * b->n_prob));
+    BCK(qc_dev_malloc((void **)&tmp, sizeof(int) * b->n_prob + 2 * sizeof(double) * b->n_prob));
     int *bad = (int *)tmp;
     double *chi_p = (double *)((unsigned char *)tmp + ((sizeof(int) * b->n_prob + 15) / 16) * 16);
     double *chi_f = chi_p + b->n_prob;
@@ -1632,7 +1635,7 @@ extern "C" int qc_batch_warmstart(qc_batch *b, const float *y, const void *fallb
         *n_fallback = nf;
     }
     cudaStreamSynchronize(st);
-    cudaFree(tmp);
+    qc_dev_free(tmp);
     if (e != cudaSuccess) return b->cuda_fail(e, "batch warm start");
     return QC_OK;
 }

@@ -10,6 +10,16 @@
 #include "qc_delay.cuh"
 #include "qc_stream_delay.cuh"
 
+// Every device allocation of the library goes through these two calls.  They count the
+// live allocations and honour the test hook of qc_test_fail_alloc (qc.h), so that tests can
+// make an allocation fail on the host and check that nothing leaks.
+cudaError_t qc_dev_malloc(void **p, size_t bytes);
+void qc_dev_free(void *p);
+// Bounded-wait settings of the pipelined kernels (qc_test_wait_limit in qc.h): the wall-time
+// limit of each wait and, for tests, a ring stage whose copies are never issued.
+uint64_t qc_wait_limit_ns();
+int qc_wait_stall_stage();
+
 struct Buf {
     void *ptr = nullptr;
     size_t bytes = 0;

@@ -980,6 +980,8 @@ struct PipeArgs {
     const int4 *chunk_info;       // [n_chunks] {fn0, fn count, fo0, fo count} of the 32-channel chunks
     const uint8_t *chunk_active;  // [n_tint of term n][n_chunks]: a 32-channel chunk has an active bin
     int *err;                     // set to 1 when a bounded wait gives up
+    unsigned long long wait_ns;   // wall-time limit of every wait on a stage barrier
+    int stall_issue;              // tests: the n-th issue of every warp is never made (-1: none)
     // shared-memory layout (bytes), fixed per launch by the host
     int ns;                       // ring stages per warp
     int slot_bytes;               // one stage of one warp: d, m, w and Jones slices
@@ -991,7 +993,6 @@ struct PipeArgs {
     int stage_fmap;
 };
 
-constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;   // 2 s
 
 // Descriptor of one row segment of a warp's step (written when its copies are issued).
 struct __align__(16) SlotDesc {
@@ -1168,9 +1169,11 @@ __global__ void __launch_bounds__(NW * 32, 1) acc_pipe_kernel(const PipeArgs P)
         for (int h = 0; h < H; ++h) total += __shfl_sync(0xffffffffu, seg_bytes, 8 * h);
         if (kind == 0 && hseg < H) desc[stage * H + hseg] = d;
         __syncwarp();
-        if (lane == 0) mbar_arrive_expect_tx(full + stage, total);
+        // a test can leave one stage's barrier without its arrival: the wait on it must give up
+        const bool stalled = (int)n_issued == P.stall_issue;
+        if (lane == 0 && !stalled) mbar_arrive_expect_tx(full + stage, total);
         __syncwarp();
-        if (copier && d.live) {
+        if (copier && d.live && !stalled) {
             size_t idx;
             uint32_t n;
             if (kind < 3) { idx = (size_t)d.row * D.n_chan + d.cc; n = d.nch; }
@@ -1201,7 +1204,7 @@ __global__ void __launch_bounds__(NW * 32, 1) acc_pipe_kernel(const PipeArgs P)
             issue(pf);
             cursor_next<H>(a, pf, n_units, stride);
         }
-        if (!mbar_wait_bounded(full + stage, phase, WAIT_LIMIT_NS)) { failed = true; break; }
+        if (!mbar_wait_bounded(full + stage, phase, P.wait_ns)) { failed = true; break; }
 #pragma unroll
         for (int h = 0; h < H; ++h) {
             const SlotDesc d = desc[stage * H + h];
@@ -1273,7 +1276,7 @@ __global__ void __launch_bounds__(NW * 32, 1) acc_pipe_kernel(const PipeArgs P)
         if (lane == 0) atomicExch(P.err, 1);
         // let this warp's copies in flight land before it leaves (bounded)
         for (uint32_t k = n_done; k < n_issued; ++k) {
-            mbar_wait_bounded(full + stage, phase, WAIT_LIMIT_NS);
+            mbar_wait_bounded(full + stage, phase, P.wait_ns);
             if (++stage == P.ns) { stage = 0; phase ^= 1u; }
         }
     }

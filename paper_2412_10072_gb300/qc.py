@@ -99,6 +99,12 @@ def load(build_if_missing: bool = True):
         lib.qc_last_error.restype = C.c_char_p
         lib.qc_version.argtypes = []
         lib.qc_version.restype = C.c_char_p
+        lib.qc_test_fail_alloc.argtypes = [C.c_int64]
+        lib.qc_test_fail_alloc.restype = None
+        lib.qc_test_live_allocs.argtypes = []
+        lib.qc_test_live_allocs.restype = C.c_int64
+        lib.qc_test_wait_limit.argtypes = [C.c_int64, i32]
+        lib.qc_test_wait_limit.restype = None
         _lib = lib
         return lib
 

@@ -22,7 +22,7 @@ CHI2_TOL = 1e-5          # the relative chi^2 tolerance of the parity tests
 def _lib():
     lib = qc.load()
     vp, i32 = C.c_void_p, C.c_int32
-    lib.qc_residual_noalloc.argtypes = [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, i32, i32, i32, vp, vp, vp, vp, vp]
+    lib.qc_residual_noalloc.argtypes = [i32, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, i32, i32, i32, vp, vp, vp, vp, vp]
     lib.qc_residual_noalloc.restype = C.c_int
     return lib
 
@@ -31,14 +31,16 @@ def _dev(a, dtype):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=dtype)).cuda()
 
 
-def _noalloc_chi2(lib, obs, term, gains):
+def _noalloc_chi2(lib, obs, term, gains, ant1=None, time_idx=None):
     d = dict(data=_dev(obs.data, np.complex64), model=_dev(obs.model, np.complex64),
-             weight=_dev(obs.weight, np.float32), flag=_dev(obs.flag, np.uint8), a1=_dev(obs.ant1, np.int32),
-             a2=_dev(obs.ant2, np.int32), t=_dev(obs.time_idx, np.int32), tm=_dev(term.t_map, np.int32),
+             weight=_dev(obs.weight, np.float32), flag=_dev(obs.flag, np.uint8),
+             a1=_dev(obs.ant1 if ant1 is None else ant1, np.int32), a2=_dev(obs.ant2, np.int32),
+             t=_dev(obs.time_idx if time_idx is None else time_idx, np.int32), tm=_dev(term.t_map, np.int32),
              fm=_dev(term.f_map, np.int32),
              g=_dev(gains, np.float32 if term.kind == "phase" else np.complex64))
     out = torch.full((1,), -1.0, dtype=torch.float64, device="cuda")
-    rc = lib.qc_residual_noalloc(obs.n_row, obs.n_chan, obs.n_ant, d["data"].data_ptr(), d["model"].data_ptr(),
+    rc = lib.qc_residual_noalloc(obs.n_row, obs.n_chan, obs.n_ant, obs.n_time, d["data"].data_ptr(),
+                                 d["model"].data_ptr(),
                                  d["weight"].data_ptr(), d["flag"].data_ptr(), d["a1"].data_ptr(), d["a2"].data_ptr(),
                                  d["t"].data_ptr(), qc.KINDS[term.kind], term.n_tint, term.n_fint,
                                  d["tm"].data_ptr(), d["fm"].data_ptr(), d["g"].data_ptr(), out.data_ptr(), None)
@@ -89,8 +91,27 @@ def test_noalloc_full_jones_and_phase_terms():
 def test_noalloc_rejects_problems_beyond_its_scratch():
     lib = _lib()
     big = np.zeros(16, np.int32)
-    rc = lib.qc_residual_noalloc(4, 4, 64, big.ctypes.data, big.ctypes.data, big.ctypes.data, None, big.ctypes.data,
+    rc = lib.qc_residual_noalloc(4, 4, 64, 4, big.ctypes.data, big.ctypes.data, big.ctypes.data, None, big.ctypes.data,
                                  big.ctypes.data, big.ctypes.data, qc.QC_TERM_DIAG, 1024, 1024, big.ctypes.data,
                                  big.ctypes.data, big.ctypes.data, big.ctypes.data, None)
     assert rc == qc.QC_EINVAL
     assert b"QC_NOALLOC_MAX_GAINS" in lib.qc_last_error(None)
+
+
+def test_noalloc_index_out_of_range_gives_nan_then_recovers():
+    """Indices in device memory are checked by the kernel before use: an antenna index equal
+    to n_ant, or a time index past n_time, is never used to read anything; the result is NaN.
+    The next call with valid indices clears the check and gives the right chi^2 again."""
+    lib = _lib()
+    obs = synth.plain_small(seed=4, noise=0.01)
+    spec = obs.terms[0]
+    g = spec.truth.astype(np.complex64)
+    bad_ant = np.array(obs.ant1, np.int32)
+    bad_ant[5] = obs.n_ant
+    assert np.isnan(_noalloc_chi2(lib, obs, spec, g, ant1=bad_ant))
+    bad_t = np.array(obs.time_idx, np.int32)
+    bad_t[-1] = obs.n_time
+    assert np.isnan(_noalloc_chi2(lib, obs, spec, g, time_idx=bad_t))
+    want = _ctx_chi2(obs, spec, g)
+    got = _noalloc_chi2(lib, obs, spec, g)
+    assert abs(got - want) <= CHI2_TOL * want, (got, want)

@@ -66,7 +66,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--block", type=int, default=0, help="threads per CTA of the accumulate kernel (0: auto)")
     ap.add_argument("--kernel", type=int, default=0,
-                    help="accumulate kernel: 0 auto (streaming), 1 bulk-copy pipeline, 2 prefetching, 3 streaming")
+                    help="accumulate kernel: 0 auto (streaming), 1 bulk-copy pipeline, 2 prefetching, 3 streaming, "
+                         "4 warp-specialised")
     return ap.parse_args()
 
 
@@ -82,13 +83,14 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-ACC_KERNEL_NAME = {0: "acc_stream_kernel", 1: "acc_pipe_kernel", 2: "acc_kernel", 3: "acc_stream_kernel"}
+ACC_KERNEL_NAME = {0: "acc_stream_kernel", 1: "acc_pipe_kernel", 2: "acc_kernel", 3: "acc_stream_kernel",
+                   4: "acc_ws_kernel", 5: "acc_run_kernel"}
 
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for name in ("qc_kernels.cuh", "qc_stream.cuh", "qc_jones.cuh", "qc_async.cuh", "qc_acc_inst.cuh", "qc_acc_diag.cu",
-                 "qc_acc_full.cu"):
+    for name in ("qc_kernels.cuh", "qc_stream.cuh", "qc_ws.cuh", "qc_jones.cuh", "qc_async.cuh", "qc_acc_inst.cuh",
+                 "qc_acc_diag.cu", "qc_acc_full.cu"):
         with open(os.path.join(ROOT, "paper_2412_10072_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

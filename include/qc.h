@@ -165,7 +165,14 @@ typedef struct {
                                   2 otherwise), 1 bulk-copy pipeline with per-warp rings
                                   (chains of <= 2 terms), 2 per-lane cp.async prefetching
                                   kernel, 3 streaming kernel (step-major row table, flags
-                                  folded into weights; chains of <= 2 terms) */
+                                  folded into weights; chains of <= 2 terms), 4 warp-
+                                  specialised kernel (a producer warp per CTA issues
+                                  cp.async.bulk copies into its consumer warps' rings),
+                                  5 self-feeding bulk-copy kernel (each warp refills its
+                                  own ring with cp.async.bulk; bookkeeping once per run of
+                                  steps with unchanged bins).  Kernels 4 and 5 take chains
+                                  of <= 2 terms; a solved delay term uses its streaming
+                                  kernel under them. */
     qc_allreduce_fn allreduce; /* required when a solved term has reduce = 1       */
     void *allreduce_user;
 } qc_opts;

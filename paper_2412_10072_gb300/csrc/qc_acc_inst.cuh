@@ -11,6 +11,8 @@ constexpr int PIPE_H = 2;     // row segments of 32 channels per warp step
 
 constexpr int ACC_DEPTH = 4;  // cp.async ring depth (segments) of the prefetching kernel
 constexpr int STREAM_DEPTH = 4;   // ring depth (steps) of the streaming kernel
+constexpr int WS_NC = 7;          // consumer warps per CTA of the warp-specialised kernel (two CTAs per SM)
+constexpr int WSS_NW = 8;         // warps per CTA of the self-feeding kernel (two CTAs per SM)
 
 template <bool M16> constexpr int stream_smem_per_warp()
 {
@@ -40,6 +42,21 @@ cudaError_t launch_stream(int grid, int block, int smem_bytes, cudaStream_t st, 
     return cudaGetLastError();
 }
 
+template <int TS, int LK, int RK, bool M16>
+cudaError_t launch_ws(int grid, int smem_bytes, cudaStream_t st, const WsArgs &a)
+{
+    acc_ws_kernel<TS, LK, RK, M16, WS_NC><<<grid, (WS_NC + 1) * 32, smem_bytes, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int TS, int LK, int RK, bool M16>
+cudaError_t launch_wsself(int grid, int smem_bytes, cudaStream_t st, const WsArgs &a)
+{
+    if (a.order == 0) acc_run_kernel<TS, LK, RK, M16, 0, WSS_NW><<<grid, WSS_NW * 32, smem_bytes, st>>>(a);
+    else acc_run_kernel<TS, LK, RK, M16, 1, WSS_NW><<<grid, WSS_NW * 32, smem_bytes, st>>>(a);
+    return cudaGetLastError();
+}
+
 template <int TS, int LK, int RK, bool SIMPLE, bool M16> AccLaunch make()
 {
     AccLaunch l;
@@ -54,6 +71,13 @@ template <int TS, int LK, int RK, bool SIMPLE, bool M16> AccLaunch make()
         l.stream_fn = (const void *)acc_stream_kernel<TS, LK, RK, M16, STREAM_DEPTH>;
         l.stream_launch = launch_stream<TS, LK, RK, M16>;
         l.stream_smem_per_warp = stream_smem_per_warp<M16>();
+        l.ws_fn = (const void *)acc_ws_kernel<TS, LK, RK, M16, WS_NC>;
+        l.ws_launch = launch_ws<TS, LK, RK, M16>;
+        l.ws_nc = WS_NC;
+        l.wss_fn = (const void *)acc_run_kernel<TS, LK, RK, M16, 0, WSS_NW>;
+        l.wss_fn1 = (const void *)acc_run_kernel<TS, LK, RK, M16, 1, WSS_NW>;
+        l.wss_launch = launch_wsself<TS, LK, RK, M16>;
+        l.wss_nw = WSS_NW;
     }
     return l;
 }

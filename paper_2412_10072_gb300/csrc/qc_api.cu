@@ -267,6 +267,8 @@ extern "C" int qc_create(const qc_problem *p, qc_ctx **out)
         cudaError_t e = cudaGetDevice(&c->dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev);
+        if (e == cudaSuccess)
+            e = cudaDeviceGetAttribute(&c->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, c->dev);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) { g_create_error = std::string("CUDA init: ") + cudaGetErrorString(e); return QC_ECUDA; }
     }
@@ -951,7 +953,15 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
     int pipe_smem = 0;
     // auto and kernel 3: the streaming kernel (chains of one or two terms; antenna pairs are
     // packed as p | q << 16); kernels 1 and 2 on request, and for longer chains
-    const bool streaming = L.stream_fn != nullptr && n_ant < 32768 && (o->kernel == 3 || o->kernel == 0);
+    // kernel 4: the warp-specialised kernel (chains of one or two terms; a solved delay term
+    // keeps its own streaming kernel)
+    // kernel 5: the self-feeding variant (every warp issues its own bulk copies)
+    bool ws = L.ws_fn != nullptr && !delay[n] && n_ant < 32768 && (o->kernel == 4 || o->kernel == 5);
+    const bool self_feed = o->kernel == 5;
+    const void *ws_fn = self_feed ? (order == 0 ? L.wss_fn : L.wss_fn1) : L.ws_fn;
+    const int ws_warps = self_feed ? L.wss_nw : L.ws_nc;     // warps that own a ring
+    const bool streaming = L.stream_fn != nullptr && n_ant < 32768 &&
+                           (o->kernel == 3 || o->kernel == 0 || ((o->kernel == 4 || o->kernel == 5) && delay[n]));
     // a solved delay term under the streaming kernel: its own kernel, which applies the chain
     // rule per sample and keeps sums per parameter interval (else: the per-channel bins)
     DelayLaunch DL;
@@ -1016,6 +1026,7 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
             }
         }
     }
+    int ws_cap = 1;            // warp-specialised kernel: other-term entries per 32-channel chunk (max)
     {
         // static per-row and per-chunk information of this term solve (both kernels)
         const int n_chunks = (n_chan + 31) / 32;
@@ -1026,6 +1037,7 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
             ci[ch].y = t.f_map[c1] - t.f_map[c0] + 1;
             ci[ch].z = has_o ? terms[1 - n].f_map[c0] : 0;
             ci[ch].w = has_o ? terms[1 - n].f_map[c1] - terms[1 - n].f_map[c0] + 1 : 0;
+            ws_cap = std::max(ws_cap, ci[ch].w);
         }
         int rc_;
         if ((rc_ = ensure(B.row_info, nbytes<int4>(std::max(1, n_row))))) return rc_;
@@ -1042,21 +1054,46 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
         pa.chunk_info = (const int4 *)B.chunk_info.ptr;
         aa.row_info = pa.row_info;
     }
+    // warp-specialised kernel: shared-memory layout of one consumer's ring stage (d, m, folded
+    // weights, the 32 channel maps, the other term's entries for p and q, a 32-byte header)
+    // and the ring depth that two CTAs per SM leave room for
+    WsArgs wa;
+    memset(&wa, 0, sizeof wa);
+    int ws_smem = 0, ws_grid = 0;
+    if (ws) {
+        const int ok_ = lk != KIND_NONE ? lk : rk;
+        const int eso = ok_ == KIND_FULL ? 32 : 16;
+        const int jo = has_o ? ((ws_cap * eso + 15) / 16) * 16 : 0;
+        wa.off_m = 1024;
+        wa.off_w = wa.off_m + 32 * (m16 ? 16 : 32);
+        wa.off_fm = wa.off_w + 512;
+        wa.off_jp = wa.off_fm + 256;
+        wa.off_jq = wa.off_jp + jo;
+        wa.off_h = wa.off_jq + jo;
+        wa.stage_bytes = ((wa.off_h + 32 + 127) / 128) * 128;
+        const int NC = ws_warps;
+        const int nbar = self_feed ? 1 : 2;        // barriers per stage: full (and empty)
+        const int budget = std::min(smem_optin, smem_per_sm / 2 - 1024) - 2560;
+        wa.depth = std::min(6, budget / (NC * (wa.stage_bytes + 8 * nbar)));
+        if (wa.depth < 2) ws = false;
+        else ws_smem = NC * wa.depth * wa.stage_bytes + nbar * NC * wa.depth * 8;
+    }
     StreamArgs sa;
     memset(&sa, 0, sizeof sa);
     int stream_smem = 0;
-    if (streaming) {
-        block = block_stream;
-        // step-major row table in the tile order, and the channel maps of both terms
-        const long n_rt = order == 0 ? (long)n_row : n_strip_rows;
+    const long n_rt = order == 0 ? (long)n_row : n_strip_rows;
+    if (streaming || ws) {
+        // step-major row table in the tile order, and the channel maps of both terms (padded
+        // to whole 32-channel chunks: the warp-specialised kernel copies them 32 at a time)
+        const int n_chunks = (n_chan + 31) / 32;
         int rc_;
         if ((rc_ = ensure(B.rt, nbytes<int4>(std::max(1L, n_rt))))) return rc_;
         if (m16 && (rc_ = ensure(B.rt_scale, nbytes<float>(std::max(1L, n_rt))))) return rc_;
-        if ((rc_ = ensure(B.fmap2, nbytes<int2>(n_chan)))) return rc_;
-        std::vector<int2> fm(n_chan);
+        if ((rc_ = ensure(B.fmap2, nbytes<int2>(32 * n_chunks)))) return rc_;
+        std::vector<int2> fm(32 * n_chunks, make_int2(0, 0));
         for (int ch = 0; ch < n_chan; ++ch)
             fm[ch] = make_int2(ded ? B.hufmap[ch] : t.f_map[ch], has_o ? terms[1 - n].f_map[ch] : 0);
-        CK(cudaMemcpyAsync(B.fmap2.ptr, fm.data(), nbytes<int2>(n_chan), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(B.fmap2.ptr, fm.data(), nbytes<int2>(32 * n_chunks), cudaMemcpyHostToDevice, st));
         if (n_rt) {
             row_table_kernel<<<(int)((n_rt + 255) / 256), 256, 0, st>>>(
                 (int)n_rt, order == 0 ? nullptr : d_strip_rows, (const int4 *)B.row_info.ptr, d_rows,
@@ -1064,6 +1101,66 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
             CK(cudaGetLastError());
             ++launches;
         }
+    }
+    if (ws) {
+        const int n_chunks = (n_chan + 31) / 32;
+        int rc_;
+        wa.vis = d_vis;
+        wa.model = d_model;
+        wa.model16 = d_model16;
+        wa.wf = d_wf;
+        wa.n_chan = n_chan;
+        wa.n_ant = n_ant;
+        wa.order = order;
+        wa.n_chunks = n_chunks;
+        wa.nwr = (n_chunks + 31) / 32;
+        wa.nwk = (int)((n_strip_rows + 31) / 32);
+        if (order == 0) {
+            if ((rc_ = ensure(B.ws_rl, nbytes<int4>(std::max(1, n_row))))) return rc_;
+            if (m16 && (rc_ = ensure(B.ws_rls, nbytes<float>(std::max(1, n_row))))) return rc_;
+            if ((rc_ = ensure(B.ws_rlb, nbytes<unsigned>((size_t)std::max(1, n_row) * wa.nwr)))) return rc_;
+            if ((rc_ = ensure(B.ws_n, sizeof(int)))) return rc_;
+            wa.rl = (const int4 *)B.ws_rl.ptr;
+            wa.rl_scale = m16 ? (const float *)B.ws_rls.ptr : nullptr;
+            wa.rl_bits = (const unsigned *)B.ws_rlb.ptr;
+            wa.n_rl = (const int *)B.ws_n.ptr;
+        } else {
+            if ((rc_ = ensure(B.ws_sb, nbytes<unsigned>((size_t)n_chunks * std::max(1, wa.nwk))))) return rc_;
+            if ((rc_ = ensure(B.units, sizeof(int)))) return rc_;
+            wa.sbits = (const unsigned *)B.ws_sb.ptr;
+            wa.unit_counter = (int *)B.units.ptr;
+        }
+        wa.rt = (const int4 *)B.rt.ptr;
+        wa.rt_scale = m16 ? (const float *)B.rt_scale.ptr : nullptr;
+        wa.unit_off = d_strip_off;
+        wa.n_strips = n_strips;
+        wa.tn = chain.t[n];
+        wa.to = has_o ? chain.t[1 - n] : chain.t[n];
+        wa.fmap2 = (const int2 *)B.fmap2.ptr;
+        wa.chunk_info = (const int4 *)B.chunk_info.ptr;
+        wa.active = (const uint8_t *)B.active.ptr;
+        wa.acc = (double *)B.acc.ptr;
+        wa.err = d_err;
+        wa.wait_ns = qc_wait_limit_ns();
+        wa.stall_fill = qc_wait_stall_stage();
+        if (!configured(ws_fn)) {
+            // the kernel's static shared memory (chunk table, abort flag) counts against the limit too
+            cudaFuncAttributes fa;
+            CK(cudaFuncGetAttributes(&fa, ws_fn));
+            CK(cudaFuncSetAttribute(ws_fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    smem_optin - (int)fa.sharedSizeBytes));
+            configured_fns.push_back(ws_fn);
+        }
+        int occ = 0;
+        const int ws_block = self_feed ? ws_warps * 32 : (ws_warps + 1) * 32;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ws_fn, ws_block, ws_smem);
+        if (e != cudaSuccess || occ < 1) return fail(QC_EUNSUPPORTED, "warp-specialised kernel does not fit on an SM");
+        per_sm = per_sm > 0 ? std::min(per_sm, occ) : occ;
+        ws_grid = sm_count * per_sm;
+    }
+    if (streaming) {
+        int rc_;
+        block = block_stream;
         sa.vis = d_vis;
         sa.model = d_model;
         sa.model16 = d_model16;
@@ -1093,7 +1190,9 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
         }
     }
     int grid;
-    if (streaming) {
+    if (ws) {
+        grid = ws_grid;
+    } else if (streaming) {
         if (per_sm == 0) {
             int occ = 0;
             cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, stream_fn, block, stream_smem);
@@ -1184,7 +1283,25 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
                 CK(cudaGetLastError());
             }
             CK(cudaEventRecordWithFlags(events[2 + 2 * (k - 1)], st, rec_flags));
-            if (streaming) {
+            if (ws) {
+                wa.n_active = cnt + (k - 1);
+                const uint8_t *ca = (const uint8_t *)B.chunk_act.ptr;
+                if (order == 0) {
+                    CK(cudaMemsetAsync(B.ws_n.ptr, 0, sizeof(int), st));
+                    if (n_row)
+                        ws_rows_kernel<<<(n_row + 255) / 256, 256, 0, st>>>(
+                            n_row, wa.rt, wa.rt_scale, ca, wa.n_chunks, wa.nwr, wa.n_active, (int4 *)B.ws_rl.ptr,
+                            m16 ? (float *)B.ws_rls.ptr : nullptr, (unsigned *)B.ws_rlb.ptr, (int *)B.ws_n.ptr);
+                } else {
+                    if (wa.nwk)
+                        ws_strip_bits_kernel<<<(wa.nwk + 7) / 8, 256, 0, st>>>(
+                            n_strip_rows, wa.rt, ca, wa.n_chunks, wa.nwk, wa.n_active, (unsigned *)B.ws_sb.ptr);
+                    CK(cudaMemsetAsync(B.units.ptr, 0, sizeof(int), st));
+                }
+                CK(cudaGetLastError());
+                if (self_feed) CK(L.wss_launch(ws_grid, ws_smem, st, wa));
+                else CK(L.ws_launch(ws_grid, ws_smem, st, wa));
+            } else if (streaming) {
                 sa.n_active = cnt + (k - 1);
                 if (sa.unit_counter) CK(cudaMemsetAsync(sa.unit_counter, 0, sizeof(int), st));
                 if (ded) {
@@ -1258,7 +1375,7 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
     CK(cudaStreamSynchronize(st));
     if (herr) {
         CK(cudaMemsetAsync(d_err, 0, sizeof(int), st));
-        return fail(QC_ETIMEOUT, "a bounded wait in the pipelined accumulate kernel gave up");
+        return fail(QC_ETIMEOUT, "a bounded wait in a bulk-copy accumulate kernel gave up");
     }
     double ms_sum = 0;
     long long worked = 0;

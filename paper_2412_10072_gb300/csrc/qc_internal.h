@@ -9,6 +9,7 @@
 #include "qc_stream.cuh"
 #include "qc_delay.cuh"
 #include "qc_stream_delay.cuh"
+#include "qc_ws.cuh"
 
 // Every device allocation of the library goes through these two calls.  They count the
 // live allocations and honour the test hook of qc_test_fail_alloc (qc.h), so that tests can
@@ -45,6 +46,11 @@ struct TermBufs {
     Buf rt_scale;  // float [n_row] its FP16 model scales
     Buf fmap2;     // int2 [n_chan] {f_map of this term, f_map of the other term}
     Buf units;     // int: unit counter of the streaming kernel's strip tiles
+    Buf ws_rl;     // warp-specialised kernel, row tiles: int4 [n_row] rows with an active chunk
+    Buf ws_rls;    //   float [n_row] their FP16 model scales
+    Buf ws_rlb;    //   uint32 [n_row][words] their active-chunk bits
+    Buf ws_n;      //   int: number of listed rows
+    Buf ws_sb;     // warp-specialised kernel, strip tiles: uint32 [n_chunks][words] active-entry bits
     Buf dfmap;     // delay terms: int [n_chan] parameter interval of each channel
     Buf dfr;       // delay terms: int2 [n_fint] first and last channel of each interval
     Buf dnu;       // delay terms: double [n_chan] channel frequencies
@@ -69,6 +75,13 @@ struct AccLaunch {
     const void *stream_fn = nullptr; // streaming kernel (chains of one or two terms only)
     cudaError_t (*stream_launch)(int grid, int block, int smem_bytes, cudaStream_t st, const qc::StreamArgs &a) = nullptr;
     int stream_smem_per_warp = 0;
+    const void *ws_fn = nullptr;     // warp-specialised kernel (chains of one or two terms only)
+    cudaError_t (*ws_launch)(int grid, int smem_bytes, cudaStream_t st, const qc::WsArgs &a) = nullptr;
+    int ws_nc = 0;                   // its consumer warps per CTA
+    const void *wss_fn = nullptr;    // self-feeding kernel, row tiles (chains of one or two terms only)
+    const void *wss_fn1 = nullptr;   //   ... strip tiles
+    cudaError_t (*wss_launch)(int grid, int smem_bytes, cudaStream_t st, const qc::WsArgs &a) = nullptr;
+    int wss_nw = 0;                  // its warps per CTA
 };
 // The streaming kernel of a solved delay term (chains of one or two terms).
 struct DelayLaunch {
@@ -85,7 +98,7 @@ inline AccLaunch acc_launcher(int ts, bool simple, int lk, int rk, bool m16)
 }
 
 struct qc_ctx {
-    int dev = 0, sm_count = 1, smem_optin = 0;
+    int dev = 0, sm_count = 1, smem_optin = 0, smem_per_sm = 0;
     cudaStream_t own_stream = nullptr;
     int n_row = 0, n_chan = 0, n_ant = 0, n_time = 0, n_bl = 0, n_strips = 0;
     long n_strip_rows = 0;            // rows in the baseline strips (cross-correlations)

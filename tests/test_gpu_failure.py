@@ -100,19 +100,20 @@ def test_batch_create_returns_enomem_and_leaks_nothing(lib):
     assert lib.qc_test_live_allocs() == base
 
 
+@pytest.mark.parametrize("kernel", [1, 4, 5])
 @pytest.mark.parametrize("order", [0, 1])
-def test_bounded_wait_gives_up_with_etimeout_and_the_context_recovers(lib, order):
+def test_bounded_wait_gives_up_with_etimeout_and_the_context_recovers(lib, order, kernel):
     obs = synth.plain_small(seed=3, noise=0.01)
     S = qc.Solver.from_obs(obs)
     lib.qc_test_wait_limit(2_000_000, 0)           # 2 ms; every warp's first stage is never filled
     term = qc.Term.from_spec(obs.terms[0], obs.n_ant, max_iter=20, tol=1e-6)
     with pytest.raises(qc.QCError) as ei:
-        S.solve([term], kernel=1, order=order, use_graph=False)
+        S.solve([term], kernel=kernel, order=order, use_graph=False)
     assert ei.value.code == qc.QC_ETIMEOUT
     lib.qc_test_wait_limit(0, -1)
     torch.cuda.synchronize()                       # the context and the device are still usable
     term = qc.Term.from_spec(obs.terms[0], obs.n_ant, max_iter=20, tol=1e-6)
-    S.solve([term], kernel=1, order=order)
+    S.solve([term], kernel=kernel, order=order)
     S.close()
     err = rel_err(reference_diag(term.gains.astype(np.complex128)), reference_diag(_oracle_gains(obs)))
     assert err < GAIN_TOL, err

@@ -76,7 +76,7 @@ def test_plain_small_workload_matches_oracle():
     assert st.vis_iters > 0 and st.acc_launches >= 1
 
 
-@pytest.mark.parametrize("kernel", [1, 2, 3])
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("order", [0, 1])
 @pytest.mark.parametrize("use_graph", [True, False])
 def test_plain_small_tile_orders_and_graph_agree(order, use_graph, kernel):
@@ -144,7 +144,7 @@ CHAINS = [("diag",), ("full",), ("phase",), ("full", "diag"), ("diag", "full"), 
 
 @pytest.mark.parametrize("kinds", CHAINS)
 @pytest.mark.parametrize("order", [0, 1])
-@pytest.mark.parametrize("kernel", [1, 2, 3])
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5])
 def test_single_step_matches_oracle_for_every_chain_position(kinds, order, kernel):
     obs = random_chain_obs(7, kinds)
     rng = np.random.default_rng(3)
@@ -166,6 +166,36 @@ def test_single_step_matches_oracle_for_every_chain_position(kinds, order, kerne
         step = want - np.asarray(start32[n], dtype=want.dtype)
         err = np.max(np.abs(got - want)) / max(np.max(np.abs(step)), 1e-30)
         assert err < 2e-3, (kinds, n, err)          # relative to the size of the step itself
+        assert np.array_equal(gt[n].gain_flags, ot[n].gain_flags)
+
+
+@pytest.mark.parametrize("kinds", [("diag",), ("full", "diag"), ("diag", "full")])
+@pytest.mark.parametrize("order", [0, 1])
+@pytest.mark.parametrize("kernel", [4, 5])
+def test_single_step_with_rows_of_more_than_32_chunks(kinds, order, kernel):
+    """Rows of 1100 channels (35 chunks of 32, the last one ragged): the warp-specialised kernel's
+    rows need two words of chunk bits and its strips span 35 chunk units each; intervals of 7
+    channels straddle the chunks, so the other term's entries per chunk vary in number."""
+    obs = random_chain_obs(13, kinds, n_ant=5, n_time=3, n_chan=1100, t_int=(1, 3), f_int=(7, 1100),
+                           flag_frac=0.3)
+    rng = np.random.default_rng(4)
+    start = start_params(obs, rng)
+    start32 = [np.asarray(s_, dtype=np.complex64) for s_ in start]
+    for n in range(len(kinds)):
+        P = O.OracleProblem.from_obs(obs)
+        ot = [O.OracleTerm.from_spec(s_, obs.n_ant, params=np.asarray(p_, np.complex128), solve=(i == n),
+                                     max_iter=1, tol=0.0) for i, (s_, p_) in enumerate(zip(obs.terms, start32))]
+        O.solve(P, ot, damping_mode=0, damping=1.0)
+        S = qc.Solver.from_obs(obs)
+        gt = [qc.Term.from_spec(s_, obs.n_ant, gains=p_, solve=(i == n), max_iter=1, tol=0.0)
+              for i, (s_, p_) in enumerate(zip(obs.terms, start32))]
+        S.solve(gt, damping_mode=0, damping=1.0, order=order, kernel=kernel)
+        S.close()
+        want = ot[n].params
+        got = np.asarray(gt[n].gains, dtype=np.complex128)
+        step = want - np.asarray(start32[n], dtype=want.dtype)
+        err = np.max(np.abs(got - want)) / max(np.max(np.abs(step)), 1e-30)
+        assert err < 2e-3, (kinds, n, err)
         assert np.array_equal(gt[n].gain_flags, ot[n].gain_flags)
 
 
@@ -194,7 +224,7 @@ def test_residual_matches_oracle_elementwise(kinds):
 # converged multi-term chains
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("kernel", [1, 2, 3])
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5])
 def test_two_term_chain_matches_oracle(kernel):
     obs = synth.plain_large(seed=3, n_ant=10, n_time=12, n_chan=40, noise=0.05, flag_row_frac=0.1, n_src=8)
     ot, _, ochi2 = run_oracle(obs, n_epochs=3)
@@ -223,7 +253,7 @@ def test_single_term_kinds_converge_like_oracle(kind):
 # edge cases
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("kernel", [0, 3])
+@pytest.mark.parametrize("kernel", [0, 3, 4, 5])
 def test_flagged_nan_data_and_dead_antenna(kernel):
     obs = synth.plain_small(seed=4, noise=0.01, n_time=16, n_chan=16)
     dead = (obs.ant1 == 3) | (obs.ant2 == 3)
@@ -242,7 +272,7 @@ def test_flagged_nan_data_and_dead_antenna(kernel):
     assert np.isfinite(gchi2) and abs(gchi2 - ochi2) <= CHI2_TOL * ochi2
 
 
-@pytest.mark.parametrize("kernel", [0, 3])
+@pytest.mark.parametrize("kernel", [0, 3, 4, 5])
 def test_autocorrelations_are_ignored(kernel):
     obs = synth.plain_small(seed=5, noise=0.01, n_time=8, n_chan=8)
     base = run_gpu(obs, kernel=kernel)[0][0].gains.copy()
@@ -260,7 +290,7 @@ def test_autocorrelations_are_ignored(kernel):
     assert np.allclose(got, base, rtol=1e-5, atol=1e-6)
 
 
-@pytest.mark.parametrize("kernel", [0, 3])
+@pytest.mark.parametrize("kernel", [0, 3, 4, 5])
 def test_empty_problem_and_fully_flagged(kernel):
     obs = synth.plain_small(seed=6, noise=0.01, n_time=4, n_chan=4)
     obs.flag[:] = 1
@@ -316,7 +346,7 @@ def fp16_dequantized_model(obs):
     return deq.view(np.complex64).reshape(m.shape)
 
 
-@pytest.mark.parametrize("kernel", [0, 2])
+@pytest.mark.parametrize("kernel", [0, 2, 4, 5])
 def test_fp16_model_matches_oracle_on_the_dequantized_model(kernel):
     """With the model the FP16 packing actually stores, the GPU solve (FP16 model, FP32 sums, FP64
     solves and accumulators) must meet the complex64 tolerances against the FP64 oracle."""

@@ -73,9 +73,14 @@ typedef struct qc_ctx qc_ctx;
 /*
  * One calibration problem: the inputs d, m, w of Algorithm 1 plus flags and
  * the row metadata of Section 4.1.
- *   n_row, n_chan, n_time : data sizes; n_corr must be 4 and n_dir 1.
+ *   n_row, n_chan, n_time : data sizes; n_corr must be 4.
+ *   n_dir                 : directions N_D of the model (Eq. baselinemodel),
+ *                           1..QC_MAX_DIRS; with N_D > 1 the model holds one
+ *                           set of visibilities per direction (see below).
  *   n_ant                 : antennas; ant1/ant2 in [0, n_ant).
- *   data, model           : complex64 [n_row][n_chan][4].
+ *   data                  : complex64 [n_row][n_chan][4].
+ *   model                 : complex64 [n_row][n_chan][n_dir][4] (the usual
+ *                           [n_row][n_chan][4] when n_dir = 1).
  *   weight                : float32 [n_row][n_chan][4], >= 0, per correlation.
  *   flag                  : uint8 [n_row][n_chan], nonzero = flagged, or NULL.
  *   ant1, ant2, time_idx  : int32 [n_row], HOST pointers always; rows with
@@ -84,8 +89,19 @@ typedef struct qc_ctx qc_ctx;
  *   model_fp16            : 1 = store the model on the device as float16
  *                           (re, im) pairs scaled by a per-baseline float32
  *                           factor (max |component| of that baseline) and
- *                           accumulate with compensated float32 sums.
+ *                           accumulate with compensated float32 sums
+ *                           (n_dir = 1 only).
+ * Directions (n_dir > 1): the model visibility of a sample is
+ * V_pq = sum_d C_{p,d} M_{pq,d} C_{q,d}^H (Eq. baselinemodel), where each
+ * chain term is direction-dependent (qc_term.dd = 1: its own gains per
+ * direction, Eq. g_derivative_dd) or direction-independent (the same gains in
+ * every direction, Eq. g_derivative_di).  Chains with directions take
+ * diagonal and full terms (QC_EUNSUPPORTED for phase-only and delay terms,
+ * for qc_mad_flag and qc_delay_init), and a solved direction-independent
+ * term must not have a direction-dependent term to its left
+ * (QC_EUNSUPPORTED otherwise; its Jacobian is then L_p (x) (sum_d X_d)^T).
  */
+#define QC_MAX_DIRS    64
 typedef struct {
     int32_t n_row, n_chan, n_corr, n_ant, n_dir, n_time;
     const void *data;
@@ -130,6 +146,12 @@ typedef struct {
  *                 rule per sample; otherwise the accumulate kernels form
  *                 diagonal blocks per (time interval, channel) bin and the
  *                 update reduces them over the interval's channels.
+ *   dd          : 1 = direction-dependent: with n_dir > 1 the gains (and
+ *                 gain_flags) carry a direction axis after the antenna axis,
+ *                 [n_tint][n_fint][n_ant][n_dir][4] ([..][n_ant][n_dir] for the
+ *                 flags), and the AllJones blocks are per (interval, antenna,
+ *                 direction) (Eq. g_derivative_dd).  0 = direction-independent.
+ *                 Ignored when n_dir = 1.
  */
 typedef struct {
     int32_t type, n_tint, n_fint;
@@ -143,6 +165,7 @@ typedef struct {
     int32_t memory;
     int32_t reduce;
     const double *chan_freq;
+    int32_t dd;
 } qc_term;
 
 /*

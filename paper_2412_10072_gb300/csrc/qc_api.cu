@@ -240,7 +240,8 @@ extern "C" int qc_create(const qc_problem *p, qc_ctx **out)
     auto bad = [](const char *m) { g_create_error = m; return QC_EINVAL; };
     if (!p) return bad("problem is NULL");
     if (p->n_corr != 4) return bad("n_corr must be 4");
-    if (p->n_dir != 1) return bad("n_dir must be 1");
+    if (p->n_dir < 1 || p->n_dir > QC_MAX_DIRS) return bad("n_dir must be in [1, QC_MAX_DIRS]");
+    if (p->n_dir > 1 && p->model_fp16) return bad("the float16 model takes one direction (n_dir = 1)");
     if (p->n_row < 0 || p->n_chan < 1 || p->n_ant < 2 || p->n_time < 1) return bad("invalid sizes");
     if ((long long)p->n_row * p->n_chan > (1LL << 40)) return bad("problem too large");
     if (!p->data || !p->model || !p->weight) return bad("data, model and weight are required");
@@ -261,6 +262,7 @@ extern "C" int qc_create(const qc_problem *p, qc_ctx **out)
     c->n_chan = p->n_chan;
     c->n_ant = p->n_ant;
     c->n_time = p->n_time;
+    c->n_dir = p->n_dir;
     c->m16 = p->model_fp16 != 0;
     c->has_flag = p->flag != nullptr;
     {
@@ -337,8 +339,8 @@ extern "C" int qc_create(const qc_problem *p, qc_ctx **out)
         c->d_vis = v;
         c->d_weight = w;
         float4 *m;
-        DALLOC(m, float4, 2 * n_vis);
-        HCOPY(m, p->model, nbytes<float4>(2 * n_vis));
+        DALLOC(m, float4, 2 * n_vis * p->n_dir);
+        HCOPY(m, p->model, nbytes<float4>(2 * n_vis * p->n_dir));
         model32 = m;
         if (p->flag) {
             uint8_t *f;
@@ -446,6 +448,15 @@ int qc_ctx::validate_terms(const qc_term *terms, int n_terms, bool need_solve_fi
             if (t.max_iter < 1) return fail(QC_EINVAL, "max_iter must be >= 1 for a solved term");
             if (!(t.tol >= 0)) return fail(QC_EINVAL, "tol must be >= 0");
         }
+        if (n_dir > 1) {
+            if (t.type != QC_TERM_DIAG && t.type != QC_TERM_FULL)
+                return fail(QC_EUNSUPPORTED, "chains with directions take diagonal and full terms only");
+            if (need_solve_fields && t.solve && !t.dd)
+                for (int i = 0; i < j; ++i)
+                    if (terms[i].dd)
+                        return fail(QC_EUNSUPPORTED, "a solved direction-independent term must not have a "
+                                                     "direction-dependent term to its left");
+        }
     }
     return QC_OK;
 }
@@ -525,8 +536,9 @@ int qc_ctx::stage_terms(const qc_term *terms, int n_terms, cudaStream_t st, Chai
     for (int j = 0; j < n_terms; ++j) {
         const qc_term &t = terms[j];
         TermBufs &B = tb[j];
+        cur_nd[j] = term_nd(t);
         const size_t nb = term_nbins(t);
-        const size_t nent = nb * n_ant;
+        const size_t nent = nb * term_nat(t);
         const size_t tab_f4 = nent * (t.type == 1 ? 2 : 1);
         int rc;
         if ((rc = ensure(B.maps, nbytes<int>(n_time + n_chan)))) return rc;
@@ -557,7 +569,7 @@ int qc_ctx::stage_terms(const qc_term *terms, int n_terms, cudaStream_t st, Chai
                 CK(cudaMemcpyAsync(B.stage.ptr, t.gains, nent * (t.type == 2 ? 8 : 32), cudaMemcpyHostToDevice, st));
                 src = B.stage.ptr;
             }
-            gains_in_kernel<<<grid_for((long)nent, 256, sm_count), 256, 0, st>>>(t.type, t.n_tint, t.n_fint, n_ant, src,
+            gains_in_kernel<<<grid_for((long)nent, 256, sm_count), 256, 0, st>>>(t.type, t.n_tint, t.n_fint, term_nat(t), src,
                                                                                 (double *)B.params.ptr,
                                                                                 (float4 *)B.tab.ptr);
             CK(cudaGetLastError());
@@ -634,6 +646,7 @@ extern "C" int qc_delay_init(qc_ctx *c, qc_term *term, int32_t ref_ant, int32_t 
     c->err.clear();
     if (!term) return c->fail(QC_EINVAL, "term is NULL");
     if (term->type != QC_TERM_DELAY) return c->fail(QC_EINVAL, "qc_delay_init needs a QC_TERM_DELAY term");
+    if (c->n_dir > 1) return c->fail(QC_EUNSUPPORTED, "qc_delay_init takes problems with one direction");
     int rc = c->validate_terms(term, 1, false);
     if (rc) return rc;
     if (ref_ant < 0 || ref_ant >= c->n_ant) return c->fail(QC_EINVAL, "ref_ant out of range");
@@ -729,6 +742,22 @@ int qc_ctx::run_residual(const Chain &chain, float4 *dres, double *d_chi2, cudaS
 {
     qc_ctx *c = this;
     CK(cudaMemsetAsync(d_chi2, 0, sizeof(double), st));
+    if (n_dir > 1) {
+        DDArgs da;
+        memset(&da, 0, sizeof da);
+        da.D = data_desc();
+        da.wf = d_wf;
+        da.row_live = d_row_live;
+        da.n_dir = n_dir;
+        da.C = chain;
+        da.C.n = -1;
+        for (int j = 0; j < chain.n_terms; ++j) da.nd[j] = cur_nd[j];
+        da.resid = dres;
+        da.chi2 = d_chi2;
+        CK(dd_launch_residual(da, grid_for((long)n_row * n_chan, 256, sm_count), st));
+        ++launches;
+        return QC_OK;
+    }
     ResArgs ra;
     ra.D = data_desc();
     ra.C = chain;
@@ -805,23 +834,24 @@ extern "C" int qc_solve(qc_ctx *c, qc_term *terms, int32_t n_terms, const qc_opt
 
     // per solved term: bin counts and byte weights
     const long long b_flag = c->has_flag ? 1 : 0;
-    const long long b_unflag = 32 + (c->m16 ? 16 : 32) + 16;
+    const long long b_unflag = 32 + (c->m16 ? 16 : 32 * c->n_dir) + 16;
     for (int j = 0; j < n_terms; ++j) {
         if (!terms[j].solve) continue;
         const qc_term &t = xt[j];
         TermBufs &B = c->tb[j];
         const size_t nb = term_nbins(t);
         const size_t KG = t.type == 1 ? KG_FULL : KG_DIAG;
-        if ((rc = c->ensure(B.acc, nbytes<double>(nb * c->n_ant * KG)))) return rc;
+        const size_t nat = c->term_nat(t);
+        if ((rc = c->ensure(B.acc, nbytes<double>(nb * nat * KG)))) return rc;
         if ((rc = c->ensure(B.active, nb))) return rc;
         if ((rc = c->ensure(B.cnt, nbytes<int>(t.max_iter + 1)))) return rc;
         if ((rc = c->ensure(B.nvis, nbytes<long long>(3 * nb)))) return rc;
         if ((rc = c->ensure(B.iters, nbytes<int>(nb)))) return rc;
-        if ((rc = c->ensure(B.flags, nb * c->n_ant))) return rc;
-        CK(cudaMemsetAsync(B.acc.ptr, 0, nbytes<double>(nb * c->n_ant * KG), st));
+        if ((rc = c->ensure(B.flags, nb * nat))) return rc;
+        CK(cudaMemsetAsync(B.acc.ptr, 0, nbytes<double>(nb * nat * KG), st));
         CK(cudaMemsetAsync(B.nvis.ptr, 0, nbytes<long long>(3 * nb), st));
         CK(cudaMemsetAsync(B.iters.ptr, 0, nbytes<int>(nb), st));
-        CK(cudaMemsetAsync(B.flags.ptr, 0, nb * c->n_ant, st));
+        CK(cudaMemsetAsync(B.flags.ptr, 0, nb * nat, st));
         long long *nvis = (long long *)B.nvis.ptr;
         CountArgs ca;
         ca.D = c->data_desc();
@@ -863,7 +893,7 @@ extern "C" int qc_solve(qc_ctx *c, qc_term *terms, int32_t n_terms, const qc_opt
         if (!terms[j].solve) continue;
         qc_term &t = terms[j];
         TermBufs &B = c->tb[j];
-        const size_t nb = term_nbins(t), nent = nb * c->n_ant;
+        const size_t nb = term_nbins(t), nent = nb * c->term_nat(t);
         const size_t gbytes = nent * (t.type == 2 ? 8 : (t.type == QC_TERM_DELAY ? 16 : 32));
         void *dst = t.memory == QC_MEM_DEVICE ? t.gains : B.stage.ptr;
         if (t.type == QC_TERM_DELAY)
@@ -946,7 +976,10 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
     int per_sm = o->ctas_per_sm > 0 ? o->ctas_per_sm : 0;
     const bool simple = n_terms <= 2;
     AccLaunch L = acc_launcher(ts, simple, lk, rk, m16);
-    if (!L.fn) return fail(QC_EUNSUPPORTED, "no accumulate kernel for this chain");
+    // chains with directions: the direction-dependent accumulate kernel (qc_dd.cu)
+    const bool ddp = n_dir > 1;
+    const int nat = term_nat(t);
+    if (!L.fn && !ddp) return fail(QC_EUNSUPPORTED, "no accumulate kernel for this chain");
     // pipelined kernel: shared-memory layout of the per-warp rings for this chain
     PipeArgs pa;
     memset(&pa, 0, sizeof pa);
@@ -956,11 +989,11 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
     // kernel 4: the warp-specialised kernel (chains of one or two terms; a solved delay term
     // keeps its own streaming kernel)
     // kernel 5: the self-feeding variant (every warp issues its own bulk copies)
-    bool ws = L.ws_fn != nullptr && !delay[n] && n_ant < 32768 && (o->kernel == 4 || o->kernel == 5);
+    bool ws = !ddp && L.ws_fn != nullptr && !delay[n] && n_ant < 32768 && (o->kernel == 4 || o->kernel == 5);
     const bool self_feed = o->kernel == 5;
     const void *ws_fn = self_feed ? (order == 0 ? L.wss_fn : L.wss_fn1) : L.ws_fn;
     const int ws_warps = self_feed ? L.wss_nw : L.ws_nc;     // warps that own a ring
-    const bool streaming = L.stream_fn != nullptr && n_ant < 32768 &&
+    const bool streaming = !ddp && L.stream_fn != nullptr && n_ant < 32768 &&
                            (o->kernel == 3 || o->kernel == 0 || ((o->kernel == 4 || o->kernel == 5) && delay[n]));
     // a solved delay term under the streaming kernel: its own kernel, which applies the chain
     // rule per sample and keeps sums per parameter interval (else: the per-channel bins)
@@ -980,7 +1013,7 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
     }
     const void *stream_fn = ded ? DL.fn : L.stream_fn;
     const int stream_smem_per_warp = ded ? DL.smem_per_warp : L.stream_smem_per_warp;
-    bool pipelined = !streaming && L.pipe_fn != nullptr && (o->kernel == 1 || (o->kernel == 0 && order == 1));
+    bool pipelined = !ddp && !streaming && L.pipe_fn != nullptr && (o->kernel == 1 || (o->kernel == 0 && order == 1));
     const bool has_o = n_terms == 2;
     if (pipelined) {
         const int NW = L.pipe_nw;
@@ -1190,7 +1223,20 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
         }
     }
     int grid;
-    if (ws) {
+    DDArgs dda;
+    memset(&dda, 0, sizeof dda);
+    if (ddp) {
+        dda.D = data_desc();
+        dda.wf = d_wf;
+        dda.row_live = d_row_live;
+        dda.n_dir = n_dir;
+        dda.C = chain;
+        for (int j = 0; j < n_terms; ++j) dda.nd[j] = cur_nd[j];
+        dda.dd_solved = cur_nd[n] > 1;
+        dda.acc = (double *)B.acc.ptr;
+        dda.active = (const uint8_t *)B.active.ptr;
+        grid = sm_count * 8;
+    } else if (ws) {
         grid = ws_grid;
     } else if (streaming) {
         if (per_sm == 0) {
@@ -1233,7 +1279,7 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
     ua.type = t.type;
     ua.n_bins = nb;
     ua.n_fint = t.n_fint;
-    ua.n_ant = n_ant;
+    ua.n_ant = nat;
     ua.acc = (double *)B.acc.ptr;
     ua.params = (double *)B.params.ptr;
     ua.tab = (float4 *)B.tab.ptr;
@@ -1246,7 +1292,7 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
     ua.acc_bytes = (unsigned long long *)scalars.ptr + 1;
     ua.tol = t.tol;
     int *cnt = (int *)B.cnt.ptr;
-    const int upd_block = n_ant >= 128 ? 128 : (n_ant > 32 ? 64 : 32);
+    const int upd_block = nat >= 128 ? 128 : (nat > 32 ? 64 : 32);
     // delay terms: the update reduces the channel bins of each parameter interval
     DelayUpdArgs dua;
     memset(&dua, 0, sizeof dua);
@@ -1283,7 +1329,10 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
                 CK(cudaGetLastError());
             }
             CK(cudaEventRecordWithFlags(events[2 + 2 * (k - 1)], st, rec_flags));
-            if (ws) {
+            if (ddp) {
+                dda.n_active = cnt + (k - 1);
+                CK(dd_launch_acc(dda, ts, grid, st));
+            } else if (ws) {
                 wa.n_active = cnt + (k - 1);
                 const uint8_t *ca = (const uint8_t *)B.chunk_act.ptr;
                 if (order == 0) {
@@ -1321,7 +1370,7 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
             CK(cudaEventRecordWithFlags(events[2 + 2 * (k - 1) + 1], st, rec_flags));
             if (t.reduce) {
                 const size_t KG = ded ? KG_SUMS : (t.type == 1 ? KG_FULL : KG_DIAG);
-                if (o->allreduce((double *)B.acc.ptr, (int64_t)(ded ? nbu : nb) * n_ant * KG, st, o->allreduce_user))
+                if (o->allreduce((double *)B.acc.ptr, (int64_t)(ded ? nbu : nb) * nat * KG, st, o->allreduce_user))
                     return fail(QC_ECUDA, "allreduce callback failed");
             }
             ua.k = k;
@@ -1594,6 +1643,7 @@ extern "C" int qc_mad_flag(qc_ctx *c, const qc_term *terms, int32_t n_terms, dou
     if (!c) return QC_EINVAL;
     c->err.clear();
     if (!flags_out) return c->fail(QC_EINVAL, "flags_out is NULL");
+    if (c->n_dir > 1) return c->fail(QC_EUNSUPPORTED, "qc_mad_flag takes problems with one direction");
     if (!(threshold > 0) || !std::isfinite(threshold)) return c->fail(QC_EINVAL, "threshold must be positive and finite");
     if (out_memory != QC_MEM_HOST && out_memory != QC_MEM_DEVICE) return c->fail(QC_EINVAL, "out_memory invalid");
     int rc = c->validate_terms(terms, n_terms, false);

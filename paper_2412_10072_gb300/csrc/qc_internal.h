@@ -21,6 +21,26 @@ void qc_dev_free(void *p);
 uint64_t qc_wait_limit_ns();
 int qc_wait_stall_stage();
 
+namespace qc {
+// Chains with direction-dependent terms (qc_dd.cu).
+struct DDArgs {
+    Data D;                  // model is [n_row][n_chan][n_dir] x 2 float4
+    const float4 *wf;        // [n_row][n_chan] weights with flags folded in
+    const uint8_t *row_live; // [n_row]
+    int n_dir;
+    Chain C;                 // C.n: the solved term (-1 for the residual)
+    int nd[MAXT];            // directions in term j's table (1: direction-independent)
+    int dd_solved;           // the solved term is direction-dependent (grid dimension y: direction)
+    double *acc;             // [bins][n_ant * nd[n]][KG]
+    const uint8_t *active;   // [bins]
+    const int *n_active;     // nonzero: some interval still iterating
+    float4 *resid;           // residual: [n_row][n_chan] x 2, or null
+    double *chi2;            // residual: one double (accumulated)
+};
+} // namespace qc
+cudaError_t dd_launch_acc(const qc::DDArgs &a, int ts, int grid_x, cudaStream_t st);
+cudaError_t dd_launch_residual(const qc::DDArgs &a, int grid, cudaStream_t st);
+
 struct Buf {
     void *ptr = nullptr;
     size_t bytes = 0;
@@ -101,6 +121,7 @@ struct qc_ctx {
     int dev = 0, sm_count = 1, smem_optin = 0, smem_per_sm = 0;
     cudaStream_t own_stream = nullptr;
     int n_row = 0, n_chan = 0, n_ant = 0, n_time = 0, n_bl = 0, n_strips = 0;
+    int n_dir = 1;                    // directions of the model (Eq. baselinemodel)
     long n_strip_rows = 0;            // rows in the baseline strips (cross-correlations)
     bool m16 = false, has_flag = false;
     const float4 *d_vis = nullptr, *d_model = nullptr, *d_weight = nullptr;
@@ -137,6 +158,11 @@ struct qc_ctx {
     // delay terms of the current call (by chain position) and the view the kernels work on:
     // a diagonal term with one bin per (time interval, channel) and the identity channel map
     bool delay[QC_MAX_TERMS] = {};
+    // directions in a term's tables: N_D for a direction-dependent term, else 1; such a term
+    // is stored over n_ant * N_D (antenna, direction) pairs
+    int term_nd(const qc_term &t) const { return (t.dd && n_dir > 1) ? n_dir : 1; }
+    int term_nat(const qc_term &t) const { return n_ant * term_nd(t); }
+    int cur_nd[QC_MAX_TERMS] = {1, 1, 1, 1};   // term_nd of the chain staged by the current call
     std::vector<int> fid;             // identity channel map [n_chan]
     int expand_terms(const qc_term *terms, int n_terms, std::vector<qc_term> &xt, cudaStream_t st);
     qc::DelayArgs delay_args(int j, const qc_term &xt_j);

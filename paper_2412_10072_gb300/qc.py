@@ -44,7 +44,7 @@ class _Term(C.Structure):
     _fields_ = [("type", C.c_int32), ("n_tint", C.c_int32), ("n_fint", C.c_int32), ("t_map", C.c_void_p),
                 ("f_map", C.c_void_p), ("gains", C.c_void_p), ("gain_flags", C.c_void_p), ("iters", C.c_void_p),
                 ("solve", C.c_int32), ("max_iter", C.c_int32), ("tol", C.c_double), ("memory", C.c_int32),
-                ("reduce", C.c_int32), ("chan_freq", C.c_void_p)]
+                ("reduce", C.c_int32), ("chan_freq", C.c_void_p), ("dd", C.c_int32)]
 
 
 ALLREDUCE_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p)
@@ -147,13 +147,18 @@ class Term:
     [..][4] = (phi_X, tau_X, phi_Y, tau_Y) (delay, with ``chan_freq`` [n_chan], the frequency of
     every channel), or a CUDA tensor of the same layout (complex64 / float32).  After a solve the
     solved values are in ``self.gains`` (host arrays are updated in place).
+    A direction-dependent term (``dd`` with ``n_dir`` > 1) has gains [n_tint][n_fint][n_ant][n_dir][4]
+    and gain flags [n_tint][n_fint][n_ant][n_dir].
     """
 
     def __init__(self, kind: str, t_map, f_map, n_tint: int, n_fint: int, n_ant: int, gains=None,
                  solve: bool = True, max_iter: int = 20, tol: float = 1e-6, reduce: bool = False,
-                 chan_freq=None):
+                 chan_freq=None, dd: bool = False, n_dir: int = 1):
         self.kind = kind
         self.type = KINDS[kind]
+        self.dd = bool(dd)
+        nd = int(n_dir) if (dd and n_dir > 1) else 1
+        ax = (n_ant, nd) if nd > 1 else (n_ant,)
         self.chan_freq = None
         if kind == "delay":
             if chan_freq is None:
@@ -168,7 +173,7 @@ class Term:
             elif kind == "delay":
                 gains = np.zeros((n_tint, n_fint, n_ant, 4), dtype=np.float32)
             else:
-                gains = np.zeros((n_tint, n_fint, n_ant, 4), dtype=np.complex64)
+                gains = np.zeros((n_tint, n_fint) + ax + (4,), dtype=np.complex64)
                 gains[..., 0] = 1
                 gains[..., 3] = 1
         if _is_dev(gains):
@@ -176,13 +181,13 @@ class Term:
             self.memory = QC_MEM_DEVICE
             dev = gains.device
             import torch
-            self.gain_flags = torch.zeros((n_tint, n_fint, n_ant), dtype=torch.int8, device=dev)
+            self.gain_flags = torch.zeros((n_tint, n_fint) + ax, dtype=torch.int8, device=dev)
             self.iters = torch.zeros((n_tint, n_fint), dtype=torch.int32, device=dev)
         else:
             dt = np.float32 if kind in ("phase", "delay") else np.complex64
             self.gains = np.array(gains, dtype=dt, copy=True, order="C")
             self.memory = QC_MEM_HOST
-            self.gain_flags = np.zeros((n_tint, n_fint, n_ant), dtype=np.int8)
+            self.gain_flags = np.zeros((n_tint, n_fint) + ax, dtype=np.int8)
             self.iters = np.zeros((n_tint, n_fint), dtype=np.int32)
         self.solve, self.max_iter, self.tol, self.reduce = bool(solve), int(max_iter), float(tol), bool(reduce)
 
@@ -193,7 +198,7 @@ class Term:
     def _c(self) -> _Term:
         return _Term(self.type, self.n_tint, self.n_fint, _addr(self.t_map), _addr(self.f_map), _addr(self.gains),
                      _addr(self.gain_flags), _addr(self.iters), int(self.solve), self.max_iter, self.tol,
-                     self.memory, int(self.reduce), _addr(self.chan_freq))
+                     self.memory, int(self.reduce), _addr(self.chan_freq), int(self.dd))
 
 
 def _terms_array(terms: Sequence[Term]):
@@ -201,7 +206,10 @@ def _terms_array(terms: Sequence[Term]):
 
 
 class Solver:
-    """A staged calibration problem (qc_create / qc_solve / qc_residual / qc_destroy)."""
+    """A staged calibration problem (qc_create / qc_solve / qc_residual / qc_destroy).
+
+    The model is [n_row][n_chan][4], or [n_row][n_chan][n_dir][4] for a model with directions.
+    """
 
     def __init__(self, data, model, weight, flag, ant1, ant2, time_idx, n_ant: int, n_time: int,
                  model_fp16: bool = False):
@@ -225,7 +233,8 @@ class Solver:
         a1, a2, ti = _host(ant1, np.int32), _host(ant2, np.int32), _host(time_idx, np.int32)
         self._meta = (a1, a2, ti)
         self.n_row, self.n_chan, self.n_ant, self.n_time = n_row, n_chan, int(n_ant), int(n_time)
-        p = _Problem(n_row, n_chan, 4, self.n_ant, 1, self.n_time, _addr(data), _addr(model), _addr(weight),
+        self.n_dir = int(model.shape[2]) if len(model.shape) == 4 else 1
+        p = _Problem(n_row, n_chan, 4, self.n_ant, self.n_dir, self.n_time, _addr(data), _addr(model), _addr(weight),
                      _addr(flag), _addr(a1), _addr(a2), _addr(ti), memory, int(bool(model_fp16)))
         h = C.c_void_p()
         rc = self._lib.qc_create(C.byref(p), C.byref(h))

@@ -63,8 +63,9 @@ def _problem(**over):
     return p, keep
 
 
-@pytest.mark.parametrize("over", [dict(n_corr=2), dict(n_dir=2), dict(n_ant=1), dict(n_chan=0), dict(n_time=0),
-                                  dict(memory=7), dict(n_ant=2), dict(n_time=1)])
+@pytest.mark.parametrize("over", [dict(n_corr=2), dict(n_dir=0), dict(n_dir=65), dict(n_dir=2, model_fp16=1),
+                                  dict(n_ant=1), dict(n_chan=0), dict(n_time=0), dict(memory=7), dict(n_ant=2),
+                                  dict(n_time=1)])
 def test_create_rejects_invalid_problems(lib, over):
     p, keep = _problem(**over)
     h = C.c_void_p()

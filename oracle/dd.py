@@ -12,7 +12,13 @@ approximation keeps one block per (interval, antenna) and, for a direction-depen
 per direction (Eq. jhj_entry_simplified, Eq. jhr_entry_simplified); the update is Algorithm 1.
 
 Plain numpy with explicit loops over rows, channels and directions: slow, small cases only.
-Term kinds: "diag" (free XX, YY) and "full" (all four entries).
+Term kinds: "diag" (free XX, YY), "full" (all four entries) and "delay" (direction-independent
+only): four real parameters u = (phi_X, tau_X, phi_Y, tau_Y) per interval and antenna, and the
+diagonal gain g_c(nu) = exp(i (phi_c + 2 pi tau_c nu)) at the frequency nu of every channel
+(Scenario 2, the residual delay and phase term K).  Its derivatives follow the chain rule
+dg_c/dphi_c = i g_c, dg_c/dtau_c = 2 pi nu i g_c, and its blocks are 2 Re(.) of the sums
+(Eq. jhj_case2, Eq. jhwr_case2); it converges on the relative change of its gains over the
+interval's channels.
 """
 from __future__ import annotations
 
@@ -25,25 +31,42 @@ PERM = [0, 2, 1, 3]
 
 @dataclasses.dataclass
 class DDTerm:
-    kind: str                 # "diag" or "full"
+    kind: str                 # "diag", "full" or "delay"
     dd: bool                  # direction-dependent
     t_map: np.ndarray         # [n_time] -> interval
     f_map: np.ndarray         # [n_chan] -> interval
-    params: np.ndarray        # complex [n_tint][n_fint][n_ant][n_dir if dd else 1][4]
+    params: np.ndarray        # complex [n_tint][n_fint][n_ant][n_dir if dd else 1][4]; delay: real [..][1][4]
     solve: bool = True
     max_iter: int = 20
     tol: float = 1e-6
+    chan_freq: np.ndarray = None   # delay: [n_chan] frequency of every channel
 
     @property
     def free(self):
         return [0, 3] if self.kind == "diag" else [0, 1, 2, 3]
 
+    def delay_gains(self, u, c):
+        nu = self.chan_freq[c]
+        return np.exp(1j * (u[0] + 2 * np.pi * u[1] * nu)), np.exp(1j * (u[2] + 2 * np.pi * u[3] * nu))
+
     def jones(self, t, c, a, d):
         g = self.params[self.t_map[t], self.f_map[c], a, d if self.dd else 0]
+        if self.kind == "delay":
+            gx, gy = self.delay_gains(g, c)
+            return np.array([[gx, 0], [0, gy]], dtype=np.complex128)
         J = g.reshape(2, 2).copy()
         if self.kind == "diag":
             J[0, 1] = J[1, 0] = 0
         return J
+
+    def columns(self, E, t, c, a):
+        """The Jacobian columns of the term's free parameters from E = dv/dvec(G) (4x4)."""
+        if self.kind != "delay":
+            return E[:, self.free]
+        nu = self.chan_freq[c]
+        gx, gy = self.delay_gains(self.params[self.t_map[t], self.f_map[c], a, 0], c)
+        Ex, Ey = E[:, 0] * 1j * gx, E[:, 3] * 1j * gy
+        return np.stack([Ex, 2 * np.pi * nu * Ex, Ey, 2 * np.pi * nu * Ey], axis=1)
 
 
 @dataclasses.dataclass
@@ -143,12 +166,14 @@ def normal_equations(P: DDProblem, terms, n):
                         M = M.conj().T
                     L, R = _factors(terms, n, t, c, a, d)
                     X = R @ M @ _chain(terms, t, c, b, d).conj().T
-                    E = np.kron(L, X.T)[:, free]           # Eq. vectrick, restricted to the free entries
+                    E = T.columns(np.kron(L, X.T), t, c, a)  # Eq. vectrick, restricted to the free parameters
                     Es.append(E)
                 blocks = [(d, Es[d]) for d in range(P.n_dir)] if T.dd else [(0, sum(Es))]
                 for k, E in blocks:
                     jhj[ti, fi, a, k] += E.conj().T @ (w[:, None] * E)
                     jhr[ti, fi, a, k] += E.conj().T @ (w * r)
+    if T.kind == "delay":                            # real parameters: 2 Re(.) (Eq. jhj_case2, Eq. jhwr_case2)
+        jhj, jhr = 2 * jhj.real + 0j, 2 * jhr.real + 0j
     return jhj, jhr
 
 
@@ -177,10 +202,23 @@ def solve_term(P: DDProblem, terms, n, damping_mode: int = 1):
                         if not tr > 0 or 1.0 / np.linalg.cond(A, 1) < 1e-12:
                             continue
                         x = np.linalg.solve(A, bvec)
-                        T.params[ti, fi, a, blk, free] += alpha * x
+                        if T.kind == "delay":
+                            T.params[ti, fi, a, blk] += alpha * x.real
+                        else:
+                            T.params[ti, fi, a, blk, free] += alpha * x
                 iters[ti, fi] = k
-                num = np.sum(np.abs(T.params[ti, fi] - old) ** 2)
-                den = np.sum(np.abs(T.params[ti, fi]) ** 2)
+                if T.kind == "delay":
+                    # relative change of the gains over the interval's channels
+                    num = den = 0.0
+                    for c in np.nonzero(T.f_map == fi)[0]:
+                        for a in range(P.n_ant):
+                            go = np.array(T.delay_gains(old[a, 0], c))
+                            gn = np.array(T.delay_gains(T.params[ti, fi, a, 0], c))
+                            num += np.sum(np.abs(gn - go) ** 2)
+                            den += np.sum(np.abs(gn) ** 2)
+                else:
+                    num = np.sum(np.abs(T.params[ti, fi] - old) ** 2)
+                    den = np.sum(np.abs(T.params[ti, fi]) ** 2)
                 if den == 0 or np.sqrt(num / den) < T.tol:
                     active[ti, fi] = False
     return iters

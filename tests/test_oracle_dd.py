@@ -122,3 +122,83 @@ def test_direction_dependent_gains_are_recovered():
     want = truth.params[0, 0][:, :, [0, 3]]
     ref = lambda g: g * np.conj(g[:1]) / np.abs(g[:1])         # each direction's phase gauge
     np.testing.assert_allclose(ref(got), ref(want), rtol=0, atol=1e-8)
+
+
+# ---------------------------------------------------------------------------
+# the delay kind (Scenario 2) in chains with directions
+# ---------------------------------------------------------------------------
+
+def _delay_term(rng, n_time, n_chan, n_ant, nt=1, nf=1, scale=1.0):
+    """K: (phi_X, tau_X, phi_Y, tau_Y) per interval and antenna; frequencies in GHz, delays in ns."""
+    par = scale * np.stack([rng.uniform(-1, 1, (nt, nf, n_ant)), rng.uniform(-0.5, 0.5, (nt, nf, n_ant)),
+                            rng.uniform(-1, 1, (nt, nf, n_ant)), rng.uniform(-0.5, 0.5, (nt, nf, n_ant))], -1)
+    tm = (np.arange(n_time) * nt // n_time).astype(np.int32)
+    fm = (np.arange(n_chan) * nf // n_chan).astype(np.int32)
+    freq = np.linspace(1.0, 1.4, n_chan)
+    return dd.DDTerm("delay", False, tm, fm, par[:, :, :, None, :].copy(), chan_freq=freq)
+
+
+def _c_terms(terms, n_ant):
+    out = []
+    for T in terms:
+        nt, nf = T.params.shape[:2]
+        par = T.params[:, :, :, 0].copy()
+        out.append(O.OracleTerm(T.kind, T.t_map, T.f_map, nt, nf, n_ant, params=par,
+                                chan_freq=T.chan_freq if T.kind == "delay" else None))
+    return out
+
+
+@pytest.mark.parametrize("kinds,n", [(("delay",), 0), (("delay", "diag"), 0), (("delay", "diag"), 1),
+                                     (("full", "delay"), 1)])
+def test_delay_with_one_direction_reproduces_the_c_oracle(kinds, n):
+    """Normal equations, chi^2 and the whole Algorithm 1 solve of a delay term, and of a term
+    beside it, equal the one-direction C oracle (itself pinned by finite differences)."""
+    P, rng = _problem(9, n_chan=4, n_dir=1)
+    terms = []
+    for k in kinds:
+        terms.append(_delay_term(rng, 2, 4, P.n_ant, nt=2) if k == "delay" else
+                     _term(rng, k, False, P.n_ant, 2, 4, 1, nt=2))
+    jhj, jhr = dd.normal_equations(P, terms, n)
+    CP = O.OracleProblem(P.data, P.model[:, :, 0], P.weight, P.flag, P.ant1, P.ant2, P.time_idx, P.n_ant, 2)
+    ct = _c_terms(terms, P.n_ant)
+    cj, cr = O.normal_equations(CP, ct, n)
+    np.testing.assert_allclose(jhj[:, :, :, 0], cj, rtol=1e-12, atol=1e-12 * np.abs(cj).max())
+    np.testing.assert_allclose(jhr[:, :, :, 0], cr, rtol=1e-12, atol=1e-12 * np.abs(cr).max())
+    assert abs(dd.residual(P, terms)[0] - O.residual(CP, ct)) <= 1e-12 * O.residual(CP, ct)
+    terms[n].max_iter, terms[n].tol = 6, 1e-9
+    ct[n].max_iter, ct[n].tol = 6, 1e-9
+    it_dd = dd.solve_term(P, terms, n, damping_mode=1)
+    it_c = O.solve_term(CP, ct, n, damping_mode=1)
+    np.testing.assert_array_equal(it_dd, it_c)
+    np.testing.assert_allclose(terms[n].params[:, :, :, 0], ct[n].params, rtol=0, atol=1e-9)
+
+
+@pytest.mark.parametrize("kinds,dds,n", [(("delay", "diag"), (False, True), 0), (("delay", "full"), (False, True), 0)])
+def test_delay_blocks_with_two_directions_match_finite_differences(kinds, dds, n):
+    """With two directions and a direction-dependent term to its right, the delay term's real
+    4x4 block is 2 Re(J^H W J) and its right-hand side 2 Re(J^H W r), J = dv/du by central
+    differences in the four real parameters (Eq. jhj_case2, Eq. jhwr_case2)."""
+    P, rng = _problem(12, n_chan=4)
+    terms = [_delay_term(rng, 2, 4, P.n_ant), _term(rng, kinds[1], True, P.n_ant, 2, 4, 2)]
+    jhj, jhr = dd.normal_equations(P, terms, n)
+    T = terms[n]
+    w = P.weight.copy()
+    w[P.flag.astype(bool)] = 0
+    w = w.reshape(-1)
+    r0 = dd.residual(P, terms)[1].reshape(-1)
+    h = 1e-6
+    for a in range(P.n_ant):
+        J = []
+        for e in range(4):
+            base = T.params[0, 0, a, 0, e]
+            T.params[0, 0, a, 0, e] = base + h
+            rp = dd.residual(P, terms)[1].reshape(-1)
+            T.params[0, 0, a, 0, e] = base - h
+            rm = dd.residual(P, terms)[1].reshape(-1)
+            T.params[0, 0, a, 0, e] = base
+            J.append(-(rp - rm) / (2 * h))                    # dv/du = -dr/du
+        J = np.stack(J, 1)
+        fj = 2 * (J.conj().T @ (w[:, None] * J)).real
+        fr = 2 * (J.conj().T @ (w * r0)).real
+        assert np.abs(jhj[0, 0, a, 0] - fj).max() <= 1e-6 * np.abs(fj).max()
+        assert np.abs(jhr[0, 0, a, 0] - fr).max() <= 1e-6 * max(np.abs(fr).max(), 1e-30)

@@ -96,8 +96,9 @@ typedef struct qc_ctx qc_ctx;
  * chain term is direction-dependent (qc_term.dd = 1: its own gains per
  * direction, Eq. g_derivative_dd) or direction-independent (the same gains in
  * every direction, Eq. g_derivative_di).  Chains with directions take
- * diagonal and full terms (QC_EUNSUPPORTED for phase-only and delay terms,
- * for qc_mad_flag and qc_delay_init), and a solved direction-independent
+ * diagonal and full terms, either kind, and direction-independent delay
+ * terms (QC_EUNSUPPORTED for phase-only terms, direction-dependent delay
+ * terms, qc_mad_flag and qc_delay_init), and a solved direction-independent
  * term must not have a direction-dependent term to its left
  * (QC_EUNSUPPORTED otherwise; its Jacobian is then L_p (x) (sum_d X_d)^T).
  */

@@ -449,8 +449,10 @@ int qc_ctx::validate_terms(const qc_term *terms, int n_terms, bool need_solve_fi
             if (!(t.tol >= 0)) return fail(QC_EINVAL, "tol must be >= 0");
         }
         if (n_dir > 1) {
-            if (t.type != QC_TERM_DIAG && t.type != QC_TERM_FULL)
-                return fail(QC_EUNSUPPORTED, "chains with directions take diagonal and full terms only");
+            if (t.type == QC_TERM_PHASE)
+                return fail(QC_EUNSUPPORTED, "chains with directions take diagonal, full and delay terms");
+            if (t.type == QC_TERM_DELAY && t.dd)
+                return fail(QC_EUNSUPPORTED, "a delay term is direction-independent");
             if (need_solve_fields && t.solve && !t.dd)
                 for (int i = 0; i < j; ++i)
                     if (terms[i].dd)

@@ -176,6 +176,84 @@ def test_converged_direction_dependent_gains_match_oracle(n_dir):
     assert gt[1].gain_flags.shape == (1, 4, n_ant, n_dir) and np.all(gt[1].gain_flags == 0)
 
 
+def _delay(rng, n_ant, n_time, n_chan, nt=1, spread=1.0):
+    par = spread * np.stack([rng.uniform(-1, 1, (nt, 1, n_ant)), rng.uniform(-0.5, 0.5, (nt, 1, n_ant)),
+                             rng.uniform(-1, 1, (nt, 1, n_ant)), rng.uniform(-0.5, 0.5, (nt, 1, n_ant))], -1)
+    tm, fm = _maps(n_time, n_chan, nt, 1)
+    return par[:, :, :, None, :], tm, fm, np.linspace(1.0, 1.4, n_chan)
+
+
+def _ok_delay(par, tm, fm, freq, solve, max_iter=1, tol=0.0):
+    return dd.DDTerm("delay", False, tm, fm, par.copy(), solve=solve, max_iter=max_iter, tol=tol, chan_freq=freq)
+
+
+def _gk_delay(par, tm, fm, freq, n_ant, solve, max_iter=1, tol=0.0):
+    nt, nf = par.shape[:2]
+    return qc.Term("delay", tm, fm, nt, nf, n_ant, gains=par[:, :, :, 0].astype(np.float32), solve=solve,
+                   max_iter=max_iter, tol=tol, chan_freq=freq)
+
+
+@pytest.mark.parametrize("n", [0, 1])
+@pytest.mark.parametrize("dekind", ["diag", "full"])
+def test_k_de_single_step_matches_oracle(n, dekind):
+    """The KdE chain: K (delay and phase per integration over every channel, direction-independent)
+    and dE (direction-dependent, over several channels), two directions; one step of either term."""
+    n_ant, n_time, n_chan, n_dir = 5, 4, 40, 2
+    P, rng = _problem(31, n_ant=n_ant, n_time=n_time, n_chan=n_chan, n_dir=n_dir)
+    kpar, ktm, kfm, freq = _delay(rng, n_ant, n_time, n_chan, nt=n_time)
+    kpar = kpar.astype(np.float32).astype(np.float64)
+    de = _params(rng, dekind, True, n_ant, n_dir, 2, 5).astype(np.complex64).astype(np.complex128)
+    dtm, dfm = _maps(n_time, n_chan, 2, 5)
+    ot = [_ok_delay(kpar, ktm, kfm, freq, n == 0), _oterm(dekind, True, dtm, dfm, de, n == 1)]
+    dd.solve_term(P, ot, n, damping_mode=0)
+    S = _solver(P)
+    gt = [_gk_delay(kpar, ktm, kfm, freq, n_ant, n == 0), _gterm(dekind, True, dtm, dfm, de, n_ant, n_dir, n == 1)]
+    S.solve(gt, damping_mode=qc.QC_DAMP_CONST, damping=1.0)
+    S.close()
+    if n == 0:
+        want, start = ot[0].params[:, :, :, 0], kpar[:, :, :, 0]
+        got = np.asarray(gt[0].gains, dtype=np.float64)
+    else:
+        want, start, got = ot[1].params, de, _gpu_params(gt[1], n_dir)
+    err = np.max(np.abs(got - want)) / max(np.max(np.abs(want - start)), 1e-30)
+    assert err < 2e-3, (n, err)
+
+
+def test_k_de_converged_matches_oracle():
+    """Noise-free KdE data; two epochs of K then dE from perturbed starts: chi^2 within 1e-5 and
+    K's delays and dE's referenced gains within 1e-4 of the oracle's."""
+    n_ant, n_time, n_chan, n_dir = 5, 2, 24, 2
+    rng = np.random.default_rng(41)
+    kpar, ktm, kfm, freq = _delay(rng, n_ant, n_time, n_chan, nt=n_time, spread=0.5)
+    de = _params(rng, "diag", True, n_ant, n_dir, 1, 2, spread=0.2)
+    dtm, dfm = _maps(n_time, n_chan, 1, 2)
+    truth = [_ok_delay(kpar, ktm, kfm, freq, False), _oterm("diag", True, dtm, dfm, de, False)]
+    P, _ = _problem(42, n_ant=n_ant, n_time=n_time, n_chan=n_chan, n_dir=n_dir, terms=truth, noise=0.0,
+                    flag_frac=0.05)
+    k0 = (kpar + 0.05 * rng.standard_normal(kpar.shape)).astype(np.float32).astype(np.float64)
+    d0 = de * (1 + 0.05 * rng.standard_normal(de.shape))
+    d0[..., 1] = d0[..., 2] = 0
+    d0 = d0.astype(np.complex64).astype(np.complex128)
+    ot = [_ok_delay(k0, ktm, kfm, freq, True, max_iter=20, tol=1e-7),
+          _oterm("diag", True, dtm, dfm, d0, True, max_iter=20, tol=1e-7)]
+    for _ in range(2):
+        dd.solve_term(P, ot, 0, damping_mode=1)
+        dd.solve_term(P, ot, 1, damping_mode=1)
+    ochi2, _ = dd.residual(P, ot)
+    S = _solver(P)
+    gt = [_gk_delay(k0, ktm, kfm, freq, n_ant, True, max_iter=20, tol=1e-7),
+          _gterm("diag", True, dtm, dfm, d0, n_ant, n_dir, True, max_iter=20, tol=1e-7)]
+    S.solve(gt, n_epochs=2)
+    gchi2 = S.residual(gt)
+    S.close()
+    scale = float(np.sum(P.weight * np.abs(P.data) ** 2))
+    assert abs(gchi2 - ochi2) <= max(CHI2_TOL * ochi2, 1e-9 * scale), (gchi2, ochi2)
+    kerr = np.max(np.abs(np.asarray(gt[0].gains, np.float64)[..., [1, 3]] - ot[0].params[:, :, :, 0][..., [1, 3]]))
+    assert kerr < 1e-3, kerr                         # delays (ns), whose scale is ~0.5
+    got, want = _ref_dd(_gpu_params(gt[1], n_dir)), _ref_dd(ot[1].params)
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < GAIN_TOL
+
+
 def test_one_direction_flagged_dd_equals_plain():
     """With n_dir = 1 a term marked direction-dependent is the plain term."""
     obs = synth.plain_small(seed=2, noise=0.01, n_time=8, n_chan=16)
@@ -197,6 +275,10 @@ def test_rejections():
     ph = qc.Term("phase", tm, fm, 1, 1, n_ant)
     with pytest.raises(qc.QCError) as e:
         S.solve([ph])
+    assert e.value.code == qc.QC_EUNSUPPORTED
+    kdd = qc.Term("delay", tm, fm, 1, 1, n_ant, chan_freq=np.linspace(1, 1.4, n_chan), dd=True, n_dir=n_dir)
+    with pytest.raises(qc.QCError) as e:
+        S.solve([kdd])
     assert e.value.code == qc.QC_EUNSUPPORTED
     # a solved direction-independent term to the right of a direction-dependent one
     left = _gterm("diag", True, tm, fm, _params(rng, "diag", True, n_ant, n_dir, 1, 1), n_ant, n_dir, False)

@@ -699,3 +699,111 @@ def make_pair_batches(shapes, noise: float = 0.01, device=None, noise_seed: int 
                              np.array([s_[3] for s_ in shapes], np.int32), np.array([s_[1] for s_ in shapes], np.int32),
                              truths, sus))
     return batches[0], batches[1]
+
+
+# ---------------------------------------------------------------------------
+# the KdE workload: two directions, a delay term K and a direction-dependent dE
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class KdESetup:
+    """Host-drawn part of the KdE workload (Section 5: K per integration over all channels; dE,
+    direction-dependent diagonal, over 16 integrations x 128 channels; two directions: the
+    field and one bright source away from it)."""
+    base: Setup                # array, rows, uvw, flagged rows, field sky (direction 0)
+    off: Sky                   # direction 1: the off-axis source
+    freqs_ghz: np.ndarray      # channel frequencies in GHz (the delay term's frequency axis)
+    k_truth: np.ndarray        # float [n_time][1][n_ant][4] (phi_X, tau_X ns, phi_Y, tau_Y ns)
+    k_tmap: np.ndarray
+    de_truth: np.ndarray       # complex [n_tint][n_fint][n_ant][2][4]
+    de_tmap: np.ndarray
+    de_fmap: np.ndarray
+
+
+def kde_setup(seed: int = 3, n_ant: int = 64, n_time: int = 300, n_chan: int = 512, n_src: int = 50,
+              flag_row_frac: float = 0.1, de_times: int = 16, de_chans: int = 128) -> KdESetup:
+    rng = np.random.default_rng(seed)
+    freqs = meerkat_band(n_chan)
+    ant_x = ew_array(n_ant, 8000.0, rng)
+    base = draw_setup(n_ant, n_time, freqs, [], n_src=n_src - 1, rng=rng, ant_x=ant_x, flag_row_frac=flag_row_frac)
+    # the off-axis source: 5 Jy at 1.5 degrees
+    ang = rng.uniform(0, 2 * np.pi)
+    l, m = np.deg2rad(1.5) * np.cos(ang), np.deg2rad(1.5) * np.sin(ang)
+    off = Sky(flux=np.array([5.0]), l=np.array([l]), m=np.array([m]))
+    k = np.zeros((n_time, 1, n_ant, 4))
+    k[..., 0] = rng.uniform(-np.pi, np.pi, (n_time, 1, n_ant))
+    k[..., 2] = rng.uniform(-np.pi, np.pi, (n_time, 1, n_ant))
+    tau = rng.normal(0.0, 1.0, (1, 1, n_ant, 2)) + 0.05 * np.cumsum(rng.normal(0, 1, (n_time, 1, n_ant, 2)), axis=0)
+    k[..., 1], k[..., 3] = tau[..., 0], tau[..., 1]
+    nt, nf = -(-n_time // de_times), -(-n_chan // de_chans)
+    de = np.zeros((nt, nf, n_ant, 2, 4), dtype=np.complex128)
+    amp = np.stack([1 + 0.02 * rng.standard_normal((nt, nf, n_ant, 2)),
+                    1 + 0.1 * rng.standard_normal((nt, nf, n_ant, 2))], axis=3)
+    ph = np.stack([0.05 * rng.standard_normal((nt, nf, n_ant, 2)),
+                   rng.uniform(-np.pi, np.pi, (nt, nf, n_ant, 2))], axis=3)
+    g = amp * np.exp(1j * ph)                                              # [nt, nf, ant, dir, corr]
+    de[..., 0], de[..., 3] = g[..., 0], g[..., 1]
+    return KdESetup(base, off, freqs / 1e9, k, interval_map(n_time, 1), de, interval_map(n_time, de_times),
+                    interval_map(n_chan, de_chans))
+
+
+def make_kde_device(ks: KdESetup, noise: float, noise_seed: int, device, rows_per_chunk: int = 2048):
+    """The KdE observation on a CUDA device: data complex64 [row][chan][4], model complex64
+    [row][chan][2][4] (direction 0: the field, 1: the off-axis source), float32 weights, uint8
+    flags.  data = sum_d K_p dE_{p,d} M_d dE_{q,d}^H K_q^H + noise (complex Gaussian, re and im
+    each N(0, noise^2))."""
+    import torch
+    su = ks.base
+    n_row, n_chan = su.ant1.size, su.freqs.size
+    dev = torch.device(device)
+    f64, c64 = torch.float64, torch.complex64
+    data = torch.empty((n_row, n_chan, 4), dtype=c64, device=dev)
+    model = torch.zeros((n_row, n_chan, 2, 4), dtype=c64, device=dev)
+    weight = torch.ones((n_row, n_chan, 4), dtype=torch.float32, device=dev)
+    flag = torch.from_numpy(np.repeat(su.flag_rows[:, None], n_chan, axis=1).astype(np.uint8)).to(dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(int(noise_seed))
+    k_nu = torch.from_numpy(-2.0 * np.pi * su.freqs / C_LIGHT).to(dev, f64)
+    skies = [su.sky, ks.off]
+    flux = [torch.from_numpy(s.flux).to(dev, torch.float32).to(c64) for s in skies]
+    lmn = [torch.from_numpy(np.stack([s.l, s.m, s.n - 1.0])).to(dev, f64) for s in skies]
+    nu = torch.from_numpy(ks.freqs_ghz).to(dev, f64)
+    kt = torch.from_numpy(ks.k_truth[:, 0]).to(dev, f64)                    # [time, ant, 4]
+    de = torch.from_numpy(ks.de_truth).to(dev, c64)                         # [nt, nf, ant, dir, 4]
+    de_t = torch.from_numpy(ks.de_tmap.astype(np.int64)).to(dev)
+    de_f = torch.from_numpy(ks.de_fmap.astype(np.int64)).to(dev)
+    two_pi = 2.0 * np.pi
+
+    def k_gain(t, a):                                                        # [R, C, 2] complex64
+        u = kt[t, a]                                                         # [R, 4]
+        px = u[:, 0:1] + two_pi * u[:, 1:2] * nu[None, :]
+        py = u[:, 2:3] + two_pi * u[:, 3:4] * nu[None, :]
+        return torch.stack([torch.polar(torch.ones_like(px), px), torch.polar(torch.ones_like(py), py)], -1).to(c64)
+
+    for r0 in range(0, n_row, rows_per_chunk):
+        r1 = min(n_row, r0 + rows_per_chunk)
+        uvw = torch.from_numpy(su.uvw[r0:r1]).to(dev, f64)
+        t = torch.from_numpy(su.time_idx[r0:r1].astype(np.int64)).to(dev)
+        a1 = torch.from_numpy(su.ant1[r0:r1].astype(np.int64)).to(dev)
+        a2 = torch.from_numpy(su.ant2[r0:r1].astype(np.int64)).to(dev)
+        kp, kq = k_gain(t, a1), k_gain(t, a2)
+        it = de_t[t][:, None]
+        jf = de_f[None, :]
+        V = torch.zeros((r1 - r0, n_chan, 2), dtype=c64, device=dev)        # parallel hands (diagonal chain)
+        for d in range(2):
+            ang = (uvw @ lmn[d])[:, :, None] * k_nu[None, None, :]
+            ang = (ang - two_pi * torch.round(ang / two_pi)).to(torch.float32)
+            scal = torch.einsum("k,rkc->rc", flux[d], torch.polar(torch.ones_like(ang), ang))
+            model[r0:r1, :, d, 0] = scal
+            model[r0:r1, :, d, 3] = scal
+            ep = de[it, jf, a1[:, None], d][..., [0, 3]]                        # [R, C, 2]
+            eq = de[it, jf, a2[:, None], d][..., [0, 3]]
+            V += (kp * ep) * scal[:, :, None] * (kq * eq).conj()
+        out = torch.zeros((r1 - r0, n_chan, 4), dtype=c64, device=dev)
+        out[..., 0], out[..., 3] = V[..., 0], V[..., 1]
+        if noise > 0:
+            nz = torch.randn((r1 - r0, n_chan, 4, 2), dtype=torch.float32, device=dev, generator=gen)
+            out = out + noise * torch.view_as_complex(nz)
+        data[r0:r1] = out
+    return dict(data=data, model=model, weight=weight, flag=flag, ant1=su.ant1, ant2=su.ant2,
+                time_idx=su.time_idx, n_ant=su.n_ant, n_time=su.n_time, n_chan=n_chan)

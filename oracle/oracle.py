@@ -51,7 +51,7 @@ class _Term(C.Structure):
 
 
 class _Opts(C.Structure):
-    _fields_ = [("n_epochs", C.c_int), ("damping_mode", C.c_int), ("damping", C.c_double)]
+    _fields_ = [("n_epochs", C.c_int), ("damping_mode", C.c_int), ("damping", C.c_double), ("div_flag", C.c_int)]
 
 
 def _load():
@@ -200,13 +200,14 @@ def normal_equations(problem: OracleProblem, terms: Sequence[OracleTerm], n: int
 
 
 def solve_term(problem: OracleProblem, terms: Sequence[OracleTerm], n: int, damping: float = 1.0,
-               damping_mode: int = 0) -> np.ndarray:
-    """Algorithm 1 for term n; gains updated in place; returns iterations per interval."""
+               damping_mode: int = 0, div_flag: bool = False) -> np.ndarray:
+    """Algorithm 1 for term n; gains updated in place; returns iterations per interval.
+    div_flag: flag (gain flag 2) and restore gains whose updates do not shrink (see oc_solve_term)."""
     lib = _load()
     T = terms[n]
     iters = np.zeros((T.n_tint, T.n_fint), dtype=np.int32)
     arr = _terms_array(terms)
-    opts = _Opts(1, damping_mode, damping)
+    opts = _Opts(1, damping_mode, damping, int(div_flag))
     rc = lib.oc_solve_term(C.addressof(problem._c), C.addressof(arr), len(terms), n, C.addressof(opts), _ptr(iters))
     if rc:
         raise RuntimeError(f"oc_solve_term failed: {rc}")
@@ -214,13 +215,13 @@ def solve_term(problem: OracleProblem, terms: Sequence[OracleTerm], n: int, damp
 
 
 def solve(problem: OracleProblem, terms: Sequence[OracleTerm], n_epochs: int = 1, damping: float = 1.0,
-          damping_mode: int = 0) -> List[np.ndarray]:
+          damping_mode: int = 0, div_flag: bool = False) -> List[np.ndarray]:
     """Chain schedule: epochs x terms x Algorithm 1.  Returns last-epoch iterations per term."""
     lib = _load()
     sizes = [t.n_tint * t.n_fint for t in terms]
     iters = np.zeros(sum(sizes), dtype=np.int32)
     arr = _terms_array(terms)
-    opts = _Opts(n_epochs, damping_mode, damping)
+    opts = _Opts(n_epochs, damping_mode, damping, int(div_flag))
     rc = lib.oc_solve(C.addressof(problem._c), C.addressof(arr), len(terms), C.addressof(opts), _ptr(iters))
     if rc:
         raise RuntimeError(f"oc_solve failed: {rc}")

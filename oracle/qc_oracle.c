@@ -83,6 +83,7 @@ typedef struct {
     int n_epochs;
     int damping_mode;            /* 0: constant alpha; 1: alternate 1, 1/2 */
     double damping;              /* alpha for mode 0 */
+    int div_flag;                /* 1: flag diverging gains (Section 4.3, "Gain flagging"; see oc_solve_term) */
 } oc_opts;
 
 /* ------------------------------------------------------------------------ */
@@ -361,6 +362,14 @@ static void term_gain_vec(const oc_term *T, size_t idx, cplx g[4])
  * Solve term n of the chain with Algorithm 1, every solution interval
  * independently (Section 2.3, last paragraph: solution intervals).  iters (nullable) receives
  * the iteration count per interval [n_tint*n_fint].
+ *
+ * Gain flagging on divergence (Section 4.3: a gain whose updates do not tend to zero), when
+ * o->div_flag is set, for diagonal, full and phase-only terms: the relative update of antenna
+ * a in an interval at iteration k is d_a(k) = ||g_a(k) - g_a(k-1)||_F / ||g_a(k)||_F.  An
+ * interval that ends at max_iter = K >= 4 without converging flags each antenna whose last two
+ * updates are not smaller than its first two, max(d_a(K-1), d_a(K)) >= max(d_a(1), d_a(2)) > 0
+ * (pairs, so that a period-2 oscillation and the alternating step length compare like with
+ * like): its gain flag becomes 2 and its gain is restored to its value before this solve.
  */
 int oc_solve_term(const oc_problem *P, oc_term *terms, int n_terms, int n, const oc_opts *o, int *iters)
 {
@@ -373,6 +382,20 @@ int oc_solve_term(const oc_problem *P, oc_term *terms, int n_terms, int n, const
     if (!jhj || !jhr || !active) { free(jhj); free(jhr); free(active); return OC_ENOMEM; }
     memset(active, 1, n_bins);
     if (iters) memset(iters, 0, sizeof(int) * n_bins);
+    /* divergence tracking: first and latest relative update per (interval, antenna), initial gains */
+    const int track = o && o->div_flag && T->type != OC_DELAY && T->max_iter >= 4;
+    const size_t pstride = T->type == OC_PHASE ? 2 : 8;
+    double *d_first = NULL, *d_last = NULL, *p0 = NULL;
+    if (track) {
+        d_first = calloc(n_bins * na, sizeof(double));
+        d_last = calloc(n_bins * na, sizeof(double));
+        p0 = malloc(sizeof(double) * n_bins * na * pstride);
+        if (!d_first || !d_last || !p0) {
+            free(jhj); free(jhr); free(active); free(d_first); free(d_last); free(p0);
+            return OC_ENOMEM;
+        }
+        memcpy(p0, T->params, sizeof(double) * n_bins * na * pstride);
+    }
 
     for (int k = 1; k <= T->max_iter; ++k) {
         int any = 0;
@@ -425,9 +448,17 @@ int oc_solve_term(const oc_problem *P, oc_term *terms, int n_terms, int n, const
                     }
                 }
                 term_gain_vec(T, idx, g_new);
+                double na_ = 0, da_ = 0;
                 for (int e = 0; e < 4; ++e) {
-                    num += creal((g_new[e] - g_old[e]) * conj(g_new[e] - g_old[e]));
-                    den += creal(g_new[e] * conj(g_new[e]));
+                    na_ += creal((g_new[e] - g_old[e]) * conj(g_new[e] - g_old[e]));
+                    da_ += creal(g_new[e] * conj(g_new[e]));
+                }
+                num += na_;
+                den += da_;
+                if (track) {
+                    const double da = da_ > 0 ? sqrt(na_ / da_) : 0.0;
+                    if (k <= 2) d_first[idx] = fmax(d_first[idx], da);       /* max(d(1), d(2)) */
+                    if (k >= T->max_iter - 1) d_last[idx] = fmax(d_last[idx], da); /* max(d(K-1), d(K)) */
                 }
             }
             if (iters) iters[b] = k;
@@ -435,7 +466,20 @@ int oc_solve_term(const oc_problem *P, oc_term *terms, int n_terms, int n, const
             if (delta < T->tol) active[b] = 0;
         }
     }
-    free(jhj); free(jhr); free(active);
+    if (track) {
+        /* intervals still active ran to max_iter without converging */
+        for (size_t b = 0; b < n_bins; ++b) {
+            if (!active[b]) continue;
+            for (int a = 0; a < na; ++a) {
+                const size_t idx = b * na + a;
+                if (d_first[idx] > 0 && d_last[idx] >= d_first[idx]) {
+                    memcpy(T->params + pstride * idx, p0 + pstride * idx, sizeof(double) * pstride);
+                    if (T->gain_flags) T->gain_flags[idx] = 2;
+                }
+            }
+        }
+    }
+    free(jhj); free(jhr); free(active); free(d_first); free(d_last); free(p0);
     return OC_OK;
 }
 

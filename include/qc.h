@@ -199,7 +199,32 @@ typedef struct {
                                   kernel under them. */
     qc_allreduce_fn allreduce; /* required when a solved term has reduce = 1       */
     void *allreduce_user;
+    int32_t div_flag;          /* 1 = flag diverging gains (see below)              */
+    int32_t robust;            /* 1 = robust reweighting between epochs (below)     */
+    double robust_nu;          /* its degrees of freedom nu (> 0; 0 -> 5)           */
 } qc_opts;
+
+/*
+ * Gain flagging on divergence (Section 4.3, "Gain flagging": gains whose updates
+ * do not tend to zero), opt-in with qc_opts.div_flag, for diagonal, full and
+ * phase-only terms solved with max_iter = K >= 4: the relative update of antenna
+ * a in an interval at iteration k is d_a(k) = ||g_a(k) - g_a(k-1)||_F / ||g_a(k)||_F
+ * (FP64).  An interval that ends at K without converging flags every antenna with
+ * max(d_a(K-1), d_a(K)) >= 0.9 max(d_a(1), d_a(2)) > 0 (its updates have not shrunk
+ * by more than a tenth): its gain flag becomes 2 and its gain is restored to its
+ * value before that term's solve in this epoch.
+ *
+ * Robust reweighting (Section 4.3, "Robust reweighting", after Sob et al. 2020),
+ * opt-in with qc_opts.robust and n_epochs >= 2: the noise is read as complex
+ * Student's t with nu degrees of freedom, a scale mixture of complex Gaussians,
+ * and between epochs one expectation-maximisation step reweights every sample s
+ * from the residual r of the current chain: z_s = sum_c w_c |r_c|^2 over its k_s
+ * correlations with w_c > 0 (w the caller's weights, flags applied),
+ * sigma^2 = sum_s lambda_s z_s / sum_s k_s (previous factors; 1 at first),
+ * lambda_s = (nu + 2 k_s) / (nu + 2 z_s / sigma^2), and the next epoch solves with
+ * weights w_c lambda_s.  The caller's weights are unchanged on return;
+ * chi2_before / chi2_after use them.
+ */
 
 typedef struct {
     double chi2_before, chi2_after;   /* Eq. min, FP64 sums (when want_chi2)           */

@@ -342,6 +342,9 @@ int oc_block_solve(int n, const cplx *A_in, const cplx *b, cplx *x)
 /* Algorithm 1 for one term, then the chain schedule over epochs              */
 /* ------------------------------------------------------------------------ */
 
+/* gain flagging on divergence: last two updates against the first two (see oc_solve_term) */
+#define DIV_RATIO 0.9
+
 static double step_length(const oc_opts *o, int k /* 1-based iteration */)
 {
     if (o && o->damping_mode == 1) return (k % 2 == 0) ? 0.5 : 1.0;
@@ -367,9 +370,11 @@ static void term_gain_vec(const oc_term *T, size_t idx, cplx g[4])
  * o->div_flag is set, for diagonal, full and phase-only terms: the relative update of antenna
  * a in an interval at iteration k is d_a(k) = ||g_a(k) - g_a(k-1)||_F / ||g_a(k)||_F.  An
  * interval that ends at max_iter = K >= 4 without converging flags each antenna whose last two
- * updates are not smaller than its first two, max(d_a(K-1), d_a(K)) >= max(d_a(1), d_a(2)) > 0
- * (pairs, so that a period-2 oscillation and the alternating step length compare like with
- * like): its gain flag becomes 2 and its gain is restored to its value before this solve.
+ * updates have not shrunk by more than a tenth from its first two,
+ * max(d_a(K-1), d_a(K)) >= 0.9 max(d_a(1), d_a(2)) > 0 (pairs, so that a period-2 oscillation
+ * and the alternating step length compare like with like; the margin keeps an exact
+ * oscillation from being decided by rounding): its gain flag becomes 2 and its gain is
+ * restored to its value before this solve.
  */
 int oc_solve_term(const oc_problem *P, oc_term *terms, int n_terms, int n, const oc_opts *o, int *iters)
 {
@@ -472,7 +477,7 @@ int oc_solve_term(const oc_problem *P, oc_term *terms, int n_terms, int n, const
             if (!active[b]) continue;
             for (int a = 0; a < na; ++a) {
                 const size_t idx = b * na + a;
-                if (d_first[idx] > 0 && d_last[idx] >= d_first[idx]) {
+                if (d_first[idx] > 0 && d_last[idx] >= DIV_RATIO * d_first[idx]) {
                     memcpy(T->params + pstride * idx, p0 + pstride * idx, sizeof(double) * pstride);
                     if (T->gain_flags) T->gain_flags[idx] = 2;
                 }

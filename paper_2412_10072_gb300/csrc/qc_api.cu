@@ -595,9 +595,9 @@ Data qc_ctx::data_desc() const
     D.n_chan = n_chan;
     D.vis = d_vis;
     D.model = d_model;
+    D.weight = d_weight_use ? d_weight_use : d_weight;
     D.model16 = d_model16;
     D.bl_scale = d_bl_scale;
-    D.weight = d_weight;
     D.flag = d_flag;
     D.rows = d_rows;
     D.strip_rows = d_strip_rows;
@@ -873,6 +873,37 @@ extern "C" int qc_solve(qc_ctx *c, qc_term *terms, int32_t n_terms, const qc_opt
         B.graph_valid = false;
     }
 
+    // robust reweighting between epochs: every kernel reads the context's folded weight copy,
+    // reweighted in place; the weights before reweighting are kept and put back on return
+    const bool robust = o->robust && o->n_epochs > 1;
+    const double nu = o->robust_nu > 0 ? o->robust_nu : 5.0;
+    const size_t n_vis = (size_t)c->n_row * c->n_chan;
+    struct RobustGuard {
+        qc_ctx *c = nullptr;
+        cudaStream_t st = nullptr;
+        size_t bytes = 0;
+        ~RobustGuard()
+        {
+            if (!c) return;
+            cudaMemcpyAsync(const_cast<float4 *>(c->d_wf), c->rob_w0.ptr, bytes, cudaMemcpyDeviceToDevice, st);
+            c->d_weight_use = nullptr;
+        }
+    } guard;
+    if (robust && n_vis) {
+        if (!std::isfinite(nu)) return c->fail(QC_EINVAL, "robust_nu must be finite");
+        if ((rc = c->ensure(c->rob_w0, nbytes<float4>(n_vis)))) return rc;
+        if ((rc = c->ensure(c->rob_lam, nbytes<float>(n_vis)))) return rc;
+        if ((rc = c->ensure(c->rob_res, nbytes<float4>(2 * n_vis)))) return rc;
+        if ((rc = c->ensure(c->rob_sums, nbytes<double>(4)))) return rc;
+        CK(cudaMemcpyAsync(c->rob_w0.ptr, c->d_wf, nbytes<float4>(n_vis), cudaMemcpyDeviceToDevice, st));
+        robust_fill_kernel<<<grid_for((long)n_vis, 256, c->sm_count), 256, 0, st>>>((long)n_vis, (float *)c->rob_lam.ptr,
+                                                                                     1.f);
+        CK(cudaGetLastError());
+        guard.c = c;
+        guard.st = st;
+        guard.bytes = nbytes<float4>(n_vis);
+        c->d_weight_use = c->d_wf;
+    }
     int n_iter_max = 0;
     for (int epoch = 0; epoch < o->n_epochs; ++epoch) {
         for (int n = 0; n < n_terms; ++n) {
@@ -885,6 +916,27 @@ extern "C" int qc_solve(qc_ctx *c, qc_term *terms, int32_t n_terms, const qc_opt
             S.acc_launches += acc_launches;
             if (epoch == o->n_epochs - 1) n_iter_max = std::max(n_iter_max, it_max);
         }
+        if (guard.c && epoch < o->n_epochs - 1) {
+            // one EM step on the residual of the current chain (whitened by the original weights)
+            double *sums = (double *)c->rob_sums.ptr;
+            if ((rc = c->run_residual(chain, (float4 *)c->rob_res.ptr, sums + 2, st))) return rc;
+            CK(cudaMemsetAsync(sums, 0, 2 * sizeof(double), st));
+            const int g = grid_for((long)n_vis, 256, c->sm_count);
+            robust_sum_kernel<<<g, 256, 0, st>>>((long)n_vis, (const float4 *)c->rob_res.ptr,
+                                                 (const float4 *)c->rob_w0.ptr, (const float *)c->rob_lam.ptr, sums);
+            robust_apply_kernel<<<g, 256, 0, st>>>((long)n_vis, (const float4 *)c->rob_res.ptr,
+                                                   (const float4 *)c->rob_w0.ptr, (float *)c->rob_lam.ptr,
+                                                   const_cast<float4 *>(c->d_wf), sums, nu);
+            CK(cudaGetLastError());
+            c->launches += 3;
+        }
+    }
+    if (guard.c) {
+        // the caller's weights again for chi2_after and for later calls
+        CK(cudaMemcpyAsync(const_cast<float4 *>(c->d_wf), c->rob_w0.ptr, nbytes<float4>(n_vis),
+                           cudaMemcpyDeviceToDevice, st));
+        c->d_weight_use = nullptr;
+        guard.c = nullptr;
     }
     if (o->want_chi2) {
         if ((rc = c->run_residual(chain, nullptr, d_chi2, st))) return rc;
@@ -1293,6 +1345,19 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
     ua.vis_iters = (unsigned long long *)scalars.ptr;
     ua.acc_bytes = (unsigned long long *)scalars.ptr + 1;
     ua.tol = t.tol;
+    // gain flagging on divergence: first / last relative updates and the parameters before the solve
+    ua.div = (o->div_flag && !delay[n] && t.max_iter >= 4) ? 1 : 0;
+    ua.max_iter = t.max_iter;
+    ua.div_stats = nullptr;
+    ua.params0 = nullptr;
+    const size_t pbytes = nbytes<double>((size_t)nb * nat * (t.type == 2 ? 2 : 8));
+    if (ua.div) {
+        int rc_;
+        if ((rc_ = ensure(B.div, nbytes<double>((size_t)nb * nat * 2)))) return rc_;
+        if ((rc_ = ensure(B.params0, pbytes))) return rc_;
+        ua.div_stats = (double *)B.div.ptr;
+        ua.params0 = (const double *)B.params0.ptr;
+    }
     int *cnt = (int *)B.cnt.ptr;
     const int upd_block = nat >= 128 ? 128 : (nat > 32 ? 64 : 32);
     // delay terms: the update reduces the channel bins of each parameter interval
@@ -1321,6 +1386,10 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
         init_term_kernel<<<(std::max(nb, max_iter + 1) + 255) / 256, 256, 0, st>>>(nb, (uint8_t *)B.active.ptr, cnt,
                                                                                    max_iter + 1);
         CK(cudaGetLastError());
+        if (ua.div) {
+            CK(cudaMemsetAsync(B.div.ptr, 0, nbytes<double>((size_t)nb * nat * 2), st));
+            CK(cudaMemcpyAsync(B.params0.ptr, B.params.ptr, pbytes, cudaMemcpyDeviceToDevice, st));
+        }
         for (int k = 1; k <= max_iter; ++k) {
             aa.n_active = cnt + (k - 1);
             // inside a capture the record must be an external event node to be timed on replay

@@ -10,6 +10,7 @@
 #include "qc_delay.cuh"
 #include "qc_stream_delay.cuh"
 #include "qc_ws.cuh"
+#include "qc_robust.cuh"
 
 // Every device allocation of the library goes through these two calls.  They count the
 // live allocations and honour the test hook of qc_test_fail_alloc (qc.h), so that tests can
@@ -71,6 +72,8 @@ struct TermBufs {
     Buf ws_rlb;    //   uint32 [n_row][words] their active-chunk bits
     Buf ws_n;      //   int: number of listed rows
     Buf ws_sb;     // warp-specialised kernel, strip tiles: uint32 [n_chunks][words] active-entry bits
+    Buf div;       // divergence flagging: double [bins][ant][2] first / last relative updates
+    Buf params0;   // divergence flagging: the FP64 parameters before the solve
     Buf dfmap;     // delay terms: int [n_chan] parameter interval of each channel
     Buf dfr;       // delay terms: int2 [n_fint] first and last channel of each interval
     Buf dnu;       // delay terms: double [n_chan] channel frequencies
@@ -132,6 +135,11 @@ struct qc_ctx {
     int *d_strip_rows = nullptr, *d_strip_off = nullptr;
     uint8_t *d_row_live = nullptr;    // [n_row]
     const float4 *d_wf = nullptr;     // [n_row][n_chan] weights with flags folded in (streaming kernel)
+    const float4 *d_weight_use = nullptr;   // robust reweighting: the weights every kernel reads (d_wf)
+    Buf rob_w0;                       // robust reweighting: the folded weights before reweighting
+    Buf rob_lam;                      //   float [n_row][n_chan] factors of the last reweighting
+    Buf rob_res;                      //   residual of the current chain
+    Buf rob_sums;                     //   double [4]: M-step sums, chi^2 scratch
     int *d_err = nullptr;             // device error flag of bounded waits
     std::vector<void *> owned;
     std::vector<cudaEvent_t> events;

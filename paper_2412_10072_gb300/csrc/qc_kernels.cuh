@@ -724,6 +724,11 @@ struct UpdArgs {
     unsigned long long *vis_iters, *acc_bytes;
     int k;                   // iteration (1-based)
     double alpha, tol;
+    // gain flagging on divergence (div != 0; max_iter >= 4): per (bin, antenna) the larger of the
+    // first two and of the last two relative updates, and the parameters before the solve
+    int div, max_iter;
+    double *div_stats;       // [n_bins][n_ant][2], zero before the first iteration
+    const double *params0;   // as params
 };
 
 __device__ __forceinline__ void store_jones_tab(const UpdArgs &u, int bin, int ant, const double2 g[4])
@@ -813,15 +818,25 @@ static __global__ void __launch_bounds__(128) update_kernel(const UpdArgs u)
         }
         if (u.gain_flags) u.gain_flags[pidx] = (int8_t)singular;
         store_jones_tab(u, bin, ant, gnew);
+        double na = 0, da = 0;
         for (int e = 0; e < 4; ++e) {
             const double dx = gnew[e].x - gold[e].x, dy = gnew[e].y - gold[e].y;
-            num += dx * dx + dy * dy;
-            den += gnew[e].x * gnew[e].x + gnew[e].y * gnew[e].y;
+            na += dx * dx + dy * dy;
+            da += gnew[e].x * gnew[e].x + gnew[e].y * gnew[e].y;
+        }
+        num += na;
+        den += da;
+        if (u.div) {
+            const double d = da > 0 ? sqrt(na / da) : 0.0;
+            double *ds = u.div_stats + 2 * pidx;
+            if (u.k <= 2) ds[0] = fmax(ds[0], d);
+            if (u.k >= u.max_iter - 1) ds[1] = fmax(ds[1], d);
         }
         for (int i = 0; i < KG; ++i) A[i] = 0.0;
     }
     // interval norms: block reduction in FP64
     __shared__ double s_num[4], s_den[4];
+    __shared__ int s_unconverged;
     for (int d = 16; d > 0; d >>= 1) {
         num += __shfl_down_sync(0xffffffffu, num, d);
         den += __shfl_down_sync(0xffffffffu, den, d);
@@ -838,6 +853,37 @@ static __global__ void __launch_bounds__(128) update_kernel(const UpdArgs u)
         atomicAdd(u.acc_bytes, (unsigned long long)u.bin_nbytes[bin]);
         if (delta < u.tol) u.active[bin] = 0;
         else atomicAdd(u.n_active_next, 1);
+        s_unconverged = delta >= u.tol;
+    }
+    if (u.div && u.k == u.max_iter) {
+        // the interval ends here: unconverged, it flags and restores the antennas whose last
+        // two updates have not shrunk by more than a tenth from their first two
+        __syncthreads();
+        if (s_unconverged) {
+            for (int ant = threadIdx.x; ant < u.n_ant; ant += blockDim.x) {
+                const size_t pidx = (size_t)bin * u.n_ant + ant;
+                const double *ds = u.div_stats + 2 * pidx;
+                if (!(ds[0] > 0 && ds[1] >= 0.9 * ds[0])) continue;
+                double2 g0[4];
+                if (u.type == 2) {
+                    const double *phi0 = u.params0 + 2 * pidx;
+                    double *phi = u.params + 2 * pidx;
+                    for (int e = 0; e < 2; ++e) phi[e] = phi0[e];
+                    double sn, cs;
+                    sincos(phi0[0], &sn, &cs);
+                    g0[0] = make_double2(cs, sn);
+                    sincos(phi0[1], &sn, &cs);
+                    g0[3] = make_double2(cs, sn);
+                    g0[1] = g0[2] = make_double2(0, 0);
+                } else {
+                    const double2 *P0 = reinterpret_cast<const double2 *>(u.params0) + 4 * pidx;
+                    double2 *P = reinterpret_cast<double2 *>(u.params) + 4 * pidx;
+                    for (int e = 0; e < 4; ++e) { g0[e] = P0[e]; P[e] = P0[e]; }
+                }
+                store_jones_tab(u, bin, ant, g0);
+                if (u.gain_flags) u.gain_flags[pidx] = 2;
+            }
+        }
     }
 }
 

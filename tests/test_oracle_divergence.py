@@ -1,7 +1,7 @@
 """Pins of gain flagging on divergence (Section 4.3, "Gain flagging": gains whose updates do not
 tend to zero), as the oracle reads it: an interval that ends at max_iter = K >= 4 without
 converging flags (gain flag 2) and restores every antenna with
-max(d(K-1), d(K)) >= max(d(1), d(2)) > 0, d(k) its relative update at iteration k.
+max(d(K-1), d(K)) >= 0.9 max(d(1), d(2)) > 0, d(k) its relative update at iteration k.
 
 The planted divergence is an interval left with a single usable baseline (p, q), solved with
 the undamped step of Algorithm 1 (alpha = 1): the product g_p conj(g_q) is fixed by the data

@@ -452,6 +452,13 @@ typedef struct {
      * sums), or is not finite, restarts from fallback_gains.                       */
     const void *fallback_gains;  /* [sum n_ant][2] complex64                           */
     const double *fallback_chi2; /* [n_prob] chi^2 at fallback_gains                  */
+    /* Size classes: with split > 0 the problems with fewer than `split` samples
+     * (rows x channels) form a second class, launched concurrently with its own CTA
+     * size (the tile: small_threads consecutive samples per CTA step) and residency
+     * (LPT schedule for both).  split = 0: tuned, else one class; split < 0: one class. */
+    int64_t split;
+    int32_t small_threads;       /* threads per CTA of the small class (0: tuned or 64)   */
+    int32_t small_ctas_per_sm;   /* its resident CTAs per SM (0: tuned or occupancy)      */
 } qc_batch_opts;
 
 typedef struct {
@@ -463,6 +470,8 @@ typedef struct {
     int32_t threads, ctas_per_sm, schedule, grid;   /* launch configuration used          */
     int32_t depth;
     int32_t n_fallback;          /* problems restarted from the fallback gains           */
+    int64_t split;               /* size threshold used (<= 0: one class)                 */
+    int32_t small_threads, small_ctas_per_sm, small_grid, n_small;   /* the small class   */
 } qc_batch_stats;
 
 /* Validate and stage a batch (host arrays copied, device arrays borrowed). */
@@ -503,13 +512,19 @@ int qc_batch_solve_moments(qc_batch *b, void *gains, int8_t *gain_flags, int32_t
 
 /*
  * Autotuner: time the batch solve (from unit gains, `base` options, results
- * discarded) for every candidate launch shape -- threads per CTA in
- * {128, 256, 512} (the warps that share one problem), copy stages per warp
- * in {3, 4, 6}, resident CTAs per SM in {1, 2, 4} (as shared memory allows),
- * schedule in {LPT, static} -- and keep the fastest for later solves with QC_SCHED_AUTO /
- * threads = 0.  Results are cached per shape class of the batch (problem
- * count and size histogram).  best (nullable) receives the chosen shape and
- * its time; `n_tried` (nullable) the number of candidates timed.
+ * discarded) for candidate launch shapes and keep the fastest for later solves
+ * that leave the shape to it (threads / ctas_per_sm / depth / split /
+ * small_* = 0, schedule QC_SCHED_AUTO).  Stage 1, one class: threads per CTA
+ * in {128, 256, 512} (the tile: that many consecutive samples per CTA step,
+ * threads / n_chan baselines x n_chan channels), copy stages per warp in
+ * {3, 4, 6}, resident CTAs per SM in {1, 2, 4} (as shared memory allows),
+ * schedule in {LPT, static}.  Stage 2, with the best stage-1 shape for the
+ * large problems: a size threshold in {2^10, 2^12, 2^14, 2^16} samples below
+ * which problems go to a concurrent class of small CTAs, threads in {64, 128}
+ * and {4, 8} per SM.  Results are cached for the process per device and shape
+ * class of the batch (problem count, FP16 model, log2 size histogram): another
+ * batch of the same class uses them without tuning.  best (nullable) receives
+ * the chosen shape and its time; `n_tried` (nullable) the candidates timed.
  */
 int qc_batch_autotune(qc_batch *b, const qc_batch_opts *base, qc_batch_stats *best, int32_t *n_tried);
 

@@ -17,6 +17,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -980,12 +981,18 @@ struct qc_batch {
     unsigned long long *counters = nullptr;
     void *gstage = nullptr;       // device staging for host gains/flags/iters
     std::vector<BProb> hprobs;
+    std::vector<long long> lpt_samples;   // samples of the problems in LPT order (non-increasing)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    struct Shape { int threads, per_sm, schedule, depth; double ms; };
-    std::map<std::string, Shape> tuned;
+    cudaStream_t aux_stream = nullptr;    // the small-problem class's launch
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // A launch shape: CTA size, residency, schedule, copy depth; with split > 0 the problems
+    // with fewer samples than split form a second class launched concurrently with its own
+    // CTA size and residency (tile = threads consecutive samples per CTA step).
+    struct Shape { int threads, per_sm, schedule, depth; double ms; long long split; int s_threads, s_per_sm; };
     std::string shape_key;
     struct GraphKey { int threads, per_sm, schedule, depth, max_iter, damping_mode; double damping, tol; bool m16;
-                      void *gains; void *flags; void *iters; cudaStream_t st; const void *fb_gains, *fb_chi2; };
+                      void *gains; void *flags; void *iters; cudaStream_t st; const void *fb_gains, *fb_chi2;
+                      long long split; int s_threads, s_per_sm; };
     cudaGraphExec_t exec = nullptr;
     GraphKey gkey;
     std::string err;
@@ -997,6 +1004,9 @@ struct qc_batch {
         for (void *p : owned) qc_dev_free(p);
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
+        if (aux_stream) cudaStreamDestroy(aux_stream);
         if (own_stream) cudaStreamDestroy(own_stream);
     }
     void *alloc(size_t bytes, cudaError_t *e)
@@ -1067,6 +1077,9 @@ extern "C" int qc_batch_create(const qc_batch_problem *p, qc_batch **out)
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->own_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->aux_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming);
     if (e != cudaSuccess) { g_batch_create_error = std::string("CUDA init: ") + cudaGetErrorString(e); return QC_ECUDA; }
     cudaStream_t st = b->own_stream;
 #define BALLOC(dst, T, n)                                                                    \
@@ -1184,7 +1197,10 @@ extern "C" int qc_batch_create(const qc_batch_problem *p, qc_batch **out)
     });
     BALLOC(b->order_lpt, int, p->n_prob);
     BALLOC(b->order_idx, int, p->n_prob);
-    BALLOC(b->queue, int, 1);
+    BALLOC(b->queue, int, 2);                  // work counters of the two size classes
+    b->lpt_samples.resize(p->n_prob);
+    for (int i = 0; i < p->n_prob; ++i)
+        b->lpt_samples[i] = (long long)b->hprobs[lpt[i]].n_rows * b->hprobs[lpt[i]].n_chan;
     BH2D(b->order_lpt, lpt.data(), sizeof(int) * p->n_prob);
     BH2D(b->order_idx, idx.data(), sizeof(int) * p->n_prob);
     BALLOC(b->gstage, unsigned char, (size_t)b->total_ant * 17 + sizeof(int) * p->n_prob + 64);
@@ -1246,47 +1262,108 @@ static const void *batch_fn(bool m16, int depth)
          : depth == 4 ? (const void *)batch_kernel<false, 4> : (const void *)batch_kernel<false, 6>;
 }
 
-// Enqueue one solve (work-counter reset + persistent kernel) on stream st.
-static int batch_enqueue(qc_batch *b, const BatchArgs &a, int threads, int depth, int grid, cudaStream_t st)
+// Tuned launch shapes, per device and shape class (problem count and size histogram),
+// shared by every batch of the process.
+static std::mutex g_tune_mutex;
+static std::map<std::string, qc_batch::Shape> g_tuned;
+
+static std::string tune_key(const qc_batch *b) { return std::to_string(b->dev) + "/" + b->shape_key; }
+
+static bool tuned_shape(const qc_batch *b, qc_batch::Shape &out)
 {
-    BCK(cudaMemsetAsync(b->queue, 0, sizeof(int), st));
-    const size_t smem = batch_smem(b, threads, depth);
-    void *args[] = { (void *)&a };
-    BCK(cudaLaunchKernel(batch_fn(b->m16, depth), dim3(grid), dim3(threads), args, smem, st));
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tuned.find(tune_key(b));
+    if (it == g_tuned.end()) return false;
+    out = it->second;
+    return true;
+}
+
+// One class of problems for a launch: a slice of a schedule order and its work counter.
+struct LaunchClass { const int *order; int n; int *queue; int threads, per_sm, depth, schedule, grid; };
+
+// Enqueue one solve on stream st: the work counters' reset and the persistent kernel of each
+// class; a second class runs on the auxiliary stream, forked from and joined into st.
+static int batch_enqueue(qc_batch *b, const BatchArgs &base, const LaunchClass *cls, int n_cls, cudaStream_t st)
+{
+    BCK(cudaMemsetAsync(b->queue, 0, 2 * sizeof(int), st));
+    if (n_cls > 1) {
+        BCK(cudaEventRecord(b->ev_fork, st));
+        BCK(cudaStreamWaitEvent(b->aux_stream, b->ev_fork, 0));
+    }
+    for (int c = 0; c < n_cls; ++c) {
+        const LaunchClass &L = cls[c];
+        if (L.n <= 0) continue;
+        BatchArgs a = base;
+        a.order = L.order;
+        a.n_prob = L.n;
+        a.queue = L.queue;
+        a.schedule = L.schedule;
+        const size_t smem = batch_smem(b, L.threads, L.depth);
+        void *args[] = { (void *)&a };
+        BCK(cudaLaunchKernel(batch_fn(b->m16, L.depth), dim3(L.grid), dim3(L.threads), args, smem,
+                             c == 0 ? st : b->aux_stream));
+    }
+    if (n_cls > 1) {
+        BCK(cudaEventRecord(b->ev_join, b->aux_stream));
+        BCK(cudaStreamWaitEvent(st, b->ev_join, 0));
+    }
     return QC_OK;
 }
 
-static int launch_shape(qc_batch *b, const qc_batch_opts *o, int &threads, int &per_sm, int &schedule, int &depth)
+// Check one CTA shape and clamp its residency to what fits on an SM (the kernel's dynamic
+// shared-memory limit is raised to the per-CTA maximum once, so shapes of both classes fit).
+static int check_shape(qc_batch *b, int threads, int depth, int &per_sm)
 {
-    threads = o->threads;
-    per_sm = o->ctas_per_sm;
-    schedule = o->schedule;
-    depth = o->depth;
-    auto it = b->tuned.find(b->shape_key);
-    if (it != b->tuned.end()) {
-        if (threads == 0) threads = it->second.threads;
-        if (per_sm == 0) per_sm = it->second.per_sm;
-        if (schedule == QC_SCHED_AUTO) schedule = it->second.schedule;
-        if (depth == 0) depth = it->second.depth;
-    }
-    if (threads == 0) threads = 256;
-    if (depth == 0) depth = 4;
-    if (schedule == QC_SCHED_AUTO) schedule = QC_SCHED_LPT;
     if (threads < 64 || threads > 512 || threads % 32) return b->fail(QC_EINVAL, "threads must be 64..512, multiple of 32");
     if (depth != 3 && depth != 4 && depth != 6) return b->fail(QC_EINVAL, "depth must be 3, 4 or 6");
     const size_t smem = batch_smem(b, threads, depth);
     int max_smem = 0;
     cudaError_t e = cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->dev);
     if (e != cudaSuccess) return b->cuda_fail(e, "cudaDeviceGetAttribute");
-    if (smem + 2 * 32 * sizeof(double) + 64 > (size_t)max_smem)
+    const size_t static_smem = 2 * 32 * sizeof(double) + 64;
+    if (smem + static_smem > (size_t)max_smem)
         return b->fail(QC_EUNSUPPORTED, "batch kernel shared memory exceeds the per-CTA limit for this shape");
-    e = cudaFuncSetAttribute(batch_fn(b->m16, depth), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(batch_fn(b->m16, depth), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             max_smem - (int)static_smem);
     if (e != cudaSuccess) return b->cuda_fail(e, "cudaFuncSetAttribute");
     int occ = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_fn(b->m16, depth), threads, smem);
     if (e != cudaSuccess) return b->cuda_fail(e, "occupancy");
     if (occ < 1) return b->fail(QC_EUNSUPPORTED, "batch kernel does not fit on an SM with this shape");
     if (per_sm <= 0 || per_sm > occ) per_sm = std::min(occ, per_sm <= 0 ? occ : per_sm);
+    return QC_OK;
+}
+
+static int launch_shape(qc_batch *b, const qc_batch_opts *o, qc_batch::Shape &sh)
+{
+    sh.threads = o->threads;
+    sh.per_sm = o->ctas_per_sm;
+    sh.schedule = o->schedule;
+    sh.depth = o->depth;
+    sh.split = o->split;
+    sh.s_threads = o->small_threads;
+    sh.s_per_sm = o->small_ctas_per_sm;
+    qc_batch::Shape t;
+    if (tuned_shape(b, t)) {
+        if (sh.threads == 0) sh.threads = t.threads;
+        if (sh.per_sm == 0) sh.per_sm = t.per_sm;
+        if (sh.schedule == QC_SCHED_AUTO) sh.schedule = t.schedule;
+        if (sh.depth == 0) sh.depth = t.depth;
+        if (sh.split == 0) sh.split = t.split;
+        if (sh.s_threads == 0) sh.s_threads = t.s_threads;
+        if (sh.s_per_sm == 0) sh.s_per_sm = t.s_per_sm;
+    }
+    if (sh.threads == 0) sh.threads = 256;
+    if (sh.depth == 0) sh.depth = 4;
+    if (sh.schedule == QC_SCHED_AUTO) sh.schedule = QC_SCHED_LPT;
+    if (sh.split < 0) sh.split = 0;
+    if (sh.s_threads == 0) sh.s_threads = 64;
+    int rc = check_shape(b, sh.threads, sh.depth, sh.per_sm);
+    if (rc) return rc;
+    if (sh.split > 0) {
+        if (sh.schedule != QC_SCHED_LPT) return b->fail(QC_EINVAL, "a size split takes the LPT schedule");
+        if ((rc = check_shape(b, sh.s_threads, sh.depth, sh.s_per_sm))) return rc;
+    }
     return QC_OK;
 }
 
@@ -1301,9 +1378,23 @@ static int batch_solve_impl(qc_batch *b, void *gains, int8_t *gain_flags, int32_
         return b->fail(QC_EINVAL, "fallback_gains and fallback_chi2 go together");
     if (o->fallback_gains && mem != QC_MEM_DEVICE) return b->fail(QC_EINVAL, "a fallback start needs device gains");
     if (o->damping_mode != QC_DAMP_CONST && o->damping_mode != QC_DAMP_ALTERNATE) return b->fail(QC_EINVAL, "damping_mode");
-    int threads, per_sm, schedule, depth, rc;
-    if ((rc = launch_shape(b, o, threads, per_sm, schedule, depth))) return rc;
+    qc_batch::Shape sh;
+    int rc;
+    if ((rc = launch_shape(b, o, sh))) return rc;
+    const int threads = sh.threads, per_sm = sh.per_sm, schedule = sh.schedule, depth = sh.depth;
     cudaStream_t st = o->stream ? (cudaStream_t)o->stream : b->own_stream;
+    // size classes: the LPT order is by non-increasing samples, so the problems with at least
+    // `split` samples are its prefix and the small class its suffix
+    int n_big = b->n_prob;
+    if (sh.split > 0)
+        n_big = (int)(std::lower_bound(b->lpt_samples.begin(), b->lpt_samples.end(), sh.split,
+                                       [](long long v, long long x) { return v >= x; }) - b->lpt_samples.begin());
+    LaunchClass cls[2];
+    cls[0] = { schedule == QC_SCHED_STATIC ? b->order_idx : b->order_lpt, n_big, b->queue, threads, per_sm, depth,
+               schedule, std::max(1, std::min(n_big, b->sm_count * per_sm)) };
+    cls[1] = { b->order_lpt + n_big, b->n_prob - n_big, b->queue + 1, sh.s_threads, sh.s_per_sm, depth, QC_SCHED_LPT,
+               std::max(1, std::min(b->n_prob - n_big, b->sm_count * std::max(1, sh.s_per_sm))) };
+    const int n_cls = sh.split > 0 ? 2 : 1;
     const size_t gbytes = (size_t)b->total_ant * 2 * sizeof(float2);
     unsigned char *stage = (unsigned char *)b->gstage;
     float2 *dg = mem == QC_MEM_DEVICE ? (float2 *)gains : (float2 *)stage;
@@ -1311,9 +1402,6 @@ static int batch_solve_impl(qc_batch *b, void *gains, int8_t *gain_flags, int32_
     int *diters = mem == QC_MEM_DEVICE ? iters
                                        : (iters ? (int *)(stage + gbytes + ((b->total_ant + 15) / 16) * 16) : nullptr);
     BatchArgs a = batch_args(b);
-    a.order = schedule == QC_SCHED_STATIC ? b->order_idx : b->order_lpt;
-    a.queue = b->queue;
-    a.schedule = schedule;
     a.gains = dg;
     a.gain_flags = dflags;
     a.iters = diters;
@@ -1324,7 +1412,7 @@ static int batch_solve_impl(qc_batch *b, void *gains, int8_t *gain_flags, int32_
     a.fb_gains = (const float2 *)o->fallback_gains;
     a.fb_chi2 = o->fallback_chi2;
     a.n_fallback = b->counters + 2 + b->n_prob;
-    const int grid = std::max(1, std::min(b->n_prob, b->sm_count * per_sm));
+    const int grid = cls[0].grid;
     BCK(cudaEventRecord(b->ev0, st));
     if (mem == QC_MEM_HOST) BCK(cudaMemcpyAsync(dg, gains, gbytes, cudaMemcpyHostToDevice, st));
     BCK(cudaMemsetAsync(b->counters, 0, 2 * sizeof(unsigned long long), st));
@@ -1336,12 +1424,13 @@ static int batch_solve_impl(qc_batch *b, void *gains, int8_t *gain_flags, int32_
         k.damping_mode = o->damping_mode; k.damping = o->damping; k.tol = o->tol; k.m16 = b->m16;
         k.gains = dg; k.flags = dflags; k.iters = diters; k.st = st;
         k.fb_gains = o->fallback_gains; k.fb_chi2 = o->fallback_chi2;
+        k.split = sh.split; k.s_threads = sh.s_threads; k.s_per_sm = sh.s_per_sm;
         const bool same = b->exec && memcmp(&k, &b->gkey, sizeof k) == 0;
         if (!same) {
             if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
             cudaGraph_t g = nullptr;
             BCK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-            rc = batch_enqueue(b, a, threads, depth, grid, st);
+            rc = batch_enqueue(b, a, cls, n_cls, st);
             cudaError_t e = cudaStreamEndCapture(st, &g);
             if (rc || e != cudaSuccess) {
                 if (g) cudaGraphDestroy(g);
@@ -1355,7 +1444,7 @@ static int batch_solve_impl(qc_batch *b, void *gains, int8_t *gain_flags, int32_
         }
         BCK(cudaGraphLaunch(b->exec, st));
     } else {
-        if ((rc = batch_enqueue(b, a, threads, depth, grid, st))) return rc;
+        if ((rc = batch_enqueue(b, a, cls, n_cls, st))) return rc;
     }
     if (mem == QC_MEM_HOST) {
         BCK(cudaMemcpyAsync(gains, dg, gbytes, cudaMemcpyDeviceToHost, st));
@@ -1381,6 +1470,11 @@ static int batch_solve_impl(qc_batch *b, void *gains, int8_t *gain_flags, int32_
         S.grid = grid;
         S.depth = depth;
         S.n_fallback = (int32_t)hfb;
+        S.split = sh.split;
+        S.small_threads = n_cls > 1 ? sh.s_threads : 0;
+        S.small_ctas_per_sm = n_cls > 1 ? sh.s_per_sm : 0;
+        S.small_grid = n_cls > 1 ? cls[1].grid : 0;
+        S.n_small = n_cls > 1 ? cls[1].n : 0;
         double tot_vis = 0;
         for (const BProb &P : b->hprobs) tot_vis += (double)P.n_rows * P.n_chan;
         S.mean_iters = tot_vis > 0 ? (double)hc[0] / tot_vis : 0;
@@ -1494,35 +1588,74 @@ extern "C" int qc_batch_autotune(qc_batch *b, const qc_batch_opts *base, qc_batc
     cudaError_t e = qc_dev_malloc((void **)&g, (size_t)b->total_ant * 2 * sizeof(float2));
     if (e != cudaSuccess) return b->cuda_fail(e, "cudaMalloc");
     std::vector<float2> unit((size_t)b->total_ant * 2, make_float2(1.f, 0.f));
-    qc_batch::Shape win{ 0, 0, 0, 0, 1e30 };
+    qc_batch::Shape win{ 0, 0, 0, 0, 1e30, 0, 0, 0 };
     int tried = 0, rc = QC_OK;
     qc_batch_stats ws;
     memset(&ws, 0, sizeof ws);
-    b->tuned.erase(b->shape_key);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tuned.erase(tune_key(b));
+    }
+    auto trial = [&](qc_batch_opts o) -> int {
+        o.use_graph = 0;
+        e = cudaMemcpy(g, unit.data(), unit.size() * sizeof(float2), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return b->cuda_fail(e, "cudaMemcpy");
+        qc_batch_stats s;
+        const int r = batch_solve_impl(b, g, nullptr, nullptr, QC_MEM_DEVICE, &o, &s, true);
+        if (r == QC_EUNSUPPORTED || r == QC_EINVAL) return QC_OK;           // shape not launchable
+        if (r) return r;
+        ++tried;
+        if (s.ctas_per_sm != o.ctas_per_sm) return QC_OK;                   // clamped: a duplicate
+        if (o.split > 0 && s.small_ctas_per_sm != o.small_ctas_per_sm) return QC_OK;
+        if (s.ms < win.ms) {
+            win = { o.threads, o.ctas_per_sm, o.schedule, o.depth, s.ms, o.split > 0 ? o.split : 0,
+                    o.split > 0 ? o.small_threads : 0, o.split > 0 ? o.small_ctas_per_sm : 0 };
+            ws = s;
+        }
+        return QC_OK;
+    };
+    // stage 1: one class -- CTA size (the tile: threads consecutive samples per CTA step),
+    // copy depth, residency and schedule
     for (int threads : { 128, 256, 512 })
         for (int depth : { 3, 4, 6 })
-        for (int per_sm : { 1, 2, 4 })
-            for (int sched : { QC_SCHED_LPT, QC_SCHED_STATIC }) {
-                qc_batch_opts o = *base;
-                o.threads = threads;
-                o.depth = depth;
-                o.ctas_per_sm = per_sm;
-                o.schedule = sched;
-                o.use_graph = 0;
-                e = cudaMemcpy(g, unit.data(), unit.size() * sizeof(float2), cudaMemcpyHostToDevice);
-                if (e != cudaSuccess) { rc = b->cuda_fail(e, "cudaMemcpy"); break; }
-                qc_batch_stats s;
-                int r = batch_solve_impl(b, g, nullptr, nullptr, QC_MEM_DEVICE, &o, &s, true);
-                if (r == QC_EUNSUPPORTED || r == QC_EINVAL) continue;      // shape not launchable
-                if (r) { rc = r; break; }
-                ++tried;
-                if (s.ctas_per_sm != per_sm) continue;                     // clamped: duplicate of a smaller one
-                if (s.ms < win.ms) { win = { threads, per_sm, sched, depth, s.ms }; ws = s; }
-            }
+            for (int per_sm : { 1, 2, 4 })
+                for (int sched : { QC_SCHED_LPT, QC_SCHED_STATIC }) {
+                    if (rc) break;
+                    qc_batch_opts o = *base;
+                    o.threads = threads;
+                    o.depth = depth;
+                    o.ctas_per_sm = per_sm;
+                    o.schedule = sched;
+                    o.split = -1;
+                    rc = trial(o);
+                }
+    // stage 2: with the best large-problem shape, a size split -- problems under the threshold
+    // (samples) go to concurrent small CTAs, several per SM
+    if (!rc && win.threads) {
+        const qc_batch::Shape big = win;
+        for (long long split : { 1LL << 10, 1LL << 12, 1LL << 14, 1LL << 16 })
+            for (int sthreads : { 64, 128 })
+                for (int sper : { 4, 8 }) {
+                    if (rc) break;
+                    qc_batch_opts o = *base;
+                    o.threads = big.threads;
+                    o.depth = big.depth;
+                    o.ctas_per_sm = big.per_sm;
+                    o.schedule = QC_SCHED_LPT;
+                    o.split = split;
+                    o.small_threads = sthreads;
+                    o.small_ctas_per_sm = sper;
+                    rc = trial(o);
+                }
+    }
     qc_dev_free(g);
     if (rc) return rc;
     if (!tried || win.threads == 0) return b->fail(QC_EUNSUPPORTED, "no launch shape could be timed");
-    b->tuned[b->shape_key] = win;
+    if (win.split == 0) win.split = -1;              // tuned: no split
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tuned[tune_key(b)] = win;
+    }
     if (best) *best = ws;
     if (n_tried) *n_tried = tried;
     return QC_OK;

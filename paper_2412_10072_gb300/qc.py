@@ -343,13 +343,16 @@ class _BatchOpts(C.Structure):
     _fields_ = [("max_iter", C.c_int32), ("tol", C.c_double), ("damping_mode", C.c_int32), ("damping", C.c_double),
                 ("stream", C.c_void_p), ("threads", C.c_int32), ("ctas_per_sm", C.c_int32),
                 ("schedule", C.c_int32), ("use_graph", C.c_int32), ("depth", C.c_int32),
-                ("fallback_gains", C.c_void_p), ("fallback_chi2", C.c_void_p)]
+                ("fallback_gains", C.c_void_p), ("fallback_chi2", C.c_void_p), ("split", C.c_int64),
+                ("small_threads", C.c_int32), ("small_ctas_per_sm", C.c_int32)]
 
 
 class BatchStats(C.Structure):
     _fields_ = [("ms", C.c_double), ("vis_iters", C.c_int64), ("bytes", C.c_int64), ("n_iter_max", C.c_int32),
                 ("mean_iters", C.c_double), ("threads", C.c_int32), ("ctas_per_sm", C.c_int32),
-                ("schedule", C.c_int32), ("grid", C.c_int32), ("depth", C.c_int32), ("n_fallback", C.c_int32)]
+                ("schedule", C.c_int32), ("grid", C.c_int32), ("depth", C.c_int32), ("n_fallback", C.c_int32),
+                ("split", C.c_int64), ("small_threads", C.c_int32), ("small_ctas_per_sm", C.c_int32),
+                ("small_grid", C.c_int32), ("n_small", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -422,11 +425,11 @@ class BatchSolver:
         return g
 
     def _opts(self, max_iter, tol, damping_mode, damping, stream, threads, ctas_per_sm, schedule, use_graph,
-              depth=0, fallback=None):
+              depth=0, fallback=None, split=0, small_threads=0, small_ctas_per_sm=0):
         st = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
         fb_g, fb_c = (None, None) if fallback is None else (fallback[0].data_ptr(), fallback[1].data_ptr())
         return _BatchOpts(max_iter, tol, damping_mode, damping, st or None, threads, ctas_per_sm, schedule,
-                          int(use_graph), depth, fb_g, fb_c)
+                          int(use_graph), depth, fb_g, fb_c, int(split), int(small_threads), int(small_ctas_per_sm))
 
     def _err(self, rc):
         raise QCError(rc, self._lib.qc_batch_last_error(self._h).decode())
@@ -434,7 +437,8 @@ class BatchSolver:
     def solve(self, gains=None, max_iter: int = 20, tol: float = 1e-6, damping_mode: int = QC_DAMP_ALTERNATE,
               damping: float = 1.0, stream=None, threads: int = 0, ctas_per_sm: int = 0,
               schedule: int = QC_SCHED_AUTO, use_graph: bool = True, want_flags: bool = True, depth: int = 0,
-              fallback=None, moments: bool = False):
+              fallback=None, moments: bool = False, split: int = 0, small_threads: int = 0,
+              small_ctas_per_sm: int = 0):
         """Solve in place; returns (gains, gain_flags, iters, BatchStats).  fallback: optional
         (device gains [sum n_ant][2] complex64, device chi^2 [n_prob] float64) -- a problem whose
         starting gains fit worse than its fallback chi^2 restarts from the fallback gains.
@@ -452,7 +456,7 @@ class BatchSolver:
             flags = np.zeros(self.total_ant, dtype=np.int8) if want_flags else None
             iters = np.zeros(self.n_prob, dtype=np.int32)
         o = self._opts(max_iter, tol, damping_mode, damping, stream, threads, ctas_per_sm, schedule, use_graph, depth,
-                       fallback)
+                       fallback, split, small_threads, small_ctas_per_sm)
         s = BatchStats()
         fn = self._lib.qc_batch_solve_moments if moments else self._lib.qc_batch_solve
         rc = fn(self._h, _addr(gains), _addr(flags), _addr(iters), QC_MEM_DEVICE if dev else QC_MEM_HOST, C.byref(o),

@@ -180,3 +180,48 @@ def test_moments_solve_fully_flagged_and_autocorrelations():
     assert np.all(flags[offs[2]:offs[3]] == 1)
     assert np.array_equal(g[offs[2]:offs[3]], g0[offs[2]:offs[3]])
     compare(b, g, flags, iters)
+
+
+def test_size_split_matches_oracle_and_the_single_class_solve():
+    """A size threshold splits the batch into concurrent launches of large and small CTAs; every
+    problem's result equals the single-class solve's and the oracle's."""
+    b = small_batch(n=40, seed_base=300)
+    samples = np.diff(b.vis_offset)
+    split = int(np.median(samples))
+    S = solver_of(b)
+    g1, f1, it1, st1 = S.solve(split=-1)
+    g2, f2, it2, st2 = S.solve(split=split, small_threads=64, small_ctas_per_sm=4)
+    assert st1.split <= 0 and st1.n_small == 0
+    assert st2.split == split and st2.n_small == int(np.sum(samples < split)) > 0
+    assert st2.small_threads == 64 and st2.small_ctas_per_sm == 4
+    assert np.array_equal(f1, f2) and np.array_equal(it1, it2)
+    np.testing.assert_allclose(g2, g1, rtol=0, atol=1e-6)
+    compare(b, g2, f2, it2)
+    S.close()
+
+
+def test_autotune_chooses_a_shape_caches_it_per_shape_class_and_matches_oracle():
+    b = small_batch(n=48, seed_base=400)
+    S = solver_of(b)
+    best, n_tried = S.autotune()
+    assert n_tried >= 20
+    assert best.threads in (128, 256, 512) and best.depth in (3, 4, 6) and best.ms > 0
+    # a solve that leaves the shape to the tuner uses the tuned one
+    g, flags, iters, st = S.solve(use_graph=False)
+    assert (st.threads, st.ctas_per_sm, st.depth, st.split) == (best.threads, best.ctas_per_sm, best.depth,
+                                                                best.split)
+    compare(b, g, flags, iters)
+    S.close()
+    # another batch of the same shape class (the same problems) reuses the cached shape untuned
+    S2 = solver_of(b)
+    g2, flags2, iters2, st2 = S2.solve(use_graph=False)
+    assert (st2.threads, st2.ctas_per_sm, st2.depth, st2.split, st2.small_threads) == \
+        (st.threads, st.ctas_per_sm, st.depth, st.split, st.small_threads)
+    assert np.array_equal(flags2, flags)
+    S2.close()
+    # a batch of another shape class does not
+    other = small_batch(n=12, seed_base=500)
+    S3 = solver_of(other)
+    _, _, _, st3 = S3.solve(use_graph=False)
+    assert st3.threads == 256 and st3.split <= 0
+    S3.close()

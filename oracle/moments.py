@@ -87,3 +87,108 @@ def chi2_from_moments(S, T, U, gains):
                     G = g[p, i] * np.conj(g[q, j])
                     tot += U[ti, p, q, c] - 2 * np.real(np.conj(G) * T[ti, p, q, c]) + abs(G) ** 2 * S[ti, p, q, c]
     return tot
+
+
+# ---------------------------------------------------------------------------
+# the 4x4 full-Jones form (any single term: diagonal, full or phase-only)
+# ---------------------------------------------------------------------------
+#
+# A single term G with gains constant over each solution interval (bin).  Per bin and
+# baseline (p, q), p < q (rows with p > q through their conjugate orientation), with the
+# weight index kj = 2k + j of correlation (k, j) and the row-major index u = 2l + m of the
+# 2x2 model entry M_lm:
+#     S[kj][u][v] = sum w_kj conj(M_u) M_v        (Hermitian in u, v)
+#     T[kj][u]    = sum w_kj conj(M_u) D_kj
+#     U[kj]       = sum w_kj |D_kj|^2
+# Antenna p: X = M G_q^H and E = I (x) X^T (Eq. vectrick with L = I), so with the parameter
+# index 2k + l of G_p,kl
+#     JHJ_p[(k,l),(k,l')] += sum_j sum_m sum_m' G_q,jm conj(G_q,jm') S[kj][(l,m)][(l',m')]
+#     b_p[(k,l)]          += sum_j sum_m G_q,jm T[kj][(l,m)]
+# and antenna q, through the conjugate baseline (D -> D^H, M -> M^H, w -> P w),
+#     JHJ_q[(k,l),(k,l')] += sum_j sum_m sum_m' G_p,jm conj(G_p,jm') conj(S[jk][(m,l)][(m',l')])
+#     b_q[(k,l)]          += sum_j sum_m G_p,jm conj(T[jk][(m,l)]).
+# Summed over an antenna's baselines, JHr = b - JHJ vec(G) (V = E vec(G_p) for every sample),
+# and chi^2 = sum U - 2 Re sum_{k,j,l,m} conj(G_p,kl) G_q,jm T[kj][(l,m)] + vec(G_p)^H JHJ_p vec(G_p)
+# per baseline.  A diagonal term takes the (0, 3) rows and columns; a phase-only term applies
+# its chain rule to those.
+
+def moments_full(problem, t_map, f_map, n_tint: int, n_fint: int):
+    """S [bin][n_ant][n_ant][4][4][4] complex, T [bin][n_ant][n_ant][4][4] complex, U [..][4] real,
+    bin = t_int * n_fint + f_int, keyed by (p, q) with p < q."""
+    na = problem.n_ant
+    nb = n_tint * n_fint
+    S = np.zeros((nb, na, na, 4, 4, 4), dtype=np.complex128)
+    T = np.zeros((nb, na, na, 4, 4), dtype=np.complex128)
+    U = np.zeros((nb, na, na, 4))
+    perm = [0, 2, 1, 3]
+    for row in range(problem.data.shape[0]):
+        p, q, t = int(problem.ant1[row]), int(problem.ant2[row]), int(problem.time_idx[row])
+        if p == q:
+            continue
+        for ch in range(problem.data.shape[1]):
+            if problem.flag is not None and problem.flag[row, ch]:
+                continue
+            b = int(t_map[t]) * n_fint + int(f_map[ch])
+            d, m, w = problem.data[row, ch], problem.model[row, ch], problem.weight[row, ch]
+            if p > q:
+                d, m, w = np.conj(d[perm]), np.conj(m[perm]), w[perm]
+            a, c = min(p, q), max(p, q)
+            S[b, a, c] += w[:, None, None] * np.conj(m)[None, :, None] * m[None, None, :]
+            T[b, a, c] += w[:, None] * np.conj(m)[None, :] * d[:, None]
+            U[b, a, c] += w * np.abs(d) ** 2
+    return S, T, U
+
+
+def normal_equations_full(S, T, gains):
+    """JHJ [bin][n_ant][4][4] and JHr [bin][n_ant][4] of a single full 2x2 term with gains
+    [bin][n_ant][4] (row-major G), from the baseline sums."""
+    nb, na = S.shape[:2]
+    jhj = np.zeros((nb, na, 4, 4), dtype=np.complex128)
+    bvec = np.zeros((nb, na, 4), dtype=np.complex128)
+    for b in range(nb):
+        G = gains[b].reshape(na, 2, 2)
+        for p in range(na):
+            for q in range(p + 1, na):
+                for k in range(2):
+                    for j in range(2):
+                        kj, jk = 2 * k + j, 2 * j + k
+                        for l in range(2):
+                            for l2 in range(2):
+                                for m in range(2):
+                                    for m2 in range(2):
+                                        u, v = 2 * l + m, 2 * l2 + m2
+                                        jhj[b, p, 2 * k + l, 2 * k + l2] += \
+                                            G[q, j, m] * np.conj(G[q, j, m2]) * S[b, p, q, kj, u, v]
+                                        uq, vq = 2 * m + l, 2 * m2 + l2
+                                        jhj[b, q, 2 * k + l, 2 * k + l2] += \
+                                            G[p, j, m] * np.conj(G[p, j, m2]) * np.conj(S[b, p, q, jk, uq, vq])
+                            for m in range(2):
+                                bvec[b, p, 2 * k + l] += G[q, j, m] * T[b, p, q, kj, 2 * l + m]
+                                bvec[b, q, 2 * k + l] += G[p, j, m] * np.conj(T[b, p, q, jk, 2 * m + l])
+    jhr = bvec - np.einsum("bauv,bav->bau", jhj, gains.reshape(nb, na, 4))
+    return jhj, jhr
+
+
+def chi2_from_moments_full(S, T, U, gains):
+    nb, na = S.shape[:2]
+    tot = 0.0
+    for b in range(nb):
+        G = gains[b].reshape(na, 2, 2)
+        for p in range(na):
+            for q in range(p + 1, na):
+                tot += float(np.sum(U[b, p, q]))
+                gp = G[p].reshape(4)
+                H = np.zeros((4, 4), dtype=np.complex128)
+                cross = 0.0 + 0.0j
+                for k in range(2):
+                    for j in range(2):
+                        kj = 2 * k + j
+                        for l in range(2):
+                            for m in range(2):
+                                cross += np.conj(G[p, k, l]) * G[q, j, m] * T[b, p, q, kj, 2 * l + m]
+                                for l2 in range(2):
+                                    for m2 in range(2):
+                                        H[2 * k + l, 2 * k + l2] += (G[q, j, m] * np.conj(G[q, j, m2]) *
+                                                                     S[b, p, q, kj, 2 * l + m, 2 * l2 + m2])
+                tot += -2.0 * cross.real + float(np.real(np.conj(gp) @ H @ gp))
+    return tot

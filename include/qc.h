@@ -202,7 +202,24 @@ typedef struct {
     int32_t div_flag;          /* 1 = flag diverging gains (see below)              */
     int32_t robust;            /* 1 = robust reweighting between epochs (below)     */
     double robust_nu;          /* its degrees of freedom nu (> 0; 0 -> 5)           */
+    int32_t moments;           /* 1 = single-term chains from per-baseline sums (below) */
 } qc_opts;
+
+/*
+ * Sufficient statistics (not in the paper), opt-in with qc_opts.moments: when the
+ * chain has a single diagonal, full or phase-only term (one direction, complex64
+ * model), its gains are constant over each solution interval, so one pass over the
+ * data forms per (interval, antenna pair) the gain-free sums
+ *   S[kj][u][v] = sum w_kj conj(M_u) M_v,  T[kj][u] = sum w_kj conj(M_u) D_kj,
+ *   U[kj] = sum w_kj |D_kj|^2
+ * (kj = 2k + j the correlation, u = 2l + m the model entry), and every iteration
+ * forms the 4x4 blocks of Eq. jhj_entry_simplified / Eq. jhr_entry_simplified from
+ * them and the current gains (800 bytes per interval and pair instead of 81 per
+ * sample).  Other chains, and sums of 2^31 or more (interval, pair) slots, ignore the
+ * option.  qc_stats.vis_iters counts the samples of the active intervals per iteration as
+ * without it; qc_stats.acc_bytes counts the pass (the samples' bytes, once) and, per
+ * iteration and active interval, the sums read on both sides and the accumulators written.
+ */
 
 /*
  * Gain flagging on divergence (Section 4.3, "Gain flagging": gains whose updates
@@ -235,6 +252,8 @@ typedef struct {
     int64_t acc_launches;             /* accumulate kernels that did work              */
     int64_t launches;                 /* kernels launched by this call                 */
     int32_t n_iter_max;               /* largest iteration count of any interval       */
+    double pass_ms;                   /* device time of the sums passes (qc_opts.moments;
+                                         included in acc_ms), else 0                    */
 } qc_stats;
 
 /*

@@ -322,6 +322,26 @@ extern "C" int qc_create(const qc_problem *p, qc_ctx **out)
     HCOPY(c->d_strip_off, strip_off.data(), nbytes<int>(n_bl + 1));
     DALLOC(c->d_strip_rows, int, std::max<size_t>(1, strip_rows.size()));
     if (!strip_rows.empty()) HCOPY(c->d_strip_rows, strip_rows.data(), nbytes<int>(strip_rows.size()));
+    {
+        // unordered antenna pairs: both orientations of a baseline share one slot of the sums
+        // of a single-term chain (qc_opts.moments)
+        std::vector<int> upair((size_t)na * na, -1), up_of_bl(std::max(1, n_bl), 0);
+        int n_up = 0;
+        for (int a1 = 0; a1 < na; ++a1)
+            for (int a2 = 0; a2 < na; ++a2) {
+                const int bl = bl_of_pair[(size_t)a1 * na + a2];
+                if (bl < 0) continue;
+                const int lo = std::min(a1, a2), hi = std::max(a1, a2);
+                int &slot = upair[(size_t)lo * na + hi];
+                if (slot < 0) { slot = n_up++; upair[(size_t)hi * na + lo] = slot; }
+                up_of_bl[bl] = slot;
+            }
+        c->n_up = n_up;
+        DALLOC(c->d_upair, int, std::max<size_t>(1, upair.size()));
+        if (!upair.empty()) HCOPY(c->d_upair, upair.data(), nbytes<int>(upair.size()));
+        DALLOC(c->d_up_of_bl, int, up_of_bl.size());
+        HCOPY(c->d_up_of_bl, up_of_bl.data(), nbytes<int>(up_of_bl.size()));
+    }
 
     const size_t n_vis = (size_t)p->n_row * p->n_chan;
     const float4 *model32 = nullptr;
@@ -909,10 +929,12 @@ extern "C" int qc_solve(qc_ctx *c, qc_term *terms, int32_t n_terms, const qc_opt
         for (int n = 0; n < n_terms; ++n) {
             if (!terms[n].solve) continue;
             int it_max = 0;
-            double acc_ms = 0;
+            double acc_ms = 0, pass_ms = 0;
             long long acc_launches = 0;
-            if ((rc = c->solve_term(xt.data(), n_terms, n, chain, o, st, &it_max, &acc_ms, &acc_launches))) return rc;
+            if ((rc = c->solve_term(xt.data(), n_terms, n, chain, o, st, &it_max, &acc_ms, &acc_launches, &pass_ms)))
+                return rc;
             S.acc_ms += acc_ms;
+            S.pass_ms += pass_ms;
             S.acc_launches += acc_launches;
             if (epoch == o->n_epochs - 1) n_iter_max = std::max(n_iter_max, it_max);
         }
@@ -1000,8 +1022,9 @@ int qc_ctx::get_event(int i, cudaEvent_t &ev)
 }
 
 int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, const qc_opts *o, cudaStream_t st,
-                       int *it_max, double *acc_ms, long long *acc_launches)
+                       int *it_max, double *acc_ms, long long *acc_launches, double *pass_ms)
 {
+    *pass_ms = 0;
     qc_ctx *c = this;
     const qc_term &t = terms[n];
     TermBufs &B = tb[n];
@@ -1034,6 +1057,10 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
     const bool ddp = n_dir > 1;
     const int nat = term_nat(t);
     if (!L.fn && !ddp) return fail(QC_EUNSUPPORTED, "no accumulate kernel for this chain");
+    // a single-term chain from per-(interval, baseline) sums (qc_moments.cu): one pass over the
+    // data, then every iteration forms the blocks from the sums and the current gains
+    const bool mom = o->moments && n_terms == 1 && !delay[n] && !ddp && d_model != nullptr && n_up > 0 &&
+                     (size_t)nb * n_up < (size_t)INT32_MAX;
     // pipelined kernel: shared-memory layout of the per-warp rings for this chain
     PipeArgs pa;
     memset(&pa, 0, sizeof pa);
@@ -1043,11 +1070,11 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
     // kernel 4: the warp-specialised kernel (chains of one or two terms; a solved delay term
     // keeps its own streaming kernel)
     // kernel 5: the self-feeding variant (every warp issues its own bulk copies)
-    bool ws = !ddp && L.ws_fn != nullptr && !delay[n] && n_ant < 32768 && (o->kernel == 4 || o->kernel == 5);
+    bool ws = !mom && !ddp && L.ws_fn != nullptr && !delay[n] && n_ant < 32768 && (o->kernel == 4 || o->kernel == 5);
     const bool self_feed = o->kernel == 5;
     const void *ws_fn = self_feed ? (order == 0 ? L.wss_fn : L.wss_fn1) : L.ws_fn;
     const int ws_warps = self_feed ? L.wss_nw : L.ws_nc;     // warps that own a ring
-    const bool streaming = !ddp && L.stream_fn != nullptr && n_ant < 32768 &&
+    const bool streaming = !mom && !ddp && L.stream_fn != nullptr && n_ant < 32768 &&
                            (o->kernel == 3 || o->kernel == 0 || ((o->kernel == 4 || o->kernel == 5) && delay[n]));
     // a solved delay term under the streaming kernel: its own kernel, which applies the chain
     // rule per sample and keeps sums per parameter interval (else: the per-channel bins)
@@ -1067,7 +1094,7 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
     }
     const void *stream_fn = ded ? DL.fn : L.stream_fn;
     const int stream_smem_per_warp = ded ? DL.smem_per_warp : L.stream_smem_per_warp;
-    bool pipelined = !ddp && !streaming && L.pipe_fn != nullptr && (o->kernel == 1 || (o->kernel == 0 && order == 1));
+    bool pipelined = !mom && !ddp && !streaming && L.pipe_fn != nullptr && (o->kernel == 1 || (o->kernel == 0 && order == 1));
     const bool has_o = n_terms == 2;
     if (pipelined) {
         const int NW = L.pipe_nw;
@@ -1290,6 +1317,8 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
         dda.acc = (double *)B.acc.ptr;
         dda.active = (const uint8_t *)B.active.ptr;
         grid = sm_count * 8;
+    } else if (mom) {
+        grid = 0;
     } else if (ws) {
         grid = ws_grid;
     } else if (streaming) {
@@ -1376,8 +1405,50 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
         dua.tol = ua.tol;
     }
 
+    // sums of a single-term chain: [bins][unordered pairs][MOM_N] FP64, then the per-bin bytes
+    // of one iteration for the byte counter
+    MomArgs ma;
+    MomNormArgs mn;
+    memset(&ma, 0, sizeof ma);
+    memset(&mn, 0, sizeof mn);
+    const size_t mom_words_all = (size_t)nb * n_up * MOM_N;
+    const size_t mom_rows_off = ((nbytes<double>(mom_words_all) + nbytes<long long>(nb) + 15) / 16) * 16;
+    if (mom) {
+        if ((rc = ensure(B.mom, mom_rows_off + nbytes<int4>(std::max(1L, n_strip_rows))))) return rc;
+        ma.n_chan = n_chan;
+        ma.n_up = n_up;
+        ma.vis = d_vis;
+        ma.model = d_model;
+        ma.wf = d_wf;
+        ma.mrows = (const int4 *)((char *)B.mom.ptr + mom_rows_off);
+        ma.strip_off = d_strip_off;
+        ma.n_strips = n_strips;
+        ma.n_chunks = (n_chan + 15) / 16;
+        // chunk groups as wide as leave about four units per resident warp (three CTAs of four
+        // warps per SM): an interval wider than a chunk then flushes once per row and group
+        {
+            const long want_units = 4L * sm_count * 12;
+            const long per_strip = std::max(1L, (want_units + std::max(1, n_strips) - 1) / std::max(1, n_strips));
+            ma.group = (int)std::max(1L, (long)ma.n_chunks / per_strip);
+        }
+        ma.tn = chain.t[n];
+        ma.mom = (double *)B.mom.ptr;
+        mn.n_bins = nb;
+        mn.n_ant = n_ant;
+        mn.n_up = n_up;
+        mn.type = t.type;
+        mn.upair = d_upair;
+        mn.mom = ma.mom;
+        mn.params = (const double *)B.params.ptr;
+        mn.active = (const uint8_t *)B.active.ptr;
+        mn.acc = (double *)B.acc.ptr;
+        ua.bin_nbytes = (const long long *)(ma.mom + mom_words_all);
+    }
+    const long long mom_iter_bytes = 2LL * n_up * MOM_N * 8 + 8LL * n_ant * (t.type == 1 ? KG_FULL : KG_DIAG);
+
     const int max_iter = t.max_iter;
-    for (int k = 0; k < 2 * max_iter; ++k) { cudaEvent_t ev; if ((rc = get_event(2 + k, ev))) return rc; }
+    for (int k = 0; k < 2 * max_iter + 2; ++k) { cudaEvent_t ev; if ((rc = get_event(2 + k, ev))) return rc; }
+    const int ev_pass = 2 + 2 * max_iter;     // the sums pass (its own bracket inside iteration 1's)
     // (no graph while a test stalls a stage: a captured graph would keep the stall)
     const bool use_graph = o->use_graph && !t.reduce && qc_wait_stall_stage() < 0;
     const unsigned rec_flags = use_graph ? cudaEventRecordExternal : cudaEventRecordDefault;
@@ -1403,6 +1474,20 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
             if (ddp) {
                 dda.n_active = cnt + (k - 1);
                 CK(dd_launch_acc(dda, ts, grid, st));
+            } else if (mom) {
+                if (k == 1) {
+                    CK(cudaMemsetAsync(B.mom.ptr, 0, nbytes<double>(mom_words_all), st));
+                    CK(mom_launch_bytes(nb, (const long long *)B.nvis.ptr + 2 * (size_t)nb, mom_iter_bytes,
+                                        (long long *)(ma.mom + mom_words_all), ua.acc_bytes, st));
+                    CK(mom_launch_rows(n_strip_rows, d_strip_rows, d_rows, d_row_live, chain.t[n].t_map,
+                                       chain.t[n].n_fint, d_up_of_bl, const_cast<int4 *>(ma.mrows), st));
+                    CK(cudaEventRecordWithFlags(events[ev_pass], st, rec_flags));
+                    ma.n_active = cnt;
+                    CK(mom_launch_pass(ma, sm_count, st));
+                    CK(cudaEventRecordWithFlags(events[ev_pass + 1], st, rec_flags));
+                }
+                mn.n_active = cnt + (k - 1);
+                CK(mom_launch_normal(mn, st));
             } else if (ws) {
                 wa.n_active = cnt + (k - 1);
                 const uint8_t *ca = (const uint8_t *)B.chunk_act.ptr;
@@ -1486,7 +1571,7 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
     } else {
         if ((rc = enqueue())) return rc;
     }
-    launches += 1 + 3 * (long long)max_iter;
+    launches += 1 + 3 * (long long)max_iter + (mom ? 3 : 0);
     // iteration bookkeeping: which accumulate launches did work, and their device time
     std::vector<int> hcnt(max_iter + 1);
     int herr = 0;
@@ -1507,6 +1592,11 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
         ms_sum += ms;
         ++worked;
         last = k;
+    }
+    if (mom && hcnt[0] != 0) {
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, events[ev_pass], events[ev_pass + 1]));
+        *pass_ms = ms;
     }
     *it_max = last;
     *acc_ms = ms_sum;

@@ -11,6 +11,7 @@
 #include "qc_stream_delay.cuh"
 #include "qc_ws.cuh"
 #include "qc_robust.cuh"
+#include "qc_moments.cuh"
 
 // Every device allocation of the library goes through these two calls.  They count the
 // live allocations and honour the test hook of qc_test_fail_alloc (qc.h), so that tests can
@@ -40,6 +41,14 @@ struct DDArgs {
 };
 } // namespace qc
 cudaError_t dd_launch_acc(const qc::DDArgs &a, int ts, int grid_x, cudaStream_t st);
+// Single-term chains from per-(interval, baseline) sums (qc_moments.cu).
+cudaError_t mom_launch_pass(const qc::MomArgs &a, int sm_count, cudaStream_t st);
+cudaError_t mom_launch_normal(const qc::MomNormArgs &a, cudaStream_t st);
+cudaError_t mom_launch_rows(long n, const int *strip_rows, const int4 *rows, const uint8_t *row_live, const int *t_map,
+                            int n_fint, const int *up_of_bl, int4 *out, cudaStream_t st);
+cudaError_t mom_launch_bytes(int n_bins, const long long *bin_nbytes, long long per_iter, long long *iter_nbytes,
+                             unsigned long long *acc_bytes, cudaStream_t st);
+size_t mom_words();
 cudaError_t dd_launch_residual(const qc::DDArgs &a, int grid, cudaStream_t st);
 
 struct Buf {
@@ -74,6 +83,7 @@ struct TermBufs {
     Buf ws_sb;     // warp-specialised kernel, strip tiles: uint32 [n_chunks][words] active-entry bits
     Buf div;       // divergence flagging: double [bins][ant][2] first / last relative updates
     Buf params0;   // divergence flagging: the FP64 parameters before the solve
+    Buf mom;       // single-term chains: FP64 sums per (interval, unordered baseline)
     Buf dfmap;     // delay terms: int [n_chan] parameter interval of each channel
     Buf dfr;       // delay terms: int2 [n_fint] first and last channel of each interval
     Buf dnu;       // delay terms: double [n_chan] channel frequencies
@@ -133,6 +143,9 @@ struct qc_ctx {
     const float *d_bl_scale = nullptr;
     int4 *d_rows = nullptr;
     int *d_strip_rows = nullptr, *d_strip_off = nullptr;
+    int n_up = 0;                     // unordered antenna pairs with cross-correlation rows
+    int *d_up_of_bl = nullptr;        // [ordered baseline] -> unordered pair
+    int *d_upair = nullptr;           // [n_ant][n_ant] -> unordered pair or -1
     uint8_t *d_row_live = nullptr;    // [n_row]
     const float4 *d_wf = nullptr;     // [n_row][n_chan] weights with flags folded in (streaming kernel)
     const float4 *d_weight_use = nullptr;   // robust reweighting: the weights every kernel reads (d_wf)
@@ -179,5 +192,5 @@ struct qc_ctx {
     int run_residual(const qc::Chain &chain, float4 *dres, double *d_chi2, cudaStream_t st);
     int pick_order(const qc_term &t, const qc_opts *o) const;
     int solve_term(const qc_term *terms, int n_terms, int n, qc::Chain chain, const qc_opts *o, cudaStream_t st,
-                   int *it_max, double *acc_ms, long long *acc_launches);
+                   int *it_max, double *acc_ms, long long *acc_launches, double *pass_ms);
 };

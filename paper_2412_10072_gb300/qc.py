@@ -56,13 +56,13 @@ class _Opts(C.Structure):
                 ("block_threads", C.c_int32), ("ctas_per_sm", C.c_int32), ("kernel", C.c_int32),
                 ("allreduce", ALLREDUCE_FN),
                 ("allreduce_user", C.c_void_p), ("div_flag", C.c_int32), ("robust", C.c_int32),
-                ("robust_nu", C.c_double)]
+                ("robust_nu", C.c_double), ("moments", C.c_int32)]
 
 
 class Stats(C.Structure):
     _fields_ = [("chi2_before", C.c_double), ("chi2_after", C.c_double), ("ms", C.c_double), ("acc_ms", C.c_double),
                 ("vis_iters", C.c_int64), ("acc_bytes", C.c_int64), ("acc_launches", C.c_int64),
-                ("launches", C.c_int64), ("n_iter_max", C.c_int32)]
+                ("launches", C.c_int64), ("n_iter_max", C.c_int32), ("pass_ms", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -256,15 +256,17 @@ class Solver:
     def solve(self, terms: List[Term], n_epochs: int = 1, damping_mode: int = QC_DAMP_ALTERNATE,
               damping: float = 1.0, use_graph: bool = True, want_chi2: bool = False, order: int = -1,
               block_threads: int = 0, ctas_per_sm: int = 0, stream=None, allreduce=None,
-              kernel: int = 0, div_flag: bool = False, robust_nu: Optional[float] = None) -> Stats:
+              kernel: int = 0, div_flag: bool = False, robust_nu: Optional[float] = None,
+              moments: bool = False) -> Stats:
         """robust_nu: robust reweighting between epochs with nu degrees of freedom (None: off);
-        div_flag: flag (gain flag 2) and restore diverging gains (include/qc.h)."""
+        div_flag: flag (gain flag 2) and restore diverging gains; moments: a single-term chain
+        from per-(interval, baseline) sums (include/qc.h)."""
         arr = _terms_array(terms)
         cb = ALLREDUCE_FN(allreduce) if allreduce is not None else ALLREDUCE_FN()
         st = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
         o = _Opts(n_epochs, damping_mode, damping, st or None, int(use_graph), int(want_chi2), order,
                   block_threads, ctas_per_sm, kernel, cb, None, int(bool(div_flag)), int(robust_nu is not None),
-                  float(robust_nu or 0.0))
+                  float(robust_nu or 0.0), int(bool(moments)))
         s = Stats()
         rc = self._lib.qc_solve(self._h, arr, len(terms), C.byref(o), C.byref(s))
         if rc != QC_OK:

@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="plain", choices=["plain", "mixed", "batched", "warmstart", "delay", "mad",
-                                                            "kde"],
+                                                            "kde", "moments"],
                     help="plain: the large two-term solve; mixed: the same with FP16 model storage; batched: 4096 "
                          "independent intervals in one persistent launch; warmstart: the batched solve at 64 "
                          "antennas from cold, previous-interval and network starts; delay: a delay and phase "
@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--dist-backend", default="nccl", choices=["nccl", "gloo"],
+                    help="process group of the multi-GPU mode (gloo: host-staged exchange, for checking the "
+                         "sharded flow with several ranks on fewer GPUs)")
     ap.add_argument("--block", type=int, default=0, help="threads per CTA of the accumulate kernel (0: auto)")
     ap.add_argument("--kernel", type=int, default=0,
                     help="accumulate kernel: 0 auto (streaming), 1 bulk-copy pipeline, 2 prefetching, 3 streaming, "
@@ -169,8 +172,32 @@ class ClockSampler:
 # the workload
 # ---------------------------------------------------------------------------
 
-def make_terms(qc, setup, n_ant, max_iter):
-    return [qc.Term.from_spec(s, n_ant, max_iter=max_iter, tol=1e-6) for s in setup.terms]
+def make_terms(qc, setup, n_ant, max_iter, world=1, rank=0):
+    """The chain's terms; with world > 1 each rank's view of them under the time-block split:
+    a term whose intervals lie inside one block (G) is solved on the rank's own intervals, a term
+    with an interval spanning blocks (B) over all of them with reduce = 1."""
+    if world == 1:
+        return [qc.Term.from_spec(s, n_ant, max_iter=max_iter, tol=1e-6) for s in setup.terms]
+    from paper_2412_10072_gb300 import shard
+    out = []
+    for s in setup.terms:
+        ts = shard.shard_term(s.t_map, s.n_tint, setup.n_time, world, rank)
+        out.append(qc.Term(s.kind, ts.t_map, s.f_map, ts.n_tint, s.n_fint, n_ant, max_iter=max_iter, tol=1e-6,
+                           reduce=ts.reduce))
+    return out
+
+
+def shard_setup(setup, world, rank):
+    """Rank's rows of the observation (a contiguous block of times) and their local time index."""
+    import dataclasses
+    import numpy as np
+    from paper_2412_10072_gb300 import shard
+    t0, t1 = shard.time_block(setup.n_time, rank, world)
+    rows = shard.block_rows(setup.time_idx, t0, t1)
+    sub = dataclasses.replace(setup, ant1=setup.ant1[rows], ant2=setup.ant2[rows], time_idx=setup.time_idx[rows],
+                              uvw=setup.uvw[rows], flag_rows=setup.flag_rows[rows],
+                              flag_samples=None if setup.flag_samples is None else setup.flag_samples[rows])
+    return sub, (setup.time_idx[rows] - t0).astype(np.int32), t1 - t0
 
 
 def cpu_baseline(args, dev_obs, setup, n_times=2, max_iter=4):
@@ -236,9 +263,11 @@ def plain_config(args, world=1):
     n_vis = args.n_ant * (args.n_ant - 1) // 2 * args.n_time * args.n_chan
     return {"workload": WORKLOAD + (" (FP16 model)" if args.mixed else ""), "n_ant": args.n_ant,
             "n_time": args.n_time, "n_chan": args.n_chan, "n_vis": n_vis,
-            "input_bytes_per_gpu": n_vis * (64 if args.mixed else 80) + n_vis,
+            "input_bytes_per_gpu": (n_vis * (64 if args.mixed else 80) + n_vis) // world,
             "l2": "inputs (25 GB) larger than L2 (129 MB)", "epochs": args.epochs, "max_iter": args.max_iter,
-            "tol": 1e-6, "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"}
+            "tol": 1e-6, "parallelism": (f"time-block shards x{world}: G per rank, B reduce=1 with an "
+                                         f"{getattr(args, 'dist_backend', 'nccl').upper()} allreduce of its normal "
+                                         "equations" if world > 1 else "1 GPU")}
 
 
 def run_reference(args):
@@ -289,6 +318,8 @@ def main():
         return run_mad(args)
     if args.workload == "kde" and args.impl == "ours":
         return run_kde(args)
+    if args.workload == "moments" and args.impl == "ours":
+        return run_moments(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -301,33 +332,45 @@ def main():
     import torch
     from paper_2412_10072_gb300 import qc, synth
 
+    local = local % max(1, torch.cuda.device_count())
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if args.dist_backend == "nccl":
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group("gloo")
 
     def barrier():
         if dist is not None:
             dist.barrier()
 
-    # ---- workload on the device (weak scaling: every rank its own observation) ----
-    setup = synth.plain_large_setup(seed=1 + rank, n_ant=args.n_ant, n_time=args.n_time, n_chan=args.n_chan,
+    # ---- workload on the device (one observation; with world > 1 every rank holds a block of its
+    # times, solves G on its own intervals and B over all of them with an NCCL allreduce of B's
+    # partial normal equations before every update) ----
+    setup = synth.plain_large_setup(seed=1, n_ant=args.n_ant, n_time=args.n_time, n_chan=args.n_chan,
                                     flag_row_frac=0.1, n_src=50)
+    if world > 1:
+        gen_setup, local_time, local_n_time = shard_setup(setup, world, rank)
+    else:
+        gen_setup, local_time, local_n_time = setup, setup.time_idx, setup.n_time
     t_gen = time.perf_counter()
-    obs = synth.make_observation_device(setup, noise=0.05, noise_seed=1000 + rank, device=f"cuda:{local}")
+    obs = synth.make_observation_device(gen_setup, noise=0.05, noise_seed=1000 + rank, device=f"cuda:{local}")
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t_gen
-    n_vis = setup.ant1.size * args.n_chan
-    input_bytes = sum(int(obs[k].numel() * obs[k].element_size()) for k in ("data", "model", "weight", "flag"))
+    geo = (gen_setup.ant1, gen_setup.ant2, local_time, setup.n_ant, local_n_time)
     stream = torch.cuda.Stream()
-    solver = qc.Solver(obs["data"], obs["model"], obs["weight"], obs["flag"], setup.ant1, setup.ant2,
-                       setup.time_idx, setup.n_ant, setup.n_time, model_fp16=args.mixed)
+    solver = qc.Solver(obs["data"], obs["model"], obs["weight"], obs["flag"], *geo, model_fp16=args.mixed)
+    allreduce = None
+    if world > 1:
+        from paper_2412_10072_gb300 import shard
+        allreduce = shard.allreduce_callback()
 
     def step():
-        terms = make_terms(qc, setup, setup.n_ant, args.max_iter)
+        terms = make_terms(qc, setup, setup.n_ant, args.max_iter, world, rank)
         return solver.solve(terms, n_epochs=args.epochs, stream=stream, kernel=args.kernel,
-                            block_threads=args.block), terms
+                            block_threads=args.block, allreduce=allreduce), terms
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -400,10 +443,10 @@ def main():
         torch.cuda.empty_cache()
 
         def e2e_step():
-            s = qc.Solver(host["data"], host["model"], host["weight"], host["flag"], setup.ant1, setup.ant2,
-                          setup.time_idx, setup.n_ant, setup.n_time, model_fp16=args.mixed)
-            terms = make_terms(qc, setup, setup.n_ant, args.max_iter)
-            st = s.solve(terms, n_epochs=args.epochs, kernel=args.kernel, block_threads=args.block)
+            s = qc.Solver(host["data"], host["model"], host["weight"], host["flag"], *geo, model_fp16=args.mixed)
+            terms = make_terms(qc, setup, setup.n_ant, args.max_iter, world, rank)
+            st = s.solve(terms, n_epochs=args.epochs, kernel=args.kernel, block_threads=args.block,
+                         allreduce=allreduce)
             s.close()
             d2h = sum(t.gains.nbytes + t.gain_flags.nbytes + t.iters.nbytes for t in terms)
             return st.vis_iters, d2h
@@ -420,16 +463,17 @@ def main():
         if dist is not None:
             t = torch.tensor([dt, float(vi)], dtype=torch.float64, device="cuda")
             dist.all_reduce(t[:1], op=dist.ReduceOp.MAX)
-            tv = t[1:].clone()
+            tv = torch.tensor([float(vi), float(h2d), float(res[0][1])], dtype=torch.float64, device="cuda")
             dist.all_reduce(tv)
-            dt, vi = float(t[0].item()), float(tv.item())
+            dt, vi = float(t[0].item()), float(tv[0].item())
+            h2d, res[0] = int(tv[1].item()), (res[0][0], int(tv[2].item()))
         e2e = {"value": vi / dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": res[0][1],
                "steps": args.e2e_steps, "note": "qc_create from pinned host buffers + qc_solve + gains D2H + qc_destroy"}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "c64+f16" if args.mixed else "c64", "data": "synthetic",
             "config": plain_config(args, world), "gen_s": round(t_gen, 2),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clock_info,
@@ -539,6 +583,84 @@ def run_delay(args):
             "gpu_launches": int(sum(s.launches for s in stats)), "accumulate_launches_with_work": int(acc_launches),
             "vis_iters": int(vis_iters), "iterations_max": int(max(s.n_iter_max for s in stats)),
             "initial_estimate_ms": init_ms}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# a single full-Jones term from per-(interval, pair) sums
+# ---------------------------------------------------------------------------
+
+MOMENTS_WORKLOAD = ("single full-Jones term G (1 t x 512 ch intervals) on the plain workload's data: 64 ant, "
+                    "300 t x 512 ch, 1 epoch, from per-(interval, pair) sums (qc_opts.moments) against the "
+                    "per-sample path")
+
+
+def run_moments(args):
+    """G alone solved from per-(interval, antenna pair) sums: one pass over the samples, then each
+    iteration on the sums.  Device-timed against the per-sample path on the same data; the pass's
+    bandwidth is the roofline (the iterations read 0.97 GB of sums, not the 25 GB of samples)."""
+    import torch
+    from paper_2412_10072_gb300 import qc, synth
+
+    torch.cuda.set_device(0)
+    setup = synth.plain_large_setup(seed=1, n_ant=args.n_ant, n_time=args.n_time, n_chan=args.n_chan,
+                                    flag_row_frac=0.1, n_src=50)
+    obs = synth.make_observation_device(setup, noise=0.05, noise_seed=1000, device="cuda:0")
+    torch.cuda.synchronize()
+    n_vis = obs["flag"].numel()
+    n_unflagged = int((obs["flag"] == 0).sum().item())
+    # the pass reads the folded weights of every sample and the data and model of usable ones
+    pass_bytes = 16 * n_vis + 64 * n_unflagged
+    stream = torch.cuda.Stream()
+    solver = qc.Solver(obs["data"], obs["model"], obs["weight"], obs["flag"], setup.ant1, setup.ant2,
+                       setup.time_idx, setup.n_ant, setup.n_time)
+    spec = setup.terms[0]
+
+    def timed(moments):
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                solver.solve([qc.Term.from_spec(spec, setup.n_ant, max_iter=args.max_iter, tol=1e-6)],
+                             stream=stream, moments=moments)
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            stats = [solver.solve([qc.Term.from_spec(spec, setup.n_ant, max_iter=args.max_iter, tol=1e-6)],
+                                  stream=stream, moments=moments) for _ in range(args.steps)]
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1), stats
+
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms, stats = timed(True)
+    clock_info = clocks.stop()
+    ms_plain, stats_plain = timed(False)
+    vis_iters = sum(s.vis_iters for s in stats)
+    pass_ms = sum(s.pass_ms for s in stats) / len(stats)
+    acc_ms = sum(s.acc_ms for s in stats) / len(stats)
+    iters = max(s.n_iter_max for s in stats)
+    peaks, peak_src = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = pass_bytes / (pass_ms / 1000.0) / 1e9 if pass_ms > 0 else None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": (achieved / hbm) if achieved else None, "traffic": None,
+                "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured"
+                else "fallback 6.8 TB/s",
+                "kernel": "mom_pass_kernel (the one pass forming the sums)",
+                "algorithmic_bytes_per_launch": pass_bytes, "launch_ms_mean": pass_ms,
+                "iteration_ms_mean": (acc_ms - pass_ms) / max(1, iters)}
+    line = {"metric": METRIC, "value": vis_iters / (ms / 1000.0), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": MOMENTS_WORKLOAD, "n_ant": args.n_ant, "n_time": args.n_time,
+                       "n_chan": args.n_chan, "max_iter": args.max_iter, "tol": 1e-6,
+                       "l2": "inputs (25 GB) larger than L2 (129 MB)", "parallelism": "1 GPU"},
+            "roofline": roofline, "cpu_baseline": None, "e2e": None, "clocks": clock_info,
+            "gpu_launches": int(sum(s.launches for s in stats)), "vis_iters": int(vis_iters),
+            "iterations_max": int(iters), "pass_ms": pass_ms,
+            "per_sample_path": {"value": sum(s.vis_iters for s in stats_plain) / (ms_plain / 1000.0),
+                                "ms_per_step": ms_plain / args.steps},
+            "speedup_over_per_sample_path": (ms_plain / ms) if ms else None}
     print(json.dumps(line), flush=True)
 
 
@@ -694,11 +816,15 @@ def _dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    local = local % max(1, torch.cuda.device_count())
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if args.dist_backend == "nccl":
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group("gloo")
     return world, rank, local, dist
 
 

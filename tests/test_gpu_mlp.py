@@ -195,3 +195,32 @@ def test_fused_fallback_restarts_worse_starts(ws):
     g2, _, _, st2 = S.solve(g0.clone(), fallback=(fb, chi_fb), tol=1e-7, max_iter=30, use_graph=True)
     assert st2.n_fallback == 2 and torch.allclose(g2, g, atol=1e-6)
     S.close()
+
+
+def test_committed_network_against_the_previous_interval_start(ws):
+    """Held-out (previous, current) interval pairs at 64 antennas, shaped as the warm-start
+    workload: mean iterations to a 1e-4 stopping tolerance from unit gains, from the previous
+    interval's solution, and from the committed network's prediction with the fused fallback to
+    the previous gains.  The previous-interval start must beat the cold start; the network arm
+    must not lose to it by more than a quarter iteration on average (a worse prediction restarts
+    from the previous gains inside the first pass).  The measured means are printed; on this
+    workload the network gains nothing over the previous-interval start."""
+    net = ws.MLP.load(ws.DEFAULT_CHECKPOINT)
+    shapes = synth.batch_shapes(256, seed_base=61000, ant=(64, 64))
+    prev_b, cur_b = synth.make_pair_batches(shapes, device="cuda")
+    Sp = qc.BatchSolver(prev_b.data, prev_b.model, prev_b.weight, prev_b.flag, prev_b.ant1, prev_b.ant2,
+                        prev_b.row_offset, prev_b.vis_offset, prev_b.n_chan, prev_b.n_ant)
+    gp, _, _, _ = Sp.solve(torch.ones((Sp.total_ant, 2), dtype=torch.complex64, device="cuda"), max_iter=50, tol=1e-8)
+    Sp.close()
+    S = qc.BatchSolver(cur_b.data, cur_b.model, cur_b.weight, cur_b.flag, cur_b.ant1, cur_b.ant2, cur_b.row_offset,
+                       cur_b.vis_offset, cur_b.n_chan, cur_b.n_ant)
+    unit = torch.ones((S.total_ant, 2), dtype=torch.complex64, device="cuda")
+    _, _, it_cold, _ = S.solve(unit.clone(), max_iter=60, tol=1e-4)
+    _, _, it_prev, _ = S.solve(gp.clone(), max_iter=60, tol=1e-4)
+    _, it_mlp, _, n_fb = ws.warm_solve(S, net, gp, max_iter=60, tol=1e-4)
+    S.close()
+    cold, prev, mlp = (float(x.float().mean()) for x in (it_cold, it_prev, it_mlp))
+    print(f"\nmean iterations to 1e-4 over {len(shapes)} held-out pairs: cold {cold:.2f}, previous interval "
+          f"{prev:.2f}, network {mlp:.2f} ({n_fb} fallbacks)")
+    assert prev < cold
+    assert mlp <= prev + 0.25

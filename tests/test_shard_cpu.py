@@ -123,3 +123,27 @@ def test_two_ranks_sum_to_the_single_process_normal_equations():
         # the spanning term: the sum over ranks equals the single-process sums (to FP64 reordering)
         np.testing.assert_allclose(buf, want_b, rtol=1e-12, atol=1e-12 * scale)
     assert res[0][3] == 0 and res[1][3] == res[0][4]
+
+
+def test_bench_shards_one_observation_by_time_block():
+    """The benchmark's multi-GPU mode: every rank takes a block of the one observation's times
+    (together all rows once), solves G on its own intervals and B over all of them with reduce."""
+    import bench
+    from paper_2412_10072_gb300 import qc
+    setup = synth.plain_large_setup(seed=1, n_ant=6, n_time=10, n_chan=8, flag_row_frac=0.1, n_src=3)
+    for world in (2, 3):
+        seen = []
+        g_ints = []
+        for rank in range(world):
+            sub, local_time, n_local = bench.shard_setup(setup, world, rank)
+            t0, t1 = shard.time_block(setup.n_time, rank, world)
+            assert n_local == t1 - t0 and np.all((local_time >= 0) & (local_time < n_local))
+            assert np.array_equal(sub.time_idx - t0, local_time)
+            seen.append(np.nonzero((setup.time_idx >= t0) & (setup.time_idx < t1))[0])
+            assert np.array_equal(sub.ant1, setup.ant1[seen[-1]]) and np.array_equal(sub.uvw, setup.uvw[seen[-1]])
+            G, B = bench.make_terms(qc, setup, setup.n_ant, 5, world, rank)
+            assert not G.reduce and G.n_tint == n_local and np.array_equal(G.t_map, np.arange(n_local))
+            assert B.reduce and B.n_tint == 1 and B.n_fint == 8
+            g_ints.append(G.n_tint)
+        assert np.array_equal(np.sort(np.concatenate(seen)), np.arange(setup.ant1.size))
+        assert sum(g_ints) == setup.n_time

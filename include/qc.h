@@ -506,6 +506,10 @@ int qc_batch_create(const qc_batch_problem *p, qc_batch **out);
  * FP64 block solve (Eq. update).  The CTA's warps stream contiguous runs of
  * 32-sample steps through per-warp rings of `depth` asynchronous-copy stages
  * in shared memory; flagged samples and autocorrelations are not read.
+ * A problem never spans CTAs: its time is bounded below by what one SM streams
+ * (about 1/152 of the device's bandwidth), so one problem of millions of
+ * samples among many small ones sets the launch's duration.  Such problems
+ * belong in qc_solve, which spreads an interval's samples over every SM.
  *   gains      : in/out [sum n_ant][2] complex64; read as g_0.
  *   gain_flags : out [sum n_ant] int8 or NULL (1: no data for the antenna).
  *   iters      : out [n_prob] int32 or NULL.

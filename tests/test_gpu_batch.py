@@ -159,7 +159,12 @@ def test_moments_solve_matches_the_sample_solve(m16):
         a = reference_diag(gains_of(b, g1, i)[good][None])[0]
         c = reference_diag(gains_of(b, g2, i)[good][None])[0]
         assert rel_err(c, a) < 1e-4, (i, rel_err(c, a))
-    assert np.abs(it1.astype(int) - it2.astype(int)).max() <= 2
+    d = np.abs(it1.astype(int) - it2.astype(int))
+    two = np.nonzero(d == 2)[0]
+    print(f"\niteration-count differences (sample vs moments, m16={m16}): "
+          f"{np.bincount(d, minlength=3).tolist()} for |d| = 0, 1, 2 ...; |d| = 2 at problems "
+          f"{[(int(i), int(it1[i]), int(it2[i])) for i in two]}")
+    assert d.max() <= 2 and two.size <= 2
     # one pass over the data instead of one per iteration
     assert s2.bytes * 2 < s2.vis_iters * 64
 
@@ -225,3 +230,44 @@ def test_autotune_chooses_a_shape_caches_it_per_shape_class_and_matches_oracle()
     _, _, _, st3 = S3.solve(use_graph=False)
     assert st3.threads == 256 and st3.split <= 0
     S3.close()
+
+
+def test_skewed_batch_one_large_problem():
+    """One problem of about 2e6 samples (64 antennas, 16 times x 62 channels) among 63 small ones:
+    the batched launch solves it correctly (the same gains as qc_solve's per-sample path on that
+    interval, the small ones against the oracle), and since a problem never spans CTAs the large
+    one sets the launch's duration (printed beside the launch without it)."""
+    import time
+    small = synth.batch_shapes(63, seed_base=1300, ant=(3, 10), times=(1, 3), chans=(1, 24), flag_max=0.3)
+    shapes = [(1299, 64, 16, 62, 0.1)] + list(small)
+    b = synth.make_batch(shapes)
+    S = solver_of(b)
+    t0 = time.perf_counter()
+    g, flags, iters, st = S.solve()
+    t_all = time.perf_counter() - t0
+    S.close()
+    rest = synth.make_batch(list(small))
+    S2 = solver_of(rest)
+    t0 = time.perf_counter()
+    S2.solve()
+    t_rest = time.perf_counter() - t0
+    S2.close()
+    print(f"\nskewed batch: {t_all * 1e3:.1f} ms with the 2e6-sample problem, {t_rest * 1e3:.1f} ms without")
+    # the large problem against qc_solve on the same interval
+    r1, v1 = int(b.row_offset[1]), int(b.vis_offset[1])
+    nc, na = int(b.n_chan[0]), int(b.n_ant[0])
+    rows = r1
+    one = qc.Solver(np.asarray(b.data[:v1]).reshape(rows, nc, 4).astype(np.complex64),
+                    np.asarray(b.model[:v1]).reshape(rows, nc, 4).astype(np.complex64),
+                    np.asarray(b.weight[:v1]).reshape(rows, nc, 4).astype(np.float32),
+                    np.asarray(b.flag[:v1]).reshape(rows, nc), b.ant1[:r1], b.ant2[:r1], np.zeros(rows, np.int32), na, 1)
+    t = qc.Term("diag", np.zeros(1, np.int32), np.zeros(nc, np.int32), 1, 1, na, max_iter=20, tol=1e-6)
+    one.solve([t], damping_mode=1)
+    one.close()
+    good = np.where(flags[:na] == 0)[0]
+    want = reference_diag(np.asarray(t.gains, np.complex128)[0, 0][good][None])[0]
+    got = reference_diag(gains_of(b, g, 0)[good][None])[0]
+    assert rel_err(got, want) < 1e-4
+    sub = synth.Batch(b.shapes[1:], b.data[v1:], b.model[v1:], b.weight[v1:], b.flag[v1:], b.ant1[r1:], b.ant2[r1:],
+                      b.row_offset[1:] - r1, b.vis_offset[1:] - v1, b.n_chan[1:], b.n_ant[1:], [], [])
+    compare(sub, g[na:], flags[na:], iters[1:])

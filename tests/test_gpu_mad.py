@@ -101,3 +101,43 @@ def test_per_baseline_flags_match_the_oracle_bit_for_bit(seed, threshold):
                                          threshold=threshold)
     np.testing.assert_array_equal(got, want)
     assert n == n_want and n > 0
+
+
+@pytest.mark.parametrize("threshold", [3.0, 5.0])
+def test_flags_after_a_solved_chain(threshold):
+    """After a solved two-term chain (G full, B diagonal) with planted outliers:
+    - bit for bit against the oracle's decision on the GPU's own residual at the solved gains
+      (qc_residual forms the same float32 residual as the flagger);
+    - against the oracle's FP64 residual at the same gains, rounded to complex64: median and MAD
+      agree to float32 rounding, and the flags differ only for samples whose deviation lies within
+      a relative 1e-4 of the threshold (float32 residual rounding decides those)."""
+    import oracle as O
+    from oracle.mad_flag import whitened_norm
+    obs = synth.plain_large(seed=8, n_ant=10, n_time=12, n_chan=40, noise=0.05, flag_row_frac=0.1, n_src=8)
+    rng = np.random.default_rng(8)
+    bad = rng.random(obs.flag.shape) < 0.005
+    obs.data[bad] += 2.0 * (rng.standard_normal((bad.sum(), 4)) + 1j * rng.standard_normal((bad.sum(), 4)))
+    S = qc.Solver.from_obs(obs)
+    terms = [qc.Term.from_spec(s, obs.n_ant, max_iter=20, tol=1e-6) for s in obs.terms]
+    S.solve(terms, n_epochs=2)
+    fixed = [qc.Term.from_spec(s, obs.n_ant, gains=np.asarray(t.gains).copy(), solve=False)
+             for s, t in zip(obs.terms, terms)]
+    got, n = S.mad_flag(fixed, threshold=threshold)
+    _, res = S.residual(fixed, want_resid=True)
+    S.close()
+    w32 = np.asarray(obs.weight, np.float32)
+    want, (med, mad, n_want) = mad_flag(res, w32, obs.flag, obs.ant1, obs.ant2, threshold=threshold)
+    np.testing.assert_array_equal(got, want)
+    assert n == n_want and n > 0
+    P = O.OracleProblem.from_obs(obs)
+    ot = [O.OracleTerm.from_spec(s, obs.n_ant, params=np.asarray(t.gains, np.complex128), solve=False)
+          for s, t in zip(obs.terms, fixed)]
+    _, ores = O.residual(P, ot, want_resid=True)
+    r64 = ores.astype(np.complex64)
+    w64, (med64, mad64, _) = mad_flag(r64, w32, obs.flag, obs.ant1, obs.ant2, threshold=threshold)
+    assert abs(float(med64) - float(med)) <= 1e-5 * float(med)
+    assert abs(float(mad64) - float(mad)) <= 1e-4 * float(mad)
+    dev = np.abs(whitened_norm(r64, w32) - med64)
+    thr = np.float32(threshold * 1.4826) * mad64
+    diff = got != w64
+    assert np.all(np.abs(dev[diff] - thr) <= 1e-4 * thr), int(diff.sum())

@@ -206,19 +206,25 @@ typedef struct {
 } qc_opts;
 
 /*
- * Sufficient statistics (not in the paper), opt-in with qc_opts.moments: when the
- * chain has a single diagonal, full or phase-only term (one direction, complex64
- * model), its gains are constant over each solution interval, so one pass over the
- * data forms per (interval, antenna pair) the gain-free sums
- *   S[kj][u][v] = sum w_kj conj(M_u) M_v,  T[kj][u] = sum w_kj conj(M_u) D_kj,
- *   U[kj] = sum w_kj |D_kj|^2
- * (kj = 2k + j the correlation, u = 2l + m the model entry), and every iteration
- * forms the 4x4 blocks of Eq. jhj_entry_simplified / Eq. jhr_entry_simplified from
- * them and the current gains (800 bytes per interval and pair instead of 81 per
- * sample).  Other chains, and sums of 2^31 or more (interval, pair) slots, ignore the
- * option.  qc_stats.vis_iters counts the samples of the active intervals per iteration as
- * without it; qc_stats.acc_bytes counts the pass (the samples' bytes, once) and, per
- * iteration and active interval, the sums read on both sides and the accumulators written.
+ * Sufficient statistics (not in the paper), opt-in with qc_opts.moments.  While one
+ * term is solved the other terms are fixed, so every sample of a baseline (p, q) in a
+ * solution interval enters Eq. jhj_entry_simplified and Eq. jhr_entry_simplified
+ * through sums that do not depend on the solved gains.  One pass over the data per
+ * term solve forms them per (interval, antenna pair); every iteration forms the blocks
+ * from the sums and the current gains.  Two forms (chains of one or two terms, one
+ * direction, complex64 model, the solved term not a delay term):
+ *  - full form, the solved term (any kind) has no term to its left: with
+ *    X = R_p M R_q^H (R the term to its right, X = M without one), per correlation kj
+ *    S[kj][u][v] = sum w_kj conj(X_u) X_v, T[kj][u] = sum w_kj conj(X_u) D_kj,
+ *    U[kj] = sum w_kj |D_kj|^2 (800 bytes per interval and pair);
+ *  - diagonal form, a diagonal or phase-only solved term with a term L to its left:
+ *    with E_kj,ab = L_p,ka M_ab conj(L_q,jb), S'[u][v] = sum sum_kj w_kj conj(E_kj,u)
+ *    E_kj,v, T'[u] = sum sum_kj w_kj conj(E_kj,u) D_kj (208 bytes per interval and pair).
+ * Other solves (a full-Jones term with a term to its left, longer chains, sums of 2^31
+ * or more slots) ignore the option.  qc_stats.vis_iters counts the samples of the
+ * active intervals per iteration as without it; qc_stats.acc_bytes counts the pass (the
+ * samples' bytes, once) and, per iteration and active interval, the sums read on both
+ * sides and the accumulators written; qc_stats.pass_ms the passes' device time.
  */
 
 /*

@@ -324,7 +324,7 @@ extern "C" int qc_create(const qc_problem *p, qc_ctx **out)
     if (!strip_rows.empty()) HCOPY(c->d_strip_rows, strip_rows.data(), nbytes<int>(strip_rows.size()));
     {
         // unordered antenna pairs: both orientations of a baseline share one slot of the sums
-        // of a single-term chain (qc_opts.moments)
+        // of a term solved from sums (qc_opts.moments)
         std::vector<int> upair((size_t)na * na, -1), up_of_bl(std::max(1, n_bl), 0);
         int n_up = 0;
         for (int a1 = 0; a1 < na; ++a1)
@@ -1057,10 +1057,17 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
     const bool ddp = n_dir > 1;
     const int nat = term_nat(t);
     if (!L.fn && !ddp) return fail(QC_EUNSUPPORTED, "no accumulate kernel for this chain");
-    // a single-term chain from per-(interval, baseline) sums (qc_moments.cu): one pass over the
-    // data, then every iteration forms the blocks from the sums and the current gains
-    const bool mom = o->moments && n_terms == 1 && !delay[n] && !ddp && d_model != nullptr && n_up > 0 &&
-                     (size_t)nb * n_up < (size_t)INT32_MAX;
+    // the term from per-(interval, pair) sums (qc_moments.cu): one pass over the data, then
+    // every iteration forms the blocks from the sums and the current gains.  No term to the
+    // left: the full form, the term to the right folded into the model; a diagonal or phase-only
+    // term with a term to its left: the diagonal form
+    int mom_form = -1, mom_ok = KIND_NONE;
+    if (o->moments && n_terms <= 2 && !delay[n] && !ddp && d_model != nullptr && n_up > 0 &&
+        (size_t)nb * n_up < (size_t)INT32_MAX) {
+        if (lk == KIND_NONE) { mom_form = FORM_FULL; mom_ok = rk; }
+        else if (t.type != QC_TERM_FULL) { mom_form = FORM_E; mom_ok = lk; }
+    }
+    const bool mom = mom_form >= 0;
     // pipelined kernel: shared-memory layout of the per-warp rings for this chain
     PipeArgs pa;
     memset(&pa, 0, sizeof pa);
@@ -1405,17 +1412,19 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
         dua.tol = ua.tol;
     }
 
-    // sums of a single-term chain: [bins][unordered pairs][MOM_N] FP64, then the per-bin bytes
-    // of one iteration for the byte counter
+    // sums of the term solve: [bins][unordered pairs][MOM_N or MOM_E] FP64, the per-bin bytes of
+    // one iteration for the byte counter, then the pass's row table
     MomArgs ma;
     MomNormArgs mn;
     memset(&ma, 0, sizeof ma);
     memset(&mn, 0, sizeof mn);
-    const size_t mom_words_all = (size_t)nb * n_up * MOM_N;
+    const int mom_n = mom_form == FORM_E ? MOM_E : MOM_N;
+    const size_t mom_words_all = mom ? (size_t)nb * n_up * mom_n : 0;
     const size_t mom_rows_off = ((nbytes<double>(mom_words_all) + nbytes<long long>(nb) + 15) / 16) * 16;
     if (mom) {
         if ((rc = ensure(B.mom, mom_rows_off + nbytes<int4>(std::max(1L, n_strip_rows))))) return rc;
         ma.n_chan = n_chan;
+        ma.n_ant = n_ant;
         ma.n_up = n_up;
         ma.vis = d_vis;
         ma.model = d_model;
@@ -1423,20 +1432,27 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
         ma.mrows = (const int4 *)((char *)B.mom.ptr + mom_rows_off);
         ma.strip_off = d_strip_off;
         ma.n_strips = n_strips;
-        ma.n_chunks = (n_chan + 15) / 16;
-        // chunk groups as wide as leave about four units per resident warp (three CTAs of four
-        // warps per SM): an interval wider than a chunk then flushes once per row and group
-        {
+        ma.n_chunks = mom_form == FORM_FULL ? (n_chan + 15) / 16 : (n_chan + 31) / 32;
+        // an interval several times long: the rows inside each chunk keep a lane's key; else a
+        // row's chunks inside each row, in groups as wide as leave about four units per
+        // resident warp (three CTAs of four warps per SM), so that an interval wider than a
+        // chunk flushes once per row and group
+        ma.chunk_major = t.n_tint < n_time ? 1 : 0;
+        if (ma.chunk_major) {
+            ma.group = 1;
+        } else {
             const long want_units = 4L * sm_count * 12;
             const long per_strip = std::max(1L, (want_units + std::max(1, n_strips) - 1) / std::max(1, n_strips));
             ma.group = (int)std::max(1L, (long)ma.n_chunks / per_strip);
         }
         ma.tn = chain.t[n];
+        ma.to = n_terms == 2 ? chain.t[1 - n] : chain.t[n];
         ma.mom = (double *)B.mom.ptr;
         mn.n_bins = nb;
         mn.n_ant = n_ant;
         mn.n_up = n_up;
         mn.type = t.type;
+        mn.form = mom_form;
         mn.upair = d_upair;
         mn.mom = ma.mom;
         mn.params = (const double *)B.params.ptr;
@@ -1444,7 +1460,7 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
         mn.acc = (double *)B.acc.ptr;
         ua.bin_nbytes = (const long long *)(ma.mom + mom_words_all);
     }
-    const long long mom_iter_bytes = 2LL * n_up * MOM_N * 8 + 8LL * n_ant * (t.type == 1 ? KG_FULL : KG_DIAG);
+    const long long mom_iter_bytes = 2LL * n_up * mom_n * 8 + 8LL * n_ant * (t.type == 1 ? KG_FULL : KG_DIAG);
 
     const int max_iter = t.max_iter;
     for (int k = 0; k < 2 * max_iter + 2; ++k) { cudaEvent_t ev; if ((rc = get_event(2 + k, ev))) return rc; }
@@ -1479,11 +1495,11 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
                     CK(cudaMemsetAsync(B.mom.ptr, 0, nbytes<double>(mom_words_all), st));
                     CK(mom_launch_bytes(nb, (const long long *)B.nvis.ptr + 2 * (size_t)nb, mom_iter_bytes,
                                         (long long *)(ma.mom + mom_words_all), ua.acc_bytes, st));
-                    CK(mom_launch_rows(n_strip_rows, d_strip_rows, d_rows, d_row_live, chain.t[n].t_map,
-                                       chain.t[n].n_fint, d_up_of_bl, const_cast<int4 *>(ma.mrows), st));
+                    CK(mom_launch_rows(n_strip_rows, d_strip_rows, d_rows, d_row_live, d_up_of_bl,
+                                       const_cast<int4 *>(ma.mrows), st));
                     CK(cudaEventRecordWithFlags(events[ev_pass], st, rec_flags));
                     ma.n_active = cnt;
-                    CK(mom_launch_pass(ma, sm_count, st));
+                    CK(mom_launch_pass(ma, mom_form, mom_ok, sm_count, st));
                     CK(cudaEventRecordWithFlags(events[ev_pass + 1], st, rec_flags));
                 }
                 mn.n_active = cnt + (k - 1);

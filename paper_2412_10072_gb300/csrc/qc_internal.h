@@ -42,13 +42,13 @@ struct DDArgs {
 } // namespace qc
 cudaError_t dd_launch_acc(const qc::DDArgs &a, int ts, int grid_x, cudaStream_t st);
 // Single-term chains from per-(interval, baseline) sums (qc_moments.cu).
-cudaError_t mom_launch_pass(const qc::MomArgs &a, int sm_count, cudaStream_t st);
+cudaError_t mom_launch_pass(const qc::MomArgs &a, int form, int ok, int sm_count, cudaStream_t st);
 cudaError_t mom_launch_normal(const qc::MomNormArgs &a, cudaStream_t st);
-cudaError_t mom_launch_rows(long n, const int *strip_rows, const int4 *rows, const uint8_t *row_live, const int *t_map,
-                            int n_fint, const int *up_of_bl, int4 *out, cudaStream_t st);
 cudaError_t mom_launch_bytes(int n_bins, const long long *bin_nbytes, long long per_iter, long long *iter_nbytes,
                              unsigned long long *acc_bytes, cudaStream_t st);
-size_t mom_words();
+cudaError_t mom_launch_rows(long n, const int *strip_rows, const int4 *rows, const uint8_t *row_live,
+                            const int *up_of_bl, int4 *out, cudaStream_t st);
+size_t mom_words(int form);
 cudaError_t dd_launch_residual(const qc::DDArgs &a, int grid, cudaStream_t st);
 
 struct Buf {

@@ -1,29 +1,37 @@
-// qc_moments.cu -- sufficient statistics for a single-term chain (the solve from per-baseline
-// sums; not in the paper).
+// qc_moments.cu -- the solve of one term from per-(interval, antenna pair) sums (not in the paper).
 //
-// When the solved term is the only term of the chain, its gains are constant over each
-// solution interval, so every sample of a baseline (p, q) in an interval enters J^H W J and
-// J^H W r (Eq. jhj_entry_simplified, Eq. jhr_entry_simplified) through gain-free sums of that
-// (interval, baseline).  With the weight index kj = 2k + j of correlation (k, j) and the
-// row-major index u = 2l + m of the model entry M_lm (rows with p > q through their conjugate
-// baseline, so the sums are kept per unordered pair p < q):
-//     S[kj][u][v] = sum w_kj conj(M_u) M_v   (Hermitian; 16 reals per kj)
-//     T[kj][u]    = sum w_kj conj(M_u) D_kj   (16 complex)
-//     U[kj]       = sum w_kj |D_kj|^2          (4 reals)
-// one pass over the data forms them (mom_pass_kernel: FP32 per lane, FP64 sums), and every
-// iteration forms each antenna's 4x4 block from them and the current gains in FP32, with
-// JHr = b - JHJ vec(G) and everything after it in FP64 (mom_normal_kernel):
+// While one term of a chain is solved the others are fixed, so every sample of a baseline
+// (p, q) in a solution interval enters J^H W J and J^H W r (Eq. jhj_entry_simplified,
+// Eq. jhr_entry_simplified) through sums that do not depend on the solved gains.  The sums are
+// kept per unordered pair p < q (a row with ant1 > ant2 enters through its conjugate baseline:
+// D -> D^H, M -> M^H, the cross-hand weights swapped, p and q exchanged); kj = 2k + j indexes the
+// weight and data of correlation (k, j).
+//
+// Full form: the solved term G (any kind) has no term to its left.  With X = R_p M R_q^H, R the
+// term to its right (X = M when there is none), and u = 2l + m indexing X_lm:
+//     S[kj][u][v] = sum w_kj conj(X_u) X_v,  T[kj][u] = sum w_kj conj(X_u) D_kj,
+//     U[kj] = sum w_kj |D_kj|^2                                               (100 words)
 //     JHJ_p[(k,l),(k,l')] += sum_j sum_m sum_m' G_q,jm conj(G_q,jm') S[kj][(l,m)][(l',m')]
 //     b_p[(k,l)]          += sum_j sum_m G_q,jm T[kj][(l,m)]
 //     JHJ_q[(k,l),(k,l')] += sum_j sum_m sum_m' G_p,jm conj(G_p,jm') conj(S[jk][(m,l)][(m',l')])
 //     b_q[(k,l)]          += sum_j sum_m G_p,jm conj(T[jk][(m,l)])
-//     JHr = b - JHJ vec(G)
-// written in the accumulator layout of the update kernel (a diagonal or phase-only term takes
-// the (0, 3) rows and columns).  An iteration then reads 800 B per (interval, baseline)
-// instead of 81 B per sample.
+// Diagonal form: the solved term g (diagonal or phase-only) has a term L to its left.  With
+// E_kj,ab = L_p,ka M_ab conj(L_q,jb) and u = 2a + b:
+//     S'[u][v] = sum sum_kj w_kj conj(E_kj,u) E_kj,v,  T'[u] = sum sum_kj w_kj conj(E_kj,u) D_kj,
+//     U = sum sum_kj w_kj |D_kj|^2                                            (25 words)
+//     JHJ_p[a][a'] += sum_b sum_b' g_q,b conj(g_q,b') S'[(a,b)][(a',b')],  b_p[a] += sum_b g_q,b T'[(a,b)]
+//     JHJ_q[b][b'] += sum_a sum_a' g_p,a conj(g_p,a') conj(S'[(a,b)][(a',b')]),
+//     b_q[b]       += sum_a g_p,a conj(T'[(a,b)])
+// In both forms JHr = b - JHJ vec(g).  One pass over the data per term solve forms the sums
+// (mom_pass_kernel: FP32 per lane, FP64 sums); every iteration forms each antenna's blocks from
+// them and the current gains in FP32 (mom_normal_kernel), JHr = b - JHJ g and everything after
+// it in FP64, in the update kernel's accumulator layout (a diagonal or phase-only term of the
+// full form takes the (0, 3) rows and columns).  An iteration then reads 800 or 208 B per
+// (interval, pair) instead of 81 B per sample.
 #include "qc_internal.h"
 
 #include <algorithm>
+#include <type_traits>
 
 namespace qc {
 
@@ -41,8 +49,9 @@ __device__ __forceinline__ int mom_word(int i, int k)
                   : (i < 48 ? MOM_T + 8 * (2 * k + (i - 32) / 8) + (i - 32) % 8 : MOM_U + 2 * k + (i - 48));
 }
 
-// One sample's terms for correlation row k added to a lane's register sums (all indices
-// compile-time constants after unrolling; k selects the data row and the weights).
+// One sample's terms for correlation row k added to a lane's register sums, full form (all
+// indices compile-time constants after unrolling; k selects the data row and the weights; M is
+// the sample's X = R_p M R_q^H).
 __device__ __forceinline__ void mom_add(float (&acc)[MOM_H], const J2 &D, const J2 &M, float4 w, int k)
 {
     const float2 m[4] = { M.a, M.b, M.c, M.d };
@@ -78,78 +87,148 @@ __device__ __forceinline__ void mom_add(float (&acc)[MOM_H], const J2 &D, const 
     }
 }
 
-// Add the warp's register sums to the FP64 sums of each lane pair's key (-1: nothing) and zero
-// them.  Lanes of one parity hold the same words, so every reduction runs over lane offsets
-// 2, 4, 8, 16:
-//  - one key for the warp (an interval at least 16 channels wide): a reduce-scatter (words
-//    padded to 64; after halving at offsets 16, 8, 4, 2 lane L holds words 4 (L >> 1) .. + 3),
-//    then one atomic per word;
-//  - 16 distinct keys: each lane adds its own words;
-//  - otherwise: a segmented reduction per word over the run of equal keys (channel intervals
-//    are contiguous, so a run is a range of lanes), added by the run's first lane pair.
-__device__ __forceinline__ void mom_flush(float (&acc)[MOM_H], int key, int lane, double *mom)
+// The diagonal form, one lane per sample: register words [0, 16) S' packed as the full form's
+// S blocks, [16, 24) T', 24 U.
+constexpr int MOM_EW = 25;
+
+template <int LK>
+__device__ __forceinline__ void mom_add_e(float (&acc)[MOM_EW], const J2 &D, const J2 &M, const J2 &Lp,
+                                          const J2 &Lq, float4 w)
 {
-    const int k = lane & 1;
+    const float2 m[4] = { M.a, M.b, M.c, M.d };       // M_ab at 2a + b
+    const float2 lp[4] = { Lp.a, Lp.b, Lp.c, Lp.d };  // L_p,ka at 2k + a
+    const float2 lq[4] = { Lq.a, Lq.b, Lq.c, Lq.d };
+    const float2 d[4] = { D.a, D.b, D.c, D.d };
+    const float wv[4] = { w.x, w.y, w.z, w.w };
+#pragma unroll
+    for (int kj = 0; kj < 4; ++kj) {
+        const int k = kj >> 1, j = kj & 1;
+        if constexpr (LK == KIND_DIAG) {
+            // E_kj,ab is non-zero only at (a, b) = (k, j): S' stays diagonal
+            const float2 e = cmulc(cmul(lp[3 * k], m[kj]), lq[3 * j]);
+            acc[kj] = fmaf(wv[kj], cnorm2(e), acc[kj]);
+            const float2 c = cmulc(cscale(d[kj], wv[kj]), e);           // conj(e) w d
+            acc[16 + 2 * kj] += c.x;
+            acc[17 + 2 * kj] += c.y;
+        } else {
+            // sqrt(w) E_kj: S' += conj(e_u) e_v, T' += conj(e_u) sqrt(w) d
+            const float sw = sqrtf(wv[kj]);
+            float2 e[4];
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int b = 0; b < 2; ++b)
+                    e[2 * a + b] = cscale(cmul(lp[2 * k + a], cmulc(m[2 * a + b], lq[2 * j + b])), sw);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[u] = fmaf(e[u].x, e[u].x, fmaf(e[u].y, e[u].y, acc[u]));
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = u + 1; v < 4; ++v) {
+                    const float2 c = cmulc(e[v], e[u]);                 // conj(e_u) e_v
+                    acc[4 + 2 * mom_pair(u, v)] += c.x;
+                    acc[5 + 2 * mom_pair(u, v)] += c.y;
+                }
+            const float2 ds = cscale(d[kj], sw);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float2 c = cmulc(ds, e[u]);
+                acc[16 + 2 * u] += c.x;
+                acc[17 + 2 * u] += c.y;
+            }
+        }
+        acc[24] = fmaf(wv[kj], cnorm2(d[kj]), acc[24]);
+    }
+}
+
+// register word -> word of the slot: full form (two lanes per sample, part k = lane & 1), and
+// the diagonal form (one lane per sample, the same order)
+struct FullWord {
+    __device__ __forceinline__ int operator()(int i, int k) const { return mom_word(i, k); }
+};
+struct DiagWord {
+    __device__ __forceinline__ int operator()(int i, int) const { return i; }
+};
+
+// Add the warp's register sums to the FP64 sums of each key (-1: nothing) and zero them.  LPS
+// lanes share a sample (lanes of one part hold the same words), so every reduction runs over
+// lane offsets LPS .. 16:
+//  - one key for the warp: a reduce-scatter (NW words padded to P = a power of two; after the
+//    halvings at offsets 16 .. LPS lane L holds words F (L / LPS) .. + F - 1, F = P LPS / 32),
+//    then one atomic per word;
+//  - a distinct key per sample: each lane adds its own words;
+//  - otherwise: a segmented reduction per word over the run of equal keys (channel intervals
+//    are contiguous, so a run is a range of lanes), added by the run's first sample.
+template <int NW, int LPS, typename WordOf>
+__device__ __forceinline__ void mom_flush(float (&acc)[NW], int key, int lane, double *mom, int stride, WordOf word)
+{
+    constexpr int P = NW <= 32 ? 32 : (NW <= 64 ? 64 : 128);
+    constexpr int F = P * LPS / 32;
+    const int k = lane & (LPS - 1);
     const int k0 = __shfl_sync(FULL_MASK, key, 0);
     if (__all_sync(FULL_MASK, key == k0)) {
         if (k0 >= 0) {
             // in place: after the halving at offset o the live words are acc[0 .. h)
 #pragma unroll
-            for (int h = 32, o = 16; h >= 4; h >>= 1, o >>= 1) {
+            for (int h = P / 2, o = 16; o >= LPS; h >>= 1, o >>= 1) {
                 const bool up = (lane & o) != 0;
 #pragma unroll
                 for (int i = 0; i < h; ++i) {
-                    const float lo = acc[i];
-                    const float hi = i + h < MOM_H ? acc[i + h] : 0.f;
+                    const float lo = i < NW ? acc[i] : 0.f;
+                    const float hi = i + h < NW ? acc[i + h] : 0.f;
                     const float send = up ? lo : hi;
                     const float keep = up ? hi : lo;
-                    acc[i] = keep + __shfl_xor_sync(FULL_MASK, send, o);
+                    if (i < NW) acc[i] = keep + __shfl_xor_sync(FULL_MASK, send, o);
                 }
             }
-            double *dst = mom + (size_t)k0 * MOM_N;
-            const int base = 4 * (lane >> 1);
+            double *dst = mom + (size_t)k0 * stride;
+            const int base = F * (lane / LPS);
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (base + j < MOM_H) atomicAdd(dst + mom_word(base + j, k), (double)acc[j]);
+            for (int j = 0; j < F; ++j)
+                if (base + j < NW) atomicAdd(dst + word(base + j, k), (double)acc[j]);
         }
     } else {
         const unsigned m = __match_any_sync(FULL_MASK, key);
-        if (__all_sync(FULL_MASK, m == (3u << (lane & ~1)))) {
+        const unsigned own = ((1u << LPS) - 1u) << (lane & ~(LPS - 1));
+        if (__all_sync(FULL_MASK, m == own)) {
             if (key >= 0) {
-                double *dst = mom + (size_t)key * MOM_N;
+                double *dst = mom + (size_t)key * stride;
 #pragma unroll
-                for (int v = 0; v < MOM_H; ++v) atomicAdd(dst + mom_word(v, k), (double)acc[v]);
+                for (int v = 0; v < NW; ++v) atomicAdd(dst + word(v, k), (double)acc[v]);
             }
         } else {
             const int seg_end = 32 - __clz(m);
-            const bool head = (lane >> 1) == ((__ffs(m) - 1) >> 1);
-            double *dst = mom + (size_t)(key >= 0 ? key : 0) * MOM_N;
+            const bool head = (lane / LPS) == ((__ffs(m) - 1) / LPS);
+            double *dst = mom + (size_t)(key >= 0 ? key : 0) * stride;
 #pragma unroll
-            for (int v = 0; v < MOM_H; ++v) {
+            for (int v = 0; v < NW; ++v) {
                 float x = acc[v];
 #pragma unroll
-                for (int d = 2; d < 32; d <<= 1) {
+                for (int d = LPS; d < 32; d <<= 1) {
                     const float o = __shfl_down_sync(FULL_MASK, x, d);
                     if (lane + d < seg_end) x += o;
                 }
-                if (head && key >= 0) atomicAdd(dst + mom_word(v, k), (double)x);
+                if (head && key >= 0) atomicAdd(dst + word(v, k), (double)x);
             }
         }
     }
 #pragma unroll
-    for (int v = 0; v < MOM_H; ++v) acc[v] = 0.f;
+    for (int v = 0; v < NW; ++v) acc[v] = 0.f;
 }
 
 // The rows of the baseline strips in strip order, as the pass reads them: {row (-1: no usable
-// sample), first bin of the row's time interval, unordered pair, 1 if ant1 > ant2}.
+// sample), time, pair | conj << 31, p | q << 16} with (p, q) the baseline as the sums orient it.
 static __global__ void mom_rows_kernel(long n, const int *strip_rows, const int4 *rows, const uint8_t *row_live,
-                                       const int *t_map, int n_fint, const int *up_of_bl, int4 *out)
+                                       const int *up_of_bl, int4 *out)
 {
     const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int row = strip_rows[k];
     const int4 r = rows[row];
-    out[k] = make_int4(row_live[row] ? row : -1, t_map[r.z] * n_fint, up_of_bl[r.w], r.x > r.y ? 1 : 0);
+    const bool conj = r.x > r.y;
+    const int p = conj ? r.y : r.x, q = conj ? r.x : r.y;
+    out[k] = make_int4(row_live[row] ? row : -1, r.z, (int)((unsigned)up_of_bl[r.w] | (conj ? 0x80000000u : 0u)),
+                       p | (q << 16));
 }
 
 // a streamed 16-byte load: read-only for the kernel's lifetime, not kept in L1
@@ -161,94 +240,150 @@ __device__ __forceinline__ float4 ld_stream(const float4 *p)
     return r;
 }
 
-// one sample as loaded: its key, folded weights and the raw data and model quads
+// one sample as loaded: its key, folded weights, the raw data and model quads, and the fixed
+// term's table entries for p ([0, 2)) and q ([2, 4))
 struct MomSample {
     int key;
     float4 w, d0, d1, m0, m1;
+    float4 o[4];
 };
 
-__device__ __forceinline__ MomSample mom_load(const MomArgs &a, const int4 &mr, int ch, int lane)
+template <int K>
+__device__ __forceinline__ void fac_load(const DevTerm &T, int n_ant, int ti, int fi, int ant, float4 *o)
+{
+    const size_t idx = ((size_t)ti * n_ant + ant) * T.n_fint + fi;
+    if constexpr (K == KIND_FULL) {
+        o[0] = __ldg(T.tab + 2 * idx);
+        o[1] = __ldg(T.tab + 2 * idx + 1);
+    } else if constexpr (K == KIND_DIAG) {
+        o[0] = __ldg(T.tab + idx);
+    }
+}
+
+template <int K>
+__device__ __forceinline__ J2 fac_jones(const float4 *o)
+{
+    if constexpr (K == KIND_FULL) return j_from(o[0], o[1]);
+    else if constexpr (K == KIND_DIAG) return j_diag(o[0]);
+    else return j_identity();
+}
+
+template <int CW, int OK>
+__device__ __forceinline__ MomSample mom_load(const MomArgs &a, const int4 &mr, int ch, int lane_ch)
 {
     MomSample x;
-    const int c = ch * 16 + (lane >> 1);
-    x.key = c < a.n_chan ? (mr.y + __ldg(a.tn.f_map + c)) * a.n_up + mr.z : -1;
-    if (c < a.n_chan && mr.x >= 0) {
+    const int c = ch * CW + lane_ch;
+    const bool in = c < a.n_chan;
+    x.key = in ? (__ldg(a.tn.t_map + mr.y) * a.tn.n_fint + __ldg(a.tn.f_map + c)) * a.n_up + (mr.z & 0x7fffffff)
+               : -1;
+    if (in && mr.x >= 0) {
         const size_t i = (size_t)mr.x * a.n_chan + c;
         x.w = ld_stream(a.wf + i);
         x.d0 = ld_stream(a.vis + 2 * i);
         x.d1 = ld_stream(a.vis + 2 * i + 1);
         x.m0 = ld_stream(a.model + 2 * i);
         x.m1 = ld_stream(a.model + 2 * i + 1);
+        if constexpr (OK != KIND_NONE) {
+            const int ti = __ldg(a.to.t_map + mr.y), fi = __ldg(a.to.f_map + c);
+            fac_load<OK>(a.to, a.n_ant, ti, fi, mr.w & 0xffff, x.o);
+            fac_load<OK>(a.to, a.n_ant, ti, fi, mr.w >> 16, x.o + 2);
+        }
     } else {
         x.w = make_float4(0.f, 0.f, 0.f, 0.f);
         x.d0 = x.d1 = x.m0 = x.m1 = x.w;
+        if constexpr (OK != KIND_NONE) x.o[0] = x.o[1] = x.o[2] = x.o[3] = x.w;
     }
     return x;
 }
 
 // One pass: warps walk units of a baseline strip (the rows of one ordered baseline in time
-// order) x a group of 16-channel chunks, row by row and chunk by chunk within a row, with the
-// next sample's loads in flight while the current one is added to the lane's register sums.
-// The sums are flushed when any lane's (interval, pair) key changes, so an interval that spans
-// the group's chunks is flushed once per row.
-static __global__ void __launch_bounds__(128, 3) mom_pass_kernel(const MomArgs a)
+// order) x a group of chunks (16 channels in the full form, two lanes per sample; 32 in the
+// diagonal form), a row's chunks inside each row or, with chunk_major, the rows inside each
+// chunk (an interval several times long then keeps its keys), with the next sample's loads in
+// flight while the current one is added to the lane's register sums.  The sums are flushed when
+// any lane's (interval, pair) key changes.  The fixed term is L (diagonal form) or R (full form)
+// of kind OK.
+template <int FORM, int OK>
+constexpr int mom_pass_ctas() { return (FORM == FORM_FULL && OK != KIND_NONE) ? 2 : 3; }
+
+template <int FORM, int OK>
+static __global__ void __launch_bounds__(128, mom_pass_ctas<FORM, OK>()) mom_pass_kernel(const MomArgs a)
 {
+    constexpr int LPS = FORM == FORM_FULL ? 2 : 1;
+    constexpr int NW = FORM == FORM_FULL ? MOM_H : MOM_EW;
+    constexpr int CW = 32 / LPS;
     if (__ldg(a.n_active) == 0) return;
-    const int lane = threadIdx.x & 31;
-    float acc[MOM_H];
+    const int lane = threadIdx.x & 31, lane_ch = lane / LPS;
+    const int stride = FORM == FORM_FULL ? MOM_N : MOM_E;
+    using Word = typename std::conditional<FORM == FORM_FULL, FullWord, DiagWord>::type;
+    float acc[NW];
 #pragma unroll
-    for (int v = 0; v < MOM_H; ++v) acc[v] = 0.f;
+    for (int v = 0; v < NW; ++v) acc[v] = 0.f;
     const long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long n_warps = ((long)gridDim.x * blockDim.x) >> 5;
     const int n_groups = (a.n_chunks + a.group - 1) / a.group;
     const long n_units = (long)a.n_strips * n_groups;
+    const bool cm = a.chunk_major != 0;
     int cur = -1;
     for (long unit = warp; unit < n_units; unit += n_warps) {
         const int s = (int)(unit / n_groups), g = (int)(unit % n_groups);
         const int ch0 = g * a.group, ch1 = min(a.n_chunks, ch0 + a.group);
-        const int k1 = __ldg(a.strip_off + s + 1);
-        int k = __ldg(a.strip_off + s), ch = ch0;
-        if (k >= k1) continue;
-        int4 mr = __ldg(a.mrows + k);
-        int4 mr_next = k + 1 < k1 ? __ldg(a.mrows + k + 1) : make_int4(-1, 0, 0, 0);
-        MomSample cs = mom_load(a, mr, ch, lane);
-        int conj = mr.w;
+        const int k0 = __ldg(a.strip_off + s), k1 = __ldg(a.strip_off + s + 1);
+        if (k0 >= k1) continue;
+        // the unit's steps (row k, chunk ch) in its order
+        auto adv = [&](int &k, int &ch) {
+            if (cm) { if (++k == k1) { k = k0; ++ch; } }
+            else { if (++ch == ch1) { ch = ch0; ++k; } }
+        };
+        auto valid = [&](int k, int ch) { return cm ? ch < ch1 : k < k1; };
+        int k2 = k0, ch2 = ch0;
+        adv(k2, ch2);
+        int ch = ch0;
+        int4 mr = __ldg(a.mrows + k0);
+        int4 mr2 = valid(k2, ch2) ? __ldg(a.mrows + k2) : make_int4(-1, 0, 0, 0);
+        MomSample cs = mom_load<CW, OK>(a, mr, ch, lane_ch);
         while (true) {
-            // the next step (chunk by chunk, then the next row) and its loads
-            int k2 = k, ch2 = ch + 1;
-            int4 mr2 = mr;
-            if (ch2 == ch1) {
-                ch2 = ch0;
-                ++k2;
-                mr2 = mr_next;
-                if (k2 + 1 < k1) mr_next = __ldg(a.mrows + k2 + 1);
-            }
             if (__any_sync(FULL_MASK, cs.key != cur)) {
-                mom_flush(acc, cur, lane, a.mom);
+                mom_flush<NW, LPS>(acc, cur, lane, a.mom, stride, Word());
                 cur = cs.key;
             }
-            const bool more = k2 < k1;
+            const bool more = valid(k2, ch2);
+            int k3 = k2, ch3 = ch2;
+            adv(k3, ch3);
+            int4 mr3 = make_int4(-1, 0, 0, 0);
             MomSample ns;
-            if (more) ns = mom_load(a, mr2, ch2, lane);
+            if (more) {
+                if (valid(k3, ch3)) mr3 = __ldg(a.mrows + k3);
+                ns = mom_load<CW, OK>(a, mr2, ch2, lane_ch);
+            }
             if (cs.w.x != 0.f || cs.w.y != 0.f || cs.w.z != 0.f || cs.w.w != 0.f) {
                 J2 D = j_from(cs.d0, cs.d1), M = j_from(cs.m0, cs.m1);
                 float4 w = cs.w;
-                if (conj) {                      // the conjugate baseline: D -> D^H, M -> M^H, w permuted
+                if (mr.z < 0) {                  // the conjugate baseline: D -> D^H, M -> M^H, w permuted
                     D = j_herm(D);
                     M = j_herm(M);
                     w = make_float4(w.x, w.z, w.y, w.w);
                 }
-                mom_add(acc, D, M, w, lane & 1);
+                if constexpr (FORM == FORM_FULL) {
+                    if constexpr (OK == KIND_DIAG)
+                        M = j_muld(j_dmul(make_float2(cs.o[0].x, cs.o[0].y), make_float2(cs.o[0].z, cs.o[0].w), M),
+                                   make_float2(cs.o[2].x, -cs.o[2].y), make_float2(cs.o[2].z, -cs.o[2].w));
+                    else if constexpr (OK == KIND_FULL)
+                        M = j_mul_h(j_mul(fac_jones<OK>(cs.o), M), fac_jones<OK>(cs.o + 2));
+                    mom_add(acc, D, M, w, lane & 1);
+                } else {
+                    mom_add_e<OK>(acc, D, M, fac_jones<OK>(cs.o), fac_jones<OK>(cs.o + 2), w);
+                }
             }
             if (!more) break;
             cs = ns;
-            k = k2;
-            ch = ch2;
             mr = mr2;
-            conj = mr.w;
+            mr2 = mr3;
+            k2 = k3;
+            ch2 = ch3;
         }
     }
-    mom_flush(acc, cur, lane, a.mom);
+    mom_flush<NW, LPS>(acc, cur, lane, a.mom, stride, Word());
 }
 
 // gains of an antenna in a bin as complex FP64 entries (row-major; phase-only: diag(e^{i phi}))
@@ -423,6 +558,95 @@ static __global__ void __launch_bounds__(128) mom_normal_kernel(const MomNormArg
     }
 }
 
+// Diagonal form: one warp per (interval, antenna a); lanes take the other antennas o and form
+// the pair's contributions to a's 2x2 block and right-hand side in FP32 (p side when a < o, q
+// side otherwise); a warp reduction sums them; lane 0 forms JHr = b - JHJ g in FP64 and writes
+// the update kernel's diagonal accumulator layout.
+static __global__ void __launch_bounds__(128) mom_normal_e_kernel(const MomNormArgs A)
+{
+    if (__ldg(A.n_active) == 0) return;
+    const long w = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= (long)A.n_bins * A.n_ant) return;
+    const int lane = threadIdx.x & 31;
+    const int bin = (int)(w / A.n_ant), a = (int)(w % A.n_ant);
+    if (!A.active[bin]) return;
+    float h00 = 0.f, h11 = 0.f;
+    float2 h01 = make_float2(0.f, 0.f), b0 = h01, b1 = h01;
+    for (int o = lane; o < A.n_ant; o += 32) {
+        if (o == a) continue;
+        const int up = __ldg(A.upair + (size_t)a * A.n_ant + o);
+        if (up < 0) continue;
+        const double *Mo = A.mom + ((size_t)bin * A.n_up + up) * MOM_E;
+        double2 Gd[4];
+        gains_of(A, bin, o, Gd);
+        const float2 g[2] = { f2(Gd[0]), f2(Gd[3]) };
+        const bool p_side = a < o;
+        // the slot's S' entry for this antenna's parameters (x, x') and the other's (y, y'):
+        // p side S'[(x,y)][(x',y')] with the other's gains g_y conj(g_y'); q side
+        // conj(S'[(y,x)][(y',x')]) with the same weights
+        float2 hh[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) hh[i] = make_float2(0.f, 0.f);
+        float2 bb[2] = { make_float2(0.f, 0.f), make_float2(0.f, 0.f) };
+#pragma unroll
+        for (int x = 0; x < 2; ++x) {
+#pragma unroll
+            for (int x2 = x; x2 < 2; ++x2)
+#pragma unroll
+                for (int y = 0; y < 2; ++y)
+#pragma unroll
+                    for (int y2 = 0; y2 < 2; ++y2) {
+                        const float2 gg = cmulc(g[y], g[y2]);
+                        const float2 sv = p_side ? slot_S(Mo, 0, 2 * x + y, 2 * x2 + y2)
+                                                 : cconj(slot_S(Mo, 0, 2 * y + x, 2 * y2 + x2));
+                        const float2 t = cmul(gg, sv);
+                        hh[x + x2].x += t.x;
+                        hh[x + x2].y += t.y;
+                    }
+#pragma unroll
+            for (int y = 0; y < 2; ++y) {
+                const double2 tv = __ldg(reinterpret_cast<const double2 *>(Mo + MOM_ET) + (p_side ? 2 * x + y : 2 * y + x));
+                const float2 tf = p_side ? make_float2((float)tv.x, (float)tv.y) : make_float2((float)tv.x, -(float)tv.y);
+                const float2 t = cmul(g[y], tf);
+                bb[x].x += t.x;
+                bb[x].y += t.y;
+            }
+        }
+        h00 += hh[0].x;
+        h01.x += hh[1].x;
+        h01.y += hh[1].y;
+        h11 += hh[2].x;
+        b0.x += bb[0].x; b0.y += bb[0].y;
+        b1.x += bb[1].x; b1.y += bb[1].y;
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        h00 += __shfl_xor_sync(FULL_MASK, h00, d);
+        h11 += __shfl_xor_sync(FULL_MASK, h11, d);
+        h01.x += __shfl_xor_sync(FULL_MASK, h01.x, d);
+        h01.y += __shfl_xor_sync(FULL_MASK, h01.y, d);
+        b0.x += __shfl_xor_sync(FULL_MASK, b0.x, d);
+        b0.y += __shfl_xor_sync(FULL_MASK, b0.y, d);
+        b1.x += __shfl_xor_sync(FULL_MASK, b1.x, d);
+        b1.y += __shfl_xor_sync(FULL_MASK, b1.y, d);
+    }
+    if (lane != 0) return;
+    double2 G[4];
+    gains_of(A, bin, a, G);
+    // JHr = b - H g, H = [[h00, h01], [conj(h01), h11]] on (g_0, g_1) = (G[0], G[3])
+    const double r0x = (double)b0.x - (h00 * G[0].x + (h01.x * G[3].x - h01.y * G[3].y));
+    const double r0y = (double)b0.y - (h00 * G[0].y + (h01.x * G[3].y + h01.y * G[3].x));
+    const double r1x = (double)b1.x - ((h01.x * G[0].x + h01.y * G[0].y) + h11 * G[3].x);
+    const double r1y = (double)b1.y - ((h01.x * G[0].y - h01.y * G[0].x) + h11 * G[3].y);
+    double *out = A.acc + ((size_t)bin * A.n_ant + a) * KG_DIAG;
+    out[0] = h00;
+    out[1] = h11;
+    out[2] = h01.x;
+    out[3] = h01.y;
+    out[4] = r0x; out[5] = r0y;
+    out[6] = r1x; out[7] = r1y;
+}
+
 // algorithmic bytes: the pass reads every sample of the bins once (their streaming bytes);
 // an iteration reads each bin's sums twice (once per side) and writes its accumulators
 static __global__ void mom_bytes_kernel(int n_bins, const long long *bin_nbytes, long long per_iter,
@@ -439,13 +663,32 @@ static __global__ void mom_bytes_kernel(int n_bins, const long long *bin_nbytes,
 
 } // namespace qc
 
-cudaError_t mom_launch_pass(const qc::MomArgs &a, int sm_count, cudaStream_t st)
+// the pass kernel of a form and fixed-term kind (ok: KIND_* of R in the full form, of L in the
+// diagonal form; the diagonal form needs one)
+cudaError_t mom_launch_pass(const qc::MomArgs &a, int form, int ok, int sm_count, cudaStream_t st)
 {
-    const int block = 128;                       // three CTAs per SM (register-bound)
+    using namespace qc;
+    const int block = 128;                       // two or three CTAs per SM (register-bound)
     const int n_groups = (a.n_chunks + a.group - 1) / a.group;
     const long units = (long)a.n_strips * n_groups;
-    const int grid = (int)std::max(1L, std::min((long)sm_count * 3, (units * 32 + block - 1) / block));
-    qc::mom_pass_kernel<<<grid, block, 0, st>>>(a);
+    auto grid = [&](int per_sm) {
+        return (int)std::max(1L, std::min((long)sm_count * per_sm, (units * 32 + block - 1) / block));
+    };
+    if (form == FORM_FULL) {
+        if (ok == KIND_NONE)
+            mom_pass_kernel<FORM_FULL, KIND_NONE><<<grid(mom_pass_ctas<FORM_FULL, KIND_NONE>()), block, 0, st>>>(a);
+        else if (ok == KIND_DIAG)
+            mom_pass_kernel<FORM_FULL, KIND_DIAG><<<grid(mom_pass_ctas<FORM_FULL, KIND_DIAG>()), block, 0, st>>>(a);
+        else
+            mom_pass_kernel<FORM_FULL, KIND_FULL><<<grid(mom_pass_ctas<FORM_FULL, KIND_FULL>()), block, 0, st>>>(a);
+    } else {
+        if (ok == KIND_DIAG)
+            mom_pass_kernel<FORM_E, KIND_DIAG><<<grid(mom_pass_ctas<FORM_E, KIND_DIAG>()), block, 0, st>>>(a);
+        else if (ok == KIND_FULL)
+            mom_pass_kernel<FORM_E, KIND_FULL><<<grid(mom_pass_ctas<FORM_E, KIND_FULL>()), block, 0, st>>>(a);
+        else
+            return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
@@ -459,17 +702,17 @@ cudaError_t mom_launch_bytes(int n_bins, const long long *bin_nbytes, long long 
 cudaError_t mom_launch_normal(const qc::MomNormArgs &a, cudaStream_t st)
 {
     const long warps = (long)a.n_bins * a.n_ant;
-    qc::mom_normal_kernel<<<(int)((warps + 3) / 4), 128, 0, st>>>(a);
+    if (a.form == qc::FORM_FULL) qc::mom_normal_kernel<<<(int)((warps + 3) / 4), 128, 0, st>>>(a);
+    else qc::mom_normal_e_kernel<<<(int)((warps + 3) / 4), 128, 0, st>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t mom_launch_rows(long n, const int *strip_rows, const int4 *rows, const uint8_t *row_live, const int *t_map,
-                            int n_fint, const int *up_of_bl, int4 *out, cudaStream_t st)
+cudaError_t mom_launch_rows(long n, const int *strip_rows, const int4 *rows, const uint8_t *row_live,
+                            const int *up_of_bl, int4 *out, cudaStream_t st)
 {
     if (n == 0) return cudaSuccess;
-    qc::mom_rows_kernel<<<(int)((n + 255) / 256), 256, 0, st>>>(n, strip_rows, rows, row_live, t_map, n_fint,
-                                                                 up_of_bl, out);
+    qc::mom_rows_kernel<<<(int)((n + 255) / 256), 256, 0, st>>>(n, strip_rows, rows, row_live, up_of_bl, out);
     return cudaGetLastError();
 }
 
-size_t mom_words() { return qc::MOM_N; }
+size_t mom_words(int form) { return form == qc::FORM_FULL ? qc::MOM_N : qc::MOM_E; }

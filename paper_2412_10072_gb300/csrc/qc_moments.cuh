@@ -6,8 +6,13 @@
 
 namespace qc {
 
-constexpr int MOM_N = 100;          // FP64 words per (interval, baseline): S 64, T 32, U 4
+constexpr int MOM_N = 100;          // FP64 words per (interval, pair), full form: S 64, T 32, U 4
 constexpr int MOM_T = 64, MOM_U = 96;
+// diagonal form (a diagonal or phase-only solved term with a term to its left): S' 16 (4x4
+// Hermitian packed as S), T' 8, U 1, one word of padding
+constexpr int MOM_E = 26;
+constexpr int MOM_ET = 16, MOM_EU = 24;
+constexpr int FORM_FULL = 0, FORM_E = 1;
 
 // Hermitian pairs (u, v), u < v, of the 4x4 S blocks: packed as 4 diagonal reals then 6 (re, im)
 __host__ __device__ constexpr int mom_pair(int u, int v)
@@ -16,21 +21,26 @@ __host__ __device__ constexpr int mom_pair(int u, int v)
 }
 
 struct MomArgs {
-    int n_chan, n_up;                    // n_up: unordered antenna pairs with data
+    int n_chan, n_ant, n_up;             // n_up: unordered antenna pairs with data
     const float4 *vis, *model, *wf;      // wf: weights with flags and autocorrelations folded in (w = 0)
-    const int4 *mrows;                   // [strip rows] {row or -1, first bin of its time, pair, ant1 > ant2}
+    // [strip rows] {row or -1 (nothing usable), time, pair | conj << 31, p | q << 16}: p, q the
+    // antennas of the baseline as oriented in the sums (p < q); conj: the row is (q, p)
+    const int4 *mrows;
     const int *strip_off;                // rows of each ordered baseline (offsets into mrows)
-    int n_strips, n_chunks;              // n_chunks: 16-channel chunks of a row
-    int group;                           // 16-channel chunks per unit of work
+    int n_strips, n_chunks;              // n_chunks: chunks of a row (16 channels full form, 32 diagonal)
+    int group;                           // chunks per unit of work
+    int chunk_major;                     // 1: a unit's rows inside each chunk; 0: a row's chunks inside it
     DevTerm tn;                          // the solved term (maps)
-    double *mom;                         // [bins][n_up][MOM_N]
+    DevTerm to;                          // the fixed other term of a two-term chain (tables)
+    double *mom;                         // [bins][n_up][MOM_N or MOM_E]
     const int *n_active;
 };
 
 struct MomNormArgs {
     int n_bins, n_ant, n_up, type;       // type: QC_TERM_* (diag, full, phase)
+    int form;                            // FORM_FULL or FORM_E
     const int *upair;                    // [n_ant][n_ant] unordered pair index or -1
-    const double *mom;                   // [bins][n_up][MOM_N]
+    const double *mom;                   // [bins][n_up][MOM_N or MOM_E]
     const double *params;                // FP64 gains of the solved term
     const uint8_t *active;               // [bins]
     const int *n_active;

@@ -191,11 +191,13 @@ def test_robust_reweighting_from_sums_matches_oracle():
 
 
 def test_chains_outside_the_option_solve_as_without_it():
-    obs = synth.plain_large(seed=3, n_ant=8, n_time=6, n_chan=40, noise=0.05, flag_row_frac=0.1, n_src=6)
-    a, _ = _gpu(obs, max_iter=10, moments=True)
-    b, _ = _gpu(obs, max_iter=10, moments=False)
+    """Three-term chains are not solved from sums: the option changes nothing."""
+    obs = _chain_obs(90, ("full", "diag", "phase"), t_int=(2, 5, 1), f_int=(7, 1, 45), noise=0.05)
+    a, sa = _gpu(obs, max_iter=10, moments=True)
+    b, sb = _gpu(obs, max_iter=10, moments=False)
     for x, y in zip(a, b):
         assert np.array_equal(np.asarray(x.gains), np.asarray(y.gains))
+    assert sa.pass_ms == 0 and sb.pass_ms == 0
 
 
 def test_byte_count_is_one_pass_plus_the_sums():
@@ -209,3 +211,103 @@ def test_byte_count_is_one_pass_plus_the_sums():
     per_iter = 2 * n_pairs * MOM_WORDS * 8 + 8 * obs.n_ant * 24
     assert mom.acc_bytes == plain.acc_bytes + n_bins * per_iter
     assert mom.vis_iters == plain.vis_iters
+
+
+# ---------------------------------------------------------------------------
+# two-term chains: the full form with the term to the right folded into the model, and the
+# diagonal form for a diagonal or phase-only term with a term to its left
+# ---------------------------------------------------------------------------
+
+def _chain_obs(seed, kinds, n_ant=6, n_time=5, n_chan=45, t_int=(2, 5), f_int=(7, 1), noise=0.1, flag_frac=0.2):
+    """Polarised random model, random per-correlation weights, flags, mixed baseline orientation,
+    intervals not aligned with the chunks, a ragged last chunk."""
+    rng = np.random.default_rng(seed)
+    p, q = synth.baselines(n_ant)
+    swap = rng.random(p.size) < 0.4
+    p, q = np.where(swap, q, p), np.where(swap, p, q)
+    ant1, ant2 = np.tile(p, n_time), np.tile(q, n_time)
+    tidx = np.repeat(np.arange(n_time, dtype=np.int32), p.size)
+    shp = (ant1.size, n_chan, 4)
+    model = rng.standard_normal(shp) + 1j * rng.standard_normal(shp)
+    specs = []
+    for i, kind in enumerate(kinds):
+        ti, fi = t_int[i], f_int[i]
+        nt, nf = -(-n_time // ti), -(-n_chan // fi)
+        spec = synth.TermSpec(kind, synth.interval_map(n_time, ti), synth.interval_map(n_chan, fi), nt, nf)
+        if kind == "phase":
+            spec.truth = 0.5 * rng.standard_normal((nt, nf, n_ant, 2))
+        elif kind == "diag":
+            spec.truth = synth.diag_truth(n_ant, nt, nf, rng)
+        else:
+            spec.truth = synth.full_truth(n_ant, nt, nf, rng, leakage=0.2)
+        specs.append(spec)
+    data = synth.corrupt(model, specs, ant1, ant2, tidx, n_chan)
+    data = data + noise * (rng.standard_normal(shp) + 1j * rng.standard_normal(shp))
+    weight = rng.uniform(0.5, 2.0, size=shp)
+    flag = (rng.random((ant1.size, n_chan)) < flag_frac).astype(np.uint8)
+    return synth.Observation(n_ant, n_time, n_chan, data.astype(np.complex64), model.astype(np.complex64),
+                             weight.astype(np.float32), flag, ant1.astype(np.int32), ant2.astype(np.int32), tidx,
+                             np.zeros(n_chan), specs, {})
+
+
+CHAINS = [("full", "diag"), ("full", "phase"), ("diag", "diag"), ("phase", "full"), ("diag", "full"),
+          ("full", "full")]
+
+
+@pytest.mark.parametrize("kinds", CHAINS)
+def test_two_term_single_step_from_sums_matches_oracle(kinds):
+    """Each term of the chain takes one step with the other fixed: the first term (nothing to
+    its left) from the full form with the second folded into the model; the second, if diagonal
+    or phase-only, from the diagonal form (a full second term takes the per-sample path)."""
+    obs = _chain_obs(70 + CHAINS.index(kinds), kinds)
+    rng = np.random.default_rng(5)
+    start = [_start(s, rng) for s in obs.terms]
+    for n in range(2):
+        P = O.OracleProblem.from_obs(obs)
+        ot = [O.OracleTerm.from_spec(s, obs.n_ant, params=g.astype(np.float64 if s.kind == "phase" else np.complex128),
+                                     solve=(i == n), max_iter=1, tol=0.0)
+              for i, (s, g) in enumerate(zip(obs.terms, start))]
+        O.solve(P, ot, damping_mode=0, damping=1.0)
+        S = qc.Solver.from_obs(obs)
+        gt = [qc.Term.from_spec(s, obs.n_ant, gains=g, solve=(i == n), max_iter=1, tol=0.0)
+              for i, (s, g) in enumerate(zip(obs.terms, start))]
+        st = S.solve(gt, damping_mode=0, damping=1.0, moments=True)
+        S.close()
+        want = ot[n].params
+        got = np.asarray(gt[n].gains, dtype=want.dtype)
+        step = want - start[n].astype(want.dtype)
+        err = np.max(np.abs(got - want)) / max(np.max(np.abs(step)), 1e-30)
+        assert err < 2e-3, (kinds, n, err)
+        assert np.array_equal(gt[n].gain_flags, ot[n].gain_flags)
+        from_sums = n == 0 or kinds[1] != "full"
+        assert (st.pass_ms > 0) == from_sums, (kinds, n, st.pass_ms)
+
+
+@pytest.mark.parametrize("kinds", [("full", "diag"), ("full", "phase")])
+def test_two_term_chain_from_sums_converges_like_oracle(kinds):
+    """The large workload's shape at a small size (G full per time, B per channel over all times),
+    three epochs, both terms from sums: chain products within 1e-4 and chi^2 within 1e-5 of the
+    oracle, and the same as the per-sample path."""
+    obs = synth.plain_large(seed=3, n_ant=10, n_time=12, n_chan=40, noise=0.05, flag_row_frac=0.1, n_src=8)
+    if kinds[1] == "phase":
+        rng = np.random.default_rng(4)
+        B = obs.terms[1]
+        spec = synth.TermSpec("phase", B.t_map, B.f_map, B.n_tint, B.n_fint)
+        spec.truth = 0.3 * rng.standard_normal((B.n_tint, B.n_fint, obs.n_ant, 2))
+        obs.terms = [obs.terms[0], spec]
+        obs.data = synth.corrupt(obs.model, obs.terms, obs.ant1, obs.ant2, obs.time_idx, obs.n_chan).astype(
+            np.complex64) + (0.05 * (rng.standard_normal(obs.data.shape) + 1j * rng.standard_normal(obs.data.shape))
+                             ).astype(np.complex64)
+    T, _, ochi2 = _oracle(obs, n_epochs=3)
+    gt, st = _gpu(obs, n_epochs=3)
+    assert _chain_err(obs, gt, T) < GAIN_TOL
+    assert abs(st.chi2_after - ochi2) <= CHI2_TOL * ochi2
+    assert st.pass_ms > 0
+    gp, _ = _gpu(obs, n_epochs=3, moments=False)
+    Cm = [_jones(t) for t in gt]
+    Cp = [_jones(t) for t in gp]
+    err = rel_err(reference_chain(chain_products(Cm, [t.t_map for t in gt], [t.f_map for t in gt], obs.n_time,
+                                                 obs.n_chan)),
+                  reference_chain(chain_products(Cp, [t.t_map for t in gp], [t.f_map for t in gp], obs.n_time,
+                                                 obs.n_chan)))
+    assert err < GAIN_TOL

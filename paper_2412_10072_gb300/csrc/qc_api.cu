@@ -303,6 +303,7 @@ extern "C" int qc_create(const qc_problem *p, qc_ctx **out)
     }
     c->n_strips = n_bl;
     c->n_strip_rows = (long)strip_rows.size();
+    for (int b = 0; b < n_bl; ++b) c->max_strip_rows = std::max(c->max_strip_rows, strip_off[b + 1] - strip_off[b]);
     cudaError_t e;
     qc_ctx *cc = c.get();
     auto dalloc = [&](size_t bytes) -> void * { return cc->alloc(bytes, &e); };
@@ -1432,19 +1433,23 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
         ma.mrows = (const int4 *)((char *)B.mom.ptr + mom_rows_off);
         ma.strip_off = d_strip_off;
         ma.n_strips = n_strips;
-        ma.n_chunks = mom_form == FORM_FULL ? (n_chan + 15) / 16 : (n_chan + 31) / 32;
-        // an interval several times long: the rows inside each chunk keep a lane's key; else a
-        // row's chunks inside each row, in groups as wide as leave about four units per
-        // resident warp (three CTAs of four warps per SM), so that an interval wider than a
-        // chunk flushes once per row and group
+        ma.n_chunks = (n_chan + 31) / 32;
+        // an interval several times long: the rows inside each chunk keep a lane's key (units of
+        // a whole strip x one chunk); else a row's chunks inside each row (units of whole rows x
+        // a block of rows), so that an interval one time long flushes once per row.  Either way
+        // about four units per resident warp
         ma.chunk_major = t.n_tint < n_time ? 1 : 0;
+        const int max_strip = std::max(1, max_strip_rows);
+        const long want_units = 4L * sm_count * 12;
         if (ma.chunk_major) {
             ma.group = 1;
+            ma.rb = max_strip;
         } else {
-            const long want_units = 4L * sm_count * 12;
-            const long per_strip = std::max(1L, (want_units + std::max(1, n_strips) - 1) / std::max(1, n_strips));
-            ma.group = (int)std::max(1L, (long)ma.n_chunks / per_strip);
+            ma.group = ma.n_chunks;
+            const long blocks = std::max(1L, (want_units + std::max(1, n_strips) - 1) / std::max(1, n_strips));
+            ma.rb = (int)std::max(1L, (max_strip + blocks - 1) / blocks);
         }
+        ma.n_rb = (max_strip + ma.rb - 1) / ma.rb;
         ma.tn = chain.t[n];
         ma.to = n_terms == 2 ? chain.t[1 - n] : chain.t[n];
         ma.mom = (double *)B.mom.ptr;

@@ -136,6 +136,7 @@ struct qc_ctx {
     int n_row = 0, n_chan = 0, n_ant = 0, n_time = 0, n_bl = 0, n_strips = 0;
     int n_dir = 1;                    // directions of the model (Eq. baselinemodel)
     long n_strip_rows = 0;            // rows in the baseline strips (cross-correlations)
+    int max_strip_rows = 0;           // rows of the longest strip
     bool m16 = false, has_flag = false;
     const float4 *d_vis = nullptr, *d_model = nullptr, *d_weight = nullptr;
     const uint8_t *d_flag = nullptr;

@@ -37,53 +37,41 @@ namespace qc {
 
 constexpr unsigned FULL_MASK = 0xffffffffu;
 
-// Two lanes share a sample: lane 2c + k takes channel c of a 16-channel chunk and the
-// correlations (k, j), j = 0, 1, i.e. the words of kj = 2k and 2k + 1, kept in registers as
-//   [0, 32)  S[2k + (i / 16)][i % 16],   [32, 48)  T[2k + (i - 32) / 8][(i - 32) % 8],
-//   48, 49   U[2k], U[2k + 1].
-constexpr int MOM_H = 50;
-
-__device__ __forceinline__ int mom_word(int i, int k)
+// One sample's terms added to a lane's register sums, full form (one lane per sample; words as
+// the slot: S[kj] at 16 kj, T[kj] at MOM_T + 8 kj, U[kj] at MOM_U + kj; all indices compile-time
+// constants after unrolling; X = R_p M R_q^H).
+__device__ __forceinline__ void mom_add(float (&acc)[MOM_N], const J2 &D, const J2 &X, float4 w)
 {
-    return i < 32 ? 16 * (2 * k + i / 16) + i % 16
-                  : (i < 48 ? MOM_T + 8 * (2 * k + (i - 32) / 8) + (i - 32) % 8 : MOM_U + 2 * k + (i - 48));
-}
-
-// One sample's terms for correlation row k added to a lane's register sums, full form (all
-// indices compile-time constants after unrolling; k selects the data row and the weights; M is
-// the sample's X = R_p M R_q^H).
-__device__ __forceinline__ void mom_add(float (&acc)[MOM_H], const J2 &D, const J2 &M, float4 w, int k)
-{
-    const float2 m[4] = { M.a, M.b, M.c, M.d };
-    const float2 d[2] = { k ? D.c : D.a, k ? D.d : D.b };
-    const float wv[2] = { k ? w.z : w.x, k ? w.w : w.y };
+    const float2 x[4] = { X.a, X.b, X.c, X.d };
+    const float2 d[4] = { D.a, D.b, D.c, D.d };
+    const float wv[4] = { w.x, w.y, w.z, w.w };
     float diag[4];
     float2 off[6];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) diag[u] = cnorm2(m[u]);
+    for (int u = 0; u < 4; ++u) diag[u] = cnorm2(x[u]);
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = u + 1; v < 4; ++v) off[mom_pair(u, v)] = cmulc(m[v], m[u]);   // conj(m_u) m_v
+        for (int v = u + 1; v < 4; ++v) off[mom_pair(u, v)] = cmulc(x[v], x[u]);   // conj(x_u) x_v
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-        const int s = 16 * j;
+    for (int kj = 0; kj < 4; ++kj) {
+        const int s = 16 * kj;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) acc[s + u] = fmaf(wv[j], diag[u], acc[s + u]);
+        for (int u = 0; u < 4; ++u) acc[s + u] = fmaf(wv[kj], diag[u], acc[s + u]);
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
-            acc[s + 4 + 2 * i] = fmaf(wv[j], off[i].x, acc[s + 4 + 2 * i]);
-            acc[s + 5 + 2 * i] = fmaf(wv[j], off[i].y, acc[s + 5 + 2 * i]);
+            acc[s + 4 + 2 * i] = fmaf(wv[kj], off[i].x, acc[s + 4 + 2 * i]);
+            acc[s + 5 + 2 * i] = fmaf(wv[kj], off[i].y, acc[s + 5 + 2 * i]);
         }
-        const float2 wd = cscale(d[j], wv[j]);
-        const int t = 32 + 8 * j;
+        const float2 wd = cscale(d[kj], wv[kj]);
+        const int t = MOM_T + 8 * kj;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const float2 c = cmulc(wd, m[u]);             // conj(m_u) w d
+            const float2 c = cmulc(wd, x[u]);             // conj(x_u) w d
             acc[t + 2 * u] += c.x;
             acc[t + 2 * u + 1] += c.y;
         }
-        acc[48 + j] = fmaf(wv[j], cnorm2(d[j]), acc[48 + j]);
+        acc[MOM_U + kj] = fmaf(wv[kj], cnorm2(d[kj]), acc[MOM_U + kj]);
     }
 }
 
@@ -141,36 +129,25 @@ __device__ __forceinline__ void mom_add_e(float (&acc)[MOM_EW], const J2 &D, con
     }
 }
 
-// register word -> word of the slot: full form (two lanes per sample, part k = lane & 1), and
-// the diagonal form (one lane per sample, the same order)
-struct FullWord {
-    __device__ __forceinline__ int operator()(int i, int k) const { return mom_word(i, k); }
-};
-struct DiagWord {
-    __device__ __forceinline__ int operator()(int i, int) const { return i; }
-};
-
-// Add the warp's register sums to the FP64 sums of each key (-1: nothing) and zero them.  LPS
-// lanes share a sample (lanes of one part hold the same words), so every reduction runs over
-// lane offsets LPS .. 16:
-//  - one key for the warp: a reduce-scatter (NW words padded to P = a power of two; after the
-//    halvings at offsets 16 .. LPS lane L holds words F (L / LPS) .. + F - 1, F = P LPS / 32),
-//    then one atomic per word;
-//  - a distinct key per sample: each lane adds its own words;
+// Add the warp's register sums (NW words, the slot's order) to the FP64 sums of each lane's key
+// (-1: nothing) and zero them:
+//  - one key for the warp: a reduce-scatter (words padded to P = a power of two; after the
+//    halvings at lane offsets 16 .. 1 lane L holds words F L .. F L + F - 1, F = P / 32), then
+//    one atomic per word;
+//  - 32 distinct keys: each lane adds its own words;
 //  - otherwise: a segmented reduction per word over the run of equal keys (channel intervals
-//    are contiguous, so a run is a range of lanes), added by the run's first sample.
-template <int NW, int LPS, typename WordOf>
-__device__ __forceinline__ void mom_flush(float (&acc)[NW], int key, int lane, double *mom, int stride, WordOf word)
+//    are contiguous, so a run is a range of lanes), added by the run's first lane.
+template <int NW>
+__device__ __forceinline__ void mom_flush(float (&acc)[NW], int key, int lane, double *mom, int stride)
 {
     constexpr int P = NW <= 32 ? 32 : (NW <= 64 ? 64 : 128);
-    constexpr int F = P * LPS / 32;
-    const int k = lane & (LPS - 1);
+    constexpr int F = P / 32;
     const int k0 = __shfl_sync(FULL_MASK, key, 0);
     if (__all_sync(FULL_MASK, key == k0)) {
         if (k0 >= 0) {
             // in place: after the halving at offset o the live words are acc[0 .. h)
 #pragma unroll
-            for (int h = P / 2, o = 16; o >= LPS; h >>= 1, o >>= 1) {
+            for (int h = P / 2, o = 16; o >= 1; h >>= 1, o >>= 1) {
                 const bool up = (lane & o) != 0;
 #pragma unroll
                 for (int i = 0; i < h; ++i) {
@@ -181,34 +158,32 @@ __device__ __forceinline__ void mom_flush(float (&acc)[NW], int key, int lane, d
                     if (i < NW) acc[i] = keep + __shfl_xor_sync(FULL_MASK, send, o);
                 }
             }
-            double *dst = mom + (size_t)k0 * stride;
-            const int base = F * (lane / LPS);
+            double *dst = mom + (size_t)k0 * stride + F * lane;
 #pragma unroll
             for (int j = 0; j < F; ++j)
-                if (base + j < NW) atomicAdd(dst + word(base + j, k), (double)acc[j]);
+                if (F * lane + j < NW) atomicAdd(dst + j, (double)acc[j]);
         }
     } else {
         const unsigned m = __match_any_sync(FULL_MASK, key);
-        const unsigned own = ((1u << LPS) - 1u) << (lane & ~(LPS - 1));
-        if (__all_sync(FULL_MASK, m == own)) {
+        if (__all_sync(FULL_MASK, m == (1u << lane))) {
             if (key >= 0) {
                 double *dst = mom + (size_t)key * stride;
 #pragma unroll
-                for (int v = 0; v < NW; ++v) atomicAdd(dst + word(v, k), (double)acc[v]);
+                for (int v = 0; v < NW; ++v) atomicAdd(dst + v, (double)acc[v]);
             }
         } else {
             const int seg_end = 32 - __clz(m);
-            const bool head = (lane / LPS) == ((__ffs(m) - 1) / LPS);
+            const bool head = lane == __ffs(m) - 1;
             double *dst = mom + (size_t)(key >= 0 ? key : 0) * stride;
 #pragma unroll
             for (int v = 0; v < NW; ++v) {
                 float x = acc[v];
 #pragma unroll
-                for (int d = LPS; d < 32; d <<= 1) {
+                for (int d = 1; d < 32; d <<= 1) {
                     const float o = __shfl_down_sync(FULL_MASK, x, d);
                     if (lane + d < seg_end) x += o;
                 }
-                if (head && key >= 0) atomicAdd(dst + word(v, k), (double)x);
+                if (head && key >= 0) atomicAdd(dst + v, (double)x);
             }
         }
     }
@@ -231,35 +206,6 @@ static __global__ void mom_rows_kernel(long n, const int *strip_rows, const int4
                        p | (q << 16));
 }
 
-// a streamed 16-byte load: read-only for the kernel's lifetime, not kept in L1
-__device__ __forceinline__ float4 ld_stream(const float4 *p)
-{
-    float4 r;
-    asm("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
-        : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w) : "l"(p));
-    return r;
-}
-
-// one sample as loaded: its key, folded weights, the raw data and model quads, and the fixed
-// term's table entries for p ([0, 2)) and q ([2, 4))
-struct MomSample {
-    int key;
-    float4 w, d0, d1, m0, m1;
-    float4 o[4];
-};
-
-template <int K>
-__device__ __forceinline__ void fac_load(const DevTerm &T, int n_ant, int ti, int fi, int ant, float4 *o)
-{
-    const size_t idx = ((size_t)ti * n_ant + ant) * T.n_fint + fi;
-    if constexpr (K == KIND_FULL) {
-        o[0] = __ldg(T.tab + 2 * idx);
-        o[1] = __ldg(T.tab + 2 * idx + 1);
-    } else if constexpr (K == KIND_DIAG) {
-        o[0] = __ldg(T.tab + idx);
-    }
-}
-
 template <int K>
 __device__ __forceinline__ J2 fac_jones(const float4 *o)
 {
@@ -268,122 +214,194 @@ __device__ __forceinline__ J2 fac_jones(const float4 *o)
     else return j_identity();
 }
 
-template <int CW, int OK>
-__device__ __forceinline__ MomSample mom_load(const MomArgs &a, const int4 &mr, int ch, int lane_ch)
-{
-    MomSample x;
-    const int c = ch * CW + lane_ch;
-    const bool in = c < a.n_chan;
-    x.key = in ? (__ldg(a.tn.t_map + mr.y) * a.tn.n_fint + __ldg(a.tn.f_map + c)) * a.n_up + (mr.z & 0x7fffffff)
-               : -1;
-    if (in && mr.x >= 0) {
-        const size_t i = (size_t)mr.x * a.n_chan + c;
-        x.w = ld_stream(a.wf + i);
-        x.d0 = ld_stream(a.vis + 2 * i);
-        x.d1 = ld_stream(a.vis + 2 * i + 1);
-        x.m0 = ld_stream(a.model + 2 * i);
-        x.m1 = ld_stream(a.model + 2 * i + 1);
-        if constexpr (OK != KIND_NONE) {
-            const int ti = __ldg(a.to.t_map + mr.y), fi = __ldg(a.to.f_map + c);
-            fac_load<OK>(a.to, a.n_ant, ti, fi, mr.w & 0xffff, x.o);
-            fac_load<OK>(a.to, a.n_ant, ti, fi, mr.w >> 16, x.o + 2);
+// Shape of a warp's ring of the pass (one lane per sample, 32-channel chunks): per stage, in
+// float4 units, the chunk's data quads d0 [0, 32), d1 [32, 64), model quads m0 [64, 96),
+// m1 [96, 128), folded weights w [128, 160), then the fixed term's table entries for p and for
+// q (NO float4 each, per channel, or only the first one when the chunk lies in one of the term's
+// frequency intervals), the lanes' keys (32 ints) and one int4 of meta data.
+template <int FORM, int OK> struct MomRing {
+    static constexpr int NO = OK == KIND_FULL ? 2 : (OK == KIND_DIAG ? 1 : 0);
+    static constexpr int OFF_OP = 160, OFF_OQ = OFF_OP + 32 * NO, OFF_KEY = OFF_OQ + 32 * NO;
+    static constexpr int OFF_META = OFF_KEY + 8;
+    static constexpr int STAGE = OFF_META + 1;               // float4 per stage
+    // the full form keeps 100 sums per lane (two CTAs of 4 warps per SM), the diagonal form 25
+    static constexpr int PER_SM = FORM == FORM_FULL ? 2 : 3;
+    static constexpr int DEPTH = FORM == FORM_FULL ? (NO == 2 ? 5 : 6) : (NO == 2 ? 3 : 4);
+    static constexpr size_t SMEM = (size_t)4 * DEPTH * STAGE * sizeof(float4);
+};
+
+constexpr int MOM_END = 2;       // meta: the warp's steps have run out (bit 0: conjugate baseline)
+
+// The issuing side of a warp: its steps in order, unit by unit (grid stride; a unit is a block
+// of rb rows of one baseline strip x a group of chunks), each copied into a ring stage by
+// cp.async (zero-filled past the last channel and for rows without usable data, whose weights
+// then read 0).
+template <int FORM, int OK> struct MomCursor {
+    using R = MomRing<FORM, OK>;
+    long unit, n_units, stride;
+    int n_groups;
+    int k0, k1, ch0, ch1, k, ch;
+    bool cm;
+
+    __device__ __forceinline__ void bounds(const MomArgs &a)
+    {
+        // the first unit from here on with rows (or none: unit >= n_units)
+        for (; unit < n_units; unit += stride) {
+            const int g = (int)(unit % n_groups);
+            const long sr = unit / n_groups;
+            const int s = (int)(sr / a.n_rb), b = (int)(sr % a.n_rb);
+            ch0 = g * a.group;
+            ch1 = min(a.n_chunks, ch0 + a.group);
+            const int kb = __ldg(a.strip_off + s);
+            k0 = kb + b * a.rb;
+            k1 = min(__ldg(a.strip_off + s + 1), k0 + a.rb);
+            if (k0 < k1) break;
         }
-    } else {
-        x.w = make_float4(0.f, 0.f, 0.f, 0.f);
-        x.d0 = x.d1 = x.m0 = x.m1 = x.w;
-        if constexpr (OK != KIND_NONE) x.o[0] = x.o[1] = x.o[2] = x.o[3] = x.w;
+        k = k0;
+        ch = ch0;
     }
-    return x;
-}
+
+    __device__ __forceinline__ void start(const MomArgs &a, long first, long step)
+    {
+        n_groups = (a.n_chunks + a.group - 1) / a.group;
+        n_units = (long)a.n_strips * a.n_rb * n_groups;
+        stride = step;
+        unit = first;
+        cm = a.chunk_major != 0;
+        bounds(a);
+    }
+
+    __device__ __forceinline__ void advance(const MomArgs &a)
+    {
+        bool done;
+        if (cm) { if (++k == k1) { k = k0; ++ch; } done = ch >= ch1; }
+        else { if (++ch == ch1) { ch = ch0; ++k; } done = k >= k1; }
+        if (done) {
+            unit += stride;
+            bounds(a);
+        }
+    }
+
+    __device__ __forceinline__ void issue(const MomArgs &a, int lane, float4 *stage)
+    {
+        int meta = MOM_END;
+        if (unit < n_units) {
+            const int4 mr = __ldg(a.mrows + k);
+            const int c0 = ch * 32, c = c0 + lane;
+            const bool in = c < a.n_chan;
+            const bool rd = mr.x >= 0 && in;
+            meta = mr.z < 0 ? 1 : 0;
+            const size_t i = rd ? (size_t)mr.x * a.n_chan + c : 0;
+            const uint32_t nb = rd ? 16u : 0u;
+            cp_async16(stage + lane, a.vis + 2 * i, nb);
+            cp_async16(stage + 32 + lane, a.vis + 2 * i + 1, nb);
+            cp_async16(stage + 64 + lane, a.model + 2 * i, nb);
+            cp_async16(stage + 96 + lane, a.model + 2 * i + 1, nb);
+            cp_async16(stage + 128 + lane, a.wf + i, nb);
+            if constexpr (R::NO > 0) {
+                const int ti = __ldg(a.to.t_map + mr.y);
+                const int f_first = __ldg(a.to.f_map + c0);
+                const int f_last = __ldg(a.to.f_map + min(a.n_chan, c0 + 32) - 1);
+                const bool uni = f_first == f_last;       // f_map is non-decreasing
+                if (uni) meta |= 4;
+                const int pa = mr.w & 0xffff, qa = mr.w >> 16;
+                if (uni) {
+                    if (lane < 2 * R::NO) {
+                        const int side = lane / R::NO, part = lane % R::NO;
+                        const size_t idx = ((size_t)ti * a.n_ant + (side ? qa : pa)) * a.to.n_fint + f_first;
+                        cp_async16(stage + (side ? R::OFF_OQ : R::OFF_OP) + part, a.to.tab + R::NO * idx + part,
+                                   mr.x >= 0 ? 16u : 0u);
+                    }
+                } else {
+                    const int fi = in ? __ldg(a.to.f_map + c) : 0;
+                    const size_t ip = ((size_t)ti * a.n_ant + pa) * a.to.n_fint + fi;
+                    const size_t iq = ((size_t)ti * a.n_ant + qa) * a.to.n_fint + fi;
+#pragma unroll
+                    for (int part = 0; part < R::NO; ++part) {
+                        cp_async16(stage + R::OFF_OP + R::NO * lane + part, a.to.tab + R::NO * ip + part, nb);
+                        cp_async16(stage + R::OFF_OQ + R::NO * lane + part, a.to.tab + R::NO * iq + part, nb);
+                    }
+                }
+            }
+            reinterpret_cast<int *>(stage + R::OFF_KEY)[lane] =
+                in ? (__ldg(a.tn.t_map + mr.y) * a.tn.n_fint + __ldg(a.tn.f_map + c)) * a.n_up + (mr.z & 0x7fffffff)
+                   : -1;
+        }
+        if (lane == 0) reinterpret_cast<int *>(stage + R::OFF_META)[0] = meta;
+        cp_async_commit();
+        if (unit < n_units) advance(a);
+    }
+};
 
 // One pass: warps walk units of a baseline strip (the rows of one ordered baseline in time
-// order) x a group of chunks (16 channels in the full form, two lanes per sample; 32 in the
-// diagonal form), a row's chunks inside each row or, with chunk_major, the rows inside each
-// chunk (an interval several times long then keeps its keys), with the next sample's loads in
-// flight while the current one is added to the lane's register sums.  The sums are flushed when
-// any lane's (interval, pair) key changes.  The fixed term is L (diagonal form) or R (full form)
-// of kind OK.
+// order): blocks of rb rows x groups of 32-channel chunks, a row's chunks inside each row or,
+// with chunk_major, the rows inside each chunk (an interval several times long then keeps its
+// keys).  Each warp streams its steps through a ring of DEPTH cp.async stages in shared memory,
+// DEPTH - 1 steps ahead of the arithmetic, which adds each lane's sample to its register sums;
+// the sums are flushed when any lane's (interval, pair) key changes.  The fixed term is L
+// (diagonal form) or R (full form) of kind OK.
 template <int FORM, int OK>
-constexpr int mom_pass_ctas() { return (FORM == FORM_FULL && OK != KIND_NONE) ? 2 : 3; }
-
-template <int FORM, int OK>
-static __global__ void __launch_bounds__(128, mom_pass_ctas<FORM, OK>()) mom_pass_kernel(const MomArgs a)
+static __global__ void __launch_bounds__(128, MomRing<FORM, OK>::PER_SM) mom_pass_kernel(const MomArgs a)
 {
-    constexpr int LPS = FORM == FORM_FULL ? 2 : 1;
-    constexpr int NW = FORM == FORM_FULL ? MOM_H : MOM_EW;
-    constexpr int CW = 32 / LPS;
+    using R = MomRing<FORM, OK>;
+    constexpr int NW = FORM == FORM_FULL ? MOM_N : MOM_EW;
     if (__ldg(a.n_active) == 0) return;
-    const int lane = threadIdx.x & 31, lane_ch = lane / LPS;
+    extern __shared__ float4 mom_ring[];
+    const int lane = threadIdx.x & 31;
+    float4 *ring = mom_ring + (size_t)(threadIdx.x >> 5) * R::DEPTH * R::STAGE;
     const int stride = FORM == FORM_FULL ? MOM_N : MOM_E;
-    using Word = typename std::conditional<FORM == FORM_FULL, FullWord, DiagWord>::type;
     float acc[NW];
 #pragma unroll
     for (int v = 0; v < NW; ++v) acc[v] = 0.f;
-    const long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long n_warps = ((long)gridDim.x * blockDim.x) >> 5;
-    const int n_groups = (a.n_chunks + a.group - 1) / a.group;
-    const long n_units = (long)a.n_strips * n_groups;
-    const bool cm = a.chunk_major != 0;
-    int cur = -1;
-    for (long unit = warp; unit < n_units; unit += n_warps) {
-        const int s = (int)(unit / n_groups), g = (int)(unit % n_groups);
-        const int ch0 = g * a.group, ch1 = min(a.n_chunks, ch0 + a.group);
-        const int k0 = __ldg(a.strip_off + s), k1 = __ldg(a.strip_off + s + 1);
-        if (k0 >= k1) continue;
-        // the unit's steps (row k, chunk ch) in its order
-        auto adv = [&](int &k, int &ch) {
-            if (cm) { if (++k == k1) { k = k0; ++ch; } }
-            else { if (++ch == ch1) { ch = ch0; ++k; } }
-        };
-        auto valid = [&](int k, int ch) { return cm ? ch < ch1 : k < k1; };
-        int k2 = k0, ch2 = ch0;
-        adv(k2, ch2);
-        int ch = ch0;
-        int4 mr = __ldg(a.mrows + k0);
-        int4 mr2 = valid(k2, ch2) ? __ldg(a.mrows + k2) : make_int4(-1, 0, 0, 0);
-        MomSample cs = mom_load<CW, OK>(a, mr, ch, lane_ch);
-        while (true) {
-            if (__any_sync(FULL_MASK, cs.key != cur)) {
-                mom_flush<NW, LPS>(acc, cur, lane, a.mom, stride, Word());
-                cur = cs.key;
-            }
-            const bool more = valid(k2, ch2);
-            int k3 = k2, ch3 = ch2;
-            adv(k3, ch3);
-            int4 mr3 = make_int4(-1, 0, 0, 0);
-            MomSample ns;
-            if (more) {
-                if (valid(k3, ch3)) mr3 = __ldg(a.mrows + k3);
-                ns = mom_load<CW, OK>(a, mr2, ch2, lane_ch);
-            }
-            if (cs.w.x != 0.f || cs.w.y != 0.f || cs.w.z != 0.f || cs.w.w != 0.f) {
-                J2 D = j_from(cs.d0, cs.d1), M = j_from(cs.m0, cs.m1);
-                float4 w = cs.w;
-                if (mr.z < 0) {                  // the conjugate baseline: D -> D^H, M -> M^H, w permuted
-                    D = j_herm(D);
-                    M = j_herm(M);
-                    w = make_float4(w.x, w.z, w.y, w.w);
-                }
-                if constexpr (FORM == FORM_FULL) {
-                    if constexpr (OK == KIND_DIAG)
-                        M = j_muld(j_dmul(make_float2(cs.o[0].x, cs.o[0].y), make_float2(cs.o[0].z, cs.o[0].w), M),
-                                   make_float2(cs.o[2].x, -cs.o[2].y), make_float2(cs.o[2].z, -cs.o[2].w));
-                    else if constexpr (OK == KIND_FULL)
-                        M = j_mul_h(j_mul(fac_jones<OK>(cs.o), M), fac_jones<OK>(cs.o + 2));
-                    mom_add(acc, D, M, w, lane & 1);
-                } else {
-                    mom_add_e<OK>(acc, D, M, fac_jones<OK>(cs.o), fac_jones<OK>(cs.o + 2), w);
-                }
-            }
-            if (!more) break;
-            cs = ns;
-            mr = mr2;
-            mr2 = mr3;
-            k2 = k3;
-            ch2 = ch3;
-        }
+    MomCursor<FORM, OK> cur;
+    cur.start(a, ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5, ((long)gridDim.x * blockDim.x) >> 5);
+    int is = 0;
+#pragma unroll
+    for (int d = 0; d < R::DEPTH - 1; ++d) {
+        cur.issue(a, lane, ring + (size_t)is * R::STAGE);
+        if (++is == R::DEPTH) is = 0;
     }
-    mom_flush<NW, LPS>(acc, cur, lane, a.mom, stride, Word());
+    int key_cur = -1, stage = 0;
+    for (;;) {
+        __syncwarp();                          // every lane is done with the stage about to be refilled
+        cur.issue(a, lane, ring + (size_t)is * R::STAGE);
+        if (++is == R::DEPTH) is = 0;
+        cp_async_wait<R::DEPTH - 1>();
+        __syncwarp();
+        const float4 *st = ring + (size_t)stage * R::STAGE;
+        const int meta = reinterpret_cast<const int *>(st + R::OFF_META)[0];
+        if (meta & MOM_END) break;
+        const int key = reinterpret_cast<const int *>(st + R::OFF_KEY)[lane];
+        if (__any_sync(FULL_MASK, key != key_cur)) {
+            mom_flush<NW>(acc, key_cur, lane, a.mom, stride);
+            key_cur = key;
+        }
+        float4 w = st[128 + lane];
+        if (w.x != 0.f || w.y != 0.f || w.z != 0.f || w.w != 0.f) {
+            J2 D = j_from(st[lane], st[32 + lane]), M = j_from(st[64 + lane], st[96 + lane]);
+            if (meta & 1) {                    // the conjugate baseline: D -> D^H, M -> M^H, w permuted
+                D = j_herm(D);
+                M = j_herm(M);
+                w = make_float4(w.x, w.z, w.y, w.w);
+            }
+            const int oc = (meta & 4) ? 0 : lane * R::NO;
+            if constexpr (FORM == FORM_FULL) {
+                if constexpr (OK == KIND_DIAG) {
+                    const float4 rp = st[R::OFF_OP + oc], rq = st[R::OFF_OQ + oc];
+                    M = j_muld(j_dmul(make_float2(rp.x, rp.y), make_float2(rp.z, rp.w), M),
+                               make_float2(rq.x, -rq.y), make_float2(rq.z, -rq.w));
+                } else if constexpr (OK == KIND_FULL) {
+                    M = j_mul_h(j_mul(fac_jones<OK>(st + R::OFF_OP + oc), M), fac_jones<OK>(st + R::OFF_OQ + oc));
+                }
+                mom_add(acc, D, M, w);
+            } else {
+                mom_add_e<OK>(acc, D, M, fac_jones<OK>(st + R::OFF_OP + oc), fac_jones<OK>(st + R::OFF_OQ + oc), w);
+            }
+        }
+        if (++stage == R::DEPTH) stage = 0;
+    }
+    mom_flush<NW>(acc, key_cur, lane, a.mom, stride);
+    cp_async_wait<0>();
 }
 
 // gains of an antenna in a bin as complex FP64 entries (row-major; phase-only: diag(e^{i phi}))
@@ -665,31 +683,38 @@ static __global__ void mom_bytes_kernel(int n_bins, const long long *bin_nbytes,
 
 // the pass kernel of a form and fixed-term kind (ok: KIND_* of R in the full form, of L in the
 // diagonal form; the diagonal form needs one)
+template <int FORM, int OK>
+static cudaError_t launch_pass(const qc::MomArgs &a, int sm_count, cudaStream_t st)
+{
+    using R = qc::MomRing<FORM, OK>;
+    static bool configured = false;              // the raised shared-memory limit, once per process
+    if (!configured) {
+        const cudaError_t e = cudaFuncSetAttribute(qc::mom_pass_kernel<FORM, OK>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R::SMEM);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    const int block = 128;
+    const int n_groups = (a.n_chunks + a.group - 1) / a.group;
+    const long units = (long)a.n_strips * a.n_rb * n_groups;
+    const int grid = (int)std::max(1L, std::min((long)sm_count * R::PER_SM, (units * 32 + block - 1) / block));
+    qc::mom_pass_kernel<FORM, OK><<<grid, block, R::SMEM, st>>>(a);
+    return cudaGetLastError();
+}
+
+// the pass kernel of a form and fixed-term kind (ok: KIND_* of R in the full form, of L in the
+// diagonal form; the diagonal form needs one)
 cudaError_t mom_launch_pass(const qc::MomArgs &a, int form, int ok, int sm_count, cudaStream_t st)
 {
     using namespace qc;
-    const int block = 128;                       // two or three CTAs per SM (register-bound)
-    const int n_groups = (a.n_chunks + a.group - 1) / a.group;
-    const long units = (long)a.n_strips * n_groups;
-    auto grid = [&](int per_sm) {
-        return (int)std::max(1L, std::min((long)sm_count * per_sm, (units * 32 + block - 1) / block));
-    };
     if (form == FORM_FULL) {
-        if (ok == KIND_NONE)
-            mom_pass_kernel<FORM_FULL, KIND_NONE><<<grid(mom_pass_ctas<FORM_FULL, KIND_NONE>()), block, 0, st>>>(a);
-        else if (ok == KIND_DIAG)
-            mom_pass_kernel<FORM_FULL, KIND_DIAG><<<grid(mom_pass_ctas<FORM_FULL, KIND_DIAG>()), block, 0, st>>>(a);
-        else
-            mom_pass_kernel<FORM_FULL, KIND_FULL><<<grid(mom_pass_ctas<FORM_FULL, KIND_FULL>()), block, 0, st>>>(a);
-    } else {
-        if (ok == KIND_DIAG)
-            mom_pass_kernel<FORM_E, KIND_DIAG><<<grid(mom_pass_ctas<FORM_E, KIND_DIAG>()), block, 0, st>>>(a);
-        else if (ok == KIND_FULL)
-            mom_pass_kernel<FORM_E, KIND_FULL><<<grid(mom_pass_ctas<FORM_E, KIND_FULL>()), block, 0, st>>>(a);
-        else
-            return cudaErrorInvalidValue;
+        if (ok == KIND_NONE) return launch_pass<FORM_FULL, KIND_NONE>(a, sm_count, st);
+        if (ok == KIND_DIAG) return launch_pass<FORM_FULL, KIND_DIAG>(a, sm_count, st);
+        return launch_pass<FORM_FULL, KIND_FULL>(a, sm_count, st);
     }
-    return cudaGetLastError();
+    if (ok == KIND_DIAG) return launch_pass<FORM_E, KIND_DIAG>(a, sm_count, st);
+    if (ok == KIND_FULL) return launch_pass<FORM_E, KIND_FULL>(a, sm_count, st);
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t mom_launch_bytes(int n_bins, const long long *bin_nbytes, long long per_iter, long long *iter_nbytes,

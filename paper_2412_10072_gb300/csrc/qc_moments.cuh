@@ -27,8 +27,9 @@ struct MomArgs {
     // antennas of the baseline as oriented in the sums (p < q); conj: the row is (q, p)
     const int4 *mrows;
     const int *strip_off;                // rows of each ordered baseline (offsets into mrows)
-    int n_strips, n_chunks;              // n_chunks: chunks of a row (16 channels full form, 32 diagonal)
+    int n_strips, n_chunks;              // n_chunks: 32-channel chunks of a row
     int group;                           // chunks per unit of work
+    int rb, n_rb;                        // rows of a strip per unit of work, blocks per strip
     int chunk_major;                     // 1: a unit's rows inside each chunk; 0: a row's chunks inside it
     DevTerm tn;                          // the solved term (maps)
     DevTerm to;                          // the fixed other term of a two-term chain (tables)

@@ -872,9 +872,22 @@ extern "C" int qc_solve(qc_ctx *c, qc_term *terms, int32_t n_terms, const qc_opt
         if ((rc = c->ensure(B.iters, nbytes<int>(nb)))) return rc;
         if ((rc = c->ensure(B.flags, nb * nat))) return rc;
         CK(cudaMemsetAsync(B.acc.ptr, 0, nbytes<double>(nb * nat * KG), st));
-        CK(cudaMemsetAsync(B.nvis.ptr, 0, nbytes<long long>(3 * nb), st));
         CK(cudaMemsetAsync(B.iters.ptr, 0, nbytes<int>(nb), st));
         CK(cudaMemsetAsync(B.flags.ptr, 0, nb * nat, st));
+        // the counts of the previous call stand while the term's maps are the same (FNV-1a
+        // over the kernels' view of them)
+        uint64_t sig = 1469598103934665603ull;
+        auto mix = [&](uint64_t v) { sig = (sig ^ v) * 1099511628211ull; };
+        mix((uint64_t)t.type);
+        mix((uint64_t)t.n_tint);
+        mix((uint64_t)t.n_fint);
+        mix((uint64_t)nat);
+        for (int i = 0; i < c->n_time; ++i) mix((uint64_t)(uint32_t)t.t_map[i]);
+        for (int i = 0; i < c->n_chan; ++i) mix((uint64_t)(uint32_t)t.f_map[i]);
+        B.graph_valid = false;
+        if (sig == B.count_sig && B.count_buf == B.nvis.ptr) continue;
+        B.count_sig = 0;
+        CK(cudaMemsetAsync(B.nvis.ptr, 0, nbytes<long long>(3 * nb), st));
         long long *nvis = (long long *)B.nvis.ptr;
         CountArgs ca;
         ca.D = c->data_desc();
@@ -891,7 +904,8 @@ extern "C" int qc_solve(qc_ctx *c, qc_term *terms, int32_t n_terms, const qc_opt
         bin_bytes_kernel<<<((int)nb + 255) / 256, 256, 0, st>>>((int)nb, nvis, nvis + nb, b_flag, b_unflag, nvis + 2 * nb);
         CK(cudaGetLastError());
         ++c->launches;
-        B.graph_valid = false;
+        B.count_sig = sig;
+        B.count_buf = B.nvis.ptr;
     }
 
     // robust reweighting between epochs: every kernel reads the context's folded weight copy,
@@ -1413,7 +1427,7 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
         dua.tol = ua.tol;
     }
 
-    // sums of the term solve: [bins][unordered pairs][MOM_N or MOM_E] FP64, the per-bin bytes of
+    // sums of the term solve: [bins][unordered pairs][MOM_N or MOM_E] FP32, the per-bin bytes of
     // one iteration for the byte counter, then the pass's row table
     MomArgs ma;
     MomNormArgs mn;
@@ -1421,7 +1435,8 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
     memset(&mn, 0, sizeof mn);
     const int mom_n = mom_form == FORM_E ? MOM_E : MOM_N;
     const size_t mom_words_all = mom ? (size_t)nb * n_up * mom_n : 0;
-    const size_t mom_rows_off = ((nbytes<double>(mom_words_all) + nbytes<long long>(nb) + 15) / 16) * 16;
+    const size_t mom_cnt_off = ((nbytes<float>(mom_words_all) + 15) / 16) * 16;
+    const size_t mom_rows_off = ((mom_cnt_off + nbytes<long long>(nb) + 15) / 16) * 16;
     if (mom) {
         if ((rc = ensure(B.mom, mom_rows_off + nbytes<int4>(std::max(1L, n_strip_rows))))) return rc;
         ma.n_chan = n_chan;
@@ -1452,7 +1467,7 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
         ma.n_rb = (max_strip + ma.rb - 1) / ma.rb;
         ma.tn = chain.t[n];
         ma.to = n_terms == 2 ? chain.t[1 - n] : chain.t[n];
-        ma.mom = (double *)B.mom.ptr;
+        ma.mom = (float *)B.mom.ptr;
         mn.n_bins = nb;
         mn.n_ant = n_ant;
         mn.n_up = n_up;
@@ -1463,9 +1478,9 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
         mn.params = (const double *)B.params.ptr;
         mn.active = (const uint8_t *)B.active.ptr;
         mn.acc = (double *)B.acc.ptr;
-        ua.bin_nbytes = (const long long *)(ma.mom + mom_words_all);
+        ua.bin_nbytes = (const long long *)((char *)B.mom.ptr + mom_cnt_off);
     }
-    const long long mom_iter_bytes = 2LL * n_up * mom_n * 8 + 8LL * n_ant * (t.type == 1 ? KG_FULL : KG_DIAG);
+    const long long mom_iter_bytes = 2LL * n_up * mom_n * 4 + 8LL * n_ant * (t.type == 1 ? KG_FULL : KG_DIAG);
 
     const int max_iter = t.max_iter;
     for (int k = 0; k < 2 * max_iter + 2; ++k) { cudaEvent_t ev; if ((rc = get_event(2 + k, ev))) return rc; }
@@ -1497,9 +1512,9 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
                 CK(dd_launch_acc(dda, ts, grid, st));
             } else if (mom) {
                 if (k == 1) {
-                    CK(cudaMemsetAsync(B.mom.ptr, 0, nbytes<double>(mom_words_all), st));
+                    CK(cudaMemsetAsync(B.mom.ptr, 0, nbytes<float>(mom_words_all), st));
                     CK(mom_launch_bytes(nb, (const long long *)B.nvis.ptr + 2 * (size_t)nb, mom_iter_bytes,
-                                        (long long *)(ma.mom + mom_words_all), ua.acc_bytes, st));
+                                        (long long *)((char *)B.mom.ptr + mom_cnt_off), ua.acc_bytes, st));
                     CK(mom_launch_rows(n_strip_rows, d_strip_rows, d_rows, d_row_live, d_up_of_bl,
                                        const_cast<int4 *>(ma.mrows), st));
                     CK(cudaEventRecordWithFlags(events[ev_pass], st, rec_flags));

@@ -58,6 +58,10 @@ struct Buf {
 
 // Device buffers of one chain position, reused across calls while large enough.
 struct TermBufs {
+    // per-bin sample counts (Buf nvis) are a function of the term's maps and of the context's
+    // flags, which are fixed for its lifetime: kept while the maps are unchanged
+    uint64_t count_sig = 0;
+    const void *count_buf = nullptr;
     Buf maps;      // t_map then f_map (int32)
     std::vector<int> hmaps;   // host copy of the maps (staging for the upload)
     Buf tab;       // FP32 kernel table of the term's Jones matrices

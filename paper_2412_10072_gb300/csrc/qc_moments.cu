@@ -22,12 +22,13 @@
 //     JHJ_p[a][a'] += sum_b sum_b' g_q,b conj(g_q,b') S'[(a,b)][(a',b')],  b_p[a] += sum_b g_q,b T'[(a,b)]
 //     JHJ_q[b][b'] += sum_a sum_a' g_p,a conj(g_p,a') conj(S'[(a,b)][(a',b')]),
 //     b_q[b]       += sum_a g_p,a conj(T'[(a,b)])
-// In both forms JHr = b - JHJ vec(g).  One pass over the data per term solve forms the sums
-// (mom_pass_kernel: FP32 per lane, FP64 sums); every iteration forms each antenna's blocks from
-// them and the current gains in FP32 (mom_normal_kernel), JHr = b - JHJ g and everything after
-// it in FP64, in the update kernel's accumulator layout (a diagonal or phase-only term of the
-// full form takes the (0, 3) rows and columns).  An iteration then reads 800 or 208 B per
-// (interval, pair) instead of 81 B per sample.
+// In both forms JHr = b - JHJ vec(g).  One pass over the data per term solve forms the sums in
+// FP32 (mom_pass_kernel: per-lane register sums, added to the slots by FP32 atomics, a few per
+// slot: a warp covers a whole row, or a whole strip of one chunk); every iteration forms each
+// antenna's blocks from them and the current gains in FP32 (mom_normal_kernel), JHr = b - JHJ g
+// and everything after it in FP64, in the update kernel's accumulator layout (a diagonal or
+// phase-only term of the full form takes the (0, 3) rows and columns).  An iteration then reads
+// 400 or 104 B per (interval, pair) instead of 81 B per sample.
 #include "qc_internal.h"
 
 #include <algorithm>
@@ -129,7 +130,7 @@ __device__ __forceinline__ void mom_add_e(float (&acc)[MOM_EW], const J2 &D, con
     }
 }
 
-// Add the warp's register sums (NW words, the slot's order) to the FP64 sums of each lane's key
+// Add the warp's register sums (NW words, the slot's order) to the sums of each lane's key
 // (-1: nothing) and zero them:
 //  - one key for the warp: a reduce-scatter (words padded to P = a power of two; after the
 //    halvings at lane offsets 16 .. 1 lane L holds words F L .. F L + F - 1, F = P / 32), then
@@ -138,7 +139,7 @@ __device__ __forceinline__ void mom_add_e(float (&acc)[MOM_EW], const J2 &D, con
 //  - otherwise: a segmented reduction per word over the run of equal keys (channel intervals
 //    are contiguous, so a run is a range of lanes), added by the run's first lane.
 template <int NW>
-__device__ __forceinline__ void mom_flush(float (&acc)[NW], int key, int lane, double *mom, int stride)
+__device__ __forceinline__ void mom_flush(float (&acc)[NW], int key, int lane, float *mom, int stride)
 {
     constexpr int P = NW <= 32 ? 32 : (NW <= 64 ? 64 : 128);
     constexpr int F = P / 32;
@@ -158,23 +159,23 @@ __device__ __forceinline__ void mom_flush(float (&acc)[NW], int key, int lane, d
                     if (i < NW) acc[i] = keep + __shfl_xor_sync(FULL_MASK, send, o);
                 }
             }
-            double *dst = mom + (size_t)k0 * stride + F * lane;
+            float *dst = mom + (size_t)k0 * stride + F * lane;
 #pragma unroll
             for (int j = 0; j < F; ++j)
-                if (F * lane + j < NW) atomicAdd(dst + j, (double)acc[j]);
+                if (F * lane + j < NW) atomicAdd(dst + j, acc[j]);
         }
     } else {
         const unsigned m = __match_any_sync(FULL_MASK, key);
         if (__all_sync(FULL_MASK, m == (1u << lane))) {
             if (key >= 0) {
-                double *dst = mom + (size_t)key * stride;
+                float *dst = mom + (size_t)key * stride;
 #pragma unroll
-                for (int v = 0; v < NW; ++v) atomicAdd(dst + v, (double)acc[v]);
+                for (int v = 0; v < NW; ++v) atomicAdd(dst + v, acc[v]);
             }
         } else {
             const int seg_end = 32 - __clz(m);
             const bool head = lane == __ffs(m) - 1;
-            double *dst = mom + (size_t)(key >= 0 ? key : 0) * stride;
+            float *dst = mom + (size_t)(key >= 0 ? key : 0) * stride;
 #pragma unroll
             for (int v = 0; v < NW; ++v) {
                 float x = acc[v];
@@ -183,7 +184,7 @@ __device__ __forceinline__ void mom_flush(float (&acc)[NW], int key, int lane, d
                     const float o = __shfl_down_sync(FULL_MASK, x, d);
                     if (lane + d < seg_end) x += o;
                 }
-                if (head && key >= 0) atomicAdd(dst + v, (double)x);
+                if (head && key >= 0) atomicAdd(dst + v, x);
             }
         }
     }
@@ -424,19 +425,18 @@ __device__ __forceinline__ void gains_of(const MomNormArgs &A, int bin, int ant,
 
 __device__ __forceinline__ float2 f2(double2 a) { return make_float2((float)a.x, (float)a.y); }
 // element (u, v) of the Hermitian S block kj of a slot, in FP32 (u, v compile-time after unrolling)
-__device__ __forceinline__ float2 slot_S(const double *Mo, int kj, int u, int v)
+__device__ __forceinline__ float2 slot_S(const float *Mo, int kj, int u, int v)
 {
-    const double *s = Mo + 16 * kj;
-    if (u == v) return make_float2((float)__ldg(s + u), 0.f);
+    const float *s = Mo + 16 * kj;
+    if (u == v) return make_float2(__ldg(s + u), 0.f);
     const int i = u < v ? mom_pair(u, v) : mom_pair(v, u);
-    const double2 x = __ldg(reinterpret_cast<const double2 *>(s + 4 + 2 * i));
-    return u < v ? make_float2((float)x.x, (float)x.y) : make_float2((float)x.x, -(float)x.y);
+    const float2 x = __ldg(reinterpret_cast<const float2 *>(s + 4 + 2 * i));
+    return u < v ? x : make_float2(x.x, -x.y);
 }
 
-__device__ __forceinline__ float2 slot_T(const double *Mo, int kj, int u)
+__device__ __forceinline__ float2 slot_T(const float *Mo, int kj, int u)
 {
-    const double2 x = __ldg(reinterpret_cast<const double2 *>(Mo + MOM_T + 8 * kj + 2 * u));
-    return make_float2((float)x.x, (float)x.y);
+    return __ldg(reinterpret_cast<const float2 *>(Mo + MOM_T + 8 * kj + 2 * u));
 }
 
 // One warp per (interval, antenna a): lanes take the other antennas o, form the contributions
@@ -463,7 +463,7 @@ static __global__ void __launch_bounds__(128) mom_normal_kernel(const MomNormArg
         if (o == a) continue;
         const int up = __ldg(A.upair + (size_t)a * A.n_ant + o);
         if (up < 0) continue;
-        const double *Mo = A.mom + ((size_t)bin * A.n_up + up) * MOM_N;
+        const float *Mo = A.mom + ((size_t)bin * A.n_up + up) * MOM_N;
         double2 Gd[4];
         gains_of(A, bin, o, Gd);
         float2 G[4];
@@ -594,7 +594,7 @@ static __global__ void __launch_bounds__(128) mom_normal_e_kernel(const MomNormA
         if (o == a) continue;
         const int up = __ldg(A.upair + (size_t)a * A.n_ant + o);
         if (up < 0) continue;
-        const double *Mo = A.mom + ((size_t)bin * A.n_up + up) * MOM_E;
+        const float *Mo = A.mom + ((size_t)bin * A.n_up + up) * MOM_E;
         double2 Gd[4];
         gains_of(A, bin, o, Gd);
         const float2 g[2] = { f2(Gd[0]), f2(Gd[3]) };
@@ -623,8 +623,8 @@ static __global__ void __launch_bounds__(128) mom_normal_e_kernel(const MomNormA
                     }
 #pragma unroll
             for (int y = 0; y < 2; ++y) {
-                const double2 tv = __ldg(reinterpret_cast<const double2 *>(Mo + MOM_ET) + (p_side ? 2 * x + y : 2 * y + x));
-                const float2 tf = p_side ? make_float2((float)tv.x, (float)tv.y) : make_float2((float)tv.x, -(float)tv.y);
+                const float2 tv = __ldg(reinterpret_cast<const float2 *>(Mo + MOM_ET) + (p_side ? 2 * x + y : 2 * y + x));
+                const float2 tf = p_side ? tv : make_float2(tv.x, -tv.y);
                 const float2 t = cmul(g[y], tf);
                 bb[x].x += t.x;
                 bb[x].y += t.y;

@@ -6,7 +6,7 @@
 
 namespace qc {
 
-constexpr int MOM_N = 100;          // FP64 words per (interval, pair), full form: S 64, T 32, U 4
+constexpr int MOM_N = 100;          // FP32 words per (interval, pair), full form: S 64, T 32, U 4
 constexpr int MOM_T = 64, MOM_U = 96;
 // diagonal form (a diagonal or phase-only solved term with a term to its left): S' 16 (4x4
 // Hermitian packed as S), T' 8, U 1, one word of padding
@@ -33,7 +33,7 @@ struct MomArgs {
     int chunk_major;                     // 1: a unit's rows inside each chunk; 0: a row's chunks inside it
     DevTerm tn;                          // the solved term (maps)
     DevTerm to;                          // the fixed other term of a two-term chain (tables)
-    double *mom;                         // [bins][n_up][MOM_N or MOM_E]
+    float *mom;                          // [bins][n_up][MOM_N or MOM_E]
     const int *n_active;
 };
 
@@ -41,7 +41,7 @@ struct MomNormArgs {
     int n_bins, n_ant, n_up, type;       // type: QC_TERM_* (diag, full, phase)
     int form;                            // FORM_FULL or FORM_E
     const int *upair;                    // [n_ant][n_ant] unordered pair index or -1
-    const double *mom;                   // [bins][n_up][MOM_N or MOM_E]
+    const float *mom;                    // [bins][n_up][MOM_N or MOM_E]
     const double *params;                // FP64 gains of the solved term
     const uint8_t *active;               // [bins]
     const int *n_active;

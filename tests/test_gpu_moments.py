@@ -26,7 +26,7 @@ pytestmark = pytest.mark.gpu
 
 GAIN_TOL = 1e-4
 CHI2_TOL = 1e-5
-MOM_WORDS = 100          # FP64 words of sums per (interval, antenna pair)
+MOM_WORDS = 100          # FP32 words of sums per (interval, antenna pair)
 
 
 def _obs(seed, kind, n_ant=6, n_time=5, n_chan=45, ti=2, fi=7, noise=0.1, flag_frac=0.2):
@@ -208,7 +208,7 @@ def test_byte_count_is_one_pass_plus_the_sums():
     spec = obs.terms[0]
     n_bins = spec.n_tint * spec.n_fint
     n_pairs = len({(min(p, q), max(p, q)) for p, q in zip(obs.ant1, obs.ant2) if p != q})
-    per_iter = 2 * n_pairs * MOM_WORDS * 8 + 8 * obs.n_ant * 24
+    per_iter = 2 * n_pairs * MOM_WORDS * 4 + 8 * obs.n_ant * 24
     assert mom.acc_bytes == plain.acc_bytes + n_bins * per_iter
     assert mom.vis_iters == plain.vis_iters
 

@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--moments", action="store_true",
+                    help="plain workload: solve each term from per-(interval, pair) sums (qc_opts.moments)")
     ap.add_argument("--dist-backend", default="nccl", choices=["nccl", "gloo"],
                     help="process group of the multi-GPU mode (gloo: host-staged exchange, for checking the "
                          "sharded flow with several ranks on fewer GPUs)")
@@ -261,7 +263,9 @@ def plain_config(args, world=1):
     """The plain workload's config block (shared by the reference arm, so that both lines name the
     same workload)."""
     n_vis = args.n_ant * (args.n_ant - 1) // 2 * args.n_time * args.n_chan
-    return {"workload": WORKLOAD + (" (FP16 model)" if args.mixed else ""), "n_ant": args.n_ant,
+    return {"workload": WORKLOAD + (" (FP16 model)" if args.mixed else "")
+            + (", each term from per-(interval, pair) sums" if getattr(args, "moments", False) else ""),
+            "n_ant": args.n_ant,
             "n_time": args.n_time, "n_chan": args.n_chan, "n_vis": n_vis,
             "input_bytes_per_gpu": (n_vis * (64 if args.mixed else 80) + n_vis) // world,
             "l2": "inputs (25 GB) larger than L2 (129 MB)", "epochs": args.epochs, "max_iter": args.max_iter,
@@ -370,7 +374,7 @@ def main():
     def step():
         terms = make_terms(qc, setup, setup.n_ant, args.max_iter, world, rank)
         return solver.solve(terms, n_epochs=args.epochs, stream=stream, kernel=args.kernel,
-                            block_threads=args.block, allreduce=allreduce), terms
+                            block_threads=args.block, allreduce=allreduce, moments=args.moments), terms
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -424,6 +428,22 @@ def main():
                 "algorithmic_bytes_per_full_launch": algo_full,
                 "launch_ms_mean": acc_ms / max(1, acc_launches), "acc_share_of_step": acc_ms / ms if ms else None}
 
+    if args.moments:
+        # the dominant kernels are the passes forming the sums (one per term and epoch): each reads
+        # the folded weights of every sample and the data and model of usable ones
+        n_unflagged = int((obs["flag"] == 0).sum().item())
+        n_vis_local = int(obs["flag"].numel())
+        pass_bytes = 16 * n_vis_local + 64 * n_unflagged
+        n_pass = args.epochs * len(setup.terms) * len(stats)
+        pass_ms = sum(s.pass_ms for s in stats)
+        p_ach = pass_bytes * n_pass / (pass_ms / 1000.0) / 1e9 if pass_ms > 0 else None
+        roofline = {"bound": "hbm", "achieved": p_ach, "peak": hbm, "unit": "GB/s",
+                    "frac": (p_ach / hbm) if p_ach else None, "traffic": None,
+                    "peak_source": roofline["peak_source"],
+                    "kernel": "mom_pass_kernel (the pass forming a term's sums, one per term and epoch)",
+                    "algorithmic_bytes_per_launch": pass_bytes, "launch_ms_mean": pass_ms / max(1, n_pass),
+                    "pass_share_of_step": pass_ms / ms if ms else None,
+                    "iterations_ms_per_step": (acc_ms - pass_ms) / args.steps}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args, obs, setup)
@@ -446,7 +466,7 @@ def main():
             s = qc.Solver(host["data"], host["model"], host["weight"], host["flag"], *geo, model_fp16=args.mixed)
             terms = make_terms(qc, setup, setup.n_ant, args.max_iter, world, rank)
             st = s.solve(terms, n_epochs=args.epochs, kernel=args.kernel, block_threads=args.block,
-                         allreduce=allreduce)
+                         allreduce=allreduce, moments=args.moments)
             s.close()
             d2h = sum(t.gains.nbytes + t.gain_flags.nbytes + t.iters.nbytes for t in terms)
             return st.vis_iters, d2h

@@ -764,7 +764,8 @@ __host__ __device__ constexpr int mom_bl(int p, int q, int n) { return p * (2 * 
 __host__ __device__ inline size_t mom_smem_bytes(int max_ant)
 {
     const size_t m = ((size_t)max_ant * (max_ant - 1) / 2 * MOM_W * sizeof(float) + 15) / 16 * 16;
-    return m + (size_t)max_ant * 2 * sizeof(double2) + (size_t)max_ant * 6 * sizeof(double);
+    return m + (size_t)max_ant * 2 * sizeof(double2) + (size_t)max_ant * 6 * sizeof(double) +
+           (size_t)max_ant * 2 * sizeof(float2);
 }
 
 template <bool M16>
@@ -775,6 +776,7 @@ __global__ void __launch_bounds__(256) batch_moments_kernel(const BatchArgs a)
     float *mom = reinterpret_cast<float *>(msm);                                  // [n_bl][MOM_W]
     double2 *g64 = reinterpret_cast<double2 *>(msm + mom_bytes);                 // [max_ant][2]
     double *acc = reinterpret_cast<double *>(g64 + 2 * a.max_ant);               // [max_ant][6]
+    float2 *g32 = reinterpret_cast<float2 *>(acc + 6 * a.max_ant);               // [max_ant][2]
     __shared__ double red[2][8];
     __shared__ int s_done;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, n_warps = blockDim.x >> 5;
@@ -789,53 +791,80 @@ __global__ void __launch_bounds__(256) batch_moments_kernel(const BatchArgs a)
     }
     __syncthreads();
     // one pass over the samples: the baseline sums.  The lanes of a warp take consecutive
-    // samples; where they all belong to one baseline (a row of 32 channels or more) a
-    // transposed reduction leaves one total per sum and one shared add each, otherwise every
-    // lane adds its own (short runs of equal baselines: few conflicts).
+    // samples, two groups of 32 per step with both groups' loads issued first; where a group's
+    // samples all belong to one baseline (a row of 32 channels or more) a transposed reduction
+    // leaves one total per sum and one shared add each, otherwise every lane adds its own (short
+    // runs of equal baselines: few conflicts).  Sample indices are 32-bit within a problem.
     const long long n_samp = (long long)P.n_rows * nc;
-    for (long long base = (long long)warp * 32; base < n_samp; base += blockDim.x) {
-        const long long s = base + lane;
+    struct Samp {
+        int key;                 // the row's baseline slot (flagged samples too: keeps runs whole)
+        bool use;                // unflagged cross-correlation sample
+        float4 w, d0, d1, m0, m1;
+        uint4 h;
+        float sc;
+        bool conj;
+    };
+    auto load = [&](long long s) {
+        Samp x;
+        x.key = -1;
+        x.use = false;
+        x.conj = false;
+        if (s < n_samp) {
+            const int si = (int)s, row = si / nc;
+            const int2 pq = a.ants[P.row_off + row];
+            const long long sg = P.vis_off + s;
+            if (pq.x != pq.y) {
+                x.conj = pq.x > pq.y;
+                x.key = x.conj ? mom_bl(pq.y, pq.x, na) : mom_bl(pq.x, pq.y, na);
+                x.use = !(a.flag && a.flag[sg]);
+            }
+            if (x.use) {
+                x.d0 = a.vis[2 * sg];
+                x.d1 = a.vis[2 * sg + 1];
+                if constexpr (M16) {
+                    x.h = a.model16[sg];
+                    x.sc = a.row_scale[P.row_off + row];
+                } else {
+                    x.m0 = a.model[2 * sg];
+                    x.m1 = a.model[2 * sg + 1];
+                }
+                x.w = a.weight[sg];
+            }
+        }
+        return x;
+    };
+    auto add = [&](const Samp &x) {
         float v[16];
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = 0.f;
-        int key = -1;
-        if (s < n_samp) {
-            const int row = (int)(s / nc);
-            const int2 pq = a.ants[P.row_off + row];
-            const long long sg = P.vis_off + s;
-            if (pq.x != pq.y && !(a.flag && a.flag[sg])) {
-                J2 D = j_from(a.vis[2 * sg], a.vis[2 * sg + 1]);
-                J2 M;
-                if constexpr (M16) {
-                    const uint4 h = a.model16[sg];
-                    const float sc = a.row_scale[P.row_off + row];
-                    M.a = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.x)), sc);
-                    M.b = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.y)), sc);
-                    M.c = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.z)), sc);
-                    M.d = cscale(h2f(*reinterpret_cast<const __half2 *>(&h.w)), sc);
-                } else {
-                    M = j_from(a.model[2 * sg], a.model[2 * sg + 1]);
-                }
-                float4 w = a.weight[sg];
-                int p = pq.x, q = pq.y;
-                if (p > q) {      // the conjugate baseline: D, M -> D^H, M^H, weights permuted
-                    D = j_herm(D);
-                    M = j_herm(M);
-                    w = make_float4(w.x, w.z, w.y, w.w);
-                    const int t = p; p = q; q = t;
-                }
-                key = mom_bl(p, q, na);
-                const float2 Mv[4] = { M.a, M.b, M.c, M.d }, Dv[4] = { D.a, D.b, D.c, D.d };
-                const float wv[4] = { w.x, w.y, w.z, w.w };
+        if (x.use) {
+            J2 D = j_from(x.d0, x.d1);
+            J2 M;
+            if constexpr (M16) {
+                M.a = cscale(h2f(*reinterpret_cast<const __half2 *>(&x.h.x)), x.sc);
+                M.b = cscale(h2f(*reinterpret_cast<const __half2 *>(&x.h.y)), x.sc);
+                M.c = cscale(h2f(*reinterpret_cast<const __half2 *>(&x.h.z)), x.sc);
+                M.d = cscale(h2f(*reinterpret_cast<const __half2 *>(&x.h.w)), x.sc);
+            } else {
+                M = j_from(x.m0, x.m1);
+            }
+            float4 w = x.w;
+            if (x.conj) {     // the conjugate baseline: D, M -> D^H, M^H, weights permuted
+                D = j_herm(D);
+                M = j_herm(M);
+                w = make_float4(w.x, w.z, w.y, w.w);
+            }
+            const float2 Mv[4] = { M.a, M.b, M.c, M.d }, Dv[4] = { D.a, D.b, D.c, D.d };
+            const float wv[4] = { w.x, w.y, w.z, w.w };
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    v[c] = wv[c] * cnorm2(Mv[c]);
-                    const float2 t = cscale(cmulc(Dv[c], Mv[c]), wv[c]);      // w conj(m) d
-                    v[4 + 2 * c] = t.x;
-                    v[5 + 2 * c] = t.y;
-                }
+            for (int c = 0; c < 4; ++c) {
+                v[c] = wv[c] * cnorm2(Mv[c]);
+                const float2 t = cscale(cmulc(Dv[c], Mv[c]), wv[c]);      // w conj(m) d
+                v[4 + 2 * c] = t.x;
+                v[5 + 2 * c] = t.y;
             }
         }
+        const int key = x.key;
         const int k0 = __shfl_sync(0xffffffffu, key, 0);
         if (__all_sync(0xffffffffu, key == k0)) {
             if (k0 >= 0) {
@@ -859,25 +888,51 @@ __global__ void __launch_bounds__(256) batch_moments_kernel(const BatchArgs a)
                 v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
                 if ((lane & 1) == 0 && idx < MOM_W) atomicAdd(&mom[(size_t)k0 * MOM_W + idx], v[0]);
             }
-        } else if (key >= 0) {
+        } else {
+            // runs of equal keys (the samples of one row, when rows are shorter than 32): a
+            // segmented reduction per sum, one shared add per run; keys that repeat apart (two
+            // rows of one baseline in a group) add per lane
+            const unsigned m = __match_any_sync(0xffffffffu, key);
+            const unsigned lo = m & (0u - m);
+            const bool contig = ((m + lo) & m) == 0;          // the set bits of m are one run
+            if (__all_sync(0xffffffffu, contig)) {
+                const int seg_end = 32 - __clz(m);
+                const bool head = lane == __ffs(m) - 1;
 #pragma unroll
-            for (int i = 0; i < MOM_W; ++i) atomicAdd(&mom[(size_t)key * MOM_W + i], v[i]);
+                for (int i = 0; i < MOM_W; ++i) {
+                    float t = v[i];
+#pragma unroll
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const float o = __shfl_down_sync(0xffffffffu, t, d);
+                        if (lane + d < seg_end) t += o;
+                    }
+                    if (head && key >= 0) atomicAdd(&mom[(size_t)key * MOM_W + i], t);
+                }
+            } else if (key >= 0) {
+#pragma unroll
+                for (int i = 0; i < MOM_W; ++i) atomicAdd(&mom[(size_t)key * MOM_W + i], v[i]);
+            }
         }
+    };
+    for (long long base = (long long)warp * 64; base < n_samp; base += 2LL * blockDim.x) {
+        const Samp x0 = load(base + lane), x1 = load(base + 32 + lane);
+        add(x0);
+        add(x1);
     }
     __syncthreads();
     int k;
     for (k = 1; k <= a.max_iter; ++k) {
         // the normal equations of each antenna from the sums of its baselines (no atomics: one
         // thread per antenna, float32 sums as batch_kernel's accumulators)
+        for (int i = tid; i < 2 * na; i += blockDim.x) g32[i] = make_float2((float)g64[i].x, (float)g64[i].y);
+        __syncthreads();
         for (int ant = tid; ant < na; ant += blockDim.x) {
-            const float2 ga0 = make_float2((float)g64[2 * ant].x, (float)g64[2 * ant].y);
-            const float2 ga1 = make_float2((float)g64[2 * ant + 1].x, (float)g64[2 * ant + 1].y);
+            const float2 ga0 = g32[2 * ant], ga1 = g32[2 * ant + 1];
             float h0 = 0.f, h1 = 0.f;
             float2 j0 = make_float2(0.f, 0.f), j1 = j0;
             for (int o = 0; o < na; ++o) {
                 if (o == ant) continue;
-                const float2 go0 = make_float2((float)g64[2 * o].x, (float)g64[2 * o].y);
-                const float2 go1 = make_float2((float)g64[2 * o + 1].x, (float)g64[2 * o + 1].y);
+                const float2 go0 = g32[2 * o], go1 = g32[2 * o + 1];
                 const float ao0 = cnorm2(go0), ao1 = cnorm2(go1);
                 if (ant < o) {      // antenna p of (ant, o)
                     const float *m = mom + (size_t)mom_bl(ant, o, na) * MOM_W;

@@ -259,8 +259,8 @@ class Solver:
               kernel: int = 0, div_flag: bool = False, robust_nu: Optional[float] = None,
               moments: bool = False) -> Stats:
         """robust_nu: robust reweighting between epochs with nu degrees of freedom (None: off);
-        div_flag: flag (gain flag 2) and restore diverging gains; moments: a single-term chain
-        from per-(interval, baseline) sums (include/qc.h)."""
+        div_flag: flag (gain flag 2) and restore diverging gains; moments: solve each term of a
+        chain of one or two terms from per-(interval, antenna pair) sums (include/qc.h)."""
         arr = _terms_array(terms)
         cb = ALLREDUCE_FN(allreduce) if allreduce is not None else ALLREDUCE_FN()
         st = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))

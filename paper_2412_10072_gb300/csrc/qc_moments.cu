@@ -38,6 +38,13 @@ namespace qc {
 
 constexpr unsigned FULL_MASK = 0xffffffffu;
 
+// (re, im) += conj(x) y, four fused multiply-adds
+__device__ __forceinline__ void cacc_conj(float &re, float &im, float2 x, float2 y)
+{
+    re = fmaf(x.x, y.x, fmaf(x.y, y.y, re));
+    im = fmaf(x.x, y.y, fmaf(-x.y, y.x, im));
+}
+
 // One sample's terms added to a lane's register sums, full form (one lane per sample; words as
 // the slot: S[kj] at 16 kj, T[kj] at MOM_T + 8 kj, U[kj] at MOM_U + kj; all indices compile-time
 // constants after unrolling; X = R_p M R_q^H).
@@ -67,11 +74,7 @@ __device__ __forceinline__ void mom_add(float (&acc)[MOM_N], const J2 &D, const 
         const float2 wd = cscale(d[kj], wv[kj]);
         const int t = MOM_T + 8 * kj;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const float2 c = cmulc(wd, x[u]);             // conj(x_u) w d
-            acc[t + 2 * u] += c.x;
-            acc[t + 2 * u + 1] += c.y;
-        }
+        for (int u = 0; u < 4; ++u) cacc_conj(acc[t + 2 * u], acc[t + 2 * u + 1], x[u], wd);   // conj(x_u) w d
         acc[MOM_U + kj] = fmaf(wv[kj], cnorm2(d[kj]), acc[MOM_U + kj]);
     }
 }
@@ -96,35 +99,27 @@ __device__ __forceinline__ void mom_add_e(float (&acc)[MOM_EW], const J2 &D, con
             // E_kj,ab is non-zero only at (a, b) = (k, j): S' stays diagonal
             const float2 e = cmulc(cmul(lp[3 * k], m[kj]), lq[3 * j]);
             acc[kj] = fmaf(wv[kj], cnorm2(e), acc[kj]);
-            const float2 c = cmulc(cscale(d[kj], wv[kj]), e);           // conj(e) w d
-            acc[16 + 2 * kj] += c.x;
-            acc[17 + 2 * kj] += c.y;
+            cacc_conj(acc[16 + 2 * kj], acc[17 + 2 * kj], e, cscale(d[kj], wv[kj]));   // conj(e) w d
         } else {
             // sqrt(w) E_kj: S' += conj(e_u) e_v, T' += conj(e_u) sqrt(w) d
             const float sw = sqrtf(wv[kj]);
             float2 e[4];
 #pragma unroll
-            for (int a = 0; a < 2; ++a)
+            for (int a = 0; a < 2; ++a) {
+                const float2 l = cscale(lp[2 * k + a], sw);
 #pragma unroll
-                for (int b = 0; b < 2; ++b)
-                    e[2 * a + b] = cscale(cmul(lp[2 * k + a], cmulc(m[2 * a + b], lq[2 * j + b])), sw);
+                for (int b = 0; b < 2; ++b) e[2 * a + b] = cmul(l, cmulc(m[2 * a + b], lq[2 * j + b]));
+            }
 #pragma unroll
             for (int u = 0; u < 4; ++u) acc[u] = fmaf(e[u].x, e[u].x, fmaf(e[u].y, e[u].y, acc[u]));
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
-                for (int v = u + 1; v < 4; ++v) {
-                    const float2 c = cmulc(e[v], e[u]);                 // conj(e_u) e_v
-                    acc[4 + 2 * mom_pair(u, v)] += c.x;
-                    acc[5 + 2 * mom_pair(u, v)] += c.y;
-                }
+                for (int v = u + 1; v < 4; ++v)
+                    cacc_conj(acc[4 + 2 * mom_pair(u, v)], acc[5 + 2 * mom_pair(u, v)], e[u], e[v]);
             const float2 ds = cscale(d[kj], sw);
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const float2 c = cmulc(ds, e[u]);
-                acc[16 + 2 * u] += c.x;
-                acc[17 + 2 * u] += c.y;
-            }
+            for (int u = 0; u < 4; ++u) cacc_conj(acc[16 + 2 * u], acc[17 + 2 * u], e[u], ds);
         }
         acc[24] = fmaf(wv[kj], cnorm2(d[kj]), acc[24]);
     }
@@ -225,9 +220,10 @@ template <int FORM, int OK> struct MomRing {
     static constexpr int OFF_OP = 160, OFF_OQ = OFF_OP + 32 * NO, OFF_KEY = OFF_OQ + 32 * NO;
     static constexpr int OFF_META = OFF_KEY + 8;
     static constexpr int STAGE = OFF_META + 1;               // float4 per stage
-    // the full form keeps 100 sums per lane (two CTAs of 4 warps per SM), the diagonal form 25
-    static constexpr int PER_SM = FORM == FORM_FULL ? 2 : 3;
-    static constexpr int DEPTH = FORM == FORM_FULL ? (NO == 2 ? 5 : 6) : (NO == 2 ? 3 : 4);
+    // three CTAs of 4 warps per SM (the full form's 100 register sums fit 168 registers); ring
+    // depth as the shared memory of three CTAs allows
+    static constexpr int PER_SM = 3;
+    static constexpr int DEPTH = NO == 2 ? 3 : (NO == 1 ? 4 : 6);
     static constexpr size_t SMEM = (size_t)4 * DEPTH * STAGE * sizeof(float4);
 };
 
@@ -362,21 +358,7 @@ static __global__ void __launch_bounds__(128, MomRing<FORM, OK>::PER_SM) mom_pas
         cur.issue(a, lane, ring + (size_t)is * R::STAGE);
         if (++is == R::DEPTH) is = 0;
     }
-    int key_cur = -1, stage = 0;
-    for (;;) {
-        __syncwarp();                          // every lane is done with the stage about to be refilled
-        cur.issue(a, lane, ring + (size_t)is * R::STAGE);
-        if (++is == R::DEPTH) is = 0;
-        cp_async_wait<R::DEPTH - 1>();
-        __syncwarp();
-        const float4 *st = ring + (size_t)stage * R::STAGE;
-        const int meta = reinterpret_cast<const int *>(st + R::OFF_META)[0];
-        if (meta & MOM_END) break;
-        const int key = reinterpret_cast<const int *>(st + R::OFF_KEY)[lane];
-        if (__any_sync(FULL_MASK, key != key_cur)) {
-            mom_flush<NW>(acc, key_cur, lane, a.mom, stride);
-            key_cur = key;
-        }
+    auto add = [&](const float4 *st, int meta) {
         float4 w = st[128 + lane];
         if (w.x != 0.f || w.y != 0.f || w.z != 0.f || w.w != 0.f) {
             J2 D = j_from(st[lane], st[32 + lane]), M = j_from(st[64 + lane], st[96 + lane]);
@@ -399,9 +381,34 @@ static __global__ void __launch_bounds__(128, MomRing<FORM, OK>::PER_SM) mom_pas
                 mom_add_e<OK>(acc, D, M, fac_jones<OK>(st + R::OFF_OP + oc), fac_jones<OK>(st + R::OFF_OQ + oc), w);
             }
         }
+    };
+    // runs of steps with unchanged keys: the inner loop only adds; a key change leaves it to
+    // flush the sums, then adds the step that changed the key
+    int key_cur = -1, stage = 0;
+    bool done = false;
+    for (;;) {
+        const float4 *st;
+        int meta = 0, key = -1;
+        for (;;) {
+            __syncwarp();                      // every lane is done with the stage about to be refilled
+            cur.issue(a, lane, ring + (size_t)is * R::STAGE);
+            if (++is == R::DEPTH) is = 0;
+            cp_async_wait<R::DEPTH - 1>();
+            __syncwarp();
+            st = ring + (size_t)stage * R::STAGE;
+            meta = reinterpret_cast<const int *>(st + R::OFF_META)[0];
+            if (meta & MOM_END) { done = true; break; }
+            key = reinterpret_cast<const int *>(st + R::OFF_KEY)[lane];
+            if (__any_sync(FULL_MASK, key != key_cur)) break;
+            add(st, meta);
+            if (++stage == R::DEPTH) stage = 0;
+        }
+        mom_flush<NW>(acc, key_cur, lane, a.mom, stride);
+        if (done) break;
+        key_cur = key;
+        add(st, meta);
         if (++stage == R::DEPTH) stage = 0;
     }
-    mom_flush<NW>(acc, key_cur, lane, a.mom, stride);
     cp_async_wait<0>();
 }
 

@@ -342,18 +342,28 @@ __global__ void __launch_bounds__(256, 2) acc_stream_kernel(const StreamArgs a)
     int ci_p = -1, ci_q = -1, act_key = -1, since_flush = 0;
     bool act_val = false;
     J2 cGp = j_identity(), cGq = j_identity();
-    for (;;) {
-        const int4 e = eA0;
-        const int4 e1 = eA1;
-        if (e.x == STREAM_END) break;
-        const int2 fm = fmA;
-        const int nst = stage + 1 == DEPTH ? 0 : stage + 1;
+    // a step in two parts: (A) its entries, the other term's and the solved term's gain entries,
+    // the issue of the copy DEPTH - 1 steps ahead, the wait and the lane's key; (B) the sample's
+    // arithmetic and the advance.  Runs of steps that need no flush stay in an inner loop that
+    // only adds; a flush leaves it (keeping the register sums out of the flush's code path in
+    // the loop that runs every step), then the step's part B follows.
+    int4 e = eA0, e1 = eA1, eB0 = eA0, eB1 = eA1;
+    int2 fm = fmA, fmB = fmA;
+    int nst = 0, key = -1;
+    bool in = false, live = false;
+    J2 Lp, Lq, Rp, Rq;
+    auto part_a = [&]() -> bool {
+        e = eA0;
+        e1 = eA1;
+        if (e.x == STREAM_END) return false;
+        fm = fmA;
+        nst = stage + 1 == DEPTH ? 0 : stage + 1;
         // the next step: its entry and channel maps
-        const int4 eB0 = meta[2 * nst], eB1 = meta[2 * nst + 1];
-        const int2 fmB = read_map(eB0, eB1);
+        eB0 = meta[2 * nst];
+        eB1 = meta[2 * nst + 1];
+        fmB = read_map(eB0, eB1);
         // this step's entries of the other term, loaded here so that the issue below covers
         // their latency
-        J2 Lp, Lq, Rp, Rq;
         if (e.z >= 0) {
             const int p = e.y & 0xffff, q = e.y >> 16;
             if constexpr (LK != KIND_NONE) {
@@ -365,9 +375,9 @@ __global__ void __launch_bounds__(256, 2) acc_stream_kernel(const StreamArgs a)
                 Rq = fetch_k<RK>(a.to, n_ant, e.w, fm.y, q);
             }
             // the solved term's entries stay in registers while the lane's table index is unchanged
-            const bool in = e1.x + lane < n_chan;
-            const int ip = in ? (e.z * n_ant + p) * a.tn.n_fint + fm.x : ci_p;
-            const int iq = in ? (e.z * n_ant + q) * a.tn.n_fint + fm.x : ci_q;
+            const bool inr = e1.x + lane < n_chan;
+            const int ip = inr ? (e.z * n_ant + p) * a.tn.n_fint + fm.x : ci_p;
+            const int iq = inr ? (e.z * n_ant + q) * a.tn.n_fint + fm.x : ci_q;
             if (__any_sync(0xffffffffu, ip != ci_p || iq != ci_q)) {
                 if (ip != ci_p) { cGp = fetch_k<GK>(a.tn, n_ant, e.z, fm.x, p); ci_p = ip; }
                 if (iq != ci_q) { cGq = fetch_k<GK>(a.tn, n_ant, e.z, fm.x, q); ci_q = iq; }
@@ -376,21 +386,13 @@ __global__ void __launch_bounds__(256, 2) acc_stream_kernel(const StreamArgs a)
         issue();
         cp_async_wait<DEPTH - 1>();
         __syncwarp();
-        const bool live = e.z >= 0;                 // warp-uniform
+        live = e.z >= 0;                            // warp-uniform
         const int c = e1.x + lane;
-        const bool in = live && c < n_chan;
-        const int key = in ? e.z * a.tn.n_fint + fm.x : -1;
-        if (live) {
-            bool change = e.y != cur_pq || key != cur_key;
-            if constexpr (M16) change = change || since_flush >= FLUSH_EVERY;
-            if constexpr (M16) ++since_flush;
-            if (__any_sync(0xffffffffu, change && cur_key >= 0)) {
-                if constexpr (M16) since_flush = 1;
-                flush_pair<KR, KG, Lay>(Ap, Aq, cur_key, cur_pq, lane, a.active, a.acc, n_ant);
-            }
-            cur_key = key;
-            cur_pq = e.y;
-        }
+        in = live && c < n_chan;
+        key = in ? e.z * a.tn.n_fint + fm.x : -1;
+        return true;
+    };
+    auto part_b = [&]() {
         const float4 *slot = ring + (size_t)stage * V4 * 32 + lane;
         const float4 w = slot[M16 ? 96 : 128];
         bool ok = in && (w.x != 0.f || w.y != 0.f || w.z != 0.f || w.w != 0.f);
@@ -408,8 +410,30 @@ __global__ void __launch_bounds__(256, 2) acc_stream_kernel(const StreamArgs a)
             sample_math<TS, LK, RK, KAHAN>(Lp, Gp, Rp, Lq, Gq, Rq, Dm, M, w, Ap, Aq);
         }
         fmA = fmB;
-        eA0 = eB0; eA1 = eB1;
+        eA0 = eB0;
+        eA1 = eB1;
         stage = nst;
+    };
+    for (;;) {
+        bool ended = false;
+        for (;;) {
+            if (!part_a()) { ended = true; break; }
+            if (live) {
+                bool change = e.y != cur_pq || key != cur_key;
+                if constexpr (M16) change = change || since_flush >= FLUSH_EVERY;
+                if constexpr (M16) ++since_flush;
+                if (__any_sync(0xffffffffu, change && cur_key >= 0)) break;
+                cur_key = key;
+                cur_pq = e.y;
+            }
+            part_b();
+        }
+        if (ended) break;
+        if constexpr (M16) since_flush = 1;
+        flush_pair<KR, KG, Lay>(Ap, Aq, cur_key, cur_pq, lane, a.active, a.acc, n_ant);
+        cur_key = key;
+        cur_pq = e.y;
+        part_b();
     }
     if (__any_sync(0xffffffffu, cur_key >= 0)) flush_pair<KR, KG, Lay>(Ap, Aq, cur_key, cur_pq, lane, a.active, a.acc, n_ant);
     cp_async_wait<0>();

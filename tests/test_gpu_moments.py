@@ -1,15 +1,18 @@
-"""Single-term chains solved from per-(interval, baseline) sums (qc_opts.moments), against the
-oracle and against the per-sample GPU path.
+"""Terms solved from per-(interval, antenna pair) sums (qc_opts.moments), against the oracle and
+against the per-sample GPU path.
 
-- One Gauss-Newton step of a diagonal, full or phase-only term from the sums equals the oracle's
-  step (relative to the size of the step), with both row orientations, random per-correlation
-  weights, flags, a ragged last chunk (45 channels) and intervals that straddle the 32-channel
-  chunks; gain flags bit for bit.
+- One Gauss-Newton step of a diagonal, full or phase-only single term from the sums equals the
+  oracle's step (relative to the size of the step), with both row orientations, random
+  per-correlation weights, flags, a ragged last chunk (45 channels) and intervals that straddle
+  the 32-channel chunks; gain flags bit for bit.
+- Two-term chains: each term's single step against the oracle, the first from the full form with
+  the second folded into the model, the second from the diagonal form when it is diagonal or
+  phase-only (a full second term takes the per-sample path); converged G+B and G+phase chains.
 - Converged solves: gains after referencing within 1e-4 and chi^2 within 1e-5 of the oracle for
   the small plain workload and for full and phase-only terms; intervals one time wide that span
-  several chunks (the sums of a row flushed once per chunk group); dead antennas with NaN data
-  under their flags; fully flagged intervals; autocorrelations; robust reweighting across epochs.
-- Chains the option does not cover (two terms) solve exactly as without it.
+  several chunks; dead antennas with NaN data under their flags; fully flagged intervals;
+  autocorrelations; robust reweighting across epochs.
+- Three-term chains are not solved from sums: the option changes nothing.
 - Statistics: the pass time lies inside the accumulate time, and the byte count is one pass over
   the samples plus, per iteration and active interval, the sums read on both sides and the
   accumulators written.

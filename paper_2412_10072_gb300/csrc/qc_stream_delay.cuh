@@ -175,18 +175,27 @@ __global__ void __launch_bounds__(256, 2) acc_delay_kernel(const DelayStreamArgs
     int ci_p = -1, ci_q = -1, act_key = -1, since_flush = 0;
     bool act_val = false;
     J2 cGp = j_identity(), cGq = j_identity();
-    for (;;) {
-        const int4 e = eA0;
-        const int4 e1 = eA1;
-        if (e.x == STREAM_END) break;
-        const int2 fm = fmA;
-        const int nst = stage + 1 == DEPTH ? 0 : stage + 1;
-        const int4 eB0 = meta[2 * nst], eB1 = meta[2 * nst + 1];
-        const int2 fmB = read_map(eB0, eB1);
+    // a step in two parts, as in acc_stream_kernel: (A) entries, gains, the issue ahead, the wait
+    // and the lane's key; (B) the arithmetic and the advance.  Steps that need no flush stay in an
+    // inner loop that only adds; the flush runs outside it.
+    int4 e = eA0, e1 = eA1, eB0 = eA0, eB1 = eA1;
+    int2 fm = fmA, fmB = fmA;
+    int nst = 0, key = -1;
+    bool in = false, live = false;
+    float om = 0.f;
+    J2 Lp, Lq, Rp, Rq;
+    auto part_a = [&]() -> bool {
+        e = eA0;
+        e1 = eA1;
+        if (e.x == STREAM_END) return false;
+        fm = fmA;
+        nst = stage + 1 == DEPTH ? 0 : stage + 1;
+        eB0 = meta[2 * nst];
+        eB1 = meta[2 * nst + 1];
+        fmB = read_map(eB0, eB1);
         const int c = e1.x + lane;
         // this step's gain entries and the lane's omega, loaded before the issue below
-        J2 Lp, Lq, Rp, Rq;
-        float om = 0.f;
+        om = 0.f;
         if (e.z >= 0) {
             const int p = e.y & 0xffff, q = e.y >> 16;
             if constexpr (LK != KIND_NONE) {
@@ -197,11 +206,11 @@ __global__ void __launch_bounds__(256, 2) acc_delay_kernel(const DelayStreamArgs
                 Rp = fetch_k<RK>(a.to, n_ant, e.w, fm.y, p);
                 Rq = fetch_k<RK>(a.to, n_ant, e.w, fm.y, q);
             }
-            const bool in = c < n_chan;
-            if (in) om = __ldg(da.omega + c);
+            const bool inr = c < n_chan;
+            if (inr) om = __ldg(da.omega + c);
             // the delay term's gains at the lane's channel: table [n_tint][n_ant][n_chan]
-            const int ip = in ? (e.z * n_ant + p) * n_chan + c : ci_p;
-            const int iq = in ? (e.z * n_ant + q) * n_chan + c : ci_q;
+            const int ip = inr ? (e.z * n_ant + p) * n_chan + c : ci_p;
+            const int iq = inr ? (e.z * n_ant + q) * n_chan + c : ci_q;
             if (__any_sync(0xffffffffu, ip != ci_p || iq != ci_q)) {
                 if (ip != ci_p) { cGp = j_diag(__ldg(a.tn.tab + ip)); ci_p = ip; }
                 if (iq != ci_q) { cGq = j_diag(__ldg(a.tn.tab + iq)); ci_q = iq; }
@@ -210,20 +219,12 @@ __global__ void __launch_bounds__(256, 2) acc_delay_kernel(const DelayStreamArgs
         issue();
         cp_async_wait<DEPTH - 1>();
         __syncwarp();
-        const bool live = e.z >= 0;
-        const bool in = live && c < n_chan;
-        const int key = in ? e.z * a.tn.n_fint + fm.x : -1;
-        if (live) {
-            bool change = e.y != cur_pq || key != cur_key;
-            if constexpr (M16) change = change || since_flush >= FLUSH_EVERY;
-            if constexpr (M16) ++since_flush;
-            if (__any_sync(0xffffffffu, change && cur_key >= 0)) {
-                if constexpr (M16) since_flush = 1;
-                flush_pair<KR, KG, Lay>(Ap, Aq, cur_key, cur_pq, lane, a.active, a.acc, n_ant);
-            }
-            cur_key = key;
-            cur_pq = e.y;
-        }
+        live = e.z >= 0;
+        in = live && c < n_chan;
+        key = in ? e.z * a.tn.n_fint + fm.x : -1;
+        return true;
+    };
+    auto part_b = [&]() {
         const float4 *slot = ring + (size_t)stage * V4 * 32 + lane;
         const float4 w = slot[M16 ? 96 : 128];
         bool ok = in && (w.x != 0.f || w.y != 0.f || w.z != 0.f || w.w != 0.f);
@@ -241,8 +242,30 @@ __global__ void __launch_bounds__(256, 2) acc_delay_kernel(const DelayStreamArgs
             delay_sample_math<LK, RK>(Lp, Gp, Rp, Lq, Gq, Rq, Dm, M, w, om, Ap, Aq);
         }
         fmA = fmB;
-        eA0 = eB0; eA1 = eB1;
+        eA0 = eB0;
+        eA1 = eB1;
         stage = nst;
+    };
+    for (;;) {
+        bool ended = false;
+        for (;;) {
+            if (!part_a()) { ended = true; break; }
+            if (live) {
+                bool change = e.y != cur_pq || key != cur_key;
+                if constexpr (M16) change = change || since_flush >= FLUSH_EVERY;
+                if constexpr (M16) ++since_flush;
+                if (__any_sync(0xffffffffu, change && cur_key >= 0)) break;
+                cur_key = key;
+                cur_pq = e.y;
+            }
+            part_b();
+        }
+        if (ended) break;
+        if constexpr (M16) since_flush = 1;
+        flush_pair<KR, KG, Lay>(Ap, Aq, cur_key, cur_pq, lane, a.active, a.acc, n_ant);
+        cur_key = key;
+        cur_pq = e.y;
+        part_b();
     }
     if (__any_sync(0xffffffffu, cur_key >= 0)) flush_pair<KR, KG, Lay>(Ap, Aq, cur_key, cur_pq, lane, a.active, a.acc, n_ant);
     cp_async_wait<0>();

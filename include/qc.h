@@ -219,7 +219,7 @@ typedef struct {
  *    U[kj] = sum w_kj |D_kj|^2 (100 FP32 words per interval and pair);
  *  - diagonal form, a diagonal or phase-only solved term with a term L to its left:
  *    with E_kj,ab = L_p,ka M_ab conj(L_q,jb), S'[u][v] = sum sum_kj w_kj conj(E_kj,u)
- *    E_kj,v, T'[u] = sum sum_kj w_kj conj(E_kj,u) D_kj (26 FP32 words per interval and pair).
+ *    E_kj,v, T'[u] = sum sum_kj w_kj conj(E_kj,u) D_kj (28 FP32 words per interval and pair).
  * Other solves (a full-Jones term with a term to its left, longer chains, sums of 2^31
  * or more slots) ignore the option.  qc_stats.vis_iters counts the samples of the
  * active intervals per iteration as without it; qc_stats.acc_bytes counts the pass (the

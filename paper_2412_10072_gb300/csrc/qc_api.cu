@@ -1476,6 +1476,8 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
         mn.upair = d_upair;
         mn.mom = ma.mom;
         mn.params = (const double *)B.params.ptr;
+        mn.tab = (const float4 *)B.tab.ptr;
+        mn.n_fint = t.n_fint;
         mn.active = (const uint8_t *)B.active.ptr;
         mn.acc = (double *)B.acc.ptr;
         ua.bin_nbytes = (const long long *)((char *)B.mom.ptr + mom_cnt_off);

@@ -28,7 +28,7 @@
 // antenna's blocks from them and the current gains in FP32 (mom_normal_kernel), JHr = b - JHJ g
 // and everything after it in FP64, in the update kernel's accumulator layout (a diagonal or
 // phase-only term of the full form takes the (0, 3) rows and columns).  An iteration then reads
-// 400 or 104 B per (interval, pair) instead of 81 B per sample.
+// 400 or 112 B per (interval, pair) instead of 81 B per sample.
 #include "qc_internal.h"
 
 #include <algorithm>
@@ -431,19 +431,41 @@ __device__ __forceinline__ void gains_of(const MomNormArgs &A, int bin, int ant,
 }
 
 __device__ __forceinline__ float2 f2(double2 a) { return make_float2((float)a.x, (float)a.y); }
-// element (u, v) of the Hermitian S block kj of a slot, in FP32 (u, v compile-time after unrolling)
-__device__ __forceinline__ float2 slot_S(const float *Mo, int kj, int u, int v)
-{
-    const float *s = Mo + 16 * kj;
-    if (u == v) return make_float2(__ldg(s + u), 0.f);
-    const int i = u < v ? mom_pair(u, v) : mom_pair(v, u);
-    const float2 x = __ldg(reinterpret_cast<const float2 *>(s + 4 + 2 * i));
-    return u < v ? x : make_float2(x.x, -x.y);
-}
 
-__device__ __forceinline__ float2 slot_T(const float *Mo, int kj, int u)
+// a slot's words held in registers (loaded as 16-byte or 8-byte vectors); word i of the slot
+template <int NV> struct SlotRegs {
+    float4 v[NV];
+    __device__ __forceinline__ float at(int i) const
+    {
+        const float4 &x = v[i >> 2];
+        const int c = i & 3;
+        return c == 0 ? x.x : c == 1 ? x.y : c == 2 ? x.z : x.w;
+    }
+    // element (u, v) of the Hermitian S block at word `base` (u, v compile-time after unrolling)
+    __device__ __forceinline__ float2 S(int base, int u, int v) const
+    {
+        if (u == v) return make_float2(at(base + u), 0.f);
+        const int i = base + 4 + 2 * (u < v ? mom_pair(u, v) : mom_pair(v, u));
+        return u < v ? make_float2(at(i), at(i + 1)) : make_float2(at(i), -at(i + 1));
+    }
+    __device__ __forceinline__ float2 C(int i) const { return make_float2(at(i), at(i + 1)); }
+};
+
+// the other antenna's gains from the solved term's FP32 table (the update kernel writes it with
+// every update): row-major entries, a diagonal or phase-only term as diag(g_0, g_1)
+__device__ __forceinline__ void gains_f32(const MomNormArgs &A, int bin, int ant, float2 G[4])
 {
-    return __ldg(reinterpret_cast<const float2 *>(Mo + MOM_T + 8 * kj + 2 * u));
+    const int tint = bin / A.n_fint, fint = bin - tint * A.n_fint;
+    const size_t idx = ((size_t)tint * A.n_ant + ant) * A.n_fint + fint;
+    if (A.type == QC_TERM_FULL) {
+        const float4 lo = __ldg(A.tab + 2 * idx), hi = __ldg(A.tab + 2 * idx + 1);
+        G[0] = make_float2(lo.x, lo.y); G[1] = make_float2(lo.z, lo.w);
+        G[2] = make_float2(hi.x, hi.y); G[3] = make_float2(hi.z, hi.w);
+    } else {
+        const float4 d = __ldg(A.tab + idx);
+        G[0] = make_float2(d.x, d.y); G[3] = make_float2(d.z, d.w);
+        G[1] = G[2] = make_float2(0.f, 0.f);
+    }
 }
 
 // One warp per (interval, antenna a): lanes take the other antennas o, form the contributions
@@ -470,12 +492,12 @@ static __global__ void __launch_bounds__(128) mom_normal_kernel(const MomNormArg
         if (o == a) continue;
         const int up = __ldg(A.upair + (size_t)a * A.n_ant + o);
         if (up < 0) continue;
-        const float *Mo = A.mom + ((size_t)bin * A.n_up + up) * MOM_N;
-        double2 Gd[4];
-        gains_of(A, bin, o, Gd);
-        float2 G[4];
+        SlotRegs<MOM_N / 4> sl;
+        const float4 *Mo = reinterpret_cast<const float4 *>(A.mom + ((size_t)bin * A.n_up + up) * MOM_N);
 #pragma unroll
-        for (int e = 0; e < 4; ++e) G[e] = f2(Gd[e]);
+        for (int i = 0; i < MOM_N / 4; ++i) sl.v[i] = __ldg(Mo + i);
+        float2 G[4];
+        gains_f32(A, bin, o, G);
         const bool p_side = a < o;           // the sums are oriented with the smaller index first
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
@@ -487,7 +509,7 @@ static __global__ void __launch_bounds__(128) mom_normal_kernel(const MomNormArg
                 for (int m2 = 0; m2 < 2; ++m2) gg[m][m2] = cmulc(G[2 * j + m], G[2 * j + m2]);
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
-                const int kj = p_side ? 2 * k + j : 2 * j + k;
+                const int kp = 2 * k + j, kq = 2 * j + k;      // the slot block for the p and the q side
 #pragma unroll
                 for (int l = 0; l < 2; ++l)
 #pragma unroll
@@ -498,8 +520,8 @@ static __global__ void __launch_bounds__(128) mom_normal_kernel(const MomNormArg
 #pragma unroll
                             for (int m2 = 0; m2 < 2; ++m2) {
                                 // p side: S[kj][(l,m)][(l2,m2)]; q side: conj(S[jk][(m,l)][(m2,l2)])
-                                const float2 sv = p_side ? slot_S(Mo, kj, 2 * l + m, 2 * l2 + m2)
-                                                         : cconj(slot_S(Mo, kj, 2 * m + l, 2 * m2 + l2));
+                                const float2 sv = p_side ? sl.S(16 * kp, 2 * l + m, 2 * l2 + m2)
+                                                         : cconj(sl.S(16 * kq, 2 * m + l, 2 * m2 + l2));
                                 const float2 t = cmul(gg[m][m2], sv);
                                 acc.x += t.x;
                                 acc.y += t.y;
@@ -512,7 +534,8 @@ static __global__ void __launch_bounds__(128) mom_normal_kernel(const MomNormArg
                 for (int l = 0; l < 2; ++l)
 #pragma unroll
                     for (int m = 0; m < 2; ++m) {
-                        const float2 tv = p_side ? slot_T(Mo, kj, 2 * l + m) : cconj(slot_T(Mo, kj, 2 * m + l));
+                        const float2 tv = p_side ? sl.C(MOM_T + 8 * kp + 2 * (2 * l + m))
+                                                 : cconj(sl.C(MOM_T + 8 * kq + 2 * (2 * m + l)));
                         const float2 t = cmul(G[2 * j + m], tv);
                         b[2 * k + l].x += t.x;
                         b[2 * k + l].y += t.y;
@@ -601,10 +624,13 @@ static __global__ void __launch_bounds__(128) mom_normal_e_kernel(const MomNormA
         if (o == a) continue;
         const int up = __ldg(A.upair + (size_t)a * A.n_ant + o);
         if (up < 0) continue;
-        const float *Mo = A.mom + ((size_t)bin * A.n_up + up) * MOM_E;
-        double2 Gd[4];
-        gains_of(A, bin, o, Gd);
-        const float2 g[2] = { f2(Gd[0]), f2(Gd[3]) };
+        SlotRegs<MOM_E / 4> sl;
+        const float4 *Mo = reinterpret_cast<const float4 *>(A.mom + ((size_t)bin * A.n_up + up) * MOM_E);
+#pragma unroll
+        for (int i = 0; i < MOM_E / 4; ++i) sl.v[i] = __ldg(Mo + i);
+        float2 Go[4];
+        gains_f32(A, bin, o, Go);
+        const float2 g[2] = { Go[0], Go[3] };
         const bool p_side = a < o;
         // the slot's S' entry for this antenna's parameters (x, x') and the other's (y, y'):
         // p side S'[(x,y)][(x',y')] with the other's gains g_y conj(g_y'); q side
@@ -622,16 +648,15 @@ static __global__ void __launch_bounds__(128) mom_normal_e_kernel(const MomNormA
 #pragma unroll
                     for (int y2 = 0; y2 < 2; ++y2) {
                         const float2 gg = cmulc(g[y], g[y2]);
-                        const float2 sv = p_side ? slot_S(Mo, 0, 2 * x + y, 2 * x2 + y2)
-                                                 : cconj(slot_S(Mo, 0, 2 * y + x, 2 * y2 + x2));
+                        const float2 sv = p_side ? sl.S(0, 2 * x + y, 2 * x2 + y2)
+                                                 : cconj(sl.S(0, 2 * y + x, 2 * y2 + x2));
                         const float2 t = cmul(gg, sv);
                         hh[x + x2].x += t.x;
                         hh[x + x2].y += t.y;
                     }
 #pragma unroll
             for (int y = 0; y < 2; ++y) {
-                const float2 tv = __ldg(reinterpret_cast<const float2 *>(Mo + MOM_ET) + (p_side ? 2 * x + y : 2 * y + x));
-                const float2 tf = p_side ? tv : make_float2(tv.x, -tv.y);
+                const float2 tf = p_side ? sl.C(MOM_ET + 2 * (2 * x + y)) : cconj(sl.C(MOM_ET + 2 * (2 * y + x)));
                 const float2 t = cmul(g[y], tf);
                 bb[x].x += t.x;
                 bb[x].y += t.y;

@@ -9,8 +9,8 @@ namespace qc {
 constexpr int MOM_N = 100;          // FP32 words per (interval, pair), full form: S 64, T 32, U 4
 constexpr int MOM_T = 64, MOM_U = 96;
 // diagonal form (a diagonal or phase-only solved term with a term to its left): S' 16 (4x4
-// Hermitian packed as S), T' 8, U 1, one word of padding
-constexpr int MOM_E = 26;
+// Hermitian packed as S), T' 8, U 1, three words of padding (slots of whole 16-byte vectors)
+constexpr int MOM_E = 28;
 constexpr int MOM_ET = 16, MOM_EU = 24;
 constexpr int FORM_FULL = 0, FORM_E = 1;
 
@@ -43,6 +43,8 @@ struct MomNormArgs {
     const int *upair;                    // [n_ant][n_ant] unordered pair index or -1
     const float *mom;                    // [bins][n_up][MOM_N or MOM_E]
     const double *params;                // FP64 gains of the solved term
+    const float4 *tab;                   // their FP32 table [n_tint][n_ant][n_fint] x (1 | 2)
+    int n_fint;
     const uint8_t *active;               // [bins]
     const int *n_active;
     double *acc;                         // [bins][n_ant][KG] (written)

@@ -649,30 +649,55 @@ __device__ int block_solve(double2 (&A)[N][N], const double2 (&b)[N], double2 (&
 {
     auto cabs = [](double2 z) { return sqrt(z.x * z.x + z.y * z.y); };
     auto cm = [](double2 u, double2 v) { return make_double2(u.x * v.x - u.y * v.y, u.x * v.y + u.y * v.x); };
-    auto cdiv = [](double2 u, double2 v) {
-        const double den = v.x * v.x + v.y * v.y;
-        return make_double2((u.x * v.x + u.y * v.y) / den, (u.y * v.x - u.x * v.y) / den);
-    };
     double trace = 0, anorm = 0;
     for (int i = 0; i < N; ++i) trace += A[i][i].x;
     if (!(trace > 0)) return 1;
+    if constexpr (N == 2) {
+        // closed form: A^-1 = [[d, -b], [-c, a]] / (a d - b c); the same singularity tests (a zero
+        // determinant is a zero pivot; reciprocal 1-norm condition number from the inverse)
+        const double2 a = A[0][0], bb = A[0][1], c = A[1][0], d = A[1][1];
+        const double2 ad = cm(a, d), bc = cm(bb, c);
+        const double2 det = make_double2(ad.x - bc.x, ad.y - bc.y);
+        const double den = det.x * det.x + det.y * det.y;
+        if (!(den > 0)) return 1;
+        const double2 r = make_double2(det.x / den, -det.y / den);       // 1 / det
+        const double2 i00 = cm(d, r), i11 = cm(a, r);
+        const double2 i01 = cm(make_double2(-bb.x, -bb.y), r), i10 = cm(make_double2(-c.x, -c.y), r);
+        anorm = fmax(cabs(a) + cabs(c), cabs(bb) + cabs(d));
+        const double inorm = fmax(cabs(i00) + cabs(i10), cabs(i01) + cabs(i11));
+        if (!(1.0 / (anorm * inorm) >= 1e-12)) return 1;
+        const double2 t0 = cm(i00, b[0]), t1 = cm(i01, b[1]), t2 = cm(i10, b[0]), t3 = cm(i11, b[1]);
+        x[0] = make_double2(t0.x + t1.x, t0.y + t1.y);
+        x[1] = make_double2(t2.x + t3.x, t2.y + t3.y);
+        return 0;
+    }
     for (int j = 0; j < N; ++j) {
         double s = 0;
         for (int i = 0; i < N; ++i) s += cabs(A[i][j]);
         anorm = fmax(anorm, s);
     }
+    // partial pivoting on |.|^2 (the same order as |.|); divisions by a pivot as products with
+    // its reciprocal, one reciprocal per pivot (FP64 division is slow on this part)
+    auto cn2 = [](double2 z) { return z.x * z.x + z.y * z.y; };
+    auto crecip = [](double2 v) {
+        const double den = v.x * v.x + v.y * v.y;
+        const double r = 1.0 / den;
+        return make_double2(v.x * r, -v.y * r);
+    };
     int piv[N];
+    double2 rpiv[N];
     for (int i = 0; i < N; ++i) piv[i] = i;
     for (int k = 0; k < N; ++k) {
         int m = k;
-        for (int i = k + 1; i < N; ++i) if (cabs(A[i][k]) > cabs(A[m][k])) m = i;
-        if (cabs(A[m][k]) == 0) return 1;
+        for (int i = k + 1; i < N; ++i) if (cn2(A[i][k]) > cn2(A[m][k])) m = i;
+        if (cn2(A[m][k]) == 0) return 1;
         if (m != k) {
             for (int j = 0; j < N; ++j) { double2 t = A[k][j]; A[k][j] = A[m][j]; A[m][j] = t; }
             int t = piv[k]; piv[k] = piv[m]; piv[m] = t;
         }
+        rpiv[k] = crecip(A[k][k]);
         for (int i = k + 1; i < N; ++i) {
-            A[i][k] = cdiv(A[i][k], A[k][k]);
+            A[i][k] = cm(A[i][k], rpiv[k]);
             for (int j = k + 1; j < N; ++j) {
                 const double2 t = cm(A[i][k], A[k][j]);
                 A[i][j].x -= t.x; A[i][j].y -= t.y;
@@ -690,7 +715,7 @@ __device__ int block_solve(double2 (&A)[N][N], const double2 (&b)[N], double2 (&
         for (int i = N - 1; i >= 0; --i) {
             double2 s = y[i];
             for (int j = i + 1; j < N; ++j) { const double2 t = cm(A[i][j], y[j]); s.x -= t.x; s.y -= t.y; }
-            y[i] = cdiv(s, A[i][i]);
+            y[i] = cm(s, rpiv[i]);
         }
         for (int i = 0; i < N; ++i) inv[i][col] = y[i];
     }

@@ -1,7 +1,7 @@
 """The bench's own workload at full size (64 antennas, 300 times x 512 channels, G full
 per time then B diagonal per channel, 3 epochs, 10% of rows flagged), solved by the
-GPU in the launch configuration bench.py times, checked on sampled intervals by the
-FP64 oracle.
+GPU in the launch configurations bench.py times (per sample, and from per-(interval, pair)
+sums), checked on sampled intervals by the FP64 oracle.
 
 The oracle cannot solve 3.1e8 samples in a test, but stationarity holds at any size:
 at the GPU's gains, the oracle's Gauss-Newton step JHJ^-1 JHr (Eq. update) of a
@@ -20,18 +20,23 @@ pytestmark = pytest.mark.gpu
 GAIN_TOL = 1e-4
 
 
-@pytest.fixture(scope="module")
-def solved():
+@pytest.fixture(scope="module", params=[False, True], ids=["per_sample", "from_sums"])
+def solved(request):
+    """The full-size solve as bench.py times it: the per-sample path (the default line) and the
+    solve from per-(interval, pair) sums (bench.py --moments)."""
     import torch
     setup = synth.plain_large_setup(seed=1, n_ant=64, n_time=300, n_chan=512)
     obs = synth.make_observation_device(setup, noise=0.05, noise_seed=1000, device="cuda:0")
     S = qc.Solver(obs["data"], obs["model"], obs["weight"], obs["flag"], setup.ant1, setup.ant2, setup.time_idx,
                   setup.n_ant, setup.n_time)
     terms = [qc.Term.from_spec(s, setup.n_ant, max_iter=20, tol=1e-6) for s in setup.terms]
-    S.solve(terms, n_epochs=3)
+    st = S.solve(terms, n_epochs=3, moments=request.param)
     torch.cuda.synchronize()
+    assert (st.pass_ms > 0) == request.param
     yield setup, obs, terms
     S.close()
+    del obs
+    torch.cuda.empty_cache()
 
 
 def _step_norms(jhj, jhr, params, kind):

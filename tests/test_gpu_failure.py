@@ -81,6 +81,35 @@ def test_solve_returns_enomem_then_the_context_still_solves(lib):
     assert err < GAIN_TOL, err
 
 
+def test_solve_from_sums_returns_enomem_at_every_allocation(lib):
+    """The solve from per-(interval, pair) sums allocates its sums and row table in the solve:
+    a failure at each allocation in turn gives QC_ENOMEM, the context keeps working, and the
+    solve that finally succeeds matches the oracle; closing frees everything."""
+    obs = synth.plain_small(seed=3, noise=0.01)
+    torch.cuda.synchronize()
+    base0 = lib.qc_test_live_allocs()
+    S = qc.Solver.from_obs(obs)
+    n_fail = 0
+    for n in range(1, 64):
+        lib.qc_test_fail_alloc(n)
+        term = qc.Term.from_spec(obs.terms[0], obs.n_ant, max_iter=20, tol=1e-6)
+        try:
+            st = S.solve([term], moments=True)
+        except qc.QCError as e:
+            assert e.code == qc.QC_ENOMEM, e
+            n_fail += 1
+            continue
+        lib.qc_test_fail_alloc(0)
+        break
+    else:
+        pytest.fail("the solve never succeeded")
+    assert n_fail >= 2 and st.pass_ms > 0
+    S.close()
+    assert lib.qc_test_live_allocs() == base0
+    err = rel_err(reference_diag(term.gains.astype(np.complex128)), reference_diag(_oracle_gains(obs)))
+    assert err < GAIN_TOL, err
+
+
 def test_batch_create_returns_enomem_and_leaks_nothing(lib):
     shapes = [(100 + i, 7 + i, 2, 8, 0.1) for i in range(4)]
     b = synth.make_batch(shapes)

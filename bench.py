@@ -1093,7 +1093,7 @@ def run_warmstart(args):
 
     arms = {}
     # the sample-based batched solve, and the same from per-baseline sums (qc_batch_solve_moments;
-    # its network arms take the start that fits better, chosen by a chi^2 pass before the solve)
+    # its network arms take the fallback rule from the sums)
     for name, solver, start, mom in (("cold", S, "unit", False), ("prev", S, "prev", False), ("mlp", S, "mlp", False),
                                      ("mlp_fp16", S16, "mlp", False), ("prev_moments", S, "prev", True),
                                      ("mlp_moments", S, "mlp", True), ("mlp_fp16_moments", S16, "mlp", True)):
@@ -1103,15 +1103,11 @@ def run_warmstart(args):
                 solver.solve(unit.clone(), max_iter=20, tol=tol, stream=stream, moments=mom)
 
             def run():
-                if start == "mlp" and not mom:
-                    return ws.warm_solve(solver, net, gp, max_iter=40, tol=tol, stream=stream)
-                n_fb = 0
                 if start == "mlp":
-                    g0, n_fb = ws.initial_gains(solver, net, prev_gains=gp, check_chi2=True, stream=stream)
-                else:
-                    g0 = unit.clone() if start == "unit" else gp.clone()
+                    return ws.warm_solve(solver, net, gp, max_iter=40, tol=tol, stream=stream, moments=mom)
+                g0 = unit.clone() if start == "unit" else gp.clone()
                 g, _, it, st = solver.solve(g0, max_iter=40, tol=tol, stream=stream, moments=mom)
-                return g, it, st, n_fb
+                return g, it, st, 0
 
             (g, it, st, n_fb), ms = timed(run)
             err = _per_problem_err(g.cpu().numpy(), ref_h, offs)

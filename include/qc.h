@@ -529,12 +529,14 @@ int qc_batch_solve(qc_batch *b, void *gains, int8_t *gain_flags, int32_t *iters,
  * problem is one solution interval of one diagonal term, so the samples of a
  * baseline enter JHJ and JHr (Eq. jhj_entry_simplified, Eq. jhr_entry_simplified)
  * only through S_c = sum w_c |m_c|^2 and T_c = sum w_c conj(m_c) d_c per
- * correlation.  One pass over the samples forms them (float32 sums in shared
- * memory); the iterations then form the normal equations from them in FP64,
- * with the update and convergence test of qc_batch_solve.  Arguments and
+ * correlation, and chi^2 (Eq. min) through them and U = sum_c w_c |d_c|^2.  One
+ * pass over the samples forms them (float32 sums in shared memory); the
+ * iterations then form the normal equations from them, with the update and
+ * convergence test of qc_batch_solve.  With a fallback start, chi^2 at the
+ * starting and at the fallback gains both come from the sums (fallback_chi2 must
+ * be given but is not read) and the rule of qc_batch_opts applies.  Arguments and
  * outputs as qc_batch_solve; stats.bytes counts the one data pass.
- * QC_EUNSUPPORTED for batches with more than 64 antennas in a problem or with
- * a fallback start.
+ * QC_EUNSUPPORTED for batches with more than 64 antennas in a problem.
  */
 int qc_batch_solve_moments(qc_batch *b, void *gains, int8_t *gain_flags, int32_t *iters, int32_t mem,
                            const qc_batch_opts *o, qc_batch_stats *stats);

@@ -756,8 +756,8 @@ __global__ void unflag_count_kernel(const uint8_t *flag, const BProb *probs, con
 //   antenna q through the conjugate baseline: S1 <-> S2, T -> conj(T) with T1 <-> T2, p <-> q.
 // The update and the convergence test are those of batch_kernel.
 
-constexpr int MOM_MAX_ANT = 64;   // baselines x 12 floats must fit in shared memory
-constexpr int MOM_W = 12;         // S[4], then T[4] as (re, im)
+constexpr int MOM_MAX_ANT = 64;   // baselines x 13 floats must fit in shared memory
+constexpr int MOM_W = 13;         // S[4], T[4] as (re, im), U = sum_c w_c |d_c|^2
 
 __host__ __device__ constexpr int mom_bl(int p, int q, int n) { return p * (2 * n - p - 1) / 2 + (q - p - 1); }
 
@@ -862,13 +862,14 @@ __global__ void __launch_bounds__(256) batch_moments_kernel(const BatchArgs a)
                 const float2 t = cscale(cmulc(Dv[c], Mv[c]), wv[c]);      // w conj(m) d
                 v[4 + 2 * c] = t.x;
                 v[5 + 2 * c] = t.y;
+                v[12] = fmaf(wv[c], cnorm2(Dv[c]), v[12]);                 // w |d|^2 (chi^2 from the sums)
             }
         }
         const int key = x.key;
         const int k0 = __shfl_sync(0xffffffffu, key, 0);
         if (__all_sync(0xffffffffu, key == k0)) {
             if (k0 >= 0) {
-                // 16 slots (12 sums + 4 zeros) over 32 lanes: four halving exchanges, then a
+                // 16 slots (13 sums + 3 zeros) over 32 lanes: four halving exchanges, then a
                 // butterfly; lane l holds the total of slot l >> 1
                 int idx = 0;
 #pragma unroll
@@ -920,6 +921,57 @@ __global__ void __launch_bounds__(256) batch_moments_kernel(const BatchArgs a)
         add(x1);
     }
     __syncthreads();
+    // a fallback start: chi^2 at the starting and at the fallback gains from the sums (per
+    // baseline U - 2 Re sum_c conj(g_pk) g_qj T_c + sum_c |g_pk|^2 |g_qj|^2 S_c, c = 2k + j, in
+    // FP64 from the FP32 sums); a start that fits worse by more than a relative 1e-5, or whose
+    // chi^2 is not finite, is replaced by the fallback gains
+    if (a.fb_gains) {
+        double c0 = 0, c1 = 0;
+        for (int idx = tid; idx < na * na; idx += blockDim.x) {
+            const int p = idx / na, q = idx - p * na;
+            if (p >= q) continue;
+            const float *m = mom + (size_t)mom_bl(p, q, na) * MOM_W;
+            const float2 *s0 = a.gains + (size_t)P.gain_off * 2, *s1 = a.fb_gains + (size_t)P.gain_off * 2;
+            double t0 = m[12], t1 = m[12];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int kk = c >> 1, jj = c & 1;
+                const double S = m[c], Tr = m[4 + 2 * c], Ti = m[5 + 2 * c];
+                const float2 gp0 = s0[2 * p + kk], gq0 = s0[2 * q + jj], gp1 = s1[2 * p + kk], gq1 = s1[2 * q + jj];
+                // conj(g_pk) g_qj
+                const double a0r = (double)gp0.x * gq0.x + (double)gp0.y * gq0.y;
+                const double a0i = (double)gp0.x * gq0.y - (double)gp0.y * gq0.x;
+                const double a1r = (double)gp1.x * gq1.x + (double)gp1.y * gq1.y;
+                const double a1i = (double)gp1.x * gq1.y - (double)gp1.y * gq1.x;
+                t0 += S * (a0r * a0r + a0i * a0i) - 2.0 * (a0r * Tr - a0i * Ti);
+                t1 += S * (a1r * a1r + a1i * a1i) - 2.0 * (a1r * Tr - a1i * Ti);
+            }
+            c0 += t0;
+            c1 += t1;
+        }
+        for (int d = 16; d > 0; d >>= 1) {
+            c0 += __shfl_down_sync(0xffffffffu, c0, d);
+            c1 += __shfl_down_sync(0xffffffffu, c1, d);
+        }
+        if (lane == 0) { red[0][warp] = c0; red[1][warp] = c1; }
+        __syncthreads();
+        if (tid == 0) {
+            double t0 = 0, t1 = 0;
+            for (int i = 0; i < n_warps; ++i) { t0 += red[0][i]; t1 += red[1][i]; }
+            s_done = !(t0 <= t1 * (1.0 + 1e-5)) ? 1 : 0;
+            if (s_done) atomicAdd(a.n_fallback, 1ull);
+        }
+        __syncthreads();
+        if (s_done) {
+            for (int i = tid; i < na; i += blockDim.x) {
+                const float2 f0 = a.fb_gains[(size_t)(P.gain_off + i) * 2];
+                const float2 f1 = a.fb_gains[(size_t)(P.gain_off + i) * 2 + 1];
+                g64[2 * i] = make_double2(f0.x, f0.y);
+                g64[2 * i + 1] = make_double2(f1.x, f1.y);
+            }
+        }
+        __syncthreads();
+    }
     int k;
     for (k = 1; k <= a.max_iter; ++k) {
         // the normal equations of each antenna from the sums of its baselines (no atomics: one
@@ -1573,7 +1625,7 @@ extern "C" int qc_batch_solve_moments(qc_batch *b, void *gains, int8_t *gain_fla
     if (o->max_iter < 1) return b->fail(QC_EINVAL, "max_iter must be >= 1");
     if (!(o->tol >= 0)) return b->fail(QC_EINVAL, "tol must be >= 0");
     if (o->damping_mode != QC_DAMP_CONST && o->damping_mode != QC_DAMP_ALTERNATE) return b->fail(QC_EINVAL, "damping_mode");
-    if (o->fallback_gains || o->fallback_chi2) return b->fail(QC_EUNSUPPORTED, "no fallback start in the moments solve");
+    if (!o->fallback_gains != !o->fallback_chi2) return b->fail(QC_EINVAL, "fallback_gains and fallback_chi2: both or neither");
     if (b->max_ant > MOM_MAX_ANT) return b->fail(QC_EUNSUPPORTED, "the moments solve takes at most 64 antennas");
     cudaStream_t st = o->stream ? (cudaStream_t)o->stream : b->own_stream;
     const size_t gbytes = (size_t)b->total_ant * 2 * sizeof(float2);
@@ -1591,12 +1643,16 @@ extern "C" int qc_batch_solve_moments(qc_batch *b, void *gains, int8_t *gain_fla
     a.damping_mode = o->damping_mode;
     a.damping = o->damping;
     a.tol = o->tol;
+    a.fb_gains = (const float2 *)o->fallback_gains;
+    a.fb_chi2 = o->fallback_chi2;
+    a.n_fallback = b->counters + 2 + b->n_prob;
     const size_t smem = mom_smem_bytes(std::max(2, b->max_ant));
     const void *fn = b->m16 ? (const void *)batch_moments_kernel<true> : (const void *)batch_moments_kernel<false>;
     BCK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     BCK(cudaEventRecord(b->ev0, st));
     if (mem == QC_MEM_HOST) BCK(cudaMemcpyAsync(dg, gains, gbytes, cudaMemcpyHostToDevice, st));
     BCK(cudaMemsetAsync(b->counters, 0, 2 * sizeof(unsigned long long), st));
+    BCK(cudaMemsetAsync(b->counters + 2 + b->n_prob, 0, sizeof(unsigned long long), st));
     if (b->m16) batch_moments_kernel<true><<<b->n_prob, 256, smem, st>>>(a);
     else batch_moments_kernel<false><<<b->n_prob, 256, smem, st>>>(a);
     BCK(cudaGetLastError());
@@ -1605,8 +1661,9 @@ extern "C" int qc_batch_solve_moments(qc_batch *b, void *gains, int8_t *gain_fla
         if (gain_flags) BCK(cudaMemcpyAsync(gain_flags, dflags, (size_t)b->total_ant, cudaMemcpyDeviceToHost, st));
         if (iters) BCK(cudaMemcpyAsync(iters, diters, sizeof(int) * b->n_prob, cudaMemcpyDeviceToHost, st));
     }
-    unsigned long long hc[2];
+    unsigned long long hc[2], hfb = 0;
     BCK(cudaMemcpyAsync(hc, b->counters, sizeof hc, cudaMemcpyDeviceToHost, st));
+    BCK(cudaMemcpyAsync(&hfb, b->counters + 2 + b->n_prob, sizeof hfb, cudaMemcpyDeviceToHost, st));
     BCK(cudaEventRecord(b->ev1, st));
     BCK(cudaStreamSynchronize(st));
     float ms = 0;
@@ -1621,6 +1678,7 @@ extern "C" int qc_batch_solve_moments(qc_batch *b, void *gains, int8_t *gain_fla
         S.ctas_per_sm = 0;
         S.schedule = QC_SCHED_LPT;
         S.grid = b->n_prob;
+        S.n_fallback = (int32_t)hfb;
         double tot_vis = 0;
         for (const BProb &Pp : b->hprobs) tot_vis += (double)Pp.n_rows * Pp.n_chan;
         S.mean_iters = tot_vis > 0 ? (double)hc[0] / tot_vis : 0;

@@ -445,7 +445,8 @@ class BatchSolver:
         (device gains [sum n_ant][2] complex64, device chi^2 [n_prob] float64) -- a problem whose
         starting gains fit worse than its fallback chi^2 restarts from the fallback gains.
         moments: one pass forms per-baseline sums and the iterations use them
-        (qc_batch_solve_moments; at most 64 antennas, no fallback)."""
+        (qc_batch_solve_moments; at most 64 antennas; with a fallback, chi^2 at both starts comes
+        from the sums and the fallback chi^2 array is not read)."""
         if gains is None:
             gains = self.unit_gains()
         dev = _is_dev(gains)

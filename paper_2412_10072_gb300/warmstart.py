@@ -162,7 +162,8 @@ def warm_solve(bsolver: "qc.BatchSolver", net: MLP, prev_gains, max_iter: int = 
     (and chi^2 at the previous-interval gains), the network, then the solve from the predicted
     gains; a problem whose prediction is not finite falls back at once, and one whose chi^2 at
     the prediction exceeds that at the previous gains restarts from them inside the solve's first
-    pass.  Returns (gains, iters, BatchStats, n_fallback)."""
+    pass (with moments=True: after the pass forming the sums, both chi^2 from the sums).  Returns
+    (gains, iters, BatchStats, n_fallback)."""
     x, chi_prev = features(bsolver, prev_gains, stream, want_prev_chi2=True)
     y = net.forward(x, stream=stream)
     import torch

@@ -224,3 +224,29 @@ def test_committed_network_against_the_previous_interval_start(ws):
           f"{prev:.2f}, network {mlp:.2f} ({n_fb} fallbacks)")
     assert prev < cold
     assert mlp <= prev + 0.25
+
+
+def test_fallback_from_sums_restarts_worse_starts(ws):
+    """The batched solve from per-baseline sums takes the same fallback rule: chi^2 at the start
+    and at the fallback gains, both from the sums; worse starts restart from the fallback (the
+    result equals the solve from the fallback gains), the others keep their start."""
+    shapes = synth.batch_shapes(6, seed_base=950, ant=(5, 9), times=(1, 3), chans=(4, 24))
+    b = synth.make_batch(shapes, device="cuda")
+    S = qc.BatchSolver(b.data, b.model, b.weight, b.flag, b.ant1, b.ant2, b.row_offset, b.vis_offset, b.n_chan,
+                       b.n_ant)
+    offs = np.concatenate([[0], np.cumsum(b.n_ant)])
+    truth = torch.from_numpy(np.concatenate(b.truths).astype(np.complex64)).cuda()
+    fb = truth * torch.exp(1j * 0.05 * torch.ones_like(truth.real)).to(torch.complex64)
+    _, chi_fb = ws.features(S, fb, want_prev_chi2=True)
+    g0 = fb.clone()
+    g0[offs[1]:offs[2]] *= 3.0                                 # problems 1 and 3 start badly
+    g0[offs[3]:offs[4]] = 1.0
+    g, _, it, st = S.solve(g0.clone(), fallback=(fb, chi_fb), tol=1e-7, max_iter=30, moments=True)
+    assert st.n_fallback == 2
+    ref, _, it_ref, _ = S.solve(fb.clone(), tol=1e-7, max_iter=30, moments=True)
+    keep, _, it_keep, _ = S.solve(g0.clone(), tol=1e-7, max_iter=30, moments=True)
+    for i in range(b.n_prob):
+        want, want_it = (ref, it_ref) if i in (1, 3) else (keep, it_keep)
+        assert torch.allclose(g[offs[i]:offs[i + 1]], want[offs[i]:offs[i + 1]], atol=1e-6), i
+        assert int(it[i]) == int(want_it[i]), i
+    S.close()

@@ -748,7 +748,8 @@ def run_kde(args):
                 "frac": (achieved / hbm) if achieved else None, "traffic": None, "bytes_per_vis_iteration": bpv,
                 "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured"
                 else "fallback 6.8 TB/s",
-                "kernel": "dd_acc_kernel (residual over both directions, blocks of the solved term)",
+                "kernel": "dd_stream_kernel (row tiles through a cp.async ring: residual over both directions, "
+                          "blocks of dE per direction, K's sums per parameter interval)",
                 "algorithmic_bytes_per_launch": bpv * vis_iters / max(1, acc_launches),
                 "launch_ms_mean": acc_ms / max(1, acc_launches), "acc_share_of_step": acc_ms / ms if ms else None}
     cpu = None

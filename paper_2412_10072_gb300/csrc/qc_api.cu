@@ -1048,7 +1048,18 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
     const int ts = t.type == 1 ? TS_FULL : TS_DIAG;
     const int lk = kind_of_range(terms, 0, n);
     const int rk = kind_of_range(terms, n + 1, n_terms);
-    const int order = pick_order(t, o);
+    // chains with directions: chains of one or two terms with at most DDS_MAX_DIR directions
+    // take the streaming direction-dependent kernel (row tiles, qc_dd_stream.cuh), longer
+    // chains the general one (qc_dd.cu)
+    const bool ddp = n_dir > 1;
+    DDSLaunch DS;
+    if (ddp && n_terms <= 2 && n_dir <= DDS_MAX_DIR && (o->kernel == 0 || o->kernel == 3) &&
+        (long long)n_ant * n_dir < 32768) {
+        const int ok_ = n_terms == 2 ? (terms[1 - n].type == 1 ? KIND_FULL : KIND_DIAG) : KIND_NONE;
+        DS = dds_launcher(t.type == 1 ? KIND_FULL : KIND_DIAG, ok_, n == 1, delay[n]);
+    }
+    const bool dds = DS.fn != nullptr;
+    const int order = dds ? 0 : pick_order(t, o);
     // the prefetching and streaming kernels are compiled for at most 256 threads per CTA
     // (the streaming kernel for two such CTAs per SM)
     const bool bt_ok = o->block_threads >= 32 && o->block_threads % 32 == 0;
@@ -1068,8 +1079,6 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
     int per_sm = o->ctas_per_sm > 0 ? o->ctas_per_sm : 0;
     const bool simple = n_terms <= 2;
     AccLaunch L = acc_launcher(ts, simple, lk, rk, m16);
-    // chains with directions: the direction-dependent accumulate kernel (qc_dd.cu)
-    const bool ddp = n_dir > 1;
     const int nat = term_nat(t);
     if (!L.fn && !ddp) return fail(QC_EUNSUPPORTED, "no accumulate kernel for this chain");
     // the term from per-(interval, pair) sums (qc_moments.cu): one pass over the data, then
@@ -1103,9 +1112,12 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
     DelayLaunch DL;
     if (delay[n] && streaming) DL = delay_launcher(lk, rk, m16);
     const bool ded = DL.fn != nullptr;
+    // a solved delay term with sums per parameter interval (the streaming kernels), else
+    // the per-channel bins
+    const bool psums = ded || (dds && delay[n]);
     DevTerm tnu = chain.t[n];
     const int nbu = delay[n] ? t.n_tint * (int)B.hfr.size() : nb;
-    if (ded) {
+    if (psums) {
         tnu.n_fint = (int)B.hfr.size();
         tnu.f_map = (const int *)B.dfmap.ptr;
         aa.tn = tnu;
@@ -1114,8 +1126,8 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
         CK(cudaMemsetAsync(B.acc.ptr, 0, nbytes<double>((size_t)nbu * n_ant * KG_SUMS), st));
         aa.acc = (double *)B.acc.ptr;
     }
-    const void *stream_fn = ded ? DL.fn : L.stream_fn;
-    const int stream_smem_per_warp = ded ? DL.smem_per_warp : L.stream_smem_per_warp;
+    const void *stream_fn = dds ? DS.fn : (ded ? DL.fn : L.stream_fn);
+    const int stream_smem_per_warp = dds ? dds_smem_per_warp(n_dir) : (ded ? DL.smem_per_warp : L.stream_smem_per_warp);
     bool pipelined = !mom && !ddp && !streaming && L.pipe_fn != nullptr && (o->kernel == 1 || (o->kernel == 0 && order == 1));
     const bool has_o = n_terms == 2;
     if (pipelined) {
@@ -1218,7 +1230,7 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
     memset(&sa, 0, sizeof sa);
     int stream_smem = 0;
     const long n_rt = order == 0 ? (long)n_row : n_strip_rows;
-    if (streaming || ws) {
+    if (streaming || ws || dds) {
         // step-major row table in the tile order, and the channel maps of both terms (padded
         // to whole 32-channel chunks: the warp-specialised kernel copies them 32 at a time)
         const int n_chunks = (n_chan + 31) / 32;
@@ -1228,7 +1240,7 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
         if ((rc_ = ensure(B.fmap2, nbytes<int2>(32 * n_chunks)))) return rc_;
         std::vector<int2> fm(32 * n_chunks, make_int2(0, 0));
         for (int ch = 0; ch < n_chan; ++ch)
-            fm[ch] = make_int2(ded ? B.hufmap[ch] : t.f_map[ch], has_o ? terms[1 - n].f_map[ch] : 0);
+            fm[ch] = make_int2(psums ? B.hufmap[ch] : t.f_map[ch], has_o ? terms[1 - n].f_map[ch] : 0);
         CK(cudaMemcpyAsync(B.fmap2.ptr, fm.data(), nbytes<int2>(32 * n_chunks), cudaMemcpyHostToDevice, st));
         if (n_rt) {
             row_table_kernel<<<(int)((n_rt + 255) / 256), 256, 0, st>>>(
@@ -1294,7 +1306,7 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
         per_sm = per_sm > 0 ? std::min(per_sm, occ) : occ;
         ws_grid = sm_count * per_sm;
     }
-    if (streaming) {
+    if (streaming || dds) {
         int rc_;
         block = block_stream;
         sa.vis = d_vis;
@@ -1309,7 +1321,7 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
         sa.order = order;
         sa.n_chunks = (n_chan + 31) / 32;
         sa.n_units = order == 0 ? n_row : n_strips * sa.n_chunks;
-        sa.tn = ded ? tnu : chain.t[n];
+        sa.tn = psums ? tnu : chain.t[n];
         sa.to = has_o ? chain.t[1 - n] : chain.t[n];
         sa.fmap2 = (const int2 *)B.fmap2.ptr;
         sa.acc = (double *)B.acc.ptr;
@@ -1328,7 +1340,15 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
     int grid;
     DDArgs dda;
     memset(&dda, 0, sizeof dda);
-    if (ddp) {
+    if (dds) {
+        if (per_sm == 0) {
+            int occ = 0;
+            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, stream_fn, block, stream_smem);
+            per_sm = (e == cudaSuccess && occ > 0) ? occ : 1;
+        }
+        const long warps_needed = std::max(1L, (long)n_row);
+        grid = (int)std::max(1L, std::min((long)sm_count * per_sm, (warps_needed * 32 + block - 1) / block));
+    } else if (ddp) {
         dda.D = data_desc();
         dda.wf = d_wf;
         dda.row_live = d_row_live;
@@ -1509,7 +1529,16 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
                 CK(cudaGetLastError());
             }
             CK(cudaEventRecordWithFlags(events[2 + 2 * (k - 1)], st, rec_flags));
-            if (ddp) {
+            if (dds) {
+                DDStreamArgs x;
+                x.s = sa;
+                x.s.n_active = cnt + (k - 1);
+                x.n_dir = n_dir;
+                x.nd_n = cur_nd[n];
+                x.nd_o = n_terms == 2 ? cur_nd[1 - n] : 1;
+                x.omega = delay[n] ? (const float *)B.domega.ptr : nullptr;
+                CK(DS.launch(dim3(grid, cur_nd[n] > 1 ? n_dir : 1), block, stream_smem, st, x));
+            } else if (ddp) {
                 dda.n_active = cnt + (k - 1);
                 CK(dd_launch_acc(dda, ts, grid, st));
             } else if (mom) {
@@ -1563,8 +1592,8 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
             }
             CK(cudaEventRecordWithFlags(events[2 + 2 * (k - 1) + 1], st, rec_flags));
             if (t.reduce) {
-                const size_t KG = ded ? KG_SUMS : (t.type == 1 ? KG_FULL : KG_DIAG);
-                if (o->allreduce((double *)B.acc.ptr, (int64_t)(ded ? nbu : nb) * nat * KG, st, o->allreduce_user))
+                const size_t KG = psums ? KG_SUMS : (t.type == 1 ? KG_FULL : KG_DIAG);
+                if (o->allreduce((double *)B.acc.ptr, (int64_t)(psums ? nbu : nb) * nat * KG, st, o->allreduce_user))
                     return fail(QC_ECUDA, "allreduce callback failed");
             }
             ua.k = k;
@@ -1577,7 +1606,7 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
                 dua.alpha = ua.alpha;
                 dua.n_active_prev = ua.n_active_prev;
                 dua.n_active_next = ua.n_active_next;
-                if (ded) delay_update_kernel<true><<<dua.d.n_tint * dua.d.n_fint, upd_block, 0, st>>>(dua);
+                if (psums) delay_update_kernel<true><<<dua.d.n_tint * dua.d.n_fint, upd_block, 0, st>>>(dua);
                 else delay_update_kernel<false><<<dua.d.n_tint * dua.d.n_fint, upd_block, 0, st>>>(dua);
             } else {
                 update_kernel<<<nb, upd_block, 0, st>>>(ua);

@@ -1,0 +1,4 @@
+// qc_dd_stream_diag.cu -- streaming kernels of chains with directions: diagonal solved terms.
+#include "qc_dd_stream_inst.cuh"
+
+DDSLaunch dds_launcher_diag(int ok, bool oleft) { return qc_dds::pick<qc::KIND_DIAG, false>(ok, oleft); }

@@ -9,6 +9,7 @@
 #include "qc_stream.cuh"
 #include "qc_delay.cuh"
 #include "qc_stream_delay.cuh"
+#include "qc_dd_stream.cuh"
 #include "qc_ws.cuh"
 #include "qc_robust.cuh"
 #include "qc_moments.cuh"
@@ -127,6 +128,21 @@ struct DelayLaunch {
     int smem_per_warp = 0;
 };
 DelayLaunch delay_launcher(int lk, int rk, bool m16);
+// The streaming kernel of chains of one or two terms with directions (qc_dd_stream_*.cu):
+// gk the solved term's kind, ok the other term's (KIND_NONE: none), oleft the other term is
+// to the left of the solved one, dsums a solved delay term with parameter sums.
+struct DDSLaunch {
+    const void *fn = nullptr;
+    cudaError_t (*launch)(dim3 grid, int block, int smem_bytes, cudaStream_t st, const qc::DDStreamArgs &a) = nullptr;
+};
+DDSLaunch dds_launcher_diag(int ok, bool oleft);
+DDSLaunch dds_launcher_full(int ok, bool oleft);
+DDSLaunch dds_launcher_delay(int ok, bool oleft);
+inline DDSLaunch dds_launcher(int gk, int ok, bool oleft, bool dsums)
+{
+    if (dsums) return gk == qc::KIND_DIAG ? dds_launcher_delay(ok, oleft) : DDSLaunch();
+    return gk == qc::KIND_FULL ? dds_launcher_full(ok, oleft) : dds_launcher_diag(ok, oleft);
+}
 AccLaunch acc_launcher_diag(bool simple, int lk, int rk, bool m16);
 AccLaunch acc_launcher_full(bool simple, int lk, int rk, bool m16);
 inline AccLaunch acc_launcher(int ts, bool simple, int lk, int rk, bool m16)

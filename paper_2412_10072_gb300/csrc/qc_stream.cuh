@@ -288,6 +288,41 @@ template <bool M16> struct StreamCursor {
             unit_start(a, lane);
         }
     }
+
+    // row tiles of a model with a direction axis: d, w and the sample's n_mw model words
+    // (contiguous, [dir][2] float4) into a stage laid out [d0][d1][w][m_0] .. [m_{n_mw-1}]
+    __device__ __forceinline__ void issue_dd(const StreamArgs &a, int lane, float4 *ring, int4 *meta, int stage,
+                                             int n_mw)
+    {
+        int4 e = make_int4(STREAM_END, 0, -1, 0);
+        int c0 = 0;
+        bool live = false;
+        if (iu < a.n_units) {
+            e = irt;
+            c0 = ii * 32;
+            live = ii >= 31 ? ((imask >> 31) & 1) : ((imask >> ii) & 1);
+            if (!live) e.z = -1;
+        }
+        const int c = c0 + lane;
+        const bool rd = live && c < a.n_chan;
+        const size_t s = rd ? (size_t)e.x * a.n_chan + c : 0;
+        const uint32_t nb = rd ? 16u : 0u;
+        float4 *slot = ring + (size_t)stage * (3 + n_mw) * 32 + lane;
+        cp_async16(slot, a.vis + 2 * s, nb);
+        cp_async16(slot + 32, a.vis + 2 * s + 1, nb);
+        cp_async16(slot + 64, a.wf + s, nb);
+        const float4 *ms = a.model + s * n_mw;
+        for (int i = 0; i < n_mw; ++i) cp_async16(slot + 96 + 32 * i, ms + i, nb);
+        cp_async_commit();
+        if (lane == 0) {
+            meta[2 * stage] = e;
+            meta[2 * stage + 1] = make_int4(c0, 0, 0, 0);
+        }
+        if (iu < a.n_units && ++ii == ilen) {
+            next_unit(a, lane);
+            unit_start(a, lane);
+        }
+    }
 };
 
 template <int TS, int LK, int RK, bool M16, int DEPTH>

@@ -1056,7 +1056,7 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
     if (ddp && n_terms <= 2 && n_dir <= DDS_MAX_DIR && (o->kernel == 0 || o->kernel == 3) &&
         (long long)n_ant * n_dir < 32768) {
         const int ok_ = n_terms == 2 ? (terms[1 - n].type == 1 ? KIND_FULL : KIND_DIAG) : KIND_NONE;
-        DS = dds_launcher(t.type == 1 ? KIND_FULL : KIND_DIAG, ok_, n == 1, delay[n]);
+        DS = dds_launcher(t.type == 1 ? KIND_FULL : KIND_DIAG, ok_, n == 1, delay[n], cur_nd[n] > 1);
     }
     const bool dds = DS.fn != nullptr;
     const int order = dds ? 0 : pick_order(t, o);
@@ -1537,7 +1537,8 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
                 x.nd_n = cur_nd[n];
                 x.nd_o = n_terms == 2 ? cur_nd[1 - n] : 1;
                 x.omega = delay[n] ? (const float *)B.domega.ptr : nullptr;
-                CK(DS.launch(dim3(grid, cur_nd[n] > 1 ? n_dir : 1), block, stream_smem, st, x));
+                const int gy = DS.dirs_per_cta > 0 ? (n_dir + DS.dirs_per_cta - 1) / DS.dirs_per_cta : 1;
+                CK(DS.launch(dim3(grid, gy), block, stream_smem, st, x));
             } else if (ddp) {
                 dda.n_active = cnt + (k - 1);
                 CK(dd_launch_acc(dda, ts, grid, st));

@@ -45,6 +45,30 @@ __device__ __forceinline__ double2 delay_gain(double phi, double tau, double w)
     return make_double2(c, s);
 }
 
+// Gain of one correlation, exp(i (phi + tau w)), in float: the phase is formed and reduced to
+// [-pi, pi] in FP64, split into a float head and tail, and the head's sine and cosine
+// (sincosf) corrected to first order by the tail, which keeps the float table within about
+// one float rounding of the exact gain at FP32 cost (FP64 sincos is slow on this part).
+__device__ __forceinline__ float2 delay_gain_f32(double phi, double tau, double w)
+{
+    const double th = phi + tau * w;
+    const double r = th - DELAY_TWO_PI * rint(th * (1.0 / DELAY_TWO_PI));
+    const float hi = (float)r, lo = (float)(r - (double)hi);
+    float s, c;
+    sincosf(hi, &s, &c);
+    return make_float2(fmaf(-s, lo, c), fmaf(c, lo, s));
+}
+
+// |exp(i a) - exp(i b)|^2 = 4 sin^2((a - b) / 2), from the phase change d = a - b (formed in
+// FP64 from the parameter changes; the sine of the reduced half angle in float)
+__device__ __forceinline__ double delay_change2(double d)
+{
+    const double h = 0.5 * d;
+    const double r = h - 0.5 * DELAY_TWO_PI * rint(h * (2.0 / DELAY_TWO_PI));
+    const double sn = (double)sinf((float)r);
+    return 4.0 * sn * sn;
+}
+
 // channel table from the FP64 parameters, one entry per (time interval, antenna, channel)
 static __global__ void delay_tab_kernel(const DelayArgs a)
 {
@@ -55,8 +79,8 @@ static __global__ void delay_tab_kernel(const DelayArgs a)
         const int ant = (int)(ta % a.n_ant), tint = (int)(ta / a.n_ant);
         const double *u = a.params + (((size_t)tint * a.n_fint + a.fmap[c]) * a.n_ant + ant) * 4;
         const double w = DELAY_TWO_PI * a.nu[c];
-        const double2 gx = delay_gain(u[0], u[1], w), gy = delay_gain(u[2], u[3], w);
-        a.tab[i] = make_float4((float)gx.x, (float)gx.y, (float)gy.x, (float)gy.y);
+        const float2 gx = delay_gain_f32(u[0], u[1], w), gy = delay_gain_f32(u[2], u[3], w);
+        a.tab[i] = make_float4(gx.x, gx.y, gy.x, gy.y);
     }
 }
 
@@ -175,15 +199,15 @@ static __global__ void __launch_bounds__(128) delay_update_kernel(const DelayUpd
             for (int e = 0; e < 4; ++e) P[e] += u.alpha * x[e].x;
         if (u.gain_flags) u.gain_flags[(size_t)bin * d.n_ant + ant] = (int8_t)singular;
         // re-evaluate the channel table; relative change of the gains over the interval's channels
+        // (the gains have unit modulus: |g_new - g_old|^2 = 4 sin^2 of half the phase change,
+        // |g_new|^2 = 1 per correlation)
+        const double d0 = P[0] - u0, d1 = P[1] - u1, d2 = P[2] - u2, d3 = P[3] - u3;
         for (int c = fr.x; c <= fr.y; ++c) {
             const double w = DELAY_TWO_PI * d.nu[c];
-            const double2 ox = delay_gain(u0, u1, w), oy = delay_gain(u2, u3, w);
-            const double2 nx = delay_gain(P[0], P[1], w), ny = delay_gain(P[2], P[3], w);
-            d.tab[((size_t)tint * d.n_ant + ant) * d.n_chan + c] =
-                make_float4((float)nx.x, (float)nx.y, (float)ny.x, (float)ny.y);
-            num += (nx.x - ox.x) * (nx.x - ox.x) + (nx.y - ox.y) * (nx.y - ox.y) + (ny.x - oy.x) * (ny.x - oy.x) +
-                   (ny.y - oy.y) * (ny.y - oy.y);
-            den += nx.x * nx.x + nx.y * nx.y + ny.x * ny.x + ny.y * ny.y;
+            const float2 nx = delay_gain_f32(P[0], P[1], w), ny = delay_gain_f32(P[2], P[3], w);
+            d.tab[((size_t)tint * d.n_ant + ant) * d.n_chan + c] = make_float4(nx.x, nx.y, ny.x, ny.y);
+            num += delay_change2(d0 + d1 * w) + delay_change2(d2 + d3 * w);
+            den += 2.0;
         }
     }
     __shared__ double s_num[4], s_den[4];

@@ -130,18 +130,24 @@ struct DelayLaunch {
 DelayLaunch delay_launcher(int lk, int rk, bool m16);
 // The streaming kernel of chains of one or two terms with directions (qc_dd_stream_*.cu):
 // gk the solved term's kind, ok the other term's (KIND_NONE: none), oleft the other term is
-// to the left of the solved one, dsums a solved delay term with parameter sums.
+// to the left of the solved one, dsums a solved delay term with parameter sums, dd the solved
+// term is direction-dependent.  dirs_per_cta: directions of a direction-dependent solved term
+// whose blocks one CTA forms (grid dimension y covers the rest), 0 otherwise.
 struct DDSLaunch {
     const void *fn = nullptr;
     cudaError_t (*launch)(dim3 grid, int block, int smem_bytes, cudaStream_t st, const qc::DDStreamArgs &a) = nullptr;
+    int dirs_per_cta = 0;
 };
 DDSLaunch dds_launcher_diag(int ok, bool oleft);
+DDSLaunch dds_launcher_diag_dd(int ok, bool oleft);
 DDSLaunch dds_launcher_full(int ok, bool oleft);
+DDSLaunch dds_launcher_full_dd(int ok, bool oleft);
 DDSLaunch dds_launcher_delay(int ok, bool oleft);
-inline DDSLaunch dds_launcher(int gk, int ok, bool oleft, bool dsums)
+inline DDSLaunch dds_launcher(int gk, int ok, bool oleft, bool dsums, bool dd)
 {
-    if (dsums) return gk == qc::KIND_DIAG ? dds_launcher_delay(ok, oleft) : DDSLaunch();
-    return gk == qc::KIND_FULL ? dds_launcher_full(ok, oleft) : dds_launcher_diag(ok, oleft);
+    if (dsums) return (gk == qc::KIND_DIAG && !dd) ? dds_launcher_delay(ok, oleft) : DDSLaunch();
+    if (gk == qc::KIND_FULL) return dd ? dds_launcher_full_dd(ok, oleft) : dds_launcher_full(ok, oleft);
+    return dd ? dds_launcher_diag_dd(ok, oleft) : dds_launcher_diag(ok, oleft);
 }
 AccLaunch acc_launcher_diag(bool simple, int lk, int rk, bool m16);
 AccLaunch acc_launcher_full(bool simple, int lk, int rk, bool m16);

@@ -87,12 +87,16 @@ CHAINS = [
     [("diag", False, 2, 45), ("full", True, 1, 3)],
     [("full", False, 4, 1), ("diag", True, 2, 9)],
     [("diag", True, 1, 5), ("full", True, 2, 2)],
+    [("full", False, 2, 1), ("diag", True, 2, 5), ("diag", False, 1, 45)],   # three terms: general kernel
 ]
 
 
+# n_dir 2 and 3: the streaming kernel (chains of one or two terms, at most 4 directions; a
+# diagonal direction-dependent solved term forms two directions per CTA, so 3 leaves one CTA
+# row with a single direction); 5: the general kernel.  kernel 2 forces the general kernel.
 @pytest.mark.parametrize("chain", CHAINS)
-@pytest.mark.parametrize("n_dir", [2, 3])
-def test_single_step_matches_oracle(chain, n_dir):
+@pytest.mark.parametrize("n_dir,kernel", [(2, 0), (3, 0), (4, 0), (5, 0), (2, 2)])
+def test_single_step_matches_oracle(chain, n_dir, kernel):
     n_ant, n_time, n_chan = 5, 4, 45
     P, rng = _problem(3 + n_dir, n_ant=n_ant, n_time=n_time, n_chan=n_chan, n_dir=n_dir)
     pars = [_params(rng, k, isdd, n_ant, n_dir, nt, nf) for (k, isdd, nt, nf) in chain]
@@ -106,7 +110,7 @@ def test_single_step_matches_oracle(chain, n_dir):
         S = _solver(P)
         gt = [_gterm(k, isdd, tm, fm, p, n_ant, n_dir, i == n)
               for i, ((k, isdd, _, _), (tm, fm), p) in enumerate(zip(chain, maps, pars32))]
-        S.solve(gt, damping_mode=qc.QC_DAMP_CONST, damping=1.0)
+        S.solve(gt, damping_mode=qc.QC_DAMP_CONST, damping=1.0, kernel=kernel)
         S.close()
         want = ot[n].params
         got = _gpu_params(gt[n], n_dir)
@@ -195,7 +199,8 @@ def _gk_delay(par, tm, fm, freq, n_ant, solve, max_iter=1, tol=0.0):
 
 @pytest.mark.parametrize("n", [0, 1])
 @pytest.mark.parametrize("dekind", ["diag", "full"])
-def test_k_de_single_step_matches_oracle(n, dekind):
+@pytest.mark.parametrize("kernel", [0, 2])
+def test_k_de_single_step_matches_oracle(n, dekind, kernel):
     """The KdE chain: K (delay and phase per integration over every channel, direction-independent)
     and dE (direction-dependent, over several channels), two directions; one step of either term."""
     n_ant, n_time, n_chan, n_dir = 5, 4, 40, 2
@@ -208,7 +213,7 @@ def test_k_de_single_step_matches_oracle(n, dekind):
     dd.solve_term(P, ot, n, damping_mode=0)
     S = _solver(P)
     gt = [_gk_delay(kpar, ktm, kfm, freq, n_ant, n == 0), _gterm(dekind, True, dtm, dfm, de, n_ant, n_dir, n == 1)]
-    S.solve(gt, damping_mode=qc.QC_DAMP_CONST, damping=1.0)
+    S.solve(gt, damping_mode=qc.QC_DAMP_CONST, damping=1.0, kernel=kernel)
     S.close()
     if n == 0:
         want, start = ot[0].params[:, :, :, 0], kpar[:, :, :, 0]

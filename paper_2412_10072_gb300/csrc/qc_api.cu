@@ -1607,7 +1607,7 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
                 dua.alpha = ua.alpha;
                 dua.n_active_prev = ua.n_active_prev;
                 dua.n_active_next = ua.n_active_next;
-                if (psums) delay_update_kernel<true><<<dua.d.n_tint * dua.d.n_fint, upd_block, 0, st>>>(dua);
+                if (psums) delay_update_kernel<true><<<dua.d.n_tint * dua.d.n_fint, 128, 0, st>>>(dua);
                 else delay_update_kernel<false><<<dua.d.n_tint * dua.d.n_fint, upd_block, 0, st>>>(dua);
             } else {
                 update_kernel<<<nb, upd_block, 0, st>>>(ua);

@@ -198,6 +198,15 @@ static __global__ void __launch_bounds__(128) delay_update_kernel(const DelayUpd
         if (!singular)
             for (int e = 0; e < 4; ++e) P[e] += u.alpha * x[e].x;
         if (u.gain_flags) u.gain_flags[(size_t)bin * d.n_ant + ant] = (int8_t)singular;
+        if (SUMS) {
+            // the parameter change, kept in the (already read) sums for the channel pass below
+            double *A = u.acc + ((size_t)bin * d.n_ant + ant) * KG_SUMS;
+            A[0] = P[0] - u0;
+            A[1] = P[1] - u1;
+            A[2] = P[2] - u2;
+            A[3] = P[3] - u3;
+            continue;
+        }
         // re-evaluate the channel table; relative change of the gains over the interval's channels
         // (the gains have unit modulus: |g_new - g_old|^2 = 4 sin^2 of half the phase change,
         // |g_new|^2 = 1 per correlation)
@@ -208,6 +217,28 @@ static __global__ void __launch_bounds__(128) delay_update_kernel(const DelayUpd
             d.tab[((size_t)tint * d.n_ant + ant) * d.n_chan + c] = make_float4(nx.x, nx.y, ny.x, ny.y);
             num += delay_change2(d0 + d1 * w) + delay_change2(d2 + d3 * w);
             den += 2.0;
+        }
+    }
+    if (SUMS) {
+        // the channel table and the change of the gains, spread over the block's threads by
+        // (antenna, channel)
+        __syncthreads();
+        const int nch = fr.y - fr.x + 1;
+        const long n = (long)d.n_ant * nch;
+        for (long i = threadIdx.x; i < n; i += blockDim.x) {
+            const int ant = (int)(i / nch), c = fr.x + (int)(i - (long)ant * nch);
+            const double *P = d.params + ((size_t)bin * d.n_ant + ant) * 4;
+            const double *A = u.acc + ((size_t)bin * d.n_ant + ant) * KG_SUMS;
+            const double w = DELAY_TWO_PI * d.nu[c];
+            const float2 nx = delay_gain_f32(P[0], P[1], w), ny = delay_gain_f32(P[2], P[3], w);
+            d.tab[((size_t)tint * d.n_ant + ant) * d.n_chan + c] = make_float4(nx.x, nx.y, ny.x, ny.y);
+            num += delay_change2(A[0] + A[1] * w) + delay_change2(A[2] + A[3] * w);
+            den += 2.0;
+        }
+        __syncthreads();
+        for (int ant = threadIdx.x; ant < d.n_ant; ant += blockDim.x) {
+            double *A = u.acc + ((size_t)bin * d.n_ant + ant) * KG_SUMS;
+            A[0] = A[1] = A[2] = A[3] = 0.0;
         }
     }
     __shared__ double s_num[4], s_den[4];

@@ -53,7 +53,7 @@ extern "C" {
 #define QC_ENOMEM        -2   /* device or host allocation failed                            */
 #define QC_ECUDA         -3   /* a CUDA runtime call or kernel launch failed                 */
 #define QC_ETIMEOUT      -4   /* a bounded device wait gave up (2 s); the context stays usable */
-#define QC_EUNSUPPORTED  -5   /* valid request outside what this build implements           */
+#define QC_EUNSUPPORTED  -5   /* valid request outside what this library implements         */
 
 #define QC_TERM_DIAG   0      /* diagonal complex gain, free parameters g_XX, g_YY           */
 #define QC_TERM_FULL   1      /* full 2x2 complex gain, free parameters all four entries     */
@@ -131,7 +131,11 @@ typedef struct {
  *   memory      : where gains, gain_flags and iters live.
  *   reduce      : 1 = the term's intervals span several processes; the
  *                 partial normal equations are summed with the options'
- *                 allreduce callback before every update.
+ *                 allreduce callback before every update.  The buffer holds
+ *                 sums over samples per (interval, antenna): the JHJ block
+ *                 and the right-hand side, as J^H W r, or as J^H W d when the
+ *                 streaming kernel formed it (the update then takes
+ *                 J^H W r = J^H W d - JHJ g); the callback sums every word.
  *   chan_freq   : QC_TERM_DELAY only (NULL otherwise): HOST float64 [n_chan],
  *                 the frequency of every channel, finite, in a unit of the
  *                 caller's choice; tau is in the inverse unit (GHz and ns keep

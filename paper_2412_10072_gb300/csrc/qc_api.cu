@@ -1421,6 +1421,8 @@ int qc_ctx::solve_term(const qc_term *terms, int n_terms, int n, Chain chain, co
     ua.max_iter = t.max_iter;
     ua.div_stats = nullptr;
     ua.params0 = nullptr;
+    // the streaming kernel sums J^H W d in place of J^H W r (the update subtracts JHJ g)
+    ua.b_form = (streaming && !dds && !delay[n]) ? 1 : 0;
     const size_t pbytes = nbytes<double>((size_t)nb * nat * (t.type == 2 ? 2 : 8));
     if (ua.div) {
         int rc_;

@@ -374,7 +374,11 @@ __device__ __forceinline__ void factors(const AccArgs &a, const SampleIdx &ix, i
 // Contribution of one unflagged sample of baseline (p, q) to the p and q blocks.
 // With Z = R_p M R_q^H:  X = Z G_q^H L_q^H = R_p M C_q^H,  V = L_p G_p X  (Eq. chain_trick),
 // and for the conjugate baseline Y = R_q M^H C_p^H = (L_p G_p Z)^H.
-template <int TS, int LK, int RK, bool KAHAN>
+// BF: the J^H W r slots receive J^H W d instead.  V is linear in the solved gains of
+// either side (V = E g_p, V^H = E' g_q), so J^H W r = J^H W d - JHJ g per block, and the
+// update forms the difference in FP64 (UpdArgs::b_form); the sample then needs neither
+// V nor the residual.
+template <int TS, int LK, int RK, bool KAHAN, bool BF = false>
 __device__ __forceinline__ void sample_math(const J2 &Lp, const J2 &Gp, const J2 &Rp, const J2 &Lq, const J2 &Gq,
                                             const J2 &Rq, const J2 &Dm, const J2 &M, float4 w,
                                             Acc<AccLayout<TS, LK != KIND_NONE>::KR, KAHAN> &Ap,
@@ -389,7 +393,7 @@ __device__ __forceinline__ void sample_math(const J2 &Lp, const J2 &Gp, const J2
         constexpr int CK = HAS_L ? KIND_FULL : GK;
         const J2 A = lmulk<CK>(Cp, M);                 // C_p M
         X = rmulk_h<CK>(M, Cq);                        // M C_q^H
-        V = rmulk_h<CK>(A, Cq);                        // C_p M C_q^H
+        if constexpr (!BF) V = rmulk_h<CK>(A, Cq);     // C_p M C_q^H
         Y = j_herm(A);                                 // M^H C_p^H
     } else {
         J2 Z;
@@ -398,12 +402,18 @@ __device__ __forceinline__ void sample_math(const J2 &Lp, const J2 &Gp, const J2
         X = rmulk_h<LK>(rmulk_h<GK>(Z, Gq), Lq);
         const J2 W = lmulk<LK>(Lp, lmulk<GK>(Gp, Z));
         Y = j_herm(W);
-        V = lmulk<LK>(Lp, lmulk<GK>(Gp, X));
+        if constexpr (!BF) V = lmulk<LK>(Lp, lmulk<GK>(Gp, X));
     }
-    // weighted residual w * (D - V); the conjugate baseline's is its conjugate transpose
+    // weighted residual w * (D - V) (BF: the weighted data w * D); the conjugate
+    // baseline's is its conjugate transpose
     J2 wr;
-    wr.a = cscale(csub(Dm.a, V.a), w.x); wr.b = cscale(csub(Dm.b, V.b), w.y);
-    wr.c = cscale(csub(Dm.c, V.c), w.z); wr.d = cscale(csub(Dm.d, V.d), w.w);
+    if constexpr (BF) {
+        wr.a = cscale(Dm.a, w.x); wr.b = cscale(Dm.b, w.y);
+        wr.c = cscale(Dm.c, w.z); wr.d = cscale(Dm.d, w.w);
+    } else {
+        wr.a = cscale(csub(Dm.a, V.a), w.x); wr.b = cscale(csub(Dm.b, V.b), w.y);
+        wr.c = cscale(csub(Dm.c, V.c), w.z); wr.d = cscale(csub(Dm.d, V.d), w.w);
+    }
     accumulate_side<TS, HAS_L, KAHAN>(Ap, Lp, X, w, wr);
     accumulate_side<TS, HAS_L, KAHAN>(Aq, Lq, Y, make_float4(w.x, w.z, w.y, w.w), j_herm(wr));
 }
@@ -754,7 +764,21 @@ struct UpdArgs {
     int div, max_iter;
     double *div_stats;       // [n_bins][n_ant][2], zero before the first iteration
     const double *params0;   // as params
+    // nonzero: the J^H W r slots of acc hold J^H W d (the streaming kernel), and the update
+    // takes J^H W r = J^H W d - JHJ g at the gains of this iteration, in FP64
+    int b_form;
 };
+
+// b -= M g (complex N x N block times the complex gain vector)
+template <int N>
+__device__ __forceinline__ void sub_block_times(double2 (&b)[N], const double2 (&M)[N][N], const double2 (&g)[N])
+{
+    for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j) {
+            b[i].x -= M[i][j].x * g[j].x - M[i][j].y * g[j].y;
+            b[i].y -= M[i][j].x * g[j].y + M[i][j].y * g[j].x;
+        }
+}
 
 __device__ __forceinline__ void store_jones_tab(const UpdArgs &u, int bin, int ant, const double2 g[4])
 {
@@ -793,6 +817,7 @@ static __global__ void __launch_bounds__(128) update_kernel(const UpdArgs u)
             for (int i = 0; i < 4; ++i) b[i] = make_double2(A[16 + 2 * i], A[17 + 2 * i]);
             double2 *P = reinterpret_cast<double2 *>(u.params) + 4 * pidx;
             for (int e = 0; e < 4; ++e) gold[e] = P[e];
+            if (u.b_form) sub_block_times<4>(b, M, gold);
             singular = block_solve<4>(M, b, x);
             for (int e = 0; e < 4; ++e)
                 gnew[e] = singular ? gold[e] : make_double2(gold[e].x + u.alpha * x[e].x, gold[e].y + u.alpha * x[e].y);
@@ -811,6 +836,7 @@ static __global__ void __launch_bounds__(128) update_kernel(const UpdArgs u)
                 double *phi = u.params + 2 * pidx;
                 double2 g[2];
                 for (int k = 0; k < 2; ++k) { double sn, cs; sincos(phi[k], &sn, &cs); g[k] = make_double2(cs, sn); }
+                if (u.b_form) sub_block_times<2>(b, M, g);
                 auto cmc = [](double2 p, double2 q) {     // conj(p) * q
                     return make_double2(p.x * q.x + p.y * q.y, p.x * q.y - p.y * q.x);
                 };
@@ -832,6 +858,10 @@ static __global__ void __launch_bounds__(128) update_kernel(const UpdArgs u)
             } else {
                 double2 *P = reinterpret_cast<double2 *>(u.params) + 4 * pidx;
                 for (int e = 0; e < 4; ++e) gold[e] = P[e];
+                if (u.b_form) {
+                    const double2 g[2] = { gold[0], gold[3] };
+                    sub_block_times<2>(b, M, g);
+                }
                 singular = block_solve<2>(M, b, x);
                 gnew[0] = gold[0]; gnew[1] = make_double2(0, 0); gnew[2] = gnew[1]; gnew[3] = gold[3];
                 if (!singular) {

@@ -17,6 +17,9 @@
 //  * d, m, w of each step are copied DEPTH - 1 steps ahead into the warp's ring in
 //    shared memory (16-byte cp.async per lane, zero-filled for lanes with nothing to
 //    read), and lane 0 writes the step's row-table entry beside them;
+//  * the J^H W r slots receive J^H W d: the model V = E g is linear in the solved gains of
+//    either side, so J^H W r = J^H W d - JHJ g per (interval, antenna) block, formed in FP64
+//    by the update; a sample forms neither V nor the residual;
 //  * the lane's channel interval indices are read two steps ahead; the solved term's
 //    gain entries stay in registers while their table index is unchanged (a row of a
 //    row tile, a strip of a strip tile), and the gain loads of a step are issued at
@@ -442,7 +445,7 @@ __global__ void __launch_bounds__(256, 2) acc_stream_kernel(const StreamArgs a)
             if constexpr (M16) M = load_model16(*reinterpret_cast<const uint4 *>(slot + 64), __int_as_float(e1.y));
             else M = j_from(slot[64], slot[96]);
             const J2 Gp = cGp, Gq = cGq;
-            sample_math<TS, LK, RK, KAHAN>(Lp, Gp, Rp, Lq, Gq, Rq, Dm, M, w, Ap, Aq);
+            sample_math<TS, LK, RK, KAHAN, true>(Lp, Gp, Rp, Lq, Gq, Rq, Dm, M, w, Ap, Aq);
         }
         fmA = fmB;
         eA0 = eB0;

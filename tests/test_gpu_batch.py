@@ -199,9 +199,10 @@ def test_size_split_matches_oracle_and_the_single_class_solve():
     assert st1.split <= 0 and st1.n_small == 0
     assert st2.split == split and st2.n_small == int(np.sum(samples < split)) > 0
     assert st2.small_threads == 64 and st2.small_ctas_per_sm == 4
-    assert np.array_equal(f1, f2) and np.array_equal(it1, it2)
     # CTAs of another size add the FP32 per-sample terms in another order, so the two solves agree
-    # to the bound of the launch-shape test above (1e-5), not bit for bit (seen: 1.4e-6)
+    # to the bound of the launch-shape test above (1e-5), not bit for bit (seen: 1.4e-6), and an
+    # interval whose last relative change lies at the tolerance may stop one iteration apart
+    assert np.array_equal(f1, f2) and np.max(np.abs(it1.astype(int) - it2.astype(int))) <= 1
     np.testing.assert_allclose(g2, g1, rtol=0, atol=1e-5)
     compare(b, g2, f2, it2)
     S.close()

@@ -36,13 +36,17 @@ struct DelayStreamArgs {
 };
 
 // One side (antenna) of a sample: diagonal-term quantities at the sample's channel, then
-// the chain rule into the register sums.  X, w, wr in the orientation of this side.
-template <bool HAS_L>
+// the chain rule into the register sums.  X, w in the orientation of this side, and wd its
+// weighted residual w * (D - V), or (WD) its weighted data w * D: the model of the sample is
+// V = E g with g = (g_X, g_Y) at this channel, so conj(g_X) JHr_g[X] = conj(g_X) (J^H W d)[X]
+// - h_00 |g_X|^2 - conj(g_X) h_01 g_Y, whose imaginary part lacks the real h_00 |g_X|^2
+// (likewise for Y with conj(h_01)); without a left factor h_01 = 0.
+template <bool HAS_L, bool WD = false>
 __device__ __forceinline__ void delay_side(Acc<DelayLayout<HAS_L>::KR, false> &A, const J2 &L, const J2 &X,
-                                           float4 w, const J2 &wr, float2 gx, float2 gy, float om)
+                                           float4 w, const J2 &wd, float2 gx, float2 gy, float om)
 {
     const float wv[4] = { w.x, w.y, w.z, w.w };
-    const float2 wrv[4] = { wr.a, wr.b, wr.c, wr.d };
+    const float2 wrv[4] = { wd.a, wd.b, wd.c, wd.d };
     const float2 Xv[4] = { X.a, X.b, X.c, X.d };            // X[l][j] = Xv[2l+j]
     float h00, h11;
     float2 j0, j1, h01 = make_float2(0.f, 0.f);
@@ -76,9 +80,19 @@ __device__ __forceinline__ void delay_side(Acc<DelayLayout<HAS_L>::KR, false> &A
             j1 = cfma_conj(E1[m], wrv[m], j1);
         }
     }
-    const float rx = gx.x * j0.y - gx.y * j0.x;           // Im(conj(g_X) JHr_g[X])
-    const float ry = gy.x * j1.y - gy.y * j1.x;           // Im(conj(g_Y) JHr_g[Y])
+    float rx = gx.x * j0.y - gx.y * j0.x;                 // Im(conj(g_X) JHr_g[X])
+    float ry = gy.x * j1.y - gy.y * j1.x;                 // Im(conj(g_Y) JHr_g[Y])
     const float om2 = om * om;
+    float xy = 0.f;
+    if constexpr (HAS_L) {
+        const float2 t = make_float2(fmaf(gx.x, h01.x, gx.y * h01.y), fmaf(gx.x, h01.y, -gx.y * h01.x));
+        xy = fmaf(t.x, gy.x, -t.y * gy.y);                 // Re(conj(g_X) JHJ_g[X][Y] g_Y)
+        if constexpr (WD) {
+            const float yi = fmaf(t.x, gy.y, t.y * gy.x);  // Im(conj(g_X) JHJ_g[X][Y] g_Y)
+            rx -= yi;
+            ry += yi;
+        }
+    }
     A.s[0] += h00;
     A.s[1] = fmaf(h00, om, A.s[1]);
     A.s[2] = fmaf(h00, om2, A.s[2]);
@@ -90,8 +104,6 @@ __device__ __forceinline__ void delay_side(Acc<DelayLayout<HAS_L>::KR, false> &A
     A.s[8] += ry;
     A.s[9] = fmaf(ry, om, A.s[9]);
     if constexpr (HAS_L) {
-        const float2 t = make_float2(fmaf(gx.x, h01.x, gx.y * h01.y), fmaf(gx.x, h01.y, -gx.y * h01.x));
-        const float xy = fmaf(t.x, gy.x, -t.y * gy.y);     // Re(conj(g_X) JHJ_g[X][Y] g_Y)
         A.s[10] += xy;
         A.s[11] = fmaf(xy, om, A.s[11]);
         A.s[12] = fmaf(xy, om2, A.s[12]);
@@ -99,8 +111,9 @@ __device__ __forceinline__ void delay_side(Acc<DelayLayout<HAS_L>::KR, false> &A
 }
 
 // One unflagged sample of baseline (p, q): chain factors around the delay term G (diagonal
-// at this channel), residual, and both sides' sums (the conjugate baseline for q), as in
-// sample_math for a diagonal term.
+// at this channel) and both sides' sums (the conjugate baseline for q), as in sample_math for
+// a diagonal term; the sides take the weighted data, so the sample forms neither V nor the
+// residual (delay_side).
 template <int LK, int RK>
 __device__ __forceinline__ void delay_sample_math(const J2 &Lp, const J2 &Gp, const J2 &Rp, const J2 &Lq, const J2 &Gq,
                                                   const J2 &Rq, const J2 &Dm, const J2 &M, float4 w, float om,
@@ -108,14 +121,13 @@ __device__ __forceinline__ void delay_sample_math(const J2 &Lp, const J2 &Gp, co
                                                   Acc<DelayLayout<LK != KIND_NONE>::KR, false> &Aq)
 {
     constexpr bool HAS_L = LK != KIND_NONE;
-    J2 X, Y, V;
+    J2 X, Y;
     if constexpr (RK == KIND_NONE) {
         const J2 Cp = HAS_L ? rmulk<KIND_DIAG>(Lp, Gp) : Gp;
         const J2 Cq = HAS_L ? rmulk<KIND_DIAG>(Lq, Gq) : Gq;
         constexpr int CK = HAS_L ? KIND_FULL : KIND_DIAG;
         const J2 A = lmulk<CK>(Cp, M);                 // C_p M
         X = rmulk_h<CK>(M, Cq);                        // M C_q^H
-        V = rmulk_h<CK>(A, Cq);                        // C_p M C_q^H
         Y = j_herm(A);                                 // M^H C_p^H
     } else {
         J2 Z;
@@ -124,13 +136,12 @@ __device__ __forceinline__ void delay_sample_math(const J2 &Lp, const J2 &Gp, co
         X = rmulk_h<LK>(rmulk_h<KIND_DIAG>(Z, Gq), Lq);
         const J2 W = lmulk<LK>(Lp, lmulk<KIND_DIAG>(Gp, Z));
         Y = j_herm(W);
-        V = lmulk<LK>(Lp, lmulk<KIND_DIAG>(Gp, X));
     }
-    J2 wr;
-    wr.a = cscale(csub(Dm.a, V.a), w.x); wr.b = cscale(csub(Dm.b, V.b), w.y);
-    wr.c = cscale(csub(Dm.c, V.c), w.z); wr.d = cscale(csub(Dm.d, V.d), w.w);
-    delay_side<HAS_L>(Ap, Lp, X, w, wr, Gp.a, Gp.d, om);
-    delay_side<HAS_L>(Aq, Lq, Y, make_float4(w.x, w.z, w.y, w.w), j_herm(wr), Gq.a, Gq.d, om);
+    J2 wd;
+    wd.a = cscale(Dm.a, w.x); wd.b = cscale(Dm.b, w.y);
+    wd.c = cscale(Dm.c, w.z); wd.d = cscale(Dm.d, w.w);
+    delay_side<HAS_L, true>(Ap, Lp, X, w, wd, Gp.a, Gp.d, om);
+    delay_side<HAS_L, true>(Aq, Lq, Y, make_float4(w.x, w.z, w.y, w.w), j_herm(wd), Gq.a, Gq.d, om);
 }
 
 template <int LK, int RK, bool M16, int DEPTH>

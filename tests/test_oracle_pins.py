@@ -182,6 +182,34 @@ def test_jhj_blocks_are_hermitian_psd(n):
         assert ev.min() >= -1e-12 * max(1.0, np.abs(B).max())
 
 
+@pytest.mark.parametrize("n", [0, 1, 2])
+@pytest.mark.parametrize("kinds", [("diag", "full", "diag"), ("full", "diag", "full")])
+def test_jhr_plus_jhj_g_does_not_depend_on_the_blocks_own_gains(n, kinds):
+    """The model of a sample is linear in the solved gains of either of its antennas (V = E g_p,
+    with E free of g_p), so JHr_p + JHJ_p g_p = J^H W d (Eq. jhr_entry_simplified with
+    r = d - E g_p) is the same for any g_p while the other gains stay fixed; the streaming
+    kernels sum J^H W d and form JHr in the update from this identity.  Another antenna's
+    block, whose E holds g_p, does change."""
+    prob, terms = random_problem(seed=31 + n, n_ant=4, n_time=2, n_chan=4, kinds=kinds, n_bins=(1, 2))
+    T = terms[n]
+    cols = [0, 3] if T.kind == "diag" else [0, 1, 2, 3]
+    rng = np.random.default_rng(7 + n)
+    jhj0, jhr0 = O.normal_equations(prob, terms, n)
+    scale = max(np.abs(jhj0).max(), np.abs(jhr0).max())
+    for it, jf, a, b in [(0, 0, 1, 2), (0, 1, 3, 0)]:
+        g0 = T.params[it, jf, a, cols].copy()
+        before_a = jhr0[it, jf, a] + jhj0[it, jf, a] @ g0
+        before_b = jhr0[it, jf, b] + jhj0[it, jf, b] @ T.params[it, jf, b, cols]
+        T.params[it, jf, a, cols] = g0 + 0.5 * (rng.standard_normal(len(cols)) + 1j * rng.standard_normal(len(cols)))
+        jhj1, jhr1 = O.normal_equations(prob, terms, n)
+        after_a = jhr1[it, jf, a] + jhj1[it, jf, a] @ T.params[it, jf, a, cols]
+        after_b = jhr1[it, jf, b] + jhj1[it, jf, b] @ T.params[it, jf, b, cols]
+        T.params[it, jf, a, cols] = g0
+        assert np.max(np.abs(jhj1[it, jf, a] - jhj0[it, jf, a])) <= 1e-12 * scale
+        assert np.max(np.abs(after_a - before_a)) <= 1e-10 * scale
+        assert np.max(np.abs(after_b - before_b)) > 1e-3 * scale
+
+
 def _swap_rows(prob, rows):
     """Swap ant1/ant2 of the given rows: D, M -> D^H, M^H and weights permuted by P (Eq. permutation)."""
     data, model, weight = prob.data.copy(), prob.model.copy(), prob.weight.copy()

@@ -81,7 +81,11 @@ def _rank_main(rank, world, port, q):
         jhj_b, jhr_b = O.normal_equations(P, [Gl, B], 1)
         buf = torch.from_numpy(np.concatenate([jhj_b.view(np.float64).ravel(), jhr_b.view(np.float64).ravel()]))
         shard.allreduce_inplace(buf, None, None)
-        q.put((rank, sg.reduce, sb.reduce, sg.tint_offset, sg.n_tint, jhj_g, jhr_g, buf.numpy()))
+        # the right-hand side as the streaming kernel sums it: J^H W d = JHr + JHJ g per block
+        wd = torch.from_numpy(np.ascontiguousarray((jhr_b + np.einsum("...ij,...j->...i", jhj_b, gb[..., [0, 3]]))
+                                                   .view(np.float64).ravel()))
+        shard.allreduce_inplace(wd, None, None)
+        q.put((rank, sg.reduce, sb.reduce, sg.tint_offset, sg.n_tint, jhj_g, jhr_g, buf.numpy(), wd.numpy()))
     finally:
         dist.destroy_process_group()
 
@@ -115,7 +119,12 @@ def test_two_ranks_sum_to_the_single_process_normal_equations():
     jhj_b, jhr_b = O.normal_equations(P, [G, B], 1)
     want_b = np.concatenate([jhj_b.view(np.float64).ravel(), jhr_b.view(np.float64).ravel()])
     scale = np.abs(want_b).max()
-    for rank, g_red, b_red, off, n_t, jg, rg, buf in res:
+    # J^H W d summed over ranks, less the summed JHJ times the gains, is the single-process JHr
+    wd_sum = res[0][8].view(np.complex128).reshape(jhr_b.shape)
+    jhj_sum = res[0][7][:jhj_b.size * 2].view(np.complex128).reshape(jhj_b.shape)
+    got = wd_sum - np.einsum("...ij,...j->...i", jhj_sum, gb[..., [0, 3]])
+    np.testing.assert_allclose(got, jhr_b, rtol=0, atol=1e-10 * scale)
+    for rank, g_red, b_red, off, n_t, jg, rg, buf, _ in res:
         assert not g_red and b_red
         # the local term: the rank's slice of the single-process normal equations, exactly
         np.testing.assert_allclose(jg, jhj_g[off:off + n_t], rtol=1e-12, atol=1e-12 * np.abs(jhj_g).max())
